@@ -1,0 +1,616 @@
+"""FP64 CPU oracle of the micro-continuum (Volume-of-Solid) time step.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg may import this module.  It shares no code
+with the CUDA path; both read the same seeded inputs from
+``paper_2204_07019_gb300.inputs``.
+
+Follows Maes, Soulaine & Menke, "Improved Volume-of-Solid formulations for
+micro-continuum simulation of mineral dissolution at the pore-scale":
+
+* Sec. 2.2: volume-averaged fields, Darcy-Brinkman-Stokes momentum
+  (Eq. momentumDBS), Kozeny-Carman permeability (Eq. perm), averaged
+  advection-diffusion-reaction (Eq. concentrationDBS), solid mass balance
+  (Eq. mbs), continuity with a dissolution source (Eq. contDBS).
+* Sec. 2.3: iVoS reaction rate from the divergence of the reactive flux
+  (Eq. RfiVoS), split into the mass-transfer part eps div(Phi) and the
+  conservative part -div(eps Phi).
+* Sec. 2.4: VoS-psi (Eq. RfVoSpsi) with psi = lambda eps (1 - eps), lambda = 4,
+  and VoS-psi' with lambda refitted from global integrals.
+* App. B: order of the sub-steps (eps, permeability, velocity, pressure,
+  concentration, reaction rate), van Leer interpolation of convective and
+  reactive fluxes.
+* App. C: eps_f = 1e-4 inside the solid.
+
+The discrete scheme (a transient step on a MAC-staggered Cartesian grid; the
+paper's OpenFOAM discretisation is prior art) is fixed by the readings listed
+in the project's design notes; every reading is restated in the docstring
+of the function that applies it.
+
+Arrays are numpy float64 with shape (nz, ny, nx) (x fastest; nz = 1 in 2D).
+Face arrays for axis a (0 = x, 1 = y, 2 = z) have one more entry along that
+axis.  Each linear system is assembled face by face as a scipy.sparse
+matrix and solved by a library routine (SuperLU, or CG/BiCGStab for large
+grids); there is no blocking, fusion or reordering beyond that.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+VOS_PSI, VOS_PSI_PRIME, VOS_IVOS = 0, 1, 2
+WALL_YM, WALL_YP, WALL_ZM, WALL_ZP = 1, 2, 4, 8
+
+# numpy axis of spatial axis a (x is the last, fastest axis)
+def _nax(a):
+    return 2 - a
+
+
+def _shape(prm):
+    return (int(prm["nz"]), int(prm["ny"]), int(prm["nx"]))
+
+
+def _axes(prm):
+    return (0, 1) if int(prm["dim"]) == 2 else (0, 1, 2)
+
+
+def _sl(a, lo, hi):
+    """Slice [lo:hi] along spatial axis a of a (nz, ny, nx)-like array."""
+    s = [slice(None)] * 3
+    s[_nax(a)] = slice(lo, hi)
+    return tuple(s)
+
+
+# --------------------------------------------------------------------------
+# Closure relations
+# --------------------------------------------------------------------------
+
+def kozeny_carman_kinv(eps, k0):
+    """Inverse permeability k^-1 = (1 - eps)^2 / (k0 eps^3)  (Eq. perm, Sec. 2.2).
+
+    Stored as the inverse so that it is finite (zero) in pure fluid.
+    """
+    return (1.0 - eps) ** 2 / (k0 * eps ** 3)
+
+
+def van_leer_psi(r):
+    """van Leer limiter psi(r) = (r + |r|) / (1 + |r|)  (ref. 1974-vanLeer, App. B)."""
+    return (r + np.abs(r)) / (1.0 + np.abs(r))
+
+
+def van_leer_weight(cUU, cU, cD, has_uu):
+    """Weight w in c_f = c_U + w (c_D - c_U), w = psi(r)/2, r = (c_U - c_UU)/(c_D - c_U).
+
+    Reading: a far-upwind cell outside the domain takes the zero-gradient
+    ghost (r = 0, w = 0); |c_D - c_U| <= 1e-300 gives w = 0.
+    """
+    den = cD - cU
+    ok = has_uu & (np.abs(den) > 1e-300)
+    r = np.where(ok, (cU - cUU) / np.where(ok, den, 1.0), 0.0)
+    return np.where(ok, 0.5 * van_leer_psi(r), 0.0)
+
+
+# --------------------------------------------------------------------------
+# Geometry helpers on the cell grid
+# --------------------------------------------------------------------------
+
+def central_gradient(eps, dx, axes):
+    """Centred gradient of eps with zero-gradient ghosts at every boundary.
+
+    Used by VoS-psi (Sec. 2.4: "centered difference scheme for the gradient")
+    and for the tangential part of the iVoS face normal.  Returns a list of
+    3 arrays (zero for axes not in ``axes``).
+    """
+    g = [np.zeros_like(eps) for _ in range(3)]
+    for a in axes:
+        n = eps.shape[_nax(a)]
+        lo = np.concatenate([np.take(eps, [0], axis=_nax(a)),
+                             np.take(eps, np.arange(0, n - 1), axis=_nax(a))], axis=_nax(a))
+        hi = np.concatenate([np.take(eps, np.arange(1, n), axis=_nax(a)),
+                             np.take(eps, [n - 1], axis=_nax(a))], axis=_nax(a))
+        g[a] = (hi - lo) / (2.0 * dx)
+    return g
+
+
+def face_average(cell, a):
+    """Arithmetic mean of the two cells adjacent to each interior face along a."""
+    n = cell.shape[_nax(a)]
+    return 0.5 * (cell[_sl(a, 0, n - 1)] + cell[_sl(a, 1, n)])
+
+
+# --------------------------------------------------------------------------
+# Linear solves (library primitives)
+# --------------------------------------------------------------------------
+
+def _solve(A, b, symmetric, solver, rtol):
+    A = A.tocsr()
+    if solver == "direct" or A.shape[0] <= 4096:
+        return spla.spsolve(A.tocsc(), b)
+    d = A.diagonal()
+    M = sp.diags(1.0 / d)
+    bn = np.linalg.norm(b)
+    if bn == 0.0:
+        return np.zeros_like(b)
+    if symmetric:
+        x, info = spla.cg(A, b, rtol=rtol, atol=0.0, M=M, maxiter=200000)
+    else:
+        x, info = spla.bicgstab(A, b, rtol=rtol, atol=0.0, M=M, maxiter=200000)
+    if info != 0:
+        raise RuntimeError(f"oracle iterative solve failed (info={info})")
+    return x
+
+
+# --------------------------------------------------------------------------
+# State
+# --------------------------------------------------------------------------
+
+def init_state(eps_s, prm):
+    """Initial fields (App. C: eps_f = max(1 - eps_s, 1e-4); reading: u = p = c = 0).
+
+    The inlet faces carry u_in from t = 0 (acid injected at t = 0, Sec. 3.1).
+    """
+    shp = _shape(prm)
+    eps_s = np.asarray(eps_s, dtype=np.float64).reshape(shp)
+    eps = np.maximum(1.0 - eps_s, prm["eps_min"])
+    u = []
+    for a in range(3):
+        fs = list(shp)
+        fs[_nax(a)] += 1
+        u.append(np.zeros(fs))
+    u[0][_sl(0, 0, 1)] = prm["u_in"]
+    if int(prm["dim"]) == 2:
+        u[2] = np.zeros((0,))
+    z = np.zeros(shp)
+    return dict(eps=eps, c=z.copy(), p=z.copy(), u=u, R=z.copy(), Rf=z.copy(),
+                t=0.0, step=0)
+
+
+# --------------------------------------------------------------------------
+# S1: solid update
+# --------------------------------------------------------------------------
+
+def solid_update(eps, R, dt, prm):
+    """eps^{n+1} = clamp(eps^n + dt V_m R^n, eps_min, 1)  (Eq. mbs, Sec. 2.2).
+
+    Reading: explicit Euler in time with the rate of the previous step; the
+    clamp keeps eps >= eps_min (App. C).  Returns (eps_new, clamp_excess)
+    where clamp_excess = sum(raw - clamped) * V.
+    """
+    raw = eps + dt * prm["Vm"] * R
+    new = np.clip(raw, prm["eps_min"], 1.0)
+    V = prm["dx"] ** int(prm["dim"])
+    return new, float(np.sum(raw - new) * V)
+
+
+# --------------------------------------------------------------------------
+# S2: momentum predictor
+# --------------------------------------------------------------------------
+
+def _face_unknown_range(a, shp):
+    """Index range along a of the unknown faces of component a.
+
+    x: faces 1..nx (face 0 = inlet, fixed u_in; face nx = outlet, unknown).
+    y, z: faces 1..n-1 (boundary faces carry zero normal velocity).
+    """
+    n = shp[_nax(a)]
+    return (1, n + 1) if a == 0 else (1, n)
+
+
+def momentum_system(a, eps, p, u_old, dt, prm):
+    """Linear system for the face velocity component a (Eq. momentumDBS, Sec. 2.2).
+
+    Multiplying Eq. momentumDBS by eps and dropping the inertia term
+    (reading: creeping flow, Re = Pe/Sc <= 0.1) gives, per face f,
+
+      (1/dt + nu eps_f k^-1_f) u_f - nu lap(u)_f = u^n_f/dt - eps_f (grad p^n)_f
+
+    eps_f, k^-1_f: arithmetic means of the adjacent cells (the outlet face
+    takes its one cell).  lap: 5/7-point with ghosts -- no-slip walls and the
+    inlet plane for tangential components: ghost = -u (zero at the boundary);
+    outlet and free-slip sides: ghost = +u; fixed boundary faces (inlet u_in,
+    zero normal velocity on walls) enter as known values.  Outlet pressure
+    p = 0 on the boundary face (ghost p = -p_P).
+    Returns (A, b, idx) with idx the flat face indices of the unknowns.
+    """
+    shp = _shape(prm)
+    axes = _axes(prm)
+    dx, nu = prm["dx"], prm["nu"]
+    fs = list(shp)
+    fs[_nax(a)] += 1
+    fs = tuple(fs)
+    lo, hi = _face_unknown_range(a, shp)
+    unk = np.zeros(fs, dtype=bool)
+    unk[_sl(a, lo, hi)] = True
+    nun = int(unk.sum())
+    num = -np.ones(fs, dtype=np.int64)
+    num[unk] = np.arange(nun)
+    # known boundary face values (inlet u_in for x, zero otherwise)
+    known = np.zeros(fs)
+    if a == 0:
+        known[_sl(0, 0, 1)] = prm["u_in"]
+
+    kinv = kozeny_carman_kinv(eps, prm["k0"])
+    n_a = shp[_nax(a)]
+    eps_f = np.zeros(fs)
+    kin_f = np.zeros(fs)
+    gp = np.zeros(fs)
+    eps_f[_sl(a, 1, n_a)] = face_average(eps, a)
+    kin_f[_sl(a, 1, n_a)] = face_average(kinv, a)
+    gp[_sl(a, 1, n_a)] = (p[_sl(a, 1, n_a)] - p[_sl(a, 0, n_a - 1)]) / dx
+    if a == 0:  # outlet face: one-sided values, Dirichlet p = 0
+        eps_f[_sl(0, n_a, n_a + 1)] = eps[_sl(0, n_a - 1, n_a)]
+        kin_f[_sl(0, n_a, n_a + 1)] = kinv[_sl(0, n_a - 1, n_a)]
+        gp[_sl(0, n_a, n_a + 1)] = -2.0 * p[_sl(0, n_a - 1, n_a)] / dx
+
+    diag = 1.0 / dt + nu * eps_f * kin_f
+    rhs = u_old / dt - eps_f * gp
+    rows, cols, vals = [], [], []
+    coef = nu / dx ** 2
+    wall = int(prm["wall_mask"])
+    for b in axes:
+        nb_len = fs[_nax(b)]
+        for sgn in (-1, 1):
+            # neighbour index along b for every face
+            idx_b = np.arange(nb_len).reshape([-1 if k == _nax(b) else 1 for k in range(3)])
+            nidx = idx_b + sgn
+            inside = (nidx >= 0) & (nidx < nb_len)
+            inside = np.broadcast_to(inside, fs)
+            # ghost factor s for neighbours outside the face array
+            if b == 0:
+                s_ghost = -1.0 if sgn < 0 else 1.0   # inlet plane: 0; outlet: zero-gradient
+            else:
+                bit = (WALL_YM if sgn < 0 else WALL_YP) if b == 1 else (WALL_ZM if sgn < 0 else WALL_ZP)
+                s_ghost = -1.0 if (wall & bit) else 1.0
+            # contributions of unknown faces
+            sel = unk & ~inside
+            diag = diag + np.where(sel, coef * (1.0 - s_ghost), 0.0)
+            # inside neighbours
+            shifted_num = np.full(fs, -1, dtype=np.int64)
+            shifted_known = np.zeros(fs)
+            src = _sl(b, max(sgn, 0), nb_len + min(sgn, 0))
+            dst = _sl(b, max(-sgn, 0), nb_len + min(-sgn, 0))
+            shifted_num[dst] = num[src]
+            shifted_known[dst] = known[src]
+            m_unk = unk & inside & (shifted_num >= 0)
+            m_fix = unk & inside & (shifted_num < 0)
+            diag = diag + np.where(m_unk | m_fix, coef, 0.0)
+            rhs = rhs + np.where(m_fix, coef * shifted_known, 0.0)
+            rows.append(num[m_unk]); cols.append(shifted_num[m_unk])
+            vals.append(np.full(int(m_unk.sum()), -coef))
+    rows.append(num[unk]); cols.append(num[unk]); vals.append(diag[unk])
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(nun, nun)).tocsr()
+    return A, rhs[unk], unk
+
+
+# --------------------------------------------------------------------------
+# S3: pressure Poisson and projection
+# --------------------------------------------------------------------------
+
+def divergence(u, prm):
+    """Cell divergence of a face field: sum over faces of the outward flux / dx."""
+    shp = _shape(prm)
+    div = np.zeros(shp)
+    for a in _axes(prm):
+        n = shp[_nax(a)]
+        div += (u[a][_sl(a, 1, n + 1)] - u[a][_sl(a, 0, n)]) / prm["dx"]
+    return div
+
+
+def pressure_system(eps, ustar, R, dt, prm):
+    """Pressure-correction system  -div(eps_f grad phi) = -(div u* - s)/dt.
+
+    The correction u^{n+1} = u* - dt eps_f grad phi makes div u^{n+1} = s with
+    s = R V_m (1 - rho_s/rho)  (Eq. contDBS; zero for rho_s = rho, the
+    quasi-static continuity of Eq. contDBSQS).  Boundary conditions: zero
+    normal gradient at the inlet and walls (velocity prescribed), phi = 0 on
+    the outlet faces (ghost -phi_P).  Face coefficient eps_f = mean of the two
+    cells.
+    """
+    shp = _shape(prm)
+    N = int(np.prod(shp))
+    dx = prm["dx"]
+    num = np.arange(N).reshape(shp)
+    rows, cols, vals = [], [], []
+    diag = np.zeros(shp)
+    for a in _axes(prm):
+        n = shp[_nax(a)]
+        ef = face_average(eps, a) / dx ** 2
+        P = num[_sl(a, 0, n - 1)].ravel(); Q = num[_sl(a, 1, n)].ravel(); cf = ef.ravel()
+        rows += [P, Q, P, Q]; cols += [P, Q, Q, P]; vals += [cf, cf, -cf, -cf]
+    # outlet Dirichlet faces
+    nx = shp[2]
+    diag[_sl(0, nx - 1, nx)] += 2.0 * eps[_sl(0, nx - 1, nx)] / dx ** 2
+    rows.append(num.ravel()); cols.append(num.ravel()); vals.append(diag.ravel())
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(N, N)).tocsr()
+    s = R * prm["Vm"] * (1.0 - prm["rho_ratio"])
+    b = -(divergence(ustar, prm) - s) / dt
+    return A, b.ravel()
+
+
+def project(ustar, phi, eps, dt, prm):
+    """u^{n+1} = u* - dt eps_f grad phi on interior and outlet faces."""
+    shp = _shape(prm)
+    dx = prm["dx"]
+    u = [x.copy() for x in ustar]
+    for a in _axes(prm):
+        n = shp[_nax(a)]
+        ef = face_average(eps, a)
+        u[a][_sl(a, 1, n)] -= dt * ef * (phi[_sl(a, 1, n)] - phi[_sl(a, 0, n - 1)]) / dx
+    nx = shp[2]
+    u[0][_sl(0, nx, nx + 1)] -= dt * eps[_sl(0, nx - 1, nx)] * (-2.0 * phi[_sl(0, nx - 1, nx)]) / dx
+    return u
+
+
+# --------------------------------------------------------------------------
+# S4: explicit van Leer advection
+# --------------------------------------------------------------------------
+
+def _upwind_triplets(c, a, positive):
+    """(c_UU, c_U, c_D, has_UU) on the interior faces along a.
+
+    ``positive``: boolean array on those faces, True where the upwind cell is
+    the minus-side cell.
+    """
+    n = c.shape[_nax(a)]
+    m1 = c[_sl(a, 0, n - 1)]          # minus-side cell of face m (cells m-1)
+    p0 = c[_sl(a, 1, n)]              # plus-side cell (m)
+    # far cells: m-2 for positive, m+1 for negative
+    mm2 = np.zeros_like(m1); has_m = np.zeros(m1.shape, dtype=bool)
+    pp1 = np.zeros_like(m1); has_p = np.zeros(m1.shape, dtype=bool)
+    if n >= 3:
+        mm2[_sl(a, 1, n - 1)] = c[_sl(a, 0, n - 2)]; has_m[_sl(a, 1, n - 1)] = True
+        pp1[_sl(a, 0, n - 2)] = c[_sl(a, 2, n)]; has_p[_sl(a, 0, n - 2)] = True
+    cU = np.where(positive, m1, p0)
+    cD = np.where(positive, p0, m1)
+    cUU = np.where(positive, mm2, pp1)
+    hUU = np.where(positive, has_m, has_p)
+    return cUU, cU, cD, hUU
+
+
+def advection_divergence(c, u, prm):
+    """Cell divergence of the explicit van Leer convective flux c_f u_f (App. B).
+
+    Interior faces: c_f = van Leer interpolation upwind of sign(u_f)
+    (u_f >= 0: minus cell upwind).  Inlet faces: inflow u_in c_in.  Outlet
+    faces: c of the last cell.  Wall faces: zero flux.
+    """
+    shp = _shape(prm)
+    dx = prm["dx"]
+    div = np.zeros(shp)
+    for a in _axes(prm):
+        n = shp[_nax(a)]
+        F = np.zeros_like(u[a])
+        uf = u[a][_sl(a, 1, n)]
+        cUU, cU, cD, h = _upwind_triplets(c, a, uf >= 0.0)
+        cf = cU + van_leer_weight(cUU, cU, cD, h) * (cD - cU)
+        F[_sl(a, 1, n)] = uf * cf
+        if a == 0:
+            F[_sl(0, 0, 1)] = u[0][_sl(0, 0, 1)] * prm["c_in"]
+            F[_sl(0, n, n + 1)] = u[0][_sl(0, n, n + 1)] * c[_sl(0, n - 1, n)]
+        div += (F[_sl(a, 1, n + 1)] - F[_sl(a, 0, n)]) / dx
+    return div
+
+
+# --------------------------------------------------------------------------
+# S6: reactive surface
+# --------------------------------------------------------------------------
+
+def vos_lambda(eps, prm):
+    """VoS-psi' parameter lambda(eps) = int |grad eps| / int |grad eps| eps (1 - eps)
+    (Sec. 2.4), from the centred gradient.  Reading: a vanishing denominator
+    (< 1e-300 x numerator, or a zero numerator) gives lambda = 4."""
+    g = central_gradient(eps, prm["dx"], _axes(prm))
+    mag = np.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2)
+    num = float(np.sum(mag))
+    den = float(np.sum(mag * eps * (1.0 - eps)))
+    if num == 0.0 or den < 1e-300 * num:
+        return 4.0
+    return num / den
+
+
+def vos_coefficient(eps, prm, lam):
+    """k_c psi |grad eps| with psi = lam eps (1 - eps), centred gradient
+    (Eq. RfVoSpsi, Sec. 2.4); R = coefficient * c."""
+    g = central_gradient(eps, prm["dx"], _axes(prm))
+    mag = np.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2)
+    return prm["kc"] * lam * eps * (1.0 - eps) * mag
+
+
+def ivos_faces(eps, c_old, prm):
+    """Per-face data of the iVoS reactive flux (Sec. 2.3, App. B).
+
+    For each interior face along a: g_f has normal part (eps_plus - eps_minus)/dx
+    and tangential parts equal to the mean of the two cells' centred
+    gradients; n_f = -g_f / (|g_f| + delta) with delta = 1e-8/dx (reading);
+    Phi_R . e_a = k_c c_f n_a.  Upwind = the cell the flux leaves
+    (n_a > 0: minus cell).  c_f uses the van Leer weight frozen from c^n;
+    eps_f is the van Leer interpolation of eps.
+    Returns per axis a dict with n_a (normal component), positive (bool),
+    w (frozen weight) and eps_vl.
+    """
+    axes = _axes(prm)
+    dx = prm["dx"]
+    g = central_gradient(eps, dx, axes)
+    delta = 1e-8 / dx
+    out = {}
+    shp = _shape(prm)
+    for a in axes:
+        n = shp[_nax(a)]
+        gn = (eps[_sl(a, 1, n)] - eps[_sl(a, 0, n - 1)]) / dx
+        g2 = gn ** 2
+        for b in axes:
+            if b != a:
+                g2 = g2 + face_average(g[b], a) ** 2
+        na = -gn / (np.sqrt(g2) + delta)
+        pos = na > 0.0
+        cUU, cU, cD, h = _upwind_triplets(c_old, a, pos)
+        w = van_leer_weight(cUU, cU, cD, h)
+        eUU, eU, eD, h2 = _upwind_triplets(eps, a, pos)
+        evl = eU + van_leer_weight(eUU, eU, eD, h2) * (eD - eU)
+        out[a] = dict(na=na, pos=pos, w=w, eps_vl=evl)
+    return out
+
+
+def ivos_face_flux(c, a, fd, prm):
+    """F_f / V = k_c n_a c_f / dx on interior faces along a (sign along +a),
+    with c_f = c_U + w (c_D - c_U) and the frozen weight w."""
+    n = c.shape[_nax(a)]
+    m1 = c[_sl(a, 0, n - 1)]; p0 = c[_sl(a, 1, n)]
+    cU = np.where(fd["pos"], m1, p0); cD = np.where(fd["pos"], p0, m1)
+    cf = cU + fd["w"] * (cD - cU)
+    return prm["kc"] * fd["na"] * cf / prm["dx"]
+
+
+def ivos_rates(eps, c, faces, prm):
+    """R_f = eps div(Phi) (mass transfer) and R = eps div(Phi) - div(eps_vl Phi)
+    (Eq. RfiVoS, Sec. 2.3).  Reading: R_f is the transport sink and R the
+    solid source, so the reactant consumed in one cell may dissolve solid in
+    its neighbour; boundary faces carry no reactive flux."""
+    shp = _shape(prm)
+    divF = np.zeros(shp)
+    divEF = np.zeros(shp)
+    for a in _axes(prm):
+        n = shp[_nax(a)]
+        F = ivos_face_flux(c, a, faces[a], prm)
+        EF = faces[a]["eps_vl"] * F
+        divF[_sl(a, 0, n - 1)] += F; divF[_sl(a, 1, n)] -= F
+        divEF[_sl(a, 0, n - 1)] += EF; divEF[_sl(a, 1, n)] -= EF
+    Rf = eps * divF
+    return Rf - divEF, Rf
+
+
+# --------------------------------------------------------------------------
+# S5: implicit diffusion-reaction for the concentration
+# --------------------------------------------------------------------------
+
+def transport_system(eps_old, eps, c_old, u, prm, dt, kr=None, faces=None):
+    """Implicit transport system for c^{n+1} (Eq. concentrationDBS, Sec. 2.2).
+
+      eps^{n+1} c^{n+1}/dt - div(eps_f D grad c^{n+1}) + zeta R_f(c^{n+1})
+          = eps^n c^n/dt - div(c^n_f u^{n+1})
+
+    with D* = D (Sec. 2.2), eps_f = mean of the two cells, c = c_in on the
+    inlet faces (ghost 2 c_in - c_P), zero diffusive flux at the outlet and
+    walls.  R_f: VoS-psi(') -> kr c (diagonal, kr from ``vos_coefficient``);
+    iVoS -> eps div(Phi_R) with the frozen-weight face values.
+    Reading: the stoichiometric coefficient zeta multiplies the transport
+    sink (boundary condition Eq. bcc1).
+    """
+    shp = _shape(prm)
+    N = int(np.prod(shp))
+    dx, D, zeta = prm["dx"], prm["D"], prm["zeta"]
+    num = np.arange(N).reshape(shp)
+    rows, cols, vals = [], [], []
+    diag = eps / dt
+    rhs = eps_old * c_old / dt - advection_divergence(c_old, u, prm)
+    for a in _axes(prm):
+        n = shp[_nax(a)]
+        ef = D * face_average(eps, a) / dx ** 2
+        P = num[_sl(a, 0, n - 1)].ravel(); Q = num[_sl(a, 1, n)].ravel(); cf = ef.ravel()
+        rows += [P, Q, P, Q]; cols += [P, Q, Q, P]; vals += [cf, cf, -cf, -cf]
+    inl = _sl(0, 0, 1)
+    diag = diag.copy()
+    diag[inl] += 2.0 * D * eps[inl] / dx ** 2
+    rhs[inl] += 2.0 * D * eps[inl] * prm["c_in"] / dx ** 2
+    if kr is not None:
+        diag = diag + zeta * kr
+    if faces is not None:
+        kc = prm["kc"]
+        for a in _axes(prm):
+            n = shp[_nax(a)]
+            fd = faces[a]
+            Pm = num[_sl(a, 0, n - 1)]; Qp = num[_sl(a, 1, n)]
+            U = np.where(fd["pos"], Pm, Qp); Dn = np.where(fd["pos"], Qp, Pm)
+            s = kc * fd["na"] / dx
+            eP = eps[_sl(a, 0, n - 1)]; eQ = eps[_sl(a, 1, n)]
+            for row, sign, ecell in ((Pm, 1.0, eP), (Qp, -1.0, eQ)):
+                coef = zeta * sign * ecell * s
+                rows += [row.ravel(), row.ravel()]
+                cols += [U.ravel(), Dn.ravel()]
+                vals += [(coef * (1.0 - fd["w"])).ravel(), (coef * fd["w"]).ravel()]
+    rows.append(num.ravel()); cols.append(num.ravel()); vals.append(diag.ravel())
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(N, N)).tocsr()
+    return A, rhs.ravel()
+
+
+# --------------------------------------------------------------------------
+# One time step
+# --------------------------------------------------------------------------
+
+def step(state, dt, prm, solver="direct", rtol=1e-13):
+    """One micro-continuum time step (App. B order, transient reading).
+
+    S1 eps (Eq. mbs) and k (Eq. perm); S2 momentum predictor per component;
+    S3 pressure correction and projection; S4 explicit van Leer advection;
+    S5 implicit diffusion + reaction; S6 reaction rates R, R_f from c^{n+1};
+    S7 diagnostics.  Returns (new_state, stats).
+    """
+    shp = _shape(prm)
+    axes = _axes(prm)
+    method = int(prm["method"])
+    eps_old = state["eps"]
+    eps, excess = solid_update(eps_old, state["R"], dt, prm)
+    # S2
+    ustar = [x.copy() for x in state["u"]]
+    for a in axes:
+        A, b, unk = momentum_system(a, eps, state["p"], state["u"][a], dt, prm)
+        ustar[a][unk] = _solve(A, b, True, solver, rtol)
+    # S3
+    A, b = pressure_system(eps, ustar, state["R"], dt, prm)
+    phi = _solve(A, b, True, solver, rtol).reshape(shp)
+    u = project(ustar, phi, eps, dt, prm)
+    p = state["p"] + phi
+    # S5/S6
+    lam = float("nan")
+    if method == VOS_IVOS:
+        faces = ivos_faces(eps, state["c"], prm)
+        A, b = transport_system(eps_old, eps, state["c"], u, prm, dt, faces=faces)
+        c = _solve(A, b, False, solver, rtol).reshape(shp)
+        R, Rf = ivos_rates(eps, c, faces, prm)
+    else:
+        lam = prm["lam"] if method == VOS_PSI else vos_lambda(eps, prm)
+        kr = vos_coefficient(eps, prm, lam)
+        A, b = transport_system(eps_old, eps, state["c"], u, prm, dt, kr=kr)
+        c = _solve(A, b, True, solver, rtol).reshape(shp)
+        R = kr * c
+        Rf = R.copy()
+    new = dict(eps=eps, c=c, p=p, u=u, R=R, Rf=Rf, t=state["t"] + dt,
+               step=state["step"] + 1)
+    V = prm["dx"] ** int(prm["dim"])
+    stats = dict(lam=lam, clamp_excess=excess, porosity=float(np.mean(eps)),
+                 sum_R=float(np.sum(R) * V), sum_Rf=float(np.sum(Rf) * V),
+                 reactant=float(np.sum(eps * c) * V))
+    return new, stats
+
+
+def run(eps_s, prm, dts, solver="direct", rtol=1e-13):
+    st = init_state(eps_s, prm)
+    stats = []
+    for dt in dts:
+        st, s = step(st, dt, prm, solver=solver, rtol=rtol)
+        stats.append(s)
+    return st, stats
+
+
+def suggest_dt(state, prm, cfl, deps_max):
+    """min(cfl dx / max_f |u_f|/eps_f, deps_max / max |V_m R|)  (App. D:
+    the time step is limited by the largest change of eps per step;
+    reading: the convective CFL uses the interstitial speed |u_f|/eps_f)."""
+    shp = _shape(prm)
+    eps = state["eps"]
+    umax = 0.0
+    for a in _axes(prm):
+        n = shp[_nax(a)]
+        ef = np.zeros_like(state["u"][a])
+        ef[_sl(a, 1, n)] = face_average(eps, a)
+        ef[_sl(a, 0, 1)] = eps[_sl(a, 0, 1)]
+        ef[_sl(a, n, n + 1)] = eps[_sl(a, n - 1, n)]
+        umax = max(umax, float(np.max(np.abs(state["u"][a]) / ef)))
+    rmax = float(np.max(np.abs(prm["Vm"] * state["R"])))
+    dt1 = cfl * prm["dx"] / umax if umax > 0 else np.inf
+    dt2 = deps_max / rmax if rmax > 0 else np.inf
+    return min(dt1, dt2)

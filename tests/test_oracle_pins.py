@@ -1,0 +1,390 @@
+"""Pins of the CPU oracle against closed forms, invariants and the paper's
+identities (no GPU).  Each test names the passage it checks.
+
+These pin the oracle to something other than itself: discrete-exact
+closed-form profiles (Poiseuille, Brinkman, Darcy, 1D diffusion-reaction),
+exact identities of the method (Sec. 2.3 conservative term, Sec. 2.4
+global area, Eq. mbs mass balance), and limiting cases (sharp interface,
+front speed of Eq. Ws).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import vos_oracle as O
+from paper_2204_07019_gb300 import inputs as I
+
+
+def _run_to_steady(es, prm, dt, max_steps=600, tol_u=1e-13):
+    st = O.init_state(es, prm)
+    for _ in range(max_steps):
+        u0 = st["u"][0].copy()
+        p0 = st["p"].copy()
+        st, _ = O.step(st, dt, prm)
+        du = np.abs(st["u"][0] - u0).max()
+        dp = np.abs(st["p"] - p0).max()
+        if du < tol_u and dp < 1e-12 * max(1.0, np.abs(st["p"]).max()):
+            return st
+    raise AssertionError("no steady state")
+
+
+# ---------------------------------------------------------------- closures
+
+def test_kozeny_carman_values():
+    """Eq. perm: k = k0 eps^3/(1-eps)^2, stored as its inverse."""
+    k0 = 2.5e-3
+    assert O.kozeny_carman_kinv(np.array(1.0), k0) == 0.0
+    assert O.kozeny_carman_kinv(np.array(0.5), k0) == pytest.approx(0.25 / (k0 * 0.125), rel=1e-15)
+    e = 0.3
+    assert 1.0 / O.kozeny_carman_kinv(np.array(e), k0) == pytest.approx(k0 * e ** 3 / (1 - e) ** 2, rel=1e-14)
+
+
+def test_van_leer_limiter_values():
+    """van Leer (1974) limiter: psi(0)=0, psi(1)=1, psi(3)=3/2, psi(1/3)=1/2,
+    psi(r<0)=0, psi -> 2, symmetry psi(1/r) = psi(r)/r, TVD region."""
+    psi = O.van_leer_psi
+    assert psi(np.array(0.0)) == 0.0
+    assert psi(np.array(1.0)) == 1.0
+    assert psi(np.array(3.0)) == pytest.approx(1.5, rel=1e-15)
+    assert psi(np.array(1.0 / 3.0)) == pytest.approx(0.5, rel=1e-15)
+    assert psi(np.array(-2.0)) == 0.0
+    assert psi(np.array(1e12)) == pytest.approx(2.0, rel=1e-11)
+    r = np.geomspace(1e-3, 1e3, 61)
+    assert np.allclose(psi(1.0 / r), psi(r) / r, rtol=1e-14)
+    assert np.all(psi(r) <= np.minimum(2 * r, 2.0) + 1e-15)
+
+
+def test_van_leer_linear_profile_exact():
+    """A second-order TVD scheme reconstructs a linear profile exactly
+    (r = 1 -> c_f = midpoint), both flow directions; first face upwind."""
+    nx = 12
+    prm = I.make_params((1, 1, nx), Pe=1, Da=0, L=1, method="psi")
+    c = (3.0 + 0.5 * np.arange(nx))[None, None, :]
+    for sgn in (1.0, -1.0):
+        pos = np.full((1, 1, nx - 1), sgn > 0)
+        cUU, cU, cD, h = O._upwind_triplets(c, 0, pos)
+        cf = cU + O.van_leer_weight(cUU, cU, cD, h) * (cD - cU)
+        mid = 0.5 * (c[..., :-1] + c[..., 1:])
+        inner = slice(1, nx - 1) if sgn > 0 else slice(0, nx - 2)
+        assert np.allclose(cf[..., inner], mid[..., inner], rtol=0, atol=1e-14)
+        edge = 0 if sgn > 0 else nx - 2
+        assert cf[0, 0, edge] == cU[0, 0, edge]
+
+
+def test_advection_tvd_no_new_extrema():
+    """Explicit van Leer advection of a step at CFL 0.5 creates no new
+    extrema (TVD property of the limiter, ref. 1974-vanLeer)."""
+    nx = 64
+    prm = I.make_params((1, 1, nx), Pe=1, Da=0, L=1, method="psi", wall_mask=0)
+    u = [np.ones((1, 1, nx + 1)), np.zeros((1, 2, nx)), np.zeros((0,))]
+    c = np.zeros((1, 1, nx))
+    c[..., :20] = 1.0
+    for _ in range(40):
+        c = c - 0.5 * O.advection_divergence(c, u, prm)
+        assert c.min() >= -1e-15 and c.max() <= 1.0 + 1e-15
+
+
+# ---------------------------------------------------------------- flow
+
+def test_poiseuille_discrete_exact():
+    """Sec. 2.2 DBS in pure fluid reduces to Stokes: fully developed channel
+    flow.  With no-slip ghosts u_{-1} = -u_0 the discrete profile is exactly
+    u_j ~ y_j (H - y_j) + dx^2/4, y_j = (j + 1/2) dx, mean = u_in."""
+    for ny in (6, 9):
+        nx = 14 * ny
+        es = np.zeros((1, ny, nx))
+        prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=1.0,
+                            c_in=0.0, kc=0.0, u_in=1.3)
+        st = _run_to_steady(es, prm, dt=1.0)
+        y = np.arange(ny) + 0.5
+        f = y * (ny - y) + 0.25
+        ref = 1.3 * f / f.mean()
+        col = st["u"][0][0, :, nx // 2]
+        assert np.max(np.abs(col - ref)) < 1e-11
+        # pressure gradient of the developed flow: nu u'' = dp/dx
+        G = -(st["p"][0, :, nx // 2 + 1] - st["p"][0, :, nx // 2])
+        assert np.allclose(G, 1.3 * 2.0 * 1.0 / f.mean(), rtol=1e-9)
+
+
+def test_brinkman_channel_discrete_exact():
+    """Eq. momentumDBS with uniform eps0 < 1 and no-slip walls (steady, 1D):
+    nu u'' - nu eps0 k^-1 u = -eps0 G.  Discrete solution
+    u_j = u_p (1 - A cosh(theta (j - c))), cosh theta = 1 + eps0 k^-1 dx^2 / 2,
+    c = (n-1)/2, A from the no-slip ghost; k^-1 from Eq. perm."""
+    ny, nx = 8, 112
+    eps0, k0 = 0.5, 1.0
+    es = np.full((1, ny, nx), 1.0 - eps0)
+    prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=1.0, c_in=0.0,
+                        kc=0.0, k0=k0)
+    st = _run_to_steady(es, prm, dt=1.0)
+    kinv = (1 - eps0) ** 2 / (k0 * eps0 ** 3)
+    th = math.acosh(1.0 + eps0 * kinv / 2.0)
+    cc = (ny - 1) / 2.0
+    A = 2.0 / (math.cosh(th * (cc + 1)) + math.cosh(th * cc))
+    j = np.arange(ny)
+    f = 1.0 - A * np.cosh(th * (j - cc))
+    ref = f / f.mean()
+    col = st["u"][0][0, :, nx // 2]
+    assert np.max(np.abs(col - ref)) < 1e-11
+
+
+def test_darcy_limit_exact():
+    """Uniform eps0, free-slip sides: plug flow u = u_in and Darcy's law
+    dp/dx = -nu k^-1 u_in with k from Eq. perm (Sec. 2.2)."""
+    ny, nx = 4, 24
+    eps0, k0, nu, uin = 0.6, 0.5, 0.7, 0.9
+    es = np.full((1, ny, nx), 1.0 - eps0)
+    prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=nu, c_in=0.0,
+                        kc=0.0, k0=k0, u_in=uin, wall_mask=0)
+    st = _run_to_steady(es, prm, dt=1.0)
+    kinv = (1 - eps0) ** 2 / (k0 * eps0 ** 3)
+    assert np.allclose(st["u"][0], uin, rtol=1e-12)
+    dpdx = np.diff(st["p"][0], axis=1)
+    assert np.allclose(dpdx, -nu * kinv * uin, rtol=1e-10)
+    # outlet Dirichlet p = 0 on the boundary face: p_last = -dp/dx * dx/2
+    assert np.allclose(st["p"][0, :, -1], nu * kinv * uin * 0.5, rtol=1e-10)
+
+
+def test_projection_divergence_equals_source():
+    """Eq. contDBS: div u^{n+1} = R V_m (1 - rho_s/rho) after the projection,
+    and 0 for rho_s = rho (Eq. contDBSQS)."""
+    es = I.calcite_post_2d(48, 16, 16.0, 8.0, 4.0)
+    for rr in (1.0, 2.5):
+        prm = I.make_params(es.shape, Pe=1, Da=1.0, L=8, method="ivos", rho_ratio=rr,
+                            Vm=0.05)
+        st = O.init_state(es, prm)
+        for _ in range(3):
+            R = st["R"].copy()
+            st, _ = O.step(st, 0.5, prm)
+            div = O.divergence(st["u"], prm)
+            s = R * prm["Vm"] * (1.0 - rr)
+            assert np.max(np.abs(div - s)) < 1e-10
+
+
+def test_pressure_operator_laplacian_and_spd():
+    """For eps = 1 the pressure operator is the 5-point Laplacian: applied to
+    phi = x^2 + 3 y^2 it returns -8/dx^2 ... at interior cells, i.e. -lap(phi).
+    It is symmetric positive definite (Dirichlet outlet)."""
+    ny, nx = 7, 9
+    es = np.zeros((1, ny, nx))
+    prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi")
+    eps = np.ones((1, ny, nx))
+    us = O.init_state(es, prm)["u"]
+    A, _ = O.pressure_system(eps, us, np.zeros_like(eps), 1.0, prm)
+    x = np.arange(nx) + 0.5
+    y = np.arange(ny) + 0.5
+    phi = (x[None, :] ** 2 + 3 * y[:, None] ** 2)[None]
+    r = (A @ phi.ravel()).reshape(phi.shape)
+    assert np.allclose(r[0, 1:-1, 1:-1], -8.0, atol=1e-11)
+    Ad = A.toarray()
+    assert np.allclose(Ad, Ad.T)
+    assert np.linalg.eigvalsh(Ad).min() > 0
+
+
+# ---------------------------------------------------------------- transport
+
+def test_diffusion_reaction_1d_discrete_exact():
+    """Steady 1D diffusion with a first-order sink (Eq. concentrationDBS with
+    R_f = kappa c, u = 0): the discrete solution is c_i = a r^i + b r^-i,
+    r + 1/r = 2 + kappa dx^2 / (eps D), with the inlet Dirichlet ghost
+    2 c_in - c_0 and a zero-gradient outlet."""
+    nx = 30
+    eps0, D, kappa, cin = 0.8, 2.0, 0.15, 1.0
+    es = np.full((1, 1, nx), 1 - eps0)
+    prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", D=D, u_in=0.0,
+                        c_in=cin, wall_mask=0)
+    eps = np.full((1, 1, nx), eps0)
+    u = [np.zeros((1, 1, nx + 1)), np.zeros((1, 2, nx)), np.zeros((0,))]
+    A, b = O.transport_system(eps, eps, np.zeros_like(eps), u, prm, 1e30,
+                              kr=np.full_like(eps, kappa))
+    import scipy.sparse.linalg as spla
+    c = spla.spsolve(A.tocsc(), b)
+    a = eps0 * D
+    t = 2.0 + kappa / a
+    r = (t + math.sqrt(t * t - 4)) / 2.0
+    # unknowns (alpha, beta): outlet ghost c_n = c_{n-1}; inlet ghost c_-1 = 2cin - c_0
+    M = np.array([[r ** nx - r ** (nx - 1), r ** -nx - r ** -(nx - 1)],
+                  [1.0 / r + 1.0, r + 1.0]])
+    al, be = np.linalg.solve(M, [0.0, 2 * cin])
+    ref = al * r ** np.arange(nx) + be * r ** -np.arange(nx)
+    assert np.max(np.abs(c - ref)) < 1e-12
+
+
+def _small_case(method, seed=3, shape=(1, 12, 40), Pe=2.0, Da=0.5):
+    es = np.zeros(shape)
+    es2 = I.calcite_post_2d(shape[2], shape[1], 14.0, shape[1] / 2, 4.0)
+    es[:] = es2
+    prm = I.make_params(shape, Pe=Pe, Da=Da, L=8, method=method, Vm=0.05)
+    return es, prm
+
+
+@pytest.mark.parametrize("method", ["psi", "psi_prime", "ivos"])
+def test_reactant_mass_balance(method):
+    """Eq. concentrationDBS in integral form over one step: change of
+    sum(eps c) V = dt (inflow - outflow - zeta sum(R_f) V) (up to the direct
+    solver's rounding)."""
+    es, prm = _small_case(method)
+    st = O.init_state(es, prm)
+    dx, D = prm["dx"], prm["D"]
+    for n in range(4):
+        dt = 0.4
+        st1, s = O.step(st, dt, prm)
+        before = np.sum(st["eps"] * st["c"])
+        after = np.sum(st1["eps"] * st1["c"])
+        inflow = np.sum(st1["u"][0][..., 0] * prm["c_in"]) \
+            + np.sum(2 * D * st1["eps"][..., 0] * (prm["c_in"] - st1["c"][..., 0]) / dx)
+        outflow = np.sum(st1["u"][0][..., -1] * st["c"][..., -1])
+        sink = prm["zeta"] * np.sum(st1["Rf"])
+        lhs = after - before
+        rhs = dt * (inflow - outflow - sink)
+        assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(before), abs(after))
+        st = st1
+
+
+def test_solid_mass_balance():
+    """Eq. mbs: sum(eps^{n+1} - eps^n) V = dt V_m sum(R^n) V - clamp excess."""
+    es, prm = _small_case("ivos", Da=5.0)
+    prm["Vm"] = 20.0
+    st = O.init_state(es, prm)
+    for n in range(5):
+        st1, s = O.step(st, 0.5, prm)
+        lhs = np.sum(st1["eps"] - st["eps"])
+        rhs = 0.5 * prm["Vm"] * np.sum(st["R"]) - s["clamp_excess"]
+        assert abs(lhs - rhs) < 1e-12 * max(1.0, np.sum(st["eps"]))
+        st = st1
+    assert s["clamp_excess"] != 0.0  # the clamp was exercised
+
+
+# ---------------------------------------------------------------- reaction
+
+def test_ivos_sharp_interface():
+    """Sec. 2.3: between a fluid cell P (eps = 1) and a solid cell N
+    (eps ~ 0) the reactant is consumed in P (R_f,P = k_c c_P / dx) and the
+    solid dissolves in N (R_N = k_c c_P / dx (1 - eps_N)), R_P = 0."""
+    nx = 4
+    prm = I.make_params((1, 1, nx), Pe=1, Da=0.7, L=1, method="ivos")
+    em = prm["eps_min"]
+    eps = np.array([1.0, 1.0, em, em])[None, None]
+    c = np.array([0.6, 0.6, 0.1, 0.1])[None, None]
+    faces = O.ivos_faces(eps, c, prm)
+    R, Rf = O.ivos_rates(eps, c, faces, prm)
+    na = (1 - em) / ((1 - em) + 1e-8)
+    F = 0.7 * 0.6 * na
+    assert np.allclose(R[0, 0], [0.0, 0.0, F * (1 - em), 0.0], rtol=1e-15, atol=1e-18)
+    assert np.allclose(Rf[0, 0], [0.0, F, -em * F, 0.0], rtol=1e-15, atol=1e-18)
+    assert abs(F - 0.7 * 0.6) < 1e-7
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_ivos_conservative_term_sums_to_zero(dim):
+    """Sec. 2.3: sum of -div(eps Phi) over the domain vanishes, so
+    sum R = sum R_f (= sum eps div Phi) for any eps, c."""
+    shape = (1, 17, 23) if dim == 2 else (7, 9, 11)
+    prm = I.make_params(shape, Pe=1, Da=1.3, L=1, method="ivos")
+    eps = I.random_field(shape, 1, 1e-4, 1.0, smooth=1)
+    c = I.random_field(shape, 2, 0.0, 1.0)
+    faces = O.ivos_faces(eps, I.random_field(shape, 3), prm)
+    R, Rf = O.ivos_rates(eps, c, faces, prm)
+    assert abs(R.sum() - Rf.sum()) < 1e-13 * np.abs(Rf).sum()
+    assert np.abs(R - Rf).max() > 1e-3  # the local split is non-trivial
+
+
+def test_ivos_smooth_limit_converges():
+    """Sec. 2.3: R = -Phi . grad eps = k_c c |grad eps| for smooth fields;
+    the discrete iVoS rate converges to it under refinement."""
+    errs = []
+    for n in (32, 64, 128):
+        dx = 1.0 / n
+        prm = I.make_params((1, n, n), Pe=1, Da=1.0, L=1, method="ivos", dx=dx)
+        x = (np.arange(n) + 0.5) * dx
+        X, Y = np.meshgrid(x, x)
+        eps = (0.5 + 0.3 * np.sin(2 * np.pi * X) * np.cos(np.pi * Y))[None]
+        c = (1.0 + 0.5 * X * Y)[None]
+        gx = 0.3 * 2 * np.pi * np.cos(2 * np.pi * X) * np.cos(np.pi * Y)
+        gy = -0.3 * np.pi * np.sin(2 * np.pi * X) * np.sin(np.pi * Y)
+        exact = 1.0 * c[0] * np.hypot(gx, gy)
+        faces = O.ivos_faces(eps, c, prm)
+        R, _ = O.ivos_rates(eps, c, faces, prm)
+        m = slice(n // 8, n - n // 8)
+        errs.append(np.mean(np.abs(R[0][m, m] - exact[m, m])))
+    assert errs[1] < 0.6 * errs[0] and errs[2] < 0.6 * errs[1]
+
+
+def test_vos_psi_prime_conserves_area():
+    """Sec. 2.4: with lambda(eps) = int|grad eps| / int|grad eps| eps(1-eps)
+    the localised area sum psi' |grad eps| equals sum |grad eps|."""
+    for shape in ((1, 20, 30), (6, 8, 10)):
+        prm = I.make_params(shape, Pe=1, Da=1.0, L=1, method="psi_prime")
+        eps = I.random_field(shape, 5, 1e-4, 1.0, smooth=1)
+        lam = O.vos_lambda(eps, prm)
+        a_psi = O.vos_coefficient(eps, prm, lam).sum() / prm["kc"]
+        g = O.central_gradient(eps, 1.0, O._axes(prm))
+        assert a_psi == pytest.approx(np.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2).sum(), rel=1e-13)
+    # degenerate: uniform eps -> lambda = 4
+    assert O.vos_lambda(np.full((1, 4, 5), 0.3), I.make_params((1, 4, 5), 1, 1, 1)) == 4.0
+
+
+def test_vos_psi_lambda_in_paper_range_calcite_post():
+    """Sec. 3.1 reports lambda between 8 and 16 for the calcite post; the
+    calcite-post stand-in geometry falls in that range (informative)."""
+    es = I.calcite_post_2d()
+    prm = I.make_params(es.shape, Pe=1, Da=0.1, L=32, method="psi_prime")
+    eps = np.maximum(1 - es, prm["eps_min"])
+    assert 8.0 <= O.vos_lambda(eps, prm) <= 16.0
+
+
+def test_front_speed_reaction_limited():
+    """Eq. Ws: the interface moves at M_ws R / rho_s.  Reaction-limited
+    (Ki << 1, c = c_in): a flat solid layer under iVoS gains fluid at
+    d eps/dt = V_m k_c c_in (1 - eps_min) / dx in its interface cells, i.e. a
+    cell holding 1 - eps_min of solid clears in dx / (V_m k_c c_in)."""
+    ny, nx = 6, 8
+    es = np.zeros((1, ny, nx))
+    es[0, :2, :] = 1.0
+    prm = I.make_params(es.shape, Pe=1, Da=0.01, L=1, method="ivos", D=1e4, u_in=0.0,
+                        Vm=0.5, wall_mask=0)
+    st = O.init_state(es, prm)
+    st["c"][:] = prm["c_in"]
+    st, _ = O.step(st, 1.0, prm)
+    e0 = st["eps"].copy()
+    st, _ = O.step(st, 1.0, prm)
+    rate = (st["eps"] - e0)[0, 1, :]
+    expect = prm["Vm"] * prm["kc"] * prm["c_in"] * (1 - prm["eps_min"]) / prm["dx"]
+    assert np.allclose(rate, expect, rtol=1e-5)
+    assert np.allclose((st["eps"] - e0)[0, 0, :], 0.0, atol=1e-12)
+
+
+def test_poiseuille_3d_plates_discrete_exact():
+    """3D: no-slip plates at y = 0, H and free-slip z sides give the same
+    discrete plane-Poiseuille profile, uniform in z (w = 0)."""
+    nz, ny, nx = 3, 6, 84
+    es = np.zeros((nz, ny, nx))
+    prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=1.0, c_in=0.0,
+                        kc=0.0, wall_mask=I.WALL_YM | I.WALL_YP)
+    st = _run_to_steady(es, prm, dt=1.0)
+    y = np.arange(ny) + 0.5
+    f = y * (ny - y) + 0.25
+    ref = f / f.mean()
+    for k in range(nz):
+        assert np.max(np.abs(st["u"][0][k, :, nx // 2] - ref)) < 1e-11
+    assert np.max(np.abs(st["u"][2])) < 1e-12
+
+
+def test_reactant_mass_balance_3d():
+    """Integral balance of Eq. concentrationDBS over one step, 3D, iVoS."""
+    shape = (6, 7, 16)
+    es = I.sphere_rock_3d(shape, seed=2, median_r=2.5, sigma=0.2, target_porosity=0.6,
+                          start_solid=0.5, band=2, margin=3.0)
+    prm = I.make_params(shape, Pe=2.0, Da=0.5, L=4, method="ivos", Vm=0.05)
+    st = O.init_state(es, prm)
+    D, dx = prm["D"], prm["dx"]
+    for _ in range(3):
+        st1, _ = O.step(st, 0.3, prm)
+        inflow = np.sum(st1["u"][0][..., 0] * prm["c_in"]) \
+            + np.sum(2 * D * st1["eps"][..., 0] * (prm["c_in"] - st1["c"][..., 0]) / dx)
+        outflow = np.sum(st1["u"][0][..., -1] * st["c"][..., -1])
+        lhs = np.sum(st1["eps"] * st1["c"]) - np.sum(st["eps"] * st["c"])
+        rhs = 0.3 * (inflow - outflow - np.sum(st1["Rf"]))
+        assert abs(lhs - rhs) < 1e-10 * max(1.0, np.sum(st1["eps"] * st1["c"]))
+        st = st1
