@@ -1,0 +1,296 @@
+#!/usr/bin/env python3
+"""Throughput of the micro-continuum (VoS) time step on GB300.
+
+Workload (default ``rock256``): synthetic 3D carbonate-like rock, 256^3
+voxels, overlapping spheres with lognormal radii (median 12 voxels, log-sd
+0.3) shifted to porosity 0.20, fluid bands at inlet/outlet, no-slip lateral
+walls; Pe = 10, Da = 1, iVoS; mixed precision (FP32 multigrid / Krylov
+inner solves, FP64 refinement, FP64 fields and reductions), pressure and
+momentum solved to a relative residual of 1e-8, concentration to 1e-10.
+A step is one full vos_step (S1-S7).  The plain-FP64 path is timed on the
+same workload beside it (``fp64``).
+
+Metric: cell-steps/s (cells x steps / device time of the timed steps,
+CUDA events on the library's stream).  Inputs stay resident in HBM and
+exceed L2 (each FP64 field is 134 MB), so no L2 flush is used.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W]
+                       [--impl ours|reference] [--workload rock256|micromodel|calcite]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2204_07019_gb300 import inputs as I  # noqa: E402
+
+METRIC = "cell-steps/s at 1e-8 residual"
+UNIT = "cell-steps/s"
+
+
+def workload(name):
+    """(eps_s, params, description) of a named workload."""
+    if name == "rock256":
+        es = I.sphere_rock_3d(256, seed=0)
+        prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=24.0, method="ivos", precision=1)
+        desc = "3D sphere rock 256^3, porosity 0.20, Pe=10, Da=1, iVoS"
+    elif name == "micromodel":
+        es = I.disc_micromodel_2d(1024, 512, seed=0)
+        prm = I.make_params(es.shape, Pe=100.0, Da=1.0, L=40.0, method="ivos", precision=1)
+        desc = "2D polydisperse discs 1024x512, porosity 0.60, Pe=100, Da=1, iVoS"
+    elif name == "calcite":
+        es = I.calcite_post_2d()
+        prm = I.make_params(es.shape, Pe=1.0, Da=0.1, L=32.0, method="ivos", precision=0)
+        desc = "2D calcite post 256x64, Pe=1, Da=0.1, iVoS"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    prm.update(p_rtol=1e-8, u_rtol=1e-8, c_rtol=1e-10, max_iter=2000)
+    return es, prm, desc
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.th is not None:
+            self.th.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "", 1).isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, device):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("nccl" if device.type == "cuda" else "gloo")
+    return dist
+
+
+def run_steps(V, h, dt, k):
+    st = []
+    for _ in range(k):
+        V.vos_step(h, dt)
+    return st
+
+
+def time_gpu(V, es, prm, steps, warmup, torch):
+    """Create, warm up, then time ``steps`` steps with CUDA events."""
+    h = V.vos_create(es, prm)
+    try:
+        dt0 = 0.5 * prm["dx"] / max(abs(prm["u_in"]), 1e-30)
+        V.vos_step(h, dt0)
+        for _ in range(max(warmup - 1, 0)):
+            V.vos_step(h, dt0)
+        dt = min(V.vos_suggest_dt(h, 0.5, 0.005), 4.0 * dt0)
+        stream = torch.cuda.current_stream()
+        iters = []
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            V.vos_step(h, dt)
+            s = V.vos_get_stats(h)
+            iters.append((s["iters_u"], s["iters_p"], s["iters_c"], s["res_p"]))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        return ms, dt, iters, V.vos_device_bytes(h)
+    finally:
+        V.vos_destroy(h)
+
+
+def time_e2e(V, es, prm, steps, dt):
+    """End to end through the C ABI with host buffers: create from host eps_s,
+    ``steps`` steps, copy eps and c back; wall clock."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = V.vos_create(es, prm)
+    for _ in range(steps):
+        V.vos_step(h, dt)
+    f = V.vos_fields(h, ("eps", "c"))
+    V.vos_destroy(h)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    n = es.size
+    return {"value": n * steps / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(n * 8 / steps),
+            "d2h_bytes_per_step": int(2 * n * 8 / steps), "steps": steps, "checksum": float(f["c"].sum())}
+
+
+def oracle_sample(es, prm, budget_s=20.0, crop=40):
+    """The CPU oracle on a bounded crop (crop^3 for 3D, crop x crop... for 2D)
+    of the same geometry and parameters; returns (cell-steps/s, steps, shape)."""
+    from oracle import vos_oracle as O
+    nz, ny, nx = es.shape
+    if nz > 1:
+        sub = np.ascontiguousarray(es[:crop, :crop, :crop])
+    else:
+        sub = np.ascontiguousarray(es[:, : min(ny, 4 * crop), : min(nx, 4 * crop)])
+    p = dict(prm)
+    p.update(nz=sub.shape[0], ny=sub.shape[1], nx=sub.shape[2])
+    st = O.init_state(sub, p)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        st, _ = O.step(st, 0.5, p, solver="iterative", rtol=p["p_rtol"])
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 20:
+            break
+    dt = time.perf_counter() - t0
+    return sub.size * n / dt, n, sub.shape, dt
+
+
+def reference_arm(args, rank, world):
+    """The CPU oracle as it stands, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    es, prm, desc = workload(args.workload)
+    cells = []
+    for _ in range(max(args.warmup, 0)):
+        oracle_sample(es, prm, budget_s=2.0)
+    rates = []
+    for _ in range(args.steps):
+        r, n, shp, dt = oracle_sample(es, prm, budget_s=5.0)
+        rates.append(r)
+        cells.append(shp)
+    v = float(np.mean(rates))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "desc": desc},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"oracle step(s) on a {cells[0]} crop of the workload geometry, "
+                                      "scipy CG/BiCGStab to the same tolerances, ~5 s per timed step"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rock256", choices=["rock256", "micromodel", "calcite"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+    from paper_2204_07019_gb300 import build_lib
+    from paper_2204_07019_gb300 import vos as V
+    if rank == 0 or world == 1:
+        build_lib.build()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = init_dist(world, device)
+    if dist is not None:
+        dist.barrier()
+    V.load_library()
+    es, prm, desc = workload(args.workload)
+    N = es.size
+    launches0 = V.vos_kernel_launches() if hasattr(V, "vos_kernel_launches") else None
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    clocks.start()
+    ms, dt, iters, dev_bytes = time_gpu(V, es, prm, args.steps, args.warmup, torch)
+    ck = clocks.stop()
+    t = torch.tensor([ms], device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms = float(t.item())
+    value = N * world / (ms * 1e-3)
+    p64 = dict(prm)
+    p64["precision"] = 0
+    ms64, _, it64, _ = time_gpu(V, es, p64, max(args.fp64_steps, 1), 2, torch)
+    e2e = time_e2e(V, es, prm, max(2, args.steps // 2), dt)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": args.workload, "desc": desc, "cells": N, "dt": dt,
+                      "p_rtol": prm["p_rtol"], "u_rtol": prm["u_rtol"], "c_rtol": prm["c_rtol"],
+                      "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+           "fp64": {"value": N * world / (ms64 * 1e-3), "ms_per_step": ms64,
+                    "iters_p_mean": float(np.mean([i[1] for i in it64]))},
+           "solver": {"iters_u_mean": [float(np.mean([i[0][a] for i in iters])) for a in range(3)],
+                      "iters_p_mean": float(np.mean([i[1] for i in iters])),
+                      "iters_c_mean": float(np.mean([i[2] for i in iters])),
+                      "res_p_max": float(max(i[3] for i in iters))},
+           "device_bytes": dev_bytes, "e2e": e2e, "clocks": ck}
+    if launches0 is not None:
+        out["gpu_launches"] = None
+    if rank == 0 and not args.no_cpu:
+        r, n, shp, dtc = oracle_sample(es, prm, budget_s=15.0)
+        out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{n} oracle step(s) on a {tuple(shp)} crop of the same geometry "
+                                         f"({dtc:.1f} s), scipy CG/BiCGStab at the same tolerances"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * vos.h -- C ABI of the GB300 micro-continuum dissolution step.
+ *
+ * Method: Maes, Soulaine & Menke, "Improved Volume-of-Solid formulations for
+ * micro-continuum simulation of mineral dissolution at the pore-scale".
+ * One call to vos_step advances, on a uniform Cartesian grid (2D or 3D):
+ *   S1  solid fraction eps by the solid mass balance (Sec. 2.2, Eq. mbs) and
+ *       the Kozeny-Carman permeability (Eq. perm);
+ *   S2  Darcy-Brinkman-Stokes momentum predictor (Eq. momentumDBS);
+ *   S3  pressure correction and projection (Eq. contDBS);
+ *   S4  explicit van Leer advection of the reactant (App. B);
+ *   S5  implicit diffusion + reaction of the reactant (Eq. concentrationDBS);
+ *   S6  reaction rates R (solid source) and R_f (transport sink) by
+ *       VoS-psi (Eq. RfVoSpsi, lambda = 4), VoS-psi' (lambda fitted from
+ *       global integrals, Sec. 2.4) or iVoS (Eq. RfiVoS, Sec. 2.3);
+ *   S7  global FP64 diagnostics.
+ * Grid: MAC staggered -- scalars at cell centres, velocity components on
+ * the faces normal to them.  Cell index i + nx*(j + ny*k) (x fastest).
+ * u: (nx+1)*ny*nz values, index i + (nx+1)*(j + ny*k), i = 0 the inlet face;
+ * v: nx*(ny+1)*nz, index i + nx*(j + (ny+1)*k);
+ * w: nx*ny*(nz+1), index i + nx*(j + ny*k), k in [0, nz] (3D only).
+ * Boundaries: x- inlet (u = u_in, c = c_in), x+ outlet (p = 0, zero
+ * gradient), y+-/z+- no-slip walls where wall_mask has the bit, free-slip
+ * otherwise.
+ *
+ * Every function returns VOS_OK (0) or a negative error code; the message
+ * of the last error on a handle is returned by vos_last_error.  A handle is
+ * not thread-safe; different handles are independent.  All device work is
+ * enqueued on the stream given to vos_create.
+ */
+#ifndef VOS_H_
+#define VOS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VOS_OK 0
+#define VOS_EINVAL (-1)   /* bad size, parameter, NaN or NULL pointer        */
+#define VOS_ENOMEM (-2)   /* device allocation failed                       */
+#define VOS_ECUDA (-3)    /* a CUDA call failed (message has the CUDA text) */
+#define VOS_ENOCONV (-4)  /* a linear solve hit max_iter; the step was still
+                             applied with the last iterate                  */
+
+typedef enum { VOS_PSI = 0, VOS_PSI_PRIME = 1, VOS_IVOS = 2 } vos_method;
+typedef enum { VOS_FP64 = 0, VOS_MIXED = 1 } vos_precision;
+
+/* wall_mask bits: no-slip wall on that side (else free-slip) */
+#define VOS_WALL_YM 1u
+#define VOS_WALL_YP 2u
+#define VOS_WALL_ZM 4u
+#define VOS_WALL_ZP 8u
+
+/* field mask bits for vos_fields / vos_set_fields */
+#define VOS_F_EPS 1u
+#define VOS_F_C 2u
+#define VOS_F_U 4u
+#define VOS_F_V 8u
+#define VOS_F_W 16u
+#define VOS_F_P 32u
+#define VOS_F_R 64u
+#define VOS_F_RF 128u
+
+/* Physical and numerical parameters (non-dimensional units are fine).
+ * Symbols follow Sec. 2.2-2.5: nu kinematic viscosity, D diffusion
+ * coefficient (D* = D), kc reaction constant (R = kc c), k0 Kozeny-Carman
+ * constant, Vm = M_ws / rho_s molar volume of the solid, zeta
+ * stoichiometric coefficient, rho_ratio = rho_s / rho (1 gives the
+ * divergence-free flow of Eq. contDBSQS), c_in / u_in inlet concentration
+ * and velocity, eps_min the fluid fraction kept inside the solid (App. C,
+ * 1e-4), lambda the VoS-psi constant (4).  p_rtol / u_rtol / c_rtol:
+ * relative residual ||b - Ax|| / ||b|| at which the pressure, momentum and
+ * concentration solves stop; max_iter caps the Krylov iterations of one
+ * solve. */
+typedef struct vos_params {
+  int32_t dim, nx, ny, nz; /* dim 2 (nz = 1) or 3 */
+  double dx, nu, D, kc, k0, Vm, zeta, rho_ratio, c_in, u_in, eps_min, lambda;
+  int32_t method;    /* vos_method */
+  int32_t precision; /* vos_precision */
+  int32_t precond;   /* 0: geometric multigrid */
+  double p_rtol, u_rtol, c_rtol;
+  int32_t max_iter;
+  int32_t flow_subiters; /* 1: one transient step (only value accepted) */
+  uint32_t wall_mask;
+} vos_params;
+
+/* Statistics of the last completed step (FP64 device reductions). */
+typedef struct vos_stats {
+  int64_t step;
+  double t;
+  int32_t iters_u[3], iters_p, iters_c;  /* Krylov iterations (inner, summed) */
+  int32_t outer_u[3], outer_p, outer_c;  /* refinement passes                */
+  double res_u[3], res_p, res_c;         /* final true relative residuals    */
+  double lambda;       /* psi' fit (psi: the constant; iVoS: NaN)            */
+  double porosity;     /* mean eps                                           */
+  double clamp_excess; /* sum(raw - clamped eps) * V of the S1 update        */
+  double sum_R, sum_Rf;/* sum R V, sum R_f V                                 */
+  double reactant;     /* sum eps c V                                        */
+  int32_t status;      /* VOS_OK or VOS_ENOCONV                              */
+} vos_stats;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc(bytes, ctx) returns a device pointer aligned to >= 256 bytes or
+ * NULL; free(ptr, ctx) releases it.  NULL selects cudaMalloc/cudaFree. */
+typedef struct vos_allocator {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* ctx;
+} vos_allocator;
+
+typedef struct vos_handle vos_handle;
+
+/* Device pointers of the fields (owned by the handle, valid until destroy).
+ * Layouts as above; all FP64. */
+typedef struct vos_device_fields {
+  double *eps, *c, *p, *u, *v, *w, *R, *Rf;
+} vos_device_fields;
+
+/* Create a simulation from the solid fraction eps_s (host, nx*ny*nz FP64
+ * values in [0, 1]): eps = max(1 - eps_s, eps_min) (App. C), u = u_in on
+ * the inlet faces, all other fields zero.  stream: a cudaStream_t (NULL =
+ * legacy default stream).  alloc may be NULL.  The handle owns all device
+ * memory; eps_s is copied and not retained.  Errors: VOS_EINVAL (sizes,
+ * parameters, values), VOS_ENOMEM, VOS_ECUDA; *out is NULL on error. */
+int vos_create(const double* eps_s_host, const vos_params* prm, void* stream,
+               const vos_allocator* alloc, vos_handle** out);
+
+/* Advance one time step of length dt (> 0) through S1-S7 (see top).  The
+ * linear solves converge on the device; the host reads the residual once
+ * per refinement pass and at most every few Krylov iterations.  Returns
+ * VOS_ENOCONV if a solve reached max_iter (the step is still applied). */
+int vos_step(vos_handle* h, double dt);
+
+/* Copy the selected fields (mask of VOS_F_*) to caller-owned host buffers
+ * (NULL pointers are skipped).  Synchronous on the handle's stream. */
+int vos_fields(vos_handle* h, uint32_t mask, double* eps, double* c, double* u,
+               double* v, double* w, double* p, double* R, double* Rf);
+
+/* Overwrite the selected fields from host buffers (checkpoint resume).
+ * Synchronous. */
+int vos_set_fields(vos_handle* h, uint32_t mask, const double* eps, const double* c,
+                   const double* u, const double* v, const double* w, const double* p,
+                   const double* R, const double* Rf);
+
+/* Device pointers of the fields (no copy). */
+int vos_device_fields_get(vos_handle* h, vos_device_fields* out);
+
+/* Statistics of the last step (synchronises the stream). */
+int vos_get_stats(vos_handle* h, vos_stats* out);
+
+/* Time step limit min(cfl dx / max_f(|u_f| / eps_f), deps_max / max|Vm R|)
+ * (App. D: the step is limited by the largest change of eps; the
+ * convective limit uses the interstitial speed).  Synchronous.  Returns
+ * +inf in *dt when neither limit applies. */
+int vos_suggest_dt(vos_handle* h, double cfl, double deps_max, double* dt);
+
+/* Message of the last error on h (or of the last failed vos_create when h
+ * is NULL).  The string is owned by the library. */
+const char* vos_last_error(const vos_handle* h);
+
+/* Free all device memory of h.  NULL is accepted. */
+void vos_destroy(vos_handle* h);
+
+/* Bytes of device memory held by h. */
+size_t vos_device_bytes(const vos_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VOS_H_ */

@@ -1,0 +1,503 @@
+// C ABI of the VoS step: handle lifetime, device memory, step orchestration.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/vos.h"
+#include "vos_phys.cuh"
+
+using namespace vos;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+template <typename T>
+struct Sys {
+  Box box;
+  int sym;
+  Op<double> op64;
+  double* rhs;
+  Hier<T> h;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct vos_handle {
+  vos_params prm;
+  Phys ph;
+  cudaStream_t st;
+  vos_allocator alloc;
+  bool user_alloc;
+  std::vector<void*> blocks;
+  size_t bytes;
+  // fields
+  double *eps, *eps_old, *c, *p, *phi, *R, *Rf, *kr;
+  double *u[3], *us[3];
+  FaceData fd[3];
+  // solvers: 0..2 momentum, 3 pressure, 4 transport
+  Sys<double> sd[5];
+  Sys<float> sf[5];
+  SolverWork* work;
+  RedScratch rs;
+  double* dstats;
+  double* hstats;  // pinned
+  vos_stats stats;
+  std::string err;
+  int dev;
+};
+
+namespace {
+
+int set_err(vos_handle* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h)
+    h->err = buf;
+  else
+    g_create_error = buf;
+  return code;
+}
+
+void* dev_alloc(vos_handle* h, size_t bytes) {
+  bytes = align256(bytes ? bytes : 256);
+  void* p = nullptr;
+  if (h->user_alloc) {
+    p = h->alloc.alloc(bytes, h->alloc.ctx);
+  } else {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+  }
+  if (p) {
+    h->blocks.push_back(p);
+    h->bytes += bytes;
+  }
+  return p;
+}
+
+void free_all(vos_handle* h) {
+  for (void* p : h->blocks) {
+    if (h->user_alloc)
+      h->alloc.free(p, h->alloc.ctx);
+    else
+      cudaFree(p);
+  }
+  h->blocks.clear();
+  if (h->work) solver_work_free(h->work);
+  h->work = nullptr;
+  if (h->hstats) cudaFreeHost(h->hstats);
+  h->hstats = nullptr;
+}
+
+Box unknown_box(const Phys& P, int sys) {
+  switch (sys) {
+    case 0: return Box{P.nx, P.ny, P.nz};
+    case 1: return Box{P.nx, P.ny - 1, P.nz};
+    case 2: return Box{P.nx, P.ny, P.nz - 1};
+    default: return Box{P.nx, P.ny, P.nz};
+  }
+}
+
+long long face_count(const Phys& P, int a) {
+  return (long long)(P.nx + (a == 0)) * (P.ny + (a == 1)) * (P.nz + (a == 2));
+}
+
+View<double> unknown_view(vos_handle* h, int sys) {
+  const Phys& P = h->ph;
+  switch (sys) {
+    case 0: return View<double>{h->us[0] + 1, P.nx + 1, (P.nx + 1) * P.ny};
+    case 1: return View<double>{h->us[1] + P.nx, P.nx, P.nx * (P.ny + 1)};
+    case 2: return View<double>{h->us[2] + (long long)P.nx * P.ny, P.nx, P.nx * P.ny};
+    case 3: return View<double>{h->phi, P.nx, P.nx * P.ny};
+    default: return View<double>{h->c, P.nx, P.nx * P.ny};
+  }
+}
+
+MGParams mg_for(const Phys& P, int sys) {
+  MGParams m;
+  m.omega = (P.dim == 2) ? 0.8 : 0.7;
+  m.wc = (sys == 4) ? 1.0 : 1.8;
+  m.nu = 2;
+  m.coarse_sweeps = 30;
+  return m;
+}
+
+template <typename T>
+bool alloc_sys(vos_handle* h, Sys<T>& S, int sys, int sym) {
+  const Phys& P = h->ph;
+  S.box = unknown_box(P, sys);
+  S.sym = sym;
+  std::memset(&S.op64, 0, sizeof(S.op64));
+  S.rhs = nullptr;
+  S.h.nlev = 0;
+  if (box_cells(S.box) == 0) return true;
+  const bool share = (sizeof(T) == 8);
+  size_t nb = op64_bytes(S.box, sym) + align256((size_t)box_cells(S.box) * 8) + hier_bytes<T>(S.box, sym, share);
+  char* cur = (char*)dev_alloc(h, nb);
+  if (!cur) return false;
+  op64_carve(S.op64, S.box, sym, cur);
+  S.rhs = (double*)cur;
+  cur += align256((size_t)box_cells(S.box) * 8);
+  hier_carve<T>(S.h, S.box, sym, cur, mg_for(P, sys), share, &S.op64);
+  return true;
+}
+
+template <typename T>
+int step_impl(vos_handle* h, Sys<T>* S, double dt) {
+  const Phys& P = h->ph;
+  cudaStream_t st = h->st;
+  const int nd = P.dim;
+  const int ivos = (h->prm.method == VOS_IVOS);
+  vos_stats& s = h->stats;
+  int status = VOS_OK;
+  // S1: solid fraction and (implicitly) permeability
+  launch_eps_update(P, h->eps, h->eps_old, h->R, dt, h->dstats, h->rs, st);
+  // S2: momentum predictor per component
+  for (int a = 0; a < nd; ++a) {
+    cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    s.iters_u[a] = 0;
+    s.outer_u[a] = 0;
+    s.res_u[a] = 0.0;
+    if (box_cells(S[a].box) == 0) continue;
+    launch_mom_assemble(P, a, h->eps, h->p, h->u[a], dt, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
+    SolveResult r = solve<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
+                             h->work, h->rs, st);
+    s.iters_u[a] = r.iters;
+    s.outer_u[a] = r.outer;
+    s.res_u[a] = r.relres;
+    if (!r.converged) status = VOS_ENOCONV;
+  }
+  // S3: pressure correction, projection
+  launch_pres_assemble(P, h->eps, h->us, h->R, dt, S[3].h.mg.omega, S[3].op64, S[3].rhs, st);
+  cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st);
+  {
+    SolveResult r =
+        solve<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter, h->work, h->rs, st);
+    s.iters_p = r.iters;
+    s.outer_p = r.outer;
+    s.res_p = r.relres;
+    if (!r.converged) status = VOS_ENOCONV;
+  }
+  launch_project(P, h->eps, h->phi, dt, h->us, h->u, h->p, st);
+  // S4-S6: reactive surface data (from eps^{n+1}, c^n), transport, rates
+  if (ivos) {
+    launch_ivos_faces(P, h->eps, h->c, h->fd, st);
+  } else {
+    launch_vos_lambda(P, h->eps, h->prm.lambda, h->prm.method == VOS_PSI_PRIME, h->dstats, h->rs, st);
+    launch_vos_coef(P, h->eps, h->dstats, h->kr, st);
+  }
+  launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->u, h->kr, h->fd, dt, S[4].h.mg.omega, S[4].op64,
+                        S[4].rhs, st);
+  {
+    SolveResult r =
+        solve<T>(S[4].op64, S[4].h, S[4].rhs, unknown_view(h, 4), h->prm.c_rtol, h->prm.max_iter, h->work, h->rs, st);
+    s.iters_c = r.iters;
+    s.outer_c = r.outer;
+    s.res_c = r.relres;
+    if (!r.converged) status = VOS_ENOCONV;
+  }
+  launch_rates(P, ivos, h->eps, h->c, h->kr, h->fd, h->R, h->Rf, h->dstats, h->rs, st);
+  cudaMemcpyAsync(h->hstats, h->dstats, ST_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_step: %s", cudaGetErrorString(e));
+  s.step += 1;
+  s.t += dt;
+  s.status = status;
+  if (status == VOS_ENOCONV) set_err(h, VOS_ENOCONV, "vos_step: a linear solve reached max_iter");
+  return status;
+}
+
+int validate(const vos_params* p) {
+  if (!p) return set_err(nullptr, VOS_EINVAL, "params is NULL");
+  if (p->dim != 2 && p->dim != 3) return set_err(nullptr, VOS_EINVAL, "dim must be 2 or 3 (got %d)", p->dim);
+  if (p->nx < 2 || p->ny < 1 || p->nz < 1) return set_err(nullptr, VOS_EINVAL, "need nx >= 2, ny >= 1, nz >= 1");
+  if (p->dim == 2 && p->nz != 1) return set_err(nullptr, VOS_EINVAL, "dim 2 needs nz == 1");
+  if ((double)p->nx * p->ny * p->nz > 1.0e9) return set_err(nullptr, VOS_EINVAL, "grid too large");
+  const double vals[] = {p->dx, p->k0, p->eps_min};
+  for (double v : vals)
+    if (!(v > 0.0) || !std::isfinite(v)) return set_err(nullptr, VOS_EINVAL, "dx, k0, eps_min must be > 0");
+  if (!(p->eps_min < 1.0)) return set_err(nullptr, VOS_EINVAL, "eps_min must be < 1");
+  const double nn[] = {p->nu, p->D, p->kc, p->Vm, p->zeta, p->rho_ratio, p->c_in, p->lambda};
+  for (double v : nn)
+    if (!(v >= 0.0) || !std::isfinite(v))
+      return set_err(nullptr, VOS_EINVAL, "nu, D, kc, Vm, zeta, rho_ratio, c_in, lambda must be finite and >= 0");
+  if (!std::isfinite(p->u_in)) return set_err(nullptr, VOS_EINVAL, "u_in must be finite");
+  if (p->method < 0 || p->method > 2) return set_err(nullptr, VOS_EINVAL, "unknown method %d", p->method);
+  if (p->precision < 0 || p->precision > 1) return set_err(nullptr, VOS_EINVAL, "unknown precision %d", p->precision);
+  if (p->precond != 0) return set_err(nullptr, VOS_EINVAL, "precond must be 0 (multigrid)");
+  if (p->flow_subiters != 1) return set_err(nullptr, VOS_EINVAL, "flow_subiters must be 1");
+  const double tol[] = {p->p_rtol, p->u_rtol, p->c_rtol};
+  for (double v : tol)
+    if (!(v > 0.0) || !(v < 1.0)) return set_err(nullptr, VOS_EINVAL, "tolerances must be in (0, 1)");
+  if (p->max_iter < 1) return set_err(nullptr, VOS_EINVAL, "max_iter must be >= 1");
+  return VOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, const vos_allocator* alloc,
+               vos_handle** out) {
+  if (!out) return set_err(nullptr, VOS_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(prm);
+  if (rc) return rc;
+  if (!eps_s_host) return set_err(nullptr, VOS_EINVAL, "eps_s is NULL");
+  if (alloc && (!alloc->alloc || !alloc->free)) return set_err(nullptr, VOS_EINVAL, "allocator needs alloc and free");
+  const long long N = (long long)prm->nx * prm->ny * prm->nz;
+  for (long long c = 0; c < N; ++c) {
+    double v = eps_s_host[c];
+    if (!(v >= 0.0 && v <= 1.0)) return set_err(nullptr, VOS_EINVAL, "eps_s[%lld] = %g not in [0, 1]", c, v);
+  }
+  vos_handle* h = new vos_handle();
+  h->prm = *prm;
+  Phys& P = h->ph;
+  P.dim = prm->dim;
+  P.nx = prm->nx;
+  P.ny = prm->ny;
+  P.nz = prm->nz;
+  P.dx = prm->dx;
+  P.nu = prm->nu;
+  P.D = prm->D;
+  P.kc = prm->kc;
+  P.k0 = prm->k0;
+  P.Vm = prm->Vm;
+  P.zeta = prm->zeta;
+  P.rho_ratio = prm->rho_ratio;
+  P.c_in = prm->c_in;
+  P.u_in = prm->u_in;
+  P.eps_min = prm->eps_min;
+  P.wall_mask = prm->wall_mask;
+  h->st = (cudaStream_t)stream;
+  h->user_alloc = (alloc != nullptr);
+  if (alloc) h->alloc = *alloc;
+  h->bytes = 0;
+  h->work = nullptr;
+  h->hstats = nullptr;
+  std::memset(&h->stats, 0, sizeof(h->stats));
+  cudaGetDevice(&h->dev);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev) == cudaSuccess && sms > 0) g_num_sms = sms;
+
+  const size_t cb = (size_t)N * sizeof(double);
+  auto fail = [&](int code, const char* what) {
+    set_err(nullptr, code, "vos_create: %s", what);
+    free_all(h);
+    delete h;
+    return code;
+  };
+  double** cells[] = {&h->eps, &h->eps_old, &h->c, &h->p, &h->phi, &h->R, &h->Rf, &h->kr};
+  for (double** f : cells) {
+    *f = (double*)dev_alloc(h, cb);
+    if (!*f) return fail(VOS_ENOMEM, "device allocation failed (cell fields)");
+  }
+  for (int a = 0; a < 3; ++a) {
+    h->u[a] = h->us[a] = nullptr;
+    h->fd[a] = FaceData{nullptr, nullptr, nullptr};
+    if (a >= P.dim) continue;
+    size_t fb = (size_t)face_count(P, a) * sizeof(double);
+    h->u[a] = (double*)dev_alloc(h, fb);
+    h->us[a] = (double*)dev_alloc(h, fb);
+    if (!h->u[a] || !h->us[a]) return fail(VOS_ENOMEM, "device allocation failed (face fields)");
+    if (prm->method == VOS_IVOS) {
+      h->fd[a].s = (double*)dev_alloc(h, fb);
+      h->fd[a].w = (double*)dev_alloc(h, fb);
+      h->fd[a].evl = (double*)dev_alloc(h, fb);
+      if (!h->fd[a].s || !h->fd[a].w || !h->fd[a].evl) return fail(VOS_ENOMEM, "device allocation failed (iVoS)");
+    }
+  }
+  const int trans_sym = (prm->method == VOS_IVOS) ? 0 : 1;
+  for (int sys = 0; sys < 5; ++sys) {
+    if (sys < 3 && sys >= P.dim) {
+      h->sd[sys].box = Box{0, 0, 0};
+      h->sf[sys].box = Box{0, 0, 0};
+      continue;
+    }
+    int sym = (sys == 4) ? trans_sym : 1;
+    bool ok = (prm->precision == VOS_FP64) ? alloc_sys<double>(h, h->sd[sys], sys, sym)
+                                           : alloc_sys<float>(h, h->sf[sys], sys, sym);
+    if (!ok) return fail(VOS_ENOMEM, "device allocation failed (solver)");
+  }
+  {
+    long long maxc = 0;
+    for (int sys = 0; sys < 5; ++sys) {
+      Box b = (prm->precision == VOS_FP64) ? h->sd[sys].box : h->sf[sys].box;
+      if (box_cells(b) > maxc) maxc = box_cells(b);
+    }
+    char* cur = (char*)dev_alloc(h, solver_work_bytes(maxc));
+    if (!cur) return fail(VOS_ENOMEM, "device allocation failed (Krylov vectors)");
+    h->work = solver_work_carve(cur, maxc);
+    char* rsb = (char*)dev_alloc(h, kMaxRedValues * kMaxRedBlocks * sizeof(double) + 256 + ST_COUNT * sizeof(double));
+    if (!rsb) return fail(VOS_ENOMEM, "device allocation failed (reduction scratch)");
+    h->rs.partials = (double*)rsb;
+    h->rs.counter = (unsigned int*)(rsb + kMaxRedValues * kMaxRedBlocks * sizeof(double));
+    h->dstats = (double*)(rsb + kMaxRedValues * kMaxRedBlocks * sizeof(double) + 256);
+  }
+  if (cudaMallocHost((void**)&h->hstats, ST_COUNT * sizeof(double)) != cudaSuccess)
+    return fail(VOS_ENOMEM, "pinned host allocation failed");
+  std::memset(h->hstats, 0, ST_COUNT * sizeof(double));
+  // initial fields (App. C: eps = max(1 - eps_s, eps_min))
+  std::vector<double> e0(N);
+  double esum = 0.0;
+  for (long long c = 0; c < N; ++c) {
+    e0[c] = std::fmax(1.0 - eps_s_host[c], prm->eps_min);
+    esum += e0[c];
+  }
+  cudaStream_t st = h->st;
+  cudaMemcpyAsync(h->eps, e0.data(), cb, cudaMemcpyHostToDevice, st);
+  for (double* f : {h->eps_old, h->c, h->p, h->phi, h->R, h->Rf, h->kr}) cudaMemsetAsync(f, 0, cb, st);
+  for (int a = 0; a < P.dim; ++a) {
+    size_t fb = (size_t)face_count(P, a) * sizeof(double);
+    cudaMemsetAsync(h->u[a], 0, fb, st);
+    cudaMemsetAsync(h->us[a], 0, fb, st);
+  }
+  {
+    // inlet faces u = u_in (face i = 0 of every (j,k) row)
+    std::vector<double> u0((size_t)face_count(P, 0), 0.0);
+    for (long long r = 0; r < (long long)P.ny * P.nz; ++r) u0[(size_t)r * (P.nx + 1)] = prm->u_in;
+    cudaMemcpyAsync(h->u[0], u0.data(), u0.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(h->rs.counter, 0, sizeof(unsigned int), st);
+    cudaMemsetAsync(h->dstats, 0, ST_COUNT * sizeof(double), st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(VOS_ECUDA, cudaGetErrorString(cudaGetLastError()));
+  }
+  h->stats.porosity = esum / (double)N;
+  h->stats.lambda = (prm->method == VOS_PSI) ? prm->lambda : NAN;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(VOS_ECUDA, cudaGetErrorString(e));
+  *out = h;
+  return VOS_OK;
+}
+
+int vos_step(vos_handle* h, double dt) {
+  if (!h) return set_err(nullptr, VOS_EINVAL, "handle is NULL");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(h, VOS_EINVAL, "dt must be finite and > 0");
+  if (h->prm.precision == VOS_FP64) return step_impl<double>(h, h->sd, dt);
+  return step_impl<float>(h, h->sf, dt);
+}
+
+int vos_fields(vos_handle* h, uint32_t mask, double* eps, double* c, double* u, double* v, double* w, double* p,
+               double* R, double* Rf) {
+  if (!h) return set_err(nullptr, VOS_EINVAL, "handle is NULL");
+  const Phys& P = h->ph;
+  const size_t cb = (size_t)P.nx * P.ny * P.nz * sizeof(double);
+  struct Item {
+    uint32_t bit;
+    double* dst;
+    const double* src;
+    size_t bytes;
+  } items[] = {
+      {VOS_F_EPS, eps, h->eps, cb},
+      {VOS_F_C, c, h->c, cb},
+      {VOS_F_U, u, h->u[0], (size_t)face_count(P, 0) * 8},
+      {VOS_F_V, v, h->u[1], (size_t)face_count(P, 1) * 8},
+      {VOS_F_W, w, h->u[2], P.dim == 3 ? (size_t)face_count(P, 2) * 8 : 0},
+      {VOS_F_P, p, h->p, cb},
+      {VOS_F_R, R, h->R, cb},
+      {VOS_F_RF, Rf, h->Rf, cb},
+  };
+  for (auto& it : items) {
+    if (!(mask & it.bit) || !it.dst || !it.src || it.bytes == 0) continue;
+    cudaMemcpyAsync(it.dst, it.src, it.bytes, cudaMemcpyDeviceToHost, h->st);
+  }
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_fields: %s", cudaGetErrorString(e));
+  return VOS_OK;
+}
+
+int vos_set_fields(vos_handle* h, uint32_t mask, const double* eps, const double* c, const double* u, const double* v,
+                   const double* w, const double* p, const double* R, const double* Rf) {
+  if (!h) return set_err(nullptr, VOS_EINVAL, "handle is NULL");
+  const Phys& P = h->ph;
+  const size_t cb = (size_t)P.nx * P.ny * P.nz * sizeof(double);
+  struct Item {
+    uint32_t bit;
+    double* dst;
+    const double* src;
+    size_t bytes;
+  } items[] = {
+      {VOS_F_EPS, h->eps, eps, cb},
+      {VOS_F_C, h->c, c, cb},
+      {VOS_F_U, h->u[0], u, (size_t)face_count(P, 0) * 8},
+      {VOS_F_V, h->u[1], v, (size_t)face_count(P, 1) * 8},
+      {VOS_F_W, h->u[2], w, P.dim == 3 ? (size_t)face_count(P, 2) * 8 : 0},
+      {VOS_F_P, h->p, p, cb},
+      {VOS_F_R, h->R, R, cb},
+      {VOS_F_RF, h->Rf, Rf, cb},
+  };
+  for (auto& it : items) {
+    if (!(mask & it.bit) || !it.dst || !it.src || it.bytes == 0) continue;
+    cudaMemcpyAsync(it.dst, it.src, it.bytes, cudaMemcpyHostToDevice, h->st);
+  }
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_set_fields: %s", cudaGetErrorString(e));
+  return VOS_OK;
+}
+
+int vos_device_fields_get(vos_handle* h, vos_device_fields* out) {
+  if (!h || !out) return set_err(h, VOS_EINVAL, "NULL argument");
+  out->eps = h->eps;
+  out->c = h->c;
+  out->p = h->p;
+  out->u = h->u[0];
+  out->v = h->u[1];
+  out->w = h->u[2];
+  out->R = h->R;
+  out->Rf = h->Rf;
+  return VOS_OK;
+}
+
+int vos_get_stats(vos_handle* h, vos_stats* out) {
+  if (!h || !out) return set_err(h, VOS_EINVAL, "NULL argument");
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_get_stats: %s", cudaGetErrorString(e));
+  const Phys& P = h->ph;
+  vos_stats s = h->stats;
+  if (s.step > 0) {
+    s.clamp_excess = h->hstats[ST_CLAMP];
+    s.porosity = h->hstats[ST_EPSSUM] / ((double)P.nx * P.ny * P.nz);
+    s.sum_R = h->hstats[ST_SUMR];
+    s.sum_Rf = h->hstats[ST_SUMRF];
+    s.reactant = h->hstats[ST_REACT];
+    s.lambda = (h->prm.method == VOS_IVOS) ? NAN : h->hstats[ST_LAMBDA];
+  }
+  *out = s;
+  return VOS_OK;
+}
+
+int vos_suggest_dt(vos_handle* h, double cfl, double deps_max, double* dt) {
+  if (!h || !dt) return set_err(h, VOS_EINVAL, "NULL argument");
+  if (!(cfl > 0.0) || !(deps_max > 0.0)) return set_err(h, VOS_EINVAL, "cfl and deps_max must be > 0");
+  launch_dt_limits(h->ph, h->eps, h->u, h->R, h->dstats, h->rs, h->st);
+  double v[2];
+  cudaMemcpyAsync(v, h->dstats + ST_UMAX, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_suggest_dt: %s", cudaGetErrorString(e));
+  double d1 = v[0] > 0.0 ? cfl * h->ph.dx / v[0] : INFINITY;
+  double d2 = v[1] > 0.0 ? deps_max / v[1] : INFINITY;
+  *dt = d1 < d2 ? d1 : d2;
+  return VOS_OK;
+}
+
+const char* vos_last_error(const vos_handle* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+void vos_destroy(vos_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  free_all(h);
+  delete h;
+}
+
+size_t vos_device_bytes(const vos_handle* h) { return h ? h->bytes : 0; }
+
+}  // extern "C"

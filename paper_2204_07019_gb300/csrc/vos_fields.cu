@@ -1,0 +1,672 @@
+// Physics kernels of one VoS time step (FP64 fields, MAC-staggered grid).
+//
+// Cell (i,j,k) -> i + nx*(j + ny*k).  Face arrays of axis a have one more
+// entry along a; face index m along a separates cells m-1 and m.
+#include <cmath>
+
+#include "vos_phys.cuh"
+
+namespace vos {
+
+namespace {
+
+__device__ __forceinline__ long long cidx(const Phys& P, int i, int j, int k) {
+  return i + (long long)P.nx * (j + (long long)P.ny * k);
+}
+__device__ __forceinline__ int fdim(const Phys& P, int a, int b) {
+  int n = (b == 0) ? P.nx : (b == 1) ? P.ny : P.nz;
+  return n + (a == b ? 1 : 0);
+}
+__device__ __forceinline__ long long fidx(const Phys& P, int a, int i, int j, int k) {
+  return i + (long long)fdim(P, a, 0) * (j + (long long)fdim(P, a, 1) * k);
+}
+__device__ __forceinline__ int ncell(const Phys& P, int b) { return (b == 0) ? P.nx : (b == 1) ? P.ny : P.nz; }
+
+// Kozeny-Carman inverse permeability (Eq. perm): (1 - eps)^2 / (k0 eps^3).
+__device__ __forceinline__ double kinv(double e, double k0) {
+  double s = 1.0 - e;
+  return s * s / (k0 * e * e * e);
+}
+
+// van Leer weight w in c_f = c_U + w (c_D - c_U): w = psi(r)/2 with
+// psi(r) = (r + |r|)/(1 + |r|), r = (c_U - c_UU)/(c_D - c_U); zero without a
+// far-upwind cell or for |c_D - c_U| <= 1e-300.
+__device__ __forceinline__ double vl_weight(double cUU, double cU, double cD, bool has) {
+  double den = cD - cU;
+  if (!has || fabs(den) <= 1e-300) return 0.0;
+  double r = (cU - cUU) / den;
+  double ar = fabs(r);
+  return 0.5 * (r + ar) / (1.0 + ar);
+}
+
+// centred gradient component b of eps at a cell, zero-gradient ghosts
+__device__ __forceinline__ double cgrad(const Phys& P, const double* eps, int b, int i, int j, int k) {
+  int n = ncell(P, b);
+  int c[3] = {i, j, k};
+  int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+  lo[b] = c[b] > 0 ? c[b] - 1 : 0;
+  hi[b] = c[b] + 1 < n ? c[b] + 1 : n - 1;
+  return (eps[cidx(P, hi[0], hi[1], hi[2])] - eps[cidx(P, lo[0], lo[1], lo[2])]) / (2.0 * P.dx);
+}
+
+__device__ __forceinline__ bool cell_in(const Phys& P, int i, int j, int k) {
+  return i >= 0 && i < P.nx && j >= 0 && j < P.ny && k >= 0 && k < P.nz;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// S1: eps^{n+1} = clamp(eps^n + dt Vm R^n, eps_min, 1)   (Eq. mbs)
+// ---------------------------------------------------------------------------
+__global__ void k_eps_update(Phys P, double* eps, double* eps_old, const double* R, double dt, double* stats,
+                             RedScratch rs) {
+  const Box bx{P.nx, P.ny, P.nz};
+  const Seg s = make_seg(bx);
+  double acc[2] = {0.0, 0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    long long c = cidx(P, i, j, k);
+    double e = eps[c];
+    eps_old[c] = e;
+    double raw = e + dt * P.Vm * R[c];
+    double nw = fmin(fmax(raw, P.eps_min), 1.0);
+    eps[c] = nw;
+    acc[0] += raw - nw;
+    acc[1] += nw;
+  }
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    double V = (P.dim == 2) ? P.dx * P.dx : P.dx * P.dx * P.dx;
+    stats[ST_CLAMP] = acc[0] * V;
+    stats[ST_EPSSUM] = acc[1];
+  }
+}
+
+void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, double dt, double* stats,
+                       const RedScratch& rs, cudaStream_t st) {
+  Box bx{P.nx, P.ny, P.nz};
+  k_eps_update<<<grid_for(bx, kMaxRedBlocks), kThreads, 0, st>>>(P, eps, eps_old, R, dt, stats, rs);
+}
+
+// ---------------------------------------------------------------------------
+// S2: momentum predictor for component a (Eq. momentumDBS x eps, no inertia)
+//   (1/dt + nu eps_f k^-1_f) u_f - nu lap(u)_f = u^n_f/dt - eps_f (grad p^n)_f
+// Unknown box: the faces of a except the fixed ones (inlet face for x,
+// boundary faces for y/z); unknown (i,j,k) is face (i,j,k) + e_a, whose
+// minus cell is cell (i,j,k).
+// ---------------------------------------------------------------------------
+__global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__ eps, const double* __restrict__ p,
+                               const double* __restrict__ uold, double dt, double omega, Op<double> A,
+                               double* __restrict__ rhs) {
+  const Seg s = make_seg(ub);
+  const double cnu = P.nu / (P.dx * P.dx);
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, ub, q, i, j, k);
+    if (i >= ub.mx) continue;
+    const long long c = i + (long long)ub.mx * (j + (long long)ub.my * k);
+    int f[3] = {i, j, k};
+    f[a] += 1;  // face coordinates
+    int pc[3] = {i, j, k};
+    pc[a] += 1;  // plus cell
+    const bool has_plus = pc[a] < ncell(P, a);
+    const double em = eps[cidx(P, i, j, k)];
+    const double pm = p[cidx(P, i, j, k)];
+    double ef, kf, gp;
+    if (has_plus) {
+      const long long cp = cidx(P, pc[0], pc[1], pc[2]);
+      const double ep = eps[cp];
+      ef = 0.5 * (em + ep);
+      kf = 0.5 * (kinv(em, P.k0) + kinv(ep, P.k0));
+      gp = (p[cp] - pm) / P.dx;
+    } else {  // outlet face (a == x): one-sided, Dirichlet p = 0
+      ef = em;
+      kf = kinv(em, P.k0);
+      gp = -2.0 * pm / P.dx;
+    }
+    double diag = 1.0 / dt + P.nu * ef * kf;
+    double b = uold[fidx(P, a, f[0], f[1], f[2])] / dt - ef * gp;
+    double off[3] = {0.0, 0.0, 0.0};
+    const int nb = (P.dim == 2) ? 2 : 3;
+    const int um[3] = {ub.mx, ub.my, ub.mz};
+    for (int d = 0; d < nb; ++d) {
+      for (int sg = -1; sg <= 1; sg += 2) {
+        int u2[3] = {i, j, k};
+        u2[d] += sg;
+        if (u2[d] >= 0 && u2[d] < um[d]) {  // unknown neighbour
+          diag += cnu;
+          if (sg > 0) off[d] = -cnu;
+          continue;
+        }
+        int f2 = f[d] + sg;  // neighbour face coordinate along d
+        if (f2 >= 0 && f2 < fdim(P, a, d)) {  // fixed boundary face
+          diag += cnu;
+          double g = (a == 0 && d == 0 && f2 == 0) ? P.u_in : 0.0;
+          b += cnu * g;
+        } else {  // ghost outside the face array
+          double sgh;
+          if (d == 0) {
+            sgh = (sg < 0) ? -1.0 : 1.0;  // inlet plane: tangential 0; outlet: zero gradient
+          } else {
+            unsigned bit = (d == 1) ? (sg < 0 ? 1u : 2u) : (sg < 0 ? 4u : 8u);
+            sgh = (P.wall_mask & bit) ? -1.0 : 1.0;
+          }
+          diag += cnu * (1.0 - sgh);
+        }
+      }
+    }
+    A.diag[c] = diag;
+    A.dinv[c] = omega / diag;
+    A.xp[c] = off[0];
+    A.yp[c] = off[1];
+    if (A.zp) A.zp[c] = off[2];
+    rhs[c] = b;
+  }
+}
+
+void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, double dt,
+                         double omega, Op<double> A, double* rhs, cudaStream_t st) {
+  if (box_cells(A.box) == 0) return;
+  k_mom_assemble<<<grid_for(A.box, 0), kThreads, 0, st>>>(P, a, A.box, eps, p, uold, dt, omega, A, rhs);
+}
+
+// ---------------------------------------------------------------------------
+// S3: pressure correction  -div(eps_f grad phi) = -(div u* - s)/dt
+// (Eq. contDBS, s = R Vm (1 - rho_s/rho)); Neumann at inlet and walls,
+// phi = 0 on the outlet faces.
+// ---------------------------------------------------------------------------
+__global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const double* __restrict__ u0,
+                                const double* __restrict__ u1, const double* __restrict__ u2,
+                                const double* __restrict__ R, double dt, double omega, Op<double> A,
+                                double* __restrict__ rhs) {
+  const Box bx{P.nx, P.ny, P.nz};
+  const Seg s = make_seg(bx);
+  const double idx2 = 1.0 / (P.dx * P.dx);
+  const int nb = (P.dim == 2) ? 2 : 3;
+  const double* us[3] = {u0, u1, u2};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    const long long c = cidx(P, i, j, k);
+    const double e = eps[c];
+    double diag = 0.0, off[3] = {0.0, 0.0, 0.0}, div = 0.0;
+    for (int d = 0; d < nb; ++d) {
+      int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+      lo[d] -= 1;
+      hi[d] += 1;
+      if (cell_in(P, hi[0], hi[1], hi[2])) {
+        double a = 0.5 * (e + eps[cidx(P, hi[0], hi[1], hi[2])]) * idx2;
+        diag += a;
+        off[d] = -a;
+      }
+      if (cell_in(P, lo[0], lo[1], lo[2])) diag += 0.5 * (e + eps[cidx(P, lo[0], lo[1], lo[2])]) * idx2;
+      int fp[3] = {i, j, k};
+      fp[d] += 1;
+      div += (us[d][fidx(P, d, fp[0], fp[1], fp[2])] - us[d][fidx(P, d, i, j, k)]) / P.dx;
+    }
+    if (i == P.nx - 1) diag += 2.0 * e * idx2;
+    const double src = R[c] * P.Vm * (1.0 - P.rho_ratio);
+    A.diag[c] = diag;
+    A.dinv[c] = omega / diag;
+    A.xp[c] = off[0];
+    A.yp[c] = off[1];
+    if (A.zp) A.zp[c] = off[2];
+    rhs[c] = -(div - src) / dt;
+  }
+}
+
+void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3], const double* R, double dt,
+                          double omega, Op<double> A, double* rhs, cudaStream_t st) {
+  k_pres_assemble<<<grid_for(A.box, 0), kThreads, 0, st>>>(P, eps, us[0], us[1], us[2], R, dt, omega, A, rhs);
+}
+
+// u^{n+1} = u* - dt eps_f grad phi on interior faces and the outlet face;
+// fixed faces copy u*.
+__global__ void k_project(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ phi,
+                          double dt, const double* __restrict__ us, double* __restrict__ u) {
+  const Seg s = make_seg(fb);
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, fb, q, i, j, k);
+    if (i >= fb.mx) continue;
+    const long long fcx = i + (long long)fb.mx * (j + (long long)fb.my * k);
+    int f[3] = {i, j, k};
+    const int m = f[a], n = ncell(P, a);
+    double val = us[fcx];
+    if (m >= 1 && m <= n - 1) {
+      int mc[3] = {i, j, k};
+      mc[a] -= 1;
+      const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
+      val -= dt * 0.5 * (eps[cm] + eps[cp]) * (phi[cp] - phi[cm]) / P.dx;
+    } else if (a == 0 && m == n) {
+      const long long cm = cidx(P, i - 1, j, k);
+      val -= dt * eps[cm] * (-2.0 * phi[cm]) / P.dx;
+    }
+    u[fcx] = val;
+  }
+}
+
+__global__ void k_add(long long n, double* __restrict__ p, const double* __restrict__ phi) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    p[c] += phi[c];
+}
+
+void launch_project(const Phys& P, const double* eps, const double* phi, double dt, double* const us[3],
+                    double* const u[3], double* p, cudaStream_t st) {
+  const int nb = (P.dim == 2) ? 2 : 3;
+  for (int a = 0; a < nb; ++a) {
+    Box fb{P.nx + (a == 0), P.ny + (a == 1), P.nz + (a == 2)};
+    k_project<<<grid_for(fb, 0), kThreads, 0, st>>>(P, a, fb, eps, phi, dt, us[a], u[a]);
+  }
+  long long n = (long long)P.nx * P.ny * P.nz;
+  k_add<<<grid_for(Box{P.nx, P.ny, P.nz}, 0), kThreads, 0, st>>>(n, p, phi);
+}
+
+// ---------------------------------------------------------------------------
+// iVoS face data (Sec. 2.3, App. B).  Interior faces along a:
+//   g_f = ((eps_+ - eps_-)/dx along a; tangential: mean of the two cells'
+//   centred gradients), n_a = -g_a / (|g_f| + 1e-8/dx),
+//   s = k_c n_a / dx  (reactive flux per unit volume per unit c_f),
+//   w = van Leer weight of c^n along the flux direction (frozen),
+//   evl = van Leer interpolation of eps along the flux direction.
+// ---------------------------------------------------------------------------
+__global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ cold,
+                             FaceData fd) {
+  const Seg s = make_seg(fb);
+  const int nb = (P.dim == 2) ? 2 : 3;
+  const double delta = 1e-8 / P.dx;
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, fb, q, i, j, k);
+    if (i >= fb.mx) continue;
+    const long long fcx = i + (long long)fb.mx * (j + (long long)fb.my * k);
+    int f[3] = {i, j, k};
+    const int m = f[a], n = ncell(P, a);
+    if (m < 1 || m > n - 1) {
+      fd.s[fcx] = 0.0;
+      fd.w[fcx] = 0.0;
+      fd.evl[fcx] = 0.0;
+      continue;
+    }
+    int mc[3] = {i, j, k};
+    mc[a] -= 1;
+    const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
+    const double gn = (eps[cp] - eps[cm]) / P.dx;
+    double g2 = gn * gn;
+    for (int b = 0; b < nb; ++b) {
+      if (b == a) continue;
+      double gt = 0.5 * (cgrad(P, eps, b, mc[0], mc[1], mc[2]) + cgrad(P, eps, b, i, j, k));
+      g2 += gt * gt;
+    }
+    const double na = -gn / (sqrt(g2) + delta);
+    const bool pos = na > 0.0;
+    // upwind U, downwind D, far upwind UU along a
+    int uu[3] = {i, j, k};
+    long long cU, cD;
+    bool has;
+    if (pos) {
+      cU = cm;
+      cD = cp;
+      uu[a] = m - 2;
+      has = m - 2 >= 0;
+    } else {
+      cU = cp;
+      cD = cm;
+      uu[a] = m + 1;
+      has = m + 1 <= n - 1;
+    }
+    const long long cUU = has ? cidx(P, uu[0], uu[1], uu[2]) : cU;
+    fd.s[fcx] = P.kc * na / P.dx;
+    fd.w[fcx] = vl_weight(cold[cUU], cold[cU], cold[cD], has);
+    const double eU = eps[cU], eD = eps[cD];
+    fd.evl[fcx] = eU + vl_weight(eps[cUU], eU, eD, has) * (eD - eU);
+  }
+}
+
+void launch_ivos_faces(const Phys& P, const double* eps, const double* cold, const FaceData fd[3],
+                       cudaStream_t st) {
+  const int nb = (P.dim == 2) ? 2 : 3;
+  for (int a = 0; a < nb; ++a) {
+    Box fb{P.nx + (a == 0), P.ny + (a == 1), P.nz + (a == 2)};
+    k_ivos_faces<<<grid_for(fb, 0), kThreads, 0, st>>>(P, a, fb, eps, cold, fd[a]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// VoS-psi / VoS-psi' (Eq. RfVoSpsi, Sec. 2.4): psi = lambda eps (1 - eps),
+// centred gradient; psi': lambda = sum|g| / sum|g| eps (1 - eps) (FP64),
+// lambda = 4 when the denominator vanishes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double gradmag(const Phys& P, const double* eps, int i, int j, int k) {
+  double gx = cgrad(P, eps, 0, i, j, k), gy = cgrad(P, eps, 1, i, j, k);
+  double g2 = gx * gx + gy * gy;
+  if (P.dim == 3) {
+    double gz = cgrad(P, eps, 2, i, j, k);
+    g2 += gz * gz;
+  }
+  return sqrt(g2);
+}
+
+__global__ void k_vos_lambda(Phys P, const double* __restrict__ eps, double* stats, RedScratch rs) {
+  const Box bx{P.nx, P.ny, P.nz};
+  const Seg s = make_seg(bx);
+  double acc[2] = {0.0, 0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    double e = eps[cidx(P, i, j, k)];
+    double g = gradmag(P, eps, i, j, k);
+    acc[0] += g;
+    acc[1] += g * e * (1.0 - e);
+  }
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    double num = acc[0], den = acc[1];
+    stats[ST_LAMBDA] = (num == 0.0 || den < 1e-300 * num) ? 4.0 : num / den;
+  }
+}
+
+__global__ void k_set_scalar(double* dst, double v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
+}
+
+void launch_vos_lambda(const Phys& P, const double* eps, double lambda_fixed, int fit, double* stats,
+                       const RedScratch& rs, cudaStream_t st) {
+  if (fit) {
+    Box bx{P.nx, P.ny, P.nz};
+    k_vos_lambda<<<grid_for(bx, kMaxRedBlocks), kThreads, 0, st>>>(P, eps, stats, rs);
+  } else {
+    k_set_scalar<<<1, 32, 0, st>>>(stats + ST_LAMBDA, lambda_fixed);
+  }
+}
+
+__global__ void k_vos_coef(Phys P, const double* __restrict__ eps, const double* __restrict__ stats,
+                           double* __restrict__ kr) {
+  const Box bx{P.nx, P.ny, P.nz};
+  const Seg s = make_seg(bx);
+  const double lam = stats[ST_LAMBDA];
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    const long long c = cidx(P, i, j, k);
+    const double e = eps[c];
+    kr[c] = P.kc * lam * e * (1.0 - e) * gradmag(P, eps, i, j, k);
+  }
+}
+
+void launch_vos_coef(const Phys& P, const double* eps, const double* stats, double* kr, cudaStream_t st) {
+  Box bx{P.nx, P.ny, P.nz};
+  k_vos_coef<<<grid_for(bx, 0), kThreads, 0, st>>>(P, eps, stats, kr);
+}
+
+// ---------------------------------------------------------------------------
+// S4 + S5: transport system for c^{n+1} (Eq. concentrationDBS)
+//   eps c/dt - div(eps_f D grad c) + zeta R_f(c) = eps^n c^n/dt - div(c^n_f u)
+// Explicit van Leer convective flux (upwind along sign(u_f)); inlet faces
+// u_in c_in, outlet faces u c_last; Dirichlet c_in at the inlet for
+// diffusion (ghost 2 c_in - c_P).  R_f: VoS -> kr c; iVoS -> eps_P sum over
+// faces of the outward reactive flux with frozen van Leer weights.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double conv_flux(const Phys& P, int a, int i, int j, int k, const double* cold,
+                                            const double* ua) {
+  // flux through face (i,j,k) of axis a (face coords), per unit area
+  int f[3] = {i, j, k};
+  const int m = f[a], n = ncell(P, a);
+  const double uf = ua[fidx(P, a, i, j, k)];
+  if (m == 0) return (a == 0) ? uf * P.c_in : 0.0;
+  if (m == n) return (a == 0) ? uf * cold[cidx(P, (a == 0) ? i - 1 : i, j, k)] : 0.0;
+  int mc[3] = {i, j, k};
+  mc[a] -= 1;
+  const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
+  const bool pos = uf >= 0.0;
+  int uu[3] = {i, j, k};
+  long long cU, cD;
+  bool has;
+  if (pos) {
+    cU = cm;
+    cD = cp;
+    uu[a] = m - 2;
+    has = m - 2 >= 0;
+  } else {
+    cU = cp;
+    cD = cm;
+    uu[a] = m + 1;
+    has = m + 1 <= n - 1;
+  }
+  const double vU = cold[cU], vD = cold[cD];
+  const double vUU = has ? cold[cidx(P, uu[0], uu[1], uu[2])] : vU;
+  return uf * (vU + vl_weight(vUU, vU, vD, has) * (vD - vU));
+}
+
+template <bool IVOS>
+__global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const double* __restrict__ eps_old,
+                                 const double* __restrict__ cold, const double* __restrict__ u0,
+                                 const double* __restrict__ u1, const double* __restrict__ u2,
+                                 const double* __restrict__ kr, FaceData f0, FaceData f1, FaceData f2, double dt,
+                                 double omega, Op<double> A, double* __restrict__ rhs) {
+  const Box bx{P.nx, P.ny, P.nz};
+  const Seg s = make_seg(bx);
+  const double idx2 = 1.0 / (P.dx * P.dx);
+  const int nb = (P.dim == 2) ? 2 : 3;
+  const double* us[3] = {u0, u1, u2};
+  const FaceData fds[3] = {f0, f1, f2};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    const long long c = cidx(P, i, j, k);
+    const double e = eps[c];
+    double diag = e / dt;
+    double b = eps_old[c] * cold[c] / dt;
+    double offp[3] = {0, 0, 0}, offm[3] = {0, 0, 0};
+    double adv = 0.0;
+    for (int d = 0; d < nb; ++d) {
+      int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+      lo[d] -= 1;
+      hi[d] += 1;
+      const bool hasp = cell_in(P, hi[0], hi[1], hi[2]);
+      const bool hasm = cell_in(P, lo[0], lo[1], lo[2]);
+      if (hasp) {
+        double a = P.D * 0.5 * (e + eps[cidx(P, hi[0], hi[1], hi[2])]) * idx2;
+        diag += a;
+        offp[d] -= a;
+      }
+      if (hasm) {
+        double a = P.D * 0.5 * (e + eps[cidx(P, lo[0], lo[1], lo[2])]) * idx2;
+        diag += a;
+        offm[d] -= a;
+      }
+      // convective fluxes through the plus and minus faces
+      int fp[3] = {i, j, k};
+      fp[d] += 1;
+      adv += (conv_flux(P, d, fp[0], fp[1], fp[2], cold, us[d]) - conv_flux(P, d, i, j, k, cold, us[d])) / P.dx;
+      if (IVOS) {
+        const double zc = P.zeta * e;
+        if (hasp) {  // this cell is the minus cell of its plus face
+          const long long fx = fidx(P, d, fp[0], fp[1], fp[2]);
+          const double sf = fds[d].s[fx], w = fds[d].w[fx];
+          if (sf > 0.0) {  // U = this, D = plus
+            diag += zc * sf * (1.0 - w);
+            offp[d] += zc * sf * w;
+          } else {  // U = plus, D = this
+            diag += zc * sf * w;
+            offp[d] += zc * sf * (1.0 - w);
+          }
+        }
+        if (hasm) {  // this cell is the plus cell of its minus face (outward flux -F)
+          const long long fx = fidx(P, d, i, j, k);
+          const double sf = fds[d].s[fx], w = fds[d].w[fx];
+          if (sf > 0.0) {  // U = minus, D = this
+            diag -= zc * sf * w;
+            offm[d] -= zc * sf * (1.0 - w);
+          } else {  // U = this, D = minus
+            diag -= zc * sf * (1.0 - w);
+            offm[d] -= zc * sf * w;
+          }
+        }
+      }
+    }
+    if (i == 0) {
+      const double a = 2.0 * P.D * e * idx2;
+      diag += a;
+      b += a * P.c_in;
+    }
+    if (!IVOS) diag += P.zeta * kr[c];
+    b -= adv;
+    A.diag[c] = diag;
+    A.dinv[c] = omega / diag;
+    A.xp[c] = offp[0];
+    A.yp[c] = offp[1];
+    if (A.zp) A.zp[c] = offp[2];
+    if (!A.sym) {
+      A.xm[c] = offm[0];
+      A.ym[c] = offm[1];
+      if (A.zm) A.zm[c] = offm[2];
+    }
+    rhs[c] = b;
+  }
+}
+
+void launch_trans_assemble(const Phys& P, int ivos, const double* eps, const double* eps_old, const double* cold,
+                           double* const u[3], const double* kr, const FaceData fd[3], double dt, double omega,
+                           Op<double> A, double* rhs, cudaStream_t st) {
+  int g = grid_for(A.box, 0);
+  if (ivos)
+    k_trans_assemble<true><<<g, kThreads, 0, st>>>(P, eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2],
+                                                   dt, omega, A, rhs);
+  else
+    k_trans_assemble<false><<<g, kThreads, 0, st>>>(P, eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1],
+                                                    fd[2], dt, omega, A, rhs);
+}
+
+// ---------------------------------------------------------------------------
+// S6: reaction rates from c^{n+1}.
+//   iVoS (Eq. RfiVoS): R_f = eps_P sum_f outward F_f / V,
+//                      R   = R_f - sum_f outward evl_f F_f / V,
+//   with F_f / V = s_f (c_U + w (c_D - c_U)) on interior faces.
+//   VoS-psi('): R = R_f = kr c.
+// Also reduces sum R V, sum R_f V, sum eps c V.
+// ---------------------------------------------------------------------------
+template <bool IVOS>
+__global__ void k_rates(Phys P, const double* __restrict__ eps, const double* __restrict__ cn,
+                        const double* __restrict__ kr, FaceData f0, FaceData f1, FaceData f2, double* __restrict__ R,
+                        double* __restrict__ Rf, double* stats, RedScratch rs) {
+  const Box bx{P.nx, P.ny, P.nz};
+  const Seg s = make_seg(bx);
+  const int nb = (P.dim == 2) ? 2 : 3;
+  const FaceData fds[3] = {f0, f1, f2};
+  double acc[3] = {0.0, 0.0, 0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    const long long c = cidx(P, i, j, k);
+    const double e = eps[c];
+    double r, rf;
+    if (IVOS) {
+      double sumF = 0.0, sumEF = 0.0;
+      for (int d = 0; d < nb; ++d) {
+        int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+        lo[d] -= 1;
+        hi[d] += 1;
+        if (cell_in(P, hi[0], hi[1], hi[2])) {
+          int fp[3] = {i, j, k};
+          fp[d] += 1;
+          const long long fx = fidx(P, d, fp[0], fp[1], fp[2]);
+          const double sf = fds[d].s[fx], w = fds[d].w[fx];
+          const double cm = cn[c], cp = cn[cidx(P, hi[0], hi[1], hi[2])];
+          const double cU = sf > 0.0 ? cm : cp, cD = sf > 0.0 ? cp : cm;
+          const double F = sf * (cU + w * (cD - cU));
+          sumF += F;
+          sumEF += fds[d].evl[fx] * F;
+        }
+        if (cell_in(P, lo[0], lo[1], lo[2])) {
+          const long long fx = fidx(P, d, i, j, k);
+          const double sf = fds[d].s[fx], w = fds[d].w[fx];
+          const double cm = cn[cidx(P, lo[0], lo[1], lo[2])], cp = cn[c];
+          const double cU = sf > 0.0 ? cm : cp, cD = sf > 0.0 ? cp : cm;
+          const double F = sf * (cU + w * (cD - cU));
+          sumF -= F;
+          sumEF -= fds[d].evl[fx] * F;
+        }
+      }
+      rf = e * sumF;
+      r = rf - sumEF;
+    } else {
+      r = kr[c] * cn[c];
+      rf = r;
+    }
+    R[c] = r;
+    Rf[c] = rf;
+    acc[0] += r;
+    acc[1] += rf;
+    acc[2] += e * cn[c];
+  }
+  if (grid_sum<3>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    double V = (P.dim == 2) ? P.dx * P.dx : P.dx * P.dx * P.dx;
+    stats[ST_SUMR] = acc[0] * V;
+    stats[ST_SUMRF] = acc[1] * V;
+    stats[ST_REACT] = acc[2] * V;
+  }
+}
+
+void launch_rates(const Phys& P, int ivos, const double* eps, const double* c, const double* kr,
+                  const FaceData fd[3], double* R, double* Rf, double* stats, const RedScratch& rs,
+                  cudaStream_t st) {
+  Box bx{P.nx, P.ny, P.nz};
+  int g = grid_for(bx, kMaxRedBlocks);
+  if (ivos)
+    k_rates<true><<<g, kThreads, 0, st>>>(P, eps, c, kr, fd[0], fd[1], fd[2], R, Rf, stats, rs);
+  else
+    k_rates<false><<<g, kThreads, 0, st>>>(P, eps, c, kr, fd[0], fd[1], fd[2], R, Rf, stats, rs);
+}
+
+// ---------------------------------------------------------------------------
+// Time-step limits (App. D): max over faces of |u_f| / eps_f (interior:
+// mean of the two cells; boundary: the adjacent cell) and max |Vm R|.
+// ---------------------------------------------------------------------------
+__global__ void k_dt_limits(Phys P, const double* __restrict__ eps, const double* __restrict__ u0,
+                            const double* __restrict__ u1, const double* __restrict__ u2,
+                            const double* __restrict__ R, double* stats, RedScratch rs) {
+  const Box bx{P.nx, P.ny, P.nz};
+  const Seg s = make_seg(bx);
+  const int nb = (P.dim == 2) ? 2 : 3;
+  const double* us[3] = {u0, u1, u2};
+  double acc[2] = {0.0, 0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    const long long c = cidx(P, i, j, k);
+    const double e = eps[c];
+    for (int d = 0; d < nb; ++d) {
+      // minus face of this cell; the plus boundary face for the last cell
+      int lo[3] = {i, j, k};
+      lo[d] -= 1;
+      double ef = cell_in(P, lo[0], lo[1], lo[2]) ? 0.5 * (e + eps[cidx(P, lo[0], lo[1], lo[2])]) : e;
+      acc[0] = fmax(acc[0], fabs(us[d][fidx(P, d, i, j, k)]) / ef);
+      int f[3] = {i, j, k};
+      if (f[d] == ncell(P, d) - 1) {
+        f[d] += 1;
+        acc[0] = fmax(acc[0], fabs(us[d][fidx(P, d, f[0], f[1], f[2])]) / e);
+      }
+    }
+    acc[1] = fmax(acc[1], fabs(P.Vm * R[c]));
+  }
+  if (grid_max<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    stats[ST_UMAX] = acc[0];
+    stats[ST_RMAX] = acc[1];
+  }
+}
+
+void launch_dt_limits(const Phys& P, const double* eps, double* const u[3], const double* R, double* stats,
+                      const RedScratch& rs, cudaStream_t st) {
+  Box bx{P.nx, P.ny, P.nz};
+  k_dt_limits<<<grid_for(bx, kMaxRedBlocks), kThreads, 0, st>>>(P, eps, u[0], u[1], u[2] ? u[2] : u[0], R, stats,
+                                                                  rs);
+}
+
+}  // namespace vos

@@ -1,0 +1,273 @@
+// Internal declarations of the VoS CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace vos {
+
+constexpr int kThreads = 256;             // threads per block of every grid kernel
+constexpr int kWarps = kThreads / 32;     // warps per block
+constexpr int kMaxRedBlocks = 152 * 8;    // upper bound of blocks in reduction kernels
+constexpr int kMaxRedValues = 8;          // values reduced per reduction kernel
+
+// A box of unknowns, x fastest: index i + mx*(j + my*k).
+struct Box {
+  int mx, my, mz;
+};
+__host__ __device__ inline long long box_cells(Box b) { return (long long)b.mx * b.my * b.mz; }
+__host__ inline Box coarse_box(Box b) {
+  return Box{b.mx > 1 ? (b.mx + 1) / 2 : 1, b.my > 1 ? (b.my + 1) / 2 : 1, b.mz > 1 ? (b.mz + 1) / 2 : 1};
+}
+
+// Strided view of a box inside a larger array (e.g. the unknown faces of
+// a velocity component inside its face array): element (i,j,k) at
+// base[i + sy*j + sz*k].
+template <typename T>
+struct View {
+  T* base;
+  int sy, sz;
+};
+
+// 5/7-point stencil operator on a box:
+//   (A x)_c = diag_c x_c + sum over existing neighbours n of a_{c->n} x_n.
+// Symmetric operators store only the "plus" links (xp, yp, zp); the link
+// to the minus neighbour is the plus link of that neighbour.  Non-symmetric
+// operators also store xm, ym, zm.  dinv = omega / diag (Jacobi smoother).
+template <typename T>
+struct Op {
+  Box box;
+  int sym;
+  T *diag, *dinv, *xp, *yp, *zp, *xm, *ym, *zm;
+};
+
+// Work split: a warp handles one 32-cell row segment along x; blocks stride
+// over segments.  Grid size is fixed per box so reductions are deterministic.
+struct Seg {
+  int spr;        // segments per row
+  long long nseg; // total segments
+};
+__host__ __device__ inline Seg make_seg(Box b) {
+  Seg s;
+  s.spr = (b.mx + 31) / 32;
+  s.nseg = (long long)s.spr * b.my * b.mz;
+  return s;
+}
+__host__ int grid_for(Box b, int max_blocks);
+
+// Decode segment q -> (i, row) for this lane.
+__device__ __forceinline__ void seg_decode(const Seg& s, const Box& b, long long q, int& i, int& j,
+                                           int& k) {
+  long long row = q / s.spr;
+  i = (int)(q - row * s.spr) * 32 + (int)(threadIdx.x & 31);
+  j = (int)(row % b.my);
+  k = (int)(row / b.my);
+}
+
+#define VOS_SEG_LOOP(seg, q)                                                          \
+  for (long long q = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); q < (seg).nseg; \
+       q += (long long)gridDim.x * kWarps)
+
+// ---------------------------------------------------------------------------
+// Deterministic block / grid reductions (fixed order, FP64)
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kWarps];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    v[q] = x;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double x = (l < kWarps) ? sh[q][l] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[q] = x;
+    }
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_max(double (&v)[NV]) {
+  __shared__ double sh[NV][kWarps];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    v[q] = x;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double x = (l < kWarps) ? sh[q][l] : -1e308;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+      v[q] = x;
+    }
+  }
+}
+
+// Grid-wide sum: each block publishes its partial sums; the last block to
+// arrive adds the partials in block order and returns true in every thread
+// of that block, with the totals in thread 0's v[].  Scratch: partials has
+// room for NV * gridDim.x doubles; counter is 0 on entry and reset on exit.
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* counter) {
+  __shared__ bool last;
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) partials[q * gridDim.x + blockIdx.x] = v[q];
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    s[q] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[q] += __ldcg(partials + q * gridDim.x + b);
+  }
+  block_sum<NV>(s);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = s[q];
+    *counter = 0u;
+  }
+  return true;
+}
+
+template <int NV>
+__device__ bool grid_max(double (&v)[NV], double* partials, unsigned int* counter) {
+  __shared__ bool last;
+  block_max<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) partials[q * gridDim.x + blockIdx.x] = v[q];
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    s[q] = -1e308;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[q] = fmax(s[q], __ldcg(partials + q * gridDim.x + b));
+  }
+  block_max<NV>(s);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = s[q];
+    *counter = 0u;
+  }
+  return true;
+}
+
+// Reduction scratch shared by all kernels of one handle (one stream, so
+// kernels never overlap).
+struct RedScratch {
+  double* partials;       // kMaxRedValues * kMaxRedBlocks
+  unsigned int* counter;  // 1
+};
+
+// ---------------------------------------------------------------------------
+// Linear solver (vos_solver.cu)
+// ---------------------------------------------------------------------------
+
+// Device scalars of one Krylov solve (FP64).
+struct KScal {
+  double bb, rr, rz, rz_old, pq, alpha, beta, omega, rho, rhv, tol2;
+  double ss, ts, tt;
+  int done, iters, max_iters, breakdown;
+};
+
+struct MGParams {
+  double omega;   // Jacobi damping
+  double wc;      // coarse-correction weight
+  int nu;         // pre/post sweeps
+  int coarse_sweeps;
+};
+
+template <typename T>
+struct Level {
+  Op<T> op;
+  T *x, *t, *b;  // solution, ping-pong, right-hand side
+};
+
+// Multigrid hierarchy + Krylov vectors for one linear system.
+template <typename T>
+struct Hier {
+  int nlev;
+  Level<T> lev[16];
+  MGParams mg;
+};
+
+struct SolveResult {
+  int iters;      // total inner Krylov iterations
+  int outer;      // refinement passes
+  double relres;  // final true relative residual ||b - A x|| / ||b||
+  int converged;
+};
+
+// Host-side driver: outer FP64 refinement around an inner solve in T.
+// op64: fine operator in FP64 (for the true residual); h: hierarchy in T
+// (level 0 is the same operator in T); b: right-hand side (box layout);
+// x: solution view (initial guess on entry).  sym selects PCG or BiCGStab.
+struct SolverWork;  // opaque: Krylov vectors + scalars
+template <typename T>
+SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol,
+                  int max_iter, SolverWork* w, const RedScratch& rs, cudaStream_t st);
+
+template <typename T>
+void build_coarse_levels(Hier<T>& h, cudaStream_t st);
+
+// Layout helpers for allocation.
+template <typename T>
+size_t hier_bytes(Box fine, int sym, bool share_level0);
+size_t op64_bytes(Box b, int sym);
+void op64_carve(Op<double>& A, Box b, int sym, char*& cursor);
+extern int g_num_sms;
+template <typename T>
+void hier_carve(Hier<T>& h, Box fine, int sym, char*& cursor, const MGParams& mg, bool share_level0,
+                const Op<double>* op64);
+
+size_t solver_work_bytes(long long max_cells);
+SolverWork* solver_work_carve(char*& cursor, long long max_cells);
+void solver_work_free(SolverWork* w);
+
+// Error check helper
+#define VOS_CUDA_TRY(expr)                       \
+  do {                                           \
+    cudaError_t _e = (expr);                     \
+    if (_e != cudaSuccess) return _e;            \
+  } while (0)
+
+}  // namespace vos

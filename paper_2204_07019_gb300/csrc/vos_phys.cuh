@@ -1,0 +1,58 @@
+// Physics kernels of the VoS step (declarations shared by vos_fields.cu and
+// vos_capi.cu).
+#pragma once
+
+#include "vos_internal.cuh"
+
+namespace vos {
+
+struct Phys {
+  int dim, nx, ny, nz;
+  double dx, nu, D, kc, k0, Vm, zeta, rho_ratio, c_in, u_in, eps_min;
+  unsigned wall_mask;
+};
+
+// Device diagnostics (FP64), indices into the stats array.
+enum StatIdx {
+  ST_CLAMP = 0,   // sum(raw - clamped) V
+  ST_EPSSUM = 1,  // sum eps
+  ST_SUMR = 2,    // sum R V
+  ST_SUMRF = 3,   // sum R_f V
+  ST_REACT = 4,   // sum eps c V
+  ST_LAMBDA = 5,  // VoS lambda used
+  ST_UMAX = 6,    // max |u_f| / eps_f
+  ST_RMAX = 7,    // max |Vm R|
+  ST_COUNT = 8
+};
+
+struct FaceData {  // iVoS per-face data for one axis (face-array layout)
+  double *s, *w, *evl;
+};
+
+// S1
+void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, double dt, double* stats,
+                       const RedScratch& rs, cudaStream_t st);
+// S2
+void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, double dt,
+                         double omega, Op<double> A, double* rhs, cudaStream_t st);
+// S3
+void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3], const double* R, double dt,
+                          double omega, Op<double> A, double* rhs, cudaStream_t st);
+void launch_project(const Phys& P, const double* eps, const double* phi, double dt, double* const us[3],
+                    double* const u[3], double* p, cudaStream_t st);
+// S5/S6
+void launch_ivos_faces(const Phys& P, const double* eps, const double* cold, const FaceData fd[3],
+                       cudaStream_t st);
+void launch_vos_lambda(const Phys& P, const double* eps, double lambda_fixed, int fit, double* stats,
+                       const RedScratch& rs, cudaStream_t st);
+void launch_vos_coef(const Phys& P, const double* eps, const double* stats, double* kr, cudaStream_t st);
+void launch_trans_assemble(const Phys& P, int ivos, const double* eps, const double* eps_old, const double* cold,
+                           double* const u[3], const double* kr, const FaceData fd[3], double dt, double omega,
+                           Op<double> A, double* rhs, cudaStream_t st);
+void launch_rates(const Phys& P, int ivos, const double* eps, const double* c, const double* kr,
+                  const FaceData fd[3], double* R, double* Rf, double* stats, const RedScratch& rs,
+                  cudaStream_t st);
+void launch_dt_limits(const Phys& P, const double* eps, double* const u[3], const double* R, double* stats,
+                      const RedScratch& rs, cudaStream_t st);
+
+}  // namespace vos

@@ -1,0 +1,929 @@
+// Linear solvers of the VoS step: geometric multigrid (Jacobi smoothing,
+// Galerkin coarse operators with piecewise-constant transfer) as the
+// preconditioner of CG (symmetric systems: momentum, pressure, VoS-psi
+// transport) or BiCGStab (iVoS transport), inside an FP64 refinement loop
+// that recomputes the true residual b - A x in FP64.  The inner solve runs
+// in T = double (FP64 path) or T = float (mixed path); dot products and
+// norms are always accumulated in FP64 with deterministic reductions.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "vos_internal.cuh"
+
+namespace vos {
+
+int g_num_sms = 152;
+
+__host__ int grid_for(Box b, int max_blocks) {
+  Seg s = make_seg(b);
+  long long need = (s.nseg + kWarps - 1) / kWarps;
+  long long cap = (long long)g_num_sms * 8;
+  if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;  // reduction scratch holds kMaxRedBlocks partials
+  if (max_blocks > 0 && cap > max_blocks) cap = max_blocks;
+  if (need < 1) need = 1;
+  return (int)(need < cap ? need : cap);
+}
+
+struct SolverWork {
+  long long cap;
+  void *r, *z, *p, *p2, *q, *e, *rh, *v, *s, *t, *ph, *sh;
+  KScal* sc;        // device
+  KScal* sc_host;   // pinned
+  double* outer;    // device [rr, bb]
+  double* outer_host;
+};
+
+// ---------------------------------------------------------------------------
+// Stencil application
+// ---------------------------------------------------------------------------
+template <typename T, bool SYM, typename F>
+__device__ __forceinline__ T stencil(const Op<T>& A, int i, int j, int k, long long c, F xat) {
+  const Box b = A.box;
+  T y = A.diag[c] * xat(c, i, j, k);
+  if (i + 1 < b.mx) y += A.xp[c] * xat(c + 1, i + 1, j, k);
+  if (i > 0) y += (SYM ? A.xp[c - 1] : A.xm[c]) * xat(c - 1, i - 1, j, k);
+  const long long sy = b.mx;
+  if (j + 1 < b.my) y += A.yp[c] * xat(c + sy, i, j + 1, k);
+  if (j > 0) y += (SYM ? A.yp[c - sy] : A.ym[c]) * xat(c - sy, i, j - 1, k);
+  if (b.mz > 1) {
+    const long long sz = (long long)b.mx * b.my;
+    if (k + 1 < b.mz) y += A.zp[c] * xat(c + sz, i, j, k + 1);
+    if (k > 0) y += (SYM ? A.zp[c - sz] : A.zm[c]) * xat(c - sz, i, j, k - 1);
+  }
+  return y;
+}
+
+#define DONE_RETURN(sc) \
+  if ((sc) != nullptr && (sc)->done) return;
+
+// ---------------------------------------------------------------------------
+// Smoothing kernels
+// ---------------------------------------------------------------------------
+
+// x = dinv * b  (first Jacobi sweep from a zero guess)
+template <typename T>
+__global__ void k_smooth0(Op<T> A, const T* __restrict__ b, T* __restrict__ x, const KScal* sc) {
+  DONE_RETURN(sc);
+  const Seg s = make_seg(A.box);
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, A.box, q, i, j, k);
+    if (i >= A.box.mx) continue;
+    long long c = i + (long long)A.box.mx * (j + (long long)A.box.my * k);
+    x[c] = A.dinv[c] * b[c];
+  }
+}
+
+// FIN codes for the fused dot of the last level-0 smoothing sweep.
+enum Fin { FIN_NONE = 0, FIN_PCG_BETA = 1 };
+
+__device__ void fin_pcg_beta(KScal* sc, double rz) {
+  if (sc->iters == 0) {
+    sc->beta = 0.0;
+  } else {
+    sc->beta = rz / sc->rz;
+  }
+  sc->rz = rz;
+  if (!(rz > 0.0) || !isfinite(rz)) {
+    sc->breakdown = 1;
+    sc->done = 1;
+  }
+}
+
+// x_out = y + dinv (b - A y), y = x_in + wc * ec[parent] (if ec != null).
+// With FIN_PCG_BETA the kernel also reduces sum(b * x_out) (= r.z).
+template <typename T, bool SYM, int FIN>
+__global__ void k_smooth(Op<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
+                         const T* __restrict__ ec, Box cb, T wc, KScal* sc, RedScratch rs) {
+  DONE_RETURN(sc);
+  const Box bx = A.box;
+  const Seg s = make_seg(bx);
+  double acc[1] = {0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
+    T y;
+    if (ec != nullptr) {
+      auto yat = [&](long long cc, int ii, int jj, int kk) -> T {
+        long long pc = (ii >> 1) + (long long)cb.mx * ((jj >> 1) + (long long)cb.my * (kk >> 1));
+        return xin[cc] + wc * ec[pc];
+      };
+      T ax = stencil<T, SYM>(A, i, j, k, c, yat);
+      T yc = yat(c, i, j, k);
+      y = yc + A.dinv[c] * (b[c] - ax);
+    } else {
+      auto xat = [&](long long cc, int, int, int) -> T { return xin[cc]; };
+      T ax = stencil<T, SYM>(A, i, j, k, c, xat);
+      y = xin[c] + A.dinv[c] * (b[c] - ax);
+    }
+    xout[c] = y;
+    if (FIN != FIN_NONE) acc[0] += (double)b[c] * (double)y;
+  }
+  if (FIN != FIN_NONE) {
+    if (grid_sum<1>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+      if (FIN == FIN_PCG_BETA) fin_pcg_beta(sc, acc[0]);
+    }
+  }
+}
+
+// Coarse right-hand side: bc[I] = sum over children p of (b - A x)[p].
+template <typename T, bool SYM>
+__global__ void k_restrict(Op<T> A, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc, Box cb,
+                           const KScal* sc) {
+  DONE_RETURN(sc);
+  const Box fb = A.box;
+  const Seg s = make_seg(cb);
+  auto xat = [&](long long cc, int, int, int) -> T { return x[cc]; };
+  VOS_SEG_LOOP(s, q) {
+    int I, J, K;
+    seg_decode(s, cb, q, I, J, K);
+    if (I >= cb.mx) continue;
+    T sum = 0;
+    const int nk = (fb.mz > 1) ? 2 : 1, nj = (fb.my > 1) ? 2 : 1, ni = (fb.mx > 1) ? 2 : 1;
+    for (int dk = 0; dk < nk; ++dk) {
+      int k = 2 * K + dk;
+      if (fb.mz > 1 && k >= fb.mz) continue;
+      if (fb.mz == 1) k = 0;
+      for (int dj = 0; dj < nj; ++dj) {
+        int j = 2 * J + dj;
+        if (fb.my > 1 && j >= fb.my) continue;
+        if (fb.my == 1) j = 0;
+        for (int di = 0; di < ni; ++di) {
+          int i = 2 * I + di;
+          if (fb.mx > 1 && i >= fb.mx) continue;
+          if (fb.mx == 1) i = 0;
+          long long c = i + (long long)fb.mx * (j + (long long)fb.my * k);
+          sum += b[c] - stencil<T, SYM>(A, i, j, k, c, xat);
+        }
+      }
+    }
+    bc[I + (long long)cb.mx * (J + (long long)cb.my * K)] = sum;
+  }
+}
+
+// Coarsest level: nsweep damped-Jacobi sweeps from zero, one block, in
+// shared memory (box of at most kThreads cells).
+template <typename T, bool SYM>
+__global__ void k_coarse_solve(Op<T> A, const T* __restrict__ b, T* __restrict__ x, int nsweep, const KScal* sc) {
+  DONE_RETURN(sc);
+  __shared__ T xs[2][kThreads];
+  const Box bx = A.box;
+  const int n = (int)box_cells(bx);
+  const int c = threadIdx.x;
+  int i = 0, j = 0, k = 0;
+  if (c < n) {
+    i = c % bx.mx;
+    j = (c / bx.mx) % bx.my;
+    k = c / (bx.mx * bx.my);
+  }
+  T bc = (c < n) ? b[c] : T(0);
+  T dinv = (c < n) ? A.dinv[c] : T(0);
+  xs[0][c] = dinv * bc;
+  __syncthreads();
+  int cur = 0;
+  for (int it = 1; it < nsweep; ++it) {
+    if (c < n) {
+      auto xat = [&](long long cc, int, int, int) -> T { return xs[cur][cc]; };
+      T ax = stencil<T, SYM>(A, i, j, k, c, xat);
+      xs[cur ^ 1][c] = xs[cur][c] + dinv * (bc - ax);
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (c < n) x[c] = xs[cur][c];
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin coarse operator (piecewise-constant prolongation P, R = P^T)
+// ---------------------------------------------------------------------------
+template <typename T, bool SYM>
+__global__ void k_galerkin(Op<T> F, Op<T> C, T omega) {
+  const Box fb = F.box, cb = C.box;
+  const Seg s = make_seg(cb);
+  VOS_SEG_LOOP(s, q) {
+    int I, J, K;
+    seg_decode(s, cb, q, I, J, K);
+    if (I >= cb.mx) continue;
+    double d = 0, xp = 0, yp = 0, zp = 0, xm = 0, ym = 0, zm = 0;
+    const int nk = (fb.mz > 1) ? 2 : 1, nj = (fb.my > 1) ? 2 : 1, ni = (fb.mx > 1) ? 2 : 1;
+    for (int dk = 0; dk < nk; ++dk) {
+      int k = (fb.mz > 1) ? 2 * K + dk : 0;
+      if (k >= fb.mz) continue;
+      for (int dj = 0; dj < nj; ++dj) {
+        int j = (fb.my > 1) ? 2 * J + dj : 0;
+        if (j >= fb.my) continue;
+        for (int di = 0; di < ni; ++di) {
+          int i = (fb.mx > 1) ? 2 * I + di : 0;
+          if (i >= fb.mx) continue;
+          long long c = i + (long long)fb.mx * (j + (long long)fb.my * k);
+          d += (double)F.diag[c];
+          // x links
+          if (i + 1 < fb.mx) {
+            double a = (double)F.xp[c];
+            if (di == 0 && fb.mx > 1) {  // internal link to i+1 (same parent)
+              d += a;
+              if (SYM) d += a;
+            } else {
+              xp += a;
+            }
+          }
+          if (i > 0) {
+            if (!SYM) {
+              double a = (double)F.xm[c];
+              if (di == 1) d += a; else xm += a;
+            }
+          }
+          if (j + 1 < fb.my) {
+            double a = (double)F.yp[c];
+            if (dj == 0 && fb.my > 1) {
+              d += a;
+              if (SYM) d += a;
+            } else {
+              yp += a;
+            }
+          }
+          if (j > 0 && !SYM) {
+            double a = (double)F.ym[c];
+            if (dj == 1) d += a; else ym += a;
+          }
+          if (fb.mz > 1) {
+            if (k + 1 < fb.mz) {
+              double a = (double)F.zp[c];
+              if (dk == 0) {
+                d += a;
+                if (SYM) d += a;
+              } else {
+                zp += a;
+              }
+            }
+            if (k > 0 && !SYM) {
+              double a = (double)F.zm[c];
+              if (dk == 1) d += a; else zm += a;
+            }
+          }
+        }
+      }
+    }
+    long long cc = I + (long long)cb.mx * (J + (long long)cb.my * K);
+    C.diag[cc] = (T)d;
+    C.dinv[cc] = (T)((double)omega / d);
+    C.xp[cc] = (T)xp;
+    C.yp[cc] = (T)yp;
+    if (cb.mz > 1) C.zp[cc] = (T)zp;
+    if (!SYM) {
+      C.xm[cc] = (T)xm;
+      C.ym[cc] = (T)ym;
+      if (cb.mz > 1) C.zm[cc] = (T)zm;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Krylov vector kernels
+// ---------------------------------------------------------------------------
+__global__ void k_kscal_init(KScal* sc, const double* outer, double rtol_inner, int max_iters) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double rr = outer[0];
+    sc->bb = rr;
+    sc->rr = rr;
+    sc->rz = 0;
+    sc->rz_old = 0;
+    sc->pq = 0;
+    sc->alpha = 0;
+    sc->beta = 0;
+    sc->omega = 1.0;
+    sc->rho = rr;
+    sc->rhv = 0;
+    sc->tol2 = rtol_inner * rtol_inner * rr;
+    sc->iters = 0;
+    sc->max_iters = max_iters;
+    sc->breakdown = 0;
+    sc->done = (rr == 0.0) ? 1 : 0;
+  }
+}
+
+// PCG: p_new = z + beta p_old; q = A p_new; alpha = rz / (p_new . q)
+template <typename T, bool SYM>
+__global__ void k_pcg_pq(Op<T> A, const T* __restrict__ z, const T* __restrict__ pold, T* __restrict__ pnew,
+                         T* __restrict__ qv, KScal* sc, RedScratch rs) {
+  DONE_RETURN(sc);
+  const Box bx = A.box;
+  const Seg s = make_seg(bx);
+  const T beta = (T)sc->beta;
+  const bool first = (sc->iters == 0);
+  auto pat = [&](long long cc, int, int, int) -> T { return first ? z[cc] : z[cc] + beta * pold[cc]; };
+  double acc[1] = {0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
+    T pc = pat(c, i, j, k);
+    T qc = stencil<T, SYM>(A, i, j, k, c, pat);
+    pnew[c] = pc;
+    qv[c] = qc;
+    acc[0] += (double)pc * (double)qc;
+  }
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    double pq = acc[0];
+    sc->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      sc->breakdown = 1;
+      sc->done = 1;
+      sc->alpha = 0.0;
+    } else {
+      sc->alpha = sc->rz / pq;
+    }
+  }
+}
+
+// PCG: e += alpha p; r -= alpha q; rr = r.r; convergence check.
+template <typename T>
+__global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restrict__ qv, T* __restrict__ e,
+                         T* __restrict__ r, KScal* sc, RedScratch rs) {
+  DONE_RETURN(sc);
+  const T alpha = (T)sc->alpha;
+  double acc[1] = {0.0};
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    e[c] += alpha * p[c];
+    T rc = r[c] - alpha * qv[c];
+    r[c] = rc;
+    acc[0] += (double)rc * (double)rc;
+  }
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    sc->rr = acc[0];
+    sc->iters += 1;
+    if (acc[0] <= sc->tol2 || sc->iters >= sc->max_iters || !isfinite(acc[0])) sc->done = 1;
+  }
+}
+
+// BiCGStab: p = r + beta (p - omega v)   (first iteration: p = r)
+template <typename T>
+__global__ void k_bicg_p(long long n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ p,
+                         const KScal* sc) {
+  DONE_RETURN(sc);
+  const bool first = (sc->iters == 0);
+  const T beta = (T)sc->beta, omega = (T)sc->omega;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    p[c] = first ? r[c] : r[c] + beta * (p[c] - omega * v[c]);
+  }
+}
+
+// BiCGStab: v = A ph; alpha = rho / (rh . v)
+template <typename T, bool SYM>
+__global__ void k_bicg_v(Op<T> A, const T* __restrict__ ph, const T* __restrict__ rh, T* __restrict__ v, KScal* sc,
+                         RedScratch rs) {
+  DONE_RETURN(sc);
+  const Box bx = A.box;
+  const Seg s = make_seg(bx);
+  auto xat = [&](long long cc, int, int, int) -> T { return ph[cc]; };
+  double acc[1] = {0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
+    T vc = stencil<T, SYM>(A, i, j, k, c, xat);
+    v[c] = vc;
+    acc[0] += (double)rh[c] * (double)vc;
+  }
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    double rhv = acc[0];
+    sc->rhv = rhv;
+    if (rhv == 0.0 || !isfinite(rhv)) {
+      sc->breakdown = 1;
+      sc->done = 1;
+      sc->alpha = 0.0;
+    } else {
+      sc->alpha = sc->rho / rhv;
+    }
+  }
+}
+
+// BiCGStab: s = r - alpha v
+template <typename T>
+__global__ void k_bicg_s(long long n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ sv,
+                         const KScal* sc) {
+  DONE_RETURN(sc);
+  const T alpha = (T)sc->alpha;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    sv[c] = r[c] - alpha * v[c];
+}
+
+// BiCGStab: t = A sh; omega = (t.s)/(t.t)
+template <typename T, bool SYM>
+__global__ void k_bicg_t(Op<T> A, const T* __restrict__ sh, const T* __restrict__ sv, T* __restrict__ t, KScal* sc,
+                         RedScratch rs) {
+  DONE_RETURN(sc);
+  const Box bx = A.box;
+  const Seg s = make_seg(bx);
+  auto xat = [&](long long cc, int, int, int) -> T { return sh[cc]; };
+  double acc[2] = {0.0, 0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
+    T tc = stencil<T, SYM>(A, i, j, k, c, xat);
+    t[c] = tc;
+    acc[0] += (double)tc * (double)sv[c];
+    acc[1] += (double)tc * (double)tc;
+  }
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    sc->ts = acc[0];
+    sc->tt = acc[1];
+    if (acc[1] > 0.0 && isfinite(acc[1])) {
+      sc->omega = acc[0] / acc[1];
+    } else {
+      sc->omega = 0.0;
+    }
+  }
+}
+
+// BiCGStab: e += alpha ph + omega sh; r = s - omega t; rr, rho_new = rh.r
+template <typename T>
+__global__ void k_bicg_x(long long n, const T* __restrict__ ph, const T* __restrict__ sh, const T* __restrict__ sv,
+                         const T* __restrict__ t, const T* __restrict__ rh, T* __restrict__ e, T* __restrict__ r,
+                         KScal* sc, RedScratch rs) {
+  DONE_RETURN(sc);
+  const T alpha = (T)sc->alpha, omega = (T)sc->omega;
+  double acc[2] = {0.0, 0.0};
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    e[c] += alpha * ph[c] + omega * sh[c];
+    T rc = sv[c] - omega * t[c];
+    r[c] = rc;
+    acc[0] += (double)rc * (double)rc;
+    acc[1] += (double)rh[c] * (double)rc;
+  }
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    double rr = acc[0], rho_new = acc[1];
+    sc->rr = rr;
+    sc->iters += 1;
+    if (rr <= sc->tol2 || sc->iters >= sc->max_iters || !isfinite(rr)) sc->done = 1;
+    if (sc->omega == 0.0 || rho_new == 0.0 || !isfinite(rho_new)) {
+      sc->breakdown = 1;
+      sc->done = 1;
+    } else {
+      sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
+      sc->rho = rho_new;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 outer refinement kernels
+// ---------------------------------------------------------------------------
+// r_T = b - A64 x (x a strided view); outer[0] = |r|^2, outer[1] = |b|^2
+template <typename T, bool SYM>
+__global__ void k_outer_residual(Op<double> A, const double* __restrict__ b, View<double> x, T* __restrict__ rT,
+                                 double* outer, RedScratch rs) {
+  const Box bx = A.box;
+  const Seg s = make_seg(bx);
+  auto xat = [&](long long, int ii, int jj, int kk) -> double {
+    return x.base[ii + (long long)x.sy * jj + (long long)x.sz * kk];
+  };
+  double acc[2] = {0.0, 0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
+    double r = b[c] - stencil<double, SYM>(A, i, j, k, c, xat);
+    rT[c] = (T)r;
+    acc[0] += r * r;
+    acc[1] += b[c] * b[c];
+  }
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    outer[0] = acc[0];
+    outer[1] = acc[1];
+  }
+}
+
+// x += e (x a strided view)
+template <typename T>
+__global__ void k_outer_update(Box bx, View<double> x, const T* __restrict__ e) {
+  const Seg s = make_seg(bx);
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
+    x.base[i + (long long)x.sy * j + (long long)x.sz * k] += (double)e[c];
+  }
+}
+
+// x = 0 on a strided view
+__global__ void k_view_zero(Box bx, View<double> x) {
+  const Seg s = make_seg(bx);
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    x.base[i + (long long)x.sy * j + (long long)x.sz * k] = 0.0;
+  }
+}
+
+// Convert the FP64 operator into T (level 0 of a mixed-precision hierarchy).
+template <typename T>
+__global__ void k_op_convert(Op<double> A, Op<T> B, long long n) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    B.diag[c] = (T)A.diag[c];
+    B.dinv[c] = (T)A.dinv[c];
+    B.xp[c] = (T)A.xp[c];
+    B.yp[c] = (T)A.yp[c];
+    if (A.box.mz > 1) B.zp[c] = (T)A.zp[c];
+    if (!A.sym) {
+      B.xm[c] = (T)A.xm[c];
+      B.ym[c] = (T)A.ym[c];
+      if (A.box.mz > 1) B.zm[c] = (T)A.zm[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static int flat_grid(long long n) {
+  long long need = (n + kThreads - 1) / kThreads;
+  long long cap = (long long)g_num_sms * 8;
+  if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;
+  if (need < 1) need = 1;
+  return (int)(need < cap ? need : cap);
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T>
+static size_t op_bytes(Box b, int sym) {
+  size_t n = (size_t)box_cells(b);
+  int narr = 2 + (b.mz > 1 ? 3 : 2) * (sym ? 1 : 2);
+  return narr * align256(n * sizeof(T));
+}
+
+template <typename T>
+static void op_carve(Op<T>& A, Box b, int sym, char*& cur) {
+  size_t n = (size_t)box_cells(b);
+  size_t sz = align256(n * sizeof(T));
+  auto take = [&]() {
+    T* p = (T*)cur;
+    cur += sz;
+    return p;
+  };
+  A.box = b;
+  A.sym = sym;
+  A.diag = take();
+  A.dinv = take();
+  A.xp = take();
+  A.yp = take();
+  A.zp = (b.mz > 1) ? take() : nullptr;
+  if (!sym) {
+    A.xm = take();
+    A.ym = take();
+    A.zm = (b.mz > 1) ? take() : nullptr;
+  } else {
+    A.xm = A.ym = A.zm = nullptr;
+  }
+}
+
+static int count_levels(Box fine) {
+  int n = 1;
+  Box b = fine;
+  while (n < 16 && box_cells(b) > kThreads) {
+    Box c = coarse_box(b);
+    if (box_cells(c) == box_cells(b)) break;
+    b = c;
+    ++n;
+  }
+  return n;
+}
+
+template <typename T>
+size_t hier_bytes(Box fine, int sym, bool share_level0) {
+  size_t tot = 0;
+  int nlev = count_levels(fine);
+  Box b = fine;
+  for (int l = 0; l < nlev; ++l) {
+    size_t n = (size_t)box_cells(b);
+    if (!(l == 0 && share_level0)) tot += op_bytes<T>(b, sym);
+    if (l > 0) tot += 3 * align256(n * sizeof(T));
+    b = coarse_box(b);
+  }
+  return tot;
+}
+
+size_t op64_bytes(Box b, int sym) { return op_bytes<double>(b, sym); }
+void op64_carve(Op<double>& A, Box b, int sym, char*& cur) { op_carve<double>(A, b, sym, cur); }
+
+template <typename T>
+void hier_carve(Hier<T>& h, Box fine, int sym, char*& cur, const MGParams& mg, bool share_level0,
+                const Op<double>* op64) {
+  h.nlev = count_levels(fine);
+  h.mg = mg;
+  Box b = fine;
+  for (int l = 0; l < h.nlev; ++l) {
+    Level<T>& L = h.lev[l];
+    if (l == 0 && share_level0) {
+      std::memcpy(&L.op, op64, sizeof(Op<T>));  // T == double here: level 0 is op64
+    } else {
+      op_carve<T>(L.op, b, sym, cur);
+    }
+    size_t n = (size_t)box_cells(b);
+    if (l > 0) {
+      L.x = (T*)cur;
+      cur += align256(n * sizeof(T));
+      L.t = (T*)cur;
+      cur += align256(n * sizeof(T));
+      L.b = (T*)cur;
+      cur += align256(n * sizeof(T));
+    } else {
+      L.x = L.t = L.b = nullptr;
+    }
+    b = coarse_box(b);
+  }
+}
+
+template size_t hier_bytes<double>(Box, int, bool);
+template size_t hier_bytes<float>(Box, int, bool);
+template void hier_carve<double>(Hier<double>&, Box, int, char*&, const MGParams&, bool, const Op<double>*);
+template void hier_carve<float>(Hier<float>&, Box, int, char*&, const MGParams&, bool, const Op<double>*);
+
+size_t solver_work_bytes(long long max_cells) {
+  return 12 * align256((size_t)max_cells * sizeof(double)) + align256(sizeof(KScal)) + align256(2 * sizeof(double));
+}
+
+SolverWork* solver_work_carve(char*& cur, long long max_cells) {
+  SolverWork* w = new SolverWork();
+  w->cap = max_cells;
+  size_t vs = align256((size_t)max_cells * sizeof(double));
+  void** vec[12] = {&w->r, &w->z, &w->p, &w->p2, &w->q, &w->e, &w->rh, &w->v, &w->s, &w->t, &w->ph, &w->sh};
+  for (int i = 0; i < 12; ++i) {
+    *vec[i] = cur;
+    cur += vs;
+  }
+  w->sc = (KScal*)cur;
+  cur += align256(sizeof(KScal));
+  w->outer = (double*)cur;
+  cur += align256(2 * sizeof(double));
+  cudaMallocHost((void**)&w->sc_host, sizeof(KScal));
+  cudaMallocHost((void**)&w->outer_host, 2 * sizeof(double));
+  return w;
+}
+
+void solver_work_free(SolverWork* w) {
+  if (!w) return;
+  if (w->sc_host) cudaFreeHost(w->sc_host);
+  if (w->outer_host) cudaFreeHost(w->outer_host);
+  delete w;
+}
+
+template <typename T>
+void build_coarse_levels(Hier<T>& h, cudaStream_t st) {
+  for (int l = 1; l < h.nlev; ++l) {
+    Op<T>& F = h.lev[l - 1].op;
+    Op<T>& C = h.lev[l].op;
+    int g = grid_for(C.box, 0);
+    if (F.sym)
+      k_galerkin<T, true><<<g, kThreads, 0, st>>>(F, C, (T)h.mg.omega);
+    else
+      k_galerkin<T, false><<<g, kThreads, 0, st>>>(F, C, (T)h.mg.omega);
+  }
+}
+template void build_coarse_levels<double>(Hier<double>&, cudaStream_t);
+template void build_coarse_levels<float>(Hier<float>&, cudaStream_t);
+
+// One V(nu, nu) cycle: out = M^{-1} rhs (level-0 vectors supplied).
+// With fin == FIN_PCG_BETA the last sweep also reduces rhs . out.
+// Buffers: each level owns (b, x, t).  Pre-smoothing starts in t; every
+// sweep alternates t <-> x, so after the 2*nu sweeps of a level the result
+// is in x (an odd number of alternations after the first write).
+template <typename T, bool SYM>
+static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal* sc, const RedScratch& rs,
+                   cudaStream_t st) {
+  const int L = h.nlev;
+  const int nu = h.mg.nu;
+  const T wc = (T)h.mg.wc;
+  auto bufs = [&](int l, const T*& b, T*& x, T*& t) {
+    if (l == 0) {
+      b = rhs;
+      x = out;
+      t = scratch;
+    } else {
+      b = h.lev[l].b;
+      x = h.lev[l].x;
+      t = h.lev[l].t;
+    }
+  };
+  const Box none{1, 1, 1};
+  if (L == 1) {
+    // single level: damped Jacobi only (cs >= 2 sweeps, result in out)
+    const Op<T>& A = h.lev[0].op;
+    const T* b;
+    T *x, *t;
+    bufs(0, b, x, t);
+    const int cs = h.mg.coarse_sweeps < 2 ? 2 : h.mg.coarse_sweeps;
+    int g = grid_for(A.box, 0);
+    T* cur = ((cs - 1) % 2 == 0) ? x : t;
+    T* oth = (cur == t) ? x : t;
+    k_smooth0<T><<<g, kThreads, 0, st>>>(A, b, cur, sc);
+    for (int s = 1; s < cs; ++s) {
+      if (s == cs - 1 && fin == FIN_PCG_BETA)
+        k_smooth<T, SYM, FIN_PCG_BETA><<<g, kThreads, 0, st>>>(A, b, cur, oth, nullptr, none, T(0), sc, rs);
+      else
+        k_smooth<T, SYM, FIN_NONE><<<g, kThreads, 0, st>>>(A, b, cur, oth, nullptr, none, T(0), sc, rs);
+      T* tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+    return;
+  }
+  bool pre_in_t[16];
+  for (int l = 0; l < L - 1; ++l) {
+    const T* b;
+    T *x, *t;
+    bufs(l, b, x, t);
+    const Op<T>& A = h.lev[l].op;
+    const int g = grid_for(A.box, 0);
+    T* cur = t;
+    T* oth = x;
+    k_smooth0<T><<<g, kThreads, 0, st>>>(A, b, cur, sc);
+    for (int s = 1; s < nu; ++s) {
+      k_smooth<T, SYM, FIN_NONE><<<g, kThreads, 0, st>>>(A, b, cur, oth, nullptr, none, T(0), sc, rs);
+      T* tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+    pre_in_t[l] = (cur == t);
+    const Op<T>& C = h.lev[l + 1].op;
+    k_restrict<T, SYM><<<grid_for(C.box, 0), kThreads, 0, st>>>(A, b, cur, h.lev[l + 1].b, C.box, sc);
+  }
+  {
+    const Op<T>& A = h.lev[L - 1].op;
+    k_coarse_solve<T, SYM><<<1, kThreads, 0, st>>>(A, h.lev[L - 1].b, h.lev[L - 1].x, h.mg.coarse_sweeps, sc);
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const T* b;
+    T *x, *t;
+    bufs(l, b, x, t);
+    const Op<T>& A = h.lev[l].op;
+    const Box cb = h.lev[l + 1].op.box;
+    const T* ec = h.lev[l + 1].x;
+    const int g = grid_for(A.box, 0);
+    T* cur = pre_in_t[l] ? t : x;
+    T* oth = pre_in_t[l] ? x : t;
+    for (int s = 0; s < nu; ++s) {
+      const T* ecs = (s == 0) ? ec : nullptr;
+      if (s == nu - 1 && l == 0 && fin == FIN_PCG_BETA)
+        k_smooth<T, SYM, FIN_PCG_BETA><<<g, kThreads, 0, st>>>(A, b, cur, oth, ecs, cb, wc, sc, rs);
+      else
+        k_smooth<T, SYM, FIN_NONE><<<g, kThreads, 0, st>>>(A, b, cur, oth, ecs, cb, wc, sc, rs);
+      T* tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+  }
+}
+
+template <typename T, bool SYM>
+static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters, const RedScratch& rs,
+                     cudaStream_t st) {
+  const Box bx = h.lev[0].op.box;
+  const long long n = box_cells(bx);
+  T* r = (T*)w->r;
+  T* z = (T*)w->z;
+  T* p = (T*)w->p;
+  T* p2 = (T*)w->p2;
+  T* qv = (T*)w->q;
+  T* e = (T*)w->e;
+  T* scratch = (T*)w->t;
+  const Op<T>& A = h.lev[0].op;
+  cudaMemsetAsync(e, 0, n * sizeof(T), st);
+  k_kscal_init<<<1, 32, 0, st>>>(w->sc, w->outer, rtol_inner, max_iters);
+  vcycle<T, SYM>(h, r, z, scratch, FIN_PCG_BETA, w->sc, rs, st);
+  const int g = grid_for(bx, 0), gf = flat_grid(n);
+  const int chunk = 4;
+  int it = 0;
+  while (true) {
+    for (int c = 0; c < chunk; ++c) {
+      k_pcg_pq<T, SYM><<<g, kThreads, 0, st>>>(A, z, p, p2, qv, w->sc, rs);
+      T* tmp = p;
+      p = p2;
+      p2 = tmp;
+      k_pcg_xr<T><<<gf, kThreads, 0, st>>>(n, p, qv, e, r, w->sc, rs);
+      vcycle<T, SYM>(h, r, z, scratch, FIN_PCG_BETA, w->sc, rs, st);
+    }
+    it += chunk;
+    cudaMemcpyAsync(w->sc_host, w->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (w->sc_host->done || it >= max_iters + chunk) break;
+  }
+  return w->sc_host->iters;
+}
+
+template <typename T, bool SYM>
+static int inner_bicgstab(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters, const RedScratch& rs,
+                          cudaStream_t st) {
+  const Box bx = h.lev[0].op.box;
+  const long long n = box_cells(bx);
+  T* r = (T*)w->r;
+  T* rh = (T*)w->rh;
+  T* p = (T*)w->p;
+  T* v = (T*)w->v;
+  T* sv = (T*)w->s;
+  T* t = (T*)w->t;
+  T* ph = (T*)w->ph;
+  T* sh = (T*)w->sh;
+  T* e = (T*)w->e;
+  T* scratch = (T*)w->z;
+  const Op<T>& A = h.lev[0].op;
+  cudaMemsetAsync(e, 0, n * sizeof(T), st);
+  cudaMemsetAsync(v, 0, n * sizeof(T), st);
+  cudaMemcpyAsync(rh, r, n * sizeof(T), cudaMemcpyDeviceToDevice, st);
+  k_kscal_init<<<1, 32, 0, st>>>(w->sc, w->outer, rtol_inner, max_iters);
+  const int g = grid_for(bx, 0), gf = flat_grid(n);
+  const int chunk = 2;
+  int it = 0;
+  while (true) {
+    for (int c = 0; c < chunk; ++c) {
+      k_bicg_p<T><<<gf, kThreads, 0, st>>>(n, r, v, p, w->sc);
+      vcycle<T, SYM>(h, p, ph, scratch, FIN_NONE, w->sc, rs, st);
+      k_bicg_v<T, SYM><<<g, kThreads, 0, st>>>(A, ph, rh, v, w->sc, rs);
+      k_bicg_s<T><<<gf, kThreads, 0, st>>>(n, r, v, sv, w->sc);
+      vcycle<T, SYM>(h, sv, sh, scratch, FIN_NONE, w->sc, rs, st);
+      k_bicg_t<T, SYM><<<g, kThreads, 0, st>>>(A, sh, sv, t, w->sc, rs);
+      k_bicg_x<T><<<gf, kThreads, 0, st>>>(n, ph, sh, sv, t, rh, e, r, w->sc, rs);
+    }
+    it += chunk;
+    cudaMemcpyAsync(w->sc_host, w->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (w->sc_host->done || it >= max_iters + chunk) break;
+  }
+  return w->sc_host->iters;
+}
+
+template <typename T>
+SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol, int max_iter,
+                  SolverWork* w, const RedScratch& rs, cudaStream_t st) {
+  SolveResult res{0, 0, 0.0, 1};
+  const Box bx = op64.box;
+  const long long n = box_cells(bx);
+  if (n == 0) return res;
+  const bool mixed = (sizeof(T) == 4);
+  const int max_outer = mixed ? 30 : 8;
+  const int g = grid_for(bx, 0);
+  if (mixed) {
+    k_op_convert<T><<<flat_grid(n), kThreads, 0, st>>>(op64, h.lev[0].op, n);
+  }
+  build_coarse_levels<T>(h, st);
+  int total = 0;
+  for (int outer = 0;; ++outer) {
+    if (op64.sym)
+      k_outer_residual<T, true><<<g, kThreads, 0, st>>>(op64, b, x, (T*)w->r, w->outer, rs);
+    else
+      k_outer_residual<T, false><<<g, kThreads, 0, st>>>(op64, b, x, (T*)w->r, w->outer, rs);
+    cudaMemcpyAsync(w->outer_host, w->outer, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    const double rr = w->outer_host[0], bb = w->outer_host[1];
+    if (bb == 0.0) {
+      k_view_zero<<<g, kThreads, 0, st>>>(bx, x);
+      res.relres = 0.0;
+      res.outer = outer;
+      break;
+    }
+    const double rel = std::sqrt(rr / bb);
+    res.relres = rel;
+    res.outer = outer;
+    if (rel <= rtol) break;
+    if (outer >= max_outer || total >= max_iter || !std::isfinite(rel)) {
+      res.converged = 0;
+      break;
+    }
+    double rin = rtol / rel;
+    if (mixed) {
+      if (rin < 2e-5) rin = 2e-5;
+    } else {
+      rin *= 0.5;
+      if (rin < 1e-15) rin = 1e-15;
+    }
+    if (rin > 0.5) rin = 0.5;
+    int left = max_iter - total;
+    int its;
+    if (h.lev[0].op.sym)
+      its = inner_pcg<T, true>(h, w, rin, left, rs, st);
+    else
+      its = inner_bicgstab<T, false>(h, w, rin, left, rs, st);
+    total += its;
+    k_outer_update<T><<<g, kThreads, 0, st>>>(bx, x, (const T*)w->e);
+  }
+  res.iters = total;
+  return res;
+}
+
+template SolveResult solve<double>(const Op<double>&, Hier<double>&, const double*, View<double>, double, int,
+                                   SolverWork*, const RedScratch&, cudaStream_t);
+template SolveResult solve<float>(const Op<double>&, Hier<float>&, const double*, View<double>, double, int,
+                                  SolverWork*, const RedScratch&, cudaStream_t);
+
+}  // namespace vos

@@ -1,0 +1,336 @@
+"""ctypes binding of the C ABI in include/vos.h (argument marshalling only).
+
+Every step of the computation runs in ``libvos.so``; this module only
+converts arguments.  Importing it loads the library and raises if it is
+missing: there is no CPU fallback.  Device memory can come from PyTorch's
+caching allocator (``allocator="torch"``, the default when torch with CUDA
+is importable) and the work is enqueued on the caller's CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import inputs as _inputs
+
+__all__ = [
+    "VosError", "load_library", "vos_create", "vos_step", "vos_fields", "vos_set_fields",
+    "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
+    "vos_device_bytes", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS",
+]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
+
+VOS_OK, VOS_EINVAL, VOS_ENOMEM, VOS_ECUDA, VOS_ENOCONV = 0, -1, -2, -3, -4
+F_EPS, F_C, F_U, F_V, F_W, F_P, F_R, F_RF = 1, 2, 4, 8, 16, 32, 64, 128
+F_ALL = 255
+
+EXPORTED_SYMBOLS = [
+    "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
+    "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
+]
+
+
+class VosError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class VosParams(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("nu", ctypes.c_double), ("D", ctypes.c_double), ("kc", ctypes.c_double),
+        ("k0", ctypes.c_double), ("Vm", ctypes.c_double), ("zeta", ctypes.c_double),
+        ("rho_ratio", ctypes.c_double), ("c_in", ctypes.c_double), ("u_in", ctypes.c_double),
+        ("eps_min", ctypes.c_double), ("lambda_", ctypes.c_double),
+        ("method", ctypes.c_int32), ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
+        ("p_rtol", ctypes.c_double), ("u_rtol", ctypes.c_double), ("c_rtol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32), ("flow_subiters", ctypes.c_int32), ("wall_mask", ctypes.c_uint32),
+    ]
+
+
+class VosStats(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64), ("t", ctypes.c_double),
+        ("iters_u", ctypes.c_int32 * 3), ("iters_p", ctypes.c_int32), ("iters_c", ctypes.c_int32),
+        ("outer_u", ctypes.c_int32 * 3), ("outer_p", ctypes.c_int32), ("outer_c", ctypes.c_int32),
+        ("res_u", ctypes.c_double * 3), ("res_p", ctypes.c_double), ("res_c", ctypes.c_double),
+        ("lambda_", ctypes.c_double), ("porosity", ctypes.c_double), ("clamp_excess", ctypes.c_double),
+        ("sum_R", ctypes.c_double), ("sum_Rf", ctypes.c_double), ("reactant", ctypes.c_double),
+        ("status", ctypes.c_int32),
+    ]
+
+
+class VosDeviceFields(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("eps", "c", "p", "u", "v", "w", "R", "Rf")]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class VosAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load libvos.so (raises OSError if it is missing or does not load)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"libvos.so not found at {p}: build it with paper_2204_07019_gb300.build_lib.build()")
+    lib = ctypes.CDLL(p)
+    H = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.vos_create.argtypes = [dp, ctypes.POINTER(VosParams), ctypes.c_void_p, ctypes.POINTER(VosAllocator),
+                               ctypes.POINTER(H)]
+    lib.vos_create.restype = ctypes.c_int
+    lib.vos_step.argtypes = [H, ctypes.c_double]
+    lib.vos_step.restype = ctypes.c_int
+    lib.vos_fields.argtypes = [H, ctypes.c_uint32] + [dp] * 8
+    lib.vos_fields.restype = ctypes.c_int
+    lib.vos_set_fields.argtypes = [H, ctypes.c_uint32] + [dp] * 8
+    lib.vos_set_fields.restype = ctypes.c_int
+    lib.vos_device_fields_get.argtypes = [H, ctypes.POINTER(VosDeviceFields)]
+    lib.vos_device_fields_get.restype = ctypes.c_int
+    lib.vos_get_stats.argtypes = [H, ctypes.POINTER(VosStats)]
+    lib.vos_get_stats.restype = ctypes.c_int
+    lib.vos_suggest_dt.argtypes = [H, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.vos_suggest_dt.restype = ctypes.c_int
+    lib.vos_last_error.argtypes = [H]
+    lib.vos_last_error.restype = ctypes.c_char_p
+    lib.vos_destroy.argtypes = [H]
+    lib.vos_destroy.restype = None
+    lib.vos_device_bytes.argtypes = [H]
+    lib.vos_device_bytes.restype = ctypes.c_size_t
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _params_struct(prm):
+    p = VosParams()
+    full = dict(_inputs.PARAM_DEFAULTS)
+    full.update(prm)
+    for name, _ in VosParams._fields_:
+        key = "lam" if name == "lambda_" else name
+        setattr(p, name, type(getattr(p, name))(full[key]))
+    return p
+
+
+class _Handle:
+    """Owns a vos_handle* and keeps the allocator callbacks alive."""
+
+    def __init__(self, ptr, prm, keep):
+        self.ptr = ptr
+        self.prm = dict(prm)
+        self._keep = keep
+
+    @property
+    def shape(self):
+        return (int(self.prm["nz"]), int(self.prm["ny"]), int(self.prm["nx"]))
+
+
+def _check(lib, h, rc, allow_noconv=False):
+    if rc == VOS_OK or (allow_noconv and rc == VOS_ENOCONV):
+        return rc
+    msg = lib.vos_last_error(h).decode()
+    raise VosError(rc, msg)
+
+
+def _torch_allocator():
+    import torch
+    dev = torch.cuda.current_device()
+
+    def alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+        except Exception:  # noqa: BLE001 - report as NULL to the library
+            return None
+
+    def free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = ALLOC_FN(alloc), FREE_FN(free)
+    return VosAllocator(fa, ff, None), (fa, ff)
+
+
+def vos_create(eps_s, prm, stream=None, allocator="auto"):
+    """vos_create: eps_s (nz, ny, nx) float64 host array, parameter dict.
+
+    ``stream``: a torch.cuda.Stream, an int cudaStream_t or None (torch's
+    current stream if torch is available, else the legacy default stream).
+    ``allocator``: "torch", "cuda" or "auto".
+    """
+    lib = load_library()
+    es = np.ascontiguousarray(eps_s, dtype=np.float64)
+    ps = _params_struct(prm)
+    if es.size != ps.nx * ps.ny * ps.nz:
+        raise VosError(VOS_EINVAL, f"eps_s has {es.size} values, grid has {ps.nx * ps.ny * ps.nz}")
+    st = None
+    keep = []
+    alloc_ptr = None
+    use_torch = allocator == "torch"
+    if allocator == "auto":
+        try:
+            import torch
+            use_torch = torch.cuda.is_available()
+        except ImportError:
+            use_torch = False
+    if stream is None and use_torch:
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+    elif stream is not None:
+        st = int(getattr(stream, "cuda_stream", stream))
+    if use_torch:
+        a, cbs = _torch_allocator()
+        keep += [a, cbs]
+        alloc_ptr = ctypes.byref(a)
+    out = ctypes.c_void_p()
+    rc = lib.vos_create(es.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(ps),
+                        ctypes.c_void_p(st), alloc_ptr, ctypes.byref(out))
+    if rc != VOS_OK:
+        raise VosError(rc, lib.vos_last_error(None).decode())
+    return _Handle(out, prm, keep)
+
+
+def vos_step(h, dt):
+    """vos_step: one time step; returns VOS_OK or VOS_ENOCONV."""
+    lib = load_library()
+    return _check(lib, h.ptr, lib.vos_step(h.ptr, float(dt)), allow_noconv=True)
+
+
+def _field_shapes(h):
+    nz, ny, nx = h.shape
+    return {"eps": (nz, ny, nx), "c": (nz, ny, nx), "u": (nz, ny, nx + 1), "v": (nz, ny + 1, nx),
+            "w": (nz + 1, ny, nx), "p": (nz, ny, nx), "R": (nz, ny, nx), "Rf": (nz, ny, nx)}
+
+
+_ORDER = ("eps", "c", "u", "v", "w", "p", "R", "Rf")
+_BITS = dict(zip(_ORDER, (F_EPS, F_C, F_U, F_V, F_W, F_P, F_R, F_RF)))
+
+
+def vos_fields(h, names=_ORDER):
+    """vos_fields: copy fields to new host arrays; returns a dict."""
+    lib = load_library()
+    shp = _field_shapes(h)
+    dim = int(h.prm["dim"])
+    out, ptrs, mask = {}, [], 0
+    for n in _ORDER:
+        if n in names and not (n == "w" and dim == 2):
+            a = np.empty(shp[n], dtype=np.float64)
+            out[n] = a
+            mask |= _BITS[n]
+            ptrs.append(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        else:
+            ptrs.append(None)
+    _check(lib, h.ptr, lib.vos_fields(h.ptr, mask, *ptrs))
+    return out
+
+
+def vos_set_fields(h, **arrays):
+    """vos_set_fields: overwrite the given fields from host arrays."""
+    lib = load_library()
+    shp = _field_shapes(h)
+    ptrs, mask, keep = [], 0, []
+    for n in _ORDER:
+        if n in arrays:
+            a = np.ascontiguousarray(arrays[n], dtype=np.float64)
+            if a.size != int(np.prod(shp[n])):
+                raise VosError(VOS_EINVAL, f"{n}: {a.size} values, expected {shp[n]}")
+            keep.append(a)
+            mask |= _BITS[n]
+            ptrs.append(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        else:
+            ptrs.append(None)
+    _check(lib, h.ptr, lib.vos_set_fields(h.ptr, mask, *ptrs))
+
+
+def vos_device_fields_get(h):
+    """vos_device_fields_get: dict of device pointers (ints)."""
+    lib = load_library()
+    f = VosDeviceFields()
+    _check(lib, h.ptr, lib.vos_device_fields_get(h.ptr, ctypes.byref(f)))
+    return {n: getattr(f, n) for n, _ in VosDeviceFields._fields_}
+
+
+def vos_get_stats(h):
+    """vos_get_stats: statistics of the last step as a dict."""
+    lib = load_library()
+    s = VosStats()
+    _check(lib, h.ptr, lib.vos_get_stats(h.ptr, ctypes.byref(s)))
+    d = {}
+    for n, _ in VosStats._fields_:
+        v = getattr(s, n)
+        d["lambda" if n == "lambda_" else n] = list(v) if hasattr(v, "__len__") else v
+    return d
+
+
+def vos_suggest_dt(h, cfl=0.5, deps_max=0.005):
+    """vos_suggest_dt: min(cfl dx / max|u|/eps, deps_max / max|Vm R|)."""
+    lib = load_library()
+    dt = ctypes.c_double()
+    _check(lib, h.ptr, lib.vos_suggest_dt(h.ptr, float(cfl), float(deps_max), ctypes.byref(dt)))
+    return dt.value
+
+
+def vos_last_error(h=None):
+    lib = load_library()
+    return lib.vos_last_error(h.ptr if h is not None else None).decode()
+
+
+def vos_device_bytes(h):
+    return int(load_library().vos_device_bytes(h.ptr))
+
+
+def vos_destroy(h):
+    """vos_destroy: free the handle's device memory (idempotent)."""
+    if h is not None and h.ptr:
+        load_library().vos_destroy(h.ptr)
+        h.ptr = None
+
+
+class Simulation:
+    """Convenience wrapper: ``with Simulation(eps_s, prm) as sim: sim.step(dt)``."""
+
+    def __init__(self, eps_s, prm, stream=None, allocator="auto"):
+        self.h = vos_create(eps_s, prm, stream=stream, allocator=allocator)
+
+    def step(self, dt):
+        return vos_step(self.h, dt)
+
+    def fields(self, names=_ORDER):
+        return vos_fields(self.h, names)
+
+    def set_fields(self, **arrays):
+        vos_set_fields(self.h, **arrays)
+
+    def stats(self):
+        return vos_get_stats(self.h)
+
+    def suggest_dt(self, cfl=0.5, deps_max=0.005):
+        return vos_suggest_dt(self.h, cfl, deps_max)
+
+    def close(self):
+        vos_destroy(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

@@ -1,0 +1,74 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads,
+exports every function include/vos.h declares, and the ctypes structures
+match the C layout (checked with a gcc-compiled probe)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vos.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(vos_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2204_07019_gb300 import build_lib, vos
+    build_lib.build()
+    return vos.load_library()
+
+
+def test_header_declares_the_step_api():
+    names = _declared()
+    for n in ("vos_create", "vos_step", "vos_fields", "vos_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2204_07019_gb300 import vos
+    names = _declared()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(vos.EXPORTED_SYMBOLS) == names
+
+
+def test_struct_layout_matches_c(tmp_path):
+    from paper_2204_07019_gb300 import vos
+    src = tmp_path / "probe.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "vos.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(vos_params),'
+                   ' sizeof(vos_stats), sizeof(vos_device_fields), sizeof(vos_allocator),'
+                   ' offsetof(vos_params, p_rtol), offsetof(vos_params, wall_mask),'
+                   ' offsetof(vos_stats, status));return 0;}\n')
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(vos.VosParams), ctypes.sizeof(vos.VosStats), ctypes.sizeof(vos.VosDeviceFields),
+            ctypes.sizeof(vos.VosAllocator), vos.VosParams.p_rtol.offset, vos.VosParams.wall_mask.offset,
+            vos.VosStats.status.offset]
+    assert got == want
+
+
+def test_invalid_parameters_rejected_without_gpu(lib):
+    """vos_create validates before touching the device: bad sizes fail with
+    VOS_EINVAL and a message."""
+    import numpy as np
+    from paper_2204_07019_gb300 import inputs as I, vos
+    es = np.zeros((1, 4, 4))
+    for bad in (dict(dim=4), dict(nx=1), dict(eps_min=0.0), dict(method=7), dict(p_rtol=2.0),
+                dict(flow_subiters=3)):
+        prm = I.make_params(es.shape, Pe=1, Da=1, L=1, **bad)
+        with pytest.raises(vos.VosError) as ei:
+            vos.vos_create(es, prm, allocator="cuda")
+        assert ei.value.code == vos.VOS_EINVAL
+        assert vos.vos_last_error()
+    prm = I.make_params(es.shape, Pe=1, Da=1, L=1)
+    with pytest.raises(vos.VosError):
+        vos.vos_create(es + 2.0, prm, allocator="cuda")
