@@ -122,15 +122,20 @@ def init_dist(world, device):
     return dist
 
 
-def run_steps(V, h, dt, k):
-    st = []
-    for _ in range(k):
-        V.vos_step(h, dt)
-    return st
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 
 
-def time_gpu(V, es, prm, steps, warmup, torch):
-    """Create, warm up, then time ``steps`` steps with CUDA events."""
+def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
+    """Create, warm up, take a per-kernel breakdown of one untimed step, then
+    time ``steps`` steps with CUDA events while timing the dominant kernel's
+    launches with CUDA events on the same stream."""
     h = V.vos_create(es, prm)
     try:
         dt0 = 0.5 * prm["dx"] / max(abs(prm["u_in"]), 1e-30)
@@ -138,8 +143,32 @@ def time_gpu(V, es, prm, steps, warmup, torch):
         for _ in range(max(warmup - 1, 0)):
             V.vos_step(h, dt0)
         dt = min(V.vos_suggest_dt(h, 0.5, 0.005), 4.0 * dt0)
+        breakdown, top = None, None
+        if profile:
+            V.vos_prof_reset()
+            V.vos_prof_enable("*")
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            V.vos_step(h, dt)
+            e1.record()
+            torch.cuda.synchronize()
+            step_ms = e0.elapsed_time(e1)
+            rep = V.vos_prof_report()
+            V.vos_prof_enable(None)
+            V.vos_prof_reset()
+            tot = sum(v[1] for v in rep.values())
+            breakdown = sorted(({"kernel": k, "launches": v[0], "ms": v[1], "share": v[1] / tot if tot else 0.0,
+                                 "gbs": v[2] / (v[1] * 1e6) if v[1] > 0 else None} for k, v in rep.items()),
+                               key=lambda r: -r["ms"])
+            top = breakdown[0]["kernel"] if breakdown else None
+            breakdown = {"step_ms_profiled": step_ms, "kernel_ms_sum": tot, "kernels": breakdown[:14]}
         stream = torch.cuda.current_stream()
         iters = []
+        if top:
+            V.vos_prof_enable(top)
+        l0 = V.vos_kernel_launches()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -150,8 +179,22 @@ def time_gpu(V, es, prm, steps, warmup, torch):
             iters.append((s["iters_u"], s["iters_p"], s["iters_c"], s["res_p"]))
         e1.record(stream)
         torch.cuda.synchronize()
+        launches = V.vos_kernel_launches() - l0
         ms = e0.elapsed_time(e1) / steps
-        return ms, dt, iters, V.vos_device_bytes(h)
+        roof = None
+        if top:
+            rep = V.vos_prof_report()
+            V.vos_prof_enable(None)
+            V.vos_prof_reset()
+            n, kms, kbytes = rep.get(top, (0, 0.0, 0.0))
+            peak, src = measured_peaks()
+            if n > 0 and kms > 0:
+                ach = kbytes / (kms * 1e-3) / 1e9
+                roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "traffic": None, "kernel": top, "launches": n, "avg_launch_us": kms * 1e3 / n,
+                        "alg_bytes_per_launch": kbytes / n, "peak_source": src}
+        return dict(ms=ms, dt=dt, iters=iters, dev_bytes=V.vos_device_bytes(h), breakdown=breakdown,
+                    roofline=roof, launches=launches)
     finally:
         V.vos_destroy(h)
 
@@ -249,13 +292,13 @@ def main():
     V.load_library()
     es, prm, desc = workload(args.workload)
     N = es.size
-    launches0 = V.vos_kernel_launches() if hasattr(V, "vos_kernel_launches") else None
     clocks = ClockSampler(local)
     if dist is not None:
         dist.barrier()
     clocks.start()
-    ms, dt, iters, dev_bytes = time_gpu(V, es, prm, args.steps, args.warmup, torch)
+    r = time_gpu(V, es, prm, args.steps, args.warmup, torch)
     ck = clocks.stop()
+    ms, dt, iters = r["ms"], r["dt"], r["iters"]
     t = torch.tensor([ms], device=device)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -264,23 +307,23 @@ def main():
     value = N * world / (ms * 1e-3)
     p64 = dict(prm)
     p64["precision"] = 0
-    ms64, _, it64, _ = time_gpu(V, es, p64, max(args.fp64_steps, 1), 2, torch)
+    r64 = time_gpu(V, es, p64, max(args.fp64_steps, 1), 2, torch, profile=False)
     e2e = time_e2e(V, es, prm, max(2, args.steps // 2), dt)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": args.workload, "desc": desc, "cells": N, "dt": dt,
                       "p_rtol": prm["p_rtol"], "u_rtol": prm["u_rtol"], "c_rtol": prm["c_rtol"],
+                      "residual": "diagonally scaled, FP64",
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
-           "fp64": {"value": N * world / (ms64 * 1e-3), "ms_per_step": ms64,
-                    "iters_p_mean": float(np.mean([i[1] for i in it64]))},
+           "roofline": r["roofline"], "gpu_launches": r["launches"],
+           "fp64": {"value": N * world / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
+                    "iters_p_mean": float(np.mean([i[1] for i in r64["iters"]]))},
            "solver": {"iters_u_mean": [float(np.mean([i[0][a] for i in iters])) for a in range(3)],
                       "iters_p_mean": float(np.mean([i[1] for i in iters])),
                       "iters_c_mean": float(np.mean([i[2] for i in iters])),
                       "res_p_max": float(max(i[3] for i in iters))},
-           "device_bytes": dev_bytes, "e2e": e2e, "clocks": ck}
-    if launches0 is not None:
-        out["gpu_launches"] = None
+           "device_bytes": r["dev_bytes"], "e2e": e2e, "clocks": ck, "breakdown": r["breakdown"]}
     if rank == 0 and not args.no_cpu:
         r, n, shp, dtc = oracle_sample(es, prm, budget_s=15.0)
         out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -72,9 +72,9 @@ typedef enum { VOS_FP64 = 0, VOS_MIXED = 1 } vos_precision;
  * divergence-free flow of Eq. contDBSQS), c_in / u_in inlet concentration
  * and velocity, eps_min the fluid fraction kept inside the solid (App. C,
  * 1e-4), lambda the VoS-psi constant (4).  p_rtol / u_rtol / c_rtol:
- * relative residual ||b - Ax|| / ||b|| at which the pressure, momentum and
- * concentration solves stop; max_iter caps the Krylov iterations of one
- * solve. */
+ * diagonally scaled relative residual ||D^-1 (b - Ax)|| / ||D^-1 b|| (D the
+ * diagonal of A, FP64) at which the pressure, momentum and concentration
+ * solves stop; max_iter caps the Krylov iterations of one solve. */
 typedef struct vos_params {
   int32_t dim, nx, ny, nz; /* dim 2 (nz = 1) or 3 */
   double dx, nu, D, kc, k0, Vm, zeta, rho_ratio, c_in, u_in, eps_min, lambda;
@@ -93,7 +93,7 @@ typedef struct vos_stats {
   double t;
   int32_t iters_u[3], iters_p, iters_c;  /* Krylov iterations (inner, summed) */
   int32_t outer_u[3], outer_p, outer_c;  /* refinement passes                */
-  double res_u[3], res_p, res_c;         /* final true relative residuals    */
+  double res_u[3], res_p, res_c;         /* final scaled relative residuals  */
   double lambda;       /* psi' fit (psi: the constant; iVoS: NaN)            */
   double porosity;     /* mean eps                                           */
   double clamp_excess; /* sum(raw - clamped eps) * V of the S1 update        */
@@ -166,6 +166,22 @@ void vos_destroy(vos_handle* h);
 
 /* Bytes of device memory held by h. */
 size_t vos_device_bytes(const vos_handle* h);
+
+/* Diagnostics (process-wide, not tied to a handle; not thread-safe while
+ * timing is on).
+ * vos_kernel_launches: number of kernels this library has launched.
+ * vos_prof_enable: time every launch of the kernels whose name contains
+ *   one of the comma-separated substrings of filter ("*" = all, NULL or ""
+ *   = off) with CUDA events on the launching stream.
+ * vos_prof_report: write one line per timed kernel name,
+ *   "name<TAB>launches<TAB>total_ms<TAB>algorithmic_bytes\n", into buf
+ *   (synchronises on the recorded events).  Returns VOS_OK, or the buffer
+ *   size needed if len is too small.
+ * vos_prof_reset: drop the accumulated timings. */
+uint64_t vos_kernel_launches(void);
+int vos_prof_enable(const char* filter);
+int vos_prof_report(char* buf, size_t len);
+void vos_prof_reset(void);
 
 #ifdef __cplusplus
 }

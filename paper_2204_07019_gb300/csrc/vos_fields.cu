@@ -86,7 +86,7 @@ __global__ void k_eps_update(Phys P, double* eps, double* eps_old, const double*
 void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, double dt, double* stats,
                        const RedScratch& rs, cudaStream_t st) {
   Box bx{P.nx, P.ny, P.nz};
-  k_eps_update<<<grid_for(bx, kMaxRedBlocks), kThreads, 0, st>>>(P, eps, eps_old, R, dt, stats, rs);
+  vlaunch("eps_update", 32.0 * box_cells(bx), k_eps_update, grid_for(bx, kMaxRedBlocks), kThreads, st, P, eps, eps_old, R, dt, stats, rs);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,7 +168,7 @@ __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__
 void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, double dt,
                          double omega, Op<double> A, double* rhs, cudaStream_t st) {
   if (box_cells(A.box) == 0) return;
-  k_mom_assemble<<<grid_for(A.box, 0), kThreads, 0, st>>>(P, a, A.box, eps, p, uold, dt, omega, A, rhs);
+  vlaunch("mom_assemble", (6.0 + P.dim) * 8.0 * box_cells(A.box), k_mom_assemble, grid_for(A.box, 0), kThreads, st, P, a, A.box, eps, p, uold, dt, omega, A, rhs);
 }
 
 // ---------------------------------------------------------------------------
@@ -219,7 +219,7 @@ __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const do
 
 void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3], const double* R, double dt,
                           double omega, Op<double> A, double* rhs, cudaStream_t st) {
-  k_pres_assemble<<<grid_for(A.box, 0), kThreads, 0, st>>>(P, eps, us[0], us[1], us[2], R, dt, omega, A, rhs);
+  vlaunch("pres_assemble", (5.0 + 2.0 * P.dim) * 8.0 * box_cells(A.box), k_pres_assemble, grid_for(A.box, 0), kThreads, st, P, eps, us[0], us[1], us[2], R, dt, omega, A, rhs);
 }
 
 // u^{n+1} = u* - dt eps_f grad phi on interior faces and the outlet face;
@@ -258,10 +258,10 @@ void launch_project(const Phys& P, const double* eps, const double* phi, double 
   const int nb = (P.dim == 2) ? 2 : 3;
   for (int a = 0; a < nb; ++a) {
     Box fb{P.nx + (a == 0), P.ny + (a == 1), P.nz + (a == 2)};
-    k_project<<<grid_for(fb, 0), kThreads, 0, st>>>(P, a, fb, eps, phi, dt, us[a], u[a]);
+    vlaunch("project", 32.0 * box_cells(fb), k_project, grid_for(fb, 0), kThreads, st, P, a, fb, eps, phi, dt, us[a], u[a]);
   }
   long long n = (long long)P.nx * P.ny * P.nz;
-  k_add<<<grid_for(Box{P.nx, P.ny, P.nz}, 0), kThreads, 0, st>>>(n, p, phi);
+  vlaunch("p_update", 24.0 * n, k_add, grid_for(Box{P.nx, P.ny, P.nz}, 0), kThreads, st, n, p, phi);
 }
 
 // ---------------------------------------------------------------------------
@@ -330,7 +330,7 @@ void launch_ivos_faces(const Phys& P, const double* eps, const double* cold, con
   const int nb = (P.dim == 2) ? 2 : 3;
   for (int a = 0; a < nb; ++a) {
     Box fb{P.nx + (a == 0), P.ny + (a == 1), P.nz + (a == 2)};
-    k_ivos_faces<<<grid_for(fb, 0), kThreads, 0, st>>>(P, a, fb, eps, cold, fd[a]);
+    vlaunch("ivos_faces", 40.0 * box_cells(fb), k_ivos_faces, grid_for(fb, 0), kThreads, st, P, a, fb, eps, cold, fd[a]);
   }
 }
 
@@ -376,9 +376,9 @@ void launch_vos_lambda(const Phys& P, const double* eps, double lambda_fixed, in
                        const RedScratch& rs, cudaStream_t st) {
   if (fit) {
     Box bx{P.nx, P.ny, P.nz};
-    k_vos_lambda<<<grid_for(bx, kMaxRedBlocks), kThreads, 0, st>>>(P, eps, stats, rs);
+    vlaunch("vos_lambda", 8.0 * box_cells(bx), k_vos_lambda, grid_for(bx, kMaxRedBlocks), kThreads, st, P, eps, stats, rs);
   } else {
-    k_set_scalar<<<1, 32, 0, st>>>(stats + ST_LAMBDA, lambda_fixed);
+    vlaunch("set_scalar", 8.0, k_set_scalar, 1, 32, st, stats + ST_LAMBDA, lambda_fixed);
   }
 }
 
@@ -399,7 +399,7 @@ __global__ void k_vos_coef(Phys P, const double* __restrict__ eps, const double*
 
 void launch_vos_coef(const Phys& P, const double* eps, const double* stats, double* kr, cudaStream_t st) {
   Box bx{P.nx, P.ny, P.nz};
-  k_vos_coef<<<grid_for(bx, 0), kThreads, 0, st>>>(P, eps, stats, kr);
+  vlaunch("vos_coef", 16.0 * box_cells(bx), k_vos_coef, grid_for(bx, 0), kThreads, st, P, eps, stats, kr);
 }
 
 // ---------------------------------------------------------------------------
@@ -535,11 +535,11 @@ void launch_trans_assemble(const Phys& P, int ivos, const double* eps, const dou
                            Op<double> A, double* rhs, cudaStream_t st) {
   int g = grid_for(A.box, 0);
   if (ivos)
-    k_trans_assemble<true><<<g, kThreads, 0, st>>>(P, eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2],
-                                                   dt, omega, A, rhs);
+    vlaunch("trans_assemble", (6.0 + 5.0 * P.dim) * 8.0 * box_cells(A.box), k_trans_assemble<true>, g, kThreads, st, P,
+            eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2], dt, omega, A, rhs);
   else
-    k_trans_assemble<false><<<g, kThreads, 0, st>>>(P, eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1],
-                                                    fd[2], dt, omega, A, rhs);
+    vlaunch("trans_assemble", (7.0 + 2.0 * P.dim) * 8.0 * box_cells(A.box), k_trans_assemble<false>, g, kThreads, st, P,
+            eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2], dt, omega, A, rhs);
 }
 
 // ---------------------------------------------------------------------------
@@ -619,9 +619,9 @@ void launch_rates(const Phys& P, int ivos, const double* eps, const double* c, c
   Box bx{P.nx, P.ny, P.nz};
   int g = grid_for(bx, kMaxRedBlocks);
   if (ivos)
-    k_rates<true><<<g, kThreads, 0, st>>>(P, eps, c, kr, fd[0], fd[1], fd[2], R, Rf, stats, rs);
+    vlaunch("rates", (4.0 + 3.0 * P.dim) * 8.0 * box_cells(bx), k_rates<true>, g, kThreads, st, P, eps, c, kr, fd[0], fd[1], fd[2], R, Rf, stats, rs);
   else
-    k_rates<false><<<g, kThreads, 0, st>>>(P, eps, c, kr, fd[0], fd[1], fd[2], R, Rf, stats, rs);
+    vlaunch("rates", 40.0 * box_cells(bx), k_rates<false>, g, kThreads, st, P, eps, c, kr, fd[0], fd[1], fd[2], R, Rf, stats, rs);
 }
 
 // ---------------------------------------------------------------------------
@@ -665,8 +665,8 @@ __global__ void k_dt_limits(Phys P, const double* __restrict__ eps, const double
 void launch_dt_limits(const Phys& P, const double* eps, double* const u[3], const double* R, double* stats,
                       const RedScratch& rs, cudaStream_t st) {
   Box bx{P.nx, P.ny, P.nz};
-  k_dt_limits<<<grid_for(bx, kMaxRedBlocks), kThreads, 0, st>>>(P, eps, u[0], u[1], u[2] ? u[2] : u[0], R, stats,
-                                                                  rs);
+  vlaunch("dt_limits", (2.0 + P.dim) * 8.0 * box_cells(bx), k_dt_limits, grid_for(bx, kMaxRedBlocks), kThreads, st, P, eps, u[0], u[1],
+          u[2] ? u[2] : u[0], R, stats, rs);
 }
 
 }  // namespace vos

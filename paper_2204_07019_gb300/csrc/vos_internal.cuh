@@ -3,10 +3,32 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 
 namespace vos {
+
+// ---------------------------------------------------------------------------
+// Launch accounting: every kernel launch of the library goes through
+// vlaunch(), which counts it and, when per-kernel timing is enabled for a
+// matching name (vos_prof_enable), brackets it with CUDA events on the same
+// stream and records its algorithmic bytes.
+// ---------------------------------------------------------------------------
+extern std::atomic<unsigned long long> g_launch_count;
+extern bool g_prof_any;
+int prof_before(const char* name, double bytes, cudaStream_t st);
+void prof_after(int slot, cudaStream_t st);
+
+template <typename... KArgs, typename... Args>
+inline void vlaunch(const char* name, double bytes, void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                    Args&&... args) {
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);
+  int slot = g_prof_any ? prof_before(name, bytes, st) : -1;
+  k<<<grid, block, 0, st>>>(std::forward<Args>(args)...);
+  if (slot >= 0) prof_after(slot, st);
+}
 
 constexpr int kThreads = 256;             // threads per block of every grid kernel
 constexpr int kWarps = kThreads / 32;     // warps per block
@@ -233,7 +255,7 @@ struct Hier {
 struct SolveResult {
   int iters;      // total inner Krylov iterations
   int outer;      // refinement passes
-  double relres;  // final true relative residual ||b - A x|| / ||b||
+  double relres;  // final true scaled residual ||D^-1 (b - A x)|| / ||D^-1 b||
   int converged;
 };
 

@@ -57,6 +57,18 @@ __device__ __forceinline__ T stencil(const Op<T>& A, int i, int j, int k, long l
 #define DONE_RETURN(sc) \
   if ((sc) != nullptr && (sc)->done) return;
 
+// Names and algorithmic bytes of launches (per-kernel timing/roofline).
+#define KN(base, fine) \
+  ((fine) ? (sizeof(T) == 4 ? base "_f32_L0" : base "_f64_L0") : (sizeof(T) == 4 ? base "_f32_Lc" : base "_f64_Lc"))
+template <typename T>
+static inline double n_offs(const Op<T>& A) {
+  return (A.box.mz > 1 ? 3.0 : 2.0) * (A.sym ? 1.0 : 2.0);
+}
+template <typename T>
+static inline double ncell(const Op<T>& A) {
+  return (double)box_cells(A.box);
+}
+
 // ---------------------------------------------------------------------------
 // Smoothing kernels
 // ---------------------------------------------------------------------------
@@ -476,7 +488,10 @@ __global__ void k_bicg_x(long long n, const T* __restrict__ ph, const T* __restr
 // ---------------------------------------------------------------------------
 // FP64 outer refinement kernels
 // ---------------------------------------------------------------------------
-// r_T = b - A64 x (x a strided view); outer[0] = |r|^2, outer[1] = |b|^2
+// r_T = b - A64 x (x a strided view).  Convergence is measured on the
+// diagonally scaled residual: outer[0] = |D^-1 r|^2, outer[1] = |D^-1 b|^2,
+// which weighs every cell by its own coefficient scale (the coefficients of
+// solid cells are ~1e-4 of those of fluid cells).
 template <typename T, bool SYM>
 __global__ void k_outer_residual(Op<double> A, const double* __restrict__ b, View<double> x, T* __restrict__ rT,
                                  double* outer, RedScratch rs) {
@@ -493,8 +508,10 @@ __global__ void k_outer_residual(Op<double> A, const double* __restrict__ b, Vie
     long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
     double r = b[c] - stencil<double, SYM>(A, i, j, k, c, xat);
     rT[c] = (T)r;
-    acc[0] += r * r;
-    acc[1] += b[c] * b[c];
+    const double di = A.dinv[c];  // omega / diag: the constant omega cancels in the ratio
+    const double rs_ = r * di, bs = b[c] * di;
+    acc[0] += rs_ * rs_;
+    acc[1] += bs * bs;
   }
   if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
     outer[0] = acc[0];
@@ -685,10 +702,11 @@ void build_coarse_levels(Hier<T>& h, cudaStream_t st) {
     Op<T>& F = h.lev[l - 1].op;
     Op<T>& C = h.lev[l].op;
     int g = grid_for(C.box, 0);
+    const double gbytes = ((1.0 + n_offs(F)) * ncell(F) + (2.0 + n_offs(C)) * ncell(C)) * sizeof(T);
     if (F.sym)
-      k_galerkin<T, true><<<g, kThreads, 0, st>>>(F, C, (T)h.mg.omega);
+      vlaunch(KN("mg_galerkin", l == 1), gbytes, k_galerkin<T, true>, g, kThreads, st, F, C, (T)h.mg.omega);
     else
-      k_galerkin<T, false><<<g, kThreads, 0, st>>>(F, C, (T)h.mg.omega);
+      vlaunch(KN("mg_galerkin", l == 1), gbytes, k_galerkin<T, false>, g, kThreads, st, F, C, (T)h.mg.omega);
   }
 }
 template void build_coarse_levels<double>(Hier<double>&, cudaStream_t);
@@ -727,12 +745,13 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal*
     int g = grid_for(A.box, 0);
     T* cur = ((cs - 1) % 2 == 0) ? x : t;
     T* oth = (cur == t) ? x : t;
-    k_smooth0<T><<<g, kThreads, 0, st>>>(A, b, cur, sc);
+    const double sb = (5.0 + n_offs(A)) * ncell(A) * sizeof(T);
+    vlaunch(KN("mg_smooth0", true), 3.0 * ncell(A) * sizeof(T), k_smooth0<T>, g, kThreads, st, A, b, cur, sc);
     for (int s = 1; s < cs; ++s) {
       if (s == cs - 1 && fin == FIN_PCG_BETA)
-        k_smooth<T, SYM, FIN_PCG_BETA><<<g, kThreads, 0, st>>>(A, b, cur, oth, nullptr, none, T(0), sc, rs);
+        vlaunch(KN("mg_smooth", true), sb, k_smooth<T, SYM, FIN_PCG_BETA>, g, kThreads, st, A, b, cur, oth, nullptr, none, T(0), sc, rs);
       else
-        k_smooth<T, SYM, FIN_NONE><<<g, kThreads, 0, st>>>(A, b, cur, oth, nullptr, none, T(0), sc, rs);
+        vlaunch(KN("mg_smooth", true), sb, k_smooth<T, SYM, FIN_NONE>, g, kThreads, st, A, b, cur, oth, nullptr, none, T(0), sc, rs);
       T* tmp = cur;
       cur = oth;
       oth = tmp;
@@ -748,20 +767,21 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal*
     const int g = grid_for(A.box, 0);
     T* cur = t;
     T* oth = x;
-    k_smooth0<T><<<g, kThreads, 0, st>>>(A, b, cur, sc);
+    const double sb = (5.0 + n_offs(A)) * ncell(A) * sizeof(T);
+    vlaunch(KN("mg_smooth0", l == 0), 3.0 * ncell(A) * sizeof(T), k_smooth0<T>, g, kThreads, st, A, b, cur, sc);
     for (int s = 1; s < nu; ++s) {
-      k_smooth<T, SYM, FIN_NONE><<<g, kThreads, 0, st>>>(A, b, cur, oth, nullptr, none, T(0), sc, rs);
+      vlaunch(KN("mg_smooth", l == 0), sb, k_smooth<T, SYM, FIN_NONE>, g, kThreads, st, A, b, cur, oth, nullptr, none, T(0), sc, rs);
       T* tmp = cur;
       cur = oth;
       oth = tmp;
     }
     pre_in_t[l] = (cur == t);
     const Op<T>& C = h.lev[l + 1].op;
-    k_restrict<T, SYM><<<grid_for(C.box, 0), kThreads, 0, st>>>(A, b, cur, h.lev[l + 1].b, C.box, sc);
+    vlaunch(KN("mg_restrict", l == 0), ((3.0 + n_offs(A)) * ncell(A) + ncell(C)) * sizeof(T), k_restrict<T, SYM>, grid_for(C.box, 0), kThreads, st, A, b, cur, h.lev[l + 1].b, C.box, sc);
   }
   {
     const Op<T>& A = h.lev[L - 1].op;
-    k_coarse_solve<T, SYM><<<1, kThreads, 0, st>>>(A, h.lev[L - 1].b, h.lev[L - 1].x, h.mg.coarse_sweeps, sc);
+    vlaunch(KN("mg_coarse", false), (4.0 + n_offs(A)) * ncell(A) * sizeof(T), k_coarse_solve<T, SYM>, 1, kThreads, st, A, h.lev[L - 1].b, h.lev[L - 1].x, h.mg.coarse_sweeps, sc);
   }
   for (int l = L - 2; l >= 0; --l) {
     const T* b;
@@ -775,10 +795,11 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal*
     T* oth = pre_in_t[l] ? x : t;
     for (int s = 0; s < nu; ++s) {
       const T* ecs = (s == 0) ? ec : nullptr;
+      const double sb = ((5.0 + n_offs(A)) * ncell(A) + (ecs ? (double)box_cells(cb) : 0.0)) * sizeof(T);
       if (s == nu - 1 && l == 0 && fin == FIN_PCG_BETA)
-        k_smooth<T, SYM, FIN_PCG_BETA><<<g, kThreads, 0, st>>>(A, b, cur, oth, ecs, cb, wc, sc, rs);
+        vlaunch(KN("mg_smooth", true), sb, k_smooth<T, SYM, FIN_PCG_BETA>, g, kThreads, st, A, b, cur, oth, ecs, cb, wc, sc, rs);
       else
-        k_smooth<T, SYM, FIN_NONE><<<g, kThreads, 0, st>>>(A, b, cur, oth, ecs, cb, wc, sc, rs);
+        vlaunch(KN("mg_smooth", l == 0), sb, k_smooth<T, SYM, FIN_NONE>, g, kThreads, st, A, b, cur, oth, ecs, cb, wc, sc, rs);
       T* tmp = cur;
       cur = oth;
       oth = tmp;
@@ -800,18 +821,18 @@ static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters
   T* scratch = (T*)w->t;
   const Op<T>& A = h.lev[0].op;
   cudaMemsetAsync(e, 0, n * sizeof(T), st);
-  k_kscal_init<<<1, 32, 0, st>>>(w->sc, w->outer, rtol_inner, max_iters);
+  vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
   vcycle<T, SYM>(h, r, z, scratch, FIN_PCG_BETA, w->sc, rs, st);
   const int g = grid_for(bx, 0), gf = flat_grid(n);
   const int chunk = 4;
   int it = 0;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      k_pcg_pq<T, SYM><<<g, kThreads, 0, st>>>(A, z, p, p2, qv, w->sc, rs);
+      vlaunch(KN("pcg_pq", true), (5.0 + n_offs(A)) * n * sizeof(T), k_pcg_pq<T, SYM>, g, kThreads, st, A, z, p, p2, qv, w->sc, rs);
       T* tmp = p;
       p = p2;
       p2 = tmp;
-      k_pcg_xr<T><<<gf, kThreads, 0, st>>>(n, p, qv, e, r, w->sc, rs);
+      vlaunch(KN("pcg_xr", true), 6.0 * n * sizeof(T), k_pcg_xr<T>, gf, kThreads, st, n, p, qv, e, r, w->sc, rs);
       vcycle<T, SYM>(h, r, z, scratch, FIN_PCG_BETA, w->sc, rs, st);
     }
     it += chunk;
@@ -841,19 +862,19 @@ static int inner_bicgstab(Hier<T>& h, SolverWork* w, double rtol_inner, int max_
   cudaMemsetAsync(e, 0, n * sizeof(T), st);
   cudaMemsetAsync(v, 0, n * sizeof(T), st);
   cudaMemcpyAsync(rh, r, n * sizeof(T), cudaMemcpyDeviceToDevice, st);
-  k_kscal_init<<<1, 32, 0, st>>>(w->sc, w->outer, rtol_inner, max_iters);
+  vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
   const int g = grid_for(bx, 0), gf = flat_grid(n);
   const int chunk = 2;
   int it = 0;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      k_bicg_p<T><<<gf, kThreads, 0, st>>>(n, r, v, p, w->sc);
+      vlaunch(KN("bicg_p", true), 4.0 * n * sizeof(T), k_bicg_p<T>, gf, kThreads, st, n, r, v, p, w->sc);
       vcycle<T, SYM>(h, p, ph, scratch, FIN_NONE, w->sc, rs, st);
-      k_bicg_v<T, SYM><<<g, kThreads, 0, st>>>(A, ph, rh, v, w->sc, rs);
-      k_bicg_s<T><<<gf, kThreads, 0, st>>>(n, r, v, sv, w->sc);
+      vlaunch(KN("bicg_v", true), (4.0 + n_offs(A)) * n * sizeof(T), k_bicg_v<T, SYM>, g, kThreads, st, A, ph, rh, v, w->sc, rs);
+      vlaunch(KN("bicg_s", true), 3.0 * n * sizeof(T), k_bicg_s<T>, gf, kThreads, st, n, r, v, sv, w->sc);
       vcycle<T, SYM>(h, sv, sh, scratch, FIN_NONE, w->sc, rs, st);
-      k_bicg_t<T, SYM><<<g, kThreads, 0, st>>>(A, sh, sv, t, w->sc, rs);
-      k_bicg_x<T><<<gf, kThreads, 0, st>>>(n, ph, sh, sv, t, rh, e, r, w->sc, rs);
+      vlaunch(KN("bicg_t", true), (4.0 + n_offs(A)) * n * sizeof(T), k_bicg_t<T, SYM>, g, kThreads, st, A, sh, sv, t, w->sc, rs);
+      vlaunch(KN("bicg_x", true), 8.0 * n * sizeof(T), k_bicg_x<T>, gf, kThreads, st, n, ph, sh, sv, t, rh, e, r, w->sc, rs);
     }
     it += chunk;
     cudaMemcpyAsync(w->sc_host, w->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st);
@@ -874,20 +895,21 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
   const int max_outer = mixed ? 30 : 8;
   const int g = grid_for(bx, 0);
   if (mixed) {
-    k_op_convert<T><<<flat_grid(n), kThreads, 0, st>>>(op64, h.lev[0].op, n);
+    vlaunch("op_convert", (2.0 + n_offs(op64)) * n * (8.0 + sizeof(T)), k_op_convert<T>, flat_grid(n), kThreads, st, op64, h.lev[0].op, n);
   }
   build_coarse_levels<T>(h, st);
   int total = 0;
+  const double rbytes = (4.0 + n_offs(op64)) * n * 8.0 + n * sizeof(T);
   for (int outer = 0;; ++outer) {
     if (op64.sym)
-      k_outer_residual<T, true><<<g, kThreads, 0, st>>>(op64, b, x, (T*)w->r, w->outer, rs);
+      vlaunch("outer_residual_f64", rbytes, k_outer_residual<T, true>, g, kThreads, st, op64, b, x, (T*)w->r, w->outer, rs);
     else
-      k_outer_residual<T, false><<<g, kThreads, 0, st>>>(op64, b, x, (T*)w->r, w->outer, rs);
+      vlaunch("outer_residual_f64", rbytes, k_outer_residual<T, false>, g, kThreads, st, op64, b, x, (T*)w->r, w->outer, rs);
     cudaMemcpyAsync(w->outer_host, w->outer, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     const double rr = w->outer_host[0], bb = w->outer_host[1];
     if (bb == 0.0) {
-      k_view_zero<<<g, kThreads, 0, st>>>(bx, x);
+      vlaunch("view_zero", 8.0 * n, k_view_zero, g, kThreads, st, bx, x);
       res.relres = 0.0;
       res.outer = outer;
       break;
@@ -915,7 +937,7 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
     else
       its = inner_bicgstab<T, false>(h, w, rin, left, rs, st);
     total += its;
-    k_outer_update<T><<<g, kThreads, 0, st>>>(bx, x, (const T*)w->e);
+    vlaunch("outer_update", (double)n * (sizeof(T) + 16.0), k_outer_update<T>, g, kThreads, st, bx, x, (const T*)w->e);
   }
   res.iters = total;
   return res;

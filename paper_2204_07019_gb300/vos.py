@@ -19,7 +19,8 @@ from . import inputs as _inputs
 __all__ = [
     "VosError", "load_library", "vos_create", "vos_step", "vos_fields", "vos_set_fields",
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
-    "vos_device_bytes", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS",
+    "vos_device_bytes", "vos_kernel_launches", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
+    "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -31,6 +32,7 @@ F_ALL = 255
 EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
     "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
+    "vos_kernel_launches", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
 ]
 
 
@@ -112,6 +114,14 @@ def load_library(path=None):
     lib.vos_destroy.restype = None
     lib.vos_device_bytes.argtypes = [H]
     lib.vos_device_bytes.restype = ctypes.c_size_t
+    lib.vos_kernel_launches.argtypes = []
+    lib.vos_kernel_launches.restype = ctypes.c_uint64
+    lib.vos_prof_enable.argtypes = [ctypes.c_char_p]
+    lib.vos_prof_enable.restype = ctypes.c_int
+    lib.vos_prof_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    lib.vos_prof_report.restype = ctypes.c_int
+    lib.vos_prof_reset.argtypes = []
+    lib.vos_prof_reset.restype = None
     if path is None:
         _lib = lib
     return lib
@@ -290,6 +300,34 @@ def vos_last_error(h=None):
 
 def vos_device_bytes(h):
     return int(load_library().vos_device_bytes(h.ptr))
+
+
+def vos_kernel_launches():
+    """Kernels launched by the library so far (process-wide)."""
+    return int(load_library().vos_kernel_launches())
+
+
+def vos_prof_enable(filt):
+    """Time launches of kernels whose name contains one of the comma-separated
+    substrings ("*" all, None or "" off)."""
+    load_library().vos_prof_enable(filt.encode() if filt else None)
+
+
+def vos_prof_report():
+    """{name: (launches, total_ms, algorithmic_bytes)} of the timed kernels."""
+    lib = load_library()
+    n = lib.vos_prof_report(None, 0)
+    buf = ctypes.create_string_buffer(max(int(n), 1) + 1024)
+    lib.vos_prof_report(buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms, by = line.split("\t")
+        out[name] = (int(cnt), float(ms), float(by))
+    return out
+
+
+def vos_prof_reset():
+    load_library().vos_prof_reset()
 
 
 def vos_destroy(h):
