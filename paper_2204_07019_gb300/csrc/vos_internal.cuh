@@ -32,7 +32,7 @@ inline void vlaunch(const char* name, double bytes, void (*k)(KArgs...), dim3 gr
 
 constexpr int kThreads = 256;             // threads per block of every grid kernel
 constexpr int kWarps = kThreads / 32;     // warps per block
-constexpr int kMaxRedBlocks = 152 * 8;    // upper bound of blocks in reduction kernels
+constexpr int kMaxRedBlocks = 8192;       // upper bound of blocks in reduction kernels
 constexpr int kMaxRedValues = 8;          // values reduced per reduction kernel
 
 // A box of unknowns, x fastest: index i + mx*(j + my*k).
@@ -93,8 +93,13 @@ __device__ __forceinline__ void seg_decode(const Seg& s, const Box& b, long long
        q += (long long)gridDim.x * kWarps)
 
 // ---------------------------------------------------------------------------
-// Deterministic block / grid reductions (fixed order, FP64)
+// Deterministic block / grid reductions (fixed order, FP64).  Blocks of
+// kThreads threads in any shape; grids in any shape.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int lin_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
+__device__ __forceinline__ unsigned lin_bid() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
+__device__ __forceinline__ unsigned n_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
+
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   __shared__ double sh[NV][kWarps];
@@ -105,14 +110,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     v[q] = x;
   }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int t = lin_tid(), w = t >> 5, l = t & 31;
   __syncthreads();
   if (l == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (t < 32) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       double x = (l < kWarps) ? sh[q][l] : 0.0;
@@ -133,14 +138,14 @@ __device__ __forceinline__ void block_max(double (&v)[NV]) {
     for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
     v[q] = x;
   }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int t = lin_tid(), w = t >> 5, l = t & 31;
   __syncthreads();
   if (l == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (t < 32) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       double x = (l < kWarps) ? sh[q][l] : -1e308;
@@ -159,12 +164,14 @@ template <int NV>
 __device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* counter) {
   __shared__ bool last;
   block_sum<NV>(v);
-  if (threadIdx.x == 0) {
+  const unsigned nb = n_blocks();
+  const int t = lin_tid();
+  if (t == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) partials[q * gridDim.x + blockIdx.x] = v[q];
+    for (int q = 0; q < NV; ++q) partials[q * nb + lin_bid()] = v[q];
     __threadfence();
     unsigned int prev = atomicAdd(counter, 1u);
-    last = (prev == gridDim.x - 1);
+    last = (prev == nb - 1);
   }
   __syncthreads();
   if (!last) return false;
@@ -173,10 +180,10 @@ __device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* counte
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     s[q] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[q] += __ldcg(partials + q * gridDim.x + b);
+    for (int b = t; b < (int)nb; b += kThreads) s[q] += __ldcg(partials + q * nb + b);
   }
   block_sum<NV>(s);
-  if (threadIdx.x == 0) {
+  if (t == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = s[q];
     *counter = 0u;
@@ -188,12 +195,14 @@ template <int NV>
 __device__ bool grid_max(double (&v)[NV], double* partials, unsigned int* counter) {
   __shared__ bool last;
   block_max<NV>(v);
-  if (threadIdx.x == 0) {
+  const unsigned nb = n_blocks();
+  const int t = lin_tid();
+  if (t == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) partials[q * gridDim.x + blockIdx.x] = v[q];
+    for (int q = 0; q < NV; ++q) partials[q * nb + lin_bid()] = v[q];
     __threadfence();
     unsigned int prev = atomicAdd(counter, 1u);
-    last = (prev == gridDim.x - 1);
+    last = (prev == nb - 1);
   }
   __syncthreads();
   if (!last) return false;
@@ -202,10 +211,10 @@ __device__ bool grid_max(double (&v)[NV], double* partials, unsigned int* counte
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     s[q] = -1e308;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[q] = fmax(s[q], __ldcg(partials + q * gridDim.x + b));
+    for (int b = t; b < (int)nb; b += kThreads) s[q] = fmax(s[q], __ldcg(partials + q * nb + b));
   }
   block_max<NV>(s);
-  if (threadIdx.x == 0) {
+  if (t == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = s[q];
     *counter = 0u;

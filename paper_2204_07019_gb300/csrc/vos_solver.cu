@@ -69,24 +69,6 @@ static inline double ncell(const Op<T>& A) {
   return (double)box_cells(A.box);
 }
 
-// ---------------------------------------------------------------------------
-// Smoothing kernels
-// ---------------------------------------------------------------------------
-
-// x = dinv * b  (first Jacobi sweep from a zero guess)
-template <typename T>
-__global__ void k_smooth0(Op<T> A, const T* __restrict__ b, T* __restrict__ x, const KScal* sc) {
-  DONE_RETURN(sc);
-  const Seg s = make_seg(A.box);
-  VOS_SEG_LOOP(s, q) {
-    int i, j, k;
-    seg_decode(s, A.box, q, i, j, k);
-    if (i >= A.box.mx) continue;
-    long long c = i + (long long)A.box.mx * (j + (long long)A.box.my * k);
-    x[c] = A.dinv[c] * b[c];
-  }
-}
-
 // FIN codes for the fused dot of the last level-0 smoothing sweep.
 enum Fin { FIN_NONE = 0, FIN_PCG_BETA = 1 };
 
@@ -103,41 +85,245 @@ __device__ void fin_pcg_beta(KScal* sc, double rz) {
   }
 }
 
-// x_out = y + dinv (b - A y), y = x_in + wc * ec[parent] (if ec != null).
-// With FIN_PCG_BETA the kernel also reduces sum(b * x_out) (= r.z).
-template <typename T, bool SYM, int FIN>
-__global__ void k_smooth(Op<T> A, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
-                         const T* __restrict__ ec, Box cb, T wc, KScal* sc, RedScratch rs) {
-  DONE_RETURN(sc);
+// ---------------------------------------------------------------------------
+// 2.5D stencil sweeps: a (blockDim.x x blockDim.y) tile of threads in the
+// (x, y) plane marches along z over zc planes; the z-neighbours of the input
+// vector and the z-link coefficient of the plane below stay in registers,
+// x/y neighbours come through L1.  2D boxes are remapped to (mx, 1, my) so
+// that y is the marched axis (see zview).
+// val(c, i, j, k) gives the input vector at a cell (it may be computed, e.g.
+// with a fused prolongation); emit(c, i, j, k, v_c, Av_c, diag_c) consumes
+// the result.  Threads outside the box do nothing but stay for reductions.
+// ---------------------------------------------------------------------------
+template <typename T, bool SYM, class VAL, class EMIT>
+__device__ __forceinline__ void zmarch(const Op<T>& A, int zc, VAL val, EMIT emit) {
   const Box bx = A.box;
-  const Seg s = make_seg(bx);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  if (i >= bx.mx || j >= bx.my || k0 >= k1) return;
+  const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+  long long c = i + sy * j + sz * k0;
+  T v_lo = (k0 > 0) ? val(c - sz, i, j, k0 - 1) : T(0);
+  T v_c = val(c, i, j, k0);
+  T zl = (SYM && k0 > 0) ? A.zp[c - sz] : T(0);
+  for (int k = k0; k < k1; ++k, c += sz) {
+    const bool up = (k + 1 < bx.mz);
+    const T v_hi = up ? val(c + sz, i, j, k + 1) : T(0);
+    const T d = A.diag[c];
+    T ax = d * v_c;
+    if (i + 1 < bx.mx) ax += A.xp[c] * val(c + 1, i + 1, j, k);
+    if (i > 0) ax += (SYM ? A.xp[c - 1] : A.xm[c]) * val(c - 1, i - 1, j, k);
+    if (j + 1 < bx.my) ax += A.yp[c] * val(c + sy, i, j + 1, k);
+    if (j > 0) ax += (SYM ? A.yp[c - sy] : A.ym[c]) * val(c - sy, i, j - 1, k);
+    if (bx.mz > 1) {
+      const T zu = up ? A.zp[c] : T(0);
+      ax += zu * v_hi;
+      if (k > 0) ax += (SYM ? zl : A.zm[c]) * v_lo;
+      zl = zu;
+    }
+    emit(c, i, j, k, v_c, ax, d);
+    v_lo = v_c;
+    v_c = v_hi;
+  }
+}
+
+// Jacobi weight omega / diag: computed in FP32 registers, read in FP64
+// (FP64 division is slow on this part).
+template <typename T>
+__device__ __forceinline__ T jacobi_w(const Op<T>& A, long long c, T d, T omega) {
+  if constexpr (sizeof(T) == 4) {
+    return __fdividef(omega, d);
+  } else {
+    return A.dinv[c];
+  }
+}
+
+// Jacobi sweep variants (MODE): 0 plain x_out = x + w (b - A x);
+// 1 first two sweeps from zero fused (x = w b computed at every cell read);
+// 2 with the coarse correction x + wc ec[parent] fused into the input.
+// FIN: also reduce b . x_out for the PCG beta.
+template <typename T, bool SYM, int MODE, int FIN>
+__global__ void __launch_bounds__(kThreads) k_jacobi(Op<T> A, const T* __restrict__ b, const T* __restrict__ xin,
+                                                    T* __restrict__ xout, const T* __restrict__ ec, Box cb, T wc,
+                                                    T omega, int zc, KScal* sc, RedScratch rs) {
+  DONE_RETURN(sc);
   double acc[1] = {0.0};
+  auto val = [&](long long c, int i, int j, int k) -> T {
+    if constexpr (MODE == 1) {
+      return jacobi_w<T>(A, c, A.diag[c], omega) * b[c];
+    } else if constexpr (MODE == 2) {
+      long long pc = (i >> 1) + (long long)cb.mx * ((j >> 1) + (long long)cb.my * (k >> 1));
+      return xin[c] + wc * ec[pc];
+    } else {
+      return xin[c];
+    }
+  };
+  auto emit = [&](long long c, int, int, int, T v, T ax, T d) {
+    const T bc = b[c];
+    const T y = v + jacobi_w<T>(A, c, d, omega) * (bc - ax);
+    xout[c] = y;
+    if (FIN) acc[0] += (double)bc * (double)y;
+  };
+  zmarch<T, SYM>(A, zc, val, emit);
+  if (FIN != FIN_NONE) {
+    if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_pcg_beta(sc, acc[0]);
+  }
+}
+
+// PCG: p_new = z + beta p_old; q = A p_new; alpha = rz / (p_new . q)
+template <typename T, bool SYM>
+__global__ void __launch_bounds__(kThreads) k_pcg_pq_z(Op<T> A, const T* __restrict__ z, const T* __restrict__ pold,
+                                                      T* __restrict__ pnew, T* __restrict__ qv, int zc, KScal* sc,
+                                                      RedScratch rs) {
+  DONE_RETURN(sc);
+  const T beta = (T)sc->beta;
+  const bool first = (sc->iters == 0);
+  double acc[1] = {0.0};
+  auto val = [&](long long c, int, int, int) -> T { return first ? z[c] : z[c] + beta * pold[c]; };
+  auto emit = [&](long long c, int, int, int, T v, T ax, T) {
+    pnew[c] = v;
+    qv[c] = ax;
+    acc[0] += (double)v * (double)ax;
+  };
+  zmarch<T, SYM>(A, zc, val, emit);
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    double pq = acc[0];
+    sc->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      sc->breakdown = 1;
+      sc->done = 1;
+      sc->alpha = 0.0;
+    } else {
+      sc->alpha = sc->rz / pq;
+    }
+  }
+}
+
+// BiCGStab: v = A ph; alpha = rho / (rh . v)
+template <typename T, bool SYM>
+__global__ void __launch_bounds__(kThreads) k_bicg_v_z(Op<T> A, const T* __restrict__ ph, const T* __restrict__ rh,
+                                                      T* __restrict__ v, int zc, KScal* sc, RedScratch rs) {
+  DONE_RETURN(sc);
+  double acc[1] = {0.0};
+  auto val = [&](long long c, int, int, int) -> T { return ph[c]; };
+  auto emit = [&](long long c, int, int, int, T, T ax, T) {
+    v[c] = ax;
+    acc[0] += (double)rh[c] * (double)ax;
+  };
+  zmarch<T, SYM>(A, zc, val, emit);
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    double rhv = acc[0];
+    sc->rhv = rhv;
+    if (rhv == 0.0 || !isfinite(rhv)) {
+      sc->breakdown = 1;
+      sc->done = 1;
+      sc->alpha = 0.0;
+    } else {
+      sc->alpha = sc->rho / rhv;
+    }
+  }
+}
+
+// BiCGStab: t = A sh; omega = (t.s)/(t.t)
+template <typename T, bool SYM>
+__global__ void __launch_bounds__(kThreads) k_bicg_t_z(Op<T> A, const T* __restrict__ sh, const T* __restrict__ sv,
+                                                      T* __restrict__ t, int zc, KScal* sc, RedScratch rs) {
+  DONE_RETURN(sc);
+  double acc[2] = {0.0, 0.0};
+  auto val = [&](long long c, int, int, int) -> T { return sh[c]; };
+  auto emit = [&](long long c, int, int, int, T, T ax, T) {
+    t[c] = ax;
+    acc[0] += (double)ax * (double)sv[c];
+    acc[1] += (double)ax * (double)ax;
+  };
+  zmarch<T, SYM>(A, zc, val, emit);
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    sc->ts = acc[0];
+    sc->tt = acc[1];
+    sc->omega = (acc[1] > 0.0 && isfinite(acc[1])) ? acc[0] / acc[1] : 0.0;
+  }
+}
+
+// FP64 true residual (see k_outer_residual) in the 2.5D form.
+template <typename T, bool SYM>
+__global__ void __launch_bounds__(kThreads) k_outer_residual_z(Op<double> A, const double* __restrict__ b,
+                                                              View<double> x, T* __restrict__ rT, double* outer,
+                                                              int zc, RedScratch rs) {
+  double acc[2] = {0.0, 0.0};
+  auto val = [&](long long, int i, int j, int k) -> double {
+    return x.base[i + (long long)x.sy * j + (long long)x.sz * k];
+  };
+  auto emit = [&](long long c, int, int, int, double, double ax, double) {
+    const double r = b[c] - ax;
+    rT[c] = (T)r;
+    const double di = A.dinv[c];  // omega / diag: the constant omega cancels in the ratio
+    const double r1 = r * di, b1 = b[c] * di;
+    acc[0] += r1 * r1;
+    acc[1] += b1 * b1;
+  };
+  zmarch<double, SYM>(A, zc, val, emit);
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    outer[0] = acc[0];
+    outer[1] = acc[1];
+  }
+}
+
+// Host: remap 2D boxes (mz == 1) so that y is the marched axis.
+template <typename T>
+static Op<T> zview(const Op<T>& A) {
+  if (A.box.mz > 1 || A.box.my == 1) return A;
+  Op<T> B = A;
+  B.box = Box{A.box.mx, 1, A.box.my};
+  B.zp = A.yp;
+  B.zm = A.ym;
+  B.yp = nullptr;
+  B.ym = nullptr;
+  return B;
+}
+static Box zbox(Box b) { return (b.mz > 1 || b.my == 1) ? b : Box{b.mx, 1, b.my}; }
+static View<double> zview_x(View<double> x, Box b) {
+  if (b.mz > 1 || b.my == 1) return x;
+  return View<double>{x.base, 0, x.sy};
+}
+
+struct ZCfg {
+  dim3 grid, block;
+  int zc;
+};
+// Tile 32 x 8 (x, y), or 256 x 1 when the box has one row per plane; z
+// chunk so that the grid has about 4096 blocks and at most kMaxRedBlocks.
+static ZCfg zcfg(Box b) {
+  ZCfg z;
+  const int tx = (b.my == 1) ? 256 : 32, ty = kThreads / tx;
+  const long long gx = (b.mx + tx - 1) / tx, gy = (b.my + ty - 1) / ty;
+  const long long tiles = gx * gy;
+  long long zc = (tiles * b.mz + 4095) / 4096;
+  if (zc < 4) zc = 4;
+  if (zc > b.mz) zc = b.mz;
+  while (tiles * ((b.mz + zc - 1) / zc) > kMaxRedBlocks) ++zc;
+  z.block = dim3(tx, ty, 1);
+  z.grid = dim3((unsigned)gx, (unsigned)gy, (unsigned)((b.mz + zc - 1) / zc));
+  z.zc = (int)zc;
+  return z;
+}
+
+// ---------------------------------------------------------------------------
+// Smoothing kernels
+// ---------------------------------------------------------------------------
+
+// x = dinv * b  (first Jacobi sweep from a zero guess)
+template <typename T>
+__global__ void k_smooth0(Op<T> A, const T* __restrict__ b, T* __restrict__ x, const KScal* sc) {
+  DONE_RETURN(sc);
+  const Seg s = make_seg(A.box);
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
-    seg_decode(s, bx, q, i, j, k);
-    if (i >= bx.mx) continue;
-    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
-    T y;
-    if (ec != nullptr) {
-      auto yat = [&](long long cc, int ii, int jj, int kk) -> T {
-        long long pc = (ii >> 1) + (long long)cb.mx * ((jj >> 1) + (long long)cb.my * (kk >> 1));
-        return xin[cc] + wc * ec[pc];
-      };
-      T ax = stencil<T, SYM>(A, i, j, k, c, yat);
-      T yc = yat(c, i, j, k);
-      y = yc + A.dinv[c] * (b[c] - ax);
-    } else {
-      auto xat = [&](long long cc, int, int, int) -> T { return xin[cc]; };
-      T ax = stencil<T, SYM>(A, i, j, k, c, xat);
-      y = xin[c] + A.dinv[c] * (b[c] - ax);
-    }
-    xout[c] = y;
-    if (FIN != FIN_NONE) acc[0] += (double)b[c] * (double)y;
-  }
-  if (FIN != FIN_NONE) {
-    if (grid_sum<1>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
-      if (FIN == FIN_PCG_BETA) fin_pcg_beta(sc, acc[0]);
-    }
+    seg_decode(s, A.box, q, i, j, k);
+    if (i >= A.box.mx) continue;
+    long long c = i + (long long)A.box.mx * (j + (long long)A.box.my * k);
+    x[c] = A.dinv[c] * b[c];
   }
 }
 
@@ -317,41 +503,6 @@ __global__ void k_kscal_init(KScal* sc, const double* outer, double rtol_inner, 
   }
 }
 
-// PCG: p_new = z + beta p_old; q = A p_new; alpha = rz / (p_new . q)
-template <typename T, bool SYM>
-__global__ void k_pcg_pq(Op<T> A, const T* __restrict__ z, const T* __restrict__ pold, T* __restrict__ pnew,
-                         T* __restrict__ qv, KScal* sc, RedScratch rs) {
-  DONE_RETURN(sc);
-  const Box bx = A.box;
-  const Seg s = make_seg(bx);
-  const T beta = (T)sc->beta;
-  const bool first = (sc->iters == 0);
-  auto pat = [&](long long cc, int, int, int) -> T { return first ? z[cc] : z[cc] + beta * pold[cc]; };
-  double acc[1] = {0.0};
-  VOS_SEG_LOOP(s, q) {
-    int i, j, k;
-    seg_decode(s, bx, q, i, j, k);
-    if (i >= bx.mx) continue;
-    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
-    T pc = pat(c, i, j, k);
-    T qc = stencil<T, SYM>(A, i, j, k, c, pat);
-    pnew[c] = pc;
-    qv[c] = qc;
-    acc[0] += (double)pc * (double)qc;
-  }
-  if (grid_sum<1>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
-    double pq = acc[0];
-    sc->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      sc->breakdown = 1;
-      sc->done = 1;
-      sc->alpha = 0.0;
-    } else {
-      sc->alpha = sc->rz / pq;
-    }
-  }
-}
-
 // PCG: e += alpha p; r -= alpha q; rr = r.r; convergence check.
 template <typename T>
 __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restrict__ qv, T* __restrict__ e,
@@ -365,7 +516,7 @@ __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restri
     r[c] = rc;
     acc[0] += (double)rc * (double)rc;
   }
-  if (grid_sum<1>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
     sc->rr = acc[0];
     sc->iters += 1;
     if (acc[0] <= sc->tol2 || sc->iters >= sc->max_iters || !isfinite(acc[0])) sc->done = 1;
@@ -384,37 +535,6 @@ __global__ void k_bicg_p(long long n, const T* __restrict__ r, const T* __restri
   }
 }
 
-// BiCGStab: v = A ph; alpha = rho / (rh . v)
-template <typename T, bool SYM>
-__global__ void k_bicg_v(Op<T> A, const T* __restrict__ ph, const T* __restrict__ rh, T* __restrict__ v, KScal* sc,
-                         RedScratch rs) {
-  DONE_RETURN(sc);
-  const Box bx = A.box;
-  const Seg s = make_seg(bx);
-  auto xat = [&](long long cc, int, int, int) -> T { return ph[cc]; };
-  double acc[1] = {0.0};
-  VOS_SEG_LOOP(s, q) {
-    int i, j, k;
-    seg_decode(s, bx, q, i, j, k);
-    if (i >= bx.mx) continue;
-    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
-    T vc = stencil<T, SYM>(A, i, j, k, c, xat);
-    v[c] = vc;
-    acc[0] += (double)rh[c] * (double)vc;
-  }
-  if (grid_sum<1>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
-    double rhv = acc[0];
-    sc->rhv = rhv;
-    if (rhv == 0.0 || !isfinite(rhv)) {
-      sc->breakdown = 1;
-      sc->done = 1;
-      sc->alpha = 0.0;
-    } else {
-      sc->alpha = sc->rho / rhv;
-    }
-  }
-}
-
 // BiCGStab: s = r - alpha v
 template <typename T>
 __global__ void k_bicg_s(long long n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ sv,
@@ -423,36 +543,6 @@ __global__ void k_bicg_s(long long n, const T* __restrict__ r, const T* __restri
   const T alpha = (T)sc->alpha;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
     sv[c] = r[c] - alpha * v[c];
-}
-
-// BiCGStab: t = A sh; omega = (t.s)/(t.t)
-template <typename T, bool SYM>
-__global__ void k_bicg_t(Op<T> A, const T* __restrict__ sh, const T* __restrict__ sv, T* __restrict__ t, KScal* sc,
-                         RedScratch rs) {
-  DONE_RETURN(sc);
-  const Box bx = A.box;
-  const Seg s = make_seg(bx);
-  auto xat = [&](long long cc, int, int, int) -> T { return sh[cc]; };
-  double acc[2] = {0.0, 0.0};
-  VOS_SEG_LOOP(s, q) {
-    int i, j, k;
-    seg_decode(s, bx, q, i, j, k);
-    if (i >= bx.mx) continue;
-    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
-    T tc = stencil<T, SYM>(A, i, j, k, c, xat);
-    t[c] = tc;
-    acc[0] += (double)tc * (double)sv[c];
-    acc[1] += (double)tc * (double)tc;
-  }
-  if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
-    sc->ts = acc[0];
-    sc->tt = acc[1];
-    if (acc[1] > 0.0 && isfinite(acc[1])) {
-      sc->omega = acc[0] / acc[1];
-    } else {
-      sc->omega = 0.0;
-    }
-  }
 }
 
 // BiCGStab: e += alpha ph + omega sh; r = s - omega t; rr, rho_new = rh.r
@@ -470,7 +560,7 @@ __global__ void k_bicg_x(long long n, const T* __restrict__ ph, const T* __restr
     acc[0] += (double)rc * (double)rc;
     acc[1] += (double)rh[c] * (double)rc;
   }
-  if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
     double rr = acc[0], rho_new = acc[1];
     sc->rr = rr;
     sc->iters += 1;
@@ -488,37 +578,6 @@ __global__ void k_bicg_x(long long n, const T* __restrict__ ph, const T* __restr
 // ---------------------------------------------------------------------------
 // FP64 outer refinement kernels
 // ---------------------------------------------------------------------------
-// r_T = b - A64 x (x a strided view).  Convergence is measured on the
-// diagonally scaled residual: outer[0] = |D^-1 r|^2, outer[1] = |D^-1 b|^2,
-// which weighs every cell by its own coefficient scale (the coefficients of
-// solid cells are ~1e-4 of those of fluid cells).
-template <typename T, bool SYM>
-__global__ void k_outer_residual(Op<double> A, const double* __restrict__ b, View<double> x, T* __restrict__ rT,
-                                 double* outer, RedScratch rs) {
-  const Box bx = A.box;
-  const Seg s = make_seg(bx);
-  auto xat = [&](long long, int ii, int jj, int kk) -> double {
-    return x.base[ii + (long long)x.sy * jj + (long long)x.sz * kk];
-  };
-  double acc[2] = {0.0, 0.0};
-  VOS_SEG_LOOP(s, q) {
-    int i, j, k;
-    seg_decode(s, bx, q, i, j, k);
-    if (i >= bx.mx) continue;
-    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
-    double r = b[c] - stencil<double, SYM>(A, i, j, k, c, xat);
-    rT[c] = (T)r;
-    const double di = A.dinv[c];  // omega / diag: the constant omega cancels in the ratio
-    const double rs_ = r * di, bs = b[c] * di;
-    acc[0] += rs_ * rs_;
-    acc[1] += bs * bs;
-  }
-  if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
-    outer[0] = acc[0];
-    outer[1] = acc[1];
-  }
-}
-
 // x += e (x a strided view)
 template <typename T>
 __global__ void k_outer_update(Box bx, View<double> x, const T* __restrict__ e) {
@@ -714,15 +773,41 @@ template void build_coarse_levels<float>(Hier<float>&, cudaStream_t);
 
 // One V(nu, nu) cycle: out = M^{-1} rhs (level-0 vectors supplied).
 // With fin == FIN_PCG_BETA the last sweep also reduces rhs . out.
-// Buffers: each level owns (b, x, t).  Pre-smoothing starts in t; every
-// sweep alternates t <-> x, so after the 2*nu sweeps of a level the result
-// is in x (an odd number of alternations after the first write).
+// Each level owns (b, x, t).  The first two pre-smoothing sweeps from zero
+// are fused into one launch; every launch writes the other buffer, and the
+// start buffer is chosen so that the last post-smoothing write lands in x.
+template <typename T, bool SYM>
+static void jacobi_launch(const char* name, double bytes, int mode, int fin, const Op<T>& A, const T* b,
+                          const T* xin, T* xout, const T* ec, Box cb, T wc, T omega, KScal* sc, const RedScratch& rs,
+                          cudaStream_t st) {
+  const Op<T> Z = zview(A);
+  const Box cz = zbox(cb);
+  const ZCfg z = zcfg(Z.box);
+  if (mode == 1) {
+    if (fin == FIN_PCG_BETA)
+      vlaunch(name, bytes, k_jacobi<T, SYM, 1, FIN_PCG_BETA>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
+    else
+      vlaunch(name, bytes, k_jacobi<T, SYM, 1, FIN_NONE>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
+  } else if (mode == 2) {
+    if (fin == FIN_PCG_BETA)
+      vlaunch(name, bytes, k_jacobi<T, SYM, 2, FIN_PCG_BETA>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
+    else
+      vlaunch(name, bytes, k_jacobi<T, SYM, 2, FIN_NONE>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
+  } else {
+    if (fin == FIN_PCG_BETA)
+      vlaunch(name, bytes, k_jacobi<T, SYM, 0, FIN_PCG_BETA>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
+    else
+      vlaunch(name, bytes, k_jacobi<T, SYM, 0, FIN_NONE>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
+  }
+}
+
 template <typename T, bool SYM>
 static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal* sc, const RedScratch& rs,
                    cudaStream_t st) {
   const int L = h.nlev;
-  const int nu = h.mg.nu;
-  const T wc = (T)h.mg.wc;
+  const int nu = h.mg.nu < 1 ? 1 : h.mg.nu;
+  const T wc = (T)h.mg.wc, om = (T)h.mg.omega;
+  const Box none{1, 1, 1};
   auto bufs = [&](int l, const T*& b, T*& x, T*& t) {
     if (l == 0) {
       b = rhs;
@@ -734,54 +819,57 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal*
       t = h.lev[l].t;
     }
   };
-  const Box none{1, 1, 1};
-  if (L == 1) {
-    // single level: damped Jacobi only (cs >= 2 sweeps, result in out)
-    const Op<T>& A = h.lev[0].op;
-    const T* b;
-    T *x, *t;
-    bufs(0, b, x, t);
-    const int cs = h.mg.coarse_sweeps < 2 ? 2 : h.mg.coarse_sweeps;
-    int g = grid_for(A.box, 0);
-    T* cur = ((cs - 1) % 2 == 0) ? x : t;
-    T* oth = (cur == t) ? x : t;
-    const double sb = (5.0 + n_offs(A)) * ncell(A) * sizeof(T);
-    vlaunch(KN("mg_smooth0", true), 3.0 * ncell(A) * sizeof(T), k_smooth0<T>, g, kThreads, st, A, b, cur, sc);
-    for (int s = 1; s < cs; ++s) {
-      if (s == cs - 1 && fin == FIN_PCG_BETA)
-        vlaunch(KN("mg_smooth", true), sb, k_smooth<T, SYM, FIN_PCG_BETA>, g, kThreads, st, A, b, cur, oth, nullptr, none, T(0), sc, rs);
-      else
-        vlaunch(KN("mg_smooth", true), sb, k_smooth<T, SYM, FIN_NONE>, g, kThreads, st, A, b, cur, oth, nullptr, none, T(0), sc, rs);
-      T* tmp = cur;
-      cur = oth;
-      oth = tmp;
-    }
-    return;
-  }
-  bool pre_in_t[16];
-  for (int l = 0; l < L - 1; ++l) {
+  // coefficient words read by a sweep: diag, offs (+ dinv in FP64)
+  auto swords = [&](const Op<T>& A) { return n_offs(A) + 1.0 + (sizeof(T) == 8 ? 1.0 : 0.0); };
+  // Run `sweeps` damped-Jacobi sweeps from zero on level l; returns the
+  // buffer holding the result.  `more` = writes that follow on this level.
+  auto presmooth = [&](int l, int sweeps, int more, int fin_last) -> T* {
+    const Op<T>& A = h.lev[l].op;
     const T* b;
     T *x, *t;
     bufs(l, b, x, t);
-    const Op<T>& A = h.lev[l].op;
-    const int g = grid_for(A.box, 0);
-    T* cur = t;
-    T* oth = x;
-    const double sb = (5.0 + n_offs(A)) * ncell(A) * sizeof(T);
-    vlaunch(KN("mg_smooth0", l == 0), 3.0 * ncell(A) * sizeof(T), k_smooth0<T>, g, kThreads, st, A, b, cur, sc);
-    for (int s = 1; s < nu; ++s) {
-      vlaunch(KN("mg_smooth", l == 0), sb, k_smooth<T, SYM, FIN_NONE>, g, kThreads, st, A, b, cur, oth, nullptr, none, T(0), sc, rs);
+    const int writes = (sweeps >= 2 ? sweeps - 1 : 1) + more;
+    T* cur = (writes % 2 == 1) ? x : t;
+    T* oth = (cur == x) ? t : x;
+    const double n = ncell(A), wT = sizeof(T);
+    const bool fine = (l == 0);
+    if (sweeps >= 2) {
+      jacobi_launch<T, SYM>(KN("mg_jacobi2", fine), (swords(A) + 2.0) * n * wT, 1,
+                            (sweeps == 2 && fin_last) ? fin : FIN_NONE, A, b, nullptr, cur, nullptr, none, T(0), om, sc,
+                            rs, st);
+    } else {
+      vlaunch(KN("mg_smooth0", fine), 3.0 * n * wT, k_smooth0<T>, grid_for(A.box, 0), kThreads, st, A, b, cur, sc);
+    }
+    for (int s = 2; s < sweeps; ++s) {
+      jacobi_launch<T, SYM>(KN("mg_jacobi", fine), (swords(A) + 3.0) * n * wT, 0,
+                            (s == sweeps - 1 && fin_last) ? fin : FIN_NONE, A, b, cur, oth, nullptr, none, T(0), om, sc,
+                            rs, st);
       T* tmp = cur;
       cur = oth;
       oth = tmp;
     }
-    pre_in_t[l] = (cur == t);
+    return cur;
+  };
+  if (L == 1) {
+    const int cs = h.mg.coarse_sweeps < 2 ? 2 : h.mg.coarse_sweeps;
+    presmooth(0, cs, 0, 1);
+    return;
+  }
+  T* pre[16];
+  for (int l = 0; l < L - 1; ++l) {
+    pre[l] = presmooth(l, nu, nu, 0);
+    const Op<T>& A = h.lev[l].op;
+    const T* b;
+    T *x, *t;
+    bufs(l, b, x, t);
     const Op<T>& C = h.lev[l + 1].op;
-    vlaunch(KN("mg_restrict", l == 0), ((3.0 + n_offs(A)) * ncell(A) + ncell(C)) * sizeof(T), k_restrict<T, SYM>, grid_for(C.box, 0), kThreads, st, A, b, cur, h.lev[l + 1].b, C.box, sc);
+    vlaunch(KN("mg_restrict", l == 0), ((3.0 + n_offs(A)) * ncell(A) + ncell(C)) * sizeof(T), k_restrict<T, SYM>,
+            grid_for(C.box, 0), kThreads, st, A, b, pre[l], h.lev[l + 1].b, C.box, sc);
   }
   {
     const Op<T>& A = h.lev[L - 1].op;
-    vlaunch(KN("mg_coarse", false), (4.0 + n_offs(A)) * ncell(A) * sizeof(T), k_coarse_solve<T, SYM>, 1, kThreads, st, A, h.lev[L - 1].b, h.lev[L - 1].x, h.mg.coarse_sweeps, sc);
+    vlaunch(KN("mg_coarse", false), (4.0 + n_offs(A)) * ncell(A) * sizeof(T), k_coarse_solve<T, SYM>, 1, kThreads, st,
+            A, h.lev[L - 1].b, h.lev[L - 1].x, h.mg.coarse_sweeps, sc);
   }
   for (int l = L - 2; l >= 0; --l) {
     const T* b;
@@ -790,16 +878,18 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal*
     const Op<T>& A = h.lev[l].op;
     const Box cb = h.lev[l + 1].op.box;
     const T* ec = h.lev[l + 1].x;
-    const int g = grid_for(A.box, 0);
-    T* cur = pre_in_t[l] ? t : x;
-    T* oth = pre_in_t[l] ? x : t;
+    T* cur = pre[l];
+    T* oth = (cur == x) ? t : x;
+    const double n = ncell(A), wT = sizeof(T);
     for (int s = 0; s < nu; ++s) {
-      const T* ecs = (s == 0) ? ec : nullptr;
-      const double sb = ((5.0 + n_offs(A)) * ncell(A) + (ecs ? (double)box_cells(cb) : 0.0)) * sizeof(T);
-      if (s == nu - 1 && l == 0 && fin == FIN_PCG_BETA)
-        vlaunch(KN("mg_smooth", true), sb, k_smooth<T, SYM, FIN_PCG_BETA>, g, kThreads, st, A, b, cur, oth, ecs, cb, wc, sc, rs);
+      const bool last = (s == nu - 1);
+      const int f = (last && l == 0) ? fin : FIN_NONE;
+      if (s == 0)
+        jacobi_launch<T, SYM>(KN("mg_jacobi_prolong", l == 0), ((swords(A) + 3.0) * n + box_cells(cb)) * wT, 2, f, A,
+                              b, cur, oth, ec, cb, wc, om, sc, rs, st);
       else
-        vlaunch(KN("mg_smooth", l == 0), sb, k_smooth<T, SYM, FIN_NONE>, g, kThreads, st, A, b, cur, oth, ecs, cb, wc, sc, rs);
+        jacobi_launch<T, SYM>(KN("mg_jacobi", l == 0), (swords(A) + 3.0) * n * wT, 0, f, A, b, cur, oth, nullptr, none,
+                              T(0), om, sc, rs, st);
       T* tmp = cur;
       cur = oth;
       oth = tmp;
@@ -823,12 +913,15 @@ static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters
   cudaMemsetAsync(e, 0, n * sizeof(T), st);
   vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
   vcycle<T, SYM>(h, r, z, scratch, FIN_PCG_BETA, w->sc, rs, st);
-  const int g = grid_for(bx, 0), gf = flat_grid(n);
+  const int gf = flat_grid(n);
+  const Op<T> Az = zview(A);
+  const ZCfg zc = zcfg(Az.box);
   const int chunk = 4;
   int it = 0;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      vlaunch(KN("pcg_pq", true), (5.0 + n_offs(A)) * n * sizeof(T), k_pcg_pq<T, SYM>, g, kThreads, st, A, z, p, p2, qv, w->sc, rs);
+      vlaunch(KN("pcg_pq", true), (5.0 + n_offs(A)) * n * sizeof(T), k_pcg_pq_z<T, SYM>, zc.grid, zc.block, st, Az, z,
+              p, p2, qv, zc.zc, w->sc, rs);
       T* tmp = p;
       p = p2;
       p2 = tmp;
@@ -863,17 +956,21 @@ static int inner_bicgstab(Hier<T>& h, SolverWork* w, double rtol_inner, int max_
   cudaMemsetAsync(v, 0, n * sizeof(T), st);
   cudaMemcpyAsync(rh, r, n * sizeof(T), cudaMemcpyDeviceToDevice, st);
   vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
-  const int g = grid_for(bx, 0), gf = flat_grid(n);
+  const int gf = flat_grid(n);
+  const Op<T> Az = zview(A);
+  const ZCfg zc = zcfg(Az.box);
   const int chunk = 2;
   int it = 0;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
       vlaunch(KN("bicg_p", true), 4.0 * n * sizeof(T), k_bicg_p<T>, gf, kThreads, st, n, r, v, p, w->sc);
       vcycle<T, SYM>(h, p, ph, scratch, FIN_NONE, w->sc, rs, st);
-      vlaunch(KN("bicg_v", true), (4.0 + n_offs(A)) * n * sizeof(T), k_bicg_v<T, SYM>, g, kThreads, st, A, ph, rh, v, w->sc, rs);
+      vlaunch(KN("bicg_v", true), (4.0 + n_offs(A)) * n * sizeof(T), k_bicg_v_z<T, SYM>, zc.grid, zc.block, st, Az, ph,
+              rh, v, zc.zc, w->sc, rs);
       vlaunch(KN("bicg_s", true), 3.0 * n * sizeof(T), k_bicg_s<T>, gf, kThreads, st, n, r, v, sv, w->sc);
       vcycle<T, SYM>(h, sv, sh, scratch, FIN_NONE, w->sc, rs, st);
-      vlaunch(KN("bicg_t", true), (4.0 + n_offs(A)) * n * sizeof(T), k_bicg_t<T, SYM>, g, kThreads, st, A, sh, sv, t, w->sc, rs);
+      vlaunch(KN("bicg_t", true), (4.0 + n_offs(A)) * n * sizeof(T), k_bicg_t_z<T, SYM>, zc.grid, zc.block, st, Az, sh,
+              sv, t, zc.zc, w->sc, rs);
       vlaunch(KN("bicg_x", true), 8.0 * n * sizeof(T), k_bicg_x<T>, gf, kThreads, st, n, ph, sh, sv, t, rh, e, r, w->sc, rs);
     }
     it += chunk;
@@ -900,11 +997,16 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
   build_coarse_levels<T>(h, st);
   int total = 0;
   const double rbytes = (4.0 + n_offs(op64)) * n * 8.0 + n * sizeof(T);
+  const Op<double> oz = zview(op64);
+  const View<double> xz = zview_x(x, bx);
+  const ZCfg zr = zcfg(oz.box);
   for (int outer = 0;; ++outer) {
     if (op64.sym)
-      vlaunch("outer_residual_f64", rbytes, k_outer_residual<T, true>, g, kThreads, st, op64, b, x, (T*)w->r, w->outer, rs);
+      vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, true>, zr.grid, zr.block, st, oz, b, xz, (T*)w->r,
+              w->outer, zr.zc, rs);
     else
-      vlaunch("outer_residual_f64", rbytes, k_outer_residual<T, false>, g, kThreads, st, op64, b, x, (T*)w->r, w->outer, rs);
+      vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, false>, zr.grid, zr.block, st, oz, b, xz, (T*)w->r,
+              w->outer, zr.zc, rs);
     cudaMemcpyAsync(w->outer_host, w->outer, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     const double rr = w->outer_host[0], bb = w->outer_host[1];
