@@ -157,6 +157,26 @@ int vos_get_stats(vos_handle* h, vos_stats* out);
  * +inf in *dt when neither limit applies. */
 int vos_suggest_dt(vos_handle* h, double cfl, double deps_max, double* dt);
 
+/* Allocation-free form of vos_suggest_dt (the paper has no counterpart: it
+ * exists for callers that cannot let a library allocate device memory --
+ * hosts that keep the GPU's memory in their own pool, or loops that must not
+ * pay the device-wide synchronisation a cudaMalloc/cudaFree can cause).
+ * Computes the same limit as vos_suggest_dt from caller-owned device fields
+ * in the layouts above (eps, u, v, w, R; v may be NULL when ny == 1, w is
+ * required in 3D); only dim, nx, ny, nz, dx and Vm of prm are used.  It
+ * allocates nothing: its scratch is a fixed file-scope device array of
+ * about 1 MiB that every GPU loading the library holds until exit, so grids
+ * above 16,777,216 cells are rejected with VOS_EINVAL.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (other streams or threads) race.  Work runs
+ * on `stream`; the call synchronises it and writes the result to the host
+ * double *dt.  Errors: VOS_EINVAL (NULL or bad arguments, too many cells),
+ * VOS_ECUDA; message via vos_last_error(NULL). */
+int vos_suggest_dt_noalloc(const vos_params* prm, const double* eps, const double* u,
+                           const double* v, const double* w, const double* R, double cfl,
+                           double deps_max, void* stream, double* dt);
+
 /* Message of the last error on h (or of the last failed vos_create when h
  * is NULL).  The string is owned by the library. */
 const char* vos_last_error(const vos_handle* h);

@@ -28,6 +28,11 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+namespace vos {
+// Error text reported by vos_last_error(NULL) for calls without a handle.
+void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace vos
+
 struct vos_handle {
   vos_params prm;
   Phys ph;

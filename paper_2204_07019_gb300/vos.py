@@ -20,7 +20,7 @@ __all__ = [
     "VosError", "load_library", "vos_create", "vos_step", "vos_fields", "vos_set_fields",
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
     "vos_device_bytes", "vos_kernel_launches", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
-    "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS",
+    "vos_suggest_dt_noalloc", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -33,6 +33,7 @@ EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
     "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
     "vos_kernel_launches", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
+    "vos_suggest_dt_noalloc",
 ]
 
 
@@ -122,6 +123,9 @@ def load_library(path=None):
     lib.vos_prof_report.restype = ctypes.c_int
     lib.vos_prof_reset.argtypes = []
     lib.vos_prof_reset.restype = None
+    lib.vos_suggest_dt_noalloc.argtypes = [ctypes.POINTER(VosParams)] + [ctypes.c_void_p] * 5 + [
+        ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    lib.vos_suggest_dt_noalloc.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -290,6 +294,20 @@ def vos_suggest_dt(h, cfl=0.5, deps_max=0.005):
     lib = load_library()
     dt = ctypes.c_double()
     _check(lib, h.ptr, lib.vos_suggest_dt(h.ptr, float(cfl), float(deps_max), ctypes.byref(dt)))
+    return dt.value
+
+
+def vos_suggest_dt_noalloc(prm, eps, u, v, w, R, cfl=0.5, deps_max=0.005, stream=None):
+    """vos_suggest_dt_noalloc: the time-step limit from caller-owned device
+    fields (int device pointers) without any device allocation; see vos.h."""
+    lib = load_library()
+    ps = _params_struct(prm)
+    dt = ctypes.c_double()
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    rc = lib.vos_suggest_dt_noalloc(ctypes.byref(ps), eps, u, v, w, R, float(cfl), float(deps_max),
+                                    ctypes.c_void_p(st), ctypes.byref(dt))
+    if rc != VOS_OK:
+        raise VosError(rc, lib.vos_last_error(None).decode())
     return dt.value
 
 
