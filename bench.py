@@ -40,12 +40,14 @@ METRIC = "cell-steps/s at 1e-8 residual"
 UNIT = "cell-steps/s"
 
 
-def workload(name):
-    """(eps_s, params, description) of a named workload."""
+def workload(name, size=256):
+    """(eps_s, params, description) of a named workload (``size`` scales the
+    rock; radii scale with it so that the pore structure is the same)."""
     if name == "rock256":
-        es = I.sphere_rock_3d(256, seed=0)
-        prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=24.0, method="ivos", precision=1)
-        desc = "3D sphere rock 256^3, porosity 0.20, Pe=10, Da=1, iVoS"
+        r = 12.0 * size / 256.0
+        es = I.sphere_rock_3d(size, seed=0, median_r=r)
+        prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=2.0 * r, method="ivos", precision=1)
+        desc = f"3D sphere rock {size}^3, porosity 0.20, Pe=10, Da=1, iVoS"
     elif name == "micromodel":
         es = I.disc_micromodel_2d(1024, 512, seed=0)
         prm = I.make_params(es.shape, Pe=100.0, Da=1.0, L=40.0, method="ivos", precision=1)
@@ -244,7 +246,7 @@ def reference_arm(args, rank, world):
     """The CPU oracle as it stands, timed on the host cores (rank 0 only)."""
     if rank != 0:
         return
-    es, prm, desc = workload(args.workload)
+    es, prm, desc = workload(args.workload, args.size)
     cells = []
     for _ in range(max(args.warmup, 0)):
         oracle_sample(es, prm, budget_s=2.0)
@@ -272,6 +274,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rock256", choices=["rock256", "micromodel", "calcite"])
+    ap.add_argument("--size", type=int, default=256, help="edge of the rock workload (profiling runs only)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -290,7 +293,7 @@ def main():
     if dist is not None:
         dist.barrier()
     V.load_library()
-    es, prm, desc = workload(args.workload)
+    es, prm, desc = workload(args.workload, args.size)
     N = es.size
     clocks = ClockSampler(local)
     if dist is not None:
