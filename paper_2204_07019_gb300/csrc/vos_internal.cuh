@@ -271,11 +271,13 @@ struct SolveResult {
 // Host-side driver: outer FP64 refinement around an inner solve in T.
 // op64: fine operator in FP64 (for the true residual); h: hierarchy in T
 // (level 0 is the same operator in T); b: right-hand side (box layout);
-// x: solution view (initial guess on entry).  sym selects PCG or BiCGStab.
+// x: solution view (initial guess on entry).  sym selects PCG or BiCGStab;
+// use_mg selects the multigrid V-cycle (else the diagonal) preconditioner
+// for PCG (BiCGStab always uses multigrid).
 struct SolverWork;  // opaque: Krylov vectors + scalars
 template <typename T>
 SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol,
-                  int max_iter, SolverWork* w, const RedScratch& rs, cudaStream_t st);
+                  int max_iter, SolverWork* w, const RedScratch& rs, cudaStream_t st, bool use_mg);
 
 template <typename T>
 void build_coarse_levels(Hier<T>& h, cudaStream_t st);

@@ -54,6 +54,31 @@ __device__ __forceinline__ T stencil(const Op<T>& A, int i, int j, int k, long l
   return y;
 }
 
+// Per-thread partial sums of dot products.  The FP32 inner solver
+// accumulates in compensated (Kahan) FP32 and converts once per thread:
+// FP64 arithmetic runs at ~1/60 of FP32 here, and a conversion plus an FP64
+// FMA per element would cap the streaming kernels near 2 TB/s.  Block and
+// grid reductions stay FP64 with a fixed order.
+template <typename T>
+struct PSum;
+template <>
+struct PSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct PSum<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float y = __fmul_rn(a, b) - c;
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
 #define DONE_RETURN(sc) \
   if ((sc) != nullptr && (sc)->done) return;
 
@@ -104,23 +129,29 @@ __device__ __forceinline__ void zmarch(const Op<T>& A, int zc, VAL val, EMIT emi
   const int k1 = min(k0 + zc, bx.mz);
   if (i >= bx.mx || j >= bx.my || k0 >= k1) return;
   const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+  // Coefficients are read-only for the kernel's lifetime (ld.global.nc), so
+  // the compiler may move their loads across the stores of emit().
+  const T* __restrict__ dg = A.diag;
+  const T* __restrict__ xp = A.xp;
+  const T* __restrict__ yp = A.yp;
+  const T* __restrict__ zp = A.zp;
   long long c = i + sy * j + sz * k0;
   T v_lo = (k0 > 0) ? val(c - sz, i, j, k0 - 1) : T(0);
   T v_c = val(c, i, j, k0);
-  T zl = (SYM && k0 > 0) ? A.zp[c - sz] : T(0);
+  T zl = (SYM && k0 > 0) ? __ldg(zp + c - sz) : T(0);
   for (int k = k0; k < k1; ++k, c += sz) {
     const bool up = (k + 1 < bx.mz);
     const T v_hi = up ? val(c + sz, i, j, k + 1) : T(0);
-    const T d = A.diag[c];
+    const T d = __ldg(dg + c);
     T ax = d * v_c;
-    if (i + 1 < bx.mx) ax += A.xp[c] * val(c + 1, i + 1, j, k);
-    if (i > 0) ax += (SYM ? A.xp[c - 1] : A.xm[c]) * val(c - 1, i - 1, j, k);
-    if (j + 1 < bx.my) ax += A.yp[c] * val(c + sy, i, j + 1, k);
-    if (j > 0) ax += (SYM ? A.yp[c - sy] : A.ym[c]) * val(c - sy, i, j - 1, k);
+    if (i + 1 < bx.mx) ax += __ldg(xp + c) * val(c + 1, i + 1, j, k);
+    if (i > 0) ax += (SYM ? __ldg(xp + c - 1) : __ldg(A.xm + c)) * val(c - 1, i - 1, j, k);
+    if (j + 1 < bx.my) ax += __ldg(yp + c) * val(c + sy, i, j + 1, k);
+    if (j > 0) ax += (SYM ? __ldg(yp + c - sy) : __ldg(A.ym + c)) * val(c - sy, i, j - 1, k);
     if (bx.mz > 1) {
-      const T zu = up ? A.zp[c] : T(0);
+      const T zu = up ? __ldg(zp + c) : T(0);
       ax += zu * v_hi;
-      if (k > 0) ax += (SYM ? zl : A.zm[c]) * v_lo;
+      if (k > 0) ax += (SYM ? zl : __ldg(A.zm + c)) * v_lo;
       zl = zu;
     }
     emit(c, i, j, k, v_c, ax, d);
@@ -129,121 +160,183 @@ __device__ __forceinline__ void zmarch(const Op<T>& A, int zc, VAL val, EMIT emi
   }
 }
 
-// Jacobi weight omega / diag: computed in FP32 registers, read in FP64
-// (FP64 division is slow on this part).
+// Pure 2.5D stencil kernels, written out explicitly (one input vector, one
+// output, no epilogue): on this part a fused reduction or extra per-
+// neighbour loads cost 30-60% of the bandwidth of the plain sweep, so dots,
+// updates and grid transfers run as separate streaming kernels.
+//   SK_JAC: out = x + (omega / diag) (b - A x)   (omega/diag in registers for
+//           FP32, read from dinv for FP64)
+//   SK_MV:  out = A x
+//   SK_RES: out = b - A x
+enum StencilKind { SK_JAC = 0, SK_MV = 1, SK_RES = 2 };
+
+template <typename T, bool SYM, int KIND>
+__global__ void __launch_bounds__(kThreads) k_stencil(Op<T> A, const T* __restrict__ b, const T* __restrict__ x,
+                                                     T* __restrict__ out, T omega, int zc, const KScal* sc) {
+  DONE_RETURN(sc);
+  const Box bx = A.box;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  if (i >= bx.mx || j >= bx.my || k0 >= k1) return;
+  const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+  const T* __restrict__ dg = A.diag;
+  const T* __restrict__ xp = A.xp;
+  const T* __restrict__ yp = A.yp;
+  const T* __restrict__ zp = A.zp;
+  const bool has_z = bx.mz > 1;
+  long long c = i + sy * j + sz * k0;
+  T vlo = (k0 > 0) ? __ldg(x + c - sz) : T(0);
+  T vc = __ldg(x + c);
+  T zl = (SYM && k0 > 0) ? __ldg(zp + c - sz) : T(0);
+  for (int k = k0; k < k1; ++k, c += sz) {
+    const bool up = (k + 1 < bx.mz);
+    const T vhi = up ? __ldg(x + c + sz) : T(0);
+    const T d = __ldg(dg + c);
+    T ax = d * vc;
+    if (i + 1 < bx.mx) ax += __ldg(xp + c) * __ldg(x + c + 1);
+    if (i > 0) ax += (SYM ? __ldg(xp + c - 1) : __ldg(A.xm + c)) * __ldg(x + c - 1);
+    if (j + 1 < bx.my) ax += __ldg(yp + c) * __ldg(x + c + sy);
+    if (j > 0) ax += (SYM ? __ldg(yp + c - sy) : __ldg(A.ym + c)) * __ldg(x + c - sy);
+    if (has_z) {
+      const T zu = up ? __ldg(zp + c) : T(0);
+      ax += zu * vhi;
+      if (k > 0) ax += (SYM ? zl : __ldg(A.zm + c)) * vlo;
+      zl = zu;
+    }
+    if (KIND == SK_JAC) {
+      T w;
+      if constexpr (sizeof(T) == 4)
+        w = __fdividef(omega, d);
+      else
+        w = __ldg(A.dinv + c);
+      out[c] = vc + w * (__ldg(b + c) - ax);
+    } else if (KIND == SK_MV) {
+      out[c] = ax;
+    } else {
+      out[c] = __ldg(b + c) - ax;
+    }
+    vlo = vc;
+    vc = vhi;
+  }
+}
+
+// First Jacobi sweep from zero: x = (omega / diag) b.
 template <typename T>
-__device__ __forceinline__ T jacobi_w(const Op<T>& A, long long c, T d, T omega) {
-  if constexpr (sizeof(T) == 4) {
-    return __fdividef(omega, d);
-  } else {
-    return A.dinv[c];
+__global__ void k_jac0(long long n, const T* __restrict__ diag, const T* __restrict__ dinv, const T* __restrict__ b,
+                       T* __restrict__ x, T omega, const KScal* sc) {
+  DONE_RETURN(sc);
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    T w;
+    if constexpr (sizeof(T) == 4)
+      w = __fdividef(omega, __ldg(diag + c));
+    else
+      w = __ldg(dinv + c);
+    x[c] = w * __ldg(b + c);
   }
 }
 
-// Jacobi sweep variants (MODE): 0 plain x_out = x + w (b - A x);
-// 1 first two sweeps from zero fused (x = w b computed at every cell read);
-// 2 with the coarse correction x + wc ec[parent] fused into the input.
-// FIN: also reduce b . x_out for the PCG beta.
-template <typename T, bool SYM, int MODE, int FIN>
-__global__ void __launch_bounds__(kThreads) k_jacobi(Op<T> A, const T* __restrict__ b, const T* __restrict__ xin,
-                                                    T* __restrict__ xout, const T* __restrict__ ec, Box cb, T wc,
-                                                    T omega, int zc, KScal* sc, RedScratch rs) {
+// Coarse correction x += wc * ec[parent] (2.5D: one thread per fine column).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong_add(Box fb, Box cb, T* __restrict__ x, const T* __restrict__ ec,
+                                                         T wc, int zc, const KScal* sc) {
   DONE_RETURN(sc);
-  double acc[1] = {0.0};
-  auto val = [&](long long c, int i, int j, int k) -> T {
-    if constexpr (MODE == 1) {
-      return jacobi_w<T>(A, c, A.diag[c], omega) * b[c];
-    } else if constexpr (MODE == 2) {
-      long long pc = (i >> 1) + (long long)cb.mx * ((j >> 1) + (long long)cb.my * (k >> 1));
-      return xin[c] + wc * ec[pc];
-    } else {
-      return xin[c];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, fb.mz);
+  if (i >= fb.mx || j >= fb.my || k0 >= k1) return;
+  const long long sz = (long long)fb.mx * fb.my, csz = (long long)cb.mx * cb.my;
+  long long c = i + (long long)fb.mx * j + sz * k0;
+  const long long pc0 = (i >> 1) + (long long)cb.mx * (j >> 1);
+  for (int k = k0; k < k1; ++k, c += sz) x[c] += wc * __ldg(ec + pc0 + csz * (k >> 1));
+}
+
+// Restriction of a fine residual: bc[I] = sum of its (up to 8) children.
+template <typename T>
+__global__ void k_restrict_sum(Box fb, Box cb, const T* __restrict__ r, T* __restrict__ bc, const KScal* sc) {
+  DONE_RETURN(sc);
+  const Seg s = make_seg(cb);
+  const int ni = fb.mx > 1 ? 2 : 1, nj = fb.my > 1 ? 2 : 1, nk = fb.mz > 1 ? 2 : 1;
+  VOS_SEG_LOOP(s, q) {
+    int I, J, K;
+    seg_decode(s, cb, q, I, J, K);
+    if (I >= cb.mx) continue;
+    T sum = 0;
+    for (int dk = 0; dk < nk; ++dk) {
+      const int k = (fb.mz > 1) ? 2 * K + dk : 0;
+      if (k >= fb.mz) continue;
+      for (int dj = 0; dj < nj; ++dj) {
+        const int j = (fb.my > 1) ? 2 * J + dj : 0;
+        if (j >= fb.my) continue;
+        const long long row = (long long)fb.mx * (j + (long long)fb.my * k);
+        for (int di = 0; di < ni; ++di) {
+          const int i = (fb.mx > 1) ? 2 * I + di : 0;
+          if (i < fb.mx) sum += __ldg(r + row + i);
+        }
+      }
     }
-  };
-  auto emit = [&](long long c, int, int, int, T v, T ax, T d) {
-    const T bc = b[c];
-    const T y = v + jacobi_w<T>(A, c, d, omega) * (bc - ax);
-    xout[c] = y;
-    if (FIN) acc[0] += (double)bc * (double)y;
-  };
-  zmarch<T, SYM>(A, zc, val, emit);
-  if (FIN != FIN_NONE) {
-    if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_pcg_beta(sc, acc[0]);
+    bc[I + (long long)cb.mx * (J + (long long)cb.my * K)] = sum;
   }
 }
 
-// PCG: p_new = z + beta p_old; q = A p_new; alpha = rz / (p_new . q)
-template <typename T, bool SYM>
-__global__ void __launch_bounds__(kThreads) k_pcg_pq_z(Op<T> A, const T* __restrict__ z, const T* __restrict__ pold,
-                                                      T* __restrict__ pnew, T* __restrict__ qv, int zc, KScal* sc,
-                                                      RedScratch rs) {
+// Dot products with a device-side finalisation (deterministic FP64 reduce).
+enum DotFin { DF_PCG_BETA = 0, DF_PCG_ALPHA = 1, DF_BICG_ALPHA = 2, DF_BICG_OMEGA = 3 };
+
+__device__ void fin_pcg_beta(KScal* sc, double rz);
+
+template <typename T, int NV, int FIN>
+__global__ void k_dots(long long n, const T* __restrict__ a0, const T* __restrict__ b0, const T* __restrict__ a1,
+                       const T* __restrict__ b1, KScal* sc, RedScratch rs) {
   DONE_RETURN(sc);
-  const T beta = (T)sc->beta;
+  PSum<T> p0, p1;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    p0.add(__ldg(a0 + c), __ldg(b0 + c));
+    if (NV == 2) p1.add(__ldg(a1 + c), __ldg(b1 + c));
+  }
+  double acc[NV];
+  acc[0] = p0.get();
+  if (NV == 2) acc[NV - 1] = p1.get();
+  if (grid_sum<NV>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    if (FIN == DF_PCG_BETA) {
+      fin_pcg_beta(sc, acc[0]);
+    } else if (FIN == DF_PCG_ALPHA) {
+      const double pq = acc[0];
+      sc->pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        sc->breakdown = 1;
+        sc->done = 1;
+        sc->alpha = 0.0;
+      } else {
+        sc->alpha = sc->rz / pq;
+      }
+    } else if (FIN == DF_BICG_ALPHA) {
+      const double rhv = acc[0];
+      sc->rhv = rhv;
+      if (rhv == 0.0 || !isfinite(rhv)) {
+        sc->breakdown = 1;
+        sc->done = 1;
+        sc->alpha = 0.0;
+      } else {
+        sc->alpha = sc->rho / rhv;
+      }
+    } else {
+      sc->ts = acc[0];
+      sc->tt = acc[NV - 1];
+      sc->omega = (acc[NV - 1] > 0.0 && isfinite(acc[NV - 1])) ? acc[0] / acc[NV - 1] : 0.0;
+    }
+  }
+}
+
+// PCG: p = z + beta p (first iteration: p = z)
+template <typename T>
+__global__ void k_pcg_p(long long n, const T* __restrict__ z, T* __restrict__ p, const KScal* sc) {
+  DONE_RETURN(sc);
   const bool first = (sc->iters == 0);
-  double acc[1] = {0.0};
-  auto val = [&](long long c, int, int, int) -> T { return first ? z[c] : z[c] + beta * pold[c]; };
-  auto emit = [&](long long c, int, int, int, T v, T ax, T) {
-    pnew[c] = v;
-    qv[c] = ax;
-    acc[0] += (double)v * (double)ax;
-  };
-  zmarch<T, SYM>(A, zc, val, emit);
-  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
-    double pq = acc[0];
-    sc->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      sc->breakdown = 1;
-      sc->done = 1;
-      sc->alpha = 0.0;
-    } else {
-      sc->alpha = sc->rz / pq;
-    }
-  }
-}
-
-// BiCGStab: v = A ph; alpha = rho / (rh . v)
-template <typename T, bool SYM>
-__global__ void __launch_bounds__(kThreads) k_bicg_v_z(Op<T> A, const T* __restrict__ ph, const T* __restrict__ rh,
-                                                      T* __restrict__ v, int zc, KScal* sc, RedScratch rs) {
-  DONE_RETURN(sc);
-  double acc[1] = {0.0};
-  auto val = [&](long long c, int, int, int) -> T { return ph[c]; };
-  auto emit = [&](long long c, int, int, int, T, T ax, T) {
-    v[c] = ax;
-    acc[0] += (double)rh[c] * (double)ax;
-  };
-  zmarch<T, SYM>(A, zc, val, emit);
-  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
-    double rhv = acc[0];
-    sc->rhv = rhv;
-    if (rhv == 0.0 || !isfinite(rhv)) {
-      sc->breakdown = 1;
-      sc->done = 1;
-      sc->alpha = 0.0;
-    } else {
-      sc->alpha = sc->rho / rhv;
-    }
-  }
-}
-
-// BiCGStab: t = A sh; omega = (t.s)/(t.t)
-template <typename T, bool SYM>
-__global__ void __launch_bounds__(kThreads) k_bicg_t_z(Op<T> A, const T* __restrict__ sh, const T* __restrict__ sv,
-                                                      T* __restrict__ t, int zc, KScal* sc, RedScratch rs) {
-  DONE_RETURN(sc);
-  double acc[2] = {0.0, 0.0};
-  auto val = [&](long long c, int, int, int) -> T { return sh[c]; };
-  auto emit = [&](long long c, int, int, int, T, T ax, T) {
-    t[c] = ax;
-    acc[0] += (double)ax * (double)sv[c];
-    acc[1] += (double)ax * (double)ax;
-  };
-  zmarch<T, SYM>(A, zc, val, emit);
-  if (grid_sum<2>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
-    sc->ts = acc[0];
-    sc->tt = acc[1];
-    sc->omega = (acc[1] > 0.0 && isfinite(acc[1])) ? acc[0] / acc[1] : 0.0;
-  }
+  const T beta = (T)sc->beta;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    p[c] = first ? __ldg(z + c) : __ldg(z + c) + beta * p[c];
 }
 
 // FP64 true residual (see k_outer_residual) in the 2.5D form.
@@ -253,10 +346,10 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual_z(Op<double> A, con
                                                               int zc, RedScratch rs) {
   double acc[2] = {0.0, 0.0};
   auto val = [&](long long, int i, int j, int k) -> double {
-    return x.base[i + (long long)x.sy * j + (long long)x.sz * k];
+    return __ldg(x.base + i + (long long)x.sy * j + (long long)x.sz * k);
   };
   auto emit = [&](long long c, int, int, int, double, double ax, double) {
-    const double r = b[c] - ax;
+    const double r = __ldg(b + c) - ax;
     rT[c] = (T)r;
     const double di = A.dinv[c];  // omega / diag: the constant omega cancels in the ratio
     const double r1 = r * di, b1 = b[c] * di;
@@ -313,53 +406,21 @@ static ZCfg zcfg(Box b) {
 // Smoothing kernels
 // ---------------------------------------------------------------------------
 
-// x = dinv * b  (first Jacobi sweep from a zero guess)
+// Diagonal preconditioner z = (omega / diag) r with the fused r.z for PCG
+// (the constant omega does not change the CG iterates).
 template <typename T>
-__global__ void k_smooth0(Op<T> A, const T* __restrict__ b, T* __restrict__ x, const KScal* sc) {
+__global__ void k_diag_prec(long long n, const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ z,
+                            KScal* sc, RedScratch rs) {
   DONE_RETURN(sc);
-  const Seg s = make_seg(A.box);
-  VOS_SEG_LOOP(s, q) {
-    int i, j, k;
-    seg_decode(s, A.box, q, i, j, k);
-    if (i >= A.box.mx) continue;
-    long long c = i + (long long)A.box.mx * (j + (long long)A.box.my * k);
-    x[c] = A.dinv[c] * b[c];
+  PSum<T> ps;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const T rc = r[c];
+    const T zc = dinv[c] * rc;
+    z[c] = zc;
+    ps.add(rc, zc);
   }
-}
-
-// Coarse right-hand side: bc[I] = sum over children p of (b - A x)[p].
-template <typename T, bool SYM>
-__global__ void k_restrict(Op<T> A, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc, Box cb,
-                           const KScal* sc) {
-  DONE_RETURN(sc);
-  const Box fb = A.box;
-  const Seg s = make_seg(cb);
-  auto xat = [&](long long cc, int, int, int) -> T { return x[cc]; };
-  VOS_SEG_LOOP(s, q) {
-    int I, J, K;
-    seg_decode(s, cb, q, I, J, K);
-    if (I >= cb.mx) continue;
-    T sum = 0;
-    const int nk = (fb.mz > 1) ? 2 : 1, nj = (fb.my > 1) ? 2 : 1, ni = (fb.mx > 1) ? 2 : 1;
-    for (int dk = 0; dk < nk; ++dk) {
-      int k = 2 * K + dk;
-      if (fb.mz > 1 && k >= fb.mz) continue;
-      if (fb.mz == 1) k = 0;
-      for (int dj = 0; dj < nj; ++dj) {
-        int j = 2 * J + dj;
-        if (fb.my > 1 && j >= fb.my) continue;
-        if (fb.my == 1) j = 0;
-        for (int di = 0; di < ni; ++di) {
-          int i = 2 * I + di;
-          if (fb.mx > 1 && i >= fb.mx) continue;
-          if (fb.mx == 1) i = 0;
-          long long c = i + (long long)fb.mx * (j + (long long)fb.my * k);
-          sum += b[c] - stencil<T, SYM>(A, i, j, k, c, xat);
-        }
-      }
-    }
-    bc[I + (long long)cb.mx * (J + (long long)cb.my * K)] = sum;
-  }
+  double acc[1] = {ps.get()};
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_pcg_beta(sc, acc[0]);
 }
 
 // Coarsest level: nsweep damped-Jacobi sweeps from zero, one block, in
@@ -509,13 +570,14 @@ __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restri
                          T* __restrict__ r, KScal* sc, RedScratch rs) {
   DONE_RETURN(sc);
   const T alpha = (T)sc->alpha;
-  double acc[1] = {0.0};
+  PSum<T> ps;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     e[c] += alpha * p[c];
     T rc = r[c] - alpha * qv[c];
     r[c] = rc;
-    acc[0] += (double)rc * (double)rc;
+    ps.add(rc, rc);
   }
+  double acc[1] = {ps.get()};
   if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
     sc->rr = acc[0];
     sc->iters += 1;
@@ -552,14 +614,15 @@ __global__ void k_bicg_x(long long n, const T* __restrict__ ph, const T* __restr
                          KScal* sc, RedScratch rs) {
   DONE_RETURN(sc);
   const T alpha = (T)sc->alpha, omega = (T)sc->omega;
-  double acc[2] = {0.0, 0.0};
+  PSum<T> p0, p1;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     e[c] += alpha * ph[c] + omega * sh[c];
     T rc = sv[c] - omega * t[c];
     r[c] = rc;
-    acc[0] += (double)rc * (double)rc;
-    acc[1] += (double)rh[c] * (double)rc;
+    p0.add(rc, rc);
+    p1.add(rh[c], rc);
   }
+  double acc[2] = {p0.get(), p1.get()};
   if (grid_sum<2>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
     double rr = acc[0], rho_new = acc[1];
     sc->rr = rr;
@@ -772,42 +835,30 @@ template void build_coarse_levels<double>(Hier<double>&, cudaStream_t);
 template void build_coarse_levels<float>(Hier<float>&, cudaStream_t);
 
 // One V(nu, nu) cycle: out = M^{-1} rhs (level-0 vectors supplied).
-// With fin == FIN_PCG_BETA the last sweep also reduces rhs . out.
-// Each level owns (b, x, t).  The first two pre-smoothing sweeps from zero
-// are fused into one launch; every launch writes the other buffer, and the
-// start buffer is chosen so that the last post-smoothing write lands in x.
+// Level l owns (b, x, t).  Pre-smoothing starts with x = w b in t, every
+// Jacobi sweep writes the other buffer, the fine residual goes to the free
+// buffer, the coarse correction is added in place; after the 2 nu - 1 buffer
+// swaps the result is in x.
 template <typename T, bool SYM>
-static void jacobi_launch(const char* name, double bytes, int mode, int fin, const Op<T>& A, const T* b,
-                          const T* xin, T* xout, const T* ec, Box cb, T wc, T omega, KScal* sc, const RedScratch& rs,
-                          cudaStream_t st) {
+static void stencil_launch(const char* name, int kind, const Op<T>& A, const T* b, const T* x, T* out, T omega,
+                           const KScal* sc, cudaStream_t st) {
   const Op<T> Z = zview(A);
-  const Box cz = zbox(cb);
   const ZCfg z = zcfg(Z.box);
-  if (mode == 1) {
-    if (fin == FIN_PCG_BETA)
-      vlaunch(name, bytes, k_jacobi<T, SYM, 1, FIN_PCG_BETA>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
-    else
-      vlaunch(name, bytes, k_jacobi<T, SYM, 1, FIN_NONE>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
-  } else if (mode == 2) {
-    if (fin == FIN_PCG_BETA)
-      vlaunch(name, bytes, k_jacobi<T, SYM, 2, FIN_PCG_BETA>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
-    else
-      vlaunch(name, bytes, k_jacobi<T, SYM, 2, FIN_NONE>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
-  } else {
-    if (fin == FIN_PCG_BETA)
-      vlaunch(name, bytes, k_jacobi<T, SYM, 0, FIN_PCG_BETA>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
-    else
-      vlaunch(name, bytes, k_jacobi<T, SYM, 0, FIN_NONE>, z.grid, z.block, st, Z, b, xin, xout, ec, cz, wc, omega, z.zc, sc, rs);
-  }
+  const double wT = sizeof(T), n = ncell(A);
+  const double words = (kind == SK_MV ? 2.0 : 3.0) + 1.0 + n_offs(A) + (kind == SK_JAC && sizeof(T) == 8 ? 1.0 : 0.0);
+  if (kind == SK_JAC)
+    vlaunch(name, words * n * wT, k_stencil<T, SYM, SK_JAC>, z.grid, z.block, st, Z, b, x, out, omega, z.zc, sc);
+  else if (kind == SK_MV)
+    vlaunch(name, words * n * wT, k_stencil<T, SYM, SK_MV>, z.grid, z.block, st, Z, b, x, out, omega, z.zc, sc);
+  else
+    vlaunch(name, words * n * wT, k_stencil<T, SYM, SK_RES>, z.grid, z.block, st, Z, b, x, out, omega, z.zc, sc);
 }
 
 template <typename T, bool SYM>
-static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal* sc, const RedScratch& rs,
-                   cudaStream_t st) {
+static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cudaStream_t st) {
   const int L = h.nlev;
   const int nu = h.mg.nu < 1 ? 1 : h.mg.nu;
   const T wc = (T)h.mg.wc, om = (T)h.mg.omega;
-  const Box none{1, 1, 1};
   auto bufs = [&](int l, const T*& b, T*& x, T*& t) {
     if (l == 0) {
       b = rhs;
@@ -819,77 +870,71 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal*
       t = h.lev[l].t;
     }
   };
-  // coefficient words read by a sweep: diag, offs (+ dinv in FP64)
-  auto swords = [&](const Op<T>& A) { return n_offs(A) + 1.0 + (sizeof(T) == 8 ? 1.0 : 0.0); };
-  // Run `sweeps` damped-Jacobi sweeps from zero on level l; returns the
-  // buffer holding the result.  `more` = writes that follow on this level.
-  auto presmooth = [&](int l, int sweeps, int more, int fin_last) -> T* {
+  auto jac0 = [&](int l, T* dst) {
     const Op<T>& A = h.lev[l].op;
     const T* b;
     T *x, *t;
     bufs(l, b, x, t);
-    const int writes = (sweeps >= 2 ? sweeps - 1 : 1) + more;
-    T* cur = (writes % 2 == 1) ? x : t;
+    const long long n = box_cells(A.box);
+    vlaunch(KN("mg_jac0", l == 0), 3.0 * n * sizeof(T), k_jac0<T>, flat_grid(n), kThreads, st, n, (const T*)A.diag,
+            (const T*)A.dinv, b, dst, om, (const KScal*)sc);
+  };
+  if (L == 1) {
+    const int cs = h.mg.coarse_sweeps < 2 ? 2 : h.mg.coarse_sweeps;
+    const Op<T>& A = h.lev[0].op;
+    const T* b;
+    T *x, *t;
+    bufs(0, b, x, t);
+    T* cur = ((cs - 1) % 2 == 0) ? x : t;
     T* oth = (cur == x) ? t : x;
-    const double n = ncell(A), wT = sizeof(T);
-    const bool fine = (l == 0);
-    if (sweeps >= 2) {
-      jacobi_launch<T, SYM>(KN("mg_jacobi2", fine), (swords(A) + 2.0) * n * wT, 1,
-                            (sweeps == 2 && fin_last) ? fin : FIN_NONE, A, b, nullptr, cur, nullptr, none, T(0), om, sc,
-                            rs, st);
-    } else {
-      vlaunch(KN("mg_smooth0", fine), 3.0 * n * wT, k_smooth0<T>, grid_for(A.box, 0), kThreads, st, A, b, cur, sc);
-    }
-    for (int s = 2; s < sweeps; ++s) {
-      jacobi_launch<T, SYM>(KN("mg_jacobi", fine), (swords(A) + 3.0) * n * wT, 0,
-                            (s == sweeps - 1 && fin_last) ? fin : FIN_NONE, A, b, cur, oth, nullptr, none, T(0), om, sc,
-                            rs, st);
+    jac0(0, cur);
+    for (int s = 1; s < cs; ++s) {
+      stencil_launch<T, SYM>(KN("mg_jac", true), SK_JAC, A, b, cur, oth, om, sc, st);
       T* tmp = cur;
       cur = oth;
       oth = tmp;
     }
-    return cur;
-  };
-  if (L == 1) {
-    const int cs = h.mg.coarse_sweeps < 2 ? 2 : h.mg.coarse_sweeps;
-    presmooth(0, cs, 0, 1);
     return;
   }
   T* pre[16];
   for (int l = 0; l < L - 1; ++l) {
-    pre[l] = presmooth(l, nu, nu, 0);
     const Op<T>& A = h.lev[l].op;
     const T* b;
     T *x, *t;
     bufs(l, b, x, t);
+    T* cur = t;
+    T* oth = x;
+    jac0(l, cur);
+    for (int s = 1; s < nu; ++s) {
+      stencil_launch<T, SYM>(KN("mg_jac", l == 0), SK_JAC, A, b, cur, oth, om, sc, st);
+      T* tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+    pre[l] = cur;
+    stencil_launch<T, SYM>(KN("mg_resid", l == 0), SK_RES, A, b, cur, oth, om, sc, st);
     const Op<T>& C = h.lev[l + 1].op;
-    vlaunch(KN("mg_restrict", l == 0), ((3.0 + n_offs(A)) * ncell(A) + ncell(C)) * sizeof(T), k_restrict<T, SYM>,
-            grid_for(C.box, 0), kThreads, st, A, b, pre[l], h.lev[l + 1].b, C.box, sc);
+    vlaunch(KN("mg_restrict", l == 0), (ncell(A) + ncell(C)) * sizeof(T), k_restrict_sum<T>, grid_for(C.box, 0),
+            kThreads, st, A.box, C.box, (const T*)oth, h.lev[l + 1].b, (const KScal*)sc);
   }
   {
     const Op<T>& A = h.lev[L - 1].op;
     vlaunch(KN("mg_coarse", false), (4.0 + n_offs(A)) * ncell(A) * sizeof(T), k_coarse_solve<T, SYM>, 1, kThreads, st,
-            A, h.lev[L - 1].b, h.lev[L - 1].x, h.mg.coarse_sweeps, sc);
+            A, h.lev[L - 1].b, h.lev[L - 1].x, h.mg.coarse_sweeps, (const KScal*)sc);
   }
   for (int l = L - 2; l >= 0; --l) {
+    const Op<T>& A = h.lev[l].op;
     const T* b;
     T *x, *t;
     bufs(l, b, x, t);
-    const Op<T>& A = h.lev[l].op;
-    const Box cb = h.lev[l + 1].op.box;
-    const T* ec = h.lev[l + 1].x;
     T* cur = pre[l];
     T* oth = (cur == x) ? t : x;
-    const double n = ncell(A), wT = sizeof(T);
+    const Box fz = zbox(A.box), cz = zbox(h.lev[l + 1].op.box);
+    const ZCfg zc = zcfg(fz);
+    vlaunch(KN("mg_prolong", l == 0), (2.0 * ncell(A) + ncell(h.lev[l + 1].op)) * sizeof(T), k_prolong_add<T>,
+            zc.grid, zc.block, st, fz, cz, cur, (const T*)h.lev[l + 1].x, wc, zc.zc, (const KScal*)sc);
     for (int s = 0; s < nu; ++s) {
-      const bool last = (s == nu - 1);
-      const int f = (last && l == 0) ? fin : FIN_NONE;
-      if (s == 0)
-        jacobi_launch<T, SYM>(KN("mg_jacobi_prolong", l == 0), ((swords(A) + 3.0) * n + box_cells(cb)) * wT, 2, f, A,
-                              b, cur, oth, ec, cb, wc, om, sc, rs, st);
-      else
-        jacobi_launch<T, SYM>(KN("mg_jacobi", l == 0), (swords(A) + 3.0) * n * wT, 0, f, A, b, cur, oth, nullptr, none,
-                              T(0), om, sc, rs, st);
+      stencil_launch<T, SYM>(KN("mg_jac", l == 0), SK_JAC, A, b, cur, oth, om, sc, st);
       T* tmp = cur;
       cur = oth;
       oth = tmp;
@@ -899,34 +944,42 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, int fin, KScal*
 
 template <typename T, bool SYM>
 static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters, const RedScratch& rs,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool use_mg) {
   const Box bx = h.lev[0].op.box;
   const long long n = box_cells(bx);
   T* r = (T*)w->r;
   T* z = (T*)w->z;
   T* p = (T*)w->p;
-  T* p2 = (T*)w->p2;
   T* qv = (T*)w->q;
   T* e = (T*)w->e;
   T* scratch = (T*)w->t;
   const Op<T>& A = h.lev[0].op;
   cudaMemsetAsync(e, 0, n * sizeof(T), st);
   vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
-  vcycle<T, SYM>(h, r, z, scratch, FIN_PCG_BETA, w->sc, rs, st);
   const int gf = flat_grid(n);
-  const Op<T> Az = zview(A);
-  const ZCfg zc = zcfg(Az.box);
-  const int chunk = 4;
+  auto precond = [&]() {
+    if (use_mg) {
+      vcycle<T, SYM>(h, r, z, scratch, w->sc, st);
+      vlaunch(KN("dot_rz", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_BETA>, gf, kThreads, st, n, (const T*)r,
+              (const T*)z, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
+    } else {
+      vlaunch(KN("diag_prec", true), 3.0 * n * sizeof(T), k_diag_prec<T>, gf, kThreads, st, n, (const T*)A.dinv,
+              (const T*)r, z, w->sc, rs);
+    }
+  };
+  precond();
+  const int chunk = use_mg ? 4 : 8;
   int it = 0;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      vlaunch(KN("pcg_pq", true), (5.0 + n_offs(A)) * n * sizeof(T), k_pcg_pq_z<T, SYM>, zc.grid, zc.block, st, Az, z,
-              p, p2, qv, zc.zc, w->sc, rs);
-      T* tmp = p;
-      p = p2;
-      p2 = tmp;
-      vlaunch(KN("pcg_xr", true), 6.0 * n * sizeof(T), k_pcg_xr<T>, gf, kThreads, st, n, p, qv, e, r, w->sc, rs);
-      vcycle<T, SYM>(h, r, z, scratch, FIN_PCG_BETA, w->sc, rs, st);
+      vlaunch(KN("pcg_p", true), 3.0 * n * sizeof(T), k_pcg_p<T>, gf, kThreads, st, n, (const T*)z, p,
+              (const KScal*)w->sc);
+      stencil_launch<T, SYM>(KN("pcg_matvec", true), SK_MV, A, nullptr, p, qv, T(0), w->sc, st);
+      vlaunch(KN("dot_pq", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_ALPHA>, gf, kThreads, st, n, (const T*)p,
+              (const T*)qv, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
+      vlaunch(KN("pcg_xr", true), 6.0 * n * sizeof(T), k_pcg_xr<T>, gf, kThreads, st, n, (const T*)p, (const T*)qv, e,
+              r, w->sc, rs);
+      precond();
     }
     it += chunk;
     cudaMemcpyAsync(w->sc_host, w->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st);
@@ -957,21 +1010,24 @@ static int inner_bicgstab(Hier<T>& h, SolverWork* w, double rtol_inner, int max_
   cudaMemcpyAsync(rh, r, n * sizeof(T), cudaMemcpyDeviceToDevice, st);
   vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
   const int gf = flat_grid(n);
-  const Op<T> Az = zview(A);
-  const ZCfg zc = zcfg(Az.box);
   const int chunk = 2;
   int it = 0;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      vlaunch(KN("bicg_p", true), 4.0 * n * sizeof(T), k_bicg_p<T>, gf, kThreads, st, n, r, v, p, w->sc);
-      vcycle<T, SYM>(h, p, ph, scratch, FIN_NONE, w->sc, rs, st);
-      vlaunch(KN("bicg_v", true), (4.0 + n_offs(A)) * n * sizeof(T), k_bicg_v_z<T, SYM>, zc.grid, zc.block, st, Az, ph,
-              rh, v, zc.zc, w->sc, rs);
-      vlaunch(KN("bicg_s", true), 3.0 * n * sizeof(T), k_bicg_s<T>, gf, kThreads, st, n, r, v, sv, w->sc);
-      vcycle<T, SYM>(h, sv, sh, scratch, FIN_NONE, w->sc, rs, st);
-      vlaunch(KN("bicg_t", true), (4.0 + n_offs(A)) * n * sizeof(T), k_bicg_t_z<T, SYM>, zc.grid, zc.block, st, Az, sh,
-              sv, t, zc.zc, w->sc, rs);
-      vlaunch(KN("bicg_x", true), 8.0 * n * sizeof(T), k_bicg_x<T>, gf, kThreads, st, n, ph, sh, sv, t, rh, e, r, w->sc, rs);
+      vlaunch(KN("bicg_p", true), 4.0 * n * sizeof(T), k_bicg_p<T>, gf, kThreads, st, n, (const T*)r, (const T*)v, p,
+              (const KScal*)w->sc);
+      vcycle<T, SYM>(h, p, ph, scratch, w->sc, st);
+      stencil_launch<T, SYM>(KN("bicg_matvec", true), SK_MV, A, nullptr, ph, v, T(0), w->sc, st);
+      vlaunch(KN("dot_rhv", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_BICG_ALPHA>, gf, kThreads, st, n, (const T*)rh,
+              (const T*)v, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
+      vlaunch(KN("bicg_s", true), 3.0 * n * sizeof(T), k_bicg_s<T>, gf, kThreads, st, n, (const T*)r, (const T*)v, sv,
+              (const KScal*)w->sc);
+      vcycle<T, SYM>(h, sv, sh, scratch, w->sc, st);
+      stencil_launch<T, SYM>(KN("bicg_matvec", true), SK_MV, A, nullptr, sh, t, T(0), w->sc, st);
+      vlaunch(KN("dot_ts_tt", true), 3.0 * n * sizeof(T), k_dots<T, 2, DF_BICG_OMEGA>, gf, kThreads, st, n,
+              (const T*)t, (const T*)sv, (const T*)t, (const T*)t, w->sc, rs);
+      vlaunch(KN("bicg_x", true), 8.0 * n * sizeof(T), k_bicg_x<T>, gf, kThreads, st, n, (const T*)ph, (const T*)sh,
+              (const T*)sv, (const T*)t, (const T*)rh, e, r, w->sc, rs);
     }
     it += chunk;
     cudaMemcpyAsync(w->sc_host, w->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st);
@@ -983,7 +1039,7 @@ static int inner_bicgstab(Hier<T>& h, SolverWork* w, double rtol_inner, int max_
 
 template <typename T>
 SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol, int max_iter,
-                  SolverWork* w, const RedScratch& rs, cudaStream_t st) {
+                  SolverWork* w, const RedScratch& rs, cudaStream_t st, bool use_mg) {
   SolveResult res{0, 0, 0.0, 1};
   const Box bx = op64.box;
   const long long n = box_cells(bx);
@@ -994,7 +1050,7 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
   if (mixed) {
     vlaunch("op_convert", (2.0 + n_offs(op64)) * n * (8.0 + sizeof(T)), k_op_convert<T>, flat_grid(n), kThreads, st, op64, h.lev[0].op, n);
   }
-  build_coarse_levels<T>(h, st);
+  if (use_mg) build_coarse_levels<T>(h, st);
   int total = 0;
   const double rbytes = (4.0 + n_offs(op64)) * n * 8.0 + n * sizeof(T);
   const Op<double> oz = zview(op64);
@@ -1035,7 +1091,7 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
     int left = max_iter - total;
     int its;
     if (h.lev[0].op.sym)
-      its = inner_pcg<T, true>(h, w, rin, left, rs, st);
+      its = inner_pcg<T, true>(h, w, rin, left, rs, st, use_mg);
     else
       its = inner_bicgstab<T, false>(h, w, rin, left, rs, st);
     total += its;
@@ -1046,8 +1102,8 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
 }
 
 template SolveResult solve<double>(const Op<double>&, Hier<double>&, const double*, View<double>, double, int,
-                                   SolverWork*, const RedScratch&, cudaStream_t);
+                                   SolverWork*, const RedScratch&, cudaStream_t, bool);
 template SolveResult solve<float>(const Op<double>&, Hier<float>&, const double*, View<double>, double, int,
-                                  SolverWork*, const RedScratch&, cudaStream_t);
+                                  SolverWork*, const RedScratch&, cudaStream_t, bool);
 
 }  // namespace vos

@@ -174,3 +174,14 @@ def test_production_tolerance_bound(V, precision):
     prm = I.make_params(es.shape, Pe=1.0, Da=0.5, L=20.0, method="ivos", Vm=0.5, precision=precision)
     errs, stats = compare(V, es, prm, [0.25] * 4, 1e-5, init=c_start(es, prm))
     assert stats["res_p"] <= 1e-8 and stats["res_c"] <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mass_dominated_momentum(V, precision):
+    """Small dt (2 d nu dt / dx^2 <= 30): the momentum solves take the
+    diagonally preconditioned CG path; same bar as the multigrid path."""
+    es = I.sphere_rock_3d((16, 18, 34), seed=2, median_r=3.0, sigma=0.3, target_porosity=0.5,
+                          start_solid=0.6, band=2, margin=3.0)
+    prm = tight(I.make_params(es.shape, Pe=10.0, Da=1.0, L=6.0, method="ivos", Vm=2.0), precision=precision)
+    assert 2 * 3 * prm["nu"] * 0.005 <= 30
+    compare(V, es, prm, [0.005] * 3, 1e-9, init=c_start(es, prm))
