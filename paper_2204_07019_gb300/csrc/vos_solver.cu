@@ -1080,9 +1080,12 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
       res.converged = 0;
       break;
     }
+    // Inner relative tolerance: just what the outer target needs, but not
+    // below what an FP32 Krylov solve reliably reaches (1e-6) in the mixed
+    // path; the FP64 path asks for a little more than needed.
     double rin = rtol / rel;
     if (mixed) {
-      if (rin < 2e-5) rin = 2e-5;
+      if (rin < 1e-6) rin = 1e-6;
     } else {
       rin *= 0.5;
       if (rin < 1e-15) rin = 1e-15;
