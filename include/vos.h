@@ -157,6 +157,28 @@ int vos_get_stats(vos_handle* h, vos_stats* out);
  * +inf in *dt when neither limit applies. */
 int vos_suggest_dt(vos_handle* h, double cfl, double deps_max, double* dt);
 
+/* Batches of independent simulations (e.g. many micromodels of uneven
+ * sizes and parameters stepped together; no counterpart in the paper's
+ * single-sample runs).  vos_batch_create makes n instances from eps_s[i]
+ * and prm[i] (as vos_create); each instance gets its own non-blocking CUDA
+ * stream and the instances are advanced by a pool of nthreads host worker
+ * threads (<= 0: 8), so their kernels overlap on the GPU.  stream is the
+ * caller's stream: vos_batch_step orders every instance after the work
+ * already on it and makes it wait for all instances, so events recorded
+ * there bracket a whole batch step.  vos_batch_step(b, dt) advances
+ * instance i by dt[i] > 0 and returns VOS_OK, VOS_ENOCONV (some solve hit
+ * max_iter) or the first hard error.  vos_batch_handle gives instance i's
+ * handle (for vos_fields, vos_get_stats, vos_suggest_dt; do not destroy it
+ * and do not use it while a batch step runs).  Per-kernel timing
+ * (vos_prof_enable) is not supported while a batch steps.  Errors are
+ * reported by vos_last_error(NULL). */
+typedef struct vos_batch vos_batch;
+int vos_batch_create(int n, const double* const* eps_s, const vos_params* prm, void* stream,
+                     int nthreads, const vos_allocator* alloc, vos_batch** out);
+int vos_batch_step(vos_batch* b, const double* dt);
+int vos_batch_handle(vos_batch* b, int i, vos_handle** h);
+void vos_batch_destroy(vos_batch* b);
+
 /* Allocation-free form of vos_suggest_dt (the paper has no counterpart: it
  * exists for callers that cannot let a library allocate device memory --
  * hosts that keep the GPU's memory in their own pool, or loops that must not

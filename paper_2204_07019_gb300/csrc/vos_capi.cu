@@ -52,6 +52,7 @@ struct vos_handle {
   RedScratch rs;
   double* dstats;
   double* hstats;  // pinned
+  double* d_dt;    // device copy of the step's dt (read by the physics kernels)
   vos_stats stats;
   std::string err;
   int dev;
@@ -162,8 +163,10 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
   const int ivos = (h->prm.method == VOS_IVOS);
   vos_stats& s = h->stats;
   int status = VOS_OK;
+  launch_set_scalar(h->d_dt, dt, st);
+  const double* dtp = h->d_dt;
   // S1: solid fraction and (implicitly) permeability
-  launch_eps_update(P, h->eps, h->eps_old, h->R, dt, h->dstats, h->rs, st);
+  launch_eps_update(P, h->eps, h->eps_old, h->R, dtp, h->dstats, h->rs, st);
   // S2: momentum predictor per component
   for (int a = 0; a < nd; ++a) {
     cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -171,7 +174,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     s.outer_u[a] = 0;
     s.res_u[a] = 0.0;
     if (box_cells(S[a].box) == 0) continue;
-    launch_mom_assemble(P, a, h->eps, h->p, h->u[a], dt, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
+    launch_mom_assemble(P, a, h->eps, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
     // The momentum operator is (1/dt + drag) I - nu lap: when the mass term
     // dominates (2 d nu dt / dx^2 <= 30) the diagonally preconditioned CG
     // converges in a grid-independent number of iterations at a third of
@@ -185,7 +188,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     if (!r.converged) status = VOS_ENOCONV;
   }
   // S3: pressure correction, projection
-  launch_pres_assemble(P, h->eps, h->us, h->R, dt, S[3].h.mg.omega, S[3].op64, S[3].rhs, st);
+  launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, st);
   cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st);
   {
     SolveResult r =
@@ -196,7 +199,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     s.res_p = r.relres;
     if (!r.converged) status = VOS_ENOCONV;
   }
-  launch_project(P, h->eps, h->phi, dt, h->us, h->u, h->p, st);
+  launch_project(P, h->eps, h->phi, dtp, h->us, h->u, h->p, st);
   // S4-S6: reactive surface data (from eps^{n+1}, c^n), transport, rates
   if (ivos) {
     launch_ivos_faces(P, h->eps, h->c, h->fd, st);
@@ -204,7 +207,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     launch_vos_lambda(P, h->eps, h->prm.lambda, h->prm.method == VOS_PSI_PRIME, h->dstats, h->rs, st);
     launch_vos_coef(P, h->eps, h->dstats, h->kr, st);
   }
-  launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->u, h->kr, h->fd, dt, S[4].h.mg.omega, S[4].op64,
+  launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->u, h->kr, h->fd, dtp, S[4].h.mg.omega, S[4].op64,
                         S[4].rhs, st);
   {
     SolveResult r =
@@ -347,11 +350,12 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     char* cur = (char*)dev_alloc(h, solver_work_bytes(maxc));
     if (!cur) return fail(VOS_ENOMEM, "device allocation failed (Krylov vectors)");
     h->work = solver_work_carve(cur, maxc);
-    char* rsb = (char*)dev_alloc(h, kMaxRedValues * kMaxRedBlocks * sizeof(double) + 256 + ST_COUNT * sizeof(double));
+    char* rsb = (char*)dev_alloc(h, kMaxRedValues * kMaxRedBlocks * sizeof(double) + 256 + ST_COUNT * sizeof(double) + 256);
     if (!rsb) return fail(VOS_ENOMEM, "device allocation failed (reduction scratch)");
     h->rs.partials = (double*)rsb;
     h->rs.counter = (unsigned int*)(rsb + kMaxRedValues * kMaxRedBlocks * sizeof(double));
     h->dstats = (double*)(rsb + kMaxRedValues * kMaxRedBlocks * sizeof(double) + 256);
+    h->d_dt = h->dstats + ST_COUNT;
   }
   if (cudaMallocHost((void**)&h->hstats, ST_COUNT * sizeof(double)) != cudaSuccess)
     return fail(VOS_ENOMEM, "pinned host allocation failed");

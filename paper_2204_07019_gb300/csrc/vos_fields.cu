@@ -58,8 +58,9 @@ __device__ __forceinline__ bool cell_in(const Phys& P, int i, int j, int k) {
 // ---------------------------------------------------------------------------
 // S1: eps^{n+1} = clamp(eps^n + dt Vm R^n, eps_min, 1)   (Eq. mbs)
 // ---------------------------------------------------------------------------
-__global__ void k_eps_update(Phys P, double* eps, double* eps_old, const double* R, double dt, double* stats,
+__global__ void k_eps_update(Phys P, double* eps, double* eps_old, const double* R, const double* __restrict__ dtp, double* stats,
                              RedScratch rs) {
+  const double dt = *dtp;
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   double acc[2] = {0.0, 0.0};
@@ -83,10 +84,10 @@ __global__ void k_eps_update(Phys P, double* eps, double* eps_old, const double*
   }
 }
 
-void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, double dt, double* stats,
+void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, const double* __restrict__ dtp, double* stats,
                        const RedScratch& rs, cudaStream_t st) {
   Box bx{P.nx, P.ny, P.nz};
-  vlaunch("eps_update", 32.0 * box_cells(bx), k_eps_update, grid_for(bx, kMaxRedBlocks), kThreads, st, P, eps, eps_old, R, dt, stats, rs);
+  vlaunch("eps_update", 32.0 * box_cells(bx), k_eps_update, grid_for(bx, kMaxRedBlocks), kThreads, st, P, eps, eps_old, R, dtp, stats, rs);
 }
 
 // ---------------------------------------------------------------------------
@@ -97,8 +98,9 @@ void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double
 // minus cell is cell (i,j,k).
 // ---------------------------------------------------------------------------
 __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__ eps, const double* __restrict__ p,
-                               const double* __restrict__ uold, double dt, double omega, Op<double> A,
+                               const double* __restrict__ uold, const double* __restrict__ dtp, double omega, Op<double> A,
                                double* __restrict__ rhs) {
+  const double dt = *dtp;
   const Seg s = make_seg(ub);
   const double cnu = P.nu / (P.dx * P.dx);
   VOS_SEG_LOOP(s, q) {
@@ -165,10 +167,10 @@ __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__
   }
 }
 
-void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, double dt,
+void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, const double* __restrict__ dtp,
                          double omega, Op<double> A, double* rhs, cudaStream_t st) {
   if (box_cells(A.box) == 0) return;
-  vlaunch("mom_assemble", (6.0 + P.dim) * 8.0 * box_cells(A.box), k_mom_assemble, grid_for(A.box, 0), kThreads, st, P, a, A.box, eps, p, uold, dt, omega, A, rhs);
+  vlaunch("mom_assemble", (6.0 + P.dim) * 8.0 * box_cells(A.box), k_mom_assemble, grid_for(A.box, 0), kThreads, st, P, a, A.box, eps, p, uold, dtp, omega, A, rhs);
 }
 
 // ---------------------------------------------------------------------------
@@ -178,8 +180,9 @@ void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* 
 // ---------------------------------------------------------------------------
 __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const double* __restrict__ u0,
                                 const double* __restrict__ u1, const double* __restrict__ u2,
-                                const double* __restrict__ R, double dt, double omega, Op<double> A,
+                                const double* __restrict__ R, const double* __restrict__ dtp, double omega, Op<double> A,
                                 double* __restrict__ rhs) {
+  const double dt = *dtp;
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   const double idx2 = 1.0 / (P.dx * P.dx);
@@ -217,15 +220,16 @@ __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const do
   }
 }
 
-void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3], const double* R, double dt,
+void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3], const double* R, const double* __restrict__ dtp,
                           double omega, Op<double> A, double* rhs, cudaStream_t st) {
-  vlaunch("pres_assemble", (5.0 + 2.0 * P.dim) * 8.0 * box_cells(A.box), k_pres_assemble, grid_for(A.box, 0), kThreads, st, P, eps, us[0], us[1], us[2], R, dt, omega, A, rhs);
+  vlaunch("pres_assemble", (5.0 + 2.0 * P.dim) * 8.0 * box_cells(A.box), k_pres_assemble, grid_for(A.box, 0), kThreads, st, P, eps, us[0], us[1], us[2], R, dtp, omega, A, rhs);
 }
 
 // u^{n+1} = u* - dt eps_f grad phi on interior faces and the outlet face;
 // fixed faces copy u*.
 __global__ void k_project(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ phi,
-                          double dt, const double* __restrict__ us, double* __restrict__ u) {
+                          const double* __restrict__ dtp, const double* __restrict__ us, double* __restrict__ u) {
+  const double dt = *dtp;
   const Seg s = make_seg(fb);
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
@@ -253,12 +257,12 @@ __global__ void k_add(long long n, double* __restrict__ p, const double* __restr
     p[c] += phi[c];
 }
 
-void launch_project(const Phys& P, const double* eps, const double* phi, double dt, double* const us[3],
+void launch_project(const Phys& P, const double* eps, const double* phi, const double* __restrict__ dtp, double* const us[3],
                     double* const u[3], double* p, cudaStream_t st) {
   const int nb = (P.dim == 2) ? 2 : 3;
   for (int a = 0; a < nb; ++a) {
     Box fb{P.nx + (a == 0), P.ny + (a == 1), P.nz + (a == 2)};
-    vlaunch("project", 32.0 * box_cells(fb), k_project, grid_for(fb, 0), kThreads, st, P, a, fb, eps, phi, dt, us[a], u[a]);
+    vlaunch("project", 32.0 * box_cells(fb), k_project, grid_for(fb, 0), kThreads, st, P, a, fb, eps, phi, dtp, us[a], u[a]);
   }
   long long n = (long long)P.nx * P.ny * P.nz;
   vlaunch("p_update", 24.0 * n, k_add, grid_for(Box{P.nx, P.ny, P.nz}, 0), kThreads, st, n, p, phi);
@@ -372,6 +376,10 @@ __global__ void k_set_scalar(double* dst, double v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
 }
 
+void launch_set_scalar(double* dst, double v, cudaStream_t st) {
+  vlaunch("set_scalar", 8.0, k_set_scalar, 1, 32, st, dst, v);
+}
+
 void launch_vos_lambda(const Phys& P, const double* eps, double lambda_fixed, int fit, double* stats,
                        const RedScratch& rs, cudaStream_t st) {
   if (fit) {
@@ -445,8 +453,9 @@ template <bool IVOS>
 __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const double* __restrict__ eps_old,
                                  const double* __restrict__ cold, const double* __restrict__ u0,
                                  const double* __restrict__ u1, const double* __restrict__ u2,
-                                 const double* __restrict__ kr, FaceData f0, FaceData f1, FaceData f2, double dt,
+                                 const double* __restrict__ kr, FaceData f0, FaceData f1, FaceData f2, const double* __restrict__ dtp,
                                  double omega, Op<double> A, double* __restrict__ rhs) {
+  const double dt = *dtp;
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   const double idx2 = 1.0 / (P.dx * P.dx);
@@ -531,15 +540,15 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
 }
 
 void launch_trans_assemble(const Phys& P, int ivos, const double* eps, const double* eps_old, const double* cold,
-                           double* const u[3], const double* kr, const FaceData fd[3], double dt, double omega,
+                           double* const u[3], const double* kr, const FaceData fd[3], const double* __restrict__ dtp, double omega,
                            Op<double> A, double* rhs, cudaStream_t st) {
   int g = grid_for(A.box, 0);
   if (ivos)
     vlaunch("trans_assemble", (6.0 + 5.0 * P.dim) * 8.0 * box_cells(A.box), k_trans_assemble<true>, g, kThreads, st, P,
-            eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2], dt, omega, A, rhs);
+            eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2], dtp, omega, A, rhs);
   else
     vlaunch("trans_assemble", (7.0 + 2.0 * P.dim) * 8.0 * box_cells(A.box), k_trans_assemble<false>, g, kThreads, st, P,
-            eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2], dt, omega, A, rhs);
+            eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2], dtp, omega, A, rhs);
 }
 
 // ---------------------------------------------------------------------------

@@ -30,15 +30,15 @@ struct FaceData {  // iVoS per-face data for one axis (face-array layout)
 };
 
 // S1
-void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, double dt, double* stats,
+void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, const double* dtp, double* stats,
                        const RedScratch& rs, cudaStream_t st);
 // S2
-void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, double dt,
+void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, const double* dtp,
                          double omega, Op<double> A, double* rhs, cudaStream_t st);
 // S3
-void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3], const double* R, double dt,
+void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3], const double* R, const double* dtp,
                           double omega, Op<double> A, double* rhs, cudaStream_t st);
-void launch_project(const Phys& P, const double* eps, const double* phi, double dt, double* const us[3],
+void launch_project(const Phys& P, const double* eps, const double* phi, const double* dtp, double* const us[3],
                     double* const u[3], double* p, cudaStream_t st);
 // S5/S6
 void launch_ivos_faces(const Phys& P, const double* eps, const double* cold, const FaceData fd[3],
@@ -47,11 +47,12 @@ void launch_vos_lambda(const Phys& P, const double* eps, double lambda_fixed, in
                        const RedScratch& rs, cudaStream_t st);
 void launch_vos_coef(const Phys& P, const double* eps, const double* stats, double* kr, cudaStream_t st);
 void launch_trans_assemble(const Phys& P, int ivos, const double* eps, const double* eps_old, const double* cold,
-                           double* const u[3], const double* kr, const FaceData fd[3], double dt, double omega,
+                           double* const u[3], const double* kr, const FaceData fd[3], const double* dtp, double omega,
                            Op<double> A, double* rhs, cudaStream_t st);
 void launch_rates(const Phys& P, int ivos, const double* eps, const double* c, const double* kr,
                   const FaceData fd[3], double* R, double* Rf, double* stats, const RedScratch& rs,
                   cudaStream_t st);
+void launch_set_scalar(double* dst, double v, cudaStream_t st);
 void launch_dt_limits(const Phys& P, const double* eps, double* const u[3], const double* R, double* stats,
                       const RedScratch& rs, cudaStream_t st);
 

@@ -20,7 +20,8 @@ __all__ = [
     "VosError", "load_library", "vos_create", "vos_step", "vos_fields", "vos_set_fields",
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
     "vos_device_bytes", "vos_kernel_launches", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
-    "vos_suggest_dt_noalloc", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS",
+    "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
+    "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -33,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
     "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
     "vos_kernel_launches", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
-    "vos_suggest_dt_noalloc",
+    "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle", "vos_batch_destroy",
 ]
 
 
@@ -126,6 +127,15 @@ def load_library(path=None):
     lib.vos_suggest_dt_noalloc.argtypes = [ctypes.POINTER(VosParams)] + [ctypes.c_void_p] * 5 + [
         ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
     lib.vos_suggest_dt_noalloc.restype = ctypes.c_int
+    lib.vos_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(dp), ctypes.POINTER(VosParams), ctypes.c_void_p,
+                                     ctypes.c_int, ctypes.POINTER(VosAllocator), ctypes.POINTER(ctypes.c_void_p)]
+    lib.vos_batch_create.restype = ctypes.c_int
+    lib.vos_batch_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    lib.vos_batch_step.restype = ctypes.c_int
+    lib.vos_batch_handle.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    lib.vos_batch_handle.restype = ctypes.c_int
+    lib.vos_batch_destroy.argtypes = [ctypes.c_void_p]
+    lib.vos_batch_destroy.restype = None
     if path is None:
         _lib = lib
     return lib
@@ -309,6 +319,72 @@ def vos_suggest_dt_noalloc(prm, eps, u, v, w, R, cfl=0.5, deps_max=0.005, stream
     if rc != VOS_OK:
         raise VosError(rc, lib.vos_last_error(None).decode())
     return dt.value
+
+
+class _Batch:
+    def __init__(self, ptr, prms, keep):
+        self.ptr = ptr
+        self.prms = prms
+        self._keep = keep
+        self.handles = []
+
+
+def vos_batch_create(eps_list, prm_list, stream=None, nthreads=8, allocator="auto"):
+    """vos_batch_create: n instances (lists of eps_s arrays and parameter
+    dicts); returns a batch whose ``handles`` are instance handles."""
+    lib = load_library()
+    n = len(eps_list)
+    arrs = [np.ascontiguousarray(e, dtype=np.float64) for e in eps_list]
+    ptrs = (ctypes.POINTER(ctypes.c_double) * n)(*[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs])
+    prms = (VosParams * n)(*[_params_struct(p) for p in prm_list])
+    keep = [arrs, ptrs, prms]
+    use_torch = allocator == "torch"
+    if allocator == "auto":
+        try:
+            import torch
+            use_torch = torch.cuda.is_available()
+        except ImportError:
+            use_torch = False
+    st = None
+    if stream is None and use_torch:
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+    elif stream is not None:
+        st = int(getattr(stream, "cuda_stream", stream))
+    alloc_ptr = None
+    if use_torch:
+        a, cbs = _torch_allocator()
+        keep += [a, cbs]
+        alloc_ptr = ctypes.byref(a)
+    out = ctypes.c_void_p()
+    rc = lib.vos_batch_create(n, ptrs, prms, ctypes.c_void_p(st), int(nthreads), alloc_ptr, ctypes.byref(out))
+    if rc != VOS_OK:
+        raise VosError(rc, lib.vos_last_error(None).decode())
+    b = _Batch(out, [dict(p) for p in prm_list], keep)
+    for i in range(n):
+        hp = ctypes.c_void_p()
+        lib.vos_batch_handle(out, i, ctypes.byref(hp))
+        b.handles.append(_Handle(hp, prm_list[i], []))
+    return b
+
+
+def vos_batch_step(b, dts):
+    """vos_batch_step: advance instance i by dts[i]; returns VOS_OK or VOS_ENOCONV."""
+    lib = load_library()
+    arr = (ctypes.c_double * len(dts))(*[float(x) for x in dts])
+    rc = lib.vos_batch_step(b.ptr, arr)
+    if rc not in (VOS_OK, VOS_ENOCONV):
+        raise VosError(rc, lib.vos_last_error(None).decode())
+    return rc
+
+
+def vos_batch_destroy(b):
+    """vos_batch_destroy: free every instance (idempotent)."""
+    if b is not None and b.ptr:
+        load_library().vos_batch_destroy(b.ptr)
+        b.ptr = None
+        for h in b.handles:
+            h.ptr = None
 
 
 def vos_last_error(h=None):
