@@ -211,7 +211,9 @@ size_t vos_device_bytes(const vos_handle* h);
 
 /* Diagnostics (process-wide, not tied to a handle; not thread-safe while
  * timing is on).
- * vos_kernel_launches: number of kernels this library has launched.
+ * vos_kernel_launches: number of kernel executions of the step so far
+ *   (counted on the device, so kernels replayed by graphs are included;
+ *   synchronises the device).
  * vos_prof_enable: time every launch of the kernels whose name contains
  *   one of the comma-separated substrings of filter ("*" = all, NULL or ""
  *   = off) with CUDA events on the launching stream.
@@ -221,6 +223,14 @@ size_t vos_device_bytes(const vos_handle* h);
  *   size needed if len is too small.
  * vos_prof_reset: drop the accumulated timings. */
 uint64_t vos_kernel_launches(void);
+/* vos_set_launch_mode(1) (default): vos_step replays the whole step as one
+ *   CUDA graph whose refinement and Krylov loops are conditional WHILE nodes
+ *   driven on the device (captured at the first step of each momentum-
+ *   preconditioner choice; replayed on an internal stream ordered after the
+ *   handle's stream by events).  vos_set_launch_mode(0): the same kernels
+ *   launched one by one with host polls of the device scalars.  While
+ *   per-kernel timing is on the eager sequence is used. */
+int vos_set_launch_mode(int graphs);
 int vos_prof_enable(const char* filter);
 int vos_prof_report(char* buf, size_t len);
 void vos_prof_reset(void);

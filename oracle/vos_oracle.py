@@ -426,10 +426,13 @@ def ivos_faces(eps, c_old, prm):
     and tangential parts equal to the mean of the two cells' centred
     gradients; n_f = -g_f / (|g_f| + delta) with delta = 1e-8/dx (reading);
     Phi_R . e_a = k_c c_f n_a.  Upwind = the cell the flux leaves
-    (n_a > 0: minus cell).  c_f uses the van Leer weight frozen from c^n;
-    eps_f is the van Leer interpolation of eps.
+    (n_a > 0: minus cell).  Reading: c_f = c_U^{n+1} + corr with the van
+    Leer correction corr = w(c^n) (c_D^n - c_U^n) taken from the previous
+    concentration (implicit upwind + explicit deferred correction), so the
+    implicit reaction matrix is an upwind M-matrix; eps_f is the van Leer
+    interpolation of eps.
     Returns per axis a dict with n_a (normal component), positive (bool),
-    w (frozen weight) and eps_vl.
+    corr (deferred van Leer correction) and eps_vl.
     """
     axes = _axes(prm)
     dx = prm["dx"]
@@ -447,20 +450,21 @@ def ivos_faces(eps, c_old, prm):
         na = -gn / (np.sqrt(g2) + delta)
         pos = na > 0.0
         cUU, cU, cD, h = _upwind_triplets(c_old, a, pos)
-        w = van_leer_weight(cUU, cU, cD, h)
+        corr = van_leer_weight(cUU, cU, cD, h) * (cD - cU)
         eUU, eU, eD, h2 = _upwind_triplets(eps, a, pos)
         evl = eU + van_leer_weight(eUU, eU, eD, h2) * (eD - eU)
-        out[a] = dict(na=na, pos=pos, w=w, eps_vl=evl)
+        out[a] = dict(na=na, pos=pos, corr=corr, eps_vl=evl)
     return out
 
 
 def ivos_face_flux(c, a, fd, prm):
     """F_f / V = k_c n_a c_f / dx on interior faces along a (sign along +a),
-    with c_f = c_U + w (c_D - c_U) and the frozen weight w."""
+    with c_f = c_U + corr (upwind value of c plus the deferred van Leer
+    correction of ``ivos_faces``)."""
     n = c.shape[_nax(a)]
     m1 = c[_sl(a, 0, n - 1)]; p0 = c[_sl(a, 1, n)]
-    cU = np.where(fd["pos"], m1, p0); cD = np.where(fd["pos"], p0, m1)
-    cf = cU + fd["w"] * (cD - cU)
+    cU = np.where(fd["pos"], m1, p0)
+    cf = cU + fd["corr"]
     return prm["kc"] * fd["na"] * cf / prm["dx"]
 
 
@@ -495,7 +499,8 @@ def transport_system(eps_old, eps, c_old, u, prm, dt, kr=None, faces=None):
     with D* = D (Sec. 2.2), eps_f = mean of the two cells, c = c_in on the
     inlet faces (ghost 2 c_in - c_P), zero diffusive flux at the outlet and
     walls.  R_f: VoS-psi(') -> kr c (diagonal, kr from ``vos_coefficient``);
-    iVoS -> eps div(Phi_R) with the frozen-weight face values.
+    iVoS -> eps div(Phi_R) with face values c_U^{n+1} + corr (implicit
+    upwind; the van Leer correction from c^n goes to the right-hand side).
     Reading: the stoichiometric coefficient zeta multiplies the transport
     sink (boundary condition Eq. bcc1).
     """
@@ -517,24 +522,24 @@ def transport_system(eps_old, eps, c_old, u, prm, dt, kr=None, faces=None):
     rhs[inl] += 2.0 * D * eps[inl] * prm["c_in"] / dx ** 2
     if kr is not None:
         diag = diag + zeta * kr
+    rhs = rhs.ravel().copy()
     if faces is not None:
         kc = prm["kc"]
         for a in _axes(prm):
             n = shp[_nax(a)]
             fd = faces[a]
             Pm = num[_sl(a, 0, n - 1)]; Qp = num[_sl(a, 1, n)]
-            U = np.where(fd["pos"], Pm, Qp); Dn = np.where(fd["pos"], Qp, Pm)
+            U = np.where(fd["pos"], Pm, Qp)
             s = kc * fd["na"] / dx
             eP = eps[_sl(a, 0, n - 1)]; eQ = eps[_sl(a, 1, n)]
             for row, sign, ecell in ((Pm, 1.0, eP), (Qp, -1.0, eQ)):
                 coef = zeta * sign * ecell * s
-                rows += [row.ravel(), row.ravel()]
-                cols += [U.ravel(), Dn.ravel()]
-                vals += [(coef * (1.0 - fd["w"])).ravel(), (coef * fd["w"]).ravel()]
+                rows.append(row.ravel()); cols.append(U.ravel()); vals.append(coef.ravel())
+                np.subtract.at(rhs, row.ravel(), (coef * fd["corr"]).ravel())
     rows.append(num.ravel()); cols.append(num.ravel()); vals.append(diag.ravel())
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(N, N)).tocsr()
-    return A, rhs.ravel()
+    return A, rhs
 
 
 # --------------------------------------------------------------------------

@@ -53,12 +53,21 @@ struct vos_handle {
   double* dstats;
   double* hstats;  // pinned
   double* d_dt;    // device copy of the step's dt (read by the physics kernels)
+  // graph mode: the whole step captured once per momentum-preconditioner
+  // choice and replayed on an internal stream ordered after the caller's
+  SolveStats* dsolve;  // device, one per system
+  SolveStats* hsolve;  // pinned copy
+  cudaStream_t gs, gs1, gs2;
+  cudaEvent_t ev_in, ev_out;
+  cudaGraphExec_t exec[2];
   vos_stats stats;
   std::string err;
   int dev;
 };
 
 namespace {
+
+bool g_use_graphs = true;
 
 int set_err(vos_handle* h, int code, const char* fmt, ...) {
   char buf[512];
@@ -100,6 +109,19 @@ void free_all(vos_handle* h) {
   h->work = nullptr;
   if (h->hstats) cudaFreeHost(h->hstats);
   h->hstats = nullptr;
+  if (h->hsolve) cudaFreeHost(h->hsolve);
+  h->hsolve = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    if (h->exec[i]) cudaGraphExecDestroy(h->exec[i]);
+    h->exec[i] = nullptr;
+  }
+  if (h->gs) cudaStreamDestroy(h->gs);
+  if (h->gs1) cudaStreamDestroy(h->gs1);
+  if (h->gs2) cudaStreamDestroy(h->gs2);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  h->gs = h->gs1 = h->gs2 = nullptr;
+  h->ev_in = h->ev_out = nullptr;
 }
 
 Box unknown_box(const Phys& P, int sys) {
@@ -229,6 +251,98 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
   return status;
 }
 
+// The step enqueued for graph capture (no host synchronisation inside).
+template <typename T>
+cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
+  const Phys& P = h->ph;
+  cudaStream_t st = h->gs;
+  const int nd = P.dim;
+  const int ivos = (h->prm.method == VOS_IVOS);
+  const double* dtp = h->d_dt;
+  launch_eps_update(P, h->eps, h->eps_old, h->R, dtp, h->dstats, h->rs, st);
+  for (int a = 0; a < nd; ++a) {
+    VOS_CUDA_TRY(cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (box_cells(S[a].box) == 0) continue;
+    launch_mom_assemble(P, a, h->eps, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
+    VOS_CUDA_TRY(solve_capture<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
+                                  h->work, h->rs, st, mom_mg, h->dsolve + a, h->gs1, h->gs2));
+  }
+  launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, st);
+  VOS_CUDA_TRY(cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st));
+  VOS_CUDA_TRY(solve_capture<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter,
+                                h->work, h->rs, st, true, h->dsolve + 3, h->gs1, h->gs2));
+  launch_project(P, h->eps, h->phi, dtp, h->us, h->u, h->p, st);
+  if (ivos) {
+    launch_ivos_faces(P, h->eps, h->c, h->fd, st);
+  } else {
+    launch_vos_lambda(P, h->eps, h->prm.lambda, h->prm.method == VOS_PSI_PRIME, h->dstats, h->rs, st);
+    launch_vos_coef(P, h->eps, h->dstats, h->kr, st);
+  }
+  launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->u, h->kr, h->fd, dtp, S[4].h.mg.omega, S[4].op64,
+                        S[4].rhs, st);
+  VOS_CUDA_TRY(solve_capture<T>(S[4].op64, S[4].h, S[4].rhs, unknown_view(h, 4), h->prm.c_rtol, h->prm.max_iter,
+                                h->work, h->rs, st, true, h->dsolve + 4, h->gs1, h->gs2));
+  launch_rates(P, ivos, h->eps, h->c, h->kr, h->fd, h->R, h->Rf, h->dstats, h->rs, st);
+  VOS_CUDA_TRY(cudaMemcpyAsync(h->hstats, h->dstats, ST_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+  VOS_CUDA_TRY(cudaMemcpyAsync(h->hsolve, h->dsolve, 5 * sizeof(SolveStats), cudaMemcpyDeviceToHost, st));
+  return cudaGetLastError();
+}
+
+template <typename T>
+int step_graph(vos_handle* h, Sys<T>* S, double dt) {
+  const Phys& P = h->ph;
+  const bool mom_mg = 2.0 * P.dim * P.nu * dt / (P.dx * P.dx) > 30.0;
+  const int gi = mom_mg ? 1 : 0;
+  if (!h->exec[gi]) {
+    cudaError_t e = cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_step: begin capture: %s", cudaGetErrorString(e));
+    cudaError_t ee = enqueue_step<T>(h, S, mom_mg);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->gs, &g);
+    if (ee != cudaSuccess || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return set_err(h, VOS_ECUDA, "vos_step: graph capture failed: %s",
+                     cudaGetErrorString(ee != cudaSuccess ? ee : e));
+    }
+    e = cudaGraphInstantiate(&h->exec[gi], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->exec[gi] = nullptr;
+      return set_err(h, VOS_ECUDA, "vos_step: graph instantiate: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaEventRecord(h->ev_in, h->st);
+  cudaStreamWaitEvent(h->gs, h->ev_in, 0);
+  launch_set_scalar(h->d_dt, dt, h->gs);
+  cudaGraphLaunch(h->exec[gi], h->gs);
+  cudaEventRecord(h->ev_out, h->gs);
+  cudaStreamWaitEvent(h->st, h->ev_out, 0);
+  cudaError_t e = cudaStreamSynchronize(h->gs);
+  if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_step: %s", cudaGetErrorString(e));
+  vos_stats& s = h->stats;
+  int status = VOS_OK;
+  for (int a = 0; a < 3; ++a) {
+    const bool on = a < P.dim && box_cells(S[a].box) > 0;
+    s.iters_u[a] = on ? h->hsolve[a].iters : 0;
+    s.outer_u[a] = on ? h->hsolve[a].outer : 0;
+    s.res_u[a] = on ? h->hsolve[a].relres : 0.0;
+    if (on && !h->hsolve[a].converged) status = VOS_ENOCONV;
+  }
+  s.iters_p = h->hsolve[3].iters;
+  s.outer_p = h->hsolve[3].outer;
+  s.res_p = h->hsolve[3].relres;
+  s.iters_c = h->hsolve[4].iters;
+  s.outer_c = h->hsolve[4].outer;
+  s.res_c = h->hsolve[4].relres;
+  if (!h->hsolve[3].converged || !h->hsolve[4].converged) status = VOS_ENOCONV;
+  s.step += 1;
+  s.t += dt;
+  s.status = status;
+  if (status == VOS_ENOCONV) set_err(h, VOS_ENOCONV, "vos_step: a linear solve reached max_iter");
+  return status;
+}
+
 int validate(const vos_params* p) {
   if (!p) return set_err(nullptr, VOS_EINVAL, "params is NULL");
   if (p->dim != 2 && p->dim != 3) return set_err(nullptr, VOS_EINVAL, "dim must be 2 or 3 (got %d)", p->dim);
@@ -297,6 +411,11 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
   h->bytes = 0;
   h->work = nullptr;
   h->hstats = nullptr;
+  h->hsolve = nullptr;
+  h->dsolve = nullptr;
+  h->gs = h->gs1 = h->gs2 = nullptr;
+  h->ev_in = h->ev_out = nullptr;
+  h->exec[0] = h->exec[1] = nullptr;
   std::memset(&h->stats, 0, sizeof(h->stats));
   cudaGetDevice(&h->dev);
   int sms = 0;
@@ -324,9 +443,9 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     if (!h->u[a] || !h->us[a]) return fail(VOS_ENOMEM, "device allocation failed (face fields)");
     if (prm->method == VOS_IVOS) {
       h->fd[a].s = (double*)dev_alloc(h, fb);
-      h->fd[a].w = (double*)dev_alloc(h, fb);
+      h->fd[a].corr = (double*)dev_alloc(h, fb);
       h->fd[a].evl = (double*)dev_alloc(h, fb);
-      if (!h->fd[a].s || !h->fd[a].w || !h->fd[a].evl) return fail(VOS_ENOMEM, "device allocation failed (iVoS)");
+      if (!h->fd[a].s || !h->fd[a].corr || !h->fd[a].evl) return fail(VOS_ENOMEM, "device allocation failed (iVoS)");
     }
   }
   const int trans_sym = (prm->method == VOS_IVOS) ? 0 : 1;
@@ -357,8 +476,17 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     h->dstats = (double*)(rsb + kMaxRedValues * kMaxRedBlocks * sizeof(double) + 256);
     h->d_dt = h->dstats + ST_COUNT;
   }
-  if (cudaMallocHost((void**)&h->hstats, ST_COUNT * sizeof(double)) != cudaSuccess)
+  if (cudaMallocHost((void**)&h->hstats, ST_COUNT * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->hsolve, 5 * sizeof(SolveStats)) != cudaSuccess)
     return fail(VOS_ENOMEM, "pinned host allocation failed");
+  h->dsolve = (SolveStats*)dev_alloc(h, 5 * sizeof(SolveStats));
+  if (!h->dsolve) return fail(VOS_ENOMEM, "device allocation failed (solve stats)");
+  if (cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->gs1, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->gs2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return fail(VOS_ECUDA, "stream/event creation failed");
   std::memset(h->hstats, 0, ST_COUNT * sizeof(double));
   // initial fields (App. C: eps = max(1 - eps_s, eps_min))
   std::vector<double> e0(N);
@@ -395,8 +523,12 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
 int vos_step(vos_handle* h, double dt) {
   if (!h) return set_err(nullptr, VOS_EINVAL, "handle is NULL");
   if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(h, VOS_EINVAL, "dt must be finite and > 0");
-  if (h->prm.precision == VOS_FP64) return step_impl<double>(h, h->sd, dt);
-  return step_impl<float>(h, h->sf, dt);
+  // CUDA-graph replay unless per-kernel timing is on (timing brackets each
+  // launch with events, so it uses the eager launch sequence -- the same
+  // kernels in the same order).
+  const bool graphs = g_use_graphs && !vos::g_prof_any;
+  if (h->prm.precision == VOS_FP64) return graphs ? step_graph<double>(h, h->sd, dt) : step_impl<double>(h, h->sd, dt);
+  return graphs ? step_graph<float>(h, h->sf, dt) : step_impl<float>(h, h->sf, dt);
 }
 
 int vos_fields(vos_handle* h, uint32_t mask, double* eps, double* c, double* u, double* v, double* w, double* p,
@@ -515,5 +647,10 @@ void vos_destroy(vos_handle* h) {
 }
 
 size_t vos_device_bytes(const vos_handle* h) { return h ? h->bytes : 0; }
+
+int vos_set_launch_mode(int graphs) {
+  g_use_graphs = graphs != 0;
+  return VOS_OK;
+}
 
 }  // extern "C"

@@ -8,6 +8,15 @@
 
 namespace vos {
 
+// Kernel executions of this file (see VOS_COUNT_EXEC).
+static __device__ unsigned long long vos_exec_count = 0;
+unsigned long long exec_count_fields() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, vos_exec_count, sizeof(v));
+  return v;
+}
+
+
 namespace {
 
 __device__ __forceinline__ long long cidx(const Phys& P, int i, int j, int k) {
@@ -60,6 +69,7 @@ __device__ __forceinline__ bool cell_in(const Phys& P, int i, int j, int k) {
 // ---------------------------------------------------------------------------
 __global__ void k_eps_update(Phys P, double* eps, double* eps_old, const double* R, const double* __restrict__ dtp, double* stats,
                              RedScratch rs) {
+  VOS_COUNT_EXEC();
   const double dt = *dtp;
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
@@ -100,6 +110,7 @@ void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double
 __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__ eps, const double* __restrict__ p,
                                const double* __restrict__ uold, const double* __restrict__ dtp, double omega, Op<double> A,
                                double* __restrict__ rhs) {
+  VOS_COUNT_EXEC();
   const double dt = *dtp;
   const Seg s = make_seg(ub);
   const double cnu = P.nu / (P.dx * P.dx);
@@ -182,6 +193,7 @@ __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const do
                                 const double* __restrict__ u1, const double* __restrict__ u2,
                                 const double* __restrict__ R, const double* __restrict__ dtp, double omega, Op<double> A,
                                 double* __restrict__ rhs) {
+  VOS_COUNT_EXEC();
   const double dt = *dtp;
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
@@ -229,6 +241,7 @@ void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3],
 // fixed faces copy u*.
 __global__ void k_project(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ phi,
                           const double* __restrict__ dtp, const double* __restrict__ us, double* __restrict__ u) {
+  VOS_COUNT_EXEC();
   const double dt = *dtp;
   const Seg s = make_seg(fb);
   VOS_SEG_LOOP(s, q) {
@@ -253,6 +266,7 @@ __global__ void k_project(Phys P, int a, Box fb, const double* __restrict__ eps,
 }
 
 __global__ void k_add(long long n, double* __restrict__ p, const double* __restrict__ phi) {
+  VOS_COUNT_EXEC();
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
     p[c] += phi[c];
 }
@@ -273,11 +287,15 @@ void launch_project(const Phys& P, const double* eps, const double* phi, const d
 //   g_f = ((eps_+ - eps_-)/dx along a; tangential: mean of the two cells'
 //   centred gradients), n_a = -g_a / (|g_f| + 1e-8/dx),
 //   s = k_c n_a / dx  (reactive flux per unit volume per unit c_f),
-//   w = van Leer weight of c^n along the flux direction (frozen),
+//   corr = w(c^n) (c_D^n - c_U^n): the van Leer correction of the face
+//          value from the previous concentration (deferred correction:
+//          c_f = c_U^{n+1} + corr keeps the implicit matrix an upwind
+//          M-matrix),
 //   evl = van Leer interpolation of eps along the flux direction.
 // ---------------------------------------------------------------------------
 __global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ cold,
                              FaceData fd) {
+  VOS_COUNT_EXEC();
   const Seg s = make_seg(fb);
   const int nb = (P.dim == 2) ? 2 : 3;
   const double delta = 1e-8 / P.dx;
@@ -290,7 +308,7 @@ __global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ e
     const int m = f[a], n = ncell(P, a);
     if (m < 1 || m > n - 1) {
       fd.s[fcx] = 0.0;
-      fd.w[fcx] = 0.0;
+      fd.corr[fcx] = 0.0;
       fd.evl[fcx] = 0.0;
       continue;
     }
@@ -323,7 +341,8 @@ __global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ e
     }
     const long long cUU = has ? cidx(P, uu[0], uu[1], uu[2]) : cU;
     fd.s[fcx] = P.kc * na / P.dx;
-    fd.w[fcx] = vl_weight(cold[cUU], cold[cU], cold[cD], has);
+    const double cu = cold[cU], cd = cold[cD];
+    fd.corr[fcx] = vl_weight(cold[cUU], cu, cd, has) * (cd - cu);
     const double eU = eps[cU], eD = eps[cD];
     fd.evl[fcx] = eU + vl_weight(eps[cUU], eU, eD, has) * (eD - eU);
   }
@@ -354,6 +373,7 @@ __device__ __forceinline__ double gradmag(const Phys& P, const double* eps, int 
 }
 
 __global__ void k_vos_lambda(Phys P, const double* __restrict__ eps, double* stats, RedScratch rs) {
+  VOS_COUNT_EXEC();
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   double acc[2] = {0.0, 0.0};
@@ -373,6 +393,7 @@ __global__ void k_vos_lambda(Phys P, const double* __restrict__ eps, double* sta
 }
 
 __global__ void k_set_scalar(double* dst, double v) {
+  VOS_COUNT_EXEC();
   if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
 }
 
@@ -392,6 +413,7 @@ void launch_vos_lambda(const Phys& P, const double* eps, double lambda_fixed, in
 
 __global__ void k_vos_coef(Phys P, const double* __restrict__ eps, const double* __restrict__ stats,
                            double* __restrict__ kr) {
+  VOS_COUNT_EXEC();
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   const double lam = stats[ST_LAMBDA];
@@ -455,6 +477,7 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
                                  const double* __restrict__ u1, const double* __restrict__ u2,
                                  const double* __restrict__ kr, FaceData f0, FaceData f1, FaceData f2, const double* __restrict__ dtp,
                                  double omega, Op<double> A, double* __restrict__ rhs) {
+  VOS_COUNT_EXEC();
   const double dt = *dtp;
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
@@ -493,28 +516,26 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
       fp[d] += 1;
       adv += (conv_flux(P, d, fp[0], fp[1], fp[2], cold, us[d]) - conv_flux(P, d, i, j, k, cold, us[d])) / P.dx;
       if (IVOS) {
+        // reactive flux F = s (c_U^{n+1} + corr): upwind value implicit,
+        // the deferred van Leer correction on the right-hand side
         const double zc = P.zeta * e;
         if (hasp) {  // this cell is the minus cell of its plus face
           const long long fx = fidx(P, d, fp[0], fp[1], fp[2]);
-          const double sf = fds[d].s[fx], w = fds[d].w[fx];
-          if (sf > 0.0) {  // U = this, D = plus
-            diag += zc * sf * (1.0 - w);
-            offp[d] += zc * sf * w;
-          } else {  // U = plus, D = this
-            diag += zc * sf * w;
-            offp[d] += zc * sf * (1.0 - w);
-          }
+          const double sf = fds[d].s[fx];
+          if (sf > 0.0)
+            diag += zc * sf;  // U = this
+          else
+            offp[d] += zc * sf;  // U = plus
+          b -= zc * sf * fds[d].corr[fx];
         }
         if (hasm) {  // this cell is the plus cell of its minus face (outward flux -F)
           const long long fx = fidx(P, d, i, j, k);
-          const double sf = fds[d].s[fx], w = fds[d].w[fx];
-          if (sf > 0.0) {  // U = minus, D = this
-            diag -= zc * sf * w;
-            offm[d] -= zc * sf * (1.0 - w);
-          } else {  // U = this, D = minus
-            diag -= zc * sf * (1.0 - w);
-            offm[d] -= zc * sf * w;
-          }
+          const double sf = fds[d].s[fx];
+          if (sf > 0.0)
+            offm[d] -= zc * sf;  // U = minus
+          else
+            diag -= zc * sf;  // U = this
+          b += zc * sf * fds[d].corr[fx];
         }
       }
     }
@@ -555,7 +576,8 @@ void launch_trans_assemble(const Phys& P, int ivos, const double* eps, const dou
 // S6: reaction rates from c^{n+1}.
 //   iVoS (Eq. RfiVoS): R_f = eps_P sum_f outward F_f / V,
 //                      R   = R_f - sum_f outward evl_f F_f / V,
-//   with F_f / V = s_f (c_U + w (c_D - c_U)) on interior faces.
+//   with F_f / V = s_f (c_U^{n+1} + corr_f) on interior faces (the face
+//   values the transport solve used, so the sink and R_f agree exactly).
 //   VoS-psi('): R = R_f = kr c.
 // Also reduces sum R V, sum R_f V, sum eps c V.
 // ---------------------------------------------------------------------------
@@ -563,6 +585,7 @@ template <bool IVOS>
 __global__ void k_rates(Phys P, const double* __restrict__ eps, const double* __restrict__ cn,
                         const double* __restrict__ kr, FaceData f0, FaceData f1, FaceData f2, double* __restrict__ R,
                         double* __restrict__ Rf, double* stats, RedScratch rs) {
+  VOS_COUNT_EXEC();
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   const int nb = (P.dim == 2) ? 2 : 3;
@@ -585,19 +608,17 @@ __global__ void k_rates(Phys P, const double* __restrict__ eps, const double* __
           int fp[3] = {i, j, k};
           fp[d] += 1;
           const long long fx = fidx(P, d, fp[0], fp[1], fp[2]);
-          const double sf = fds[d].s[fx], w = fds[d].w[fx];
-          const double cm = cn[c], cp = cn[cidx(P, hi[0], hi[1], hi[2])];
-          const double cU = sf > 0.0 ? cm : cp, cD = sf > 0.0 ? cp : cm;
-          const double F = sf * (cU + w * (cD - cU));
+          const double sf = fds[d].s[fx];
+          const double cU = sf > 0.0 ? cn[c] : cn[cidx(P, hi[0], hi[1], hi[2])];
+          const double F = sf * (cU + fds[d].corr[fx]);
           sumF += F;
           sumEF += fds[d].evl[fx] * F;
         }
         if (cell_in(P, lo[0], lo[1], lo[2])) {
           const long long fx = fidx(P, d, i, j, k);
-          const double sf = fds[d].s[fx], w = fds[d].w[fx];
-          const double cm = cn[cidx(P, lo[0], lo[1], lo[2])], cp = cn[c];
-          const double cU = sf > 0.0 ? cm : cp, cD = sf > 0.0 ? cp : cm;
-          const double F = sf * (cU + w * (cD - cU));
+          const double sf = fds[d].s[fx];
+          const double cU = sf > 0.0 ? cn[cidx(P, lo[0], lo[1], lo[2])] : cn[c];
+          const double F = sf * (cU + fds[d].corr[fx]);
           sumF -= F;
           sumEF -= fds[d].evl[fx] * F;
         }
@@ -640,6 +661,7 @@ void launch_rates(const Phys& P, int ivos, const double* eps, const double* c, c
 __global__ void k_dt_limits(Phys P, const double* __restrict__ eps, const double* __restrict__ u0,
                             const double* __restrict__ u1, const double* __restrict__ u2,
                             const double* __restrict__ R, double* stats, RedScratch rs) {
+  VOS_COUNT_EXEC();
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   const int nb = (P.dim == 2) ? 2 : 3;

@@ -17,9 +17,19 @@ namespace vos {
 // stream and records its algorithmic bytes.
 // ---------------------------------------------------------------------------
 extern std::atomic<unsigned long long> g_launch_count;
+unsigned long long exec_count_sum();  // sum of the per-file device counters
 extern bool g_prof_any;
 int prof_before(const char* name, double bytes, cudaStream_t st);
 void prof_after(int slot, cudaStream_t st);
+
+// Kernel executions counted on the device (one atomic per execution, by
+// block 0 thread 0), so launches replayed inside CUDA graphs are counted.
+#define VOS_COUNT_EXEC()                                                        \
+  do {                                                                          \
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && \
+        threadIdx.y == 0 && threadIdx.z == 0)                                   \
+      atomicAdd(&vos_exec_count, 1ull);                                         \
+  } while (0)
 
 template <typename... KArgs, typename... Args>
 inline void vlaunch(const char* name, double bytes, void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
@@ -261,6 +271,17 @@ struct Hier {
   MGParams mg;
 };
 
+// Device-side record of one solve when the loops run inside a CUDA graph.
+struct SolveStats {
+  double relres;  // last scaled relative residual
+  int iters;      // inner Krylov iterations (summed over passes)
+  int outer;      // refinement passes
+  int converged;
+  int zero;       // right-hand side was zero: x set to 0
+  int started;    // an inner pass has been initialised
+  int pad;
+};
+
 struct SolveResult {
   int iters;      // total inner Krylov iterations
   int outer;      // refinement passes
@@ -291,6 +312,15 @@ extern int g_num_sms;
 template <typename T>
 void hier_carve(Hier<T>& h, Box fine, int sym, char*& cursor, const MGParams& mg, bool share_level0,
                 const Op<double>* op64);
+
+// Enqueue a whole solve on a stream that is being captured into a CUDA
+// graph: the refinement loop and the Krylov loop become conditional WHILE
+// nodes driven by device-side controller kernels (no host round trip).
+// Bodies are captured on s1 (outer) and s2 (inner).  Results in *ss.
+template <typename T>
+cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol,
+                          int max_iter, SolverWork* w, const RedScratch& rs, cudaStream_t st, bool use_mg,
+                          SolveStats* ss, cudaStream_t s1, cudaStream_t s2);
 
 size_t solver_work_bytes(long long max_cells);
 SolverWork* solver_work_carve(char*& cursor, long long max_cells);

@@ -26,7 +26,9 @@ enum StatIdx {
 };
 
 struct FaceData {  // iVoS per-face data for one axis (face-array layout)
-  double *s, *w, *evl;
+  double *s;     // k_c n_a / dx: reactive flux per unit volume per unit c_f
+  double *corr;  // deferred van Leer correction w(c^n) (c_D^n - c_U^n)
+  double *evl;   // van Leer interpolation of eps
 };
 
 // S1

@@ -14,6 +14,9 @@
 namespace vos {
 
 std::atomic<unsigned long long> g_launch_count{0};
+unsigned long long exec_count_solver();
+unsigned long long exec_count_fields();
+unsigned long long exec_count_sum() { return exec_count_solver() + exec_count_fields(); }
 bool g_prof_any = false;
 
 namespace {
@@ -137,6 +140,11 @@ void vos_prof_reset(void) {
   vos::g_ids.clear();
 }
 
-uint64_t vos_kernel_launches(void) { return vos::g_launch_count.load(); }
+uint64_t vos_kernel_launches(void) {
+  // Executions counted on the device: includes kernels replayed by CUDA
+  // graphs (synchronises with the device).
+  cudaDeviceSynchronize();
+  return vos::exec_count_sum();
+}
 
 }  // extern "C"

@@ -13,6 +13,15 @@
 
 namespace vos {
 
+// Kernel executions of this file (see VOS_COUNT_EXEC).
+static __device__ unsigned long long vos_exec_count = 0;
+unsigned long long exec_count_solver() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, vos_exec_count, sizeof(v));
+  return v;
+}
+
+
 int g_num_sms = 152;
 
 __host__ int grid_for(Box b, int max_blocks) {
@@ -173,6 +182,7 @@ enum StencilKind { SK_JAC = 0, SK_MV = 1, SK_RES = 2 };
 template <typename T, bool SYM, int KIND>
 __global__ void __launch_bounds__(kThreads) k_stencil(Op<T> A, const T* __restrict__ b, const T* __restrict__ x,
                                                      T* __restrict__ out, T omega, int zc, const KScal* sc) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   const Box bx = A.box;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,6 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Op<T> A, const T* __restri
 template <typename T>
 __global__ void k_jac0(long long n, const T* __restrict__ diag, const T* __restrict__ dinv, const T* __restrict__ b,
                        T* __restrict__ x, T omega, const KScal* sc) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     T w;
@@ -241,6 +252,7 @@ __global__ void k_jac0(long long n, const T* __restrict__ diag, const T* __restr
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_prolong_add(Box fb, Box cb, T* __restrict__ x, const T* __restrict__ ec,
                                                          T wc, int zc, const KScal* sc) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -256,6 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(Box fb, Box cb, T* __r
 // Restriction of a fine residual: bc[I] = sum of its (up to 8) children.
 template <typename T>
 __global__ void k_restrict_sum(Box fb, Box cb, const T* __restrict__ r, T* __restrict__ bc, const KScal* sc) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   const Seg s = make_seg(cb);
   const int ni = fb.mx > 1 ? 2 : 1, nj = fb.my > 1 ? 2 : 1, nk = fb.mz > 1 ? 2 : 1;
@@ -289,6 +302,7 @@ __device__ void fin_pcg_beta(KScal* sc, double rz);
 template <typename T, int NV, int FIN>
 __global__ void k_dots(long long n, const T* __restrict__ a0, const T* __restrict__ b0, const T* __restrict__ a1,
                        const T* __restrict__ b1, KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   PSum<T> p0, p1;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -332,6 +346,7 @@ __global__ void k_dots(long long n, const T* __restrict__ a0, const T* __restric
 // PCG: p = z + beta p (first iteration: p = z)
 template <typename T>
 __global__ void k_pcg_p(long long n, const T* __restrict__ z, T* __restrict__ p, const KScal* sc) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   const bool first = (sc->iters == 0);
   const T beta = (T)sc->beta;
@@ -344,6 +359,7 @@ template <typename T, bool SYM>
 __global__ void __launch_bounds__(kThreads) k_outer_residual_z(Op<double> A, const double* __restrict__ b,
                                                               View<double> x, T* __restrict__ rT, double* outer,
                                                               int zc, RedScratch rs) {
+  VOS_COUNT_EXEC();
   // outer[0] = |D^-1 r|^2 and outer[1] = |D^-1 b|^2 (convergence test);
   // outer[2] = |r|^2, the unscaled norm the inner Krylov loop measures.
   double acc[3] = {0.0, 0.0, 0.0};
@@ -415,6 +431,7 @@ static ZCfg zcfg(Box b) {
 template <typename T>
 __global__ void k_diag_prec(long long n, const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ z,
                             KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   PSum<T> ps;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -431,6 +448,7 @@ __global__ void k_diag_prec(long long n, const T* __restrict__ dinv, const T* __
 // shared memory (box of at most kThreads cells).
 template <typename T, bool SYM>
 __global__ void k_coarse_solve(Op<T> A, const T* __restrict__ b, T* __restrict__ x, int nsweep, const KScal* sc) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   __shared__ T xs[2][kThreads];
   const Box bx = A.box;
@@ -464,6 +482,7 @@ __global__ void k_coarse_solve(Op<T> A, const T* __restrict__ b, T* __restrict__
 // ---------------------------------------------------------------------------
 template <typename T, bool SYM>
 __global__ void k_galerkin(Op<T> F, Op<T> C, T omega) {
+  VOS_COUNT_EXEC();
   const Box fb = F.box, cb = C.box;
   const Seg s = make_seg(cb);
   VOS_SEG_LOOP(s, q) {
@@ -548,6 +567,7 @@ __global__ void k_galerkin(Op<T> F, Op<T> C, T omega) {
 // Krylov vector kernels
 // ---------------------------------------------------------------------------
 __global__ void k_kscal_init(KScal* sc, const double* outer, double rtol_inner, int max_iters) {
+  VOS_COUNT_EXEC();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double rr = outer[2];  // unscaled |r|^2 of the inner right-hand side
     sc->bb = rr;
@@ -572,6 +592,7 @@ __global__ void k_kscal_init(KScal* sc, const double* outer, double rtol_inner, 
 template <typename T>
 __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restrict__ qv, T* __restrict__ e,
                          T* __restrict__ r, KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   const T alpha = (T)sc->alpha;
   PSum<T> ps;
@@ -593,6 +614,7 @@ __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restri
 template <typename T>
 __global__ void k_bicg_p(long long n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ p,
                          const KScal* sc) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   const bool first = (sc->iters == 0);
   const T beta = (T)sc->beta, omega = (T)sc->omega;
@@ -605,6 +627,7 @@ __global__ void k_bicg_p(long long n, const T* __restrict__ r, const T* __restri
 template <typename T>
 __global__ void k_bicg_s(long long n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ sv,
                          const KScal* sc) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   const T alpha = (T)sc->alpha;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
@@ -616,6 +639,7 @@ template <typename T>
 __global__ void k_bicg_x(long long n, const T* __restrict__ ph, const T* __restrict__ sh, const T* __restrict__ sv,
                          const T* __restrict__ t, const T* __restrict__ rh, T* __restrict__ e, T* __restrict__ r,
                          KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   const T alpha = (T)sc->alpha, omega = (T)sc->omega;
   PSum<T> p0, p1;
@@ -648,6 +672,7 @@ __global__ void k_bicg_x(long long n, const T* __restrict__ ph, const T* __restr
 // x += e (x a strided view)
 template <typename T>
 __global__ void k_outer_update(Box bx, View<double> x, const T* __restrict__ e) {
+  VOS_COUNT_EXEC();
   const Seg s = make_seg(bx);
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
@@ -660,6 +685,7 @@ __global__ void k_outer_update(Box bx, View<double> x, const T* __restrict__ e) 
 
 // x = 0 on a strided view
 __global__ void k_view_zero(Box bx, View<double> x) {
+  VOS_COUNT_EXEC();
   const Seg s = make_seg(bx);
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
@@ -672,6 +698,7 @@ __global__ void k_view_zero(Box bx, View<double> x) {
 // Convert the FP64 operator into T (level 0 of a mixed-precision hierarchy).
 template <typename T>
 __global__ void k_op_convert(Op<double> A, Op<T> B, long long n) {
+  VOS_COUNT_EXEC();
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     B.diag[c] = (T)A.diag[c];
     B.dinv[c] = (T)A.dinv[c];
@@ -946,45 +973,94 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
   }
 }
 
+// Vectors of the inner solves (views of SolverWork).
+template <typename T>
+struct KVec {
+  T *r, *z, *p, *q, *e, *rh, *v, *s, *t, *ph, *sh, *scratch;
+};
+template <typename T>
+static KVec<T> kvec(SolverWork* w, bool bicg) {
+  KVec<T> k;
+  k.r = (T*)w->r;
+  k.z = (T*)w->z;
+  k.p = (T*)w->p;
+  k.q = (T*)w->q;
+  k.e = (T*)w->e;
+  k.rh = (T*)w->rh;
+  k.v = (T*)w->v;
+  k.s = (T*)w->s;
+  k.t = (T*)w->t;
+  k.ph = (T*)w->ph;
+  k.sh = (T*)w->sh;
+  k.scratch = bicg ? (T*)w->z : (T*)w->t;
+  return k;
+}
+
+// z = M^-1 r and the PCG beta (multigrid V-cycle or diagonal).
+template <typename T, bool SYM>
+static void pcg_precond(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w, const RedScratch& rs,
+                        cudaStream_t st, bool use_mg) {
+  const int gf = flat_grid(n);
+  if (use_mg) {
+    vcycle<T, SYM>(h, k.r, k.z, k.scratch, w->sc, st);
+    vlaunch(KN("dot_rz", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_BETA>, gf, kThreads, st, n, (const T*)k.r,
+            (const T*)k.z, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
+  } else {
+    vlaunch(KN("diag_prec", true), 3.0 * n * sizeof(T), k_diag_prec<T>, gf, kThreads, st, n,
+            (const T*)h.lev[0].op.dinv, (const T*)k.r, k.z, w->sc, rs);
+  }
+}
+
+// One PCG iteration (kernels early-exit once the solve is done).
+template <typename T, bool SYM>
+static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w, const RedScratch& rs,
+                          cudaStream_t st, bool use_mg) {
+  const Op<T>& A = h.lev[0].op;
+  const int gf = flat_grid(n);
+  vlaunch(KN("pcg_p", true), 3.0 * n * sizeof(T), k_pcg_p<T>, gf, kThreads, st, n, (const T*)k.z, k.p,
+          (const KScal*)w->sc);
+  stencil_launch<T, SYM>(KN("pcg_matvec", true), SK_MV, A, nullptr, k.p, k.q, T(0), w->sc, st);
+  vlaunch(KN("dot_pq", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_ALPHA>, gf, kThreads, st, n, (const T*)k.p,
+          (const T*)k.q, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
+  vlaunch(KN("pcg_xr", true), 6.0 * n * sizeof(T), k_pcg_xr<T>, gf, kThreads, st, n, (const T*)k.p, (const T*)k.q,
+          k.e, k.r, w->sc, rs);
+  pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg);
+}
+
+// One BiCGStab iteration (right preconditioned, two V-cycles).
+template <typename T, bool SYM>
+static void bicg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w, const RedScratch& rs,
+                           cudaStream_t st) {
+  const Op<T>& A = h.lev[0].op;
+  const int gf = flat_grid(n);
+  vlaunch(KN("bicg_p", true), 4.0 * n * sizeof(T), k_bicg_p<T>, gf, kThreads, st, n, (const T*)k.r, (const T*)k.v,
+          k.p, (const KScal*)w->sc);
+  vcycle<T, SYM>(h, k.p, k.ph, k.scratch, w->sc, st);
+  stencil_launch<T, SYM>(KN("bicg_matvec", true), SK_MV, A, nullptr, k.ph, k.v, T(0), w->sc, st);
+  vlaunch(KN("dot_rhv", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_BICG_ALPHA>, gf, kThreads, st, n, (const T*)k.rh,
+          (const T*)k.v, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
+  vlaunch(KN("bicg_s", true), 3.0 * n * sizeof(T), k_bicg_s<T>, gf, kThreads, st, n, (const T*)k.r, (const T*)k.v, k.s,
+          (const KScal*)w->sc);
+  vcycle<T, SYM>(h, k.s, k.sh, k.scratch, w->sc, st);
+  stencil_launch<T, SYM>(KN("bicg_matvec", true), SK_MV, A, nullptr, k.sh, k.t, T(0), w->sc, st);
+  vlaunch(KN("dot_ts_tt", true), 3.0 * n * sizeof(T), k_dots<T, 2, DF_BICG_OMEGA>, gf, kThreads, st, n, (const T*)k.t,
+          (const T*)k.s, (const T*)k.t, (const T*)k.t, w->sc, rs);
+  vlaunch(KN("bicg_x", true), 8.0 * n * sizeof(T), k_bicg_x<T>, gf, kThreads, st, n, (const T*)k.ph, (const T*)k.sh,
+          (const T*)k.s, (const T*)k.t, (const T*)k.rh, k.e, k.r, w->sc, rs);
+}
+
 template <typename T, bool SYM>
 static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters, const RedScratch& rs,
                      cudaStream_t st, bool use_mg) {
-  const Box bx = h.lev[0].op.box;
-  const long long n = box_cells(bx);
-  T* r = (T*)w->r;
-  T* z = (T*)w->z;
-  T* p = (T*)w->p;
-  T* qv = (T*)w->q;
-  T* e = (T*)w->e;
-  T* scratch = (T*)w->t;
-  const Op<T>& A = h.lev[0].op;
-  cudaMemsetAsync(e, 0, n * sizeof(T), st);
+  const long long n = box_cells(h.lev[0].op.box);
+  const KVec<T> k = kvec<T>(w, false);
+  cudaMemsetAsync(k.e, 0, n * sizeof(T), st);
   vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
-  const int gf = flat_grid(n);
-  auto precond = [&]() {
-    if (use_mg) {
-      vcycle<T, SYM>(h, r, z, scratch, w->sc, st);
-      vlaunch(KN("dot_rz", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_BETA>, gf, kThreads, st, n, (const T*)r,
-              (const T*)z, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
-    } else {
-      vlaunch(KN("diag_prec", true), 3.0 * n * sizeof(T), k_diag_prec<T>, gf, kThreads, st, n, (const T*)A.dinv,
-              (const T*)r, z, w->sc, rs);
-    }
-  };
-  precond();
+  pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg);
   const int chunk = use_mg ? 4 : 8;
   int it = 0;
   while (true) {
-    for (int c = 0; c < chunk; ++c) {
-      vlaunch(KN("pcg_p", true), 3.0 * n * sizeof(T), k_pcg_p<T>, gf, kThreads, st, n, (const T*)z, p,
-              (const KScal*)w->sc);
-      stencil_launch<T, SYM>(KN("pcg_matvec", true), SK_MV, A, nullptr, p, qv, T(0), w->sc, st);
-      vlaunch(KN("dot_pq", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_ALPHA>, gf, kThreads, st, n, (const T*)p,
-              (const T*)qv, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
-      vlaunch(KN("pcg_xr", true), 6.0 * n * sizeof(T), k_pcg_xr<T>, gf, kThreads, st, n, (const T*)p, (const T*)qv, e,
-              r, w->sc, rs);
-      precond();
-    }
+    for (int c = 0; c < chunk; ++c) pcg_iteration<T, SYM>(h, k, n, w, rs, st, use_mg);
     it += chunk;
     cudaMemcpyAsync(w->sc_host, w->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -996,43 +1072,16 @@ static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters
 template <typename T, bool SYM>
 static int inner_bicgstab(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters, const RedScratch& rs,
                           cudaStream_t st) {
-  const Box bx = h.lev[0].op.box;
-  const long long n = box_cells(bx);
-  T* r = (T*)w->r;
-  T* rh = (T*)w->rh;
-  T* p = (T*)w->p;
-  T* v = (T*)w->v;
-  T* sv = (T*)w->s;
-  T* t = (T*)w->t;
-  T* ph = (T*)w->ph;
-  T* sh = (T*)w->sh;
-  T* e = (T*)w->e;
-  T* scratch = (T*)w->z;
-  const Op<T>& A = h.lev[0].op;
-  cudaMemsetAsync(e, 0, n * sizeof(T), st);
-  cudaMemsetAsync(v, 0, n * sizeof(T), st);
-  cudaMemcpyAsync(rh, r, n * sizeof(T), cudaMemcpyDeviceToDevice, st);
+  const long long n = box_cells(h.lev[0].op.box);
+  const KVec<T> k = kvec<T>(w, true);
+  cudaMemsetAsync(k.e, 0, n * sizeof(T), st);
+  cudaMemsetAsync(k.v, 0, n * sizeof(T), st);
+  cudaMemcpyAsync(k.rh, k.r, n * sizeof(T), cudaMemcpyDeviceToDevice, st);
   vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
-  const int gf = flat_grid(n);
   const int chunk = 2;
   int it = 0;
   while (true) {
-    for (int c = 0; c < chunk; ++c) {
-      vlaunch(KN("bicg_p", true), 4.0 * n * sizeof(T), k_bicg_p<T>, gf, kThreads, st, n, (const T*)r, (const T*)v, p,
-              (const KScal*)w->sc);
-      vcycle<T, SYM>(h, p, ph, scratch, w->sc, st);
-      stencil_launch<T, SYM>(KN("bicg_matvec", true), SK_MV, A, nullptr, ph, v, T(0), w->sc, st);
-      vlaunch(KN("dot_rhv", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_BICG_ALPHA>, gf, kThreads, st, n, (const T*)rh,
-              (const T*)v, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
-      vlaunch(KN("bicg_s", true), 3.0 * n * sizeof(T), k_bicg_s<T>, gf, kThreads, st, n, (const T*)r, (const T*)v, sv,
-              (const KScal*)w->sc);
-      vcycle<T, SYM>(h, sv, sh, scratch, w->sc, st);
-      stencil_launch<T, SYM>(KN("bicg_matvec", true), SK_MV, A, nullptr, sh, t, T(0), w->sc, st);
-      vlaunch(KN("dot_ts_tt", true), 3.0 * n * sizeof(T), k_dots<T, 2, DF_BICG_OMEGA>, gf, kThreads, st, n,
-              (const T*)t, (const T*)sv, (const T*)t, (const T*)t, w->sc, rs);
-      vlaunch(KN("bicg_x", true), 8.0 * n * sizeof(T), k_bicg_x<T>, gf, kThreads, st, n, (const T*)ph, (const T*)sh,
-              (const T*)sv, (const T*)t, (const T*)rh, e, r, w->sc, rs);
-    }
+    for (int c = 0; c < chunk; ++c) bicg_iteration<T, SYM>(h, k, n, w, rs, st);
     it += chunk;
     cudaMemcpyAsync(w->sc_host, w->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -1040,6 +1089,213 @@ static int inner_bicgstab(Hier<T>& h, SolverWork* w, double rtol_inner, int max_
   }
   return w->sc_host->iters;
 }
+
+// ---------------------------------------------------------------------------
+// Graph mode: device-side loop control
+// ---------------------------------------------------------------------------
+__global__ void k_ctrl_init(SolveStats* ss, KScal* sc) {
+  VOS_COUNT_EXEC();
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ss->relres = 0.0;
+    ss->iters = 0;
+    ss->outer = 0;
+    ss->converged = 0;
+    ss->zero = 0;
+    ss->started = 0;
+    sc->iters = 0;
+    sc->done = 1;
+  }
+}
+
+// Refinement controller (one thread), run after each FP64 true residual:
+// decides convergence, sets the outer and inner loop conditions and
+// initialises the inner Krylov scalars (the same rules as the host loop).
+template <bool MIXED>
+__global__ void k_ctrl(SolveStats* ss, KScal* sc, const double* outer, double rtol, int max_outer, int max_iter,
+                       cudaGraphConditionalHandle ho, cudaGraphConditionalHandle hi) {
+  VOS_COUNT_EXEC();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (ss->started) ss->iters += sc->iters;
+  const double rr = outer[0], bb = outer[1];
+  bool stop = false;
+  if (bb == 0.0) {
+    ss->zero = 1;
+    ss->relres = 0.0;
+    ss->converged = 1;
+    stop = true;
+  } else {
+    const double rel = sqrt(rr / bb);
+    ss->relres = rel;
+    if (rel <= rtol) {
+      ss->converged = 1;
+      stop = true;
+    } else if (ss->outer >= max_outer || ss->iters >= max_iter || !isfinite(rel)) {
+      ss->converged = 0;
+      stop = true;
+    } else {
+      double rin = rtol / rel;
+      if (MIXED) {
+        if (rin < 2e-5) rin = 2e-5;
+      } else {
+        rin *= 0.5;
+        if (rin < 1e-15) rin = 1e-15;
+      }
+      if (rin > 0.5) rin = 0.5;
+      const double r2 = outer[2];
+      sc->bb = r2;
+      sc->rr = r2;
+      sc->rz = 0.0;
+      sc->rz_old = 0.0;
+      sc->pq = 0.0;
+      sc->alpha = 0.0;
+      sc->beta = 0.0;
+      sc->omega = 1.0;
+      sc->rho = r2;
+      sc->rhv = 0.0;
+      sc->tol2 = rin * rin * r2;
+      sc->iters = 0;
+      sc->max_iters = max_iter - ss->iters;
+      sc->breakdown = 0;
+      sc->done = (r2 == 0.0) ? 1 : 0;
+      ss->outer += 1;
+      ss->started = 1;
+    }
+  }
+  if (stop) {
+    sc->done = 1;
+    sc->iters = 0;
+    ss->started = 0;
+  }
+  cudaGraphSetConditional(ho, stop ? 0u : 1u);
+  cudaGraphSetConditional(hi, sc->done ? 0u : 1u);
+}
+
+__global__ void k_loop_check(const KScal* sc, cudaGraphConditionalHandle hi) {
+  VOS_COUNT_EXEC();
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(hi, sc->done ? 0u : 1u);
+}
+
+// x += e, or x = 0 when the right-hand side was zero.
+template <typename T>
+__global__ void k_outer_update_g(Box bx, View<double> x, const T* __restrict__ e, const SolveStats* ss) {
+  VOS_COUNT_EXEC();
+  const bool zero = ss->zero != 0;
+  const Seg s = make_seg(bx);
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
+    double* px = x.base + i + (long long)x.sy * j + (long long)x.sz * k;
+    *px = zero ? 0.0 : *px + (double)e[c];
+  }
+}
+
+// Add a WHILE node (condition handle hnd) to the graph being captured on st
+// and begin capturing its body on sb.
+static cudaError_t begin_while(cudaStream_t st, cudaGraphConditionalHandle hnd, cudaStream_t sb) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  VOS_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+  std::memset(pbuf, 0, sizeof(pbuf));
+  cudaGraphNodeParams& p = *reinterpret_cast<cudaGraphNodeParams*>(pbuf);
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hnd;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  VOS_CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  VOS_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  VOS_CUDA_TRY(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  return cudaSuccess;
+}
+
+static cudaError_t end_body(cudaStream_t sb) {
+  cudaGraph_t g;
+  return cudaStreamEndCapture(sb, &g);
+}
+
+static cudaError_t capture_graph_of(cudaStream_t st, cudaGraph_t* g) {
+  cudaStreamCaptureStatus cs;
+  VOS_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, g, nullptr, nullptr, nullptr));
+  return cs == cudaStreamCaptureStatusActive ? cudaSuccess : cudaErrorStreamCaptureInvalidated;
+}
+
+template <typename T>
+cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol,
+                          int max_iter, SolverWork* w, const RedScratch& rs, cudaStream_t st, bool use_mg,
+                          SolveStats* ss, cudaStream_t s1, cudaStream_t s2) {
+  const Box bx = op64.box;
+  const long long n = box_cells(bx);
+  if (n == 0) return cudaSuccess;
+  const bool mixed = (sizeof(T) == 4);
+  const int max_outer = mixed ? 30 : 8;
+  const bool sym = h.lev[0].op.sym != 0;
+  if (mixed) {
+    vlaunch("op_convert", (2.0 + n_offs(op64)) * n * (8.0 + sizeof(T)), k_op_convert<T>, flat_grid(n), kThreads, st,
+            op64, h.lev[0].op, n);
+  }
+  if (use_mg || !sym) build_coarse_levels<T>(h, st);
+  vlaunch("ctrl_init", 0.0, k_ctrl_init, 1, 32, st, ss, w->sc);
+  cudaGraph_t g0;
+  VOS_CUDA_TRY(capture_graph_of(st, &g0));
+  cudaGraphConditionalHandle ho, hi;
+  VOS_CUDA_TRY(cudaGraphConditionalHandleCreate(&ho, g0, 1, cudaGraphCondAssignDefault));
+  VOS_CUDA_TRY(begin_while(st, ho, s1));
+  {
+    const Op<double> oz = zview(op64);
+    const View<double> xz = zview_x(x, bx);
+    const ZCfg zr = zcfg(oz.box);
+    const double rbytes = (4.0 + n_offs(op64)) * n * 8.0 + n * sizeof(T);
+    if (op64.sym)
+      vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, true>, zr.grid, zr.block, s1, oz, b, xz, (T*)w->r,
+              w->outer, zr.zc, rs);
+    else
+      vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, false>, zr.grid, zr.block, s1, oz, b, xz, (T*)w->r,
+              w->outer, zr.zc, rs);
+    cudaGraph_t g1;
+    VOS_CUDA_TRY(capture_graph_of(s1, &g1));
+    VOS_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, g1, 0, cudaGraphCondAssignDefault));
+    if (mixed)
+      vlaunch("ctrl", 0.0, k_ctrl<true>, 1, 32, s1, ss, w->sc, (const double*)w->outer, rtol, max_outer, max_iter, ho,
+              hi);
+    else
+      vlaunch("ctrl", 0.0, k_ctrl<false>, 1, 32, s1, ss, w->sc, (const double*)w->outer, rtol, max_outer, max_iter, ho,
+              hi);
+    const KVec<T> k = kvec<T>(w, !sym);
+    VOS_CUDA_TRY(cudaMemsetAsync(k.e, 0, n * sizeof(T), s1));
+    if (sym) {
+      if (h.lev[0].op.sym) pcg_precond<T, true>(h, k, n, w, rs, s1, use_mg);
+    } else {
+      VOS_CUDA_TRY(cudaMemsetAsync(k.v, 0, n * sizeof(T), s1));
+      VOS_CUDA_TRY(cudaMemcpyAsync(k.rh, k.r, n * sizeof(T), cudaMemcpyDeviceToDevice, s1));
+    }
+    VOS_CUDA_TRY(begin_while(s1, hi, s2));
+    if (sym) {
+      for (int c = 0; c < 2; ++c) pcg_iteration<T, true>(h, k, n, w, rs, s2, use_mg);
+    } else {
+      bicg_iteration<T, false>(h, k, n, w, rs, s2);
+    }
+    vlaunch("loop_check", 0.0, k_loop_check, 1, 32, s2, (const KScal*)w->sc, hi);
+    VOS_CUDA_TRY(end_body(s2));
+    vlaunch("outer_update", (double)n * (sizeof(T) + 16.0), k_outer_update_g<T>, grid_for(bx, 0), kThreads, s1, bx, x,
+            (const T*)k.e, (const SolveStats*)ss);
+  }
+  VOS_CUDA_TRY(end_body(s1));
+  return cudaGetLastError();
+}
+
+template cudaError_t solve_capture<double>(const Op<double>&, Hier<double>&, const double*, View<double>, double, int,
+                                           SolverWork*, const RedScratch&, cudaStream_t, bool, SolveStats*,
+                                           cudaStream_t, cudaStream_t);
+template cudaError_t solve_capture<float>(const Op<double>&, Hier<float>&, const double*, View<double>, double, int,
+                                          SolverWork*, const RedScratch&, cudaStream_t, bool, SolveStats*,
+                                          cudaStream_t, cudaStream_t);
 
 template <typename T>
 SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol, int max_iter,

@@ -19,7 +19,7 @@ from . import inputs as _inputs
 __all__ = [
     "VosError", "load_library", "vos_create", "vos_step", "vos_fields", "vos_set_fields",
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
-    "vos_device_bytes", "vos_kernel_launches", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
+    "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
     "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS",
 ]
@@ -33,7 +33,7 @@ F_ALL = 255
 EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
     "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
-    "vos_kernel_launches", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
+    "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle", "vos_batch_destroy",
 ]
 
@@ -118,6 +118,8 @@ def load_library(path=None):
     lib.vos_device_bytes.restype = ctypes.c_size_t
     lib.vos_kernel_launches.argtypes = []
     lib.vos_kernel_launches.restype = ctypes.c_uint64
+    lib.vos_set_launch_mode.argtypes = [ctypes.c_int]
+    lib.vos_set_launch_mode.restype = ctypes.c_int
     lib.vos_prof_enable.argtypes = [ctypes.c_char_p]
     lib.vos_prof_enable.restype = ctypes.c_int
     lib.vos_prof_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -399,6 +401,12 @@ def vos_device_bytes(h):
 def vos_kernel_launches():
     """Kernels launched by the library so far (process-wide)."""
     return int(load_library().vos_kernel_launches())
+
+
+def vos_set_launch_mode(graphs):
+    """1: replay each step as a CUDA graph with device-side loops (default);
+    0: launch the same kernels one by one."""
+    load_library().vos_set_launch_mode(1 if graphs else 0)
 
 
 def vos_prof_enable(filt):

@@ -185,3 +185,25 @@ def test_mass_dominated_momentum(V, precision):
     prm = tight(I.make_params(es.shape, Pe=10.0, Da=1.0, L=6.0, method="ivos", Vm=2.0), precision=precision)
     assert 2 * 3 * prm["nu"] * 0.005 <= 30
     compare(V, es, prm, [0.005] * 3, 1e-9, init=c_start(es, prm))
+
+
+@pytest.mark.parametrize("precision,dt", [(0, 0.2), (1, 0.2), (1, 0.005)])
+def test_graph_mode_equals_eager(V, precision, dt):
+    """The step replayed as one CUDA graph (device-side refinement and
+    Krylov loops) gives exactly the fields of the eager launch sequence."""
+    es = I.sphere_rock_3d((14, 18, 30), seed=4, median_r=3.0, sigma=0.3, target_porosity=0.5,
+                          start_solid=0.6, band=2, margin=3.0)
+    prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=6.0, method="ivos", Vm=0.3, precision=precision)
+    init = c_start(es, prm)
+    out = {}
+    try:
+        for mode in (0, 1):
+            V.vos_set_launch_mode(mode)
+            got, stats = run_gpu(V, es, prm, [dt] * 3, init=init)
+            out[mode] = (got, stats)
+    finally:
+        V.vos_set_launch_mode(1)
+    for n in ("eps", "c", "u", "v", "w", "p", "R", "Rf"):
+        assert np.array_equal(out[0][0][n], out[1][0][n]), n
+    assert out[0][1]["iters_p"] == out[1][1]["iters_p"]
+    assert out[0][1]["iters_u"] == out[1][1]["iters_u"]
