@@ -38,14 +38,15 @@ __device__ __forceinline__ double kinv(double e, double k0) {
 }
 
 // van Leer weight w in c_f = c_U + w (c_D - c_U): w = psi(r)/2 with
-// psi(r) = (r + |r|)/(1 + |r|), r = (c_U - c_UU)/(c_D - c_U); zero without a
-// far-upwind cell or for |c_D - c_U| <= 1e-300.
+// psi(r) = (r + |r|)/(1 + |r|), r = a/b, a = c_U - c_UU, b = c_D - c_U; zero
+// without a far-upwind cell or for |b| <= 1e-300.  For r > 0 (a b > 0)
+// psi(r)/2 = r/(1 + r) = a/(a + b), and psi = 0 otherwise: one FP64
+// division instead of two (FP64 division is slow on this part).
 __device__ __forceinline__ double vl_weight(double cUU, double cU, double cD, bool has) {
-  double den = cD - cU;
-  if (!has || fabs(den) <= 1e-300) return 0.0;
-  double r = (cU - cUU) / den;
-  double ar = fabs(r);
-  return 0.5 * (r + ar) / (1.0 + ar);
+  const double b = cD - cU;
+  if (!has || fabs(b) <= 1e-300) return 0.0;
+  const double a = cU - cUU;
+  return (a * b > 0.0) ? a / (a + b) : 0.0;
 }
 
 // centred gradient component b of eps at a cell, zero-gradient ghosts
@@ -55,7 +56,7 @@ __device__ __forceinline__ double cgrad(const Phys& P, const double* eps, int b,
   int lo[3] = {i, j, k}, hi[3] = {i, j, k};
   lo[b] = c[b] > 0 ? c[b] - 1 : 0;
   hi[b] = c[b] + 1 < n ? c[b] + 1 : n - 1;
-  return (eps[cidx(P, hi[0], hi[1], hi[2])] - eps[cidx(P, lo[0], lo[1], lo[2])]) / (2.0 * P.dx);
+  return (eps[cidx(P, hi[0], hi[1], hi[2])] - eps[cidx(P, lo[0], lo[1], lo[2])]) * (0.5 / P.dx);
 }
 
 __device__ __forceinline__ bool cell_in(const Phys& P, int i, int j, int k) {
@@ -315,7 +316,8 @@ __global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ e
     int mc[3] = {i, j, k};
     mc[a] -= 1;
     const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
-    const double gn = (eps[cp] - eps[cm]) / P.dx;
+    const double idx = 1.0 / P.dx;
+    const double gn = (eps[cp] - eps[cm]) * idx;
     double g2 = gn * gn;
     for (int b = 0; b < nb; ++b) {
       if (b == a) continue;
@@ -340,7 +342,7 @@ __global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ e
       has = m + 1 <= n - 1;
     }
     const long long cUU = has ? cidx(P, uu[0], uu[1], uu[2]) : cU;
-    fd.s[fcx] = P.kc * na / P.dx;
+    fd.s[fcx] = P.kc * na * idx;
     const double cu = cold[cU], cd = cold[cD];
     fd.corr[fcx] = vl_weight(cold[cUU], cu, cd, has) * (cd - cu);
     const double eU = eps[cU], eD = eps[cD];
@@ -481,7 +483,7 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
   const double dt = *dtp;
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
-  const double idx2 = 1.0 / (P.dx * P.dx);
+  const double idx2 = 1.0 / (P.dx * P.dx), idx1 = 1.0 / P.dx;
   const int nb = (P.dim == 2) ? 2 : 3;
   const double* us[3] = {u0, u1, u2};
   const FaceData fds[3] = {f0, f1, f2};
@@ -514,7 +516,7 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
       // convective fluxes through the plus and minus faces
       int fp[3] = {i, j, k};
       fp[d] += 1;
-      adv += (conv_flux(P, d, fp[0], fp[1], fp[2], cold, us[d]) - conv_flux(P, d, i, j, k, cold, us[d])) / P.dx;
+      adv += (conv_flux(P, d, fp[0], fp[1], fp[2], cold, us[d]) - conv_flux(P, d, i, j, k, cold, us[d])) * idx1;
       if (IVOS) {
         // reactive flux F = s (c_U^{n+1} + corr): upwind value implicit,
         // the deferred van Leer correction on the right-hand side
