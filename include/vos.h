@@ -64,6 +64,15 @@ typedef enum { VOS_FP64 = 0, VOS_MIXED = 1 } vos_precision;
 #define VOS_F_R 64u
 #define VOS_F_RF 128u
 
+/* Preconditioner flags (vos_params.precond).  0 (default): the pressure,
+ * momentum and transport solves use the geometric multigrid V-cycle, and the
+ * pressure solve adds the deflation of floating pore clusters (pockets of
+ * pore cells joined to the outlet only through solid cells; see
+ * vos_floating_clusters).  VOS_PRECOND_NO_DEFLATION drops the deflation.
+ * A solver aid, not part of the paper's method: it changes the iteration
+ * count, not the converged solution. */
+#define VOS_PRECOND_NO_DEFLATION 1
+
 /* Physical and numerical parameters (non-dimensional units are fine).
  * Symbols follow Sec. 2.2-2.5: nu kinematic viscosity, D diffusion
  * coefficient (D* = D), kc reaction constant (R = kc c), k0 Kozeny-Carman
@@ -80,7 +89,7 @@ typedef struct vos_params {
   double dx, nu, D, kc, k0, Vm, zeta, rho_ratio, c_in, u_in, eps_min, lambda;
   int32_t method;    /* vos_method */
   int32_t precision; /* vos_precision */
-  int32_t precond;   /* 0: geometric multigrid */
+  int32_t precond;   /* vos_precond flags; 0: multigrid + pocket deflation */
   double p_rtol, u_rtol, c_rtol;
   int32_t max_iter;
   int32_t flow_subiters; /* 1: one transient step (only value accepted) */
@@ -198,6 +207,21 @@ void vos_batch_destroy(vos_batch* b);
 int vos_suggest_dt_noalloc(const vos_params* prm, const double* eps, const double* u,
                            const double* v, const double* w, const double* R, double cfl,
                            double deps_max, void* stream, double* dt);
+
+/* Floating pore clusters of the pressure operator for a fluid fraction
+ * field (host only, no GPU needed; a solver aid with no counterpart in the
+ * paper).  eps: host, nx*ny*nz FP64, x fastest, the fluid fraction (the
+ * solver's eps = max(1 - eps_s, eps_min)).  A face is strong when the
+ * arithmetic mean of its two cells' eps (the face porosity of the pressure
+ * operator, Sec. 2.2) is >= 0.01; a cluster is a connected set of cells
+ * joined by strong faces with at least 2 cells and no cell in the outlet
+ * column i = nx - 1 (the Dirichlet row).  label (may be NULL): host int32,
+ * nx*ny*nz, receives the cluster id (0..K-1, numbered in order of each
+ * cluster's smallest cell index) or -1.  *nclusters = K, *ncells (may be
+ * NULL) = cells in clusters.  Errors: VOS_EINVAL (NULL eps/prm/nclusters,
+ * invalid prm). */
+int vos_floating_clusters(const double* eps, const vos_params* prm, int32_t* label, int32_t* nclusters,
+                          int64_t* ncells);
 
 /* Message of the last error on h (or of the last failed vos_create when h
  * is NULL).  The string is owned by the library. */

@@ -40,7 +40,12 @@ struct vos_handle {
   vos_allocator alloc;
   bool user_alloc;
   std::vector<void*> blocks;
+  std::vector<size_t> block_bytes;
   size_t bytes;
+  // floating-cluster deflation of the pressure solve (one device block)
+  void* defl_mem;
+  size_t defl_cap;
+  Defl defl;
   // fields
   double *eps, *eps_old, *c, *p, *phi, *R, *Rf, *kr;
   double *u[3], *us[3];
@@ -92,9 +97,24 @@ void* dev_alloc(vos_handle* h, size_t bytes) {
   }
   if (p) {
     h->blocks.push_back(p);
+    h->block_bytes.push_back(bytes);
     h->bytes += bytes;
   }
   return p;
+}
+
+void dev_free(vos_handle* h, void* p) {
+  for (size_t i = 0; i < h->blocks.size(); ++i) {
+    if (h->blocks[i] != p) continue;
+    if (h->user_alloc)
+      h->alloc.free(p, h->alloc.ctx);
+    else
+      cudaFree(p);
+    h->bytes -= h->block_bytes[i];
+    h->blocks.erase(h->blocks.begin() + (long)i);
+    h->block_bytes.erase(h->block_bytes.begin() + (long)i);
+    return;
+  }
 }
 
 void free_all(vos_handle* h) {
@@ -105,6 +125,10 @@ void free_all(vos_handle* h) {
       cudaFree(p);
   }
   h->blocks.clear();
+  h->block_bytes.clear();
+  h->defl_mem = nullptr;
+  h->defl_cap = 0;
+  h->defl = Defl{0, nullptr, nullptr, nullptr};
   if (h->work) solver_work_free(h->work);
   h->work = nullptr;
   if (h->hstats) cudaFreeHost(h->hstats);
@@ -211,6 +235,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
   }
   // S3: pressure correction, projection
   launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, st);
+  launch_defl_energy(S[3].h.defl, S[3].op64, st);
   cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st);
   {
     SolveResult r =
@@ -268,6 +293,7 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
                                   h->work, h->rs, st, mom_mg, h->dsolve + a, h->gs1, h->gs2));
   }
   launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, st);
+  launch_defl_energy(S[3].h.defl, S[3].op64, st);
   VOS_CUDA_TRY(cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st));
   VOS_CUDA_TRY(solve_capture<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter,
                                 h->work, h->rs, st, true, h->dsolve + 3, h->gs1, h->gs2));
@@ -343,6 +369,54 @@ int step_graph(vos_handle* h, Sys<T>* S, double dt) {
   return status;
 }
 
+void drop_graphs(vos_handle* h) {
+  for (int i = 0; i < 2; ++i) {
+    if (h->exec[i]) cudaGraphExecDestroy(h->exec[i]);
+    h->exec[i] = nullptr;
+  }
+}
+
+// Label the floating pore clusters of the pressure operator for the host
+// fluid fraction eps and upload them; the pressure hierarchies of both
+// precisions point at the result.  Captured graphs hold the old launch
+// configuration, so they are dropped.
+int setup_deflation(vos_handle* h, const double* eps) {
+  const Phys& P = h->ph;
+  Defl D{0, nullptr, nullptr, nullptr};
+  if (!(h->prm.precond & VOS_PRECOND_NO_DEFLATION)) {
+    std::vector<int> ptr;
+    std::vector<unsigned long long> ent;
+    const int K = floating_clusters(eps, P.nx, P.ny, P.nz, kDeflTheta, ptr, ent, nullptr);
+    if (K > 0) {
+      const size_t b0 = align256((size_t)(K + 1) * sizeof(int)), b1 = align256(ent.size() * sizeof(unsigned long long));
+      const size_t need = b0 + b1 + align256((size_t)K * sizeof(double));
+      if (need > h->defl_cap) {
+        if (h->defl_mem) dev_free(h, h->defl_mem);
+        h->defl_cap = 0;
+        h->defl_mem = dev_alloc(h, need);
+        if (!h->defl_mem) return set_err(h, VOS_ENOMEM, "device allocation failed (deflation)");
+        h->defl_cap = need;
+      }
+      char* cur = (char*)h->defl_mem;
+      D.K = K;
+      D.ptr = (const int*)cur;
+      D.ent = (const unsigned long long*)(cur + b0);
+      D.Einv = (double*)(cur + b0 + b1);
+      cudaMemcpyAsync((void*)D.ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, h->st);
+      cudaMemcpyAsync((void*)D.ent, ent.data(), ent.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, h->st);
+      cudaMemsetAsync(D.Einv, 0, (size_t)K * sizeof(double), h->st);
+      // the copies read the host vectors: finish them before they go away
+      cudaError_t e = cudaStreamSynchronize(h->st);
+      if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "deflation upload: %s", cudaGetErrorString(e));
+    }
+  }
+  h->defl = D;
+  h->sd[3].h.defl = D;
+  h->sf[3].h.defl = D;
+  drop_graphs(h);
+  return VOS_OK;
+}
+
 int validate(const vos_params* p) {
   if (!p) return set_err(nullptr, VOS_EINVAL, "params is NULL");
   if (p->dim != 2 && p->dim != 3) return set_err(nullptr, VOS_EINVAL, "dim must be 2 or 3 (got %d)", p->dim);
@@ -360,7 +434,7 @@ int validate(const vos_params* p) {
   if (!std::isfinite(p->u_in)) return set_err(nullptr, VOS_EINVAL, "u_in must be finite");
   if (p->method < 0 || p->method > 2) return set_err(nullptr, VOS_EINVAL, "unknown method %d", p->method);
   if (p->precision < 0 || p->precision > 1) return set_err(nullptr, VOS_EINVAL, "unknown precision %d", p->precision);
-  if (p->precond != 0) return set_err(nullptr, VOS_EINVAL, "precond must be 0 (multigrid)");
+  if (p->precond & ~VOS_PRECOND_NO_DEFLATION) return set_err(nullptr, VOS_EINVAL, "unknown precond flags %d", p->precond);
   if (p->flow_subiters != 1) return set_err(nullptr, VOS_EINVAL, "flow_subiters must be 1");
   const double tol[] = {p->p_rtol, p->u_rtol, p->c_rtol};
   for (double v : tol)
@@ -416,6 +490,9 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
   h->gs = h->gs1 = h->gs2 = nullptr;
   h->ev_in = h->ev_out = nullptr;
   h->exec[0] = h->exec[1] = nullptr;
+  h->defl_mem = nullptr;
+  h->defl_cap = 0;
+  h->defl = Defl{0, nullptr, nullptr, nullptr};
   std::memset(&h->stats, 0, sizeof(h->stats));
   cudaGetDevice(&h->dev);
   int sms = 0;
@@ -512,6 +589,8 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     cudaMemsetAsync(h->dstats, 0, ST_COUNT * sizeof(double), st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(VOS_ECUDA, cudaGetErrorString(cudaGetLastError()));
   }
+  rc = setup_deflation(h, e0.data());
+  if (rc != VOS_OK) return fail(rc, h->err.c_str());
   h->stats.porosity = esum / (double)N;
   h->stats.lambda = (prm->method == VOS_PSI) ? prm->lambda : NAN;
   cudaError_t e = cudaGetLastError();
@@ -586,6 +665,7 @@ int vos_set_fields(vos_handle* h, uint32_t mask, const double* eps, const double
   }
   cudaError_t e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_set_fields: %s", cudaGetErrorString(e));
+  if ((mask & VOS_F_EPS) && eps) return setup_deflation(h, eps);
   return VOS_OK;
 }
 
@@ -647,6 +727,18 @@ void vos_destroy(vos_handle* h) {
 }
 
 size_t vos_device_bytes(const vos_handle* h) { return h ? h->bytes : 0; }
+
+int vos_floating_clusters(const double* eps, const vos_params* prm, int32_t* label, int32_t* nclusters,
+                          int64_t* ncells) {
+  if (!eps || !nclusters) return set_err(nullptr, VOS_EINVAL, "vos_floating_clusters: NULL argument");
+  int rc = validate(prm);
+  if (rc) return rc;
+  std::vector<int> ptr;
+  std::vector<unsigned long long> ent;
+  *nclusters = floating_clusters(eps, prm->nx, prm->ny, prm->nz, kDeflTheta, ptr, ent, label);
+  if (ncells) *ncells = (int64_t)ent.size();
+  return VOS_OK;
+}
 
 int vos_set_launch_mode(int graphs) {
   g_use_graphs = graphs != 0;

@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <utility>
+#include <vector>
 
 namespace vos {
 
@@ -263,13 +264,53 @@ struct Level {
   T *x, *t, *b;  // solution, ping-pong, right-hand side
 };
 
+// Deflation of floating pore clusters (vos_deflate.cu).  A cluster is a
+// connected set of cells joined by strong faces (face porosity >= a
+// threshold) that reaches no Dirichlet cell: in the pressure operator it is
+// tied to the rest of the domain only through solid-solid links, which are
+// eps_min / 1 times weaker, so its mean value is a near-null mode that the
+// smoother and the aggregation hierarchy hardly reduce.  The preconditioner
+// adds the exact correction of those modes, M^-1 = V + W E^-1 W^T, with W the
+// 0/1 indicator of each cluster and E = W^T A W (diagonal: distinct clusters
+// are never joined by a link of A when every cluster boundary is weak, and
+// the off-diagonal part is dropped when they are).
+// ent[q] = cell | mask << kDeflMaskShift, mask bit d set when the neighbour in
+// direction d (x-, x+, y-, y+, z-, z+) belongs to the same cluster; the
+// entries of cluster k are ent[ptr[k] .. ptr[k+1]), cells ascending.
+constexpr int kDeflMaskShift = 58;
+constexpr unsigned long long kDeflCellMask = (1ull << kDeflMaskShift) - 1ull;
+struct Defl {
+  int K;                           // number of clusters (0: no deflation)
+  const int* ptr;                  // K + 1
+  const unsigned long long* ent;   // ptr[K]
+  double* Einv;                    // K: 1 / E_kk (0 when E_kk <= 0)
+};
+
 // Multigrid hierarchy + Krylov vectors for one linear system.
 template <typename T>
 struct Hier {
   int nlev;
   Level<T> lev[16];
   MGParams mg;
+  Defl defl;  // floating-cluster deflation (pressure only)
 };
+
+// Host: label the floating clusters of the pressure operator built from the
+// fluid fraction eps (nx*ny*nz, x fastest).  Faces with 0.5 (eps_a + eps_b)
+// >= theta are strong; clusters of >= 2 cells that contain no outlet cell
+// (i = nx - 1, the Dirichlet row of the pressure operator) are kept.  Fills
+// ptr/ent (layout of Defl) and, when label is not NULL, label[c] = cluster
+// id or -1.  Returns the number of clusters.
+int floating_clusters(const double* eps, int nx, int ny, int nz, double theta, std::vector<int>& ptr,
+                      std::vector<unsigned long long>& ent, int32_t* label);
+constexpr double kDeflTheta = 0.01;
+
+// E_kk = sum over the cluster's cells of (A 1_k)_c from the FP64 symmetric
+// operator; stores 1 / E_kk in D.Einv.
+void launch_defl_energy(const Defl& D, const Op<double>& A, cudaStream_t st);
+// z += W E^-1 W^T r (skipped when the solve is done).
+template <typename T>
+void launch_defl_apply(const Defl& D, const T* r, T* z, const KScal* sc, cudaStream_t st);
 
 // Device-side record of one solve when the loops run inside a CUDA graph.
 struct SolveStats {

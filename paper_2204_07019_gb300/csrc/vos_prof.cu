@@ -16,7 +16,8 @@ namespace vos {
 std::atomic<unsigned long long> g_launch_count{0};
 unsigned long long exec_count_solver();
 unsigned long long exec_count_fields();
-unsigned long long exec_count_sum() { return exec_count_solver() + exec_count_fields(); }
+unsigned long long exec_count_deflate();
+unsigned long long exec_count_sum() { return exec_count_solver() + exec_count_fields() + exec_count_deflate(); }
 bool g_prof_any = false;
 
 namespace {

@@ -792,6 +792,7 @@ void hier_carve(Hier<T>& h, Box fine, int sym, char*& cur, const MGParams& mg, b
                 const Op<double>* op64) {
   h.nlev = count_levels(fine);
   h.mg = mg;
+  h.defl = Defl{0, nullptr, nullptr, nullptr};
   Box b = fine;
   for (int l = 0; l < h.nlev; ++l) {
     Level<T>& L = h.lev[l];
@@ -996,13 +997,15 @@ static KVec<T> kvec(SolverWork* w, bool bicg) {
   return k;
 }
 
-// z = M^-1 r and the PCG beta (multigrid V-cycle or diagonal).
+// z = M^-1 r and the PCG beta (multigrid V-cycle plus the floating-cluster
+// deflation when the hierarchy has one, or the diagonal).
 template <typename T, bool SYM>
 static void pcg_precond(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w, const RedScratch& rs,
                         cudaStream_t st, bool use_mg) {
   const int gf = flat_grid(n);
   if (use_mg) {
     vcycle<T, SYM>(h, k.r, k.z, k.scratch, w->sc, st);
+    launch_defl_apply<T>(h.defl, k.r, k.z, w->sc, st);
     vlaunch(KN("dot_rz", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_BETA>, gf, kThreads, st, n, (const T*)k.r,
             (const T*)k.z, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
   } else {

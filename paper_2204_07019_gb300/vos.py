@@ -21,7 +21,7 @@ __all__ = [
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
     "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
-    "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS",
+    "vos_floating_clusters", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -29,12 +29,14 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libv
 VOS_OK, VOS_EINVAL, VOS_ENOMEM, VOS_ECUDA, VOS_ENOCONV = 0, -1, -2, -3, -4
 F_EPS, F_C, F_U, F_V, F_W, F_P, F_R, F_RF = 1, 2, 4, 8, 16, 32, 64, 128
 F_ALL = 255
+PRECOND_NO_DEFLATION = 1
 
 EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
     "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
     "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle", "vos_batch_destroy",
+    "vos_floating_clusters",
 ]
 
 
@@ -138,6 +140,9 @@ def load_library(path=None):
     lib.vos_batch_handle.restype = ctypes.c_int
     lib.vos_batch_destroy.argtypes = [ctypes.c_void_p]
     lib.vos_batch_destroy.restype = None
+    lib.vos_floating_clusters.argtypes = [dp, ctypes.POINTER(VosParams), ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
+    lib.vos_floating_clusters.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -321,6 +326,26 @@ def vos_suggest_dt_noalloc(prm, eps, u, v, w, R, cfl=0.5, deps_max=0.005, stream
     if rc != VOS_OK:
         raise VosError(rc, lib.vos_last_error(None).decode())
     return dt.value
+
+
+def vos_floating_clusters(eps, prm):
+    """vos_floating_clusters (host only): labels of the floating pore clusters
+    that the pressure solve deflates, for a fluid-fraction array eps of the
+    grid's shape.  Returns (labels int32 array of eps's shape, -1 outside
+    clusters; number of clusters; cells in clusters)."""
+    lib = load_library()
+    ps = _params_struct(prm)
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    if e.size != int(ps.nx) * int(ps.ny) * int(ps.nz):
+        raise ValueError("eps has %d cells, the grid %d" % (e.size, int(ps.nx) * int(ps.ny) * int(ps.nz)))
+    lab = np.empty(e.shape, dtype=np.int32)
+    k = ctypes.c_int32()
+    m = ctypes.c_int64()
+    rc = lib.vos_floating_clusters(e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(ps),
+                                   ctypes.c_void_p(lab.ctypes.data), ctypes.byref(k), ctypes.byref(m))
+    if rc != VOS_OK:
+        raise VosError(rc, lib.vos_last_error(None).decode())
+    return lab, k.value, m.value
 
 
 class _Batch:
