@@ -209,8 +209,15 @@ def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
                         "traffic": None, "kernel": top, "launches": n, "avg_launch_us": kms * 1e3 / n,
                         "alg_bytes_per_launch": kbytes / n, "peak_source": src,
                         "window": "steps after the timed ones, same handle and dt, kernel launches event-timed"}
+        tiles = {}
+        for lev in (0, 1):
+            try:
+                tx, ty, zc, tuned = V.vos_tile_config(h, 3, lev)
+                tiles["p_L%d" % lev] = {"tile": [tx, ty], "zc": zc, "tuned": bool(tuned)}
+            except V.VosError:
+                pass
         return dict(ms=ms, dt=dt, iters=iters, dev_bytes=V.vos_device_bytes(h), breakdown=breakdown,
-                    roofline=roof, launches=launches)
+                    roofline=roof, launches=launches, tiles=tiles)
     finally:
         V.vos_destroy(h)
 
@@ -388,7 +395,8 @@ def main():
            "config": {"workload": args.workload, "desc": desc, "cells": N, "dt": dt,
                       "p_rtol": prm["p_rtol"], "u_rtol": prm["u_rtol"], "c_rtol": prm["c_rtol"],
                       "residual": "diagonally scaled, FP64",
-                      "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+                      "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
+                      "tiles": r["tiles"]},
            "roofline": r["roofline"], "gpu_launches": r["launches"],
            "fp64": {"value": N * world / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
                     "iters_p_mean": float(np.mean([i[1] for i in r64["iters"]]))},

@@ -233,6 +233,18 @@ void vos_destroy(vos_handle* h);
 /* Bytes of device memory held by h. */
 size_t vos_device_bytes(const vos_handle* h);
 
+/* Stencil tile of one multigrid level of one linear system of h: sys 0-2
+ * the momentum components u, v, w, 3 the pressure correction, 4 the
+ * concentration; level 0 is the fine grid.  *tx, *ty: threads of a block
+ * along x and y (tx * ty = 256); *zc: planes each block marches along z
+ * (along y for 2D grids); *tuned: 1 when the autotuner measured this shape
+ * at create (levels of >= 65,536 cells; the fastest Jacobi sweep among tile
+ * widths 32/64/128 and z chunks for about 1024-8192 blocks), 0 for the
+ * default (32 x 8, or 256 x 1 on 2D grids, about 4096 blocks).  Errors:
+ * VOS_EINVAL (NULL argument, sys or level out of range). */
+int vos_tile_config(const vos_handle* h, int32_t sys, int32_t level, int32_t* tx, int32_t* ty, int32_t* zc,
+                    int32_t* tuned);
+
 /* Diagnostics (process-wide, not tied to a handle; not thread-safe while
  * timing is on).
  * vos_kernel_launches: number of kernel executions of the step so far

@@ -553,6 +553,13 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     h->dstats = (double*)(rsb + kMaxRedValues * kMaxRedBlocks * sizeof(double) + 256);
     h->d_dt = h->dstats + ST_COUNT;
   }
+  for (int sys = 0; sys < 5; ++sys) {
+    if (prm->precision == VOS_FP64) {
+      if (box_cells(h->sd[sys].box) > 0) autotune_hier<double>(h->sd[sys].h, h->work, h->st);
+    } else {
+      if (box_cells(h->sf[sys].box) > 0) autotune_hier<float>(h->sf[sys].h, h->work, h->st);
+    }
+  }
   if (cudaMallocHost((void**)&h->hstats, ST_COUNT * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&h->hsolve, 5 * sizeof(SolveStats)) != cudaSuccess)
     return fail(VOS_ENOMEM, "pinned host allocation failed");
@@ -727,6 +734,36 @@ void vos_destroy(vos_handle* h) {
 }
 
 size_t vos_device_bytes(const vos_handle* h) { return h ? h->bytes : 0; }
+
+int vos_tile_config(const vos_handle* h, int32_t sys, int32_t level, int32_t* tx, int32_t* ty, int32_t* zc,
+                    int32_t* tuned) {
+  if (!h || !tx || !ty || !zc || !tuned) return set_err(nullptr, VOS_EINVAL, "vos_tile_config: NULL argument");
+  if (sys < 0 || sys > 4) return set_err(nullptr, VOS_EINVAL, "vos_tile_config: sys must be 0..4");
+  const bool fp64 = h->prm.precision == VOS_FP64;
+  const int nlev = fp64 ? h->sd[sys].h.nlev : h->sf[sys].h.nlev;
+  if (level < 0 || level >= nlev) return set_err(nullptr, VOS_EINVAL, "vos_tile_config: level out of range");
+  Box b = fp64 ? h->sd[sys].h.lev[level].op.box : h->sf[sys].h.lev[level].op.box;
+  const int sym = fp64 ? h->sd[sys].h.lev[level].op.sym : h->sf[sys].h.lev[level].op.sym;
+  if (b.mz == 1 && b.my > 1) b = Box{b.mx, 1, b.my};  // 2D boxes march along y
+  int x = 0, y = 0, z = 0;
+  if (tuned_config(b.mx, b.my, b.mz, fp64 ? 8 : 4, sym ? 1 : 0, &x, &y, &z)) {
+    *tuned = 1;
+  } else {
+    *tuned = 0;
+    x = (b.my == 1) ? 256 : 32;
+    y = 256 / x;
+    const long long tiles = (long long)((b.mx + x - 1) / x) * ((b.my + y - 1) / y);
+    long long c = (tiles * b.mz + 4095) / 4096;
+    if (c < 4) c = 4;
+    if (c > b.mz) c = b.mz;
+    while (tiles * ((b.mz + c - 1) / c) > kMaxRedBlocks) ++c;
+    z = (int)c;
+  }
+  *tx = x;
+  *ty = y;
+  *zc = z;
+  return VOS_OK;
+}
 
 int vos_floating_clusters(const double* eps, const vos_params* prm, int32_t* label, int32_t* nclusters,
                           int64_t* ncells) {

@@ -363,6 +363,15 @@ cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, V
                           int max_iter, SolverWork* w, const RedScratch& rs, cudaStream_t st, bool use_mg,
                           SolveStats* ss, cudaStream_t s1, cudaStream_t s2);
 
+// Tile autotuner: time the Jacobi sweep of every level of h with at least
+// 2^16 cells over a fixed set of tile shapes / z chunks and keep the fastest
+// per (box, operand type, symmetry) for all later stencil launches of the
+// process.  Uses the Krylov vectors of w as scratch; synchronises st.
+template <typename T>
+void autotune_hier(const Hier<T>& h, SolverWork* w, cudaStream_t st);
+// The tuned tile of a box, if any: returns 1 and fills (tx, ty, zc).
+int tuned_config(int mx, int my, int mz, int tsize, int sym, int* tx, int* ty, int* zc);
+
 size_t solver_work_bytes(long long max_cells);
 SolverWork* solver_work_carve(char*& cursor, long long max_cells);
 void solver_work_free(SolverWork* w);

@@ -8,6 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "vos_internal.cuh"
 
@@ -405,14 +408,15 @@ struct ZCfg {
   dim3 grid, block;
   int zc;
 };
-// Tile 32 x 8 (x, y), or 256 x 1 when the box has one row per plane; z
-// chunk so that the grid has about 4096 blocks and at most kMaxRedBlocks.
-static ZCfg zcfg(Box b) {
+// A tile of tx x (kThreads / tx) threads in (x, y) marching over zc planes,
+// zc chosen so that the grid has about target blocks (at least 4 planes per
+// block, at most kMaxRedBlocks blocks).
+static ZCfg zcfg_tile(Box b, int tx, long long target) {
   ZCfg z;
-  const int tx = (b.my == 1) ? 256 : 32, ty = kThreads / tx;
+  const int ty = kThreads / tx;
   const long long gx = (b.mx + tx - 1) / tx, gy = (b.my + ty - 1) / ty;
   const long long tiles = gx * gy;
-  long long zc = (tiles * b.mz + 4095) / 4096;
+  long long zc = (tiles * b.mz + target - 1) / target;
   if (zc < 4) zc = 4;
   if (zc > b.mz) zc = b.mz;
   while (tiles * ((b.mz + zc - 1) / zc) > kMaxRedBlocks) ++zc;
@@ -420,6 +424,41 @@ static ZCfg zcfg(Box b) {
   z.grid = dim3((unsigned)gx, (unsigned)gy, (unsigned)((b.mz + zc - 1) / zc));
   z.zc = (int)zc;
   return z;
+}
+// Default: tile 32 x 8, or 256 x 1 when the box has one row per plane, and
+// about 4096 blocks.  Kernels with grid reductions always use this shape, so
+// their summation order does not depend on tuning.
+static ZCfg zcfg(Box b) { return zcfg_tile(b, (b.my == 1) ? 256 : 32, 4096); }
+
+// ---------------------------------------------------------------------------
+// Tile autotuner for the stencil sweeps (Jacobi / matvec / residual): per box
+// shape, operand type and symmetry, the tile shape and z chunk with the
+// shortest measured Jacobi sweep among a fixed candidate set.  Each cell's
+// result is computed by the same arithmetic whatever the tile, so the choice
+// changes timings only, never values.  Results are cached per process.
+// ---------------------------------------------------------------------------
+using TuneKey = std::tuple<int, int, int, int, int>;  // mx, my, mz, sizeof(T), SYM
+static std::map<TuneKey, ZCfg> g_tuned;
+static std::mutex g_tuned_mu;
+constexpr long long kTuneMinCells = 1 << 16;  // smaller boxes are launch-latency bound
+
+static ZCfg zcfg_stencil(Box b, int tsize, bool sym) {
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  auto it = g_tuned.find(TuneKey{b.mx, b.my, b.mz, tsize, sym ? 1 : 0});
+  return it == g_tuned.end() ? zcfg(b) : it->second;
+}
+
+static int tune_candidates(Box b, ZCfg* out) {
+  int n = 0;
+  const long long targets[] = {1024, 2048, 4096, 8192};
+  if (b.my == 1) {
+    for (long long t : targets) out[n++] = zcfg_tile(b, 256, t);
+  } else {
+    const int txs[] = {32, 64, 128};
+    for (int tx : txs)
+      for (long long t : targets) out[n++] = zcfg_tile(b, tx, t);
+  }
+  return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -866,6 +905,82 @@ void build_coarse_levels(Hier<T>& h, cudaStream_t st) {
 template void build_coarse_levels<double>(Hier<double>&, cudaStream_t);
 template void build_coarse_levels<float>(Hier<float>&, cudaStream_t);
 
+template <typename T, bool SYM>
+static void tune_launch(const ZCfg& z, const Op<T>& Z, const T* b, const T* x, T* out, cudaStream_t st) {
+  k_stencil<T, SYM, SK_JAC><<<z.grid, z.block, 0, st>>>(Z, b, x, out, T(0.7), z.zc, nullptr);
+}
+
+template <typename T>
+void autotune_hier(const Hier<T>& h, SolverWork* w, cudaStream_t st) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return;
+  }
+  T* b = (T*)w->r;
+  T* x = (T*)w->z;
+  T* out = (T*)w->p;
+  for (int l = 0; l < h.nlev; ++l) {
+    const Op<T>& A = h.lev[l].op;
+    const long long n = box_cells(A.box);
+    if (n < kTuneMinCells || n > w->cap) continue;
+    const Op<T> Z = zview(A);
+    const bool sym = A.sym != 0;
+    const TuneKey key{Z.box.mx, Z.box.my, Z.box.mz, (int)sizeof(T), sym ? 1 : 0};
+    {
+      std::lock_guard<std::mutex> lk(g_tuned_mu);
+      if (g_tuned.count(key)) continue;
+    }
+    cudaMemsetAsync(b, 0, (size_t)n * sizeof(T), st);
+    cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), st);
+    ZCfg cand[16];
+    const int nc = tune_candidates(Z.box, cand);
+    const int reps = n >= (1 << 22) ? 3 : 10;
+    float best = 0.0f;
+    int bi = -1;
+    for (int c = 0; c < nc; ++c) {
+      auto run = [&] {
+        if (sym)
+          tune_launch<T, true>(cand[c], Z, b, x, out, st);
+        else
+          tune_launch<T, false>(cand[c], Z, b, x, out, st);
+      };
+      run();  // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps; ++r) run();
+      cudaEventRecord(e1, st);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (bi < 0 || ms < best) {
+        best = ms;
+        bi = c;
+      }
+    }
+    if (bi >= 0) {
+      std::lock_guard<std::mutex> lk(g_tuned_mu);
+      g_tuned[key] = cand[bi];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+template void autotune_hier<double>(const Hier<double>&, SolverWork*, cudaStream_t);
+template void autotune_hier<float>(const Hier<float>&, SolverWork*, cudaStream_t);
+
+int tuned_config(int mx, int my, int mz, int tsize, int sym, int* tx, int* ty, int* zc) {
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  auto it = g_tuned.find(TuneKey{mx, my, mz, tsize, sym});
+  if (it == g_tuned.end()) return 0;
+  *tx = (int)it->second.block.x;
+  *ty = (int)it->second.block.y;
+  *zc = it->second.zc;
+  return 1;
+}
+
 // One V(nu, nu) cycle: out = M^{-1} rhs (level-0 vectors supplied).
 // Level l owns (b, x, t).  Pre-smoothing starts with x = w b in t, every
 // Jacobi sweep writes the other buffer, the fine residual goes to the free
@@ -875,7 +990,7 @@ template <typename T, bool SYM>
 static void stencil_launch(const char* name, int kind, const Op<T>& A, const T* b, const T* x, T* out, T omega,
                            const KScal* sc, cudaStream_t st) {
   const Op<T> Z = zview(A);
-  const ZCfg z = zcfg(Z.box);
+  const ZCfg z = zcfg_stencil(Z.box, (int)sizeof(T), SYM);
   const double wT = sizeof(T), n = ncell(A);
   const double words = (kind == SK_MV ? 2.0 : 3.0) + 1.0 + n_offs(A) + (kind == SK_JAC && sizeof(T) == 8 ? 1.0 : 0.0);
   if (kind == SK_JAC)

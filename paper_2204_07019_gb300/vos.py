@@ -21,7 +21,7 @@ __all__ = [
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
     "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
-    "vos_floating_clusters", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
+    "vos_floating_clusters", "vos_tile_config", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -36,7 +36,7 @@ EXPORTED_SYMBOLS = [
     "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
     "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle", "vos_batch_destroy",
-    "vos_floating_clusters",
+    "vos_floating_clusters", "vos_tile_config",
 ]
 
 
@@ -143,6 +143,8 @@ def load_library(path=None):
     lib.vos_floating_clusters.argtypes = [dp, ctypes.POINTER(VosParams), ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
     lib.vos_floating_clusters.restype = ctypes.c_int
+    lib.vos_tile_config.argtypes = [H, ctypes.c_int32, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4
+    lib.vos_tile_config.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -326,6 +328,17 @@ def vos_suggest_dt_noalloc(prm, eps, u, v, w, R, cfl=0.5, deps_max=0.005, stream
     if rc != VOS_OK:
         raise VosError(rc, lib.vos_last_error(None).decode())
     return dt.value
+
+
+def vos_tile_config(h, sys, level):
+    """vos_tile_config: (tx, ty, zc, tuned) of the stencil tile used on one
+    multigrid level of one system (0-2 momentum, 3 pressure, 4 transport)."""
+    lib = load_library()
+    v = [ctypes.c_int32() for _ in range(4)]
+    rc = lib.vos_tile_config(h.ptr, int(sys), int(level), *[ctypes.byref(x) for x in v])
+    if rc != VOS_OK:
+        raise VosError(rc, lib.vos_last_error(None).decode())
+    return tuple(x.value for x in v)
 
 
 def vos_floating_clusters(eps, prm):

@@ -1,0 +1,64 @@
+"""Stencil tile autotuner: levels of >= 65,536 cells get a measured tile
+from the candidate set, smaller levels keep the default, and tuning never
+changes values (a grid whose fine level is tuned steps bit-identically in
+two handles, the second of which reuses the process-wide choice)."""
+import numpy as np
+import pytest
+
+from paper_2204_07019_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_07019_gb300 import build_lib, vos
+    build_lib.build()
+    vos.load_library()
+    return vos
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tuned_levels(V, precision):
+    es = I.sphere_rock_3d((48, 48, 64), seed=3, median_r=4.0, sigma=0.3, target_porosity=0.4,
+                          start_solid=0.7, band=2, margin=4.0)
+    prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=8.0, method="ivos", Vm=0.2, precision=precision)
+    h = V.vos_create(es, prm)
+    try:
+        for sys in range(5):
+            tx, ty, zc, tuned = V.vos_tile_config(h, sys, 0)
+            assert tuned == 1 and tx * ty == 256 and tx in (32, 64, 128) and zc >= 4
+            tx, ty, zc, tuned = V.vos_tile_config(h, sys, 2)  # 12 x 12 x 16 cells
+            assert tuned == 0 and (tx, ty) == (32, 8)
+        with pytest.raises(V.VosError):
+            V.vos_tile_config(h, 5, 0)
+        with pytest.raises(V.VosError):
+            V.vos_tile_config(h, 3, 40)
+        for _ in range(2):
+            assert V.vos_step(h, 0.2) == 0
+        f1 = V.vos_fields(h)
+    finally:
+        V.vos_destroy(h)
+    h = V.vos_create(es, prm)
+    try:
+        for _ in range(2):
+            assert V.vos_step(h, 0.2) == 0
+        f2 = V.vos_fields(h)
+    finally:
+        V.vos_destroy(h)
+    for n in ("eps", "c", "u", "v", "w", "p", "R", "Rf"):
+        assert np.array_equal(f1[n], f2[n]), n
+
+
+def test_2d_tiles(V):
+    es = I.disc_micromodel_2d(512, 256, seed=1, rmin=6, rmax=14, target_porosity=0.6)
+    prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=20.0, method="ivos", precision=1)
+    h = V.vos_create(es, prm)
+    try:
+        tx, ty, zc, tuned = V.vos_tile_config(h, 3, 0)
+        assert tuned == 1 and (tx, ty) == (256, 1) and zc >= 4
+    finally:
+        V.vos_destroy(h)
