@@ -42,6 +42,7 @@ extern "C" {
 #define VOS_EINVAL (-1)   /* bad size, parameter, NaN or NULL pointer        */
 #define VOS_ENOMEM (-2)   /* device allocation failed                       */
 #define VOS_ECUDA (-3)    /* a CUDA call failed (message has the CUDA text) */
+#define VOS_ETIMEOUT (-5) /* a bounded device wait gave up (tensor-core path) */
 #define VOS_ENOCONV (-4)  /* a linear solve hit max_iter; the step was still
                              applied with the last iterate                  */
 
@@ -232,6 +233,22 @@ void vos_destroy(vos_handle* h);
 
 /* Bytes of device memory held by h. */
 size_t vos_device_bytes(const vos_handle* h);
+
+/* 3x3x3 zero-padded convolution on the tensor cores (BF16 operands, FP32
+ * accumulation): the building block of the learned pressure preconditioner
+ * (no counterpart in the paper).  All pointers are device memory; the call
+ * runs on `stream` and synchronises it.
+ *   x: BF16 [nx*ny*nz][cin], voxel i + nx*(j + ny*k), channels last;
+ *   w: BF16 [cout][27][cin], tap = (dz+1)*9 + (dy+1)*3 + (dx+1);
+ *   bias: FP32 [cout] or NULL; relu: clamp the result at 0;
+ *   y_f32 (FP32) and/or y_bf16 (BF16, round to nearest even): [V][cout].
+ *   y[v][o] = bias[o] + sum over taps t and channels c of
+ *             w[o][t][c] x[v + t][c], x = 0 outside the box.
+ * cin must be a multiple of 8, cout a multiple of 16 in [16, 256].
+ * Errors: VOS_EINVAL, VOS_ECUDA, VOS_ETIMEOUT (a tensor-core wait gave up
+ * after 2 s; the output is invalid); message via vos_last_error(NULL). */
+int vos_conv3d_bf16(const uint16_t* x, int32_t nx, int32_t ny, int32_t nz, int32_t cin, const uint16_t* w,
+                    const float* bias, int32_t cout, int32_t relu, float* y_f32, uint16_t* y_bf16, void* stream);
 
 /* Stencil tile of one multigrid level of one linear system of h: sys 0-2
  * the momentum components u, v, w, 3 the pressure correction, 4 the

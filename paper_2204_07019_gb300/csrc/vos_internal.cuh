@@ -41,6 +41,15 @@ inline void vlaunch(const char* name, double bytes, void (*k)(KArgs...), dim3 gr
   if (slot >= 0) prof_after(slot, st);
 }
 
+template <typename... KArgs, typename... Args>
+inline void vlaunch_smem(const char* name, double bytes, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                         cudaStream_t st, Args&&... args) {
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);
+  int slot = g_prof_any ? prof_before(name, bytes, st) : -1;
+  k<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+  if (slot >= 0) prof_after(slot, st);
+}
+
 constexpr int kThreads = 256;             // threads per block of every grid kernel
 constexpr int kWarps = kThreads / 32;     // warps per block
 constexpr int kMaxRedBlocks = 8192;       // upper bound of blocks in reduction kernels

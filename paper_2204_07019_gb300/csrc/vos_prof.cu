@@ -17,7 +17,10 @@ std::atomic<unsigned long long> g_launch_count{0};
 unsigned long long exec_count_solver();
 unsigned long long exec_count_fields();
 unsigned long long exec_count_deflate();
-unsigned long long exec_count_sum() { return exec_count_solver() + exec_count_fields() + exec_count_deflate(); }
+unsigned long long exec_count_unet();
+unsigned long long exec_count_sum() {
+  return exec_count_solver() + exec_count_fields() + exec_count_deflate() + exec_count_unet();
+}
 bool g_prof_any = false;
 
 namespace {

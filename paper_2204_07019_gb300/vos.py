@@ -21,7 +21,7 @@ __all__ = [
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
     "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
-    "vos_floating_clusters", "vos_tile_config", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
+    "vos_floating_clusters", "vos_tile_config", "vos_conv3d_bf16", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -36,7 +36,7 @@ EXPORTED_SYMBOLS = [
     "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
     "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle", "vos_batch_destroy",
-    "vos_floating_clusters", "vos_tile_config",
+    "vos_floating_clusters", "vos_tile_config", "vos_conv3d_bf16",
 ]
 
 
@@ -145,6 +145,9 @@ def load_library(path=None):
     lib.vos_floating_clusters.restype = ctypes.c_int
     lib.vos_tile_config.argtypes = [H, ctypes.c_int32, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4
     lib.vos_tile_config.restype = ctypes.c_int
+    lib.vos_conv3d_bf16.argtypes = [ctypes.c_void_p] + [ctypes.c_int32] * 4 + [ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.vos_conv3d_bf16.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -328,6 +331,26 @@ def vos_suggest_dt_noalloc(prm, eps, u, v, w, R, cfl=0.5, deps_max=0.005, stream
     if rc != VOS_OK:
         raise VosError(rc, lib.vos_last_error(None).decode())
     return dt.value
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or an int / None)."""
+    if t is None:
+        return None
+    return int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t)
+
+
+def vos_conv3d_bf16(x, shape, cin, w, bias, cout, relu=False, y_f32=None, y_bf16=None, stream=None):
+    """vos_conv3d_bf16 on device tensors: x BF16 [V, cin] for a box of
+    ``shape`` = (nz, ny, nx), w BF16 [cout, 27, cin], bias FP32 [cout] or
+    None; writes y_f32 [V, cout] FP32 and/or y_bf16 [V, cout] BF16."""
+    lib = load_library()
+    nz, ny, nx = shape
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    rc = lib.vos_conv3d_bf16(_ptr(x), int(nx), int(ny), int(nz), int(cin), _ptr(w), _ptr(bias), int(cout),
+                             1 if relu else 0, _ptr(y_f32), _ptr(y_bf16), st)
+    if rc != VOS_OK:
+        raise VosError(rc, lib.vos_last_error(None).decode())
 
 
 def vos_tile_config(h, sys, level):
