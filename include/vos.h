@@ -250,6 +250,64 @@ size_t vos_device_bytes(const vos_handle* h);
 int vos_conv3d_bf16(const uint16_t* x, int32_t nx, int32_t ny, int32_t nz, int32_t cin, const uint16_t* w,
                     const float* bias, int32_t cout, int32_t relu, float* y_f32, uint16_t* y_bf16, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner for the pressure correction (a solver aid with no
+ * counterpart in the paper).  A 3-level U-Net on the pressure grid: inputs
+ * r / rms(r) and eps, 3x3x3 convolutions 2->16->16 | pool | 16->32->32 |
+ * pool | 32->64->64 | up, concat | 96->32->32 | up, concat | 48->16->16 |
+ * 1x1x1 head 16->1, ReLU after every 3x3x3 conv, 2x2x2 average pooling,
+ * nearest-neighbour upsampling, zero padding.  Convolutions run on the
+ * tensor cores (BF16 operands and activations, FP32 accumulation); training
+ * uses the library's own backward kernels and Adam.  Attached to a handle,
+ * the pressure solve becomes flexible CG with z = UNet(r / rms(r)) rms(r)
+ * and falls back to MG-PCG when the residual stops falling, so it always
+ * reaches p_rtol.  Boxes whose sides are not multiples of 4 are padded with
+ * zeros inside the network.
+ *
+ * Parameters travel as one FP32 host vector: for each conv in the order
+ * above, W[cout][3][3][3][cin] (taps z, y, x; channels of a concat in the
+ * order coarse, skip) then b[cout]; then the head's w[16] and b.
+ * vos_unet_num_params() gives its length.  Device vectors are FP32 (r, z,
+ * dz) or FP64 (eps), one value per cell, cell i + nx*(j + ny*k).
+ * -------------------------------------------------------------------------*/
+typedef struct vos_unet vos_unet;
+
+/* Network for an nx x ny x nz grid (each >= 4), weights zero until
+ * vos_unet_set_params; train != 0 also allocates gradient and optimiser
+ * buffers.  Work is enqueued on `stream`.  Errors: VOS_EINVAL, VOS_ENOMEM. */
+int vos_unet_create(int32_t nx, int32_t ny, int32_t nz, int32_t train, void* stream, vos_unet** out);
+int64_t vos_unet_num_params(void);
+/* Copy parameters in (resets the optimiser state) or out; gradients of the
+ * last vos_unet_backward out.  n must equal vos_unet_num_params(). */
+int vos_unet_set_params(vos_unet* net, const float* host, int64_t n);
+int vos_unet_get_params(vos_unet* net, float* host, int64_t n);
+int vos_unet_get_grads(vos_unet* net, float* host, int64_t n);
+/* z = UNet(r / rms(r), eps) (no rescaling), device pointers; synchronises.
+ * Errors: VOS_EINVAL, VOS_ECUDA, VOS_ETIMEOUT. */
+int vos_unet_forward(vos_unet* net, const float* r, const double* eps, float* z);
+/* Gradients of sum(dz * z) for the last forward (training networks only). */
+int vos_unet_backward(vos_unet* net, const float* dz);
+/* One Adam step (learning rate lr > 0) on L = |A z - r_hat|^2 / |r_hat|^2,
+ * r_hat = r / rms(r), z = UNet(r_hat, eps), A the pressure operator and eps
+ * the fluid fraction of h's last step (same grid).  *loss = L before the
+ * step.  vos_unet_eval_loss computes L only. */
+int vos_unet_train_step(vos_unet* net, vos_handle* h, const float* r, float lr, float* loss);
+int vos_unet_eval_loss(vos_unet* net, vos_handle* h, const float* r, float* loss);
+void vos_unet_destroy(vos_unet* net);
+
+/* Use net (NULL: none) as the pressure preconditioner of h.  The network is
+ * not owned by h and must outlive its use; its grid must be h's.  While a
+ * network is attached vos_step launches kernels one by one (no CUDA graph). */
+int vos_set_unet_preconditioner(vos_handle* h, vos_unet* net);
+/* Of the last step's pressure solve: flexible-CG iterations with the
+ * network, and 1 if it stalled and MG-PCG finished the solve. */
+int vos_unet_solve_stats(const vos_handle* h, int32_t* net_iters, int32_t* fallback);
+/* Training data: residuals of MG-PCG on the last step's pressure system
+ * A e = b from e = 0 after iters[i] iterations (0 gives b), as FP32 device
+ * vectors out + i * nx*ny*nz.  Needs one completed step; uses the pressure
+ * correction field as scratch (it is rebuilt by every step). */
+int vos_pressure_snapshots(vos_handle* h, int32_t count, const int32_t* iters, float* out);
+
 /* Stencil tile of one multigrid level of one linear system of h: sys 0-2
  * the momentum components u, v, w, 3 the pressure correction, 4 the
  * concentration; level 0 is the fine grid.  *tx, *ty: threads of a block

@@ -29,6 +29,10 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 
 namespace vos {
+const Op<double>* handle_pressure_op(vos_handle* h);
+const double* handle_eps(vos_handle* h);
+void unet_box(const vos_unet* net, int* px, int* py, int* pz);
+void unet_attach_eps(vos_unet* net, const double* eps);
 // Error text reported by vos_last_error(NULL) for calls without a handle.
 void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
 }  // namespace vos
@@ -65,6 +69,8 @@ struct vos_handle {
   cudaStream_t gs, gs1, gs2;
   cudaEvent_t ev_in, ev_out;
   cudaGraphExec_t exec[2];
+  vos_unet* net;       // learned pressure preconditioner (not owned)
+  int net_iters, net_fallback;
   vos_stats stats;
   std::string err;
   int dev;
@@ -241,6 +247,8 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     SolveResult r =
         solve<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter, h->work, h->rs, st,
                  true);
+    h->net_iters = r.net_iters;
+    h->net_fallback = r.fallback;
     s.iters_p = r.iters;
     s.outer_p = r.outer;
     s.res_p = r.relres;
@@ -493,6 +501,8 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
   h->defl_mem = nullptr;
   h->defl_cap = 0;
   h->defl = Defl{0, nullptr, nullptr, nullptr};
+  h->net = nullptr;
+  h->net_iters = h->net_fallback = 0;
   std::memset(&h->stats, 0, sizeof(h->stats));
   cudaGetDevice(&h->dev);
   int sms = 0;
@@ -612,7 +622,8 @@ int vos_step(vos_handle* h, double dt) {
   // CUDA-graph replay unless per-kernel timing is on (timing brackets each
   // launch with events, so it uses the eager launch sequence -- the same
   // kernels in the same order).
-  const bool graphs = g_use_graphs && !vos::g_prof_any;
+  const bool graphs = g_use_graphs && !vos::g_prof_any && !h->net;
+  h->net_iters = h->net_fallback = 0;
   if (h->prm.precision == VOS_FP64) return graphs ? step_graph<double>(h, h->sd, dt) : step_impl<double>(h, h->sd, dt);
   return graphs ? step_graph<float>(h, h->sf, dt) : step_impl<float>(h, h->sf, dt);
 }
@@ -765,6 +776,51 @@ int vos_tile_config(const vos_handle* h, int32_t sys, int32_t level, int32_t* tx
   return VOS_OK;
 }
 
+int vos_set_unet_preconditioner(vos_handle* h, vos_unet* net) {
+  if (!h) return set_err(nullptr, VOS_EINVAL, "vos_set_unet_preconditioner: handle is NULL");
+  if (net) {
+    const Box b = h->sd[3].box.mx ? h->sd[3].box : h->sf[3].box;
+    int px = 0, py = 0, pz = 0;
+    unet_box(net, &px, &py, &pz);
+    if (px != b.mx || py != b.my || pz != b.mz)
+      return set_err(h, VOS_EINVAL, "vos_set_unet_preconditioner: network box %dx%dx%d, grid %dx%dx%d", px, py, pz,
+                     b.mx, b.my, b.mz);
+    unet_attach_eps(net, h->eps);
+  }
+  h->net = net;
+  h->sd[3].h.net = net;
+  h->sf[3].h.net = net;
+  return VOS_OK;
+}
+
+int vos_unet_solve_stats(const vos_handle* h, int32_t* net_iters, int32_t* fallback) {
+  if (!h || !net_iters || !fallback) return set_err(nullptr, VOS_EINVAL, "vos_unet_solve_stats: NULL argument");
+  *net_iters = h->net_iters;
+  *fallback = h->net_fallback;
+  return VOS_OK;
+}
+
+int vos_pressure_snapshots(vos_handle* h, int32_t count, const int32_t* iters, float* out) {
+  if (!h || count < 1 || !iters || !out) return set_err(nullptr, VOS_EINVAL, "vos_pressure_snapshots: bad argument");
+  for (int i = 0; i < count; ++i)
+    if (iters[i] < 0 || iters[i] > 100000) return set_err(h, VOS_EINVAL, "vos_pressure_snapshots: iters out of range");
+  if (h->stats.step < 1) return set_err(h, VOS_EINVAL, "vos_pressure_snapshots: no step taken yet");
+  const Phys& P = h->ph;
+  cudaStream_t st = h->st;
+  cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st);
+  std::vector<int> it(iters, iters + count);
+  int rc;
+  if (h->prm.precision == VOS_FP64)
+    rc = residual_snapshots<double>(h->sd[3].op64, h->sd[3].h, h->sd[3].rhs, unknown_view(h, 3), h->work, h->rs, st,
+                                    count, it.data(), out);
+  else
+    rc = residual_snapshots<float>(h->sf[3].op64, h->sf[3].h, h->sf[3].rhs, unknown_view(h, 3), h->work, h->rs, st,
+                                   count, it.data(), out);
+  cudaError_t e = cudaGetLastError();
+  if (rc != 0 || e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_pressure_snapshots: %s", cudaGetErrorString(e));
+  return VOS_OK;
+}
+
 int vos_floating_clusters(const double* eps, const vos_params* prm, int32_t* label, int32_t* nclusters,
                           int64_t* ncells) {
   if (!eps || !nclusters) return set_err(nullptr, VOS_EINVAL, "vos_floating_clusters: NULL argument");
@@ -783,3 +839,11 @@ int vos_set_launch_mode(int graphs) {
 }
 
 }  // extern "C"
+
+namespace vos {
+const Op<double>* handle_pressure_op(vos_handle* h) {
+  if (!h) return nullptr;
+  return h->prm.precision == VOS_FP64 ? &h->sd[3].op64 : &h->sf[3].op64;
+}
+const double* handle_eps(vos_handle* h) { return h ? h->eps : nullptr; }
+}  // namespace vos

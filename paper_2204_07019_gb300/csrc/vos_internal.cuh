@@ -9,6 +9,9 @@
 #include <utility>
 #include <vector>
 
+struct vos_unet;
+struct vos_handle;
+
 namespace vos {
 
 // ---------------------------------------------------------------------------
@@ -301,7 +304,8 @@ struct Hier {
   int nlev;
   Level<T> lev[16];
   MGParams mg;
-  Defl defl;  // floating-cluster deflation (pressure only)
+  Defl defl;     // floating-cluster deflation (pressure only)
+  vos_unet* net; // learned preconditioner (pressure only; eager solves)
 };
 
 // Host: label the floating clusters of the pressure operator built from the
@@ -337,6 +341,8 @@ struct SolveResult {
   int outer;      // refinement passes
   double relres;  // final true scaled residual ||D^-1 (b - A x)|| / ||D^-1 b||
   int converged;
+  int net_iters;  // of which flexible-CG iterations with the learned preconditioner
+  int fallback;   // 1 if the learned preconditioner stagnated and MG-PCG finished
 };
 
 // Host-side driver: outer FP64 refinement around an inner solve in T.
@@ -352,6 +358,12 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
 
 template <typename T>
 void build_coarse_levels(Hier<T>& h, cudaStream_t st);
+
+// MG-PCG residual snapshots of A e = b (training data of the learned
+// preconditioner); see vos_pressure_snapshots.
+template <typename T>
+int residual_snapshots(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, SolverWork* w,
+                       const RedScratch& rs, cudaStream_t st, int count, const int* iters, float* out);
 
 // Layout helpers for allocation.
 template <typename T>
@@ -380,6 +392,15 @@ template <typename T>
 void autotune_hier(const Hier<T>& h, SolverWork* w, cudaStream_t st);
 // The tuned tile of a box, if any: returns 1 and fills (tx, ty, zc).
 int tuned_config(int mx, int my, int mz, int tsize, int sym, int* tx, int* ty, int* zc);
+
+// Learned preconditioner (vos_unet.cu): z = UNet(r / rms(r), eps) rms(r),
+// rr = |r|^2 on the device.
+template <typename T>
+void unet_precond(vos_unet* net, const T* r, T* z, const double* rr, cudaStream_t st);
+// Accessors of a handle (vos_capi.cu): the FP64 pressure operator of the
+// last step and the fluid fraction.
+const Op<double>* handle_pressure_op(vos_handle* h);
+const double* handle_eps(vos_handle* h);
 
 size_t solver_work_bytes(long long max_cells);
 SolverWork* solver_work_carve(char*& cursor, long long max_cells);

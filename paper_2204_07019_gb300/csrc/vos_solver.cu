@@ -298,7 +298,7 @@ __global__ void k_restrict_sum(Box fb, Box cb, const T* __restrict__ r, T* __res
 }
 
 // Dot products with a device-side finalisation (deterministic FP64 reduce).
-enum DotFin { DF_PCG_BETA = 0, DF_PCG_ALPHA = 1, DF_BICG_ALPHA = 2, DF_BICG_OMEGA = 3 };
+enum DotFin { DF_PCG_BETA = 0, DF_PCG_ALPHA = 1, DF_BICG_ALPHA = 2, DF_BICG_OMEGA = 3, DF_FCG_BETA = 4 };
 
 __device__ void fin_pcg_beta(KScal* sc, double rz);
 
@@ -318,6 +318,18 @@ __global__ void k_dots(long long n, const T* __restrict__ a0, const T* __restric
   if (grid_sum<NV>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
     if (FIN == DF_PCG_BETA) {
       fin_pcg_beta(sc, acc[0]);
+    } else if (FIN == DF_FCG_BETA) {
+      // Flexible CG with one stored direction (the preconditioner may vary
+      // between iterations): beta = -(z.q_prev) / (p_prev.q_prev) makes the
+      // new direction A-orthogonal to the previous one; alpha = (r.z) / (p.q)
+      // stays the exact line search because r is orthogonal to p_prev.
+      const double rz = acc[0];
+      sc->beta = (sc->iters == 0 || !(sc->pq > 0.0)) ? 0.0 : -acc[NV - 1] / sc->pq;
+      sc->rz = rz;
+      if (!isfinite(rz) || !isfinite(sc->beta) || rz == 0.0) {
+        sc->breakdown = 1;
+        sc->done = 1;
+      }
     } else if (FIN == DF_PCG_ALPHA) {
       const double pq = acc[0];
       sc->pq = pq;
@@ -832,6 +844,7 @@ void hier_carve(Hier<T>& h, Box fine, int sym, char*& cur, const MGParams& mg, b
   h.nlev = count_levels(fine);
   h.mg = mg;
   h.defl = Defl{0, nullptr, nullptr, nullptr};
+  h.net = nullptr;
   Box b = fine;
   for (int l = 0; l < h.nlev; ++l) {
     Level<T>& L = h.lev[l];
@@ -1116,9 +1129,13 @@ static KVec<T> kvec(SolverWork* w, bool bicg) {
 // deflation when the hierarchy has one, or the diagonal).
 template <typename T, bool SYM>
 static void pcg_precond(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w, const RedScratch& rs,
-                        cudaStream_t st, bool use_mg) {
+                        cudaStream_t st, bool use_mg, bool use_net = false) {
   const int gf = flat_grid(n);
-  if (use_mg) {
+  if (use_net && h.net) {
+    unet_precond<T>(h.net, k.r, k.z, &w->sc->rr, st);
+    vlaunch(KN("dot_rz_zq", true), 3.0 * n * sizeof(T), k_dots<T, 2, DF_FCG_BETA>, gf, kThreads, st, n,
+            (const T*)k.r, (const T*)k.z, (const T*)k.z, (const T*)k.q, w->sc, rs);
+  } else if (use_mg) {
     vcycle<T, SYM>(h, k.r, k.z, k.scratch, w->sc, st);
     launch_defl_apply<T>(h.defl, k.r, k.z, w->sc, st);
     vlaunch(KN("dot_rz", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_BETA>, gf, kThreads, st, n, (const T*)k.r,
@@ -1132,7 +1149,7 @@ static void pcg_precond(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w
 // One PCG iteration (kernels early-exit once the solve is done).
 template <typename T, bool SYM>
 static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w, const RedScratch& rs,
-                          cudaStream_t st, bool use_mg) {
+                          cudaStream_t st, bool use_mg, bool use_net = false) {
   const Op<T>& A = h.lev[0].op;
   const int gf = flat_grid(n);
   vlaunch(KN("pcg_p", true), 3.0 * n * sizeof(T), k_pcg_p<T>, gf, kThreads, st, n, (const T*)k.z, k.p,
@@ -1142,7 +1159,7 @@ static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork*
           (const T*)k.q, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
   vlaunch(KN("pcg_xr", true), 6.0 * n * sizeof(T), k_pcg_xr<T>, gf, kThreads, st, n, (const T*)k.p, (const T*)k.q,
           k.e, k.r, w->sc, rs);
-  pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg);
+  pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg, use_net);
 }
 
 // One BiCGStab iteration (right preconditioned, two V-cycles).
@@ -1167,23 +1184,40 @@ static void bicg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork
           (const T*)k.s, (const T*)k.t, (const T*)k.rh, k.e, k.r, w->sc, rs);
 }
 
+// With the learned preconditioner (use_net) the pass stops early, with
+// *stagnated = true, when the inner residual norm falls by less than a
+// factor 2 over two successive polls (8 iterations): the caller then
+// finishes the solve with MG-PCG.
 template <typename T, bool SYM>
 static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters, const RedScratch& rs,
-                     cudaStream_t st, bool use_mg) {
+                     cudaStream_t st, bool use_mg, bool use_net = false, bool* stagnated = nullptr) {
   const long long n = box_cells(h.lev[0].op.box);
   const KVec<T> k = kvec<T>(w, false);
   cudaMemsetAsync(k.e, 0, n * sizeof(T), st);
   vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
-  pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg);
-  const int chunk = use_mg ? 4 : 8;
+  pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg, use_net);
+  const int chunk = (use_mg || use_net) ? 4 : 8;
   int it = 0;
+  double rr_prev = -1.0;
+  int slow = 0;
+  if (stagnated) *stagnated = false;
   while (true) {
-    for (int c = 0; c < chunk; ++c) pcg_iteration<T, SYM>(h, k, n, w, rs, st, use_mg);
+    for (int c = 0; c < chunk; ++c) pcg_iteration<T, SYM>(h, k, n, w, rs, st, use_mg, use_net);
     it += chunk;
     cudaMemcpyAsync(w->sc_host, w->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     if (w->sc_host->done || it >= max_iters + chunk) break;
+    if (use_net) {
+      const double rr = w->sc_host->rr;
+      slow = (rr_prev > 0.0 && rr > 0.25 * rr_prev) ? slow + 1 : 0;
+      rr_prev = rr;
+      if (slow >= 2) {
+        if (stagnated) *stagnated = true;
+        break;
+      }
+    }
   }
+  if (use_net && stagnated && w->sc_host->breakdown) *stagnated = true;
   return w->sc_host->iters;
 }
 
@@ -1418,12 +1452,13 @@ template cudaError_t solve_capture<float>(const Op<double>&, Hier<float>&, const
 template <typename T>
 SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol, int max_iter,
                   SolverWork* w, const RedScratch& rs, cudaStream_t st, bool use_mg) {
-  SolveResult res{0, 0, 0.0, 1};
+  SolveResult res{0, 0, 0.0, 1, 0, 0};
   const Box bx = op64.box;
   const long long n = box_cells(bx);
   if (n == 0) return res;
   const bool mixed = (sizeof(T) == 4);
   const int max_outer = mixed ? 30 : 8;
+  bool use_net = use_mg && h.net != nullptr && op64.sym;
   const int g = grid_for(bx, 0);
   if (mixed) {
     vlaunch("op_convert", (2.0 + n_offs(op64)) * n * (8.0 + sizeof(T)), k_op_convert<T>, flat_grid(n), kThreads, st, op64, h.lev[0].op, n);
@@ -1472,16 +1507,67 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
     if (rin > 0.5) rin = 0.5;
     int left = max_iter - total;
     int its;
-    if (h.lev[0].op.sym)
-      its = inner_pcg<T, true>(h, w, rin, left, rs, st, use_mg);
-    else
+    if (h.lev[0].op.sym) {
+      bool stag = false;
+      its = inner_pcg<T, true>(h, w, rin, left, rs, st, use_mg, use_net, &stag);
+      if (use_net) {
+        res.net_iters += its;
+        if (stag) {  // the learned preconditioner stalled: MG-PCG from here on
+          use_net = false;
+          res.fallback = 1;
+        }
+      }
+    } else {
       its = inner_bicgstab<T, false>(h, w, rin, left, rs, st);
+    }
     total += its;
     vlaunch("outer_update", (double)n * (sizeof(T) + 16.0), k_outer_update<T>, g, kThreads, st, bx, x, (const T*)w->e);
   }
   res.iters = total;
   return res;
 }
+
+template <typename T>
+__global__ void k_to_float(long long n, const T* __restrict__ src, float* __restrict__ dst) {
+  VOS_COUNT_EXEC();
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    dst[c] = (float)src[c];
+}
+
+// Residuals of MG-PCG (multigrid + deflation, no learned preconditioner) on
+// A e = b from e = 0 after iters[i] iterations (0 = b itself), written as
+// FP32 to out + i * n.  x must be a zero vector of the box (scratch).
+template <typename T>
+int residual_snapshots(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, SolverWork* w,
+                       const RedScratch& rs, cudaStream_t st, int count, const int* iters, float* out) {
+  const Box bx = op64.box;
+  const long long n = box_cells(bx);
+  if (sizeof(T) == 4)
+    vlaunch("op_convert", 0.0, k_op_convert<T>, flat_grid(n), kThreads, st, op64, h.lev[0].op, n);
+  build_coarse_levels<T>(h, st);
+  const Op<double> oz = zview(op64);
+  const View<double> xz = zview_x(x, bx);
+  const ZCfg zr = zcfg(oz.box);
+  vlaunch("outer_residual_f64", 0.0, k_outer_residual_z<T, true>, zr.grid, zr.block, st, oz, b, xz, (T*)w->r,
+          w->outer, zr.zc, rs);
+  int maxit = 0;
+  for (int i = 0; i < count; ++i) maxit = iters[i] > maxit ? iters[i] : maxit;
+  const KVec<T> k = kvec<T>(w, false);
+  cudaMemsetAsync(k.e, 0, n * sizeof(T), st);
+  vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, 1e-30, maxit + 1);
+  pcg_precond<T, true>(h, k, n, w, rs, st, true, false);
+  for (int it = 0; it <= maxit; ++it) {
+    if (it > 0) pcg_iteration<T, true>(h, k, n, w, rs, st, true, false);
+    for (int i = 0; i < count; ++i)
+      if (iters[i] == it)
+        vlaunch("to_float", 0.0, k_to_float<T>, flat_grid(n), kThreads, st, n, (const T*)k.r, out + (long long)i * n);
+  }
+  return cudaStreamSynchronize(st) == cudaSuccess ? 0 : -1;
+}
+template int residual_snapshots<double>(const Op<double>&, Hier<double>&, const double*, View<double>, SolverWork*,
+                                        const RedScratch&, cudaStream_t, int, const int*, float*);
+template int residual_snapshots<float>(const Op<double>&, Hier<float>&, const double*, View<double>, SolverWork*,
+                                       const RedScratch&, cudaStream_t, int, const int*, float*);
 
 template SolveResult solve<double>(const Op<double>&, Hier<double>&, const double*, View<double>, double, int,
                                    SolverWork*, const RedScratch&, cudaStream_t, bool);

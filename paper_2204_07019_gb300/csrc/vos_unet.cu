@@ -17,6 +17,7 @@
 // tensor memory and is read back once, with bias and ReLU fused.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -227,6 +228,809 @@ int take_timeout_flag() {
 }  // namespace unet
 }  // namespace vos
 
+namespace vos {
+namespace unet {
+
+// ---------------------------------------------------------------------------
+// Element-wise and data-movement kernels (CUDA cores).  Flat grid-stride
+// loops; every reduction is a fixed-order block / grid sum.
+// ---------------------------------------------------------------------------
+struct Dims {
+  int nx, ny, nz;  // padded network box (multiples of 4)
+  int px, py, pz;  // physical box (the pressure unknowns)
+};
+
+__device__ __forceinline__ long long phys_index(const Dims& d, long long v, bool& in) {
+  const long long plane = (long long)d.nx * d.ny;
+  const int k = (int)(v / plane);
+  const int j = (int)((v - (long long)k * plane) / d.nx);
+  const int i = (int)(v - (long long)k * plane - (long long)j * d.nx);
+  in = i < d.px && j < d.py && k < d.pz;
+  return i + (long long)d.px * (j + (long long)d.py * k);
+}
+
+#define UNET_LOOP(v, n) for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < (n); v += (long long)gridDim.x * blockDim.x)
+
+static int ugrid(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  const long long cap = (long long)g_num_sms * 16;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// inv_rms and rms of a vector from its squared norm (FP64 on one thread).
+__global__ void k_rms(const double* rr, double n, float* out) {
+  VOS_COUNT_EXEC();
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double ms = *rr / n;
+    out[0] = ms > 0.0 ? (float)(1.0 / sqrt(ms)) : 0.0f;
+    out[1] = ms > 0.0 ? (float)sqrt(ms) : 0.0f;
+  }
+}
+
+// x0[v] = (r_c * inv_rms, eps_c, 0 x 6) in BF16; zeros in the padding.
+template <typename T>
+__global__ void k_pack(Dims d, const T* __restrict__ r, const double* __restrict__ eps, const float* scal,
+                       __nv_bfloat16* __restrict__ x0) {
+  VOS_COUNT_EXEC();
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  const float inv = scal[0];
+  UNET_LOOP(v, n) {
+    bool in;
+    const long long c = phys_index(d, v, in);
+    const float a = in ? (float)r[c] * inv : 0.0f;
+    const float e = in ? (float)eps[c] : 0.0f;
+    __align__(16) __nv_bfloat162 h[4];
+    h[0] = __floats2bfloat162_rn(a, e);
+    h[1] = h[2] = h[3] = __floats2bfloat162_rn(0.0f, 0.0f);
+    *(uint4*)(x0 + v * 8) = *(const uint4*)h;
+  }
+}
+
+// 2x2x2 average pooling, C a multiple of 8; coarse box (cx, cy, cz).
+__global__ void k_pool(int cx, int cy, int cz, int C, const __nv_bfloat16* __restrict__ f,
+                       __nv_bfloat16* __restrict__ c) {
+  VOS_COUNT_EXEC();
+  const int cg = C >> 3;
+  const long long n = (long long)cx * cy * cz * cg;
+  const int fx = 2 * cx, fy = 2 * cy;
+  UNET_LOOP(t, n) {
+    const int g = (int)(t % cg);
+    const long long q = t / cg;
+    const int i = (int)(q % cx), j = (int)((q / cx) % cy), k = (int)(q / ((long long)cx * cy));
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const long long fv = (2 * i + dx) + (long long)fx * ((2 * j + dy) + (long long)fy * (2 * k + dz));
+          const uint4 u = *(const uint4*)(f + fv * C + g * 8);
+          const __nv_bfloat162* h = (const __nv_bfloat162*)&u;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 p = __bfloat1622float2(h[e]);
+            acc[2 * e] += p.x;
+            acc[2 * e + 1] += p.y;
+          }
+        }
+    __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o[e] = __floats2bfloat162_rn(acc[2 * e] * 0.125f, acc[2 * e + 1] * 0.125f);
+    *(uint4*)(c + q * C + g * 8) = *(const uint4*)o;
+  }
+}
+
+// out[v] = [coarse[parent(v)] (Cu channels), skip[v] (Cs channels)].
+__global__ void k_up_concat(int fx, int fy, int fz, int Cu, int Cs, const __nv_bfloat16* __restrict__ coarse,
+                            const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ out) {
+  VOS_COUNT_EXEC();
+  const int C = Cu + Cs, cg = C >> 3, ug = Cu >> 3;
+  const long long n = (long long)fx * fy * fz * cg;
+  const int cx = fx / 2, cy = fy / 2;
+  UNET_LOOP(t, n) {
+    const int g = (int)(t % cg);
+    const long long v = t / cg;
+    uint4 u;
+    if (g < ug) {
+      const int i = (int)(v % fx), j = (int)((v / fx) % fy), k = (int)(v / ((long long)fx * fy));
+      const long long p = (i / 2) + (long long)cx * ((j / 2) + (long long)cy * (k / 2));
+      u = *(const uint4*)(coarse + p * Cu + g * 8);
+    } else {
+      u = *(const uint4*)(skip + v * Cs + (g - ug) * 8);
+    }
+    *(uint4*)(out + v * C + g * 8) = u;
+  }
+}
+
+// z_c = (sum_k w_k d1[v][k] + b) * scale for the physical voxels.
+template <typename T>
+__global__ void k_head(Dims d, const __nv_bfloat16* __restrict__ d1, const float* __restrict__ head,
+                       const float* scal, int use_scale, T* __restrict__ z) {
+  VOS_COUNT_EXEC();
+  const long long n = (long long)d.px * d.py * d.pz;
+  const float sc = use_scale ? scal[1] : 1.0f;
+  UNET_LOOP(c, n) {
+    const int i = (int)(c % d.px), j = (int)((c / d.px) % d.py), k = (int)(c / ((long long)d.px * d.py));
+    const long long v = i + (long long)d.nx * (j + (long long)d.ny * k);
+    const uint4* src = (const uint4*)(d1 + v * 16);
+    float acc = head[16];
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const uint4 u = src[h2];
+      const __nv_bfloat162* h = (const __nv_bfloat162*)&u;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 p = __bfloat1622float2(h[e]);
+        acc += head[h2 * 8 + 2 * e] * p.x + head[h2 * 8 + 2 * e + 1] * p.y;
+      }
+    }
+    z[c] = (T)(acc * sc);
+  }
+}
+
+// Head backward: g_d1[v][k] = dz_v w_k; grid sums of dz_v d1[v][k] and dz_v.
+__global__ void __launch_bounds__(kThreads) k_head_bwd(Dims d, const float* __restrict__ dz,
+                                                      const __nv_bfloat16* __restrict__ d1,
+                                                      const float* __restrict__ head, float* __restrict__ g,
+                                                      float* __restrict__ ghead, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  double acc[17];
+#pragma unroll
+  for (int q = 0; q < 17; ++q) acc[q] = 0.0;
+  UNET_LOOP(v, n) {
+    bool in;
+    const long long c = phys_index(d, v, in);
+    const float dzv = in ? dz[c] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float x = __bfloat162float(d1[v * 16 + k]);
+      g[v * 16 + k] = dzv * head[k];
+      acc[k] += (double)(dzv * x);
+    }
+    acc[16] += (double)dzv;
+  }
+  if (grid_sum<17>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+#pragma unroll
+    for (int q = 0; q < 17; ++q) ghead[q] = (float)acc[q];
+  }
+}
+
+// g_pre = g * (out > 0) (FP32) and its BF16 copy.
+__global__ void k_relu_bwd(long long n, const float* __restrict__ g, const __nv_bfloat16* __restrict__ out,
+                           float* __restrict__ gp, __nv_bfloat16* __restrict__ gp16) {
+  VOS_COUNT_EXEC();
+  UNET_LOOP(t, n) {
+    const float y = __bfloat162float(out[t]);
+    const float v = y > 0.0f ? g[t] : 0.0f;
+    gp[t] = v;
+    gp16[t] = __float2bfloat16_rn(v);
+  }
+}
+
+// Weight gradient of one tap for a chunk of voxels (CUDA cores, FP32):
+// partial[chunk][tap][o][i] = sum over the chunk's voxels v of
+// g[v][o] x[v + t][i].  A thread owns a 4 x 4 (o, i) tile; when the layer has
+// fewer than 256 tiles, R replicas of the tile set split the voxels and are
+// added in a fixed order at the end.
+constexpr int kDwSub = 32;
+__global__ void __launch_bounds__(kThreads) k_dw(int nx, int ny, int nz, int Cin, int Cout, long long chunk,
+                                                const __nv_bfloat16* __restrict__ x, const float* __restrict__ g,
+                                                float* __restrict__ partial) {
+  VOS_COUNT_EXEC();
+  __shared__ float xs[kDwSub][96];
+  __shared__ float gs[kDwSub][64];
+  __shared__ float red[128 * 16];  // replicas > 1 only when tiles <= 128
+  const int tap = blockIdx.y;
+  const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dzz = tap / 9 - 1;
+  const long long V = (long long)nx * ny * nz;
+  const long long v0 = (long long)blockIdx.x * chunk;
+  const long long v1 = min(V, v0 + chunk);
+  const int to = Cout / 4, ti = Cin / 4, tiles = to * ti;
+  const int R = kThreads / tiles;
+  const int t = threadIdx.x;
+  const int tile = t % tiles, rep = t / tiles;
+  const bool active = rep < R;
+  const int o0 = (tile / ti) * 4, i0 = (tile % ti) * 4;
+  float acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+  for (long long s0 = v0; s0 < v1; s0 += kDwSub) {
+    const int ns = (int)min((long long)kDwSub, v1 - s0);
+    for (int e = t; e < kDwSub * Cin; e += kThreads) {
+      const int vv = e / Cin, ci = e % Cin;
+      float val = 0.0f;
+      if (vv < ns) {
+        const long long v = s0 + vv;
+        const int k = (int)(v / ((long long)nx * ny)), j = (int)((v / nx) % ny), i = (int)(v % nx);
+        const int ii = i + dx, jj = j + dy, kk = k + dzz;
+        if (ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz)
+          val = __bfloat162float(x[(ii + (long long)nx * (jj + (long long)ny * kk)) * Cin + ci]);
+      }
+      xs[vv][ci] = val;
+    }
+    for (int e = t; e < kDwSub * Cout; e += kThreads) {
+      const int vv = e / Cout, co = e % Cout;
+      gs[vv][co] = (vv < ns) ? g[(s0 + vv) * Cout + co] : 0.0f;
+    }
+    __syncthreads();
+    if (active) {
+      for (int vv = rep; vv < kDwSub; vv += R) {
+        float a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          a[q] = gs[vv][o0 + q];
+          b[q] = xs[vv][i0 + q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p * 4 + q] += a[p] * b[q];
+      }
+    }
+    __syncthreads();
+  }
+  float* dst = partial + ((long long)blockIdx.x * 27 + tap) * Cout * Cin;
+  if (R == 1) {
+    if (active)
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[(o0 + p) * Cin + i0 + q] = acc[p * 4 + q];
+    return;
+  }
+  // replicas: tiles * 16 * R <= 256 * 16 floats; sum in replica order
+  for (int r = 1; r < R; ++r) {
+    if (active && rep == r)
+#pragma unroll
+      for (int q = 0; q < 16; ++q) red[tile * 16 + q] = acc[q];
+    __syncthreads();
+    if (active && rep == 0)
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] += red[tile * 16 + q];
+    __syncthreads();
+  }
+  if (active && rep == 0)
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[(o0 + p) * Cin + i0 + q] = acc[p * 4 + q];
+}
+
+// dW[o][tap][i] = sum over chunks of partial[chunk][tap][o][i] (fixed order).
+__global__ void k_dw_reduce(int nchunk, int Cin, int Cout, const float* __restrict__ partial, float* __restrict__ dW) {
+  VOS_COUNT_EXEC();
+  const long long n = 27LL * Cout * Cin;
+  UNET_LOOP(e, n) {
+    const int i = (int)(e % Cin), o = (int)((e / Cin) % Cout), tap = (int)(e / ((long long)Cin * Cout));
+    float s = 0.0f;
+    for (int c = 0; c < nchunk; ++c) s += partial[((long long)c * 27 + tap) * Cout * Cin + (long long)o * Cin + i];
+    dW[((long long)o * 27 + tap) * Cin + i] = s;
+  }
+}
+
+// db[o] = sum_v g[v][o]: per-block partial sums, then a fixed-order total.
+__global__ void __launch_bounds__(kThreads) k_db(long long V, int C, const float* __restrict__ g,
+                                                float* __restrict__ partial) {
+  VOS_COUNT_EXEC();
+  __shared__ float sh[kThreads];
+  const int per = kThreads / C;  // voxels handled side by side (C divides 256)
+  const int c = threadIdx.x % C, lane = threadIdx.x / C;
+  float acc = 0.0f;
+  for (long long v = (long long)blockIdx.x * per + lane; v < V; v += (long long)gridDim.x * per)
+    acc += g[v * C + c];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < C) {
+    float s = 0.0f;
+    for (int l = 0; l < per; ++l) s += sh[l * C + threadIdx.x];
+    partial[(long long)blockIdx.x * C + threadIdx.x] = s;
+  }
+}
+__global__ void k_db_reduce(int nb, int C, const float* __restrict__ partial, float* __restrict__ db) {
+  VOS_COUNT_EXEC();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  float s = 0.0f;
+  for (int b = 0; b < nb; ++b) s += partial[(long long)b * C + c];
+  db[c] = s;
+}
+
+// gf[v][c] += gc[parent(v)][c] / 8   (pool backward, added into gf)
+__global__ void k_pool_bwd_add(int fx, int fy, int fz, int C, const float* __restrict__ gc, float* __restrict__ gf) {
+  VOS_COUNT_EXEC();
+  const long long n = (long long)fx * fy * fz * C;
+  const int cx = fx / 2, cy = fy / 2;
+  UNET_LOOP(t, n) {
+    const int c = (int)(t % C);
+    const long long v = t / C;
+    const int i = (int)(v % fx), j = (int)((v / fx) % fy), k = (int)(v / ((long long)fx * fy));
+    const long long p = (i / 2) + (long long)cx * ((j / 2) + (long long)cy * (k / 2));
+    gf[t] += 0.125f * gc[p * C + c];
+  }
+}
+
+// Up-concat backward: gcoarse[p][c] = sum over the 8 children of
+// gcat[child][c] (c < Cu); gskip[v][c] = gcat[v][Cu + c].
+__global__ void k_up_bwd(int cx, int cy, int cz, int Cu, int Ctot, const float* __restrict__ gcat,
+                         float* __restrict__ gcoarse) {
+  VOS_COUNT_EXEC();
+  const long long n = (long long)cx * cy * cz * Cu;
+  const int fx = 2 * cx, fy = 2 * cy;
+  UNET_LOOP(t, n) {
+    const int c = (int)(t % Cu);
+    const long long p = t / Cu;
+    const int i = (int)(p % cx), j = (int)((p / cx) % cy), k = (int)(p / ((long long)cx * cy));
+    float s = 0.0f;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const long long fv = (2 * i + dx) + (long long)fx * ((2 * j + dy) + (long long)fy * (2 * k + dz));
+          s += gcat[fv * Ctot + c];
+        }
+    gcoarse[t] = s;
+  }
+}
+__global__ void k_split_skip(long long V, int Cu, int Cs, const float* __restrict__ gcat, float* __restrict__ gskip) {
+  VOS_COUNT_EXEC();
+  const long long n = V * Cs;
+  UNET_LOOP(t, n) {
+    const long long v = t / Cs;
+    gskip[t] = gcat[v * (Cu + Cs) + Cu + (t % Cs)];
+  }
+}
+
+// FP32 master weights W [o][tap][i] -> BF16 W16 (same layout) and the
+// flipped transpose WT16 [i][26 - tap][o] used by the data gradient.
+__global__ void k_prep_w(int Cout, int Cin, const float* __restrict__ W, __nv_bfloat16* __restrict__ W16,
+                         __nv_bfloat16* __restrict__ WT16) {
+  VOS_COUNT_EXEC();
+  const long long n = 27LL * Cout * Cin;
+  UNET_LOOP(e, n) {
+    const int i = (int)(e % Cin), tap = (int)((e / Cin) % 27), o = (int)(e / (27LL * Cin));
+    const __nv_bfloat16 h = __float2bfloat16_rn(W[e]);
+    W16[e] = h;
+    if (WT16) WT16[((long long)i * 27 + (26 - tap)) * Cout + o] = h;
+  }
+}
+
+// Adam (bias-corrected moments) on a flat parameter range.
+__global__ void k_adam(long long n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+  VOS_COUNT_EXEC();
+  UNET_LOOP(e, n) {
+    const float gi = g[e];
+    const float mi = b1 * m[e] + (1.0f - b1) * gi;
+    const float vi = b2 * v[e] + (1.0f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    p[e] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+// out = A z for the symmetric FP64 pressure operator (FP64 sums, FP32 out).
+__global__ void k_apply_op(Op<double> A, const float* __restrict__ z, float* __restrict__ out) {
+  VOS_COUNT_EXEC();
+  const Box b = A.box;
+  const long long n = box_cells(b), sy = b.mx, sz = (long long)b.mx * b.my;
+  UNET_LOOP(c, n) {
+    const int i = (int)(c % b.mx), j = (int)((c / b.mx) % b.my), k = (int)(c / sz);
+    double y = A.diag[c] * (double)z[c];
+    if (i + 1 < b.mx) y += A.xp[c] * (double)z[c + 1];
+    if (i > 0) y += A.xp[c - 1] * (double)z[c - 1];
+    if (j + 1 < b.my) y += A.yp[c] * (double)z[c + sy];
+    if (j > 0) y += A.yp[c - sy] * (double)z[c - sy];
+    if (b.mz > 1) {
+      if (k + 1 < b.mz) y += A.zp[c] * (double)z[c + sz];
+      if (k > 0) y += A.zp[c - sz] * (double)z[c - sz];
+    }
+    out[c] = (float)y;
+  }
+}
+
+// res = A z - r inv_rms; sums of res^2 and (r inv_rms)^2.
+__global__ void __launch_bounds__(kThreads) k_loss_res(long long n, const float* __restrict__ Az,
+                                                      const float* __restrict__ r, const float* scal,
+                                                      float* __restrict__ res, double* out, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  const float inv = scal[0];
+  double acc[2] = {0.0, 0.0};
+  UNET_LOOP(c, n) {
+    const float rh = r[c] * inv;
+    const float e = Az[c] - rh;
+    res[c] = e;
+    acc[0] += (double)e * e;
+    acc[1] += (double)rh * rh;
+  }
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    out[0] = acc[0];
+    out[1] = acc[1];
+  }
+}
+// dz = (2 / |r_hat|^2) A res  (A res already in dz)
+__global__ void k_scale_dz(long long n, const double* sums, float* __restrict__ dz) {
+  VOS_COUNT_EXEC();
+  const float f = sums[1] > 0.0 ? (float)(2.0 / sums[1]) : 0.0f;
+  UNET_LOOP(c, n) dz[c] *= f;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sumsq(long long n, const float* __restrict__ r, double* out,
+                                                   RedScratch rs) {
+  VOS_COUNT_EXEC();
+  double acc[1] = {0.0};
+  UNET_LOOP(c, n) acc[0] += (double)r[c] * r[c];
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) out[0] = acc[0];
+}
+
+}  // namespace unet
+}  // namespace vos
+
+// ---------------------------------------------------------------------------
+// The network object: weights, Adam state, activations and gradients for
+// one box.
+// ---------------------------------------------------------------------------
+namespace vos {
+namespace unet {
+
+struct LayerSpec {
+  int cin, cout, lev;
+};
+// enc1a enc1b enc2a enc2b enc3a enc3b dec2a dec2b dec1a dec1b
+constexpr LayerSpec kSpec[10] = {{2, 16, 0},  {16, 16, 0}, {16, 32, 1}, {32, 32, 1}, {32, 64, 2},
+                                 {64, 64, 2}, {96, 32, 1}, {32, 32, 1}, {48, 16, 0}, {16, 16, 0}};
+enum { ENC1A, ENC1B, ENC2A, ENC2B, ENC3A, ENC3B, DEC2A, DEC2B, DEC1A, DEC1B };
+
+struct Layer {
+  int cin, cing, cout, lev;
+  float *W, *b, *gW, *gb, *mW, *vW, *mb, *vb;  // W: [cout][27][cing]
+  __nv_bfloat16 *W16, *WT16, *out;             // out: [V_lev][cout] after ReLU
+};
+
+long long num_params() {
+  long long n = 17;
+  for (const auto& l : kSpec) n += (long long)l.cout * 27 * l.cin + l.cout;
+  return n;
+}
+
+}  // namespace unet
+}  // namespace vos
+
+struct vos_unet {
+  vos::unet::Dims d;
+  int lx[3], ly[3], lz[3];
+  long long V[3];
+  vos::unet::Layer L[10];
+  float *head, *ghead, *mhead, *vhead;  // 17 = w[16], b
+  __nv_bfloat16 *x0, *p1, *p2, *cat2, *cat1;
+  float* scal;    // [inv_rms, rms]
+  double* dscal;  // [|r|^2, |res|^2, |r_hat|^2]
+  float* z;       // [physical cells] network output of the last forward
+  vos::RedScratch rs;
+  bool train;
+  float *gA, *gB, *ge1, *ge2, *gpre;
+  __nv_bfloat16* gpre16;
+  float *part_dw, *part_db;
+  long long chunk[3];
+  int nchunk[3], ndb;
+  float *az, *res, *dz;
+  const double* eps;  // fluid fraction of the attached handle (device)
+  int adam_t;
+  cudaStream_t st;
+  std::vector<void*> blocks;
+};
+
+namespace vos {
+namespace unet {
+
+static void* ualloc(vos_unet* u, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, (bytes + 255) & ~(size_t)255) != cudaSuccess) return nullptr;
+  u->blocks.push_back(p);
+  return p;
+}
+
+static void destroy_net(vos_unet* u) {
+  if (!u) return;
+  cudaStreamSynchronize(u->st);
+  for (void* p : u->blocks) cudaFree(p);
+  delete u;
+}
+
+static ConvArgs conv_args(const vos_unet* u, int lev, const __nv_bfloat16* x, int cin, const __nv_bfloat16* w,
+                          const float* bias, int cout, int relu, float* yf, __nv_bfloat16* yb) {
+  ConvArgs a;
+  a.x = x;
+  a.w = w;
+  a.bias = bias;
+  a.yf = yf;
+  a.yb = yb;
+  a.nx = u->lx[lev];
+  a.ny = u->ly[lev];
+  a.nz = u->lz[lev];
+  a.cin = cin;
+  a.cout = cout;
+  a.relu = relu;
+  a.V = u->V[lev];
+  return a;
+}
+
+static void prep_weights(vos_unet* u) {
+  for (auto& l : u->L) {
+    const long long n = 27LL * l.cout * l.cing;
+    vlaunch("unet_prep_w", 0.0, k_prep_w, ugrid(n), kThreads, u->st, l.cout, l.cing, (const float*)l.W, l.W16,
+            l.WT16);
+  }
+}
+
+// Forward pass: x0 from (r, eps), ten convs, head -> z (T, physical cells).
+// rr: device |r|^2; use_scale multiplies the output by rms(r).
+template <typename T>
+static cudaError_t forward(vos_unet* u, const T* r, const double* eps, const double* rr, int use_scale, T* zout) {
+  cudaStream_t st = u->st;
+  const Dims d = u->d;
+  const double nphys = (double)d.px * d.py * d.pz;
+  vlaunch("unet_rms", 0.0, k_rms, 1, 32, st, rr, nphys, u->scal);
+  vlaunch("unet_pack", 0.0, k_pack<T>, ugrid(u->V[0]), kThreads, st, d, r, eps, (const float*)u->scal, u->x0);
+  Layer* L = u->L;
+  auto conv = [&](int li, const __nv_bfloat16* x) -> cudaError_t {
+    Layer& l = L[li];
+    return conv3d(conv_args(u, l.lev, x, l.cing, l.W16, l.b, l.cout, 1, nullptr, l.out), st);
+  };
+  VOS_CUDA_TRY(conv(ENC1A, u->x0));
+  VOS_CUDA_TRY(conv(ENC1B, L[ENC1A].out));
+  vlaunch("unet_pool", 0.0, k_pool, ugrid(u->V[1] * 2), kThreads, st, u->lx[1], u->ly[1], u->lz[1], 16,
+          (const __nv_bfloat16*)L[ENC1B].out, u->p1);
+  VOS_CUDA_TRY(conv(ENC2A, u->p1));
+  VOS_CUDA_TRY(conv(ENC2B, L[ENC2A].out));
+  vlaunch("unet_pool", 0.0, k_pool, ugrid(u->V[2] * 4), kThreads, st, u->lx[2], u->ly[2], u->lz[2], 32,
+          (const __nv_bfloat16*)L[ENC2B].out, u->p2);
+  VOS_CUDA_TRY(conv(ENC3A, u->p2));
+  VOS_CUDA_TRY(conv(ENC3B, L[ENC3A].out));
+  vlaunch("unet_up", 0.0, k_up_concat, ugrid(u->V[1] * 12), kThreads, st, u->lx[1], u->ly[1], u->lz[1], 64, 32,
+          (const __nv_bfloat16*)L[ENC3B].out, (const __nv_bfloat16*)L[ENC2B].out, u->cat2);
+  VOS_CUDA_TRY(conv(DEC2A, u->cat2));
+  VOS_CUDA_TRY(conv(DEC2B, L[DEC2A].out));
+  vlaunch("unet_up", 0.0, k_up_concat, ugrid(u->V[0] * 6), kThreads, st, u->lx[0], u->ly[0], u->lz[0], 32, 16,
+          (const __nv_bfloat16*)L[DEC2B].out, (const __nv_bfloat16*)L[ENC1B].out, u->cat1);
+  VOS_CUDA_TRY(conv(DEC1A, u->cat1));
+  VOS_CUDA_TRY(conv(DEC1B, L[DEC1A].out));
+  vlaunch("unet_head", 0.0, k_head<T>, ugrid((long long)nphys), kThreads, st, d, (const __nv_bfloat16*)L[DEC1B].out,
+          (const float*)u->head, (const float*)u->scal, use_scale, zout);
+  return cudaGetLastError();
+}
+
+// Backward of one conv layer: g_out (FP32 [V][cout]) -> gW, gb and, when
+// g_in is given, the data gradient g_in (FP32 [V][cing]).
+static cudaError_t layer_backward(vos_unet* u, int li, const __nv_bfloat16* xin, const float* g_out, float* g_in) {
+  cudaStream_t st = u->st;
+  Layer& l = u->L[li];
+  const long long V = u->V[l.lev];
+  vlaunch("unet_relu_bwd", 0.0, k_relu_bwd, ugrid(V * l.cout), kThreads, st, V * l.cout, g_out,
+          (const __nv_bfloat16*)l.out, u->gpre, u->gpre16);
+  const int nch = u->nchunk[l.lev];
+  vlaunch("unet_dw", 0.0, k_dw, dim3((unsigned)nch, 27), kThreads, st, u->lx[l.lev], u->ly[l.lev], u->lz[l.lev],
+          l.cing, l.cout, u->chunk[l.lev], xin, (const float*)u->gpre, u->part_dw);
+  vlaunch("unet_dw_reduce", 0.0, k_dw_reduce, ugrid(27LL * l.cout * l.cing), kThreads, st, nch, l.cing, l.cout,
+          (const float*)u->part_dw, l.gW);
+  vlaunch("unet_db", 0.0, k_db, u->ndb, kThreads, st, V, l.cout, (const float*)u->gpre, u->part_db);
+  vlaunch("unet_db_reduce", 0.0, k_db_reduce, 1, 64, st, u->ndb, l.cout, (const float*)u->part_db, l.gb);
+  if (g_in) VOS_CUDA_TRY(conv3d(conv_args(u, l.lev, u->gpre16, l.cout, l.WT16, nullptr, l.cing, 0, g_in, nullptr), st));
+  return cudaGetLastError();
+}
+
+// Gradients of sum(dz * z) for the last forward (dz: FP32 physical cells).
+static cudaError_t backward(vos_unet* u, const float* dz) {
+  cudaStream_t st = u->st;
+  Layer* L = u->L;
+  vlaunch("unet_head_bwd", 0.0, k_head_bwd, ugrid(u->V[0]), kThreads, st, u->d, dz,
+          (const __nv_bfloat16*)L[DEC1B].out, (const float*)u->head, u->gA, u->ghead, u->rs);
+  VOS_CUDA_TRY(layer_backward(u, DEC1B, L[DEC1A].out, u->gA, u->gB));
+  VOS_CUDA_TRY(layer_backward(u, DEC1A, u->cat1, u->gB, u->gA));  // gA = g_cat1 [V0][48]
+  vlaunch("unet_up_bwd", 0.0, k_up_bwd, ugrid(u->V[1] * 32), kThreads, st, u->lx[1], u->ly[1], u->lz[1], 32, 48,
+          (const float*)u->gA, u->gB);
+  vlaunch("unet_split", 0.0, k_split_skip, ugrid(u->V[0] * 16), kThreads, st, u->V[0], 32, 16, (const float*)u->gA,
+          u->ge1);
+  VOS_CUDA_TRY(layer_backward(u, DEC2B, L[DEC2A].out, u->gB, u->gA));
+  VOS_CUDA_TRY(layer_backward(u, DEC2A, u->cat2, u->gA, u->gB));  // gB = g_cat2 [V1][96]
+  vlaunch("unet_up_bwd", 0.0, k_up_bwd, ugrid(u->V[2] * 64), kThreads, st, u->lx[2], u->ly[2], u->lz[2], 64, 96,
+          (const float*)u->gB, u->gA);
+  vlaunch("unet_split", 0.0, k_split_skip, ugrid(u->V[1] * 32), kThreads, st, u->V[1], 64, 32, (const float*)u->gB,
+          u->ge2);
+  VOS_CUDA_TRY(layer_backward(u, ENC3B, L[ENC3A].out, u->gA, u->gB));
+  VOS_CUDA_TRY(layer_backward(u, ENC3A, u->p2, u->gB, u->gA));  // gA = g_p2 [V2][32]
+  vlaunch("unet_pool_bwd", 0.0, k_pool_bwd_add, ugrid(u->V[1] * 32), kThreads, st, u->lx[1], u->ly[1], u->lz[1], 32,
+          (const float*)u->gA, u->ge2);
+  VOS_CUDA_TRY(layer_backward(u, ENC2B, L[ENC2A].out, u->ge2, u->gA));
+  VOS_CUDA_TRY(layer_backward(u, ENC2A, u->p1, u->gA, u->gB));  // gB = g_p1 [V1][16]
+  vlaunch("unet_pool_bwd", 0.0, k_pool_bwd_add, ugrid(u->V[0] * 16), kThreads, st, u->lx[0], u->ly[0], u->lz[0], 16,
+          (const float*)u->gB, u->ge1);
+  VOS_CUDA_TRY(layer_backward(u, ENC1B, L[ENC1A].out, u->ge1, u->gA));
+  VOS_CUDA_TRY(layer_backward(u, ENC1A, u->x0, u->gA, nullptr));
+  return cudaGetLastError();
+}
+
+static void adam_step(vos_unet* u, float lr) {
+  u->adam_t += 1;
+  const float b1 = 0.9f, b2 = 0.999f, e = 1e-8f;
+  const float c1 = 1.0f / (1.0f - powf(b1, (float)u->adam_t)), c2 = 1.0f / (1.0f - powf(b2, (float)u->adam_t));
+  for (auto& l : u->L) {
+    const long long nw = 27LL * l.cout * l.cing;
+    vlaunch("unet_adam", 0.0, k_adam, ugrid(nw), kThreads, u->st, nw, l.W, (const float*)l.gW, l.mW, l.vW, lr, b1, b2,
+            e, c1, c2);
+    vlaunch("unet_adam", 0.0, k_adam, 1, kThreads, u->st, (long long)l.cout, l.b, (const float*)l.gb, l.mb, l.vb, lr,
+            b1, b2, e, c1, c2);
+  }
+  vlaunch("unet_adam", 0.0, k_adam, 1, kThreads, u->st, 17LL, u->head, (const float*)u->ghead, u->mhead, u->vhead,
+          lr, b1, b2, e, c1, c2);
+  prep_weights(u);
+}
+
+// Host flat vector (oracle layout: per layer W[cout][3][3][3][cin] then b,
+// then head w[16], b) <-> device tensors (padded input channels).
+static cudaError_t params_io(vos_unet* u, float* host, bool to_device, bool grads) {
+  long long off = 0;
+  std::vector<float> buf;
+  for (auto& l : u->L) {
+    const long long nw = 27LL * l.cout * l.cing;
+    buf.assign((size_t)nw, 0.0f);
+    float* dW = grads ? l.gW : l.W;
+    float* db = grads ? l.gb : l.b;
+    if (to_device) {
+      for (int o = 0; o < l.cout; ++o)
+        for (int t = 0; t < 27; ++t)
+          for (int i = 0; i < l.cin; ++i)
+            buf[((size_t)o * 27 + t) * l.cing + i] = host[off + ((long long)o * 27 + t) * l.cin + i];
+      VOS_CUDA_TRY(cudaMemcpy(dW, buf.data(), nw * sizeof(float), cudaMemcpyHostToDevice));
+      VOS_CUDA_TRY(cudaMemcpy(db, host + off + 27LL * l.cout * l.cin, l.cout * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+      VOS_CUDA_TRY(cudaMemcpy(buf.data(), dW, nw * sizeof(float), cudaMemcpyDeviceToHost));
+      for (int o = 0; o < l.cout; ++o)
+        for (int t = 0; t < 27; ++t)
+          for (int i = 0; i < l.cin; ++i)
+            host[off + ((long long)o * 27 + t) * l.cin + i] = buf[((size_t)o * 27 + t) * l.cing + i];
+      VOS_CUDA_TRY(cudaMemcpy(host + off + 27LL * l.cout * l.cin, db, l.cout * sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    off += 27LL * l.cout * l.cin + l.cout;
+  }
+  float* dh = grads ? u->ghead : u->head;
+  if (to_device)
+    VOS_CUDA_TRY(cudaMemcpy(dh, host + off, 17 * sizeof(float), cudaMemcpyHostToDevice));
+  else
+    VOS_CUDA_TRY(cudaMemcpy(host + off, dh, 17 * sizeof(float), cudaMemcpyDeviceToHost));
+  if (to_device && !grads) {
+    // a new parameter set restarts the optimiser
+    for (auto& l : u->L) {
+      const long long nw = 27LL * l.cout * l.cing;
+      cudaMemset(l.mW, 0, nw * 4);
+      cudaMemset(l.vW, 0, nw * 4);
+      cudaMemset(l.mb, 0, l.cout * 4);
+      cudaMemset(l.vb, 0, l.cout * 4);
+    }
+    cudaMemset(u->mhead, 0, 17 * 4);
+    cudaMemset(u->vhead, 0, 17 * 4);
+    u->adam_t = 0;
+    prep_weights(u);
+  }
+  return cudaStreamSynchronize(u->st);
+}
+
+static vos_unet* create_net(int px, int py, int pz, bool train, cudaStream_t st) {
+  vos_unet* u = new vos_unet();
+  u->st = st;
+  u->train = train;
+  u->adam_t = 0;
+  u->eps = nullptr;
+  auto up4 = [](int n) { return (n + 3) & ~3; };
+  u->d = Dims{up4(px), up4(py), up4(pz), px, py, pz};
+  for (int l = 0; l < 3; ++l) {
+    u->lx[l] = u->d.nx >> l;
+    u->ly[l] = u->d.ny >> l;
+    u->lz[l] = u->d.nz >> l;
+    u->V[l] = (long long)u->lx[l] * u->ly[l] * u->lz[l];
+  }
+  bool ok = true;
+  auto A = [&](size_t bytes) -> void* {
+    void* p = ualloc(u, bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  const long long V0 = u->V[0], V1 = u->V[1], V2 = u->V[2];
+  const long long nphys = (long long)px * py * pz;
+  for (int i = 0; i < 10; ++i) {
+    Layer& l = u->L[i];
+    l.cin = kSpec[i].cin;
+    l.cing = kSpec[i].cin < 8 ? 8 : kSpec[i].cin;
+    l.cout = kSpec[i].cout;
+    l.lev = kSpec[i].lev;
+    const long long nw = 27LL * l.cout * l.cing;
+    l.W = (float*)A(nw * 4);
+    l.b = (float*)A(l.cout * 4);
+    l.W16 = (__nv_bfloat16*)A(nw * 2);
+    l.WT16 = (__nv_bfloat16*)A(nw * 2);
+    l.out = (__nv_bfloat16*)A((size_t)u->V[l.lev] * l.cout * 2);
+    l.gW = (float*)A(nw * 4);
+    l.gb = (float*)A(l.cout * 4);
+    l.mW = (float*)A(nw * 4);
+    l.vW = (float*)A(nw * 4);
+    l.mb = (float*)A(l.cout * 4);
+    l.vb = (float*)A(l.cout * 4);
+  }
+  u->head = (float*)A(17 * 4);
+  u->ghead = (float*)A(17 * 4);
+  u->mhead = (float*)A(17 * 4);
+  u->vhead = (float*)A(17 * 4);
+  u->x0 = (__nv_bfloat16*)A((size_t)V0 * 8 * 2);
+  u->p1 = (__nv_bfloat16*)A((size_t)V1 * 16 * 2);
+  u->p2 = (__nv_bfloat16*)A((size_t)V2 * 32 * 2);
+  u->cat2 = (__nv_bfloat16*)A((size_t)V1 * 96 * 2);
+  u->cat1 = (__nv_bfloat16*)A((size_t)V0 * 48 * 2);
+  u->scal = (float*)A(16);
+  u->dscal = (double*)A(64);
+  u->z = (float*)A((size_t)nphys * 4);
+  u->rs.partials = (double*)A(32 * kMaxRedBlocks * sizeof(double));
+  u->rs.counter = (unsigned int*)A(256);
+  if (train) {
+    const long long gmax = std::max(std::max(V0 * 48, V1 * 96), V2 * 64);
+    u->gA = (float*)A(gmax * 4);
+    u->gB = (float*)A(gmax * 4);
+    u->ge1 = (float*)A(V0 * 16 * 4);
+    u->ge2 = (float*)A(V1 * 32 * 4);
+    const long long pmax = std::max(std::max(V0 * 16, V1 * 32), V2 * 64);
+    u->gpre = (float*)A(pmax * 4);
+    u->gpre16 = (__nv_bfloat16*)A(pmax * 2);
+    long long pdw = 0;
+    for (int l = 0; l < 3; ++l) {
+      long long ch = 2048;
+      while ((u->V[l] + ch - 1) / ch > 512) ch *= 2;
+      u->chunk[l] = ch;
+      u->nchunk[l] = (int)((u->V[l] + ch - 1) / ch);
+    }
+    for (auto& l : u->L) pdw = std::max(pdw, (long long)u->nchunk[l.lev] * 27 * l.cout * l.cing);
+    u->part_dw = (float*)A(pdw * 4);
+    u->ndb = 2 * g_num_sms;
+    u->part_db = (float*)A((size_t)u->ndb * 64 * 4);
+    u->az = (float*)A(nphys * 4);
+    u->res = (float*)A(nphys * 4);
+    u->dz = (float*)A(nphys * 4);
+  } else {
+    u->gA = u->gB = u->ge1 = u->ge2 = u->gpre = nullptr;
+    u->gpre16 = nullptr;
+    u->part_dw = u->part_db = nullptr;
+    u->az = u->res = u->dz = nullptr;
+  }
+  if (!ok) {
+    destroy_net(u);
+    return nullptr;
+  }
+  cudaMemsetAsync(u->rs.counter, 0, 256, st);
+  return u;
+}
+
+// Solver hook: z = UNet(r / rms(r), eps) * rms(r), rr = |r|^2 on the device.
+template <typename T>
+void precond_apply(vos_unet* u, const T* r, T* z, const double* rr, cudaStream_t st) {
+  cudaStream_t keep = u->st;
+  u->st = st;
+  forward<T>(u, r, u->eps, rr, 1, z);
+  u->st = keep;
+}
+
+}  // namespace unet
+
+void unet_box(const vos_unet* net, int* px, int* py, int* pz) {
+  *px = net->d.px;
+  *py = net->d.py;
+  *pz = net->d.pz;
+}
+void unet_attach_eps(vos_unet* net, const double* eps) { net->eps = eps; }
+
+template <typename T>
+void unet_precond(vos_unet* net, const T* r, T* z, const double* rr, cudaStream_t st) {
+  unet::precond_apply<T>(net, r, z, rr, st);
+}
+template void unet_precond<float>(vos_unet*, const float*, float*, const double*, cudaStream_t);
+template void unet_precond<double>(vos_unet*, const double*, double*, const double*, cudaStream_t);
+
+}  // namespace vos
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -266,5 +1070,153 @@ int vos_conv3d_bf16(const uint16_t* x, int32_t nx, int32_t ny, int32_t nz, int32
   }
   return VOS_OK;
 }
+
+int vos_unet_create(int32_t nx, int32_t ny, int32_t nz, int32_t train, void* stream, vos_unet** out) {
+  if (!out || nx < 4 || ny < 4 || nz < 4) {
+    set_global_error("vos_unet_create: need out and a box of at least 4 x 4 x 4");
+    return VOS_EINVAL;
+  }
+  *out = nullptr;
+  if ((double)nx * ny * nz > 4.0e8) {
+    set_global_error("vos_unet_create: box too large");
+    return VOS_EINVAL;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) g_num_sms = sms;
+  vos_unet* u = unet::create_net(nx, ny, nz, train != 0, (cudaStream_t)stream);
+  if (!u) {
+    set_global_error("vos_unet_create: device allocation failed");
+    return VOS_ENOMEM;
+  }
+  *out = u;
+  return VOS_OK;
+}
+
+int64_t vos_unet_num_params(void) { return unet::num_params(); }
+
+static int unet_io(vos_unet* u, float* host, int64_t n, bool to_dev, bool grads, const char* what) {
+  if (!u || !host || n != unet::num_params()) {
+    set_global_error(what);
+    return VOS_EINVAL;
+  }
+  if (grads && !u->train) {
+    set_global_error("vos_unet_get_grads: the network was created without training buffers");
+    return VOS_EINVAL;
+  }
+  cudaError_t e = unet::params_io(u, host, to_dev, grads);
+  if (e != cudaSuccess) {
+    set_global_error(cudaGetErrorString(e));
+    return VOS_ECUDA;
+  }
+  return VOS_OK;
+}
+
+int vos_unet_set_params(vos_unet* u, const float* host, int64_t n) {
+  return unet_io(u, const_cast<float*>(host), n, true, false, "vos_unet_set_params: bad argument");
+}
+int vos_unet_get_params(vos_unet* u, float* host, int64_t n) {
+  return unet_io(u, host, n, false, false, "vos_unet_get_params: bad argument");
+}
+int vos_unet_get_grads(vos_unet* u, float* host, int64_t n) {
+  return unet_io(u, host, n, false, true, "vos_unet_get_grads: bad argument");
+}
+
+static int unet_finish(vos_unet* u, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(u->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_global_error(cudaGetErrorString(e));
+    return VOS_ECUDA;
+  }
+  if (unet::take_timeout_flag()) {
+    set_global_error(what);
+    return VOS_ETIMEOUT;
+  }
+  return VOS_OK;
+}
+
+int vos_unet_forward(vos_unet* u, const float* r, const double* eps, float* z) {
+  if (!u || !r || !eps || !z) {
+    set_global_error("vos_unet_forward: NULL argument");
+    return VOS_EINVAL;
+  }
+  const long long n = (long long)u->d.px * u->d.py * u->d.pz;
+  vlaunch("unet_sumsq", 0.0, unet::k_sumsq, unet::ugrid(n), kThreads, u->st, n, r, u->dscal, u->rs);
+  cudaError_t e = unet::forward<float>(u, r, eps, u->dscal, 0, u->z);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(z, u->z, n * sizeof(float), cudaMemcpyDeviceToDevice, u->st);
+  if (e != cudaSuccess) {
+    set_global_error(cudaGetErrorString(e));
+    return VOS_ECUDA;
+  }
+  return unet_finish(u, "vos_unet_forward: a tensor-core wait ran out of time");
+}
+
+int vos_unet_backward(vos_unet* u, const float* dz) {
+  if (!u || !dz || !u->train) {
+    set_global_error("vos_unet_backward: NULL argument or no training buffers");
+    return VOS_EINVAL;
+  }
+  cudaError_t e = unet::backward(u, dz);
+  if (e != cudaSuccess) {
+    set_global_error(cudaGetErrorString(e));
+    return VOS_ECUDA;
+  }
+  return unet_finish(u, "vos_unet_backward: a tensor-core wait ran out of time");
+}
+
+// Loss of the network on one residual r of h's pressure operator; with
+// lr > 0 also one Adam step.
+static int unet_loss_step(vos_unet* u, vos_handle* h, const float* r, float lr, bool update, float* loss) {
+  if (!u || !h || !r || !loss || !u->train) {
+    set_global_error("vos_unet_train_step: NULL argument or no training buffers");
+    return VOS_EINVAL;
+  }
+  const Op<double>* A = handle_pressure_op(h);
+  const double* eps = handle_eps(h);
+  if (!A || !A->diag || A->box.mx != u->d.px || A->box.my != u->d.py || A->box.mz != u->d.pz) {
+    set_global_error("vos_unet_train_step: the network box differs from the handle's grid");
+    return VOS_EINVAL;
+  }
+  cudaStream_t st = u->st;
+  const long long n = (long long)u->d.px * u->d.py * u->d.pz;
+  const int g = unet::ugrid(n);
+  vlaunch("unet_sumsq", 0.0, unet::k_sumsq, g, kThreads, st, n, r, u->dscal, u->rs);
+  cudaError_t e = unet::forward<float>(u, r, eps, u->dscal, 0, u->z);
+  if (e == cudaSuccess) {
+    vlaunch("unet_apply_op", 0.0, unet::k_apply_op, g, kThreads, st, *A, (const float*)u->z, u->az);
+    vlaunch("unet_loss", 0.0, unet::k_loss_res, g, kThreads, st, n, (const float*)u->az, r, (const float*)u->scal,
+            u->res, u->dscal + 1, u->rs);
+    if (update) {
+      vlaunch("unet_apply_op", 0.0, unet::k_apply_op, g, kThreads, st, *A, (const float*)u->res, u->dz);
+      vlaunch("unet_scale_dz", 0.0, unet::k_scale_dz, g, kThreads, st, n, (const double*)(u->dscal + 1), u->dz);
+      e = unet::backward(u, u->dz);
+      if (e == cudaSuccess) unet::adam_step(u, lr);
+    }
+  }
+  if (e != cudaSuccess) {
+    set_global_error(cudaGetErrorString(e));
+    return VOS_ECUDA;
+  }
+  double sums[2] = {0.0, 0.0};
+  cudaMemcpyAsync(sums, u->dscal + 1, sizeof(sums), cudaMemcpyDeviceToHost, st);
+  int rc = unet_finish(u, "vos_unet_train_step: a tensor-core wait ran out of time");
+  if (rc != VOS_OK) return rc;
+  *loss = sums[1] > 0.0 ? (float)(sums[0] / sums[1]) : 0.0f;
+  return VOS_OK;
+}
+
+int vos_unet_train_step(vos_unet* u, vos_handle* h, const float* r, float lr, float* loss) {
+  if (!(lr > 0.0f) || !std::isfinite(lr)) {
+    set_global_error("vos_unet_train_step: lr must be > 0");
+    return VOS_EINVAL;
+  }
+  return unet_loss_step(u, h, r, lr, true, loss);
+}
+int vos_unet_eval_loss(vos_unet* u, vos_handle* h, const float* r, float* loss) {
+  return unet_loss_step(u, h, r, 0.0f, false, loss);
+}
+
+void vos_unet_destroy(vos_unet* u) { unet::destroy_net(u); }
 
 }  // extern "C"

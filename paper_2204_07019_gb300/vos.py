@@ -21,7 +21,8 @@ __all__ = [
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
     "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
-    "vos_floating_clusters", "vos_tile_config", "vos_conv3d_bf16", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
+    "vos_floating_clusters", "vos_tile_config", "vos_conv3d_bf16", "UNet", "vos_set_unet_preconditioner",
+    "vos_unet_solve_stats", "vos_pressure_snapshots", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -37,6 +38,9 @@ EXPORTED_SYMBOLS = [
     "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle", "vos_batch_destroy",
     "vos_floating_clusters", "vos_tile_config", "vos_conv3d_bf16",
+    "vos_unet_create", "vos_unet_num_params", "vos_unet_set_params", "vos_unet_get_params", "vos_unet_get_grads",
+    "vos_unet_forward", "vos_unet_backward", "vos_unet_train_step", "vos_unet_eval_loss", "vos_unet_destroy",
+    "vos_set_unet_preconditioner", "vos_unet_solve_stats", "vos_pressure_snapshots",
 ]
 
 
@@ -148,6 +152,30 @@ def load_library(path=None):
     lib.vos_conv3d_bf16.argtypes = [ctypes.c_void_p] + [ctypes.c_int32] * 4 + [ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.vos_conv3d_bf16.restype = ctypes.c_int
+    vp, fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)
+    lib.vos_unet_create.argtypes = [ctypes.c_int32] * 4 + [vp, ctypes.POINTER(vp)]
+    lib.vos_unet_create.restype = ctypes.c_int
+    lib.vos_unet_num_params.argtypes = []
+    lib.vos_unet_num_params.restype = ctypes.c_int64
+    for name in ("vos_unet_set_params", "vos_unet_get_params", "vos_unet_get_grads"):
+        getattr(lib, name).argtypes = [vp, vp, ctypes.c_int64]
+        getattr(lib, name).restype = ctypes.c_int
+    lib.vos_unet_forward.argtypes = [vp, vp, vp, vp]
+    lib.vos_unet_forward.restype = ctypes.c_int
+    lib.vos_unet_backward.argtypes = [vp, vp]
+    lib.vos_unet_backward.restype = ctypes.c_int
+    lib.vos_unet_train_step.argtypes = [vp, vp, vp, ctypes.c_float, fp]
+    lib.vos_unet_train_step.restype = ctypes.c_int
+    lib.vos_unet_eval_loss.argtypes = [vp, vp, vp, fp]
+    lib.vos_unet_eval_loss.restype = ctypes.c_int
+    lib.vos_unet_destroy.argtypes = [vp]
+    lib.vos_unet_destroy.restype = None
+    lib.vos_set_unet_preconditioner.argtypes = [vp, vp]
+    lib.vos_set_unet_preconditioner.restype = ctypes.c_int
+    lib.vos_unet_solve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.vos_unet_solve_stats.restype = ctypes.c_int
+    lib.vos_pressure_snapshots.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), vp]
+    lib.vos_pressure_snapshots.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -351,6 +379,97 @@ def vos_conv3d_bf16(x, shape, cin, w, bias, cout, relu=False, y_f32=None, y_bf16
                              1 if relu else 0, _ptr(y_f32), _ptr(y_bf16), st)
     if rc != VOS_OK:
         raise VosError(rc, lib.vos_last_error(None).decode())
+
+
+def _raise(lib, rc, h=None):
+    if rc != VOS_OK:
+        raise VosError(rc, lib.vos_last_error(h).decode())
+
+
+class UNet:
+    """The learned pressure preconditioner (vos_unet_*): a network for one
+    grid shape (nz, ny, nx).  Device vectors are torch CUDA tensors."""
+
+    def __init__(self, shape, train=True, stream=None):
+        lib = load_library()
+        nz, ny, nx = shape
+        self.shape = tuple(shape)
+        st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        ptr = ctypes.c_void_p()
+        _raise(lib, lib.vos_unet_create(int(nx), int(ny), int(nz), 1 if train else 0, st, ctypes.byref(ptr)))
+        self.ptr = ptr
+
+    @staticmethod
+    def num_params():
+        return int(load_library().vos_unet_num_params())
+
+    def set_params(self, flat):
+        lib = load_library()
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _raise(lib, lib.vos_unet_set_params(self.ptr, a.ctypes.data, a.size))
+
+    def _get(self, name):
+        lib = load_library()
+        a = np.empty(self.num_params(), dtype=np.float32)
+        _raise(lib, getattr(lib, name)(self.ptr, a.ctypes.data, a.size))
+        return a
+
+    def get_params(self):
+        return self._get("vos_unet_get_params")
+
+    def get_grads(self):
+        return self._get("vos_unet_get_grads")
+
+    def forward(self, r, eps, z):
+        lib = load_library()
+        _raise(lib, lib.vos_unet_forward(self.ptr, _ptr(r), _ptr(eps), _ptr(z)))
+
+    def backward(self, dz):
+        lib = load_library()
+        _raise(lib, lib.vos_unet_backward(self.ptr, _ptr(dz)))
+
+    def train_step(self, h, r, lr):
+        lib = load_library()
+        loss = ctypes.c_float()
+        _raise(lib, lib.vos_unet_train_step(self.ptr, h.ptr, _ptr(r), float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def eval_loss(self, h, r):
+        lib = load_library()
+        loss = ctypes.c_float()
+        _raise(lib, lib.vos_unet_eval_loss(self.ptr, h.ptr, _ptr(r), ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self.ptr:
+            load_library().vos_unet_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vos_set_unet_preconditioner(h, net):
+    lib = load_library()
+    _raise(lib, lib.vos_set_unet_preconditioner(h.ptr, net.ptr if net is not None else None), h.ptr)
+
+
+def vos_unet_solve_stats(h):
+    lib = load_library()
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _raise(lib, lib.vos_unet_solve_stats(h.ptr, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def vos_pressure_snapshots(h, iters, out):
+    """Residual snapshots of the last pressure solve into ``out`` (a CUDA
+    float32 tensor of len(iters) x cells)."""
+    lib = load_library()
+    arr = (ctypes.c_int32 * len(iters))(*[int(i) for i in iters])
+    _raise(lib, lib.vos_pressure_snapshots(h.ptr, len(iters), arr, _ptr(out)), h.ptr)
 
 
 def vos_tile_config(h, sys, level):
