@@ -222,6 +222,92 @@ def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
         V.vos_destroy(h)
 
 
+def measured_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def learned_leg(V, es, prm, dt, steps, torch, crop=64, rounds=2, adam_per_round=60, lr=2e-3, seed=0):
+    """The learned pressure preconditioner on the same workload: train the
+    U-Net with the library's own kernels on residual snapshots of short runs
+    on crop^3 pieces of the rock (the network is fully convolutional), then
+    time steps of the full workload with the network attached (flexible CG,
+    MG-PCG fallback; eager launches).  Also the tensor-core conv throughput."""
+    t0 = time.time()
+    net_t = V.UNet((crop,) * 3, train=True)
+    net_t.set_params(V.UNet.he_init(seed))
+    snap_iters = [0, 2, 5, 10, 20, 40]
+    losses = []
+    n = es.shape[0]
+    offsets = [(0, 0, 0), (n - crop, n - crop, n - crop)]
+    dt0 = 0.1 * prm["dx"] / max(abs(prm["u_in"]), 1e-30)
+    for oz, oy, ox in offsets:
+        esc = np.ascontiguousarray(es[oz:oz + crop, oy:oy + crop, ox:ox + crop])
+        prc = dict(prm)
+        prc.update(nx=crop, ny=crop, nz=crop)
+        h = V.vos_create(esc, prc)
+        try:
+            V.vos_step(h, dt0)
+            snaps = torch.empty((len(snap_iters), crop ** 3), dtype=torch.float32, device="cuda")
+            for _ in range(rounds):
+                V.vos_step(h, min(V.vos_suggest_dt(h, 0.5, 0.005), 5.0 * dt0))
+                V.vos_pressure_snapshots(h, snap_iters, snaps)
+                for k in range(adam_per_round):
+                    losses.append(net_t.train_step(h, snaps[k % len(snap_iters)], lr))
+        finally:
+            V.vos_destroy(h)
+    params = net_t.get_params()
+    net_t.close()
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    net = V.UNet(es.shape, train=False)
+    net.set_params(params)
+    h = V.vos_create(es, prm)
+    try:
+        V.vos_step(h, dt0)
+        V.vos_step(h, dt)
+        V.vos_set_unet_preconditioner(h, net)
+        V.vos_step(h, dt)  # warm-up with the network
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        its, nets, fbs = [], [], []
+        e0.record(stream)
+        for _ in range(steps):
+            V.vos_step(h, dt)
+            s = V.vos_get_stats(h)
+            ni, fb = V.vos_unet_solve_stats(h)
+            its.append(s["iters_p"])
+            nets.append(ni)
+            fbs.append(fb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        V.vos_prof_reset()
+        V.vos_prof_enable("unet_conv")
+        V.vos_step(h, dt)
+        rep = V.vos_prof_report()
+        V.vos_prof_enable(None)
+        V.vos_prof_reset()
+    finally:
+        V.vos_destroy(h)
+        net.close()
+    nconv, cms, cflops = rep.get("unet_conv", (0, 0.0, 0.0))
+    peak, src = measured_bf16_peak()
+    tf = cflops / (cms * 1e-3) / 1e12 if cms > 0 else None
+    return {"ms_per_step": ms, "value": es.size / (ms * 1e-3), "iters_p_mean": float(np.mean(its)),
+            "net_iters_mean": float(np.mean(nets)), "fallbacks": int(sum(fbs)), "steps": steps,
+            "train": {"seconds": train_s, "adam_steps": len(losses), "crop": crop, "crops": len(offsets),
+                      "snapshot_iters": snap_iters, "loss_first": float(np.mean(losses[:6])),
+                      "loss_last": float(np.mean(losses[-6:]))},
+            "conv": {"launches": nconv, "ms": cms, "tflops": tf, "peak_tflops": peak, "peak_source": src,
+                     "frac": (tf / peak) if tf else None, "bound": "tensor"}}
+
+
 def batch_workload(count=64):
     """64 disc micromodels, side lengths U[128, 768], log-uniform Pe in [1, 100]
     and Da in [0.01, 100], iVoS, mixed precision."""
@@ -336,6 +422,7 @@ def main():
     ap.add_argument("--size", type=int, default=256, help="edge of the rock workload (profiling runs only)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner leg")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -389,6 +476,10 @@ def main():
     p64["precision"] = 0
     r64 = time_gpu(V, es, p64, max(args.fp64_steps, 1), 2, torch, profile=False)
     e2e = time_e2e(V, es, prm, max(2, args.steps // 2), dt)
+    learned = None
+    if not args.no_learned and es.ndim == 3 and min(es.shape) >= 64:
+        learned = learned_leg(V, es, prm, dt, 3, torch)
+        learned["vs_fp64"] = learned["value"] / (N / (r64["ms"] * 1e-3))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -404,7 +495,8 @@ def main():
                       "iters_p_mean": float(np.mean([i[1] for i in iters])),
                       "iters_c_mean": float(np.mean([i[2] for i in iters])),
                       "res_p_max": float(max(i[3] for i in iters))},
-           "device_bytes": r["dev_bytes"], "e2e": e2e, "clocks": ck, "breakdown": r["breakdown"]}
+           "device_bytes": r["dev_bytes"], "e2e": e2e, "clocks": ck, "learned": learned,
+           "breakdown": r["breakdown"]}
     if rank == 0 and not args.no_cpu:
         r, n, shp, dtc = oracle_sample(es, prm, budget_s=15.0)
         out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -8,13 +8,12 @@
 // channels of one tap are one 16-byte vector.
 //
 // Convolution as an implicit GEMM: D[v, o] = sum_K A[v, K] B[o, K] with
-// K = tap * C_in + i (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)), A the gathered
-// neighbourhood (zero outside the box) and B the weights [C_out][27][C_in].
-// One CTA of 128 threads owns 128 consecutive voxels (the MMA's M); K runs
-// in stages of 64 (four K = 16 MMAs), double buffered: all threads gather
-// the next stage into shared memory while the tensor core works on the
-// current one.  The FP32 accumulator (128 lanes x C_out columns) lives in
-// tensor memory and is read back once, with bias and ReLU fused.
+// K = (tap, input channel) (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)), A the
+// neighbourhood of v (zero outside the box) and B the weights
+// [C_out][27][C_in].  The A operand is never materialised: the MMA
+// descriptors point into an input tile in shared memory (see k_conv3d_tc).
+// The FP32 accumulator (128 lanes x C_out columns) lives in tensor memory
+// and is read back once, with bias and ReLU fused.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -42,10 +41,13 @@ static __device__ int g_tc_timeout = 0;
 
 namespace unet {
 
-constexpr int kTM = 128;                    // voxels per CTA (MMA M)
-constexpr int kStageK = 64;                 // K elements per stage
-constexpr int kStageA = kTM * kStageK * 2;  // bytes of one A stage (16 KB)
-constexpr uint64_t kWaitNs = 2000000000ull; // 2 s per mbarrier wait
+constexpr int kTM = 128;                     // output voxels per CTA (MMA M)
+constexpr int kTX = 8, kTY = 16;             // output tile: 8 (x) x 16 (y) x 1 (z)
+constexpr int kHX = kTX + 2, kHY = kTY + 2;  // input tile with a one-voxel halo
+constexpr int kHalo = kHX * kHY * 3;         // 540 voxels
+constexpr int kPlaneA = kHalo * 16;          // one 8-channel group of the tile (8640 B)
+constexpr int kStageA = 2 * kPlaneA;         // 16 input channels per stage
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per mbarrier wait
 
 struct ConvArgs {
   const __nv_bfloat16* x;  // [V][cin]
@@ -60,19 +62,27 @@ struct ConvArgs {
 __host__ __device__ inline int tmem_cols(int cout) {
   return cout <= 32 ? 32 : (cout <= 64 ? 64 : (cout <= 128 ? 128 : 256));
 }
-inline size_t conv_smem_bytes(int cout) { return 2 * (size_t)kStageA + 2 * (size_t)cout * 128 + 64; }
+inline size_t stage_b_bytes(int cout) { return (size_t)27 * cout * 32; }
+inline size_t conv_smem_bytes(int cout) { return 2 * ((size_t)kStageA + stage_b_bytes(cout)) + 64; }
 
-// Byte offset of (row, K-group g) in a stage: 8-row groups 1024 B apart
-// (SBO), K groups of 8 elements 128 B apart (LBO), 16 B per row.
-__device__ __forceinline__ uint32_t stage_off(int row, int g) {
-  return (uint32_t)((row >> 3) * 1024 + g * 128 + (row & 7) * 16);
-}
-
+// Implicit-GEMM convolution with the input tile in shared memory.  A CTA
+// owns an 8 x 16 x 1 output tile (M = 128 rows, row m = (x0 + m % 8, y0 +
+// m / 8)).  K runs over stages of 16 input channels; a stage holds the
+// 10 x 18 x 3 input tile of those channels, laid out [channel group][z][y][x]
+// with 16 B (8 channels) per voxel, and the weights of all 27 taps.  For tap
+// (dz, dy, dx) the A operand is the tile itself, seen through a descriptor:
+// the 8 rows of a core matrix are 8 consecutive x voxels (128 contiguous
+// bytes), consecutive 8-row groups are consecutive y rows (SBO = 160 B), the
+// two K core matrices are the two channel groups (LBO = 8640 B), and the tap
+// shifts the start address.  So one stage costs one tile load and 27 MMAs
+// with no im2col copy.  The weights of a stage are [tap][C_out][16] in the
+// same canonical layout (SBO = 256 B between 8-channel row groups, LBO =
+// 128 B).  Stages are double buffered against the tensor core.
 __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
   VOS_COUNT_EXEC();
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int bstage = a.cout * 128;
+  const int bstage = 27 * a.cout * 32;
   unsigned char* sA = smem;
   unsigned char* sB = smem + 2 * kStageA;
   uint64_t* mbar = (uint64_t*)(sB + 2 * bstage);
@@ -90,16 +100,11 @@ __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
 
-  const long long v = (long long)blockIdx.x * kTM + tid;
-  const bool vin = v < a.V;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z;
   const long long plane = (long long)a.nx * a.ny;
-  const int vk = vin ? (int)(v / plane) : 0;
-  const int vj = vin ? (int)((v - (long long)vk * plane) / a.nx) : 0;
-  const int vi = vin ? (int)(v - (long long)vk * plane - (long long)vj * a.nx) : 0;
-  const int cg = a.cin >> 3;       // channel groups per tap
-  const int G = 27 * cg;           // K groups in total
+  const int ncg = a.cin >> 3;           // 8-channel groups of the input
+  const int nst = (ncg + 1) >> 1;       // stages of 16 channels
   const int K = 27 * a.cin;
-  const int nst = (G + 7) >> 3;    // stages
   const uint32_t idesc = tc::idesc_bf16_f32(kTM, a.cout);
   uint32_t phase[2] = {0u, 0u};
   bool ok = true;
@@ -113,23 +118,20 @@ __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
     }
     unsigned char* A = sA + s * kStageA;
     unsigned char* B = sB + s * bstage;
-#pragma unroll 2
-    for (int g = 0; g < 8; ++g) {
-      const int gg = c * 8 + g;
+    for (int e = tid; e < 2 * kHalo; e += kTM) {
+      const int kg = e / kHalo, hv = e - kg * kHalo;
+      const int xi = hv % kHX, yi = (hv / kHX) % kHY, zi = hv / (kHX * kHY);
+      const int gx = x0 - 1 + xi, gy = y0 - 1 + yi, gz = z0 - 1 + zi, cg = 2 * c + kg;
       uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (vin && gg < G) {
-        const int tap = gg / cg, ch = (gg - tap * cg) * 8;
-        const int ii = vi + (tap % 3) - 1, jj = vj + (tap / 3) % 3 - 1, kk = vk + tap / 9 - 1;
-        if (ii >= 0 && ii < a.nx && jj >= 0 && jj < a.ny && kk >= 0 && kk < a.nz)
-          val = __ldg((const uint4*)(a.x + ((long long)kk * plane + (long long)jj * a.nx + ii) * a.cin + ch));
-      }
-      *(uint4*)(A + stage_off(tid, g)) = val;
+      if (cg < ncg && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
+        val = __ldg((const uint4*)(a.x + ((long long)gz * plane + (long long)gy * a.nx + gx) * a.cin + cg * 8));
+      *(uint4*)(A + kg * kPlaneA + hv * 16) = val;
     }
-    for (int it = tid; it < a.cout * 8; it += kTM) {
-      const int n = it >> 3, g = it & 7, gg = c * 8 + g;
+    for (int e = tid; e < 27 * a.cout * 2; e += kTM) {
+      const int kg = e & 1, n = (e >> 1) % a.cout, t = (e >> 1) / a.cout, cg = 2 * c + kg;
       uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (gg < G) val = __ldg((const uint4*)(a.w + (long long)n * K + gg * 8));
-      *(uint4*)(B + stage_off(n, g)) = val;
+      if (cg < ncg) val = __ldg((const uint4*)(a.w + ((long long)n * 27 + t) * a.cin + cg * 8));
+      *(uint4*)(B + t * (a.cout * 32) + (n >> 3) * 256 + kg * 128 + (n & 7) * 16) = val;
     }
     tc::fence_proxy_async_smem();
     if (!__syncthreads_and(okw ? 1 : 0)) {  // block-uniform: a wait ran out of time
@@ -139,15 +141,16 @@ __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
     if (tid == 0) {
       tc::fence_after_sync();
       const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
-#pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        const uint64_t ad = tc::desc_kmajor(a0 + ks * 256, 128, 1024);
-        const uint64_t bd = tc::desc_kmajor(b0 + ks * 256, 128, 1024);
-        tc::mma_bf16(tmem, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+      for (int t = 0; t < 27; ++t) {
+        const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;  // halo offsets 0..2
+        const uint64_t ad = tc::desc_kmajor(a0 + (uint32_t)(((dz * kHY + dy) * kHX + dx) * 16), kPlaneA, kHX * 16);
+        const uint64_t bd = tc::desc_kmajor(b0 + (uint32_t)(t * a.cout * 32), 128, 256);
+        tc::mma_bf16(tmem, ad, bd, idesc, (c > 0 || t > 0) ? 1u : 0u);
       }
       tc::commit(tc::smem_addr(&mbar[s]));
     }
   }
+  (void)K;
   // Wait for the last stage's MMAs (a commit tracks all earlier MMAs of the
   // issuing thread) and for the other buffer's outstanding arrival.
   if (ok) {
@@ -160,6 +163,10 @@ __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
     if (tid == 0) atomicExch(&g_tc_timeout, 1);
   } else {
     tc::fence_after_sync();
+    const int m = tid;  // TMEM lane of this thread = output row
+    const int ox = x0 + (m & 7), oy = y0 + (m >> 3);
+    const bool vin = ox < a.nx && oy < a.ny;
+    const long long v = (long long)z0 * plane + (long long)oy * a.nx + ox;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     for (int n0 = 0; n0 < a.cout; n0 += 16) {
       uint32_t r[16];
@@ -198,21 +205,21 @@ __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
 // Host launcher: y = conv3(x, w) (+ bias, ReLU).  Returns a CUDA error.
 cudaError_t conv3d(const ConvArgs& a, cudaStream_t st) {
   static bool attr_done = false;
-  const size_t sm = conv_smem_bytes(256);
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)conv_smem_bytes(96));
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  const long long nb = (a.V + kTM - 1) / kTM;
-  if (nb <= 0) return cudaSuccess;
+  if (a.V <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((a.nx + kTX - 1) / kTX), (unsigned)((a.ny + kTY - 1) / kTY), (unsigned)a.nz);
   const double flops = 2.0 * 27.0 * a.cin * a.cout * (double)a.V;
-  vlaunch_smem("unet_conv", flops, k_conv3d_tc, dim3((unsigned)nb), dim3(kTM), conv_smem_bytes(a.cout), st, a);
+  vlaunch_smem("unet_conv", flops, k_conv3d_tc, grid, dim3(kTM), conv_smem_bytes(a.cout), st, a);
   return cudaGetLastError();
 }
 
 bool conv_shape_ok(int cin, int cout) {
-  return cin >= 8 && cin % 8 == 0 && cout >= 16 && cout <= 256 && cout % 16 == 0;
+  return cin >= 8 && cin % 8 == 0 && cout >= 16 && cout <= 96 && cout % 16 == 0;
 }
 
 int take_timeout_flag() {
@@ -1041,7 +1048,7 @@ extern "C" {
 int vos_conv3d_bf16(const uint16_t* x, int32_t nx, int32_t ny, int32_t nz, int32_t cin, const uint16_t* w,
                     const float* bias, int32_t cout, int32_t relu, float* y_f32, uint16_t* y_bf16, void* stream) {
   if (!x || !w || (!y_f32 && !y_bf16) || nx < 1 || ny < 1 || nz < 1 || !unet::conv_shape_ok(cin, cout)) {
-    set_global_error("vos_conv3d_bf16: bad argument (cin a multiple of 8, cout a multiple of 16 in [16, 256])");
+    set_global_error("vos_conv3d_bf16: bad argument (cin a multiple of 8, cout a multiple of 16 in [16, 96])");
     return VOS_EINVAL;
   }
   unet::ConvArgs a;

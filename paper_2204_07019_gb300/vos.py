@@ -403,6 +403,21 @@ class UNet:
     def num_params():
         return int(load_library().vos_unet_num_params())
 
+    # (C_in, C_out) of the ten 3x3x3 convs in parameter order
+    CONVS = ((2, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16), (16, 16))
+
+    @classmethod
+    def he_init(cls, seed):
+        """Seeded He-normal weights and zero biases as a flat parameter vector."""
+        g = np.random.default_rng(seed)
+        parts = []
+        for ci, co in cls.CONVS:
+            parts.append(g.standard_normal(co * 27 * ci) * np.sqrt(2.0 / (27 * ci)))
+            parts.append(np.zeros(co))
+        parts.append(g.standard_normal(16) * np.sqrt(1.0 / 16))
+        parts.append(np.zeros(1))
+        return np.concatenate(parts).astype(np.float32)
+
     def set_params(self, flat):
         lib = load_library()
         a = np.ascontiguousarray(flat, dtype=np.float32)
