@@ -423,6 +423,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner leg")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the step's kernels one by one instead of replaying CUDA graphs "
+                         "(the same kernels; for profilers)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -439,6 +442,8 @@ def main():
     if dist is not None:
         dist.barrier()
     V.load_library()
+    if args.eager:
+        V.vos_set_launch_mode(0)
     if args.workload == "batch64":
         eps, prms = batch_workload(64)
         N = int(sum(e.size for e in eps))
@@ -487,7 +492,7 @@ def main():
                       "p_rtol": prm["p_rtol"], "u_rtol": prm["u_rtol"], "c_rtol": prm["c_rtol"],
                       "residual": "diagonally scaled, FP64",
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
-                      "tiles": r["tiles"]},
+                      "launch": "eager" if args.eager else "graph", "tiles": r["tiles"]},
            "roofline": r["roofline"], "gpu_launches": r["launches"],
            "fp64": {"value": N * world / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
                     "iters_p_mean": float(np.mean([i[1] for i in r64["iters"]]))},
