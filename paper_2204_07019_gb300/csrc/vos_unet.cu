@@ -63,7 +63,13 @@ __host__ __device__ inline int tmem_cols(int cout) {
   return cout <= 32 ? 32 : (cout <= 64 ? 64 : (cout <= 128 ? 128 : 256));
 }
 inline size_t stage_b_bytes(int cout) { return (size_t)27 * cout * 32; }
-inline size_t conv_smem_bytes(int cout) { return 2 * ((size_t)kStageA + stage_b_bytes(cout)) + 64; }
+// Stages of 16 input channels, and the buffers they cycle through (one
+// buffer when there is one stage: half the shared memory, twice the CTAs).
+__host__ __device__ inline int conv_stages(int cin) { return ((cin >> 3) + 1) >> 1; }
+__host__ __device__ inline int conv_buffers(int cin) { return conv_stages(cin) >= 2 ? 2 : 1; }
+inline size_t conv_smem_bytes(int cin, int cout) {
+  return conv_buffers(cin) * ((size_t)kStageA + stage_b_bytes(cout)) + 64;
+}
 
 // Implicit-GEMM convolution with the input tile in shared memory.  A CTA
 // owns an 8 x 16 x 1 output tile (M = 128 rows, row m = (x0 + m % 8, y0 +
@@ -83,9 +89,10 @@ __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int bstage = 27 * a.cout * 32;
+  const int nbuf = conv_buffers(a.cin);
   unsigned char* sA = smem;
-  unsigned char* sB = smem + 2 * kStageA;
-  uint64_t* mbar = (uint64_t*)(sB + 2 * bstage);
+  unsigned char* sB = smem + nbuf * kStageA;
+  uint64_t* mbar = (uint64_t*)(sB + nbuf * bstage);
   uint32_t* slot = (uint32_t*)(mbar + 2);
   const uint32_t ncols = (uint32_t)tmem_cols(a.cout);
 
@@ -103,16 +110,16 @@ __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z;
   const long long plane = (long long)a.nx * a.ny;
   const int ncg = a.cin >> 3;           // 8-channel groups of the input
-  const int nst = (ncg + 1) >> 1;       // stages of 16 channels
+  const int nst = conv_stages(a.cin);   // stages of 16 channels
   const int K = 27 * a.cin;
   const uint32_t idesc = tc::idesc_bf16_f32(kTM, a.cout);
   uint32_t phase[2] = {0u, 0u};
   bool ok = true;
 
   for (int c = 0; c < nst; ++c) {
-    const int s = c & 1;
+    const int s = c % nbuf;
     bool okw = true;
-    if (c >= 2) {  // the MMAs of stage c - 2 must be done reading buffer s
+    if (c >= nbuf) {  // the MMAs of stage c - nbuf must be done reading buffer s
       okw = tc::mbar_wait(tc::smem_addr(&mbar[s]), phase[s], kWaitNs);
       phase[s] ^= 1u;
     }
@@ -154,7 +161,7 @@ __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
   // Wait for the last stage's MMAs (a commit tracks all earlier MMAs of the
   // issuing thread) and for the other buffer's outstanding arrival.
   if (ok) {
-    const int sl = (nst - 1) & 1;
+    const int sl = (nst - 1) % nbuf;
     ok = tc::mbar_wait(tc::smem_addr(&mbar[sl]), phase[sl], kWaitNs);
     if (ok && nst >= 2) ok = tc::mbar_wait(tc::smem_addr(&mbar[sl ^ 1]), phase[sl ^ 1], kWaitNs);
   }
@@ -207,14 +214,14 @@ cudaError_t conv3d(const ConvArgs& a, cudaStream_t st) {
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)conv_smem_bytes(96));
+                                         (int)conv_smem_bytes(96, 96));
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
   if (a.V <= 0) return cudaSuccess;
   const dim3 grid((unsigned)((a.nx + kTX - 1) / kTX), (unsigned)((a.ny + kTY - 1) / kTY), (unsigned)a.nz);
   const double flops = 2.0 * 27.0 * a.cin * a.cout * (double)a.V;
-  vlaunch_smem("unet_conv", flops, k_conv3d_tc, grid, dim3(kTM), conv_smem_bytes(a.cout), st, a);
+  vlaunch_smem("unet_conv", flops, k_conv3d_tc, grid, dim3(kTM), conv_smem_bytes(a.cin, a.cout), st, a);
   return cudaGetLastError();
 }
 
