@@ -244,9 +244,12 @@ size_t vos_device_bytes(const vos_handle* h);
  *   y_f32 (FP32) and/or y_bf16 (BF16, round to nearest even): [V][cout].
  *   y[v][o] = bias[o] + sum over taps t and channels c of
  *             w[o][t][c] x[v + t][c], x = 0 outside the box.
- * cin must be a multiple of 8, cout a multiple of 16 in [16, 96].
- * Errors: VOS_EINVAL, VOS_ECUDA, VOS_ETIMEOUT (a tensor-core wait gave up
- * after 2 s; the output is invalid); message via vos_last_error(NULL). */
+ * cin must be a multiple of 8, cout a multiple of 16 in [16, 96].  The call
+ * allocates (and frees) a device buffer of 27 * cout * 16 * ceil(cin / 16)
+ * BF16 values for the weights in the kernel's shared-memory layout.
+ * Errors: VOS_EINVAL, VOS_ENOMEM, VOS_ECUDA, VOS_ETIMEOUT (a tensor-core
+ * wait gave up after 2 s; the output is invalid); message via
+ * vos_last_error(NULL). */
 int vos_conv3d_bf16(const uint16_t* x, int32_t nx, int32_t ny, int32_t nz, int32_t cin, const uint16_t* w,
                     const float* bias, int32_t cout, int32_t relu, float* y_f32, uint16_t* y_bf16, void* stream);
 

@@ -14,6 +14,8 @@
 // descriptors point into an input tile in shared memory (see k_conv3d_tc).
 // The FP32 accumulator (128 lanes x C_out columns) lives in tensor memory
 // and is read back once, with bias and ReLU fused.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -45,16 +47,18 @@ constexpr int kTM = 128;                     // output voxels per CTA (MMA M)
 constexpr int kTX = 8, kTY = 16;             // output tile: 8 (x) x 16 (y) x 1 (z)
 constexpr int kHX = kTX + 2, kHY = kTY + 2;  // input tile with a one-voxel halo
 constexpr int kHalo = kHX * kHY * 3;         // 540 voxels
-constexpr int kPlaneA = kHalo * 16;          // one 8-channel group of the tile (8640 B)
+constexpr int kBoxBytes = kHalo * 16;        // one 8-channel group of the tile (8640 B)
+constexpr int kPlaneA = 8704;                // the same, padded to a multiple of 128 B (TMA)
 constexpr int kStageA = 2 * kPlaneA;         // 16 input channels per stage
+constexpr int kBulkChunk = 16384;            // bytes per bulk copy of the weights
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per mbarrier wait
 
 struct ConvArgs {
-  const __nv_bfloat16* x;  // [V][cin]
-  const __nv_bfloat16* w;  // [cout][27 * cin]
-  const float* bias;       // [cout] or null
-  float* yf;               // [V][cout] FP32 output or null
-  __nv_bfloat16* yb;       // [V][cout] BF16 output or null
+  const __nv_bfloat16* x;    // [V][cin] (described to the kernel by a TMA tensor map)
+  const __nv_bfloat16* img;  // weights in the shared-memory image layout (see conv_image)
+  const float* bias;         // [cout] or null
+  float* yf;                 // [V][cout] FP32 output or null
+  __nv_bfloat16* yb;         // [V][cout] BF16 output or null
   int nx, ny, nz, cin, cout, relu;
   long long V;
 };
@@ -62,118 +66,170 @@ struct ConvArgs {
 __host__ __device__ inline int tmem_cols(int cout) {
   return cout <= 32 ? 32 : (cout <= 64 ? 64 : (cout <= 128 ? 128 : 256));
 }
-inline size_t stage_b_bytes(int cout) { return (size_t)27 * cout * 32; }
+__host__ __device__ inline int stage_b_bytes(int cout) { return 27 * cout * 32; }
 // Stages of 16 input channels, and the buffers they cycle through (one
 // buffer when there is one stage: half the shared memory, twice the CTAs).
 __host__ __device__ inline int conv_stages(int cin) { return ((cin >> 3) + 1) >> 1; }
 __host__ __device__ inline int conv_buffers(int cin) { return conv_stages(cin) >= 2 ? 2 : 1; }
 inline size_t conv_smem_bytes(int cin, int cout) {
-  return conv_buffers(cin) * ((size_t)kStageA + stage_b_bytes(cout)) + 64;
+  return (size_t)conv_buffers(cin) * ((size_t)kStageA + stage_b_bytes(cout)) + 64;
+}
+// Elements of a conv's weight image: stages x 27 taps x cout x 16 channels.
+__host__ __device__ inline long long conv_image_elems(int cin, int cout) { return (long long)conv_stages(cin) * 27 * cout * 16; }
+
+// The weight image: the bytes that the B operand of stage s needs in shared
+// memory, stored contiguously so that one bulk copy brings a whole stage.
+// Element (output n, tap t, input channel c) sits in stage s = c / 16 at
+// byte t*cout*32 + (n/8)*256 + kg*128 + (n%8)*16 + (c%8)*2 with
+// kg = (c%16)/8: per tap an N x 16 K-major operand in the no-swizzle
+// canonical layout (8-row groups 256 B apart, the two K core matrices
+// 128 B apart).  Channels >= cin are zero.
+__device__ __forceinline__ void image_decode(long long e, int cout, int& n, int& t, int& c) {
+  const int j = (int)(e & 7);
+  const int nr = (int)((e >> 3) & 7);
+  const int kg = (int)((e >> 6) & 1);
+  const long long q = e >> 7;  // (s * 27 + t) * (cout / 8) + n / 8
+  const int ng = cout >> 3;
+  const int n8 = (int)(q % ng);
+  const long long st = q / ng;
+  t = (int)(st % 27);
+  const int s = (int)(st / 27);
+  n = n8 * 8 + nr;
+  c = s * 16 + kg * 8 + j;
 }
 
-// Implicit-GEMM convolution with the input tile in shared memory.  A CTA
-// owns an 8 x 16 x 1 output tile (M = 128 rows, row m = (x0 + m % 8, y0 +
-// m / 8)).  K runs over stages of 16 input channels; a stage holds the
-// 10 x 18 x 3 input tile of those channels, laid out [channel group][z][y][x]
-// with 16 B (8 channels) per voxel, and the weights of all 27 taps.  For tap
-// (dz, dy, dx) the A operand is the tile itself, seen through a descriptor:
+// Image of a forward conv from FP32 weights W[cout][27][cin] (transpose =
+// 0), or of its data gradient (transpose = 1: a conv with cin' = cout and
+// cout' = cin whose weights are W[c][26 - t][n]).
+__global__ void k_image_f32(int wcout, int wcin, int transpose, const float* __restrict__ W,
+                            __nv_bfloat16* __restrict__ img) {
+  VOS_COUNT_EXEC();
+  const int cout = transpose ? wcin : wcout, cin = transpose ? wcout : wcin;
+  const long long n_el = conv_image_elems(cin, cout);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
+    int n, t, c;
+    image_decode(e, cout, n, t, c);
+    float v = 0.0f;
+    if (c < cin) v = transpose ? W[((long long)c * 27 + (26 - t)) * wcin + n] : W[((long long)n * 27 + t) * wcin + c];
+    img[e] = __float2bfloat16_rn(v);
+  }
+}
+// Image from BF16 weights w[cout][27][cin] (the standalone conv entry point).
+__global__ void k_image_bf16(int cout, int cin, const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ img) {
+  VOS_COUNT_EXEC();
+  const long long n_el = conv_image_elems(cin, cout);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
+    int n, t, c;
+    image_decode(e, cout, n, t, c);
+    img[e] = (c < cin) ? w[((long long)n * 27 + t) * cin + c] : __float2bfloat16_rn(0.0f);
+  }
+}
+
+// Implicit-GEMM convolution on the tensor cores.  A CTA owns an 8 x 16 x 1
+// output tile (M = 128 rows, row m = (x0 + m % 8, y0 + m / 8)).  K runs
+// over stages of 16 input channels.  For a stage, TMA brings the 10 x 18 x 3
+// input halo tile of each 8-channel group (two 4-D boxes; out-of-range
+// voxels arrive as zeros) into a plane laid out [z][y][x] with 16 bytes per
+// voxel, and one bulk copy brings the stage's weight image.  For tap
+// (dz, dy, dx) the A operand is the tile itself seen through a descriptor:
 // the 8 rows of a core matrix are 8 consecutive x voxels (128 contiguous
 // bytes), consecutive 8-row groups are consecutive y rows (SBO = 160 B), the
-// two K core matrices are the two channel groups (LBO = 8640 B), and the tap
-// shifts the start address.  So one stage costs one tile load and 27 MMAs
-// with no im2col copy.  The weights of a stage are [tap][C_out][16] in the
-// same canonical layout (SBO = 256 B between 8-channel row groups, LBO =
-// 128 B).  Stages are double buffered against the tensor core.
-__global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
+// two K core matrices are the two channel planes (LBO = 8704 B), and the tap
+// shifts the start address.  So a stage costs two TMA boxes, one bulk copy
+// and 27 MMAs, with no im2col copy and no loads issued by other threads.
+// One thread drives the pipeline: loads of stage c + 1 are in flight while
+// the tensor core works on stage c; a buffer is refilled once the commit of
+// the MMAs that read it has arrived.  The other threads join for the
+// epilogue (TMEM -> registers, bias, ReLU, stores).
+__global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a, const __grid_constant__ CUtensorMap tmx) {
   VOS_COUNT_EXEC();
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int bstage = 27 * a.cout * 32;
+  const int bstage = stage_b_bytes(a.cout);
   const int nbuf = conv_buffers(a.cin);
   unsigned char* sA = smem;
   unsigned char* sB = smem + nbuf * kStageA;
-  uint64_t* mbar = (uint64_t*)(sB + nbuf * bstage);
-  uint32_t* slot = (uint32_t*)(mbar + 2);
+  uint64_t* full = (uint64_t*)(sB + nbuf * bstage);
+  uint64_t* empty = full + 2;
+  uint32_t* slot = (uint32_t*)(empty + 2);
+  int* s_ok = (int*)(slot + 1);
   const uint32_t ncols = (uint32_t)tmem_cols(a.cout);
+  const int ncg = a.cin >> 3;          // 8-channel groups of the input
+  const int nst = conv_stages(a.cin);  // stages of 16 channels
 
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), ncols);
   if (tid == 0) {
-    tc::mbar_init(tc::smem_addr(&mbar[0]), 1);
-    tc::mbar_init(tc::smem_addr(&mbar[1]), 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(tc::smem_addr(&full[i]), 1);
+      tc::mbar_init(tc::smem_addr(&empty[i]), 1);
+    }
     tc::fence_mbar_init();
+  }
+  if (ncg & 1) {  // an odd channel count leaves the last stage's second plane empty: zero it
+    uint4* z = (uint4*)(sA + ((nst - 1) % nbuf) * kStageA + kPlaneA);
+    for (int e = tid; e < kPlaneA / 16; e += kTM) z[e] = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_proxy_async_smem();
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
-
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z;
-  const long long plane = (long long)a.nx * a.ny;
-  const int ncg = a.cin >> 3;           // 8-channel groups of the input
-  const int nst = conv_stages(a.cin);   // stages of 16 channels
-  const int K = 27 * a.cin;
-  const uint32_t idesc = tc::idesc_bf16_f32(kTM, a.cout);
-  uint32_t phase[2] = {0u, 0u};
-  bool ok = true;
 
-  for (int c = 0; c < nst; ++c) {
-    const int s = c % nbuf;
-    bool okw = true;
-    if (c >= nbuf) {  // the MMAs of stage c - nbuf must be done reading buffer s
-      okw = tc::mbar_wait(tc::smem_addr(&mbar[s]), phase[s], kWaitNs);
-      phase[s] ^= 1u;
-    }
-    unsigned char* A = sA + s * kStageA;
-    unsigned char* B = sB + s * bstage;
-    for (int e = tid; e < 2 * kHalo; e += kTM) {
-      const int kg = e / kHalo, hv = e - kg * kHalo;
-      const int xi = hv % kHX, yi = (hv / kHX) % kHY, zi = hv / (kHX * kHY);
-      const int gx = x0 - 1 + xi, gy = y0 - 1 + yi, gz = z0 - 1 + zi, cg = 2 * c + kg;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (cg < ncg && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
-        val = __ldg((const uint4*)(a.x + ((long long)gz * plane + (long long)gy * a.nx + gx) * a.cin + cg * 8));
-      *(uint4*)(A + kg * kPlaneA + hv * 16) = val;
-    }
-    for (int e = tid; e < 27 * a.cout * 2; e += kTM) {
-      const int kg = e & 1, n = (e >> 1) % a.cout, t = (e >> 1) / a.cout, cg = 2 * c + kg;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (cg < ncg) val = __ldg((const uint4*)(a.w + ((long long)n * 27 + t) * a.cin + cg * 8));
-      *(uint4*)(B + t * (a.cout * 32) + (n >> 3) * 256 + kg * 128 + (n & 7) * 16) = val;
-    }
-    tc::fence_proxy_async_smem();
-    if (!__syncthreads_and(okw ? 1 : 0)) {  // block-uniform: a wait ran out of time
-      ok = false;
-      break;
-    }
-    if (tid == 0) {
+  if (tid == 0) {
+    bool ok = true;
+    uint32_t fph[2] = {0u, 0u}, eph[2] = {0u, 0u};
+    const uint32_t idesc = tc::idesc_bf16_f32(kTM, a.cout);
+    auto issue = [&](int c) {
+      const int s = c % nbuf;
+      const uint32_t fb = tc::smem_addr(&full[s]);
+      const bool two = (2 * c + 1) < ncg;
+      tc::mbar_arrive_expect_tx(fb, (uint32_t)((two ? 2 : 1) * kBoxBytes + bstage));
+      const uint32_t A = tc::smem_addr(sA + s * kStageA);
+      tc::tma_load_4d(A, &tmx, 16 * c, x0 - 1, y0 - 1, z0 - 1, fb);
+      if (two) tc::tma_load_4d(A + kPlaneA, &tmx, 16 * c + 8, x0 - 1, y0 - 1, z0 - 1, fb);
+      const unsigned char* src = (const unsigned char*)a.img + (size_t)c * bstage;
+      const uint32_t B = tc::smem_addr(sB + s * bstage);
+      for (int off = 0; off < bstage; off += kBulkChunk) {
+        const int n = (bstage - off) < kBulkChunk ? (bstage - off) : kBulkChunk;
+        tc::bulk_load(B + off, src + off, (uint32_t)n, fb);
+      }
+    };
+    issue(0);
+    if (nst > 1) issue(1);
+    for (int c = 0; c < nst && ok; ++c) {
+      const int s = c % nbuf;
+      ok = tc::mbar_wait(tc::smem_addr(&full[s]), fph[s], kWaitNs);
+      fph[s] ^= 1u;
+      if (!ok) break;
       tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
+      const uint32_t a0 = tc::smem_addr(sA + s * kStageA), b0 = tc::smem_addr(sB + s * bstage);
       for (int t = 0; t < 27; ++t) {
         const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;  // halo offsets 0..2
         const uint64_t ad = tc::desc_kmajor(a0 + (uint32_t)(((dz * kHY + dy) * kHX + dx) * 16), kPlaneA, kHX * 16);
         const uint64_t bd = tc::desc_kmajor(b0 + (uint32_t)(t * a.cout * 32), 128, 256);
         tc::mma_bf16(tmem, ad, bd, idesc, (c > 0 || t > 0) ? 1u : 0u);
       }
-      tc::commit(tc::smem_addr(&mbar[s]));
+      tc::commit(tc::smem_addr(&empty[s]));
+      if (c + nbuf < nst) {  // refill buffer s once the MMAs just issued have read it
+        ok = tc::mbar_wait(tc::smem_addr(&empty[s]), eph[s], kWaitNs);
+        eph[s] ^= 1u;
+        if (ok) issue(c + nbuf);
+      }
     }
+    // the last commit of each buffer: all MMAs done, no arrival left pending
+    for (int s = 0; s < nbuf && ok; ++s)
+      if (nst > s) ok = tc::mbar_wait(tc::smem_addr(&empty[(nst - 1 - s) % nbuf]), eph[(nst - 1 - s) % nbuf], kWaitNs);
+    *s_ok = ok ? 1 : 0;
+    if (!ok) atomicExch(&g_tc_timeout, 1);
   }
-  (void)K;
-  // Wait for the last stage's MMAs (a commit tracks all earlier MMAs of the
-  // issuing thread) and for the other buffer's outstanding arrival.
-  if (ok) {
-    const int sl = (nst - 1) % nbuf;
-    ok = tc::mbar_wait(tc::smem_addr(&mbar[sl]), phase[sl], kWaitNs);
-    if (ok && nst >= 2) ok = tc::mbar_wait(tc::smem_addr(&mbar[sl ^ 1]), phase[sl ^ 1], kWaitNs);
-  }
-  ok = __syncthreads_and(ok ? 1 : 0) != 0;
-  if (!ok) {
-    if (tid == 0) atomicExch(&g_tc_timeout, 1);
-  } else {
+  __syncthreads();
+  if (*s_ok) {
     tc::fence_after_sync();
     const int m = tid;  // TMEM lane of this thread = output row
     const int ox = x0 + (m & 7), oy = y0 + (m >> 3);
     const bool vin = ox < a.nx && oy < a.ny;
-    const long long v = (long long)z0 * plane + (long long)oy * a.nx + ox;
+    const long long v = (long long)z0 * ((long long)a.nx * a.ny) + (long long)oy * a.nx + ox;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     for (int n0 = 0; n0 < a.cout; n0 += 16) {
       uint32_t r[16];
@@ -209,7 +265,32 @@ __global__ void __launch_bounds__(kTM) k_conv3d_tc(ConvArgs a) {
   }
 }
 
-// Host launcher: y = conv3(x, w) (+ bias, ReLU).  Returns a CUDA error.
+// TMA descriptor of a channels-last BF16 tensor [nz][ny][nx][cin] with
+// boxes of 8 channels x 10 x 18 x 3 voxels (the encoder comes from the
+// driver through the runtime, so no driver library is linked).
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
+static cudaError_t make_input_map(CUtensorMap* m, const ConvArgs& a) {
+  if (!g_encode_tiled) {
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&g_encode_tiled, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !g_encode_tiled) {
+      g_encode_tiled = nullptr;
+      return e != cudaSuccess ? e : cudaErrorNotSupported;
+    }
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz};
+  const cuuint64_t strides[3] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.cin * 2 * a.nx,
+                                 (cuuint64_t)a.cin * 2 * a.nx * a.ny};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kHX, (cuuint32_t)kHY, 3};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = g_encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)a.x, dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Host launcher: y = conv3(x, w) (+ bias, ReLU), w given as its image.
 cudaError_t conv3d(const ConvArgs& a, cudaStream_t st) {
   static bool attr_done = false;
   if (!attr_done) {
@@ -219,10 +300,22 @@ cudaError_t conv3d(const ConvArgs& a, cudaStream_t st) {
     attr_done = true;
   }
   if (a.V <= 0) return cudaSuccess;
+  alignas(64) CUtensorMap tm;
+  VOS_CUDA_TRY(make_input_map(&tm, a));
   const dim3 grid((unsigned)((a.nx + kTX - 1) / kTX), (unsigned)((a.ny + kTY - 1) / kTY), (unsigned)a.nz);
   const double flops = 2.0 * 27.0 * a.cin * a.cout * (double)a.V;
-  vlaunch_smem("unet_conv", flops, k_conv3d_tc, grid, dim3(kTM), conv_smem_bytes(a.cin, a.cout), st, a);
+  vlaunch_smem("unet_conv", flops, k_conv3d_tc, grid, dim3(kTM), conv_smem_bytes(a.cin, a.cout), st, a, tm);
   return cudaGetLastError();
+}
+
+// Build the weight image of a forward (transpose = 0) or data-gradient
+// (transpose = 1) conv from FP32 weights.
+void conv_image(int wcout, int wcin, int transpose, const float* W, __nv_bfloat16* img, cudaStream_t st) {
+  const int cout = transpose ? wcin : wcout, cin = transpose ? wcout : wcin;
+  const long long n = conv_image_elems(cin, cout);
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b > 4096) b = 4096;
+  vlaunch("unet_image", 0.0, k_image_f32, (int)b, kThreads, st, wcout, wcin, transpose, W, img);
 }
 
 bool conv_shape_ok(int cin, int cout) {
@@ -592,20 +685,6 @@ __global__ void k_split_skip(long long V, int Cu, int Cs, const float* __restric
   }
 }
 
-// FP32 master weights W [o][tap][i] -> BF16 W16 (same layout) and the
-// flipped transpose WT16 [i][26 - tap][o] used by the data gradient.
-__global__ void k_prep_w(int Cout, int Cin, const float* __restrict__ W, __nv_bfloat16* __restrict__ W16,
-                         __nv_bfloat16* __restrict__ WT16) {
-  VOS_COUNT_EXEC();
-  const long long n = 27LL * Cout * Cin;
-  UNET_LOOP(e, n) {
-    const int i = (int)(e % Cin), tap = (int)((e / Cin) % 27), o = (int)(e / (27LL * Cin));
-    const __nv_bfloat16 h = __float2bfloat16_rn(W[e]);
-    W16[e] = h;
-    if (WT16) WT16[((long long)i * 27 + (26 - tap)) * Cout + o] = h;
-  }
-}
-
 // Adam (bias-corrected moments) on a flat parameter range.
 __global__ void k_adam(long long n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -693,9 +772,9 @@ constexpr LayerSpec kSpec[10] = {{2, 16, 0},  {16, 16, 0}, {16, 32, 1}, {32, 32,
 enum { ENC1A, ENC1B, ENC2A, ENC2B, ENC3A, ENC3B, DEC2A, DEC2B, DEC1A, DEC1B };
 
 struct Layer {
-  int cin, cing, cout, lev;
+  int li, cin, cing, cout, lev;
   float *W, *b, *gW, *gb, *mW, *vW, *mb, *vb;  // W: [cout][27][cing]
-  __nv_bfloat16 *W16, *WT16, *out;             // out: [V_lev][cout] after ReLU
+  __nv_bfloat16 *img, *imgT, *out;             // weight images (forward, data gradient); out: [V_lev][cout]
 };
 
 long long num_params() {
@@ -752,7 +831,7 @@ static ConvArgs conv_args(const vos_unet* u, int lev, const __nv_bfloat16* x, in
                           const float* bias, int cout, int relu, float* yf, __nv_bfloat16* yb) {
   ConvArgs a;
   a.x = x;
-  a.w = w;
+  a.img = w;
   a.bias = bias;
   a.yf = yf;
   a.yb = yb;
@@ -769,8 +848,9 @@ static ConvArgs conv_args(const vos_unet* u, int lev, const __nv_bfloat16* x, in
 static void prep_weights(vos_unet* u) {
   for (auto& l : u->L) {
     const long long n = 27LL * l.cout * l.cing;
-    vlaunch("unet_prep_w", 0.0, k_prep_w, ugrid(n), kThreads, u->st, l.cout, l.cing, (const float*)l.W, l.W16,
-            l.WT16);
+    (void)n;
+    conv_image(l.cout, l.cing, 0, l.W, l.img, u->st);
+    if (l.li > 0) conv_image(l.cout, l.cing, 1, l.W, l.imgT, u->st);
   }
 }
 
@@ -786,7 +866,7 @@ static cudaError_t forward(vos_unet* u, const T* r, const double* eps, const dou
   Layer* L = u->L;
   auto conv = [&](int li, const __nv_bfloat16* x) -> cudaError_t {
     Layer& l = L[li];
-    return conv3d(conv_args(u, l.lev, x, l.cing, l.W16, l.b, l.cout, 1, nullptr, l.out), st);
+    return conv3d(conv_args(u, l.lev, x, l.cing, l.img, l.b, l.cout, 1, nullptr, l.out), st);
   };
   VOS_CUDA_TRY(conv(ENC1A, u->x0));
   VOS_CUDA_TRY(conv(ENC1B, L[ENC1A].out));
@@ -826,7 +906,7 @@ static cudaError_t layer_backward(vos_unet* u, int li, const __nv_bfloat16* xin,
           (const float*)u->part_dw, l.gW);
   vlaunch("unet_db", 0.0, k_db, u->ndb, kThreads, st, V, l.cout, (const float*)u->gpre, u->part_db);
   vlaunch("unet_db_reduce", 0.0, k_db_reduce, 1, 64, st, u->ndb, l.cout, (const float*)u->part_db, l.gb);
-  if (g_in) VOS_CUDA_TRY(conv3d(conv_args(u, l.lev, u->gpre16, l.cout, l.WT16, nullptr, l.cing, 0, g_in, nullptr), st));
+  if (g_in) VOS_CUDA_TRY(conv3d(conv_args(u, l.lev, u->gpre16, l.cout, l.imgT, nullptr, l.cing, 0, g_in, nullptr), st));
   return cudaGetLastError();
 }
 
@@ -957,8 +1037,9 @@ static vos_unet* create_net(int px, int py, int pz, bool train, cudaStream_t st)
     const long long nw = 27LL * l.cout * l.cing;
     l.W = (float*)A(nw * 4);
     l.b = (float*)A(l.cout * 4);
-    l.W16 = (__nv_bfloat16*)A(nw * 2);
-    l.WT16 = (__nv_bfloat16*)A(nw * 2);
+    l.li = i;
+    l.img = (__nv_bfloat16*)A(conv_image_elems(l.cing, l.cout) * 2);
+    l.imgT = (__nv_bfloat16*)A(conv_image_elems(l.cout, l.cing) * 2);
     l.out = (__nv_bfloat16*)A((size_t)u->V[l.lev] * l.cout * 2);
     l.gW = (float*)A(nw * 4);
     l.gb = (float*)A(l.cout * 4);
@@ -1058,9 +1139,25 @@ int vos_conv3d_bf16(const uint16_t* x, int32_t nx, int32_t ny, int32_t nz, int32
     set_global_error("vos_conv3d_bf16: bad argument (cin a multiple of 8, cout a multiple of 16 in [16, 96])");
     return VOS_EINVAL;
   }
+  // the kernel reads the weights in its shared-memory image layout: build
+  // that in a temporary buffer
+  __nv_bfloat16* img = nullptr;
+  const long long nimg = unet::conv_image_elems(cin, cout);
+  if (cudaMalloc((void**)&img, (size_t)nimg * 2) != cudaSuccess) {
+    cudaGetLastError();
+    set_global_error("vos_conv3d_bf16: device allocation failed");
+    return VOS_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  {
+    long long b = (nimg + kThreads - 1) / kThreads;
+    if (b > 4096) b = 4096;
+    vlaunch("unet_image", 0.0, unet::k_image_bf16, (int)b, kThreads, st, (int)cout, (int)cin,
+            (const __nv_bfloat16*)w, img);
+  }
   unet::ConvArgs a;
   a.x = (const __nv_bfloat16*)x;
-  a.w = (const __nv_bfloat16*)w;
+  a.img = img;
   a.bias = bias;
   a.yf = y_f32;
   a.yb = (__nv_bfloat16*)y_bf16;
@@ -1071,9 +1168,9 @@ int vos_conv3d_bf16(const uint16_t* x, int32_t nx, int32_t ny, int32_t nz, int32
   a.cout = cout;
   a.relu = relu ? 1 : 0;
   a.V = (long long)nx * ny * nz;
-  cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = unet::conv3d(a, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(img);
   if (e != cudaSuccess) {
     set_global_error(cudaGetErrorString(e));
     return VOS_ECUDA;
