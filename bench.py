@@ -137,6 +137,12 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# DRAM bytes per algorithmic byte of the fine-level FP32 Jacobi sweep, from one
+# ncu capture of the 128^3 rock (profiles/mg_jac_f32_L0_traffic_rock128.md):
+# 23.94 B/cell read against 28 B/cell algorithmic (the output stays in L2).
+JAC_TRAFFIC_PER_ALG_BYTE = 23.94 / 28.0
+
+
 def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
     """Create, warm up, take a per-kernel breakdown of one untimed step, then
     time ``steps`` steps with CUDA events while timing the dominant kernel's
@@ -205,10 +211,13 @@ def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
             peak, src = measured_peaks()
             if n > 0 and kms > 0:
                 ach = kbytes / (kms * 1e-3) / 1e9
+                traffic = kbytes / n * JAC_TRAFFIC_PER_ALG_BYTE if top.startswith("mg_jac_f32") else None
                 roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                        "traffic": None, "kernel": top, "launches": n, "avg_launch_us": kms * 1e3 / n,
+                        "traffic": traffic, "kernel": top, "launches": n, "avg_launch_us": kms * 1e3 / n,
                         "alg_bytes_per_launch": kbytes / n, "peak_source": src,
-                        "window": "steps after the timed ones, same handle and dt, kernel launches event-timed"}
+                        "window": "steps after the timed ones, same handle and dt, kernel launches event-timed",
+                        "traffic_source": ("ncu dram bytes of the 128^3 capture scaled by units processed"
+                                           if traffic is not None else None)}
         tiles = {}
         for lev in (0, 1):
             try:

@@ -243,6 +243,19 @@ def test_unet_training_reduces_loss(env):
         l1 = [net.eval_loss(h, snaps[i]) for i in range(3)]
         print("loss before", l0, "after", l1)
         assert np.mean(l1) < 0.5 * np.mean(l0), (l0, l1)
+        # what training gains on residuals it has not seen (a later step):
+        # the trained network against the same network untrained
+        assert V.vos_step(h, 0.05) == 0
+        V.vos_pressure_snapshots(h, [0, 6, 15], snaps)
+        fresh = V.UNet((n, n, n), train=True)
+        try:
+            fresh.set_params(flat_params(random_params(3)))
+            lu = [fresh.eval_loss(h, snaps[i]) for i in range(3)]
+        finally:
+            fresh.close()
+        lt = [net.eval_loss(h, snaps[i]) for i in range(3)]
+        print("held-out loss untrained", lu, "trained", lt)
+        assert np.mean(lt) < 0.6 * np.mean(lu), (lu, lt)
     finally:
         net.close()
         V.vos_destroy(h)
