@@ -1,11 +1,18 @@
 // Batched stepping of many independent simulations (e.g. micromodels of
-// uneven sizes).  Each instance owns a non-blocking CUDA stream and is
-// advanced by one of a pool of host worker threads, so the GPU overlaps the
-// instances' (mostly latency-bound) kernels and the host-side solver polls
-// of different instances run concurrently.  A batch step is fenced on the
-// caller's stream: every instance stream waits for an event recorded there
-// first, and the caller's stream waits for every instance at the end, so
-// CUDA events on the caller's stream time the whole batch step.
+// uneven sizes).  In the default (graph) launch mode a batch step is ONE
+// CUDA-graph launch: the steps of all instances are captured once into a
+// single graph as parallel branches (each branch the instance's own step,
+// with its device-driven refinement and Krylov WHILE loops), forked from and
+// joined into one capture stream; the per-instance time steps are scattered
+// into the instances' device dt slots by one kernel before the launch.  The
+// graph is captured again only when an instance's momentum-preconditioner
+// choice (it depends on dt) or its captured parameters (geometry reset by
+// vos_set_fields, a network attached) change.  In the eager launch mode, or
+// when an instance has a learned preconditioner attached, each instance is
+// advanced by one of a pool of host worker threads on its own stream.  A
+// batch step is fenced on the caller's stream in both modes, so CUDA events
+// on the caller's stream time the whole batch step.
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <mutex>
@@ -18,7 +25,28 @@
 
 namespace vos {
 void set_global_error(const char* msg);
+bool graphs_enabled();
+bool batch_graphable(const vos_handle* h);
+unsigned batch_generation(const vos_handle* h);
+int batch_key(const vos_handle* h, double dt);
+double* batch_dt_slot(vos_handle* h);
+cudaError_t batch_enqueue(vos_handle* h, int key, cudaEvent_t fork, cudaEvent_t* join);
+int batch_finish(vos_handle* h, double dt);
+
+static __device__ unsigned long long vos_exec_count = 0;
+__global__ void k_scatter_dt(int n, const double* __restrict__ dt, double* const* __restrict__ slot) {
+  VOS_COUNT_EXEC();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) *slot[i] = dt[i];
 }
+unsigned long long exec_count_batch() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, vos_exec_count, sizeof(v));
+  return v;
+}
+}  // namespace vos
+
+using namespace vos;
 
 struct vos_batch {
   int n;
@@ -35,6 +63,14 @@ struct vos_batch {
   std::vector<int> status;
   int next = 0, finished = 0;
   bool quit = false;
+  // single-graph path
+  cudaStream_t cap = nullptr;          // capture / launch stream
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int> gkey;               // momentum-preconditioner choice per instance
+  std::vector<unsigned> ggen;          // captured generation per instance
+  double* h_dt = nullptr;              // pinned, n
+  double* d_dt = nullptr;              // device, n
+  double** d_slot = nullptr;           // device, n: each instance's dt slot
 };
 
 namespace {
@@ -62,11 +98,83 @@ void destroy_batch(vos_batch* b) {
   }
   b->cv_work.notify_all();
   for (auto& t : b->workers) t.join();
+  if (b->cap) cudaStreamSynchronize(b->cap);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
   for (auto* h : b->h) vos_destroy(h);
   for (auto e : b->done) cudaEventDestroy(e);
   for (auto s : b->streams) cudaStreamDestroy(s);
   if (b->start) cudaEventDestroy(b->start);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->h_dt) cudaFreeHost(b->h_dt);
+  if (b->d_dt) cudaFree(b->d_dt);
+  if (b->d_slot) cudaFree(b->d_slot);
   delete b;
+}
+
+// Capture the steps of all instances into one graph (keys: momentum
+// preconditioner per instance).
+cudaError_t capture_batch(vos_batch* b, const std::vector<int>& key) {
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  VOS_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+  cudaError_t err = cudaEventRecord(b->start, b->cap);
+  for (int i = 0; i < b->n && err == cudaSuccess; ++i) {
+    cudaEvent_t join = nullptr;
+    err = batch_enqueue(b->h[i], key[i], b->start, &join);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(b->cap, join, 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+  if (err == cudaSuccess) err = e2;
+  if (err == cudaSuccess && g) err = cudaGraphInstantiate(&b->gexec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (err != cudaSuccess) {
+    b->gexec = nullptr;
+    cudaGetLastError();
+    return err;
+  }
+  b->gkey = key;
+  b->ggen.resize(b->n);
+  for (int i = 0; i < b->n; ++i) b->ggen[i] = batch_generation(b->h[i]);
+  return cudaSuccess;
+}
+
+int batch_step_graph(vos_batch* b, const double* dt) {
+  std::vector<int> key(b->n);
+  bool same = b->gexec != nullptr && (int)b->gkey.size() == b->n;
+  for (int i = 0; i < b->n; ++i) {
+    key[i] = batch_key(b->h[i], dt[i]);
+    if (same && (key[i] != b->gkey[i] || b->ggen[i] != batch_generation(b->h[i]))) same = false;
+  }
+  if (!same) {
+    cudaError_t e = capture_batch(b, key);
+    if (e != cudaSuccess) {
+      vos::set_global_error((std::string("vos_batch_step: graph capture failed: ") + cudaGetErrorString(e)).c_str());
+      return VOS_ECUDA;
+    }
+  }
+  std::memcpy(b->h_dt, dt, b->n * sizeof(double));
+  cudaEventRecord(b->start, b->main);
+  cudaStreamWaitEvent(b->cap, b->start, 0);
+  cudaMemcpyAsync(b->d_dt, b->h_dt, b->n * sizeof(double), cudaMemcpyHostToDevice, b->cap);
+  vlaunch("batch_dt", 0.0, k_scatter_dt, (b->n + 127) / 128, 128, b->cap, b->n, (const double*)b->d_dt,
+          (double* const*)b->d_slot);
+  cudaGraphLaunch(b->gexec, b->cap);
+  cudaEventRecord(b->done[0], b->cap);
+  cudaStreamWaitEvent(b->main, b->done[0], 0);
+  cudaError_t e = cudaStreamSynchronize(b->cap);
+  if (e != cudaSuccess) {
+    vos::set_global_error((std::string("vos_batch_step: ") + cudaGetErrorString(e)).c_str());
+    return VOS_ECUDA;
+  }
+  int worst = VOS_OK;
+  for (int i = 0; i < b->n; ++i) {
+    const int rc = batch_finish(b->h[i], dt[i]);
+    if (rc != VOS_OK && (worst == VOS_OK || worst == VOS_ENOCONV)) worst = rc;
+  }
+  return worst;
 }
 
 }  // namespace
@@ -117,6 +225,23 @@ int vos_batch_create(int n, const double* const* eps_s, const vos_params* prm, v
     }
     b->h.push_back(h);
   }
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&b->h_dt, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_dt, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_slot, n * sizeof(double*)) != cudaSuccess) {
+    vos::set_global_error("vos_batch_create: stream or buffer allocation failed");
+    destroy_batch(b);
+    return VOS_ECUDA;
+  }
+  {
+    std::vector<double*> slots(n);
+    for (int i = 0; i < n; ++i) slots[i] = batch_dt_slot(b->h[i]);
+    if (cudaMemcpy(b->d_slot, slots.data(), n * sizeof(double*), cudaMemcpyHostToDevice) != cudaSuccess) {
+      vos::set_global_error("vos_batch_create: cudaMemcpy failed");
+      destroy_batch(b);
+      return VOS_ECUDA;
+    }
+  }
   int nt = nthreads > 0 ? nthreads : 8;
   if (nt > n) nt = n;
   for (int t = 0; t < nt; ++t) b->workers.emplace_back(worker, b);
@@ -130,10 +255,13 @@ int vos_batch_step(vos_batch* b, const double* dt) {
     return VOS_EINVAL;
   }
   for (int i = 0; i < b->n; ++i)
-    if (!(dt[i] > 0.0)) {
-      vos::set_global_error("vos_batch_step: every dt must be > 0");
+    if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) {
+      vos::set_global_error("vos_batch_step: every dt must be finite and > 0");
       return VOS_EINVAL;
     }
+  bool graph = graphs_enabled();
+  for (int i = 0; i < b->n && graph; ++i) graph = batch_graphable(b->h[i]);
+  if (graph) return batch_step_graph(b, dt);
   cudaEventRecord(b->start, b->main);
   for (int i = 0; i < b->n; ++i) cudaStreamWaitEvent(b->streams[i], b->start, 0);
   {

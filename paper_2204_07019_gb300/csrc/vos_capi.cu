@@ -70,6 +70,7 @@ struct vos_handle {
   cudaEvent_t ev_in, ev_out;
   cudaGraphExec_t exec[2];
   vos_unet* net;       // learned pressure preconditioner (not owned)
+  unsigned graph_gen;  // bumped whenever captured launch parameters change
   int net_iters, net_fallback;
   vos_stats stats;
   std::string err;
@@ -323,6 +324,11 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
 }
 
 template <typename T>
+int finish_graph_step(vos_handle* h, Sys<T>* S, double dt);
+
+bool mom_mg_for(const Phys& P, double dt) { return 2.0 * P.dim * P.nu * dt / (P.dx * P.dx) > 30.0; }
+
+template <typename T>
 int step_graph(vos_handle* h, Sys<T>* S, double dt) {
   const Phys& P = h->ph;
   const bool mom_mg = 2.0 * P.dim * P.nu * dt / (P.dx * P.dx) > 30.0;
@@ -354,6 +360,14 @@ int step_graph(vos_handle* h, Sys<T>* S, double dt) {
   cudaStreamWaitEvent(h->st, h->ev_out, 0);
   cudaError_t e = cudaStreamSynchronize(h->gs);
   if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_step: %s", cudaGetErrorString(e));
+  return finish_graph_step<T>(h, S, dt);
+}
+
+// Host side of a graph-replayed step once its graph has run: the solver
+// statistics from the pinned copy the graph wrote.
+template <typename T>
+int finish_graph_step(vos_handle* h, Sys<T>* S, double dt) {
+  const Phys& P = h->ph;
   vos_stats& s = h->stats;
   int status = VOS_OK;
   for (int a = 0; a < 3; ++a) {
@@ -382,6 +396,7 @@ void drop_graphs(vos_handle* h) {
     if (h->exec[i]) cudaGraphExecDestroy(h->exec[i]);
     h->exec[i] = nullptr;
   }
+  h->graph_gen += 1;  // graphs that captured this handle elsewhere (batch) are stale too
 }
 
 // Label the floating pore clusters of the pressure operator for the host
@@ -502,6 +517,7 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
   h->defl_cap = 0;
   h->defl = Defl{0, nullptr, nullptr, nullptr};
   h->net = nullptr;
+  h->graph_gen = 0;
   h->net_iters = h->net_fallback = 0;
   std::memset(&h->stats, 0, sizeof(h->stats));
   cudaGetDevice(&h->dev);
@@ -788,6 +804,7 @@ int vos_set_unet_preconditioner(vos_handle* h, vos_unet* net) {
     unet_attach_eps(net, h->eps);
   }
   h->net = net;
+  h->graph_gen += 1;
   h->sd[3].h.net = net;
   h->sf[3].h.net = net;
   return VOS_OK;
@@ -846,4 +863,32 @@ const Op<double>* handle_pressure_op(vos_handle* h) {
   return h->prm.precision == VOS_FP64 ? &h->sd[3].op64 : &h->sf[3].op64;
 }
 const double* handle_eps(vos_handle* h) { return h ? h->eps : nullptr; }
+}  // namespace vos
+
+// ---------------------------------------------------------------------------
+// Batch support (vos_batch.cu): one CUDA graph holding the steps of many
+// handles as parallel branches.
+// ---------------------------------------------------------------------------
+namespace vos {
+bool graphs_enabled() { return g_use_graphs && !g_prof_any; }
+bool batch_graphable(const vos_handle* h) { return h->net == nullptr; }
+unsigned batch_generation(const vos_handle* h) { return h->graph_gen; }
+int batch_key(const vos_handle* h, double dt) { return mom_mg_for(h->ph, dt) ? 1 : 0; }
+double* batch_dt_slot(vos_handle* h) { return h->d_dt; }
+// Enqueue h's step on its internal stream inside an active capture: fork
+// from `fork` (recorded on the capture's origin stream), join into `join`,
+// which the origin then waits for.
+cudaError_t batch_enqueue(vos_handle* h, int key, cudaEvent_t fork, cudaEvent_t* join) {
+  VOS_CUDA_TRY(cudaStreamWaitEvent(h->gs, fork, 0));
+  cudaError_t e = (h->prm.precision == VOS_FP64) ? enqueue_step<double>(h, h->sd, key != 0)
+                                                 : enqueue_step<float>(h, h->sf, key != 0);
+  if (e != cudaSuccess) return e;
+  VOS_CUDA_TRY(cudaEventRecord(h->ev_out, h->gs));
+  *join = h->ev_out;
+  return cudaSuccess;
+}
+int batch_finish(vos_handle* h, double dt) {
+  return (h->prm.precision == VOS_FP64) ? finish_graph_step<double>(h, h->sd, dt)
+                                        : finish_graph_step<float>(h, h->sf, dt);
+}
 }  // namespace vos

@@ -18,8 +18,9 @@ unsigned long long exec_count_solver();
 unsigned long long exec_count_fields();
 unsigned long long exec_count_deflate();
 unsigned long long exec_count_unet();
+unsigned long long exec_count_batch();
 unsigned long long exec_count_sum() {
-  return exec_count_solver() + exec_count_fields() + exec_count_deflate() + exec_count_unet();
+  return exec_count_solver() + exec_count_fields() + exec_count_deflate() + exec_count_unet() + exec_count_batch();
 }
 bool g_prof_any = false;
 
