@@ -52,6 +52,7 @@ struct vos_handle {
   Defl defl;
   // fields
   double *eps, *eps_old, *c, *p, *phi, *R, *Rf, *kr;
+  float* eps32;  // FP32 fluid fraction for the matrix-free pressure sweeps (mixed precision)
   double *u[3], *us[3];
   FaceData fd[3];
   // solvers: 0..2 momentum, 3 pressure, 4 transport
@@ -241,7 +242,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     if (!r.converged) status = VOS_ENOCONV;
   }
   // S3: pressure correction, projection
-  launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, st);
+  launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, h->eps32, st);
   launch_defl_energy(S[3].h.defl, S[3].op64, st);
   cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st);
   {
@@ -301,7 +302,7 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
     VOS_CUDA_TRY(solve_capture<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
                                   h->work, h->rs, st, mom_mg, h->dsolve + a, h->gs1, h->gs2));
   }
-  launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, st);
+  launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, h->eps32, st);
   launch_defl_energy(S[3].h.defl, S[3].op64, st);
   VOS_CUDA_TRY(cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st));
   VOS_CUDA_TRY(solve_capture<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter,
@@ -551,6 +552,12 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
       if (!h->fd[a].s || !h->fd[a].corr || !h->fd[a].evl) return fail(VOS_ENOMEM, "device allocation failed (iVoS)");
     }
   }
+  h->eps32 = nullptr;
+  if (prm->precision != VOS_FP64) {
+    h->eps32 = (float*)dev_alloc(h, (size_t)N * sizeof(float));
+    if (!h->eps32) return fail(VOS_ENOMEM, "device allocation failed (eps32)");
+    cudaMemsetAsync(h->eps32, 0, (size_t)N * sizeof(float), h->st);
+  }
   const int trans_sym = (prm->method == VOS_IVOS) ? 0 : 1;
   for (int sys = 0; sys < 5; ++sys) {
     if (sys < 3 && sys >= P.dim) {
@@ -562,6 +569,10 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     bool ok = (prm->precision == VOS_FP64) ? alloc_sys<double>(h, h->sd[sys], sys, sym)
                                            : alloc_sys<float>(h, h->sf[sys], sys, sym);
     if (!ok) return fail(VOS_ENOMEM, "device allocation failed (solver)");
+  }
+  if (h->eps32 && h->sf[3].h.nlev > 0) {  // the FP32 pressure fine level runs matrix-free
+    h->sf[3].h.lev[0].op.mfe = h->eps32;
+    h->sf[3].h.lev[0].op.mfs = (float)(1.0 / (P.dx * P.dx));
   }
   {
     long long maxc = 0;

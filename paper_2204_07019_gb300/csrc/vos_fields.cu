@@ -193,7 +193,7 @@ void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* 
 __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const double* __restrict__ u0,
                                 const double* __restrict__ u1, const double* __restrict__ u2,
                                 const double* __restrict__ R, const double* __restrict__ dtp, double omega, Op<double> A,
-                                double* __restrict__ rhs) {
+                                double* __restrict__ rhs, float* __restrict__ eps32) {
   VOS_COUNT_EXEC();
   const double dt = *dtp;
   const Box bx{P.nx, P.ny, P.nz};
@@ -226,6 +226,7 @@ __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const do
     const double src = R[c] * P.Vm * (1.0 - P.rho_ratio);
     A.diag[c] = diag;
     A.dinv[c] = omega / diag;
+    if (eps32) eps32[c] = (float)e;  // the matrix-free FP32 form of this operator
     A.xp[c] = off[0];
     A.yp[c] = off[1];
     if (A.zp) A.zp[c] = off[2];
@@ -234,8 +235,8 @@ __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const do
 }
 
 void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3], const double* R, const double* __restrict__ dtp,
-                          double omega, Op<double> A, double* rhs, cudaStream_t st) {
-  vlaunch("pres_assemble", (5.0 + 2.0 * P.dim) * 8.0 * box_cells(A.box), k_pres_assemble, grid_for(A.box, 0), kThreads, st, P, eps, us[0], us[1], us[2], R, dtp, omega, A, rhs);
+                          double omega, Op<double> A, double* rhs, float* eps32, cudaStream_t st) {
+  vlaunch("pres_assemble", (5.0 + 2.0 * P.dim) * 8.0 * box_cells(A.box), k_pres_assemble, grid_for(A.box, 0), kThreads, st, P, eps, us[0], us[1], us[2], R, dtp, omega, A, rhs, eps32);
 }
 
 // u^{n+1} = u* - dt eps_f grad phi on interior faces and the outlet face;

@@ -86,6 +86,12 @@ struct Op {
   Box box;
   int sym;
   T *diag, *dinv, *xp, *yp, *zp, *xm, *ym, *zm;
+  // Matrix-free form of the pressure operator (FP32 fine level only): when
+  // mfe is set, stencil sweeps compute the links from the fluid fraction,
+  // a_cn = 0.5 (e_c + e_n) mfs, diag = sum of the links + 2 e_c mfs on the
+  // outlet column (i = mx - 1), instead of reading diag/xp/yp/zp.
+  const float* mfe;
+  float mfs;
 };
 
 // Work split: a warp handles one 32-cell row segment along x; blocks stride

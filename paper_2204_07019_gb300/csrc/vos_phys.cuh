@@ -38,8 +38,10 @@ void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double
 void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, const double* dtp,
                          double omega, Op<double> A, double* rhs, cudaStream_t st);
 // S3
+// eps32 (may be NULL): receives the FP32 fluid fraction that the matrix-free
+// FP32 pressure sweeps read.
 void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3], const double* R, const double* dtp,
-                          double omega, Op<double> A, double* rhs, cudaStream_t st);
+                          double omega, Op<double> A, double* rhs, float* eps32, cudaStream_t st);
 void launch_project(const Phys& P, const double* eps, const double* phi, const double* dtp, double* const us[3],
                     double* const u[3], double* p, cudaStream_t st);
 // S5/S6

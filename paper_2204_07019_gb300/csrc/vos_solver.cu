@@ -180,7 +180,7 @@ __device__ __forceinline__ void zmarch(const Op<T>& A, int zc, VAL val, EMIT emi
 //           FP32, read from dinv for FP64)
 //   SK_MV:  out = A x
 //   SK_RES: out = b - A x
-enum StencilKind { SK_JAC = 0, SK_MV = 1, SK_RES = 2 };
+enum StencilKind { SK_JAC = 0, SK_MV = 1, SK_RES = 2, SK_JAC0 = 3 };
 
 template <typename T, bool SYM, int KIND>
 __global__ void __launch_bounds__(kThreads) k_stencil(Op<T> A, const T* __restrict__ b, const T* __restrict__ x,
@@ -236,6 +236,84 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Op<T> A, const T* __restri
 }
 
 // First Jacobi sweep from zero: x = (omega / diag) b.
+// Matrix-free FP32 sweeps of the pressure operator (Op::mfe): the same z
+// march as k_stencil, but the links and the diagonal are formed from the
+// fluid fraction e in registers, a_cn = 0.5 (e_c + e_n) s, so a sweep reads
+// one coefficient word per cell instead of four.  KIND as in k_stencil, plus
+// SK_JAC0: out = (omega / diag) b (the first sweep from zero).
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) k_stencil_mf(Box bx, const float* __restrict__ e, float s,
+                                                        const float* __restrict__ b, const float* __restrict__ x,
+                                                        float* __restrict__ out, float omega, int zc, const KScal* sc) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  if (i >= bx.mx || j >= bx.my || k0 >= k1) return;
+  const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+  const float hs = 0.5f * s;
+  const bool has_x = KIND != SK_JAC0;
+  long long c = i + sy * j + sz * k0;
+  float elo = (k0 > 0) ? __ldg(e + c - sz) : 0.0f;
+  float ec = __ldg(e + c);
+  float vlo = (has_x && k0 > 0) ? __ldg(x + c - sz) : 0.0f;
+  float vc = has_x ? __ldg(x + c) : 0.0f;
+  for (int k = k0; k < k1; ++k, c += sz) {
+    const bool up = (k + 1 < bx.mz);
+    const float ehi = up ? __ldg(e + c + sz) : 0.0f;
+    const float vhi = (has_x && up) ? __ldg(x + c + sz) : 0.0f;
+    float d = (i == bx.mx - 1) ? 2.0f * ec * s : 0.0f;  // outlet: phi = 0 on the face
+    float off = 0.0f;                                    // sum over links of a_cn x_n
+    if (i + 1 < bx.mx) {
+      const float a = (ec + __ldg(e + c + 1)) * hs;
+      d += a;
+      if (has_x) off += a * __ldg(x + c + 1);
+    }
+    if (i > 0) {
+      const float a = (ec + __ldg(e + c - 1)) * hs;
+      d += a;
+      if (has_x) off += a * __ldg(x + c - 1);
+    }
+    if (j + 1 < bx.my) {
+      const float a = (ec + __ldg(e + c + sy)) * hs;
+      d += a;
+      if (has_x) off += a * __ldg(x + c + sy);
+    }
+    if (j > 0) {
+      const float a = (ec + __ldg(e + c - sy)) * hs;
+      d += a;
+      if (has_x) off += a * __ldg(x + c - sy);
+    }
+    if (up) {
+      const float a = (ec + ehi) * hs;
+      d += a;
+      off += a * vhi;
+    }
+    if (k > 0) {
+      const float a = (ec + elo) * hs;
+      d += a;
+      off += a * vlo;
+    }
+    if (KIND == SK_JAC0) {
+      out[c] = __fdividef(omega, d) * __ldg(b + c);
+    } else {
+      const float ax = d * vc - off;
+      if (KIND == SK_JAC)
+        out[c] = vc + __fdividef(omega, d) * (__ldg(b + c) - ax);
+      else if (KIND == SK_MV)
+        out[c] = ax;
+      else
+        out[c] = __ldg(b + c) - ax;
+    }
+    elo = ec;
+    ec = ehi;
+    vlo = vc;
+    vc = vhi;
+  }
+}
+
 template <typename T>
 __global__ void k_jac0(long long n, const T* __restrict__ diag, const T* __restrict__ dinv, const T* __restrict__ b,
                        T* __restrict__ x, T omega, const KScal* sc) {
@@ -795,6 +873,8 @@ static void op_carve(Op<T>& A, Box b, int sym, char*& cur) {
   };
   A.box = b;
   A.sym = sym;
+  A.mfe = nullptr;
+  A.mfs = 0.0f;
   A.diag = take();
   A.dinv = take();
   A.xp = take();
@@ -1004,6 +1084,29 @@ static void stencil_launch(const char* name, int kind, const Op<T>& A, const T* 
                            const KScal* sc, cudaStream_t st) {
   const Op<T> Z = zview(A);
   const ZCfg z = zcfg_stencil(Z.box, (int)sizeof(T), SYM);
+  if constexpr (sizeof(T) == 4 && SYM) {
+    if (A.mfe) {  // matrix-free fine level: one coefficient word (e) per cell
+      const double n = ncell(A);
+      const double words = 1.0 + (kind == SK_MV ? 2.0 : (kind == SK_JAC0 ? 2.0 : 3.0));
+      const float om = (float)omega;
+      const float* bb = (const float*)b;
+      const float* xx = (const float*)x;
+      float* oo = (float*)out;
+      if (kind == SK_JAC)
+        vlaunch(name, words * n * 4.0, k_stencil_mf<SK_JAC>, z.grid, z.block, st, Z.box, A.mfe, A.mfs, bb, xx, oo, om,
+                z.zc, sc);
+      else if (kind == SK_MV)
+        vlaunch(name, words * n * 4.0, k_stencil_mf<SK_MV>, z.grid, z.block, st, Z.box, A.mfe, A.mfs, bb, xx, oo, om,
+                z.zc, sc);
+      else if (kind == SK_RES)
+        vlaunch(name, words * n * 4.0, k_stencil_mf<SK_RES>, z.grid, z.block, st, Z.box, A.mfe, A.mfs, bb, xx, oo, om,
+                z.zc, sc);
+      else
+        vlaunch(name, words * n * 4.0, k_stencil_mf<SK_JAC0>, z.grid, z.block, st, Z.box, A.mfe, A.mfs, bb, xx, oo,
+                om, z.zc, sc);
+      return;
+    }
+  }
   const double wT = sizeof(T), n = ncell(A);
   const double words = (kind == SK_MV ? 2.0 : 3.0) + 1.0 + n_offs(A) + (kind == SK_JAC && sizeof(T) == 8 ? 1.0 : 0.0);
   if (kind == SK_JAC)
@@ -1036,6 +1139,10 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     T *x, *t;
     bufs(l, b, x, t);
     const long long n = box_cells(A.box);
+    if (sizeof(T) == 4 && SYM && A.mfe) {
+      stencil_launch<T, SYM>(KN("mg_jac0", l == 0), SK_JAC0, A, b, nullptr, dst, om, sc, st);
+      return;
+    }
     vlaunch(KN("mg_jac0", l == 0), 3.0 * n * sizeof(T), k_jac0<T>, flat_grid(n), kThreads, st, n, (const T*)A.diag,
             (const T*)A.dinv, b, dst, om, (const KScal*)sc);
   };
