@@ -211,7 +211,7 @@ def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
             peak, src = measured_peaks()
             if n > 0 and kms > 0:
                 ach = kbytes / (kms * 1e-3) / 1e9
-                traffic = kbytes / n * JAC_TRAFFIC_PER_ALG_BYTE if top.startswith("mg_jac_f32") else None
+                traffic = kbytes / n * JAC_TRAFFIC_PER_ALG_BYTE if top == "mg_jac_f32_L0" else None
                 roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                         "traffic": traffic, "kernel": top, "launches": n, "avg_launch_us": kms * 1e3 / n,
                         "alg_bytes_per_launch": kbytes / n, "peak_source": src,

@@ -781,10 +781,11 @@ int vos_tile_config(const vos_handle* h, int32_t sys, int32_t level, int32_t* tx
   const int nlev = fp64 ? h->sd[sys].h.nlev : h->sf[sys].h.nlev;
   if (level < 0 || level >= nlev) return set_err(nullptr, VOS_EINVAL, "vos_tile_config: level out of range");
   Box b = fp64 ? h->sd[sys].h.lev[level].op.box : h->sf[sys].h.lev[level].op.box;
-  const int sym = fp64 ? h->sd[sys].h.lev[level].op.sym : h->sf[sys].h.lev[level].op.sym;
+  int sym = fp64 ? h->sd[sys].h.lev[level].op.sym : h->sf[sys].h.lev[level].op.sym;
+  if (!fp64 && sym && h->sf[sys].h.lev[level].op.mfe) sym = 2;  // matrix-free sweep, tuned on its own
   if (b.mz == 1 && b.my > 1) b = Box{b.mx, 1, b.my};  // 2D boxes march along y
   int x = 0, y = 0, z = 0;
-  if (tuned_config(b.mx, b.my, b.mz, fp64 ? 8 : 4, sym ? 1 : 0, &x, &y, &z)) {
+  if (tuned_config(b.mx, b.my, b.mz, fp64 ? 8 : 4, sym, &x, &y, &z)) {
     *tuned = 1;
   } else {
     *tuned = 0;

@@ -255,15 +255,23 @@ __global__ void __launch_bounds__(kThreads) k_stencil_mf(Box bx, const float* __
   const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
   const float hs = 0.5f * s;
   const bool has_x = KIND != SK_JAC0;
+  // Registers hold planes k-1, k, k+1 of e and x; the loads of plane k+2
+  // (and of b at k+1) are issued before plane k is computed, so each thread
+  // keeps two planes of DRAM loads in flight.
   long long c = i + sy * j + sz * k0;
   float elo = (k0 > 0) ? __ldg(e + c - sz) : 0.0f;
   float ec = __ldg(e + c);
+  float ehi = (k0 + 1 < bx.mz) ? __ldg(e + c + sz) : 0.0f;
   float vlo = (has_x && k0 > 0) ? __ldg(x + c - sz) : 0.0f;
   float vc = has_x ? __ldg(x + c) : 0.0f;
+  float vhi = (has_x && k0 + 1 < bx.mz) ? __ldg(x + c + sz) : 0.0f;
+  float bc = (KIND != SK_MV) ? __ldg(b + c) : 0.0f;
   for (int k = k0; k < k1; ++k, c += sz) {
     const bool up = (k + 1 < bx.mz);
-    const float ehi = up ? __ldg(e + c + sz) : 0.0f;
-    const float vhi = (has_x && up) ? __ldg(x + c + sz) : 0.0f;
+    const bool up2 = (k + 2 < bx.mz) && (k + 1 < k1);
+    const float e2 = up2 ? __ldg(e + c + 2 * sz) : 0.0f;
+    const float v2 = (has_x && up2) ? __ldg(x + c + 2 * sz) : 0.0f;
+    const float bn = (KIND != SK_MV && k + 1 < k1) ? __ldg(b + c + sz) : 0.0f;
     float d = (i == bx.mx - 1) ? 2.0f * ec * s : 0.0f;  // outlet: phi = 0 on the face
     float off = 0.0f;                                    // sum over links of a_cn x_n
     if (i + 1 < bx.mx) {
@@ -297,20 +305,23 @@ __global__ void __launch_bounds__(kThreads) k_stencil_mf(Box bx, const float* __
       off += a * vlo;
     }
     if (KIND == SK_JAC0) {
-      out[c] = __fdividef(omega, d) * __ldg(b + c);
+      out[c] = __fdividef(omega, d) * bc;
     } else {
       const float ax = d * vc - off;
       if (KIND == SK_JAC)
-        out[c] = vc + __fdividef(omega, d) * (__ldg(b + c) - ax);
+        out[c] = vc + __fdividef(omega, d) * (bc - ax);
       else if (KIND == SK_MV)
         out[c] = ax;
       else
-        out[c] = __ldg(b + c) - ax;
+        out[c] = bc - ax;
     }
     elo = ec;
     ec = ehi;
+    ehi = e2;
     vlo = vc;
     vc = vhi;
+    vhi = v2;
+    bc = bn;
   }
 }
 
@@ -527,14 +538,14 @@ static ZCfg zcfg(Box b) { return zcfg_tile(b, (b.my == 1) ? 256 : 32, 4096); }
 // result is computed by the same arithmetic whatever the tile, so the choice
 // changes timings only, never values.  Results are cached per process.
 // ---------------------------------------------------------------------------
-using TuneKey = std::tuple<int, int, int, int, int>;  // mx, my, mz, sizeof(T), SYM
+using TuneKey = std::tuple<int, int, int, int, int>;  // mx, my, mz, sizeof(T), SYM (2: matrix-free)
 static std::map<TuneKey, ZCfg> g_tuned;
 static std::mutex g_tuned_mu;
 constexpr long long kTuneMinCells = 1 << 16;  // smaller boxes are launch-latency bound
 
-static ZCfg zcfg_stencil(Box b, int tsize, bool sym) {
+static ZCfg zcfg_stencil(Box b, int tsize, int sym) {
   std::lock_guard<std::mutex> lk(g_tuned_mu);
-  auto it = g_tuned.find(TuneKey{b.mx, b.my, b.mz, tsize, sym ? 1 : 0});
+  auto it = g_tuned.find(TuneKey{b.mx, b.my, b.mz, tsize, sym});
   return it == g_tuned.end() ? zcfg(b) : it->second;
 }
 
@@ -1000,6 +1011,13 @@ template void build_coarse_levels<float>(Hier<float>&, cudaStream_t);
 
 template <typename T, bool SYM>
 static void tune_launch(const ZCfg& z, const Op<T>& Z, const T* b, const T* x, T* out, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4 && SYM) {
+    if (Z.mfe) {
+      k_stencil_mf<SK_JAC><<<z.grid, z.block, 0, st>>>(Z.box, Z.mfe, Z.mfs, (const float*)b, (const float*)x,
+                                                       (float*)out, 0.7f, z.zc, nullptr);
+      return;
+    }
+  }
   k_stencil<T, SYM, SK_JAC><<<z.grid, z.block, 0, st>>>(Z, b, x, out, T(0.7), z.zc, nullptr);
 }
 
@@ -1020,7 +1038,8 @@ void autotune_hier(const Hier<T>& h, SolverWork* w, cudaStream_t st) {
     if (n < kTuneMinCells || n > w->cap) continue;
     const Op<T> Z = zview(A);
     const bool sym = A.sym != 0;
-    const TuneKey key{Z.box.mx, Z.box.my, Z.box.mz, (int)sizeof(T), sym ? 1 : 0};
+    const int code = (sizeof(T) == 4 && sym && A.mfe) ? 2 : (sym ? 1 : 0);
+    const TuneKey key{Z.box.mx, Z.box.my, Z.box.mz, (int)sizeof(T), code};
     {
       std::lock_guard<std::mutex> lk(g_tuned_mu);
       if (g_tuned.count(key)) continue;
@@ -1083,11 +1102,14 @@ template <typename T, bool SYM>
 static void stencil_launch(const char* name, int kind, const Op<T>& A, const T* b, const T* x, T* out, T omega,
                            const KScal* sc, cudaStream_t st) {
   const Op<T> Z = zview(A);
-  const ZCfg z = zcfg_stencil(Z.box, (int)sizeof(T), SYM);
   if constexpr (sizeof(T) == 4 && SYM) {
     if (A.mfe) {  // matrix-free fine level: one coefficient word (e) per cell
+      const ZCfg z = zcfg_stencil(Z.box, 4, 2);
       const double n = ncell(A);
       const double words = 1.0 + (kind == SK_MV ? 2.0 : (kind == SK_JAC0 ? 2.0 : 3.0));
+      static const char* const mf_names[4] = {"mg_jac_mf_f32_L0", "pcg_matvec_mf_f32_L0", "mg_resid_mf_f32_L0",
+                                              "mg_jac0_mf_f32_L0"};
+      name = mf_names[kind];
       const float om = (float)omega;
       const float* bb = (const float*)b;
       const float* xx = (const float*)x;
@@ -1107,6 +1129,7 @@ static void stencil_launch(const char* name, int kind, const Op<T>& A, const T* 
       return;
     }
   }
+  const ZCfg z = zcfg_stencil(Z.box, (int)sizeof(T), SYM ? 1 : 0);
   const double wT = sizeof(T), n = ncell(A);
   const double words = (kind == SK_MV ? 2.0 : 3.0) + 1.0 + n_offs(A) + (kind == SK_JAC && sizeof(T) == 8 ? 1.0 : 0.0);
   if (kind == SK_JAC)
