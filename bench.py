@@ -190,7 +190,7 @@ def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
         for _ in range(steps):
             V.vos_step(h, dt)
             s = V.vos_get_stats(h)
-            iters.append((s["iters_u"], s["iters_p"], s["iters_c"], s["res_p"]))
+            iters.append((s["iters_u"], s["iters_p"], s["iters_c"], s["res_p"], s["outer_u"], s["outer_p"], s["outer_c"]))
         e1.record(stream)
         torch.cuda.synchronize()
         launches = V.vos_kernel_launches() - l0
@@ -508,7 +508,10 @@ def main():
            "solver": {"iters_u_mean": [float(np.mean([i[0][a] for i in iters])) for a in range(3)],
                       "iters_p_mean": float(np.mean([i[1] for i in iters])),
                       "iters_c_mean": float(np.mean([i[2] for i in iters])),
-                      "res_p_max": float(max(i[3] for i in iters))},
+                      "res_p_max": float(max(i[3] for i in iters)),
+                      "outer_passes_mean": {"u": [float(np.mean([i[4][a] for i in iters])) for a in range(3)],
+                                            "p": float(np.mean([i[5] for i in iters])),
+                                            "c": float(np.mean([i[6] for i in iters]))}},
            "device_bytes": r["dev_bytes"], "e2e": e2e, "clocks": ck, "learned": learned,
            "breakdown": r["breakdown"]}
     if rank == 0 and not args.no_cpu:
