@@ -265,6 +265,7 @@ struct RedScratch {
 // Device scalars of one Krylov solve (FP64).
 struct KScal {
   double bb, rr, rz, rz_old, pq, alpha, beta, omega, rho, rhv, tol2;
+  double tol2s;  // diagonally preconditioned CG: stop when z.z <= tol2s (scaled norm)
   double ss, ts, tt;
   int done, iters, max_iters, breakdown;
 };

@@ -26,6 +26,7 @@ unsigned long long exec_count_solver() {
 
 
 int g_num_sms = 152;
+constexpr double kDiagFloor32 = 2e-5;
 
 __host__ int grid_for(Box b, int max_blocks) {
   Seg s = make_seg(b);
@@ -573,15 +574,21 @@ __global__ void k_diag_prec(long long n, const T* __restrict__ dinv, const T* __
                             KScal* sc, RedScratch rs) {
   VOS_COUNT_EXEC();
   DONE_RETURN(sc);
-  PSum<T> ps;
+  PSum<T> ps, pz;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     const T rc = r[c];
     const T zc = dinv[c] * rc;
     z[c] = zc;
     ps.add(rc, zc);
+    pz.add(zc, zc);
   }
-  double acc[1] = {ps.get()};
-  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_pcg_beta(sc, acc[0]);
+  double acc[2] = {ps.get(), pz.get()};
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    fin_pcg_beta(sc, acc[0]);
+    // z = (omega / diag) r, so z.z is omega^2 |D^-1 r|^2: the same scaled norm
+    // as the FP64 refinement test, which ends the pass here
+    if (sc->iters > 0 && acc[1] <= sc->tol2s) sc->done = 1;
+  }
 }
 
 // Coarsest level: nsweep damped-Jacobi sweeps from zero, one block, in
@@ -706,7 +713,11 @@ __global__ void k_galerkin(Op<T> F, Op<T> C, T omega) {
 // ---------------------------------------------------------------------------
 // Krylov vector kernels
 // ---------------------------------------------------------------------------
-__global__ void k_kscal_init(KScal* sc, const double* outer, double rtol_inner, int max_iters) {
+// scaled != 0 (diagonally preconditioned CG): the pass ends on the scaled
+// norm z.z (see k_diag_prec) instead of the unscaled r.r.  (For MG-PCG the
+// same test cut the refinement passes of the rock's pressure solve from 4.1
+// to 2.9 but not the iterations, and the extra read made the step slower.)
+__global__ void k_kscal_init(KScal* sc, const double* outer, double rtol_inner, int max_iters, int scaled) {
   VOS_COUNT_EXEC();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double rr = outer[2];  // unscaled |r|^2 of the inner right-hand side
@@ -720,7 +731,8 @@ __global__ void k_kscal_init(KScal* sc, const double* outer, double rtol_inner, 
     sc->omega = 1.0;
     sc->rho = rr;
     sc->rhv = 0;
-    sc->tol2 = rtol_inner * rtol_inner * rr;
+    sc->tol2 = scaled ? -1.0 : rtol_inner * rtol_inner * rr;
+    sc->tol2s = rtol_inner * rtol_inner * outer[0];
     sc->iters = 0;
     sc->max_iters = max_iters;
     sc->breakdown = 0;
@@ -1324,7 +1336,8 @@ static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters
   const long long n = box_cells(h.lev[0].op.box);
   const KVec<T> k = kvec<T>(w, false);
   cudaMemsetAsync(k.e, 0, n * sizeof(T), st);
-  vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
+  vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters,
+          (!use_mg && !use_net) ? 1 : 0);
   pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg, use_net);
   const int chunk = (use_mg || use_net) ? 4 : 8;
   int it = 0;
@@ -1359,7 +1372,7 @@ static int inner_bicgstab(Hier<T>& h, SolverWork* w, double rtol_inner, int max_
   cudaMemsetAsync(k.e, 0, n * sizeof(T), st);
   cudaMemsetAsync(k.v, 0, n * sizeof(T), st);
   cudaMemcpyAsync(k.rh, k.r, n * sizeof(T), cudaMemcpyDeviceToDevice, st);
-  vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters);
+  vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters, 0);
   const int chunk = 2;
   int it = 0;
   while (true) {
@@ -1375,6 +1388,13 @@ static int inner_bicgstab(Hier<T>& h, SolverWork* w, double rtol_inner, int max_
 // ---------------------------------------------------------------------------
 // Graph mode: device-side loop control
 // ---------------------------------------------------------------------------
+// Smallest relative tolerance asked of one FP32 inner pass (mixed path).
+// Measured on the 256^3 rock: asking an FP32 MG-PCG pass for less than 2e-5
+// costs more iterations than the refinement pass it saves, and 1e-6 or 1e-7
+// for the diagonally preconditioned momentum passes made the step slower
+// (142 vs 138 ms).
+static double inner_floor32(bool use_mg) { return use_mg ? 2e-5 : kDiagFloor32; }
+
 __global__ void k_ctrl_init(SolveStats* ss, KScal* sc) {
   VOS_COUNT_EXEC();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -1394,7 +1414,7 @@ __global__ void k_ctrl_init(SolveStats* ss, KScal* sc) {
 // initialises the inner Krylov scalars (the same rules as the host loop).
 template <bool MIXED>
 __global__ void k_ctrl(SolveStats* ss, KScal* sc, const double* outer, double rtol, int max_outer, int max_iter,
-                       cudaGraphConditionalHandle ho, cudaGraphConditionalHandle hi) {
+                       double floor32, int scaled, cudaGraphConditionalHandle ho, cudaGraphConditionalHandle hi) {
   VOS_COUNT_EXEC();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (ss->started) ss->iters += sc->iters;
@@ -1417,7 +1437,7 @@ __global__ void k_ctrl(SolveStats* ss, KScal* sc, const double* outer, double rt
     } else {
       double rin = rtol / rel;
       if (MIXED) {
-        if (rin < 2e-5) rin = 2e-5;
+        if (rin < floor32) rin = floor32;
       } else {
         rin *= 0.5;
         if (rin < 1e-15) rin = 1e-15;
@@ -1434,7 +1454,8 @@ __global__ void k_ctrl(SolveStats* ss, KScal* sc, const double* outer, double rt
       sc->omega = 1.0;
       sc->rho = r2;
       sc->rhv = 0.0;
-      sc->tol2 = rin * rin * r2;
+      sc->tol2 = scaled ? -1.0 : rin * rin * r2;
+      sc->tol2s = rin * rin * rr;
       sc->iters = 0;
       sc->max_iters = max_iter - ss->iters;
       sc->breakdown = 0;
@@ -1544,11 +1565,11 @@ cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, V
     VOS_CUDA_TRY(capture_graph_of(s1, &g1));
     VOS_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, g1, 0, cudaGraphCondAssignDefault));
     if (mixed)
-      vlaunch("ctrl", 0.0, k_ctrl<true>, 1, 32, s1, ss, w->sc, (const double*)w->outer, rtol, max_outer, max_iter, ho,
-              hi);
+      vlaunch("ctrl", 0.0, k_ctrl<true>, 1, 32, s1, ss, w->sc, (const double*)w->outer, rtol, max_outer, max_iter,
+              inner_floor32(use_mg), (sym && !use_mg) ? 1 : 0, ho, hi);
     else
-      vlaunch("ctrl", 0.0, k_ctrl<false>, 1, 32, s1, ss, w->sc, (const double*)w->outer, rtol, max_outer, max_iter, ho,
-              hi);
+      vlaunch("ctrl", 0.0, k_ctrl<false>, 1, 32, s1, ss, w->sc, (const double*)w->outer, rtol, max_outer, max_iter,
+              inner_floor32(use_mg), (sym && !use_mg) ? 1 : 0, ho, hi);
     const KVec<T> k = kvec<T>(w, !sym);
     VOS_CUDA_TRY(cudaMemsetAsync(k.e, 0, n * sizeof(T), s1));
     if (sym) {
@@ -1629,7 +1650,7 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
     // the FP64 path asks for a little more than needed.
     double rin = rtol / rel;
     if (mixed) {
-      if (rin < 2e-5) rin = 2e-5;
+      if (rin < inner_floor32(use_mg)) rin = inner_floor32(use_mg);
     } else {
       rin *= 0.5;
       if (rin < 1e-15) rin = 1e-15;
@@ -1684,7 +1705,7 @@ int residual_snapshots(const Op<double>& op64, Hier<T>& h, const double* b, View
   for (int i = 0; i < count; ++i) maxit = iters[i] > maxit ? iters[i] : maxit;
   const KVec<T> k = kvec<T>(w, false);
   cudaMemsetAsync(k.e, 0, n * sizeof(T), st);
-  vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, 1e-30, maxit + 1);
+  vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, 1e-30, maxit + 1, 0);
   pcg_precond<T, true>(h, k, n, w, rs, st, true, false);
   for (int it = 0; it <= maxit; ++it) {
     if (it > 0) pcg_iteration<T, true>(h, k, n, w, rs, st, true, false);
