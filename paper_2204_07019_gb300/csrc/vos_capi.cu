@@ -51,7 +51,7 @@ struct vos_handle {
   size_t defl_cap;
   Defl defl;
   // fields
-  double *eps, *eps_old, *c, *p, *phi, *R, *Rf, *kr;
+  double *eps, *eps_old, *c, *p, *phi, *R, *Rf, *kr, *kic;
   float* eps32;  // FP32 fluid fraction for the matrix-free pressure sweeps (mixed precision)
   double *u[3], *us[3];
   FaceData fd[3];
@@ -225,7 +225,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
   launch_set_scalar(h->d_dt, dt, st);
   const double* dtp = h->d_dt;
   // S1: solid fraction and (implicitly) permeability
-  launch_eps_update(P, h->eps, h->eps_old, h->R, dtp, h->dstats, h->rs, st);
+  launch_eps_update(P, h->eps, h->eps_old, h->R, dtp, h->dstats, h->rs, h->kic, st);
   // S2: momentum predictor per component
   for (int a = 0; a < nd; ++a) {
     cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -233,7 +233,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     s.outer_u[a] = 0;
     s.res_u[a] = 0.0;
     if (box_cells(S[a].box) == 0) continue;
-    launch_mom_assemble(P, a, h->eps, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
+    launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
     // The momentum operator is (1/dt + drag) I - nu lap: when the mass term
     // dominates (2 d nu dt / dx^2 <= 30) the diagonally preconditioned CG
     // converges in a grid-independent number of iterations at a third of
@@ -299,11 +299,11 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
   const int nd = P.dim;
   const int ivos = (h->prm.method == VOS_IVOS);
   const double* dtp = h->d_dt;
-  launch_eps_update(P, h->eps, h->eps_old, h->R, dtp, h->dstats, h->rs, st);
+  launch_eps_update(P, h->eps, h->eps_old, h->R, dtp, h->dstats, h->rs, h->kic, st);
   for (int a = 0; a < nd; ++a) {
     VOS_CUDA_TRY(cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (box_cells(S[a].box) == 0) continue;
-    launch_mom_assemble(P, a, h->eps, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
+    launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
     VOS_CUDA_TRY(solve_capture<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
                                   h->work, h->rs, st, mom_mg, h->dsolve + a, h->gs1, h->gs2));
   }
@@ -537,7 +537,7 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     delete h;
     return code;
   };
-  double** cells[] = {&h->eps, &h->eps_old, &h->c, &h->p, &h->phi, &h->R, &h->Rf, &h->kr};
+  double** cells[] = {&h->eps, &h->eps_old, &h->c, &h->p, &h->phi, &h->R, &h->Rf, &h->kr, &h->kic};
   for (double** f : cells) {
     *f = (double*)dev_alloc(h, cb);
     if (!*f) return fail(VOS_ENOMEM, "device allocation failed (cell fields)");
@@ -623,7 +623,7 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
   }
   cudaStream_t st = h->st;
   cudaMemcpyAsync(h->eps, e0.data(), cb, cudaMemcpyHostToDevice, st);
-  for (double* f : {h->eps_old, h->c, h->p, h->phi, h->R, h->Rf, h->kr}) cudaMemsetAsync(f, 0, cb, st);
+  for (double* f : {h->eps_old, h->c, h->p, h->phi, h->R, h->Rf, h->kr, h->kic}) cudaMemsetAsync(f, 0, cb, st);
   for (int a = 0; a < P.dim; ++a) {
     size_t fb = (size_t)face_count(P, a) * sizeof(double);
     cudaMemsetAsync(h->u[a], 0, fb, st);

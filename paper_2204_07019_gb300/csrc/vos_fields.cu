@@ -32,6 +32,11 @@ __device__ __forceinline__ long long fidx(const Phys& P, int a, int i, int j, in
 __device__ __forceinline__ int ncell(const Phys& P, int b) { return (b == 0) ? P.nx : (b == 1) ? P.ny : P.nz; }
 
 // Kozeny-Carman inverse permeability (Eq. perm): (1 - eps)^2 / (k0 eps^3).
+// omega / diag for the Jacobi smoother, the diagonal preconditioner and the
+// scaled residual norm (exact: with an FP32 reciprocal here an FP64 solve of
+// the 1024 x 512 micromodel to 1e-10 no longer converged).
+__device__ __forceinline__ double jacobi_weight(double omega, double diag) { return omega / diag; }
+
 __device__ __forceinline__ double kinv(double e, double k0) {
   double s = 1.0 - e;
   return s * s / (k0 * e * e * e);
@@ -69,7 +74,7 @@ __device__ __forceinline__ bool cell_in(const Phys& P, int i, int j, int k) {
 // S1: eps^{n+1} = clamp(eps^n + dt Vm R^n, eps_min, 1)   (Eq. mbs)
 // ---------------------------------------------------------------------------
 __global__ void k_eps_update(Phys P, double* eps, double* eps_old, const double* R, const double* __restrict__ dtp, double* stats,
-                             RedScratch rs) {
+                             RedScratch rs, double* __restrict__ kic) {
   VOS_COUNT_EXEC();
   const double dt = *dtp;
   const Box bx{P.nx, P.ny, P.nz};
@@ -85,6 +90,7 @@ __global__ void k_eps_update(Phys P, double* eps, double* eps_old, const double*
     double raw = e + dt * P.Vm * R[c];
     double nw = fmin(fmax(raw, P.eps_min), 1.0);
     eps[c] = nw;
+    kic[c] = kinv(nw, P.k0);  // Kozeny-Carman k^-1 of the new eps, once per cell
     acc[0] += raw - nw;
     acc[1] += nw;
   }
@@ -96,9 +102,9 @@ __global__ void k_eps_update(Phys P, double* eps, double* eps_old, const double*
 }
 
 void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, const double* __restrict__ dtp, double* stats,
-                       const RedScratch& rs, cudaStream_t st) {
+                       const RedScratch& rs, double* kic, cudaStream_t st) {
   Box bx{P.nx, P.ny, P.nz};
-  vlaunch("eps_update", 32.0 * box_cells(bx), k_eps_update, grid_for(bx, kMaxRedBlocks), kThreads, st, P, eps, eps_old, R, dtp, stats, rs);
+  vlaunch("eps_update", 40.0 * box_cells(bx), k_eps_update, grid_for(bx, kMaxRedBlocks), kThreads, st, P, eps, eps_old, R, dtp, stats, rs, kic);
 }
 
 // ---------------------------------------------------------------------------
@@ -108,11 +114,11 @@ void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double
 // boundary faces for y/z); unknown (i,j,k) is face (i,j,k) + e_a, whose
 // minus cell is cell (i,j,k).
 // ---------------------------------------------------------------------------
-__global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__ eps, const double* __restrict__ p,
-                               const double* __restrict__ uold, const double* __restrict__ dtp, double omega, Op<double> A,
-                               double* __restrict__ rhs) {
+__global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__ eps, const double* __restrict__ kic,
+                               const double* __restrict__ p, const double* __restrict__ uold,
+                               const double* __restrict__ dtp, double omega, Op<double> A, double* __restrict__ rhs) {
   VOS_COUNT_EXEC();
-  const double dt = *dtp;
+  const double idt = 1.0 / *dtp, idx = 1.0 / P.dx;
   const Seg s = make_seg(ub);
   const double cnu = P.nu / (P.dx * P.dx);
   VOS_SEG_LOOP(s, q) {
@@ -132,15 +138,15 @@ __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__
       const long long cp = cidx(P, pc[0], pc[1], pc[2]);
       const double ep = eps[cp];
       ef = 0.5 * (em + ep);
-      kf = 0.5 * (kinv(em, P.k0) + kinv(ep, P.k0));
-      gp = (p[cp] - pm) / P.dx;
+      kf = 0.5 * (kic[cidx(P, i, j, k)] + kic[cp]);
+      gp = (p[cp] - pm) * idx;
     } else {  // outlet face (a == x): one-sided, Dirichlet p = 0
       ef = em;
-      kf = kinv(em, P.k0);
-      gp = -2.0 * pm / P.dx;
+      kf = kic[cidx(P, i, j, k)];
+      gp = -2.0 * pm * idx;
     }
-    double diag = 1.0 / dt + P.nu * ef * kf;
-    double b = uold[fidx(P, a, f[0], f[1], f[2])] / dt - ef * gp;
+    double diag = idt + P.nu * ef * kf;
+    double b = uold[fidx(P, a, f[0], f[1], f[2])] * idt - ef * gp;
     double off[3] = {0.0, 0.0, 0.0};
     const int nb = (P.dim == 2) ? 2 : 3;
     const int um[3] = {ub.mx, ub.my, ub.mz};
@@ -171,7 +177,7 @@ __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__
       }
     }
     A.diag[c] = diag;
-    A.dinv[c] = omega / diag;
+    A.dinv[c] = jacobi_weight(omega, diag);
     A.xp[c] = off[0];
     A.yp[c] = off[1];
     if (A.zp) A.zp[c] = off[2];
@@ -179,10 +185,10 @@ __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__
   }
 }
 
-void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, const double* __restrict__ dtp,
+void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* kic, const double* p, const double* uold, const double* __restrict__ dtp,
                          double omega, Op<double> A, double* rhs, cudaStream_t st) {
   if (box_cells(A.box) == 0) return;
-  vlaunch("mom_assemble", (6.0 + P.dim) * 8.0 * box_cells(A.box), k_mom_assemble, grid_for(A.box, 0), kThreads, st, P, a, A.box, eps, p, uold, dtp, omega, A, rhs);
+  vlaunch("mom_assemble", (6.0 + P.dim) * 8.0 * box_cells(A.box), k_mom_assemble, grid_for(A.box, 0), kThreads, st, P, a, A.box, eps, kic, p, uold, dtp, omega, A, rhs);
 }
 
 // ---------------------------------------------------------------------------
@@ -195,7 +201,7 @@ __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const do
                                 const double* __restrict__ R, const double* __restrict__ dtp, double omega, Op<double> A,
                                 double* __restrict__ rhs, float* __restrict__ eps32) {
   VOS_COUNT_EXEC();
-  const double dt = *dtp;
+  const double idt = 1.0 / *dtp, idx = 1.0 / P.dx;
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   const double idx2 = 1.0 / (P.dx * P.dx);
@@ -220,17 +226,17 @@ __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const do
       if (cell_in(P, lo[0], lo[1], lo[2])) diag += 0.5 * (e + eps[cidx(P, lo[0], lo[1], lo[2])]) * idx2;
       int fp[3] = {i, j, k};
       fp[d] += 1;
-      div += (us[d][fidx(P, d, fp[0], fp[1], fp[2])] - us[d][fidx(P, d, i, j, k)]) / P.dx;
+      div += (us[d][fidx(P, d, fp[0], fp[1], fp[2])] - us[d][fidx(P, d, i, j, k)]) * idx;
     }
     if (i == P.nx - 1) diag += 2.0 * e * idx2;
     const double src = R[c] * P.Vm * (1.0 - P.rho_ratio);
     A.diag[c] = diag;
-    A.dinv[c] = omega / diag;
+    A.dinv[c] = jacobi_weight(omega, diag);
     if (eps32) eps32[c] = (float)e;  // the matrix-free FP32 form of this operator
     A.xp[c] = off[0];
     A.yp[c] = off[1];
     if (A.zp) A.zp[c] = off[2];
-    rhs[c] = -(div - src) / dt;
+    rhs[c] = -(div - src) * idt;
   }
 }
 
@@ -244,7 +250,7 @@ void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3],
 __global__ void k_project(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ phi,
                           const double* __restrict__ dtp, const double* __restrict__ us, double* __restrict__ u) {
   VOS_COUNT_EXEC();
-  const double dt = *dtp;
+  const double dt = *dtp, idx = 1.0 / P.dx;
   const Seg s = make_seg(fb);
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
@@ -258,10 +264,10 @@ __global__ void k_project(Phys P, int a, Box fb, const double* __restrict__ eps,
       int mc[3] = {i, j, k};
       mc[a] -= 1;
       const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
-      val -= dt * 0.5 * (eps[cm] + eps[cp]) * (phi[cp] - phi[cm]) / P.dx;
+      val -= dt * 0.5 * (eps[cm] + eps[cp]) * (phi[cp] - phi[cm]) * idx;
     } else if (a == 0 && m == n) {
       const long long cm = cidx(P, i - 1, j, k);
-      val -= dt * eps[cm] * (-2.0 * phi[cm]) / P.dx;
+      val -= dt * eps[cm] * (-2.0 * phi[cm]) * idx;
     }
     u[fcx] = val;
   }
@@ -481,7 +487,7 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
                                  const double* __restrict__ kr, FaceData f0, FaceData f1, FaceData f2, const double* __restrict__ dtp,
                                  double omega, Op<double> A, double* __restrict__ rhs) {
   VOS_COUNT_EXEC();
-  const double dt = *dtp;
+  const double idt = 1.0 / *dtp;
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   const double idx2 = 1.0 / (P.dx * P.dx), idx1 = 1.0 / P.dx;
@@ -494,8 +500,8 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
     if (i >= bx.mx) continue;
     const long long c = cidx(P, i, j, k);
     const double e = eps[c];
-    double diag = e / dt;
-    double b = eps_old[c] * cold[c] / dt;
+    double diag = e * idt;
+    double b = eps_old[c] * cold[c] * idt;
     double offp[3] = {0, 0, 0}, offm[3] = {0, 0, 0};
     double adv = 0.0;
     for (int d = 0; d < nb; ++d) {
@@ -550,7 +556,7 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
     if (!IVOS) diag += P.zeta * kr[c];
     b -= adv;
     A.diag[c] = diag;
-    A.dinv[c] = omega / diag;
+    A.dinv[c] = jacobi_weight(omega, diag);
     A.xp[c] = offp[0];
     A.yp[c] = offp[1];
     if (A.zp) A.zp[c] = offp[2];

@@ -32,10 +32,13 @@ struct FaceData {  // iVoS per-face data for one axis (face-array layout)
 };
 
 // S1
+// kic: receives the Kozeny-Carman k^-1 of the new eps per cell (read by the
+// momentum assembly).
 void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, const double* dtp, double* stats,
-                       const RedScratch& rs, cudaStream_t st);
+                       const RedScratch& rs, double* kic, cudaStream_t st);
 // S2
-void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* p, const double* uold, const double* dtp,
+void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* kic, const double* p, const double* uold,
+                         const double* dtp,
                          double omega, Op<double> A, double* rhs, cudaStream_t st);
 // S3
 // eps32 (may be NULL): receives the FP32 fluid fraction that the matrix-free

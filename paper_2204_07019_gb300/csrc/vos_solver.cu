@@ -713,10 +713,9 @@ __global__ void k_galerkin(Op<T> F, Op<T> C, T omega) {
 // ---------------------------------------------------------------------------
 // Krylov vector kernels
 // ---------------------------------------------------------------------------
-// scaled != 0 (diagonally preconditioned CG): the pass ends on the scaled
-// norm z.z (see k_diag_prec) instead of the unscaled r.r.  (For MG-PCG the
-// same test cut the refinement passes of the rock's pressure solve from 4.1
-// to 2.9 but not the iterations, and the extra read made the step slower.)
+// scaled != 0: the pass ends on the diagonally scaled norm (z.z in
+// k_diag_prec, or |dscale r|^2 in k_pcg_xr) instead of the unscaled r.r
+// (see scaled_test).
 __global__ void k_kscal_init(KScal* sc, const double* outer, double rtol_inner, int max_iters, int scaled) {
   VOS_COUNT_EXEC();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -741,24 +740,32 @@ __global__ void k_kscal_init(KScal* sc, const double* outer, double rtol_inner, 
 }
 
 // PCG: e += alpha p; r -= alpha q; rr = r.r; convergence check.
+// PCG: e += alpha p; r -= alpha q.  With dscale (= omega / diag of the fine
+// operator) the pass ends on the diagonally scaled norm |dscale r|^2 <=
+// tol2s, the norm of the FP64 refinement test; otherwise on |r|^2 <= tol2.
 template <typename T>
 __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restrict__ qv, T* __restrict__ e,
-                         T* __restrict__ r, KScal* sc, RedScratch rs) {
+                         T* __restrict__ r, const T* __restrict__ dscale, KScal* sc, RedScratch rs) {
   VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   const T alpha = (T)sc->alpha;
-  PSum<T> ps;
+  PSum<T> ps, pd;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     e[c] += alpha * p[c];
     T rc = r[c] - alpha * qv[c];
     r[c] = rc;
     ps.add(rc, rc);
+    if (dscale) {
+      const T rsc = rc * __ldg(dscale + c);
+      pd.add(rsc, rsc);
+    }
   }
-  double acc[1] = {ps.get()};
-  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+  double acc[2] = {ps.get(), pd.get()};
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
     sc->rr = acc[0];
     sc->iters += 1;
-    if (acc[0] <= sc->tol2 || sc->iters >= sc->max_iters || !isfinite(acc[0])) sc->done = 1;
+    const bool conv = dscale ? (acc[1] <= sc->tol2s) : (acc[0] <= sc->tol2);
+    if (conv || sc->iters >= sc->max_iters || !isfinite(acc[0])) sc->done = 1;
   }
 }
 
@@ -1299,8 +1306,12 @@ static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork*
   stencil_launch<T, SYM>(KN("pcg_matvec", true), SK_MV, A, nullptr, k.p, k.q, T(0), w->sc, st);
   vlaunch(KN("dot_pq", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_ALPHA>, gf, kThreads, st, n, (const T*)k.p,
           (const T*)k.q, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
-  vlaunch(KN("pcg_xr", true), 6.0 * n * sizeof(T), k_pcg_xr<T>, gf, kThreads, st, n, (const T*)k.p, (const T*)k.q,
-          k.e, k.r, w->sc, rs);
+  // FP64 MG-PCG passes end on the scaled norm (the diagonal preconditioner
+  // tests z.z itself; FP32 MG-PCG and the learned path keep |r|, see
+  // scaled_test)
+  const T* dscale = (sizeof(T) == 8 && use_mg && !use_net) ? (const T*)A.dinv : nullptr;
+  vlaunch(KN("pcg_xr", true), (dscale ? 7.0 : 6.0) * n * sizeof(T), k_pcg_xr<T>, gf, kThreads, st, n, (const T*)k.p,
+          (const T*)k.q, k.e, k.r, dscale, w->sc, rs);
   pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg, use_net);
 }
 
@@ -1326,6 +1337,18 @@ static void bicg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork
           (const T*)k.s, (const T*)k.t, (const T*)k.rh, k.e, k.r, w->sc, rs);
 }
 
+// Which PCG passes end on the diagonally scaled norm (the refinement's own
+// test) rather than |r|: diagonal PCG always (z.z is free), MG-PCG in FP64
+// (one more read per iteration; the FP64 path is arithmetic-bound, and with
+// |r| an FP64 pressure solve of the 1024 x 512 micromodel stalled at 1.7e-10
+// in 8 passes).  FP32 MG-PCG keeps |r|: the scaled test cut the rock's
+// pressure passes from 4.1 to 2.9 but not the iterations and the extra read
+// made the step slower.
+template <typename T>
+static int scaled_test(bool use_mg, bool use_net) {
+  return (!use_net && (!use_mg || sizeof(T) == 8)) ? 1 : 0;
+}
+
 // With the learned preconditioner (use_net) the pass stops early, with
 // *stagnated = true, when the inner residual norm falls by less than a
 // factor 2 over two successive polls (8 iterations): the caller then
@@ -1337,7 +1360,7 @@ static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters
   const KVec<T> k = kvec<T>(w, false);
   cudaMemsetAsync(k.e, 0, n * sizeof(T), st);
   vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, rtol_inner, max_iters,
-          (!use_mg && !use_net) ? 1 : 0);
+          scaled_test<T>(use_mg, use_net));
   pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg, use_net);
   const int chunk = (use_mg || use_net) ? 4 : 8;
   int it = 0;
@@ -1566,10 +1589,10 @@ cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, V
     VOS_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, g1, 0, cudaGraphCondAssignDefault));
     if (mixed)
       vlaunch("ctrl", 0.0, k_ctrl<true>, 1, 32, s1, ss, w->sc, (const double*)w->outer, rtol, max_outer, max_iter,
-              inner_floor32(use_mg), (sym && !use_mg) ? 1 : 0, ho, hi);
+              inner_floor32(use_mg), sym ? scaled_test<T>(use_mg, false) : 0, ho, hi);
     else
       vlaunch("ctrl", 0.0, k_ctrl<false>, 1, 32, s1, ss, w->sc, (const double*)w->outer, rtol, max_outer, max_iter,
-              inner_floor32(use_mg), (sym && !use_mg) ? 1 : 0, ho, hi);
+              inner_floor32(use_mg), sym ? scaled_test<T>(use_mg, false) : 0, ho, hi);
     const KVec<T> k = kvec<T>(w, !sym);
     VOS_CUDA_TRY(cudaMemsetAsync(k.e, 0, n * sizeof(T), s1));
     if (sym) {
