@@ -575,6 +575,10 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
                                            : alloc_sys<float>(h, h->sf[sys], sys, sym);
     if (!ok) return fail(VOS_ENOMEM, "device allocation failed (solver)");
   }
+  if (prm->precision != VOS_FP64) {  // FP32 momentum fine levels: constant links -nu/dx^2
+    for (int a = 0; a < P.dim; ++a)
+      if (h->sf[a].h.nlev > 0) h->sf[a].h.lev[0].op.mfc = (float)(-P.nu / (P.dx * P.dx));
+  }
   if (h->eps32 && h->sf[3].h.nlev > 0) {  // the FP32 pressure fine level runs matrix-free
     h->sf[3].h.lev[0].op.mfe = h->eps32;
     h->sf[3].h.lev[0].op.mfs = (float)(1.0 / (P.dx * P.dx));

@@ -92,6 +92,10 @@ struct Op {
   // outlet column (i = mx - 1), instead of reading diag/xp/yp/zp.
   const float* mfe;
   float mfs;
+  // Constant-link form (FP32 momentum fine levels): when mfc != 0 every link
+  // between two unknowns of the box is mfc (-nu / dx^2) and sweeps read only
+  // diag, not xp/yp/zp.
+  float mfc;
 };
 
 // Work split: a warp handles one 32-cell row segment along x; blocks stride

@@ -326,6 +326,59 @@ __global__ void __launch_bounds__(kThreads) k_stencil_mf(Box bx, const float* __
   }
 }
 
+// Constant-link FP32 sweeps (Op::mfc): links to the neighbours inside the
+// box are all `a`, so a sweep reads diag and x (and b), not xp/yp/zp.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) k_stencil_mfc(Box bx, const float* __restrict__ dg, float a,
+                                                         const float* __restrict__ b, const float* __restrict__ x,
+                                                         float* __restrict__ out, float omega, int zc,
+                                                         const KScal* sc) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  if (i >= bx.mx || j >= bx.my || k0 >= k1) return;
+  const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+  const bool has_x = KIND != SK_JAC0;
+  long long c = i + sy * j + sz * k0;
+  float vlo = (has_x && k0 > 0) ? __ldg(x + c - sz) : 0.0f;
+  float vc = has_x ? __ldg(x + c) : 0.0f;
+  float vhi = (has_x && k0 + 1 < bx.mz) ? __ldg(x + c + sz) : 0.0f;
+  float dc = __ldg(dg + c);
+  float bc = (KIND != SK_MV) ? __ldg(b + c) : 0.0f;
+  for (int k = k0; k < k1; ++k, c += sz) {
+    const bool nxt = k + 1 < k1;
+    const float v2 = (has_x && nxt && k + 2 < bx.mz) ? __ldg(x + c + 2 * sz) : 0.0f;
+    const float dn = nxt ? __ldg(dg + c + sz) : 0.0f;
+    const float bn = (KIND != SK_MV && nxt) ? __ldg(b + c + sz) : 0.0f;
+    if (KIND == SK_JAC0) {
+      out[c] = __fdividef(omega, dc) * bc;
+    } else {
+      float sum = 0.0f;  // sum of the neighbours inside the box
+      if (i + 1 < bx.mx) sum += __ldg(x + c + 1);
+      if (i > 0) sum += __ldg(x + c - 1);
+      if (j + 1 < bx.my) sum += __ldg(x + c + sy);
+      if (j > 0) sum += __ldg(x + c - sy);
+      if (k + 1 < bx.mz) sum += vhi;
+      if (k > 0) sum += vlo;
+      const float ax = dc * vc + a * sum;
+      if (KIND == SK_JAC)
+        out[c] = vc + __fdividef(omega, dc) * (bc - ax);
+      else if (KIND == SK_MV)
+        out[c] = ax;
+      else
+        out[c] = bc - ax;
+    }
+    vlo = vc;
+    vc = vhi;
+    vhi = v2;
+    dc = dn;
+    bc = bn;
+  }
+}
+
 template <typename T>
 __global__ void k_jac0(long long n, const T* __restrict__ diag, const T* __restrict__ dinv, const T* __restrict__ b,
                        T* __restrict__ x, T omega, const KScal* sc) {
@@ -905,6 +958,7 @@ static void op_carve(Op<T>& A, Box b, int sym, char*& cur) {
   A.sym = sym;
   A.mfe = nullptr;
   A.mfs = 0.0f;
+  A.mfc = 0.0f;
   A.diag = take();
   A.dinv = take();
   A.xp = take();
@@ -1122,6 +1176,31 @@ static void stencil_launch(const char* name, int kind, const Op<T>& A, const T* 
                            const KScal* sc, cudaStream_t st) {
   const Op<T> Z = zview(A);
   if constexpr (sizeof(T) == 4 && SYM) {
+    if (A.mfc != 0.0f) {  // constant links: diag is the only coefficient word
+      const ZCfg z = zcfg_stencil(Z.box, 4, 1);
+      static const char* const mfc_names[4] = {"mg_jac_mfc_f32_L0", "pcg_matvec_mfc_f32_L0", "mg_resid_mfc_f32_L0",
+                                               "mg_jac0_mfc_f32_L0"};
+      const double words = 1.0 + (kind == SK_MV ? 2.0 : (kind == SK_JAC0 ? 2.0 : 3.0));
+      const double n = ncell(A);
+      const float om = (float)omega;
+      const float* dg = (const float*)Z.diag;
+      const float* bb = (const float*)b;
+      const float* xx = (const float*)x;
+      float* oo = (float*)out;
+      if (kind == SK_JAC)
+        vlaunch(mfc_names[kind], words * n * 4.0, k_stencil_mfc<SK_JAC>, z.grid, z.block, st, Z.box, dg, A.mfc, bb, xx,
+                oo, om, z.zc, sc);
+      else if (kind == SK_MV)
+        vlaunch(mfc_names[kind], words * n * 4.0, k_stencil_mfc<SK_MV>, z.grid, z.block, st, Z.box, dg, A.mfc, bb, xx,
+                oo, om, z.zc, sc);
+      else if (kind == SK_RES)
+        vlaunch(mfc_names[kind], words * n * 4.0, k_stencil_mfc<SK_RES>, z.grid, z.block, st, Z.box, dg, A.mfc, bb,
+                xx, oo, om, z.zc, sc);
+      else
+        vlaunch(mfc_names[kind], words * n * 4.0, k_stencil_mfc<SK_JAC0>, z.grid, z.block, st, Z.box, dg, A.mfc, bb,
+                xx, oo, om, z.zc, sc);
+      return;
+    }
     if (A.mfe) {  // matrix-free fine level: one coefficient word (e) per cell
       const ZCfg z = zcfg_stencil(Z.box, 4, 2);
       const double n = ncell(A);
@@ -1181,7 +1260,7 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     T *x, *t;
     bufs(l, b, x, t);
     const long long n = box_cells(A.box);
-    if (sizeof(T) == 4 && SYM && A.mfe) {
+    if (sizeof(T) == 4 && SYM && (A.mfe || A.mfc != 0.0f)) {
       stencil_launch<T, SYM>(KN("mg_jac0", l == 0), SK_JAC0, A, b, nullptr, dst, om, sc, st);
       return;
     }
