@@ -822,6 +822,59 @@ __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restri
   }
 }
 
+// Constant-link FP32 matvec q = A p fused with p.q (alpha = r.z / p.q).
+// Threads outside the box stay for the grid reduction.
+__global__ void __launch_bounds__(kThreads) k_matvec_mfc_dot(Box bx, const float* __restrict__ dg, float a,
+                                                            const float* __restrict__ x, float* __restrict__ out,
+                                                            int zc, KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  PSum<float> ps;
+  if (i < bx.mx && j < bx.my && k0 < k1) {
+    const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+    long long c = i + sy * j + sz * k0;
+    float vlo = (k0 > 0) ? __ldg(x + c - sz) : 0.0f;
+    float vc = __ldg(x + c);
+    float vhi = (k0 + 1 < bx.mz) ? __ldg(x + c + sz) : 0.0f;
+    float dc = __ldg(dg + c);
+    for (int k = k0; k < k1; ++k, c += sz) {
+      const bool nxt = k + 1 < k1;
+      const float v2 = (nxt && k + 2 < bx.mz) ? __ldg(x + c + 2 * sz) : 0.0f;
+      const float dn = nxt ? __ldg(dg + c + sz) : 0.0f;
+      float sum = 0.0f;
+      if (i + 1 < bx.mx) sum += __ldg(x + c + 1);
+      if (i > 0) sum += __ldg(x + c - 1);
+      if (j + 1 < bx.my) sum += __ldg(x + c + sy);
+      if (j > 0) sum += __ldg(x + c - sy);
+      if (k + 1 < bx.mz) sum += vhi;
+      if (k > 0) sum += vlo;
+      const float ax = dc * vc + a * sum;
+      out[c] = ax;
+      ps.add(vc, ax);
+      vlo = vc;
+      vc = vhi;
+      vhi = v2;
+      dc = dn;
+    }
+  }
+  double acc[1] = {ps.get()};
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    const double pq = acc[0];
+    sc->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      sc->breakdown = 1;
+      sc->done = 1;
+      sc->alpha = 0.0;
+    } else {
+      sc->alpha = sc->rz / pq;
+    }
+  }
+}
+
 // BiCGStab: p = r + beta (p - omega v)   (first iteration: p = r)
 template <typename T>
 __global__ void k_bicg_p(long long n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ p,
@@ -1382,9 +1435,21 @@ static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork*
   const int gf = flat_grid(n);
   vlaunch(KN("pcg_p", true), 3.0 * n * sizeof(T), k_pcg_p<T>, gf, kThreads, st, n, (const T*)k.z, k.p,
           (const KScal*)w->sc);
-  stencil_launch<T, SYM>(KN("pcg_matvec", true), SK_MV, A, nullptr, k.p, k.q, T(0), w->sc, st);
-  vlaunch(KN("dot_pq", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_ALPHA>, gf, kThreads, st, n, (const T*)k.p,
-          (const T*)k.q, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
+  bool fused_mv = false;
+  if constexpr (sizeof(T) == 4 && SYM) {
+    if (A.mfc != 0.0f && !use_mg && !use_net) {  // constant-link matvec fused with p.q
+      const Op<T> Z = zview(A);
+      const ZCfg z = zcfg(Z.box);  // grid-reduction kernel: default shape, fixed summation order
+      vlaunch("pcg_matvec_dot_mfc_f32_L0", 4.0 * n * 4.0, k_matvec_mfc_dot, z.grid, z.block, st, Z.box,
+              (const float*)Z.diag, A.mfc, (const float*)k.p, (float*)k.q, z.zc, w->sc, rs);
+      fused_mv = true;
+    }
+  }
+  if (!fused_mv) {
+    stencil_launch<T, SYM>(KN("pcg_matvec", true), SK_MV, A, nullptr, k.p, k.q, T(0), w->sc, st);
+    vlaunch(KN("dot_pq", true), 2.0 * n * sizeof(T), k_dots<T, 1, DF_PCG_ALPHA>, gf, kThreads, st, n, (const T*)k.p,
+            (const T*)k.q, (const T*)nullptr, (const T*)nullptr, w->sc, rs);
+  }
   // FP64 MG-PCG passes end on the scaled norm (the diagonal preconditioner
   // tests z.z itself; FP32 MG-PCG and the learned path keep |r|, see
   // scaled_test)
