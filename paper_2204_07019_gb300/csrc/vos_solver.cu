@@ -875,6 +875,90 @@ __global__ void __launch_bounds__(kThreads) k_matvec_mfc_dot(Box bx, const float
   }
 }
 
+// Matrix-free pressure matvec q = A p (links from e, see k_stencil_mf) fused
+// with p.q (alpha = r.z / p.q).  Threads outside the box stay for the grid
+// reduction.
+__global__ void __launch_bounds__(kThreads) k_matvec_mf_dot(Box bx, const float* __restrict__ e, float s,
+                                                           const float* __restrict__ x, float* __restrict__ out,
+                                                           int zc, KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  PSum<float> ps;
+  if (i < bx.mx && j < bx.my && k0 < k1) {
+    const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+    const float hs = 0.5f * s;
+    long long c = i + sy * j + sz * k0;
+    float elo = (k0 > 0) ? __ldg(e + c - sz) : 0.0f;
+    float ec = __ldg(e + c);
+    float ehi = (k0 + 1 < bx.mz) ? __ldg(e + c + sz) : 0.0f;
+    float vlo = (k0 > 0) ? __ldg(x + c - sz) : 0.0f;
+    float vc = __ldg(x + c);
+    float vhi = (k0 + 1 < bx.mz) ? __ldg(x + c + sz) : 0.0f;
+    for (int k = k0; k < k1; ++k, c += sz) {
+      const bool up2 = (k + 2 < bx.mz) && (k + 1 < k1);
+      const float e2 = up2 ? __ldg(e + c + 2 * sz) : 0.0f;
+      const float v2 = up2 ? __ldg(x + c + 2 * sz) : 0.0f;
+      float d = (i == bx.mx - 1) ? 2.0f * ec * s : 0.0f;
+      float off = 0.0f;
+      if (i + 1 < bx.mx) {
+        const float a = (ec + __ldg(e + c + 1)) * hs;
+        d += a;
+        off += a * __ldg(x + c + 1);
+      }
+      if (i > 0) {
+        const float a = (ec + __ldg(e + c - 1)) * hs;
+        d += a;
+        off += a * __ldg(x + c - 1);
+      }
+      if (j + 1 < bx.my) {
+        const float a = (ec + __ldg(e + c + sy)) * hs;
+        d += a;
+        off += a * __ldg(x + c + sy);
+      }
+      if (j > 0) {
+        const float a = (ec + __ldg(e + c - sy)) * hs;
+        d += a;
+        off += a * __ldg(x + c - sy);
+      }
+      if (k + 1 < bx.mz) {
+        const float a = (ec + ehi) * hs;
+        d += a;
+        off += a * vhi;
+      }
+      if (k > 0) {
+        const float a = (ec + elo) * hs;
+        d += a;
+        off += a * vlo;
+      }
+      const float ax = d * vc - off;
+      out[c] = ax;
+      ps.add(vc, ax);
+      elo = ec;
+      ec = ehi;
+      ehi = e2;
+      vlo = vc;
+      vc = vhi;
+      vhi = v2;
+    }
+  }
+  double acc[1] = {ps.get()};
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    const double pq = acc[0];
+    sc->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      sc->breakdown = 1;
+      sc->done = 1;
+      sc->alpha = 0.0;
+    } else {
+      sc->alpha = sc->rz / pq;
+    }
+  }
+}
+
 // BiCGStab: p = r + beta (p - omega v)   (first iteration: p = r)
 template <typename T>
 __global__ void k_bicg_p(long long n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ p,
@@ -1442,6 +1526,12 @@ static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork*
       const ZCfg z = zcfg(Z.box);  // grid-reduction kernel: default shape, fixed summation order
       vlaunch("pcg_matvec_dot_mfc_f32_L0", 4.0 * n * 4.0, k_matvec_mfc_dot, z.grid, z.block, st, Z.box,
               (const float*)Z.diag, A.mfc, (const float*)k.p, (float*)k.q, z.zc, w->sc, rs);
+      fused_mv = true;
+    } else if (A.mfe && !use_net) {  // matrix-free pressure matvec fused with p.q
+      const Op<T> Z = zview(A);
+      const ZCfg z = zcfg(Z.box);
+      vlaunch("pcg_matvec_dot_mf_f32_L0", 4.0 * n * 4.0, k_matvec_mf_dot, z.grid, z.block, st, Z.box, A.mfe, A.mfs,
+              (const float*)k.p, (float*)k.q, z.zc, w->sc, rs);
       fused_mv = true;
     }
   }
