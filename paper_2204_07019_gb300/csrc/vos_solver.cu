@@ -508,7 +508,23 @@ __global__ void k_pcg_p(long long n, const T* __restrict__ z, T* __restrict__ p,
   DONE_RETURN(sc);
   const bool first = (sc->iters == 0);
   const T beta = (T)sc->beta;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+  long long c0 = 0;
+  if constexpr (sizeof(T) == 4) {  // FP32: 16-byte accesses (vectors are 256-byte aligned)
+    const long long n4 = n >> 2;
+    const float4* z4 = (const float4*)z;
+    float4* p4 = (float4*)p;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n4; v += (long long)gridDim.x * blockDim.x) {
+      const float4 zv = __ldg(z4 + v);
+      if (first) {
+        p4[v] = zv;
+      } else {
+        const float4 pv = p4[v];
+        p4[v] = make_float4(zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, zv.w + beta * pv.w);
+      }
+    }
+    c0 = n4 << 2;
+  }
+  for (long long c = c0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
     p[c] = first ? __ldg(z + c) : __ldg(z + c) + beta * p[c];
 }
 
@@ -628,7 +644,25 @@ __global__ void k_diag_prec(long long n, const T* __restrict__ dinv, const T* __
   VOS_COUNT_EXEC();
   DONE_RETURN(sc);
   PSum<T> ps, pz;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+  long long c0 = 0;
+  if constexpr (sizeof(T) == 4) {  // FP32: 16-byte accesses (256-byte aligned arrays)
+    const long long n4 = n >> 2;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n4; v += (long long)gridDim.x * blockDim.x) {
+      const float4 rv = __ldg((const float4*)r + v), dv = __ldg((const float4*)dinv + v);
+      const float4 zv = make_float4(dv.x * rv.x, dv.y * rv.y, dv.z * rv.z, dv.w * rv.w);
+      ((float4*)z)[v] = zv;
+      ps.add(rv.x, zv.x);
+      ps.add(rv.y, zv.y);
+      ps.add(rv.z, zv.z);
+      ps.add(rv.w, zv.w);
+      pz.add(zv.x, zv.x);
+      pz.add(zv.y, zv.y);
+      pz.add(zv.z, zv.z);
+      pz.add(zv.w, zv.w);
+    }
+    c0 = n4 << 2;
+  }
+  for (long long c = c0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     const T rc = r[c];
     const T zc = dinv[c] * rc;
     z[c] = zc;
@@ -803,7 +837,33 @@ __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restri
   DONE_RETURN(sc);
   const T alpha = (T)sc->alpha;
   PSum<T> ps, pd;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+  long long c0 = 0;
+  if constexpr (sizeof(T) == 4) {  // FP32 without the scaled norm: 16-byte accesses
+    if (!dscale) {
+      const long long n4 = n >> 2;
+      for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n4;
+           v += (long long)gridDim.x * blockDim.x) {
+        const float4 pv = __ldg((const float4*)p + v), qv4 = __ldg((const float4*)qv + v);
+        float4 ev = ((float4*)e)[v], rv = ((float4*)r)[v];
+        ev.x += alpha * pv.x;
+        ev.y += alpha * pv.y;
+        ev.z += alpha * pv.z;
+        ev.w += alpha * pv.w;
+        rv.x -= alpha * qv4.x;
+        rv.y -= alpha * qv4.y;
+        rv.z -= alpha * qv4.z;
+        rv.w -= alpha * qv4.w;
+        ((float4*)e)[v] = ev;
+        ((float4*)r)[v] = rv;
+        ps.add(rv.x, rv.x);
+        ps.add(rv.y, rv.y);
+        ps.add(rv.z, rv.z);
+        ps.add(rv.w, rv.w);
+      }
+      c0 = n4 << 2;
+    }
+  }
+  for (long long c = c0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     e[c] += alpha * p[c];
     T rc = r[c] - alpha * qv[c];
     r[c] = rc;
