@@ -178,7 +178,7 @@ def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
                                  "gbs": v[2] / (v[1] * 1e6) if v[1] > 0 else None} for k, v in rep.items()),
                                key=lambda r: -r["ms"])
             top = breakdown[0]["kernel"] if breakdown else None
-            breakdown = {"step_ms_profiled": step_ms, "kernel_ms_sum": tot, "kernels": breakdown[:14]}
+            breakdown = {"step_ms_profiled": step_ms, "kernel_ms_sum": tot, "kernels": breakdown[:48]}
         # timed steps: CUDA-graph replay (default launch mode), no per-kernel timing
         stream = torch.cuda.current_stream()
         iters = []

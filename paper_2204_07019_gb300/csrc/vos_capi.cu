@@ -262,14 +262,16 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     if (!r.converged) status = VOS_ENOCONV;
   }
   launch_project(P, h->eps, h->phi, dtp, h->us, h->u, h->p, st);
-  // S4-S6: reactive surface data (from eps^{n+1}, c^n), transport, rates
-  if (ivos) {
-    launch_ivos_faces(P, h->eps, h->c, h->fd, st);
-  } else {
+  // S4-S6: face data (convective fluxes of c^n; iVoS: reactive surface data
+  // from eps^{n+1}, c^n), transport, rates.  us[a] is dead from the
+  // projection until the next step copies u into it, so it holds the
+  // convective face fluxes meanwhile.
+  launch_face_data(P, ivos, h->eps, h->c, h->u, h->us, h->fd, st);
+  if (!ivos) {
     launch_vos_lambda(P, h->eps, h->prm.lambda, h->prm.method == VOS_PSI_PRIME, h->dstats, h->rs, st);
     launch_vos_coef(P, h->eps, h->dstats, h->kr, st);
   }
-  launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->u, h->kr, h->fd, dtp, S[4].h.mg.omega, S[4].op64,
+  launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->us, h->kr, h->fd, dtp, S[4].h.mg.omega, S[4].op64,
                         S[4].rhs, st);
   {
     SolveResult r =
@@ -313,13 +315,12 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
   VOS_CUDA_TRY(solve_capture<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter,
                                 h->work, h->rs, st, true, h->dsolve + 3, h->gs1, h->gs2));
   launch_project(P, h->eps, h->phi, dtp, h->us, h->u, h->p, st);
-  if (ivos) {
-    launch_ivos_faces(P, h->eps, h->c, h->fd, st);
-  } else {
+  launch_face_data(P, ivos, h->eps, h->c, h->u, h->us, h->fd, st);  // us: face-flux scratch (see the eager step)
+  if (!ivos) {
     launch_vos_lambda(P, h->eps, h->prm.lambda, h->prm.method == VOS_PSI_PRIME, h->dstats, h->rs, st);
     launch_vos_coef(P, h->eps, h->dstats, h->kr, st);
   }
-  launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->u, h->kr, h->fd, dtp, S[4].h.mg.omega, S[4].op64,
+  launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->us, h->kr, h->fd, dtp, S[4].h.mg.omega, S[4].op64,
                         S[4].rhs, st);
   VOS_CUDA_TRY(solve_capture<T>(S[4].op64, S[4].h, S[4].rhs, unknown_view(h, 4), h->prm.c_rtol, h->prm.max_iter,
                                 h->work, h->rs, st, true, h->dsolve + 4, h->gs1, h->gs2));

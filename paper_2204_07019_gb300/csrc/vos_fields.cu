@@ -291,7 +291,11 @@ void launch_project(const Phys& P, const double* eps, const double* phi, const d
 }
 
 // ---------------------------------------------------------------------------
-// iVoS face data (Sec. 2.3, App. B).  Interior faces along a:
+// Per-face data of the transport step, one launch per axis.
+// Every face: the explicit convective flux (per unit area) of c^n with the
+// van Leer face value upwinded along sign(u_f) (Sec. 2.5), evaluated once per
+// face here instead of once from each of the two adjacent cells.
+// iVoS interior faces along a (Sec. 2.3, App. B):
 //   g_f = ((eps_+ - eps_-)/dx along a; tangential: mean of the two cells'
 //   centred gradients), n_a = -g_a / (|g_f| + 1e-8/dx),
 //   s = k_c n_a / dx  (reactive flux per unit volume per unit c_f),
@@ -300,18 +304,55 @@ void launch_project(const Phys& P, const double* eps, const double* phi, const d
 //          c_f = c_U^{n+1} + corr keeps the implicit matrix an upwind
 //          M-matrix),
 //   evl = van Leer interpolation of eps along the flux direction.
+// FP64 arithmetic is scarce on this part, so the square root and division
+// of n_a are skipped where the eps gradient vanishes (pore and solid
+// interiors): there g2 = 0 and n_a = -g_n / delta = -0.
 // ---------------------------------------------------------------------------
-__global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ cold,
-                             FaceData fd) {
+__device__ __forceinline__ double conv_flux(const Phys& P, int a, int i, int j, int k, const double* cold,
+                                            const double* ua) {
+  // flux through face (i,j,k) of axis a (face coords), per unit area
+  int f[3] = {i, j, k};
+  const int m = f[a], n = ncell(P, a);
+  const double uf = ua[fidx(P, a, i, j, k)];
+  if (m == 0) return (a == 0) ? uf * P.c_in : 0.0;
+  if (m == n) return (a == 0) ? uf * cold[cidx(P, (a == 0) ? i - 1 : i, j, k)] : 0.0;
+  int mc[3] = {i, j, k};
+  mc[a] -= 1;
+  const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
+  const bool pos = uf >= 0.0;
+  int uu[3] = {i, j, k};
+  long long cU, cD;
+  bool has;
+  if (pos) {
+    cU = cm;
+    cD = cp;
+    uu[a] = m - 2;
+    has = m - 2 >= 0;
+  } else {
+    cU = cp;
+    cD = cm;
+    uu[a] = m + 1;
+    has = m + 1 <= n - 1;
+  }
+  const double vU = cold[cU], vD = cold[cD];
+  const double vUU = has ? cold[cidx(P, uu[0], uu[1], uu[2])] : vU;
+  return uf * (vU + vl_weight(vUU, vU, vD, has) * (vD - vU));
+}
+
+template <bool IVOS>
+__global__ void k_face_data(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ cold,
+                            const double* __restrict__ ua, double* __restrict__ cf, FaceData fd) {
   VOS_COUNT_EXEC();
   const Seg s = make_seg(fb);
   const int nb = (P.dim == 2) ? 2 : 3;
-  const double delta = 1e-8 / P.dx;
+  const double delta = 1e-8 / P.dx, idelta = 1.0 / delta, idx = 1.0 / P.dx;
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
     seg_decode(s, fb, q, i, j, k);
     if (i >= fb.mx) continue;
     const long long fcx = i + (long long)fb.mx * (j + (long long)fb.my * k);
+    cf[fcx] = conv_flux(P, a, i, j, k, cold, ua);
+    if (!IVOS) continue;
     int f[3] = {i, j, k};
     const int m = f[a], n = ncell(P, a);
     if (m < 1 || m > n - 1) {
@@ -323,7 +364,6 @@ __global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ e
     int mc[3] = {i, j, k};
     mc[a] -= 1;
     const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
-    const double idx = 1.0 / P.dx;
     const double gn = (eps[cp] - eps[cm]) * idx;
     double g2 = gn * gn;
     for (int b = 0; b < nb; ++b) {
@@ -331,7 +371,7 @@ __global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ e
       double gt = 0.5 * (cgrad(P, eps, b, mc[0], mc[1], mc[2]) + cgrad(P, eps, b, i, j, k));
       g2 += gt * gt;
     }
-    const double na = -gn / (sqrt(g2) + delta);
+    const double na = (g2 > 0.0) ? -gn / (sqrt(g2) + delta) : -gn * idelta;
     const bool pos = na > 0.0;
     // upwind U, downwind D, far upwind UU along a
     int uu[3] = {i, j, k};
@@ -357,12 +397,17 @@ __global__ void k_ivos_faces(Phys P, int a, Box fb, const double* __restrict__ e
   }
 }
 
-void launch_ivos_faces(const Phys& P, const double* eps, const double* cold, const FaceData fd[3],
-                       cudaStream_t st) {
+void launch_face_data(const Phys& P, int ivos, const double* eps, const double* cold, double* const u[3],
+                      double* const cf[3], const FaceData fd[3], cudaStream_t st) {
   const int nb = (P.dim == 2) ? 2 : 3;
   for (int a = 0; a < nb; ++a) {
     Box fb{P.nx + (a == 0), P.ny + (a == 1), P.nz + (a == 2)};
-    vlaunch("ivos_faces", 40.0 * box_cells(fb), k_ivos_faces, grid_for(fb, 0), kThreads, st, P, a, fb, eps, cold, fd[a]);
+    if (ivos)
+      vlaunch("face_data", 64.0 * box_cells(fb), k_face_data<true>, grid_for(fb, 0), kThreads, st, P, a, fb, eps, cold,
+              u[a], cf[a], fd[a]);
+    else
+      vlaunch("face_data", 24.0 * box_cells(fb), k_face_data<false>, grid_for(fb, 0), kThreads, st, P, a, fb, eps, cold,
+              u[a], cf[a], fd[a]);
   }
 }
 
@@ -449,41 +494,10 @@ void launch_vos_coef(const Phys& P, const double* eps, const double* stats, doub
 // diffusion (ghost 2 c_in - c_P).  R_f: VoS -> kr c; iVoS -> eps_P sum over
 // faces of the outward reactive flux with frozen van Leer weights.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double conv_flux(const Phys& P, int a, int i, int j, int k, const double* cold,
-                                            const double* ua) {
-  // flux through face (i,j,k) of axis a (face coords), per unit area
-  int f[3] = {i, j, k};
-  const int m = f[a], n = ncell(P, a);
-  const double uf = ua[fidx(P, a, i, j, k)];
-  if (m == 0) return (a == 0) ? uf * P.c_in : 0.0;
-  if (m == n) return (a == 0) ? uf * cold[cidx(P, (a == 0) ? i - 1 : i, j, k)] : 0.0;
-  int mc[3] = {i, j, k};
-  mc[a] -= 1;
-  const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
-  const bool pos = uf >= 0.0;
-  int uu[3] = {i, j, k};
-  long long cU, cD;
-  bool has;
-  if (pos) {
-    cU = cm;
-    cD = cp;
-    uu[a] = m - 2;
-    has = m - 2 >= 0;
-  } else {
-    cU = cp;
-    cD = cm;
-    uu[a] = m + 1;
-    has = m + 1 <= n - 1;
-  }
-  const double vU = cold[cU], vD = cold[cD];
-  const double vUU = has ? cold[cidx(P, uu[0], uu[1], uu[2])] : vU;
-  return uf * (vU + vl_weight(vUU, vU, vD, has) * (vD - vU));
-}
-
 template <bool IVOS>
 __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const double* __restrict__ eps_old,
-                                 const double* __restrict__ cold, const double* __restrict__ u0,
-                                 const double* __restrict__ u1, const double* __restrict__ u2,
+                                 const double* __restrict__ cold, const double* __restrict__ cf0,
+                                 const double* __restrict__ cf1, const double* __restrict__ cf2,
                                  const double* __restrict__ kr, FaceData f0, FaceData f1, FaceData f2, const double* __restrict__ dtp,
                                  double omega, Op<double> A, double* __restrict__ rhs) {
   VOS_COUNT_EXEC();
@@ -491,8 +505,9 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
   const Box bx{P.nx, P.ny, P.nz};
   const Seg s = make_seg(bx);
   const double idx2 = 1.0 / (P.dx * P.dx), idx1 = 1.0 / P.dx;
+  const double dh = P.D * 0.5 * idx2;  // diffusion link = dh (eps_P + eps_N)
   const int nb = (P.dim == 2) ? 2 : 3;
-  const double* us[3] = {u0, u1, u2};
+  const double* cfs[3] = {cf0, cf1, cf2};
   const FaceData fds[3] = {f0, f1, f2};
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
@@ -511,19 +526,19 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
       const bool hasp = cell_in(P, hi[0], hi[1], hi[2]);
       const bool hasm = cell_in(P, lo[0], lo[1], lo[2]);
       if (hasp) {
-        double a = P.D * 0.5 * (e + eps[cidx(P, hi[0], hi[1], hi[2])]) * idx2;
+        double a = dh * (e + eps[cidx(P, hi[0], hi[1], hi[2])]);
         diag += a;
         offp[d] -= a;
       }
       if (hasm) {
-        double a = P.D * 0.5 * (e + eps[cidx(P, lo[0], lo[1], lo[2])]) * idx2;
+        double a = dh * (e + eps[cidx(P, lo[0], lo[1], lo[2])]);
         diag += a;
         offm[d] -= a;
       }
-      // convective fluxes through the plus and minus faces
+      // convective fluxes through the plus and minus faces (k_face_data)
       int fp[3] = {i, j, k};
       fp[d] += 1;
-      adv += (conv_flux(P, d, fp[0], fp[1], fp[2], cold, us[d]) - conv_flux(P, d, i, j, k, cold, us[d])) * idx1;
+      adv += (cfs[d][fidx(P, d, fp[0], fp[1], fp[2])] - cfs[d][fidx(P, d, i, j, k)]) * idx1;
       if (IVOS) {
         // reactive flux F = s (c_U^{n+1} + corr): upwind value implicit,
         // the deferred van Leer correction on the right-hand side
@@ -570,15 +585,15 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
 }
 
 void launch_trans_assemble(const Phys& P, int ivos, const double* eps, const double* eps_old, const double* cold,
-                           double* const u[3], const double* kr, const FaceData fd[3], const double* __restrict__ dtp, double omega,
+                           double* const cf[3], const double* kr, const FaceData fd[3], const double* __restrict__ dtp, double omega,
                            Op<double> A, double* rhs, cudaStream_t st) {
   int g = grid_for(A.box, 0);
   if (ivos)
     vlaunch("trans_assemble", (6.0 + 5.0 * P.dim) * 8.0 * box_cells(A.box), k_trans_assemble<true>, g, kThreads, st, P,
-            eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2], dtp, omega, A, rhs);
+            eps, eps_old, cold, cf[0], cf[1], cf[2], kr, fd[0], fd[1], fd[2], dtp, omega, A, rhs);
   else
     vlaunch("trans_assemble", (7.0 + 2.0 * P.dim) * 8.0 * box_cells(A.box), k_trans_assemble<false>, g, kThreads, st, P,
-            eps, eps_old, cold, u[0], u[1], u[2], kr, fd[0], fd[1], fd[2], dtp, omega, A, rhs);
+            eps, eps_old, cold, cf[0], cf[1], cf[2], kr, fd[0], fd[1], fd[2], dtp, omega, A, rhs);
 }
 
 // ---------------------------------------------------------------------------

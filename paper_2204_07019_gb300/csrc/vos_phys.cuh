@@ -48,13 +48,15 @@ void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3],
 void launch_project(const Phys& P, const double* eps, const double* phi, const double* dtp, double* const us[3],
                     double* const u[3], double* p, cudaStream_t st);
 // S5/S6
-void launch_ivos_faces(const Phys& P, const double* eps, const double* cold, const FaceData fd[3],
-                       cudaStream_t st);
+// cf[a]: receives the convective flux of c^n through every face of axis a
+// (read by the transport assembly); fd: the iVoS face data (ivos only).
+void launch_face_data(const Phys& P, int ivos, const double* eps, const double* cold, double* const u[3],
+                      double* const cf[3], const FaceData fd[3], cudaStream_t st);
 void launch_vos_lambda(const Phys& P, const double* eps, double lambda_fixed, int fit, double* stats,
                        const RedScratch& rs, cudaStream_t st);
 void launch_vos_coef(const Phys& P, const double* eps, const double* stats, double* kr, cudaStream_t st);
 void launch_trans_assemble(const Phys& P, int ivos, const double* eps, const double* eps_old, const double* cold,
-                           double* const u[3], const double* kr, const FaceData fd[3], const double* dtp, double omega,
+                           double* const cf[3], const double* kr, const FaceData fd[3], const double* dtp, double omega,
                            Op<double> A, double* rhs, cudaStream_t st);
 void launch_rates(const Phys& P, int ivos, const double* eps, const double* c, const double* kr,
                   const FaceData fd[3], double* R, double* Rf, double* stats, const RedScratch& rs,

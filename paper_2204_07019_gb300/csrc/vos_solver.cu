@@ -532,27 +532,35 @@ __global__ void k_pcg_p(long long n, const T* __restrict__ z, T* __restrict__ p,
 template <typename T, bool SYM>
 __global__ void __launch_bounds__(kThreads) k_outer_residual_z(Op<double> A, const double* __restrict__ b,
                                                               View<double> x, T* __restrict__ rT, double* outer,
-                                                              int zc, RedScratch rs) {
+                                                              const int* pass, int zc, RedScratch rs) {
   VOS_COUNT_EXEC();
   // outer[0] = |D^-1 r|^2 and outer[1] = |D^-1 b|^2 (convergence test);
   // outer[2] = |r|^2, the unscaled norm the inner Krylov loop measures.
+  // b is fixed during a solve, so |D^-1 b|^2 is summed on its first pass
+  // only (*pass == 0; always when pass is null) and kept in outer[1]: FP64
+  // arithmetic, not memory, bounds this kernel on this part.
+  const bool need_bb = (pass == nullptr) || (*pass == 0);
   double acc[3] = {0.0, 0.0, 0.0};
   auto val = [&](long long, int i, int j, int k) -> double {
     return __ldg(x.base + i + (long long)x.sy * j + (long long)x.sz * k);
   };
   auto emit = [&](long long c, int, int, int, double, double ax, double) {
-    const double r = __ldg(b + c) - ax;
+    const double bc = __ldg(b + c);
+    const double r = bc - ax;
     rT[c] = (T)r;
     const double di = A.dinv[c];  // omega / diag: the constant omega cancels in the ratio
-    const double r1 = r * di, b1 = b[c] * di;
+    const double r1 = r * di;
     acc[0] += r1 * r1;
-    acc[1] += b1 * b1;
+    if (need_bb) {
+      const double b1 = bc * di;
+      acc[1] += b1 * b1;
+    }
     acc[2] += r * r;
   };
   zmarch<double, SYM>(A, zc, val, emit);
   if (grid_sum<3>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
     outer[0] = acc[0];
-    outer[1] = acc[1];
+    if (need_bb) outer[1] = acc[1];
     outer[2] = acc[2];
   }
 }
@@ -1105,12 +1113,15 @@ __global__ void k_view_zero(Box bx, View<double> x) {
 }
 
 // Convert the FP64 operator into T (level 0 of a mixed-precision hierarchy).
+// links == 0: diagonal and Jacobi weights only (a constant-link fine level
+// without coarse levels reads nothing else).
 template <typename T>
-__global__ void k_op_convert(Op<double> A, Op<T> B, long long n) {
+__global__ void k_op_convert(Op<double> A, Op<T> B, long long n, int links) {
   VOS_COUNT_EXEC();
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     B.diag[c] = (T)A.diag[c];
     B.dinv[c] = (T)A.dinv[c];
+    if (!links) continue;
     B.xp[c] = (T)A.xp[c];
     B.yp[c] = (T)A.yp[c];
     if (A.box.mz > 1) B.zp[c] = (T)A.zp[c];
@@ -1857,8 +1868,9 @@ cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, V
   const int max_outer = mixed ? 30 : 8;
   const bool sym = h.lev[0].op.sym != 0;
   if (mixed) {
-    vlaunch("op_convert", (2.0 + n_offs(op64)) * n * (8.0 + sizeof(T)), k_op_convert<T>, flat_grid(n), kThreads, st,
-            op64, h.lev[0].op, n);
+    const int links = (use_mg || !sym || h.lev[0].op.mfc == 0.0f) ? 1 : 0;
+    vlaunch("op_convert", (2.0 + (links ? n_offs(op64) : 0)) * n * (8.0 + sizeof(T)), k_op_convert<T>, flat_grid(n),
+            kThreads, st, op64, h.lev[0].op, n, links);
   }
   if (use_mg || !sym) build_coarse_levels<T>(h, st);
   vlaunch("ctrl_init", 0.0, k_ctrl_init, 1, 32, st, ss, w->sc);
@@ -1872,12 +1884,13 @@ cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, V
     const View<double> xz = zview_x(x, bx);
     const ZCfg zr = zcfg(oz.box);
     const double rbytes = (4.0 + n_offs(op64)) * n * 8.0 + n * sizeof(T);
+    const int* pass = &ss->outer;  // 0 until the controller starts the first pass
     if (op64.sym)
       vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, true>, zr.grid, zr.block, s1, oz, b, xz, (T*)w->r,
-              w->outer, zr.zc, rs);
+              w->outer, pass, zr.zc, rs);
     else
       vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, false>, zr.grid, zr.block, s1, oz, b, xz, (T*)w->r,
-              w->outer, zr.zc, rs);
+              w->outer, pass, zr.zc, rs);
     cudaGraph_t g1;
     VOS_CUDA_TRY(capture_graph_of(s1, &g1));
     VOS_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, g1, 0, cudaGraphCondAssignDefault));
@@ -1929,7 +1942,7 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
   bool use_net = use_mg && h.net != nullptr && op64.sym;
   const int g = grid_for(bx, 0);
   if (mixed) {
-    vlaunch("op_convert", (2.0 + n_offs(op64)) * n * (8.0 + sizeof(T)), k_op_convert<T>, flat_grid(n), kThreads, st, op64, h.lev[0].op, n);
+    vlaunch("op_convert", (2.0 + n_offs(op64)) * n * (8.0 + sizeof(T)), k_op_convert<T>, flat_grid(n), kThreads, st, op64, h.lev[0].op, n, 1);
   }
   if (use_mg) build_coarse_levels<T>(h, st);
   int total = 0;
@@ -1940,10 +1953,10 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
   for (int outer = 0;; ++outer) {
     if (op64.sym)
       vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, true>, zr.grid, zr.block, st, oz, b, xz, (T*)w->r,
-              w->outer, zr.zc, rs);
+              w->outer, (const int*)nullptr, zr.zc, rs);
     else
       vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, false>, zr.grid, zr.block, st, oz, b, xz, (T*)w->r,
-              w->outer, zr.zc, rs);
+              w->outer, (const int*)nullptr, zr.zc, rs);
     cudaMemcpyAsync(w->outer_host, w->outer, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     const double rr = w->outer_host[0], bb = w->outer_host[1];
@@ -2011,13 +2024,13 @@ int residual_snapshots(const Op<double>& op64, Hier<T>& h, const double* b, View
   const Box bx = op64.box;
   const long long n = box_cells(bx);
   if (sizeof(T) == 4)
-    vlaunch("op_convert", 0.0, k_op_convert<T>, flat_grid(n), kThreads, st, op64, h.lev[0].op, n);
+    vlaunch("op_convert", 0.0, k_op_convert<T>, flat_grid(n), kThreads, st, op64, h.lev[0].op, n, 1);
   build_coarse_levels<T>(h, st);
   const Op<double> oz = zview(op64);
   const View<double> xz = zview_x(x, bx);
   const ZCfg zr = zcfg(oz.box);
   vlaunch("outer_residual_f64", 0.0, k_outer_residual_z<T, true>, zr.grid, zr.block, st, oz, b, xz, (T*)w->r,
-          w->outer, zr.zc, rs);
+          w->outer, (const int*)nullptr, zr.zc, rs);
   int maxit = 0;
   for (int i = 0; i < count; ++i) maxit = iters[i] > maxit ? iters[i] : maxit;
   const KVec<T> k = kvec<T>(w, false);
