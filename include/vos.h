@@ -311,6 +311,19 @@ int vos_unet_solve_stats(const vos_handle* h, int32_t* net_iters, int32_t* fallb
  * correction field as scratch (it is rebuilt by every step). */
 int vos_pressure_snapshots(vos_handle* h, int32_t count, const int32_t* iters, float* out);
 
+/* Self-check of the FP64 quotient the physics kernels use in place of IEEE
+ * division (no counterpart in the paper; FP64 instructions are the scarce
+ * resource of those kernels): Newton-Raphson refinement of the hardware
+ * reciprocal estimate, one step on the reciprocal and one on the quotient,
+ * IEEE division for |d| outside [2^-1000, 2^1000] or not finite (a zero
+ * numerator gives +0 whatever its sign).  For the
+ * n pairs (a[i], d[i]) writes q_fast[i] = that quotient and q_ieee[i] = the
+ * IEEE-rounded a[i] / d[i].  All four arrays are device memory of n doubles
+ * owned by the caller; the call runs on the legacy default stream and
+ * synchronises it.  Errors: VOS_EINVAL (n < 0, NULL array with n > 0),
+ * VOS_ECUDA; message via vos_last_error(NULL). */
+int vos_fp64_div_check(const double* a, const double* d, int64_t n, double* q_fast, double* q_ieee);
+
 /* Stencil tile of one multigrid level of one linear system of h: sys 0-2
  * the momentum components u, v, w, 3 the pressure correction, 4 the
  * concentration; level 0 is the fine grid.  *tx, *ty: threads of a block

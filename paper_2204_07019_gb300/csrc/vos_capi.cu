@@ -783,6 +783,17 @@ void vos_destroy(vos_handle* h) {
 
 size_t vos_device_bytes(const vos_handle* h) { return h ? h->bytes : 0; }
 
+int vos_fp64_div_check(const double* a, const double* d, int64_t n, double* q_fast, double* q_ieee) {
+  if (n < 0) return set_err(nullptr, VOS_EINVAL, "vos_fp64_div_check: n < 0");
+  if (n == 0) return VOS_OK;
+  if (!a || !d || !q_fast || !q_ieee) return set_err(nullptr, VOS_EINVAL, "vos_fp64_div_check: NULL array");
+  launch_div_check(a, d, (long long)n, q_fast, q_ieee, 0);
+  cudaError_t e = cudaStreamSynchronize(0);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(nullptr, VOS_ECUDA, "vos_fp64_div_check: %s", cudaGetErrorString(e));
+  return VOS_OK;
+}
+
 int vos_tile_config(const vos_handle* h, int32_t sys, int32_t level, int32_t* tx, int32_t* ty, int32_t* zc,
                     int32_t* tuned) {
   if (!h || !tx || !ty || !zc || !tuned) return set_err(nullptr, VOS_EINVAL, "vos_tile_config: NULL argument");

@@ -31,27 +31,46 @@ __device__ __forceinline__ long long fidx(const Phys& P, int a, int i, int j, in
 }
 __device__ __forceinline__ int ncell(const Phys& P, int b) { return (b == 0) ? P.nx : (b == 1) ? P.ny : P.nz; }
 
-// Kozeny-Carman inverse permeability (Eq. perm): (1 - eps)^2 / (k0 eps^3).
 // omega / diag for the Jacobi smoother, the diagonal preconditioner and the
-// scaled residual norm (exact: with an FP32 reciprocal here an FP64 solve of
-// the 1024 x 512 micromodel to 1e-10 no longer converged).
-__device__ __forceinline__ double jacobi_weight(double omega, double diag) { return omega / diag; }
+// scaled residual norm (within a couple of ulp of the IEEE quotient; an FP32
+// reciprocal here, 6e-8 off, is too coarse for the FP64 solves).
+__device__ __forceinline__ double jacobi_weight(double omega, double diag) { return fdiv_nr(omega, diag); }
 
+// Kozeny-Carman inverse permeability (Eq. perm): (1 - eps)^2 / (k0 eps^3).
 __device__ __forceinline__ double kinv(double e, double k0) {
   double s = 1.0 - e;
-  return s * s / (k0 * e * e * e);
+  return fdiv_nr(s * s, k0 * e * e * e);
 }
 
-// van Leer weight w in c_f = c_U + w (c_D - c_U): w = psi(r)/2 with
-// psi(r) = (r + |r|)/(1 + |r|), r = a/b, a = c_U - c_UU, b = c_D - c_U; zero
-// without a far-upwind cell or for |b| <= 1e-300.  For r > 0 (a b > 0)
-// psi(r)/2 = r/(1 + r) = a/(a + b), and psi = 0 otherwise: one FP64
-// division instead of two (FP64 division is slow on this part).
-__device__ __forceinline__ double vl_weight(double cUU, double cU, double cD, bool has) {
+// |x| <= 1e-300 on the bit pattern (no FP64 instruction): the magnitude bits
+// of a double order like its absolute value.
+__device__ __forceinline__ bool tiny300(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) <= 0x01a56e1fc2f8f359LL;  // bits of 1e-300
+}
+
+// van Leer correction of a face value, c_f = c_U + w (c_D - c_U): w = psi(r)/2
+// with psi(r) = (r + |r|)/(1 + |r|), r = a/b, a = c_U - c_UU, b = c_D - c_U.
+// For r > 0 (a, b non-zero with one sign) psi(r)/2 = r/(1 + r) = a/(a + b),
+// so w b = a b / (a + b); psi = 0 otherwise, without a far-upwind cell, or
+// for |b| <= 1e-300.  Returns w b; the sign and magnitude tests run on the
+// bit patterns (FP64 instructions are the bottleneck of these kernels).
+__device__ __forceinline__ double vl_corr(double cUU, double cU, double cD, bool has) {
   const double b = cD - cU;
-  if (!has || fabs(b) <= 1e-300) return 0.0;
+  if (!has || tiny300(b)) return 0.0;
   const double a = cU - cUU;
-  return (a * b > 0.0) ? a / (a + b) : 0.0;
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  if ((ia ^ ib) < 0 || (ia << 1) == 0) return 0.0;  // a b <= 0
+  return fdiv_nr(a * b, a + b);
+}
+
+// eps difference across a cell along b (zero-gradient ghosts): 2 dx times the
+// centred gradient component
+__device__ __forceinline__ double cdiff(const Phys& P, const double* eps, int b, int i, int j, int k) {
+  int n = ncell(P, b);
+  int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+  lo[b] = lo[b] > 0 ? lo[b] - 1 : 0;
+  hi[b] = hi[b] + 1 < n ? hi[b] + 1 : n - 1;
+  return eps[cidx(P, hi[0], hi[1], hi[2])] - eps[cidx(P, lo[0], lo[1], lo[2])];
 }
 
 // centred gradient component b of eps at a cell, zero-gradient ghosts
@@ -336,7 +355,7 @@ __device__ __forceinline__ double conv_flux(const Phys& P, int a, int i, int j, 
   }
   const double vU = cold[cU], vD = cold[cD];
   const double vUU = has ? cold[cidx(P, uu[0], uu[1], uu[2])] : vU;
-  return uf * (vU + vl_weight(vUU, vU, vD, has) * (vD - vU));
+  return uf * (vU + vl_corr(vUU, vU, vD, has));
 }
 
 template <bool IVOS>
@@ -345,7 +364,7 @@ __global__ void k_face_data(Phys P, int a, Box fb, const double* __restrict__ ep
   VOS_COUNT_EXEC();
   const Seg s = make_seg(fb);
   const int nb = (P.dim == 2) ? 2 : 3;
-  const double delta = 1e-8 / P.dx, idelta = 1.0 / delta, idx = 1.0 / P.dx;
+  const double kcx = P.kc / P.dx;
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
     seg_decode(s, fb, q, i, j, k);
@@ -364,15 +383,19 @@ __global__ void k_face_data(Phys P, int a, Box fb, const double* __restrict__ ep
     int mc[3] = {i, j, k};
     mc[a] -= 1;
     const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
-    const double gn = (eps[cp] - eps[cm]) * idx;
-    double g2 = gn * gn;
+    // gradient in eps differences (dx g): normal dn, tangential the mean of
+    // the two cells' centred components; n_a = -g_n / (|g| + 1e-8/dx)
+    // = -dn / (|dx g| + 1e-8)
+    const double dn = eps[cp] - eps[cm];
+    double g2 = dn * dn;
     for (int b = 0; b < nb; ++b) {
       if (b == a) continue;
-      double gt = 0.5 * (cgrad(P, eps, b, mc[0], mc[1], mc[2]) + cgrad(P, eps, b, i, j, k));
-      g2 += gt * gt;
+      const double tg = 0.25 * (cdiff(P, eps, b, mc[0], mc[1], mc[2]) + cdiff(P, eps, b, i, j, k));
+      g2 += tg * tg;
     }
-    const double na = (g2 > 0.0) ? -gn / (sqrt(g2) + delta) : -gn * idelta;
-    const bool pos = na > 0.0;
+    const double na = (__double_as_longlong(g2) != 0) ? -fdiv_nr(dn, sqrt(g2) + 1e-8) : -dn * 1e8;
+    const long long idn = __double_as_longlong(dn);
+    const bool pos = idn < 0 && (idn << 1) != 0;  // n_a > 0
     // upwind U, downwind D, far upwind UU along a
     int uu[3] = {i, j, k};
     long long cU, cD;
@@ -389,11 +412,9 @@ __global__ void k_face_data(Phys P, int a, Box fb, const double* __restrict__ ep
       has = m + 1 <= n - 1;
     }
     const long long cUU = has ? cidx(P, uu[0], uu[1], uu[2]) : cU;
-    fd.s[fcx] = P.kc * na * idx;
-    const double cu = cold[cU], cd = cold[cD];
-    fd.corr[fcx] = vl_weight(cold[cUU], cu, cd, has) * (cd - cu);
-    const double eU = eps[cU], eD = eps[cD];
-    fd.evl[fcx] = eU + vl_weight(eps[cUU], eU, eD, has) * (eD - eU);
+    fd.s[fcx] = kcx * na;
+    fd.corr[fcx] = vl_corr(cold[cUU], cold[cU], cold[cD], has);
+    fd.evl[fcx] = eps[cU] + vl_corr(eps[cUU], eps[cU], eps[cD], has);
   }
 }
 
@@ -449,6 +470,23 @@ __global__ void k_vos_lambda(Phys P, const double* __restrict__ eps, double* sta
 __global__ void k_set_scalar(double* dst, double v) {
   VOS_COUNT_EXEC();
   if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
+}
+
+__global__ void k_div_check(const double* __restrict__ a, const double* __restrict__ d, long long n,
+                            double* __restrict__ qf, double* __restrict__ qi) {
+  VOS_COUNT_EXEC();
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    qf[c] = fdiv_nr(a[c], d[c]);
+    qi[c] = a[c] / d[c];
+  }
+}
+
+void launch_div_check(const double* a, const double* d, long long n, double* q_fast, double* q_ieee,
+                      cudaStream_t st) {
+  long long g = (n + kThreads - 1) / kThreads;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  vlaunch("div_check", 32.0 * n, k_div_check, (int)g, kThreads, st, a, d, n, q_fast, q_ieee);
 }
 
 void launch_set_scalar(double* dst, double v, cudaStream_t st) {

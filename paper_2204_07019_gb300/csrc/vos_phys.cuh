@@ -12,6 +12,28 @@ struct Phys {
   unsigned wall_mask;
 };
 
+// ---------------------------------------------------------------------------
+// FP64 arithmetic is the scarce resource of the physics kernels on this part
+// (a few FP64 operations per SM and clock, against 128 FP32 ones), so their
+// divisions use this quotient instead of the IEEE one: Newton-Raphson on the
+// reciprocal seeded by the hardware estimate (PTX rcp.approx.ftz.f64),
+// y1 = y0 + y0 (1 - d y0), then one Newton step on the quotient,
+// q1 = q0 + y1 (a - d q0) with q0 = a y1.  A seed with relative error e
+// leaves e^2 after the first step and e^4 after the second, so q1 is within
+// a couple of ulp of a/d (vos_fp64_div_check compares it with the IEEE
+// quotient): five FP64 operations.  |d| outside [2^-1000, 2^1000], zero,
+// infinite or NaN takes the IEEE division.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fdiv_nr(double a, double d) {
+  const unsigned ex = ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;
+  if (ex < 23u || ex > 2023u) return a / d;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  y = fma(y, fma(-d, y, 1.0), y);
+  const double q = a * y;
+  return fma(y, fma(-d, q, a), q);
+}
+
 // Device diagnostics (FP64), indices into the stats array.
 enum StatIdx {
   ST_CLAMP = 0,   // sum(raw - clamped) V
@@ -62,6 +84,9 @@ void launch_rates(const Phys& P, int ivos, const double* eps, const double* c, c
                   const FaceData fd[3], double* R, double* Rf, double* stats, const RedScratch& rs,
                   cudaStream_t st);
 void launch_set_scalar(double* dst, double v, cudaStream_t st);
+// q_fast[i] = fdiv_nr(a[i], d[i]), q_ieee[i] = a[i] / d[i] (device arrays).
+void launch_div_check(const double* a, const double* d, long long n, double* q_fast, double* q_ieee,
+                      cudaStream_t st);
 void launch_dt_limits(const Phys& P, const double* eps, double* const u[3], const double* R, double* stats,
                       const RedScratch& rs, cudaStream_t st);
 

@@ -21,7 +21,7 @@ __all__ = [
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
     "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
-    "vos_floating_clusters", "vos_tile_config", "vos_conv3d_bf16", "UNet", "vos_set_unet_preconditioner",
+    "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16", "UNet", "vos_set_unet_preconditioner",
     "vos_unet_solve_stats", "vos_pressure_snapshots", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
 ]
 
@@ -37,7 +37,7 @@ EXPORTED_SYMBOLS = [
     "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
     "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle", "vos_batch_destroy",
-    "vos_floating_clusters", "vos_tile_config", "vos_conv3d_bf16",
+    "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16",
     "vos_unet_create", "vos_unet_num_params", "vos_unet_set_params", "vos_unet_get_params", "vos_unet_get_grads",
     "vos_unet_forward", "vos_unet_backward", "vos_unet_train_step", "vos_unet_eval_loss", "vos_unet_destroy",
     "vos_set_unet_preconditioner", "vos_unet_solve_stats", "vos_pressure_snapshots",
@@ -149,6 +149,9 @@ def load_library(path=None):
     lib.vos_floating_clusters.restype = ctypes.c_int
     lib.vos_tile_config.argtypes = [H, ctypes.c_int32, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4
     lib.vos_tile_config.restype = ctypes.c_int
+    lib.vos_fp64_div_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+    lib.vos_fp64_div_check.restype = ctypes.c_int
     lib.vos_conv3d_bf16.argtypes = [ctypes.c_void_p] + [ctypes.c_int32] * 4 + [ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.vos_conv3d_bf16.restype = ctypes.c_int
@@ -366,6 +369,27 @@ def _ptr(t):
     if t is None:
         return None
     return int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t)
+
+
+def vos_fp64_div_check(a, d):
+    """vos_fp64_div_check on host arrays: returns (q_fast, q_ieee), the
+    physics kernels' FP64 quotient a/d and the IEEE one, computed on the
+    device (torch provides the device buffers)."""
+    import torch
+    lib = load_library()
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    d = np.ascontiguousarray(d, dtype=np.float64).ravel()
+    if a.shape != d.shape:
+        raise ValueError("a and d differ in size")
+    torch.cuda.synchronize()
+    ad = torch.from_numpy(a).cuda()
+    dd = torch.from_numpy(d).cuda()
+    qf = torch.empty_like(ad)
+    qi = torch.empty_like(ad)
+    torch.cuda.synchronize()
+    rc = lib.vos_fp64_div_check(_ptr(ad), _ptr(dd), int(a.size), _ptr(qf), _ptr(qi))
+    _check(lib, None, rc)
+    return qf.cpu().numpy(), qi.cpu().numpy()
 
 
 def vos_conv3d_bf16(x, shape, cin, w, bias, cout, relu=False, y_f32=None, y_bf16=None, stream=None):
