@@ -137,10 +137,18 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes per algorithmic byte of the fine-level FP32 Jacobi sweep, from one
-# ncu capture of the 128^3 rock (profiles/mg_jac_f32_L0_traffic_rock128.md):
-# 23.94 B/cell read against 28 B/cell algorithmic (the output stays in L2).
-JAC_TRAFFIC_PER_ALG_BYTE = 23.94 / 28.0
+# DRAM bytes per algorithmic byte of the kernels that can be the roofline's
+# dominant kernel, each from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of a full launch, caches flushed):
+#   pcg_xr_f32_L0: 356,163,072 B against 402,653,184 B algorithmic (24 B per
+#     unknown, 16,777,216 unknowns of the rock 256^3 momentum system; every
+#     operand read once, part of the writes still in L2 when the kernel ends);
+#   mg_jac_f32_L0: 23.94 B/cell read against 28 B/cell algorithmic (rock 128^3,
+#     the output stays in L2).
+TRAFFIC_PER_ALG_BYTE = {
+    "pcg_xr_f32_L0": (356163072.0 / 402653184.0, "ncu dram bytes of one full-size launch (rock 256^3) per algorithmic byte"),
+    "mg_jac_f32_L0": (23.94 / 28.0, "ncu dram bytes of the 128^3 capture scaled by units processed"),
+}
 
 
 def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
@@ -211,13 +219,13 @@ def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
             peak, src = measured_peaks()
             if n > 0 and kms > 0:
                 ach = kbytes / (kms * 1e-3) / 1e9
-                traffic = kbytes / n * JAC_TRAFFIC_PER_ALG_BYTE if top == "mg_jac_f32_L0" else None
+                tr = TRAFFIC_PER_ALG_BYTE.get(top)
+                traffic = kbytes / n * tr[0] if tr else None
                 roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                         "traffic": traffic, "kernel": top, "launches": n, "avg_launch_us": kms * 1e3 / n,
                         "alg_bytes_per_launch": kbytes / n, "peak_source": src,
                         "window": "steps after the timed ones, same handle and dt, kernel launches event-timed",
-                        "traffic_source": ("ncu dram bytes of the 128^3 capture scaled by units processed"
-                                           if traffic is not None else None)}
+                        "traffic_source": tr[1] if tr else None}
         tiles = {}
         for lev in (0, 1):
             try:
@@ -464,7 +472,8 @@ def main():
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                "config": {"workload": "batch64", "desc": "64 disc micromodels, sides U[128,768], Pe U_log[1,100], "
-                          "Da U_log[0.01,100], iVoS, mixed; one stream + host worker per instance",
+                          "Da U_log[0.01,100], iVoS, mixed; each batch step one CUDA graph with "
+                          "every instance as a parallel branch",
                           "cells": N, "dt_range": r["dt_range"]},
                "gpu_launches": r["launches"], "iters_p_mean": r["iters_p_mean"], "clocks": ck,
                "roofline": None}
@@ -488,12 +497,13 @@ def main():
     value = N * world / (ms * 1e-3)
     p64 = dict(prm)
     p64["precision"] = 0
-    r64 = time_gpu(V, es, p64, max(args.fp64_steps, 1), 2, torch, profile=False)
+    # FP64-only solver leg (--fp64-steps 0 skips it, for profiling runs)
+    r64 = time_gpu(V, es, p64, args.fp64_steps, 2, torch, profile=False) if args.fp64_steps > 0 else None
     e2e = time_e2e(V, es, prm, max(2, args.steps // 2), dt)
     learned = None
     if not args.no_learned and es.ndim == 3 and min(es.shape) >= 64:
         learned = learned_leg(V, es, prm, dt, 3, torch)
-        learned["vs_fp64"] = learned["value"] / (N / (r64["ms"] * 1e-3))
+        learned["vs_fp64"] = learned["value"] / (N / (r64["ms"] * 1e-3)) if r64 else None
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -503,8 +513,8 @@ def main():
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "launch": "eager" if args.eager else "graph", "tiles": r["tiles"]},
            "roofline": r["roofline"], "gpu_launches": r["launches"],
-           "fp64": {"value": N * world / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
-                    "iters_p_mean": float(np.mean([i[1] for i in r64["iters"]]))},
+           "fp64": ({"value": N * world / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
+                     "iters_p_mean": float(np.mean([i[1] for i in r64["iters"]]))} if r64 else None),
            "solver": {"iters_u_mean": [float(np.mean([i[0][a] for i in iters])) for a in range(3)],
                       "iters_p_mean": float(np.mean([i[1] for i in iters])),
                       "iters_c_mean": float(np.mean([i[2] for i in iters])),
