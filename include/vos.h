@@ -330,8 +330,9 @@ int vos_fp64_div_check(const double* a, const double* d, int64_t n, double* q_fa
  * along x and y (tx * ty = 256); *zc: planes each block marches along z
  * (along y for 2D grids); *tuned: 1 when the autotuner measured this shape
  * at create (levels of >= 65,536 cells; the fastest Jacobi sweep among tile
- * widths 32/64/128 and z chunks for about 1024-8192 blocks), 0 for the
- * default (32 x 8, or 256 x 1 on 2D grids, about 4096 blocks).  Errors:
+ * widths 32/64/128 and z chunks of one or more planes for about 1024-8192
+ * blocks), 0 for the default (32 x 8, or 256 x 1 on 2D grids, about 4096
+ * blocks of one or more planes).  Errors:
  * VOS_EINVAL (NULL argument, sys or level out of range). */
 int vos_tile_config(const vos_handle* h, int32_t sys, int32_t level, int32_t* tx, int32_t* ty, int32_t* zc,
                     int32_t* tuned);

@@ -588,15 +588,15 @@ struct ZCfg {
   int zc;
 };
 // A tile of tx x (kThreads / tx) threads in (x, y) marching over zc planes,
-// zc chosen so that the grid has about target blocks (at least 4 planes per
-// block, at most kMaxRedBlocks blocks).
-static ZCfg zcfg_tile(Box b, int tx, long long target) {
+// zc chosen so that the grid has about target blocks (at least zmin planes
+// per block, at most kMaxRedBlocks blocks).
+static ZCfg zcfg_tile(Box b, int tx, long long target, int zmin = 4) {
   ZCfg z;
   const int ty = kThreads / tx;
   const long long gx = (b.mx + tx - 1) / tx, gy = (b.my + ty - 1) / ty;
   const long long tiles = gx * gy;
   long long zc = (tiles * b.mz + target - 1) / target;
-  if (zc < 4) zc = 4;
+  if (zc < zmin) zc = zmin;
   if (zc > b.mz) zc = b.mz;
   while (tiles * ((b.mz + zc - 1) / zc) > kMaxRedBlocks) ++zc;
   z.block = dim3(tx, ty, 1);
@@ -608,6 +608,12 @@ static ZCfg zcfg_tile(Box b, int tx, long long target) {
 // about 4096 blocks.  Kernels with grid reductions always use this shape, so
 // their summation order does not depend on tuning.
 static ZCfg zcfg(Box b) { return zcfg_tile(b, (b.my == 1) ? 256 : 32, 4096); }
+// Kernels without reductions (stencil sweeps, prolongation): the same tile,
+// but blocks may march as little as one plane.  On small coarse levels each
+// plane step waits for its loads, so fewer planes per block and more blocks
+// cut the sweep's latency (a 64^3 level has 256 blocks of 4 planes with the
+// default, 1,024 of one plane here).
+static ZCfg zcfg_sweep(Box b) { return zcfg_tile(b, (b.my == 1) ? 256 : 32, 4096, 1); }
 
 // ---------------------------------------------------------------------------
 // Tile autotuner for the stencil sweeps (Jacobi / matvec / residual): per box
@@ -624,18 +630,18 @@ constexpr long long kTuneMinCells = 1 << 16;  // smaller boxes are launch-latenc
 static ZCfg zcfg_stencil(Box b, int tsize, int sym) {
   std::lock_guard<std::mutex> lk(g_tuned_mu);
   auto it = g_tuned.find(TuneKey{b.mx, b.my, b.mz, tsize, sym});
-  return it == g_tuned.end() ? zcfg(b) : it->second;
+  return it == g_tuned.end() ? zcfg_sweep(b) : it->second;
 }
 
 static int tune_candidates(Box b, ZCfg* out) {
   int n = 0;
   const long long targets[] = {1024, 2048, 4096, 8192};
   if (b.my == 1) {
-    for (long long t : targets) out[n++] = zcfg_tile(b, 256, t);
+    for (long long t : targets) out[n++] = zcfg_tile(b, 256, t, 1);
   } else {
     const int txs[] = {32, 64, 128};
     for (int tx : txs)
-      for (long long t : targets) out[n++] = zcfg_tile(b, tx, t);
+      for (long long t : targets) out[n++] = zcfg_tile(b, tx, t, 1);
   }
   return n;
 }
@@ -1526,7 +1532,7 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     T* cur = pre[l];
     T* oth = (cur == x) ? t : x;
     const Box fz = zbox(A.box), cz = zbox(h.lev[l + 1].op.box);
-    const ZCfg zc = zcfg(fz);
+    const ZCfg zc = zcfg_sweep(fz);
     vlaunch(KN("mg_prolong", l == 0), (2.0 * ncell(A) + ncell(h.lev[l + 1].op)) * sizeof(T), k_prolong_add<T>,
             zc.grid, zc.block, st, fz, cz, cur, (const T*)h.lev[l + 1].x, wc, zc.zc, (const KScal*)sc);
     for (int s = 0; s < nu; ++s) {
