@@ -383,7 +383,9 @@ def time_e2e(V, es, prm, steps, dt):
 
 def oracle_sample(es, prm, budget_s=20.0, crop=40):
     """The CPU oracle on a bounded crop (crop^3 for 3D, crop x crop... for 2D)
-    of the same geometry and parameters; returns (cell-steps/s, steps, shape)."""
+    of the same geometry and parameters; returns (cell-steps/s, steps, shape,
+    wall seconds, threads used = process CPU time / wall time over the timed
+    steps, at least 1)."""
     from oracle import vos_oracle as O
     nz, ny, nx = es.shape
     if nz > 1:
@@ -394,6 +396,7 @@ def oracle_sample(es, prm, budget_s=20.0, crop=40):
     p.update(nz=sub.shape[0], ny=sub.shape[1], nx=sub.shape[2])
     st = O.init_state(sub, p)
     t0 = time.perf_counter()
+    c0 = time.process_time()
     n = 0
     while True:
         st, _ = O.step(st, 0.5, p, solver="iterative", rtol=p["p_rtol"])
@@ -401,7 +404,8 @@ def oracle_sample(es, prm, budget_s=20.0, crop=40):
         if time.perf_counter() - t0 > budget_s or n >= 20:
             break
     dt = time.perf_counter() - t0
-    return sub.size * n / dt, n, sub.shape, dt
+    cores = max(1, int(round((time.process_time() - c0) / dt)))
+    return sub.size * n / dt, n, sub.shape, dt, cores
 
 
 def reference_arm(args, rank, world):
@@ -412,17 +416,18 @@ def reference_arm(args, rank, world):
     cells = []
     for _ in range(max(args.warmup, 0)):
         oracle_sample(es, prm, budget_s=2.0)
-    rates = []
+    rates, used = [], []
     for _ in range(args.steps):
-        r, n, shp, dt = oracle_sample(es, prm, budget_s=5.0)
+        r, n, shp, dt, cores = oracle_sample(es, prm, budget_s=5.0)
         rates.append(r)
         cells.append(shp)
+        used.append(cores)
     v = float(np.mean(rates))
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "desc": desc},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": max(used), "kind": "oracle",
                             "sample": f"oracle step(s) on a {cells[0]} crop of the workload geometry, "
                                       "scipy CG/BiCGStab to the same tolerances, ~5 s per timed step"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -525,8 +530,8 @@ def main():
            "device_bytes": r["dev_bytes"], "e2e": e2e, "clocks": ck, "learned": learned,
            "breakdown": r["breakdown"]}
     if rank == 0 and not args.no_cpu:
-        r, n, shp, dtc = oracle_sample(es, prm, budget_s=15.0)
-        out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+        r, n, shp, dtc, cores = oracle_sample(es, prm, budget_s=15.0)
+        out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{n} oracle step(s) on a {tuple(shp)} crop of the same geometry "
                                          f"({dtc:.1f} s), scipy CG/BiCGStab at the same tolerances"}
     if rank == 0:
