@@ -55,6 +55,23 @@ def test_van_leer_limiter_values():
     assert np.all(psi(r) <= np.minimum(2 * r, 2.0) + 1e-15)
 
 
+def test_van_leer_harmonic_mean_form():
+    """van Leer's limited correction is half the harmonic mean of the two
+    one-sided differences (ref. 1974-vanLeer): with a = c_U - c_UU and
+    b = c_D - c_U, w (c_D - c_U) = a b / (a + b) when a and b have one sign
+    and 0 otherwise, so the face value stays between c_U and c_D."""
+    rng = np.random.default_rng(5)
+    cUU, cU, cD = rng.uniform(-1.0, 1.0, (3, 20000))
+    a, b = cU - cUU, cD - cU
+    corr = O.van_leer_weight(cUU, cU, cD, np.ones(cU.shape, dtype=bool)) * b
+    same = a * b > 0
+    assert 0.3 < same.mean() < 0.7
+    np.testing.assert_allclose(corr[same], (a * b / (a + b))[same], rtol=1e-13, atol=0)
+    assert np.all(corr[~same] == 0.0)
+    cf = cU + corr
+    assert np.all(cf >= np.minimum(cU, cD) - 1e-15) and np.all(cf <= np.maximum(cU, cD) + 1e-15)
+
+
 def test_van_leer_linear_profile_exact():
     """A second-order TVD scheme reconstructs a linear profile exactly
     (r = 1 -> c_f = midpoint), both flow directions; first face upwind."""
