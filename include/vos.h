@@ -114,7 +114,9 @@ typedef struct vos_stats {
 
 /* Optional device allocator (e.g. a framework's caching allocator).
  * alloc(bytes, ctx) returns a device pointer aligned to >= 256 bytes or
- * NULL; free(ptr, ctx) releases it.  NULL selects cudaMalloc/cudaFree. */
+ * NULL (a pointer with less alignment is handed back to free and the
+ * allocation fails: VOS_ENOMEM); free(ptr, ctx) releases it.  NULL selects
+ * cudaMalloc/cudaFree. */
 typedef struct vos_allocator {
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);

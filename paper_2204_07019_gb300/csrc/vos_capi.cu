@@ -100,6 +100,13 @@ void* dev_alloc(vos_handle* h, size_t bytes) {
   void* p = nullptr;
   if (h->user_alloc) {
     p = h->alloc.alloc(bytes, h->alloc.ctx);
+    // the kernels' 16-byte vector accesses and 256-byte carves rely on the
+    // allocator's alignment promise: a block that breaks it is released and
+    // counts as a failed allocation
+    if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0) {
+      h->alloc.free(p, h->alloc.ctx);
+      p = nullptr;
+    }
   } else {
     if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
   }

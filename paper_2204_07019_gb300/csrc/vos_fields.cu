@@ -312,8 +312,9 @@ void launch_project(const Phys& P, const double* eps, const double* phi, const d
 // ---------------------------------------------------------------------------
 // Per-face data of the transport step, one launch per axis.
 // Every face: the explicit convective flux (per unit area) of c^n with the
-// van Leer face value upwinded along sign(u_f) (Sec. 2.5), evaluated once per
-// face here instead of once from each of the two adjacent cells.
+// van Leer face value upwinded along sign(u_f) (Eq. concentrationDBS,
+// App. B), evaluated once per face here instead of once from each of the two
+// adjacent cells.
 // iVoS interior faces along a (Sec. 2.3, App. B):
 //   g_f = ((eps_+ - eps_-)/dx along a; tangential: mean of the two cells'
 //   centred gradients), n_a = -g_a / (|g_f| + 1e-8/dx),
@@ -325,7 +326,7 @@ void launch_project(const Phys& P, const double* eps, const double* phi, const d
 //   evl = van Leer interpolation of eps along the flux direction.
 // FP64 arithmetic is scarce on this part, so the square root and division
 // of n_a are skipped where the eps gradient vanishes (pore and solid
-// interiors): there g2 = 0 and n_a = -g_n / delta = -0.
+// interiors): there g2 = 0, the normal difference dn = 0 and n_a = -0.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double conv_flux(const Phys& P, int a, int i, int j, int k, const double* cold,
                                             const double* ua) {
