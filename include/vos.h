@@ -65,11 +65,14 @@ typedef enum { VOS_FP64 = 0, VOS_MIXED = 1 } vos_precision;
 #define VOS_F_R 64u
 #define VOS_F_RF 128u
 
-/* Preconditioner flags (vos_params.precond).  0 (default): the pressure,
- * momentum and transport solves use the geometric multigrid V-cycle, and the
- * pressure solve adds the deflation of floating pore clusters (pockets of
- * pore cells joined to the outlet only through solid cells; see
- * vos_floating_clusters).  VOS_PRECOND_NO_DEFLATION drops the deflation.
+/* Preconditioner flags (vos_params.precond).  0 (default): the pressure and
+ * transport solves use the multigrid V-cycle (Galerkin aggregation, damped
+ * Jacobi); each momentum solve uses it when the viscous term dominates the
+ * mass term (2 dim nu dt / dx^2 > 30) and the diagonal (Jacobi)
+ * preconditioner otherwise; the pressure solve adds the deflation of
+ * floating pore clusters (pockets of pore cells joined to the outlet only
+ * through solid cells; see vos_floating_clusters).
+ * VOS_PRECOND_NO_DEFLATION drops the deflation.
  * A solver aid, not part of the paper's method: it changes the iteration
  * count, not the converged solution. */
 #define VOS_PRECOND_NO_DEFLATION 1
@@ -141,9 +144,12 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream,
                const vos_allocator* alloc, vos_handle** out);
 
 /* Advance one time step of length dt (> 0) through S1-S7 (see top).  The
- * linear solves converge on the device; the host reads the residual once
- * per refinement pass and at most every few Krylov iterations.  Returns
- * VOS_ENOCONV if a solve reached max_iter (the step is still applied). */
+ * linear solves converge on the device: in the default launch mode the step
+ * is one CUDA-graph replay whose solver loops are device-driven, and the
+ * host waits once, at the end, for the solver statistics; in the eager mode
+ * (vos_set_launch_mode(0)) the host reads the residual once per refinement
+ * pass and every few Krylov iterations.  Returns VOS_ENOCONV if a solve
+ * reached max_iter (the step is still applied). */
 int vos_step(vos_handle* h, double dt);
 
 /* Copy the selected fields (mask of VOS_F_*) to caller-owned host buffers
@@ -173,8 +179,12 @@ int vos_suggest_dt(vos_handle* h, double cfl, double deps_max, double* dt);
  * sizes and parameters stepped together; no counterpart in the paper's
  * single-sample runs).  vos_batch_create makes n instances from eps_s[i]
  * and prm[i] (as vos_create); each instance gets its own non-blocking CUDA
- * stream and the instances are advanced by a pool of nthreads host worker
- * threads (<= 0: 8), so their kernels overlap on the GPU.  stream is the
+ * stream.  In the default launch mode a batch step is one CUDA-graph launch
+ * that holds every instance's whole step as a parallel branch (captured
+ * again when an instance's momentum-preconditioner choice or captured
+ * parameters change); in the eager mode, or while an instance has a learned
+ * preconditioner, a pool of nthreads host worker threads (<= 0: 8) advances
+ * the instances, so their kernels overlap on the GPU.  stream is the
  * caller's stream: vos_batch_step orders every instance after the work
  * already on it and makes it wait for all instances, so events recorded
  * there bracket a whole batch step.  vos_batch_step(b, dt) advances
