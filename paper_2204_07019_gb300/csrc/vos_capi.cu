@@ -817,14 +817,7 @@ int vos_tile_config(const vos_handle* h, int32_t sys, int32_t level, int32_t* tx
     *tuned = 1;
   } else {
     *tuned = 0;
-    x = (b.my == 1) ? 256 : 32;
-    y = 256 / x;
-    const long long tiles = (long long)((b.mx + x - 1) / x) * ((b.my + y - 1) / y);
-    long long c = (tiles * b.mz + 4095) / 4096;  // the sweeps' default: >= 1 plane per block
-    if (c < 1) c = 1;
-    if (c > b.mz) c = b.mz;
-    while (tiles * ((b.mz + c - 1) / c) > kMaxRedBlocks) ++c;
-    z = (int)c;
+    default_sweep_config(b.mx, b.my, b.mz, &x, &y, &z);
   }
   *tx = x;
   *ty = y;

@@ -403,6 +403,8 @@ template <typename T>
 void autotune_hier(const Hier<T>& h, SolverWork* w, cudaStream_t st);
 // The tuned tile of a box, if any: returns 1 and fills (tx, ty, zc).
 int tuned_config(int mx, int my, int mz, int tsize, int sym, int* tx, int* ty, int* zc);
+// The sweep shape of a box the autotuner did not measure.
+void default_sweep_config(int mx, int my, int mz, int* tx, int* ty, int* zc);
 
 // Learned preconditioner (vos_unet.cu): z = UNet(r / rms(r), eps) rms(r),
 // rr = |r|^2 on the device.

@@ -1370,6 +1370,13 @@ void autotune_hier(const Hier<T>& h, SolverWork* w, cudaStream_t st) {
 template void autotune_hier<double>(const Hier<double>&, SolverWork*, cudaStream_t);
 template void autotune_hier<float>(const Hier<float>&, SolverWork*, cudaStream_t);
 
+void default_sweep_config(int mx, int my, int mz, int* tx, int* ty, int* zc) {
+  const ZCfg z = zcfg_sweep(Box{mx, my, mz});
+  *tx = (int)z.block.x;
+  *ty = (int)z.block.y;
+  *zc = z.zc;
+}
+
 int tuned_config(int mx, int my, int mz, int tsize, int sym, int* tx, int* ty, int* zc) {
   std::lock_guard<std::mutex> lk(g_tuned_mu);
   auto it = g_tuned.find(TuneKey{mx, my, mz, tsize, sym});
