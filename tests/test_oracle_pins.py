@@ -259,6 +259,25 @@ def test_reactant_mass_balance(method):
         st = st1
 
 
+@pytest.mark.parametrize("method", ["psi", "psi_prime", "ivos"])
+def test_no_reaction_degenerate(method):
+    """Da = 0 (k_c = 0): every rate is exactly zero and the solid does not
+    change, whatever the reactive-surface form; the reactant is only
+    transported, so with c = 0 inside and c_in = 1 at the inlet it stays in
+    [0, c_in] (explicit TVD advection at CFL <= 1/2, implicit M-matrix
+    diffusion)."""
+    es = I.calcite_post_2d(40, 20, 14.0, 10.0, 5.0)
+    prm = I.make_params(es.shape, Pe=5.0, Da=0.0, L=10.0, method=method)
+    st = O.init_state(es, prm)
+    eps0 = st["eps"].copy()
+    for _ in range(4):
+        st, _ = O.step(st, 0.2, prm)
+        assert np.all(st["R"] == 0.0) and np.all(st["Rf"] == 0.0)
+        np.testing.assert_array_equal(st["eps"], eps0)
+        assert st["c"].min() >= -1e-12 and st["c"].max() <= prm["c_in"] + 1e-12
+    assert st["c"][..., 0].mean() > 0.05  # the reactant did enter
+
+
 def test_solid_mass_balance():
     """Eq. mbs: sum(eps^{n+1} - eps^n) V = dt V_m sum(R^n) V - clamp excess."""
     es, prm = _small_case("ivos", Da=5.0)
