@@ -72,3 +72,25 @@ def test_invalid_parameters_rejected_without_gpu(lib):
     prm = I.make_params(es.shape, Pe=1, Da=1, L=1)
     with pytest.raises(vos.VosError):
         vos.vos_create(es + 2.0, prm, allocator="cuda")
+
+
+def test_other_entry_points_reject_bad_arguments_without_gpu(lib):
+    """Entry points that validate before any CUDA call: the FP64-quotient
+    check, the tensor-core convolution and the U-Net constructor return
+    VOS_EINVAL with a message (n = 0 is a no-op)."""
+    import ctypes as C
+    from paper_2204_07019_gb300 import vos
+    assert lib.vos_fp64_div_check(None, None, -1, None, None) == vos.VOS_EINVAL
+    assert lib.vos_fp64_div_check(None, None, 0, None, None) == vos.VOS_OK
+    assert lib.vos_fp64_div_check(None, None, 5, None, None) == vos.VOS_EINVAL
+    assert b"NULL" in lib.vos_last_error(None)
+    # cin not a multiple of 8, cout out of [16, 96] or not a multiple of 16, no output
+    dummy = C.c_void_p(16)
+    for cin, cout, y in ((12, 16, dummy), (8, 8, dummy), (8, 112, dummy), (8, 24, dummy), (8, 16, None)):
+        rc = lib.vos_conv3d_bf16(dummy, 4, 4, 4, cin, dummy, None, cout, 0, y, None, None)
+        assert rc == vos.VOS_EINVAL, (cin, cout)
+    assert b"vos_conv3d_bf16" in lib.vos_last_error(None)
+    out = C.c_void_p()
+    assert lib.vos_unet_create(3, 8, 8, 0, None, C.byref(out)) == vos.VOS_EINVAL
+    assert lib.vos_unet_create(2048, 2048, 2048, 0, None, C.byref(out)) == vos.VOS_EINVAL
+    assert not out.value
