@@ -171,8 +171,10 @@ int vos_get_stats(vos_handle* h, vos_stats* out);
 
 /* Time step limit min(cfl dx / max_f(|u_f| / eps_f), deps_max / max|Vm R|)
  * (App. D: the step is limited by the largest change of eps; the
- * convective limit uses the interstitial speed).  Synchronous.  Returns
- * +inf in *dt when neither limit applies. */
+ * convective limit uses the interstitial speed).  eps_f is the mean of the
+ * two cells of an interior face and the one cell of a boundary face.
+ * Synchronous.  Returns +inf in *dt when neither limit applies and 0 when a
+ * face speed or a rate is NaN. */
 int vos_suggest_dt(vos_handle* h, double cfl, double deps_max, double* dt);
 
 /* Batches of independent simulations (e.g. many micromodels of uneven
@@ -206,17 +208,22 @@ void vos_batch_destroy(vos_batch* b);
  * hosts that keep the GPU's memory in their own pool, or loops that must not
  * pay the device-wide synchronisation a cudaMalloc/cudaFree can cause).
  * Computes the same limit as vos_suggest_dt from caller-owned device fields
- * in the layouts above (eps, u, v, w, R; v may be NULL when ny == 1, w is
- * required in 3D); only dim, nx, ny, nz, dx and Vm of prm are used.  It
- * allocates nothing: its scratch is a fixed file-scope device array of
- * about 1 MiB that every GPU loading the library holds until exit, so grids
- * above 16,777,216 cells are rejected with VOS_EINVAL.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) and
- * should come before any stream capture.  All calls share the one array:
- * calls that overlap on the GPU (other streams or threads) race.  Work runs
- * on `stream`; the call synchronises it and writes the result to the host
- * double *dt.  Errors: VOS_EINVAL (NULL or bad arguments, too many cells),
- * VOS_ECUDA; message via vos_last_error(NULL). */
+ * in the layouts above (eps, u, v, w, R; w is required in 3D; v is required
+ * when ny > 1 and may be NULL when ny == 1, where every v face is a wall
+ * face: the y faces are then not read); only dim, nx, ny, nz, dx and Vm of
+ * prm are used (nx >= 2, as vos_create).  It allocates nothing: its scratch
+ * is a fixed file-scope device array of about 1 MiB that every GPU loading
+ * the library holds until exit, so grids above 16,777,216 cells are
+ * rejected with VOS_EINVAL.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) and should come before any
+ * stream capture.  All calls share the one array: calls that overlap on the
+ * GPU (other streams or threads) race.  Work runs on `stream`, which must
+ * belong to the current device (NULL = legacy default stream); the call
+ * synchronises it and writes the result to the host double *dt (0 when a
+ * speed or rate is NaN, as vos_suggest_dt).  Errors: VOS_EINVAL (NULL or
+ * bad arguments, too many cells, a stream of another device), VOS_ECUDA (a
+ * failed copy or launch; *dt is then not written); message via
+ * vos_last_error(NULL). */
 int vos_suggest_dt_noalloc(const vos_params* prm, const double* eps, const double* u,
                            const double* v, const double* w, const double* R, double cfl,
                            double deps_max, void* stream, double* dt);

@@ -719,8 +719,12 @@ void launch_rates(const Phys& P, int ivos, const double* eps, const double* c, c
 
 // ---------------------------------------------------------------------------
 // Time-step limits (App. D): max over faces of |u_f| / eps_f (interior:
-// mean of the two cells; boundary: the adjacent cell) and max |Vm R|.
+// mean of the two cells; boundary: the adjacent cell) and max |Vm R|.  A NaN
+// speed or rate counts as +inf (fmax alone would drop it), so the limit
+// becomes dt = 0 instead of a finite value.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double nan_inf(double x) { return (x == x) ? x : INFINITY; }
+
 __global__ void k_dt_limits(Phys P, const double* __restrict__ eps, const double* __restrict__ u0,
                             const double* __restrict__ u1, const double* __restrict__ u2,
                             const double* __restrict__ R, double* stats, RedScratch rs) {
@@ -741,14 +745,14 @@ __global__ void k_dt_limits(Phys P, const double* __restrict__ eps, const double
       int lo[3] = {i, j, k};
       lo[d] -= 1;
       double ef = cell_in(P, lo[0], lo[1], lo[2]) ? 0.5 * (e + eps[cidx(P, lo[0], lo[1], lo[2])]) : e;
-      acc[0] = fmax(acc[0], fabs(us[d][fidx(P, d, i, j, k)]) / ef);
+      acc[0] = fmax(acc[0], nan_inf(fabs(us[d][fidx(P, d, i, j, k)]) / ef));
       int f[3] = {i, j, k};
       if (f[d] == ncell(P, d) - 1) {
         f[d] += 1;
-        acc[0] = fmax(acc[0], fabs(us[d][fidx(P, d, f[0], f[1], f[2])]) / e);
+        acc[0] = fmax(acc[0], nan_inf(fabs(us[d][fidx(P, d, f[0], f[1], f[2])]) / e));
       }
     }
-    acc[1] = fmax(acc[1], fabs(P.Vm * R[c]));
+    acc[1] = fmax(acc[1], nan_inf(fabs(P.Vm * R[c])));
   }
   if (grid_max<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
     stats[ST_UMAX] = acc[0];

@@ -39,6 +39,7 @@ double* g_addr[kMaxDevices] = {};
 
 struct Grid {
   int dim, nx, ny, nz;
+  int hasv;  // 0: no v array (ny == 1, every v face is a wall face with zero velocity)
   double Vm;
 };
 
@@ -50,10 +51,15 @@ __device__ __forceinline__ long long fix(const Grid& g, int a, int i, int j, int
   return i + (long long)fx * (j + (long long)fy * k);
 }
 
+// NaN compares false with everything, so fmax would drop it: a NaN speed or
+// rate is taken as +inf instead (the limit then becomes dt = 0).
+__device__ __forceinline__ double nan_to_inf(double x) { return (x == x) ? x : INFINITY; }
+
 // One block per 256-cell tile: per cell, |u_f| / eps_f over its minus faces
 // (and its plus face at the last cell along an axis) and |Vm R|; block
 // maxima to scratch[2 tile], scratch[2 tile + 1]; the last block reduces
-// the tiles in order and writes the two results.
+// the tiles in order and writes the two results.  Axis y is skipped when
+// there is no v array (g.hasv == 0, only allowed for ny == 1).
 __global__ void k_dt_limits_tiles(Grid g, const double* __restrict__ eps, const double* __restrict__ u0,
                                   const double* __restrict__ u1, const double* __restrict__ u2,
                                   const double* __restrict__ R, double* scratch) {
@@ -69,17 +75,18 @@ __global__ void k_dt_limits_tiles(Grid g, const double* __restrict__ eps, const 
     const double e = eps[c];
     const int nb = (g.dim == 2) ? 2 : 3;
     for (int d = 0; d < nb; ++d) {
+      if (d == 1 && !g.hasv) continue;
       int lo[3] = {i, j, k};
       lo[d] -= 1;
       const double ef = (lo[d] >= 0) ? 0.5 * (e + eps[cix(g, lo[0], lo[1], lo[2])]) : e;
-      v[0] = fmax(v[0], fabs(us[d][fix(g, d, i, j, k)]) / ef);
+      v[0] = fmax(v[0], nan_to_inf(fabs(us[d][fix(g, d, i, j, k)]) / ef));
       int f[3] = {i, j, k};
       if (f[d] == n3[d] - 1) {
         f[d] += 1;
-        v[0] = fmax(v[0], fabs(us[d][fix(g, d, f[0], f[1], f[2])]) / e);
+        v[0] = fmax(v[0], nan_to_inf(fabs(us[d][fix(g, d, f[0], f[1], f[2])]) / e));
       }
     }
-    v[1] = fabs(g.Vm * R[c]);
+    v[1] = nan_to_inf(fabs(g.Vm * R[c]));
   }
   unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + kCounterSlot);
   __shared__ double sh[2][kTile / 32];
@@ -140,8 +147,10 @@ extern "C" int vos_suggest_dt_noalloc(const vos_params* prm, const double* eps, 
                                       double* dt) {
   if (!prm || !eps || !u || !R || !dt) return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: NULL argument");
   if (prm->dim != 2 && prm->dim != 3) return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: dim must be 2 or 3");
-  if (prm->nx < 1 || prm->ny < 1 || prm->nz < 1 || (prm->dim == 2 && prm->nz != 1))
-    return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: bad grid size");
+  if (prm->nx < 2 || prm->ny < 1 || prm->nz < 1 || (prm->dim == 2 && prm->nz != 1))
+    return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: need nx >= 2, ny >= 1, nz >= 1 (nz == 1 in 2D)");
+  if (!(prm->dx > 0.0) || !std::isfinite(prm->dx) || !std::isfinite(prm->Vm))
+    return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: dx must be finite and > 0, Vm finite");
   if (prm->ny > 1 && !v) return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: v is NULL");
   if (prm->dim == 3 && !w) return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: w is NULL for a 3D grid");
   if (!(cfl > 0.0) || !(deps_max > 0.0)) return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: cfl and deps_max must be > 0");
@@ -153,6 +162,17 @@ extern "C" int vos_suggest_dt_noalloc(const vos_params* prm, const double* eps, 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(VOS_ECUDA, "vos_suggest_dt_noalloc: no usable current device");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (st != nullptr) {
+    // the scratch address below is the current device's: the stream must
+    // belong to that device
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: stream is not a valid CUDA stream");
+    }
+    if (sdev != dev) return fail(VOS_EINVAL, "vos_suggest_dt_noalloc: stream belongs to another device than the current one");
+  }
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -167,15 +187,20 @@ extern "C" int vos_suggest_dt_noalloc(const vos_params* prm, const double* eps, 
     }
     scratch = g_addr[dev];
   }
-  cudaStream_t st = (cudaStream_t)stream;
   // The counter must start at zero (the array keeps the last call's contents).
-  cudaMemsetAsync(scratch + kCounterSlot, 0, sizeof(double), st);
-  Grid g{prm->dim, prm->nx, prm->ny, prm->nz, prm->Vm};
+  cudaError_t e = cudaMemsetAsync(scratch + kCounterSlot, 0, sizeof(double), st);
+  if (e != cudaSuccess) return fail(VOS_ECUDA, cudaGetErrorString(e));
+  Grid g{prm->dim, prm->nx, prm->ny, prm->nz, v != nullptr, prm->Vm};
   const unsigned tiles = (unsigned)((N + kTile - 1) / kTile);
+  // v and w are never read when absent (hasv == 0; w only in 3D): u stands
+  // in for the unused pointer arguments
   k_dt_limits_tiles<<<tiles, kTile, 0, st>>>(g, eps, u, v ? v : u, w ? w : u, R, scratch);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(VOS_ECUDA, cudaGetErrorString(e));
   double res[2] = {0.0, 0.0};
-  cudaMemcpyAsync(res, scratch + kResultSlot, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
-  cudaError_t e = cudaStreamSynchronize(st);
+  e = cudaMemcpyAsync(res, scratch + kResultSlot, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return fail(VOS_ECUDA, cudaGetErrorString(e));
+  e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(VOS_ECUDA, cudaGetErrorString(e));
   const double d1 = res[0] > 0.0 ? cfl * prm->dx / res[0] : INFINITY;
   const double d2 = res[1] > 0.0 ? deps_max / res[1] : INFINITY;

@@ -94,3 +94,21 @@ def test_other_entry_points_reject_bad_arguments_without_gpu(lib):
     assert lib.vos_unet_create(3, 8, 8, 0, None, C.byref(out)) == vos.VOS_EINVAL
     assert lib.vos_unet_create(2048, 2048, 2048, 0, None, C.byref(out)) == vos.VOS_EINVAL
     assert not out.value
+
+
+def test_noalloc_dt_rejects_bad_arguments_without_gpu(lib):
+    """vos_suggest_dt_noalloc checks its arguments before any CUDA call:
+    nx < 2, a missing v array on a grid with ny > 1 (v may only be NULL when
+    ny == 1) and a missing w array in 3D are refused with VOS_EINVAL."""
+    import ctypes as C
+    from paper_2204_07019_gb300 import inputs as I, vos
+    d = C.c_void_p(256)
+    out = C.c_double(-1.0)
+    # (grid shape (nz, ny, nx), v, w): nx < 2; ny > 1 without v; 3D without w
+    cases = (((1, 4, 1), d, None), ((1, 4, 8), None, None), ((3, 4, 8), d, None))
+    for shape, v, w in cases:
+        ps = vos._params_struct(I.make_params(shape, Pe=1, Da=1, L=1))
+        rc = lib.vos_suggest_dt_noalloc(C.byref(ps), d, d, v, w, d, 0.5, 0.005, None, C.byref(out))
+        assert rc == vos.VOS_EINVAL, shape
+        assert b"vos_suggest_dt_noalloc" in lib.vos_last_error(None)
+    assert out.value == -1.0

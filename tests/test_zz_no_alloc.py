@@ -60,6 +60,31 @@ def test_noalloc_matches_suggest_dt_twice(V, case):
         V.vos_destroy(h)
 
 
+def test_noalloc_single_row_without_v_and_on_a_side_stream(V):
+    """ny == 1: every v face is a wall face, so v may be NULL; the result
+    equals vos_suggest_dt (which reads the zero wall faces).  Also run on a
+    non-default torch stream, twice in a row."""
+    import torch
+    es = np.zeros((1, 1, 64))
+    es[0, 0, 20:30] = 0.7
+    prm = I.make_params(es.shape, Pe=1.0, Da=1.0, L=8.0, method="ivos", Vm=0.5, wall_mask=0)
+    h = V.vos_create(es, prm)
+    try:
+        V.vos_set_fields(h, c=np.linspace(1.0, 0.2, 64).reshape(es.shape))
+        for _ in range(2):
+            V.vos_step(h, 0.2)
+        f = V.vos_device_fields_get(h)
+        ref = V.vos_suggest_dt(h, 0.5, 0.005)
+        side = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        for _ in range(2):
+            got = V.vos_suggest_dt_noalloc(prm, f["eps"], f["u"], None, None, f["R"], 0.5, 0.005, stream=side)
+            assert np.isfinite(got) and got > 0
+            assert abs(got - ref) <= 1e-9 * abs(ref)
+    finally:
+        V.vos_destroy(h)
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch(V):
     prm = I.make_params((257, 256, 256), Pe=1.0, Da=1.0, L=1.0)
     with pytest.raises(V.VosError) as ei:
