@@ -100,7 +100,11 @@ typedef struct vos_params {
   uint32_t wall_mask;
 } vos_params;
 
-/* Statistics of the last completed step (FP64 device reductions). */
+/* Statistics of the last completed step (FP64 device reductions; S7).
+ * V = dx^dim is the cell volume, A = dx^(dim-1) the face area.  The flux
+ * terms close the reactant balance of the step (Eq. concentrationDBS
+ * integrated over the domain):
+ *   reactant^{n+1} - reactant^n = dt (flux_in - flux_out - zeta sum_Rf). */
 typedef struct vos_stats {
   int64_t step;
   double t;
@@ -108,11 +112,19 @@ typedef struct vos_stats {
   int32_t outer_u[3], outer_p, outer_c;  /* refinement passes                */
   double res_u[3], res_p, res_c;         /* final scaled relative residuals  */
   double lambda;       /* psi' fit (psi: the constant; iVoS: NaN)            */
-  double porosity;     /* mean eps                                           */
+  double porosity;     /* mean eps (the total porosity phi of Sec. 2.5)      */
   double clamp_excess; /* sum(raw - clamped eps) * V of the S1 update        */
   double sum_R, sum_Rf;/* sum R V, sum R_f V                                 */
   double reactant;     /* sum eps c V                                        */
   int32_t status;      /* VOS_OK or VOS_ENOCONV                              */
+  double q_in, q_out;  /* sum over inlet / outlet faces of u_f A (Q_i, Sec. 2.5) */
+  double flux_in;      /* reactant inflow: inlet faces u_f c_in plus the
+                          diffusive flux 2 D eps_P (c_in - c_P) / dx, times A */
+  double flux_out;     /* reactant outflow: outlet faces u_f c_P^n, times A  */
+  double umax;         /* max over faces of |u_f| / eps_f (interior faces:
+                          mean of the two cells; boundary: adjacent cell)    */
+  double rmax;         /* max |Vm R|: dt <= deps_max / rmax bounds the change
+                          of eps per step (App. D)                          */
 } vos_stats;
 
 /* Optional device allocator (e.g. a framework's caching allocator).

@@ -585,11 +585,45 @@ def step(state, dt, prm, solver="direct", rtol=1e-13):
         Rf = R.copy()
     new = dict(eps=eps, c=c, p=p, u=u, R=R, Rf=Rf, t=state["t"] + dt,
                step=state["step"] + 1)
-    V = prm["dx"] ** int(prm["dim"])
-    stats = dict(lam=lam, clamp_excess=excess, porosity=float(np.mean(eps)),
-                 sum_R=float(np.sum(R) * V), sum_Rf=float(np.sum(Rf) * V),
-                 reactant=float(np.sum(eps * c) * V))
+    stats = diagnostics(state, new, prm)
+    stats.update(lam=lam, clamp_excess=excess)
     return new, stats
+
+
+def diagnostics(prev, new, prm):
+    """Global FP64 diagnostics of a step from ``prev`` (fields at t^n) to
+    ``new`` (t^{n+1}).
+
+    * porosity: mean eps^{n+1} (the total porosity phi of Sec. 2.5);
+    * reactant = sum eps c V, sum_R = sum R V, sum_Rf = sum R_f V;
+    * q_in, q_out: volumetric flow through the inlet and outlet faces,
+      sum u_f A_f with A_f = dx^(d-1) (Q_i of Sec. 2.5 at the inlet);
+    * flux_in, flux_out: reactant carried through the inlet and outlet
+      faces during the step: inlet u_f c_in plus the diffusive flux
+      2 D eps_P (c_in - c_P^{n+1}) / dx of the Dirichlet ghost, outlet
+      u_f c_P^n (the explicit convective flux), times A_f.  With them the
+      integral form of Eq. concentrationDBS over a step reads
+      sum(eps c V)^{n+1} - sum(eps c V)^n = dt (flux_in - flux_out - zeta sum_Rf);
+    * umax = max over all faces of |u_f| / eps_f (interior faces: mean of
+      the two cells; boundary faces: the adjacent cell) and rmax = max |V_m R|,
+      the two quantities the time-step limit of App. D is built from.
+    """
+    shp = _shape(prm)
+    dim = int(prm["dim"])
+    dx, D = prm["dx"], prm["D"]
+    V = dx ** dim
+    A = dx ** (dim - 1)
+    eps, c, u = new["eps"], new["c"], new["u"]
+    nx = shp[2]
+    q_in = float(np.sum(u[0][_sl(0, 0, 1)]) * A)
+    q_out = float(np.sum(u[0][_sl(0, nx, nx + 1)]) * A)
+    e0 = eps[_sl(0, 0, 1)]
+    fin = u[0][_sl(0, 0, 1)] * prm["c_in"] + 2.0 * D * e0 * (prm["c_in"] - c[_sl(0, 0, 1)]) / dx
+    fout = u[0][_sl(0, nx, nx + 1)] * prev["c"][_sl(0, nx - 1, nx)]
+    return dict(porosity=float(np.mean(eps)), reactant=float(np.sum(eps * c) * V),
+                sum_R=float(np.sum(new["R"]) * V), sum_Rf=float(np.sum(new["Rf"]) * V),
+                q_in=q_in, q_out=q_out, flux_in=float(np.sum(fin) * A), flux_out=float(np.sum(fout) * A),
+                umax=interstitial_speed_max(new, prm), rmax=float(np.max(np.abs(prm["Vm"] * new["R"]))))
 
 
 def run(eps_s, prm, dts, solver="direct", rtol=1e-13):
@@ -601,10 +635,9 @@ def run(eps_s, prm, dts, solver="direct", rtol=1e-13):
     return st, stats
 
 
-def suggest_dt(state, prm, cfl, deps_max):
-    """min(cfl dx / max_f |u_f|/eps_f, deps_max / max |V_m R|)  (App. D:
-    the time step is limited by the largest change of eps per step;
-    reading: the convective CFL uses the interstitial speed |u_f|/eps_f)."""
+def interstitial_speed_max(state, prm):
+    """max over all faces of |u_f| / eps_f: eps_f is the mean of the two cells
+    of an interior face and the adjacent cell of a boundary face."""
     shp = _shape(prm)
     eps = state["eps"]
     umax = 0.0
@@ -615,6 +648,15 @@ def suggest_dt(state, prm, cfl, deps_max):
         ef[_sl(a, 0, 1)] = eps[_sl(a, 0, 1)]
         ef[_sl(a, n, n + 1)] = eps[_sl(a, n - 1, n)]
         umax = max(umax, float(np.max(np.abs(state["u"][a]) / ef)))
+    return umax
+
+
+def suggest_dt(state, prm, cfl, deps_max):
+    """min(cfl dx / max_f |u_f|/eps_f, deps_max / max |V_m R|)  (App. D:
+    the time step is limited by the largest change of eps per step, here
+    eps changes by dt V_m R (Eq. mbs); reading: the convective CFL uses the
+    interstitial speed |u_f|/eps_f).  +inf when neither limit applies."""
+    umax = interstitial_speed_max(state, prm)
     rmax = float(np.max(np.abs(prm["Vm"] * state["R"])))
     dt1 = cfl * prm["dx"] / umax if umax > 0 else np.inf
     dt2 = deps_max / rmax if rmax > 0 else np.inf

@@ -290,6 +290,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     if (!r.converged) status = VOS_ENOCONV;
   }
   launch_rates(P, ivos, h->eps, h->c, h->kr, h->fd, h->R, h->Rf, h->dstats, h->rs, st);
+  launch_step_diag(P, h->eps, h->u, h->R, h->c, h->us[0], h->dstats, h->rs, st);  // S7
   cudaMemcpyAsync(h->hstats, h->dstats, ST_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_step: %s", cudaGetErrorString(e));
@@ -332,6 +333,7 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
   VOS_CUDA_TRY(solve_capture<T>(S[4].op64, S[4].h, S[4].rhs, unknown_view(h, 4), h->prm.c_rtol, h->prm.max_iter,
                                 h->work, h->rs, st, true, h->dsolve + 4, h->gs1, h->gs2));
   launch_rates(P, ivos, h->eps, h->c, h->kr, h->fd, h->R, h->Rf, h->dstats, h->rs, st);
+  launch_step_diag(P, h->eps, h->u, h->R, h->c, h->us[0], h->dstats, h->rs, st);  // S7
   VOS_CUDA_TRY(cudaMemcpyAsync(h->hstats, h->dstats, ST_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
   VOS_CUDA_TRY(cudaMemcpyAsync(h->hsolve, h->dsolve, 5 * sizeof(SolveStats), cudaMemcpyDeviceToHost, st));
   return cudaGetLastError();
@@ -757,6 +759,12 @@ int vos_get_stats(vos_handle* h, vos_stats* out) {
     s.sum_Rf = h->hstats[ST_SUMRF];
     s.reactant = h->hstats[ST_REACT];
     s.lambda = (h->prm.method == VOS_IVOS) ? NAN : h->hstats[ST_LAMBDA];
+    s.q_in = h->hstats[ST_QIN];
+    s.q_out = h->hstats[ST_QOUT];
+    s.flux_in = h->hstats[ST_FIN];
+    s.flux_out = h->hstats[ST_FOUT];
+    s.umax = h->hstats[ST_UMAX];
+    s.rmax = h->hstats[ST_RMAX];
   }
   *out = s;
   return VOS_OK;

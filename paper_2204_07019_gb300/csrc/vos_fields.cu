@@ -760,6 +760,72 @@ __global__ void k_dt_limits(Phys P, const double* __restrict__ eps, const double
   }
 }
 
+// S7 diagnostics at the end of a step: the two maxima of k_dt_limits on
+// u^{n+1}, R^{n+1} (|u_f| / eps_f with the physics kernels' FP64 quotient,
+// within 2 ulp of the IEEE one) and, on the inlet (i = 0) and outlet
+// (i = nx - 1) columns, q_in = sum u_f A, q_out, the reactant inflow
+// (convective u c_in from the face fluxes plus the Dirichlet ghost's
+// diffusive flux 2 D eps_P (c_in - c_P) / dx) and outflow (convective flux
+// u c^n of the outlet face), all times the face area A = dx^(d-1).
+__global__ void k_step_diag(Phys P, const double* __restrict__ eps, const double* __restrict__ u0,
+                            const double* __restrict__ u1, const double* __restrict__ u2,
+                            const double* __restrict__ R, const double* __restrict__ c,
+                            const double* __restrict__ cf0, double* stats, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  const Box bx{P.nx, P.ny, P.nz};
+  const Seg s = make_seg(bx);
+  const int nb = (P.dim == 2) ? 2 : 3;
+  const double* us[3] = {u0, u1, u2};
+  const double idx = 1.0 / P.dx;
+  double mx[2] = {0.0, 0.0};
+  double sm[4] = {0.0, 0.0, 0.0, 0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    const long long c0 = cidx(P, i, j, k);
+    const double e = eps[c0];
+    for (int d = 0; d < nb; ++d) {
+      int lo[3] = {i, j, k};
+      lo[d] -= 1;
+      const double ef = cell_in(P, lo[0], lo[1], lo[2]) ? 0.5 * (e + eps[cidx(P, lo[0], lo[1], lo[2])]) : e;
+      mx[0] = fmax(mx[0], nan_inf(fdiv_nr(fabs(us[d][fidx(P, d, i, j, k)]), ef)));
+      int f[3] = {i, j, k};
+      if (f[d] == ncell(P, d) - 1) {
+        f[d] += 1;
+        mx[0] = fmax(mx[0], nan_inf(fdiv_nr(fabs(us[d][fidx(P, d, f[0], f[1], f[2])]), e)));
+      }
+    }
+    mx[1] = fmax(mx[1], nan_inf(fabs(P.Vm * R[c0])));
+    if (i == 0) {
+      const long long fx = fidx(P, 0, 0, j, k);
+      sm[0] += u0[fx];
+      sm[2] += cf0[fx] + 2.0 * P.D * e * (P.c_in - c[c0]) * idx;
+    }
+    if (i == P.nx - 1) {
+      const long long fx = fidx(P, 0, P.nx, j, k);
+      sm[1] += u0[fx];
+      sm[3] += cf0[fx];
+    }
+  }
+  if (grid_sum_max<4, 2>(sm, mx, rs.partials, rs.counter) && threadIdx.x == 0) {
+    const double A = (P.dim == 2) ? P.dx : P.dx * P.dx;
+    stats[ST_UMAX] = mx[0];
+    stats[ST_RMAX] = mx[1];
+    stats[ST_QIN] = sm[0] * A;
+    stats[ST_QOUT] = sm[1] * A;
+    stats[ST_FIN] = sm[2] * A;
+    stats[ST_FOUT] = sm[3] * A;
+  }
+}
+
+void launch_step_diag(const Phys& P, const double* eps, double* const u[3], const double* R, const double* c,
+                      const double* cf0, double* stats, const RedScratch& rs, cudaStream_t st) {
+  Box bx{P.nx, P.ny, P.nz};
+  vlaunch("step_diag", (2.0 + P.dim) * 8.0 * box_cells(bx), k_step_diag, grid_for(bx, kMaxRedBlocks), kThreads, st,
+          P, eps, u[0], u[1], u[2] ? u[2] : u[0], R, c, cf0, stats, rs);
+}
+
 void launch_dt_limits(const Phys& P, const double* eps, double* const u[3], const double* R, double* stats,
                       const RedScratch& rs, cudaStream_t st) {
   Box bx{P.nx, P.ny, P.nz};

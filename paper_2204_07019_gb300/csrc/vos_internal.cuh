@@ -255,6 +255,52 @@ __device__ bool grid_max(double (&v)[NV], double* partials, unsigned int* counte
   return true;
 }
 
+// Grid-wide NS sums and NM maxima in one pass (same protocol as grid_sum:
+// partials of value q at partials[q * nb + block], the last block to arrive
+// combines them in block order, thread 0 of that block holds the totals in
+// s[] and m[]; NS + NM <= kMaxRedValues).
+template <int NS, int NM>
+__device__ bool grid_sum_max(double (&s)[NS], double (&m)[NM], double* partials, unsigned int* counter) {
+  __shared__ bool last;
+  block_sum<NS>(s);
+  block_max<NM>(m);
+  const unsigned nb = n_blocks();
+  const int t = lin_tid();
+  if (t == 0) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) partials[q * nb + lin_bid()] = s[q];
+#pragma unroll
+    for (int q = 0; q < NM; ++q) partials[(NS + q) * nb + lin_bid()] = m[q];
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    last = (prev == nb - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double ts[NS], tm[NM];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    ts[q] = 0.0;
+    for (int b = t; b < (int)nb; b += kThreads) ts[q] += __ldcg(partials + q * nb + b);
+  }
+#pragma unroll
+  for (int q = 0; q < NM; ++q) {
+    tm[q] = -1e308;
+    for (int b = t; b < (int)nb; b += kThreads) tm[q] = fmax(tm[q], __ldcg(partials + (NS + q) * nb + b));
+  }
+  block_sum<NS>(ts);
+  block_max<NM>(tm);
+  if (t == 0) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) s[q] = ts[q];
+#pragma unroll
+    for (int q = 0; q < NM; ++q) m[q] = tm[q];
+    *counter = 0u;
+  }
+  return true;
+}
+
 // Reduction scratch shared by all kernels of one handle (one stream, so
 // kernels never overlap).
 struct RedScratch {

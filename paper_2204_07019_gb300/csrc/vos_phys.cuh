@@ -44,7 +44,11 @@ enum StatIdx {
   ST_LAMBDA = 5,  // VoS lambda used
   ST_UMAX = 6,    // max |u_f| / eps_f
   ST_RMAX = 7,    // max |Vm R|
-  ST_COUNT = 8
+  ST_QIN = 8,     // sum over inlet faces of u_f A_f
+  ST_QOUT = 9,    // sum over outlet faces of u_f A_f
+  ST_FIN = 10,    // reactant inflow: inlet convective + diffusive flux, times A_f
+  ST_FOUT = 11,   // reactant outflow: outlet convective flux (c^n), times A_f
+  ST_COUNT = 12
 };
 
 struct FaceData {  // iVoS per-face data for one axis (face-array layout)
@@ -89,5 +93,10 @@ void launch_div_check(const double* a, const double* d, long long n, double* q_f
                       cudaStream_t st);
 void launch_dt_limits(const Phys& P, const double* eps, double* const u[3], const double* R, double* stats,
                       const RedScratch& rs, cudaStream_t st);
+// End-of-step diagnostics (S7): ST_UMAX, ST_RMAX of u^{n+1}, R^{n+1} and
+// the boundary sums ST_QIN..ST_FOUT.  cf0: convective face fluxes of axis x
+// written by launch_face_data (inlet u c_in, outlet u c^n); c: c^{n+1}.
+void launch_step_diag(const Phys& P, const double* eps, double* const u[3], const double* R, const double* c,
+                      const double* cf0, double* stats, const RedScratch& rs, cudaStream_t st);
 
 }  // namespace vos

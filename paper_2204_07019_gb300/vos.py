@@ -72,6 +72,8 @@ class VosStats(ctypes.Structure):
         ("lambda_", ctypes.c_double), ("porosity", ctypes.c_double), ("clamp_excess", ctypes.c_double),
         ("sum_R", ctypes.c_double), ("sum_Rf", ctypes.c_double), ("reactant", ctypes.c_double),
         ("status", ctypes.c_int32),
+        ("q_in", ctypes.c_double), ("q_out", ctypes.c_double), ("flux_in", ctypes.c_double),
+        ("flux_out", ctypes.c_double), ("umax", ctypes.c_double), ("rmax", ctypes.c_double),
     ]
 
 

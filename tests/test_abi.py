@@ -46,13 +46,13 @@ def test_struct_layout_matches_c(tmp_path):
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(vos_params),'
                    ' sizeof(vos_stats), sizeof(vos_device_fields), sizeof(vos_allocator),'
                    ' offsetof(vos_params, p_rtol), offsetof(vos_params, wall_mask),'
-                   ' offsetof(vos_stats, status));return 0;}\n')
+                   ' offsetof(vos_stats, status) + offsetof(vos_stats, rmax));return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(vos.VosParams), ctypes.sizeof(vos.VosStats), ctypes.sizeof(vos.VosDeviceFields),
             ctypes.sizeof(vos.VosAllocator), vos.VosParams.p_rtol.offset, vos.VosParams.wall_mask.offset,
-            vos.VosStats.status.offset]
+            vos.VosStats.status.offset + vos.VosStats.rmax.offset]
     assert got == want
 
 

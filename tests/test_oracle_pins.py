@@ -424,3 +424,93 @@ def test_reactant_mass_balance_3d():
         rhs = 0.3 * (inflow - outflow - np.sum(st1["Rf"]))
         assert abs(lhs - rhs) < 1e-10 * max(1.0, np.sum(st1["eps"] * st1["c"]))
         st = st1
+
+
+# ---------------------------------------------------------------- time step and diagnostics
+
+def _dt_state(prm, eps, u0, R):
+    shp = (int(prm["nz"]), int(prm["ny"]), int(prm["nx"]))
+    u = [np.asarray(u0, dtype=float).reshape(shp[0], shp[1], shp[2] + 1),
+         np.zeros((shp[0], shp[1] + 1, shp[2])), np.zeros((0,))]
+    return dict(eps=np.asarray(eps, dtype=float).reshape(shp), u=u, R=np.asarray(R, dtype=float).reshape(shp))
+
+
+def test_suggest_dt_closed_forms():
+    """App. D: dt is limited by the largest change of eps in a step, which by
+    Eq. mbs is dt V_m |R|, and (reading) by the interstitial CFL number
+    |u_f| dt / (eps_f dx).  Hand-built fields whose binding term is known:
+    the face porosity of an interior face is the mean of its two cells (a
+    cell-based eps would give a different number), |R| enters with V_m and
+    its sign does not matter, and the smaller of the two limits wins."""
+    prm = I.make_params((1, 1, 4), Pe=1, Da=1, L=1, Vm=0.5, dx=0.25)
+    eps = [0.2, 0.6, 1.0, 1.0]
+    # faces 0..4: inlet 0.1 / eps 0.2 = 0.5; interior face 1: 0.4 / mean(0.2, 0.6) = 1.0;
+    # outlet 0.5 / eps 1.0 = 0.5
+    u = [0.1, 0.4, 0.0, 0.0, 0.5]
+    st = _dt_state(prm, eps, u, [0.0, 0.0, 0.0, 0.0])
+    assert O.suggest_dt(st, prm, 0.5, 0.005) == pytest.approx(0.5 * 0.25 / 1.0, rel=1e-15)
+    # the rate limit alone: max |Vm R| = 0.5 * 5 = 2.5 (a negative rate binds)
+    st = _dt_state(prm, eps, np.zeros(5), [0.0, 3.0, 0.0, -5.0])
+    assert O.suggest_dt(st, prm, 0.5, 0.005) == pytest.approx(0.005 / 2.5, rel=1e-15)
+    # both: the smaller limit
+    st = _dt_state(prm, eps, u, [0.0, 3.0, 0.0, -5.0])
+    assert O.suggest_dt(st, prm, 0.5, 0.005) == pytest.approx(min(0.125, 0.002), rel=1e-15)
+    # nothing moves: no limit
+    st = _dt_state(prm, eps, np.zeros(5), np.zeros(4))
+    assert O.suggest_dt(st, prm, 0.5, 0.005) == np.inf
+    # uniform flow through pure fluid in 3D: dt = cfl dx / U along every axis
+    shp = (3, 4, 5)
+    prm3 = I.make_params(shp, Pe=1, Da=1, L=1)
+    u3 = [np.full((3, 4, 6), 2.0), np.zeros((3, 5, 5)), np.full((4, 4, 5), -4.0)]
+    st3 = dict(eps=np.ones(shp), u=u3, R=np.zeros(shp))
+    assert O.suggest_dt(st3, prm3, 0.5, 0.005) == pytest.approx(0.5 / 4.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("method", ["psi", "ivos"])
+def test_step_diagnostics_balance(method):
+    """The step's flux diagnostics close the integral balances: with
+    rho_s = rho the flow is divergence-free (Eq. contDBSQS), so q_out = q_in
+    = u_in x inlet area; the reactant content changes by
+    dt (flux_in - flux_out - zeta sum R_f) (Eq. concentrationDBS integrated
+    over the domain); umax and rmax give back suggest_dt."""
+    es, prm = _small_case(method)
+    st = O.init_state(es, prm)
+    ny = es.shape[1]
+    for _ in range(3):
+        dt = 0.4
+        st1, s = O.step(st, dt, prm)
+        assert s["q_in"] == pytest.approx(prm["u_in"] * ny * prm["dx"], rel=1e-14)
+        assert s["q_out"] == pytest.approx(s["q_in"], rel=1e-9)
+        before = np.sum(st["eps"] * st["c"]) * prm["dx"] ** 2
+        lhs = s["reactant"] - before
+        rhs = dt * (s["flux_in"] - s["flux_out"] - prm["zeta"] * s["sum_Rf"])
+        assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(before))
+        assert s["umax"] > 0 and s["rmax"] > 0
+        dt_ref = min(0.5 * prm["dx"] / s["umax"], 0.005 / s["rmax"])
+        assert O.suggest_dt(st1, prm, 0.5, 0.005) == pytest.approx(dt_ref, rel=1e-15)
+        st = st1
+
+
+def test_vos_psi_rate_on_linear_ramp():
+    """Eq. RfVoSpsi with lambda = 4 (Sec. 2.4): R = k_c c 4 eps (1 - eps) |grad eps|
+    with the centred gradient.  On eps = a + b x + g y the centred gradient
+    is exact in interior cells, |grad eps| = sqrt(b^2 + g^2); in the first
+    and last column the zero-gradient ghost halves the x component."""
+    ny, nx, dx = 9, 12, 0.5
+    prm = I.make_params((1, ny, nx), Pe=1, Da=0.7, L=1, method="psi", dx=dx)
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dx
+    b, g = 0.05, -0.03
+    eps = (0.2 + b * x[None, :] + g * y[:, None] + 0.2)[None]
+    c = (1.0 + 0.1 * x[None, :] * y[:, None])[None]
+    kr = O.vos_coefficient(eps, prm, 4.0)
+    R = kr * c
+    gx = np.full((ny, nx), b)
+    gx[:, 0] = gx[:, -1] = b / 2
+    gy = np.full((ny, nx), g)
+    gy[0, :] = gy[-1, :] = g / 2
+    ref = 0.7 * c[0] * 4.0 * eps[0] * (1 - eps[0]) * np.sqrt(gx ** 2 + gy ** 2)
+    np.testing.assert_allclose(R[0], ref, rtol=1e-13, atol=0)
+    # the fitted lambda of VoS-psi' replaces the 4, nothing else changes
+    lam = O.vos_lambda(eps, prm)
+    np.testing.assert_allclose(O.vos_coefficient(eps, prm, lam), kr * lam / 4.0, rtol=1e-14)
