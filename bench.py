@@ -10,6 +10,13 @@ momentum solved to a relative residual of 1e-8, concentration to 1e-10.
 A step is one full vos_step (S1-S7).  The plain-FP64 path is timed on the
 same workload beside it (``fp64``).
 
+Every leg runs W warm-up steps from rest and then K timed steps, all at one
+fixed time step (``config.dt``; 2.5e-3 on the rock, close to the CFL-0.5
+limit of its developed flow, which the line reports as ``dt_cfl05_after``),
+so the mixed, FP64 and learned legs advance the same state and their ratios
+are like for like; ``config.momentum_precond`` says which momentum
+preconditioner that dt selects.
+
 Metric: cell-steps/s (cells x steps / device time of the timed steps,
 CUDA events on the caller's stream; each step is one CUDA-graph replay with
 device-side solver loops).  Inputs stay resident in HBM and exceed L2 (each
@@ -151,28 +158,45 @@ TRAFFIC_PER_ALG_BYTE = {
 }
 
 
-def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
-    """Create, warm up, take a per-kernel breakdown of one untimed step, then
-    time ``steps`` steps with CUDA events while timing the dominant kernel's
-    launches with CUDA events on the same stream."""
+DEFAULT_DT = {"rock256": 2.5e-3, "micromodel": 0.02, "calcite": 0.25}
+
+
+def _stats_row(s):
+    return (s["iters_u"], s["iters_p"], s["iters_c"], s["res_p"], s["outer_u"], s["outer_p"], s["outer_c"])
+
+
+def time_gpu(V, es, prm, steps, warmup, dt, torch, profile=True, keep_fields=False):
+    """Create, run ``warmup`` untimed steps from rest, time ``steps`` steps
+    with CUDA events (all at the same fixed dt), then -- untimed -- take a
+    per-kernel breakdown of one step and event-time the dominant kernel's
+    launches over a few more steps."""
     h = V.vos_create(es, prm)
     try:
-        # first step with a small dt (the flow starts from rest), then the
-        # CFL / Delta-eps limit of vos_suggest_dt for the remaining steps
-        dt0 = 0.1 * prm["dx"] / max(abs(prm["u_in"]), 1e-30)
-        V.vos_step(h, dt0)
-        dt = dt0
-        for _ in range(max(warmup - 1, 0)):
-            dt = min(V.vos_suggest_dt(h, 0.5, 0.005), 5.0 * dt0)
+        for _ in range(warmup):
             V.vos_step(h, dt)
-        dt = min(V.vos_suggest_dt(h, 0.5, 0.005), 5.0 * dt0)
-        breakdown, top = None, None
+        # timed steps: CUDA-graph replay (default launch mode), no per-kernel timing
+        stream = torch.cuda.current_stream()
+        iters = []
+        l0 = V.vos_kernel_launches()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            V.vos_step(h, dt)
+            iters.append(_stats_row(V.vos_get_stats(h)))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = V.vos_kernel_launches() - l0
+        ms = e0.elapsed_time(e1) / steps
+        final = V.vos_get_stats(h)
+        fields = V.vos_fields(h, ("eps", "c", "u", "p")) if keep_fields else None
+        dt_cfl = V.vos_suggest_dt(h, 0.5, 0.005)
+        breakdown, top, roof = None, None, None
         if profile:
             V.vos_prof_reset()
             V.vos_prof_enable("*")
             torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             V.vos_step(h, dt)
             e1.record()
@@ -187,25 +211,8 @@ def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
                                key=lambda r: -r["ms"])
             top = breakdown[0]["kernel"] if breakdown else None
             breakdown = {"step_ms_profiled": step_ms, "kernel_ms_sum": tot, "kernels": breakdown[:48]}
-        # timed steps: CUDA-graph replay (default launch mode), no per-kernel timing
-        stream = torch.cuda.current_stream()
-        iters = []
-        l0 = V.vos_kernel_launches()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            V.vos_step(h, dt)
-            s = V.vos_get_stats(h)
-            iters.append((s["iters_u"], s["iters_p"], s["iters_c"], s["res_p"], s["outer_u"], s["outer_p"], s["outer_c"]))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        launches = V.vos_kernel_launches() - l0
-        ms = e0.elapsed_time(e1) / steps
-        roof = None
         if top:
-            # roofline window: the same steps with the dominant kernel's
+            # roofline window: further steps with the dominant kernel's
             # launches bracketed by CUDA events on the launching stream
             # (per-kernel timing uses the eager launch sequence)
             V.vos_prof_reset()
@@ -234,9 +241,19 @@ def time_gpu(V, es, prm, steps, warmup, torch, profile=True):
             except V.VosError:
                 pass
         return dict(ms=ms, dt=dt, iters=iters, dev_bytes=V.vos_device_bytes(h), breakdown=breakdown,
-                    roofline=roof, launches=launches, tiles=tiles)
+                    roofline=roof, launches=launches, tiles=tiles, final=final, fields=fields, dt_cfl=dt_cfl)
     finally:
         V.vos_destroy(h)
+
+
+def mom_precond_name(prm, dt):
+    """Which momentum preconditioner vos_step picks (include/vos.h rule)."""
+    fl = int(prm.get("precond", 0))
+    if fl & 2:
+        return "diag"
+    if fl & 4:
+        return "mg"
+    return "mg" if 2.0 * prm["dim"] * prm["nu"] * dt / prm["dx"] ** 2 > 30.0 else "diag"
 
 
 def measured_bf16_peak():
@@ -247,7 +264,7 @@ def measured_bf16_peak():
         return 1900.0, "fallback"
 
 
-def learned_leg(V, es, prm, dt, steps, torch, crop=64, rounds=2, adam_per_round=60, lr=2e-3, seed=0):
+def learned_leg(V, es, prm, dt, steps, warmup, torch, crop=64, rounds=2, adam_per_round=60, lr=2e-3, seed=0):
     """The learned pressure preconditioner on the same workload: train the
     U-Net with the library's own kernels on residual snapshots of short runs
     on crop^3 pieces of the rock (the network is fully convolutional), then
@@ -260,17 +277,16 @@ def learned_leg(V, es, prm, dt, steps, torch, crop=64, rounds=2, adam_per_round=
     losses = []
     n = es.shape[0]
     offsets = [(0, 0, 0), (n - crop, n - crop, n - crop)]
-    dt0 = 0.1 * prm["dx"] / max(abs(prm["u_in"]), 1e-30)
     for oz, oy, ox in offsets:
         esc = np.ascontiguousarray(es[oz:oz + crop, oy:oy + crop, ox:ox + crop])
         prc = dict(prm)
         prc.update(nx=crop, ny=crop, nz=crop)
         h = V.vos_create(esc, prc)
         try:
-            V.vos_step(h, dt0)
+            V.vos_step(h, dt)
             snaps = torch.empty((len(snap_iters), crop ** 3), dtype=torch.float32, device="cuda")
             for _ in range(rounds):
-                V.vos_step(h, min(V.vos_suggest_dt(h, 0.5, 0.005), 5.0 * dt0))
+                V.vos_step(h, dt)
                 V.vos_pressure_snapshots(h, snap_iters, snaps)
                 for k in range(adam_per_round):
                     losses.append(net_t.train_step(h, snaps[k % len(snap_iters)], lr))
@@ -284,10 +300,10 @@ def learned_leg(V, es, prm, dt, steps, torch, crop=64, rounds=2, adam_per_round=
     net.set_params(params)
     h = V.vos_create(es, prm)
     try:
-        V.vos_step(h, dt0)
-        V.vos_step(h, dt)
+        for _ in range(max(warmup - 1, 0)):
+            V.vos_step(h, dt)
         V.vos_set_unet_preconditioner(h, net)
-        V.vos_step(h, dt)  # warm-up with the network
+        V.vos_step(h, dt)  # last warm-up step, with the network
         stream = torch.cuda.current_stream()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -338,13 +354,12 @@ def batch_workload(count=64):
     return eps, prms
 
 
-def time_batch(V, eps, prms, steps, warmup, torch, nthreads=16):
+def time_batch(V, eps, prms, steps, warmup, torch, nthreads=16, dt=0.02):
     b = V.vos_batch_create(eps, prms, nthreads=nthreads)
     try:
-        dts = [0.05] * len(eps)
+        dts = [dt] * len(eps)
         for _ in range(max(warmup, 1)):
             V.vos_batch_step(b, dts)
-            dts = [min(V.vos_suggest_dt(h, 0.5, 0.005), 0.5) for h in b.handles]
         l0 = V.vos_kernel_launches()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -381,7 +396,7 @@ def time_e2e(V, es, prm, steps, dt):
             "d2h_bytes_per_step": int(2 * n * 8 / steps), "steps": steps, "checksum": float(f["c"].sum())}
 
 
-def oracle_sample(es, prm, budget_s=20.0, crop=40):
+def oracle_sample(es, prm, dt, budget_s=20.0, crop=40):
     """The CPU oracle on a bounded crop (crop^3 for 3D, crop x crop... for 2D)
     of the same geometry and parameters; returns (cell-steps/s, steps, shape,
     wall seconds, threads used = process CPU time / wall time over the timed
@@ -399,7 +414,7 @@ def oracle_sample(es, prm, budget_s=20.0, crop=40):
     c0 = time.process_time()
     n = 0
     while True:
-        st, _ = O.step(st, 0.5, p, solver="iterative", rtol=p["p_rtol"])
+        st, _ = O.step(st, dt, p, solver="iterative", rtol=p["p_rtol"])
         n += 1
         if time.perf_counter() - t0 > budget_s or n >= 20:
             break
@@ -413,12 +428,13 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     es, prm, desc = workload(args.workload, args.size)
+    dt_step = args.dt if args.dt else DEFAULT_DT[args.workload]
     cells = []
     for _ in range(max(args.warmup, 0)):
-        oracle_sample(es, prm, budget_s=2.0)
+        oracle_sample(es, prm, dt_step, budget_s=2.0)
     rates, used = [], []
     for _ in range(args.steps):
-        r, n, shp, dt, cores = oracle_sample(es, prm, budget_s=5.0)
+        r, n, shp, dt, cores = oracle_sample(es, prm, dt_step, budget_s=5.0)
         rates.append(r)
         cells.append(shp)
         used.append(cores)
@@ -426,7 +442,7 @@ def reference_arm(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "desc": desc},
+           "config": {"workload": args.workload, "desc": desc, "dt": dt_step},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": max(used), "kind": "oracle",
                             "sample": f"oracle step(s) on a {cells[0]} crop of the workload geometry, "
                                       "scipy CG/BiCGStab to the same tolerances, ~5 s per timed step"},
@@ -442,7 +458,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rock256", choices=["rock256", "micromodel", "calcite", "batch64"])
     ap.add_argument("--size", type=int, default=256, help="edge of the rock workload (profiling runs only)")
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="0 skips the FP64 leg; otherwise it runs the same W + K steps as the mixed leg")
+    ap.add_argument("--dt", type=float, default=None, help="fixed time step of every leg (default per workload)")
+    ap.add_argument("--mom-precond", default="auto", choices=["auto", "diag", "mg"],
+                    help="momentum preconditioner: the library's rule, or forced")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner leg")
     ap.add_argument("--eager", action="store_true",
@@ -471,7 +491,7 @@ def main():
         N = int(sum(e.size for e in eps))
         clocks = ClockSampler(local)
         clocks.start()
-        r = time_batch(V, eps, prms, args.steps, args.warmup, torch)
+        r = time_batch(V, eps, prms, args.steps, args.warmup, torch, dt=args.dt or 0.02)
         ck = clocks.stop()
         out = {"metric": METRIC, "value": N / (r["ms"] * 1e-3), "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
@@ -486,40 +506,67 @@ def main():
             print(json.dumps(out), flush=True)
         return
     es, prm, desc = workload(args.workload, args.size)
+    if args.mom_precond != "auto":
+        prm["precond"] = int(prm.get("precond", 0)) | (2 if args.mom_precond == "diag" else 4)
+    dt = args.dt if args.dt else DEFAULT_DT[args.workload]
     N = es.size
     clocks = ClockSampler(local)
     if dist is not None:
         dist.barrier()
     clocks.start()
-    r = time_gpu(V, es, prm, args.steps, args.warmup, torch)
+    r = time_gpu(V, es, prm, args.steps, args.warmup, dt, torch, keep_fields=args.fp64_steps > 0)
     ck = clocks.stop()
-    ms, dt, iters = r["ms"], r["dt"], r["iters"]
+    ms, iters = r["ms"], r["iters"]
     t = torch.tensor([ms], device=device)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
     ms = float(t.item())
     value = N * world / (ms * 1e-3)
-    p64 = dict(prm)
-    p64["precision"] = 0
-    # FP64-only solver leg (--fp64-steps 0 skips it, for profiling runs)
-    r64 = time_gpu(V, es, p64, args.fp64_steps, 2, torch, profile=False) if args.fp64_steps > 0 else None
+    # FP64-only solver leg: same workload, dt and step sequence (warm-up W,
+    # then K timed steps), so its fields after W + K steps are the FP64
+    # counterpart of the mixed leg's (--fp64-steps 0 skips it)
+    r64, prec = None, None
+    if args.fp64_steps > 0:
+        p64 = dict(prm)
+        p64["precision"] = 0
+        r64 = time_gpu(V, es, p64, args.steps, args.warmup, dt, torch, profile=False, keep_fields=True)
+        f32, f64 = r["fields"], r64["fields"]
+        prec = {"steps": args.warmup + args.steps,
+                "porosity_err": abs(r["final"]["porosity"] - r64["final"]["porosity"]),
+                "rel_l2": {n: float(np.linalg.norm(f32[n] - f64[n]) / max(np.linalg.norm(f64[n]), 1e-300))
+                           for n in f64},
+                "reference": "the FP64 GPU path (parity-tested against the FP64 oracle to 1e-9) after the same steps"}
     e2e = time_e2e(V, es, prm, max(2, args.steps // 2), dt)
     learned = None
     if not args.no_learned and es.ndim == 3 and min(es.shape) >= 64:
-        learned = learned_leg(V, es, prm, dt, 3, torch)
+        learned = learned_leg(V, es, prm, dt, 3, args.warmup, torch)
         learned["vs_fp64"] = learned["value"] / (N / (r64["ms"] * 1e-3)) if r64 else None
+        learned["vs_mixed"] = learned["value"] / (N / (r["ms"] * 1e-3))
+    fp64_value = N * world / (r64["ms"] * 1e-3) if r64 else None
+    mom = mom_precond_name(prm, dt)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": args.workload, "desc": desc, "cells": N, "dt": dt,
+                      "dt_rule": "fixed for every leg and step (warm-up from rest included)",
+                      "dt_cfl05_after": r["dt_cfl"],
                       "p_rtol": prm["p_rtol"], "u_rtol": prm["u_rtol"], "c_rtol": prm["c_rtol"],
+                      "momentum_precond": mom,
                       "residual": "diagonally scaled, FP64",
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "launch": "eager" if args.eager else "graph", "tiles": r["tiles"]},
            "roofline": r["roofline"], "gpu_launches": r["launches"],
-           "fp64": ({"value": N * world / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"],
+           "fp64_value": fp64_value, "fp64_ms_per_step": r64["ms"] if r64 else None,
+           "mixed_vs_fp64": (value / fp64_value) if fp64_value else None,
+           "learned_value": learned["value"] if learned else None,
+           "learned_vs_fp64": learned["vs_fp64"] if learned else None,
+           "iters_p": float(np.mean([i[1] for i in iters])),
+           "iters_u": [float(np.mean([i[0][a] for i in iters])) for a in range(3)],
+           "porosity_err": prec["porosity_err"] if prec else None,
+           "fp64": ({"value": fp64_value, "ms_per_step": r64["ms"],
                      "iters_p_mean": float(np.mean([i[1] for i in r64["iters"]]))} if r64 else None),
+           "mixed_precision_error": prec,
            "solver": {"iters_u_mean": [float(np.mean([i[0][a] for i in iters])) for a in range(3)],
                       "iters_p_mean": float(np.mean([i[1] for i in iters])),
                       "iters_c_mean": float(np.mean([i[2] for i in iters])),
@@ -530,7 +577,7 @@ def main():
            "device_bytes": r["dev_bytes"], "e2e": e2e, "clocks": ck, "learned": learned,
            "breakdown": r["breakdown"]}
     if rank == 0 and not args.no_cpu:
-        r, n, shp, dtc, cores = oracle_sample(es, prm, budget_s=15.0)
+        r, n, shp, dtc, cores = oracle_sample(es, prm, dt, budget_s=15.0)
         out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{n} oracle step(s) on a {tuple(shp)} crop of the same geometry "
                                          f"({dtc:.1f} s), scipy CG/BiCGStab at the same tolerances"}

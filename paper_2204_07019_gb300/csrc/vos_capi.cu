@@ -221,6 +221,18 @@ bool alloc_sys(vos_handle* h, Sys<T>& S, int sys, int sym) {
   return true;
 }
 
+// The momentum operator is (1/dt + drag) I - nu lap: when the mass term
+// dominates (2 d nu dt / dx^2 <= 30) the diagonally preconditioned CG
+// converges in a grid-independent number of iterations at a third of the
+// traffic of a multigrid iteration; otherwise use multigrid.  The precond
+// flags VOS_PRECOND_MOM_DIAG / VOS_PRECOND_MOM_MG override the rule.
+bool mom_mg_for(const vos_handle* h, double dt) {
+  if (h->prm.precond & VOS_PRECOND_MOM_DIAG) return false;
+  if (h->prm.precond & VOS_PRECOND_MOM_MG) return true;
+  const Phys& P = h->ph;
+  return 2.0 * P.dim * P.nu * dt / (P.dx * P.dx) > 30.0;
+}
+
 template <typename T>
 int step_impl(vos_handle* h, Sys<T>* S, double dt) {
   const Phys& P = h->ph;
@@ -241,11 +253,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     s.res_u[a] = 0.0;
     if (box_cells(S[a].box) == 0) continue;
     launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
-    // The momentum operator is (1/dt + drag) I - nu lap: when the mass term
-    // dominates (2 d nu dt / dx^2 <= 30) the diagonally preconditioned CG
-    // converges in a grid-independent number of iterations at a third of
-    // the traffic of a multigrid iteration; otherwise use multigrid.
-    const bool mom_mg = 2.0 * nd * P.nu * dt / (P.dx * P.dx) > 30.0;
+    const bool mom_mg = mom_mg_for(h, dt);
     SolveResult r = solve<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
                              h->work, h->rs, st, mom_mg);
     s.iters_u[a] = r.iters;
@@ -342,12 +350,9 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
 template <typename T>
 int finish_graph_step(vos_handle* h, Sys<T>* S, double dt);
 
-bool mom_mg_for(const Phys& P, double dt) { return 2.0 * P.dim * P.nu * dt / (P.dx * P.dx) > 30.0; }
-
 template <typename T>
 int step_graph(vos_handle* h, Sys<T>* S, double dt) {
-  const Phys& P = h->ph;
-  const bool mom_mg = 2.0 * P.dim * P.nu * dt / (P.dx * P.dx) > 30.0;
+  const bool mom_mg = mom_mg_for(h, dt);
   const int gi = mom_mg ? 1 : 0;
   if (!h->exec[gi]) {
     cudaError_t e = cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeRelaxed);
@@ -473,7 +478,10 @@ int validate(const vos_params* p) {
   if (!std::isfinite(p->u_in)) return set_err(nullptr, VOS_EINVAL, "u_in must be finite");
   if (p->method < 0 || p->method > 2) return set_err(nullptr, VOS_EINVAL, "unknown method %d", p->method);
   if (p->precision < 0 || p->precision > 1) return set_err(nullptr, VOS_EINVAL, "unknown precision %d", p->precision);
-  if (p->precond & ~VOS_PRECOND_NO_DEFLATION) return set_err(nullptr, VOS_EINVAL, "unknown precond flags %d", p->precond);
+  if (p->precond & ~(VOS_PRECOND_NO_DEFLATION | VOS_PRECOND_MOM_DIAG | VOS_PRECOND_MOM_MG))
+    return set_err(nullptr, VOS_EINVAL, "unknown precond flags %d", p->precond);
+  if ((p->precond & VOS_PRECOND_MOM_DIAG) && (p->precond & VOS_PRECOND_MOM_MG))
+    return set_err(nullptr, VOS_EINVAL, "VOS_PRECOND_MOM_DIAG and VOS_PRECOND_MOM_MG exclude each other");
   if (p->flow_subiters != 1) return set_err(nullptr, VOS_EINVAL, "flow_subiters must be 1");
   const double tol[] = {p->p_rtol, p->u_rtol, p->c_rtol};
   for (double v : tol)
@@ -914,7 +922,7 @@ namespace vos {
 bool graphs_enabled() { return g_use_graphs && !g_prof_any; }
 bool batch_graphable(const vos_handle* h) { return h->net == nullptr; }
 unsigned batch_generation(const vos_handle* h) { return h->graph_gen; }
-int batch_key(const vos_handle* h, double dt) { return mom_mg_for(h->ph, dt) ? 1 : 0; }
+int batch_key(const vos_handle* h, double dt) { return mom_mg_for(h, dt) ? 1 : 0; }
 double* batch_dt_slot(vos_handle* h) { return h->d_dt; }
 // Enqueue h's step on its internal stream inside an active capture: fork
 // from `fork` (recorded on the capture's origin stream), join into `join`,
