@@ -11,8 +11,8 @@ A step is one full vos_step (S1-S7).  The plain-FP64 path is timed on the
 same workload beside it (``fp64``).
 
 Every leg runs W warm-up steps from rest and then K timed steps, all at one
-fixed time step (``config.dt``; 2.5e-3 on the rock, close to the CFL-0.5
-limit of its developed flow, which the line reports as ``dt_cfl05_after``),
+fixed time step (``config.dt``; 1e-3 on the rock, below the CFL-0.5 limit
+of its developed flow, which the line reports as ``dt_cfl05_after``),
 so the mixed, FP64 and learned legs advance the same state and their ratios
 are like for like; ``config.momentum_precond`` says which momentum
 preconditioner that dt selects.
@@ -158,7 +158,10 @@ TRAFFIC_PER_ALG_BYTE = {
 }
 
 
-DEFAULT_DT = {"rock256": 2.5e-3, "micromodel": 0.02, "calcite": 0.25}
+# Fixed time steps: on the rock 1e-3 lies below the CFL-0.5 limit of the
+# interstitial speed that vos_suggest_dt reports once the flow has developed
+# (1.2e-3 measured after 7 steps at 2.5e-3).
+DEFAULT_DT = {"rock256": 1.0e-3, "micromodel": 0.02, "calcite": 0.25}
 
 
 def _stats_row(s):
@@ -463,6 +466,9 @@ def main():
     ap.add_argument("--dt", type=float, default=None, help="fixed time step of every leg (default per workload)")
     ap.add_argument("--mom-precond", default="auto", choices=["auto", "diag", "mg"],
                     help="momentum preconditioner: the library's rule, or forced")
+    ap.add_argument("--no-coarse-cycle", action="store_true",
+                    help="one launch per multigrid operation on every level instead of the cluster-resident "
+                         "coarse cycle (same results; for comparison)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner leg")
     ap.add_argument("--eager", action="store_true",
@@ -486,6 +492,8 @@ def main():
     V.load_library()
     if args.eager:
         V.vos_set_launch_mode(0)
+    if args.no_coarse_cycle:
+        V.vos_set_coarse_cycle(0)
     if args.workload == "batch64":
         eps, prms = batch_workload(64)
         N = int(sum(e.size for e in eps))
@@ -555,7 +563,8 @@ def main():
                       "momentum_precond": mom,
                       "residual": "diagonally scaled, FP64",
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
-                      "launch": "eager" if args.eager else "graph", "tiles": r["tiles"]},
+                      "launch": "eager" if args.eager else "graph", "tiles": r["tiles"],
+                      "coarse_cycle": "separate launches" if args.no_coarse_cycle else "cluster-resident"},
            "roofline": r["roofline"], "gpu_launches": r["launches"],
            "fp64_value": fp64_value, "fp64_ms_per_step": r64["ms"] if r64 else None,
            "mixed_vs_fp64": (value / fp64_value) if fp64_value else None,

@@ -100,8 +100,11 @@ typedef struct vos_params {
   int32_t precond;   /* vos_precond flags; 0: multigrid + pocket deflation */
   double p_rtol, u_rtol, c_rtol;
   int32_t max_iter;
-  int32_t flow_subiters; /* 1: one transient step (only value accepted) */
+  int32_t flow_subiters; /* 1: one transient step; M > 1: quasi-static step,
+                            at most M sub-iterations (see vos_step)        */
   uint32_t wall_mask;
+  double qs_rtol;        /* quasi-static stop test (0: always M iterations)  */
+  double qs_dtau;        /* pseudo time step of the sub-iterations (0: dt)   */
 } vos_params;
 
 /* Statistics of the last completed step (FP64 device reductions; S7).
@@ -129,6 +132,10 @@ typedef struct vos_stats {
                           mean of the two cells; boundary: adjacent cell)    */
   double rmax;         /* max |Vm R|: dt <= deps_max / rmax bounds the change
                           of eps per step (App. D)                          */
+  int32_t qs_iters;    /* sub-iterations of the step (1 for a transient step) */
+  double qs_du, qs_dp, qs_dc; /* last relative changes of u, p (eps-weighted)
+                          and c between sub-iterations (quasi-static steps;
+                          NaN otherwise)                                     */
 } vos_stats;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
@@ -165,7 +172,21 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream,
  * host waits once, at the end, for the solver statistics; in the eager mode
  * (vos_set_launch_mode(0)) the host reads the residual once per refinement
  * pass and every few Krylov iterations.  Returns VOS_ENOCONV if a solve
- * reached max_iter (the step is still applied). */
+ * reached max_iter (the step is still applied).
+ * Quasi-static step (flow_subiters = M > 1; App. A and B: flow and
+ * transport iterated to a steady state with eps frozen, the rate refreshed
+ * after every iteration): S1 advances eps by dt once; S2-S6 then repeat with
+ * the latest iterate as the old velocity and concentration, eps^{n+1} in
+ * both storage terms and qs_dtau (0: dt) as the time step, so that a fixed
+ * point solves the quasi-static equations (Eq. momentumDBSQS without
+ * inertia, Eq. contDBSQS, Eq. concentrationDBSQS).  The loop ends after M
+ * sub-iterations or when the relative L2 changes of u, of p (weighted by
+ * eps: the pressure inside the solid relaxes far more slowly and barely
+ * moves the flow) and of c are all <= qs_rtol; with qs_rtol > 0 a loop that
+ * reaches M without meeting the test returns VOS_ENOCONV (step applied).
+ * Quasi-static steps always launch eagerly (no CUDA graph); vos_stats
+ * reports the sub-iterations and the last relative changes, and its solver
+ * iteration counts are summed over the sub-iterations. */
 int vos_step(vos_handle* h, double dt);
 
 /* Copy the selected fields (mask of VOS_F_*) to caller-owned host buffers
@@ -192,6 +213,34 @@ int vos_get_stats(vos_handle* h, vos_stats* out);
  * Synchronous.  Returns +inf in *dt when neither limit applies and 0 when a
  * face speed or a rate is NaN. */
 int vos_suggest_dt(vos_handle* h, double cfl, double deps_max, double* dt);
+
+/* Darcy-scale properties of the current fields (Sec. 2.5), FP64 device
+ * reductions; synchronous.  V_Omega = nx ny nz dx^dim, face area
+ * A = dx^(dim-1).
+ *   phi    total porosity, mean eps;
+ *   Q_in   inlet flow rate, sum over the inlet faces of u_f A;
+ *   A_in   inlet area ny nz A;  U_D = Q_in / A_in (Darcy velocity);
+ *   dP     kinematic pressure drop: mean p of the first cell column (i = 0)
+ *          minus the outlet face value 0 (the inlet condition is
+ *          zero-gradient, so the first cell centres carry the inlet
+ *          pressure);  L_D = (nx - 1/2) dx, the distance between them;
+ *   K      permeability nu U_D L_D / dP (uniform Darcy flow gives exactly
+ *          k = k0 eps^3 / (1 - eps)^2 of Eq. perm);
+ *   a      specific surface area (1/V_Omega) int |grad eps| dV (centred
+ *          gradient; |grad eps| is the surface-area density of the
+ *          micro-continuum);
+ *   alpha  (1/a) sum c |grad eps| / sum eps c: the surface-averaged over
+ *          the volume-averaged concentration (1/phi for uniform c);
+ *   L_ref  sqrt(f K / phi), f = 12 in 2D (channel width of a bundle of
+ *          straight channels) and 8 in 3D (throat radius of a capillary
+ *          bundle);  U_ref = U_D / phi;
+ *   Pe = U_ref L_ref / D, Da = kc / U_ref, Ki = Da Pe.
+ * A quantity whose denominator vanishes is NaN.  Errors: VOS_EINVAL,
+ * VOS_ECUDA. */
+typedef struct vos_upscaled_props {
+  double phi, Q_in, A_in, U_D, dP, L_D, K, a, alpha, L_ref, U_ref, Pe, Da, Ki;
+} vos_upscaled_props;
+int vos_upscaled(vos_handle* h, vos_upscaled_props* out);
 
 /* Batches of independent simulations (e.g. many micromodels of uneven
  * sizes and parameters stepped together; no counterpart in the paper's
@@ -394,6 +443,15 @@ uint64_t vos_kernel_launches(void);
  *   launched one by one with host polls of the device scalars.  While
  *   per-kernel timing is on the eager sequence is used. */
 int vos_set_launch_mode(int graphs);
+/* vos_set_coarse_cycle(1) (default): in every multigrid hierarchy set up
+ *   afterwards (vos_create, vos_batch_create), the levels from the first one
+ *   with at most 32,768 cells down to the coarsest run as ONE launch per
+ *   V-cycle of one thread-block cluster of 8 CTAs that keeps those levels in
+ *   distributed shared memory (when the device can run that cluster);
+ *   vos_set_coarse_cycle(0): one launch per sweep, residual, restriction and
+ *   prolongation on every level.  Both give bit-identical results (the same
+ *   arithmetic per cell, in the same order). */
+int vos_set_coarse_cycle(int on);
 int vos_prof_enable(const char* filter);
 int vos_prof_report(char* buf, size_t len);
 void vos_prof_reset(void);

@@ -547,47 +547,98 @@ def transport_system(eps_old, eps, c_old, u, prm, dt, kr=None, faces=None):
 # --------------------------------------------------------------------------
 
 def step(state, dt, prm, solver="direct", rtol=1e-13):
-    """One micro-continuum time step (App. B order, transient reading).
+    """One micro-continuum time step (App. B order).
 
     S1 eps (Eq. mbs) and k (Eq. perm); S2 momentum predictor per component;
     S3 pressure correction and projection; S4 explicit van Leer advection;
     S5 implicit diffusion + reaction; S6 reaction rates R, R_f from c^{n+1};
     S7 diagnostics.  Returns (new_state, stats).
+
+    Transient reading (flow_subiters = 1): S2-S6 run once.  Quasi-static
+    reading (flow_subiters = M > 1, App. A and B: flow and transport iterated
+    to a steady state with eps frozen, the rate refreshed after every
+    iteration): S1 runs once, then S2-S6 are repeated with the latest
+    iterate as the "old" velocity and concentration and eps^{n+1} in both
+    storage terms, so that a fixed point u = u^m, p = p^m, c = c^m satisfies
+    the quasi-static equations (Eq. momentumDBSQS without inertia,
+    Eq. contDBSQS, Eq. concentrationDBSQS) exactly; the sub-iterations
+    march in a pseudo time step qs_dtau (0: dt), while dt itself only
+    advances eps (App. A: with the flow and transport quasi-static, the
+    time step is set by the motion of the solid).  The loop stops after M iterations or when the
+    relative changes |u^{m+1} - u^m| / |u^{m+1}|, |p^{m+1} - p^m|_eps /
+    |p^{m+1}|_eps and |c^{m+1} - c^m| / |c^{m+1}| are all <= qs_rtol
+    (qs_rtol = 0: always M iterations); L2 norms over all faces / cells, the
+    pressure's weighted by eps.  Reading: the pressure inside the solid,
+    tied to the rest only through links of order eps_min and damped by the
+    Kozeny-Carman drag, relaxes orders of magnitude more slowly than in the
+    pore space while it barely moves the flow, so its change is measured
+    with the fluid fraction as weight.
     """
     shp = _shape(prm)
     axes = _axes(prm)
     method = int(prm["method"])
-    eps_old = state["eps"]
-    eps, excess = solid_update(eps_old, state["R"], dt, prm)
-    # S2
-    ustar = [x.copy() for x in state["u"]]
-    for a in axes:
-        A, b, unk = momentum_system(a, eps, state["p"], state["u"][a], dt, prm)
-        ustar[a][unk] = _solve(A, b, True, solver, rtol)
-    # S3
-    A, b = pressure_system(eps, ustar, state["R"], dt, prm)
-    phi = _solve(A, b, True, solver, rtol).reshape(shp)
-    u = project(ustar, phi, eps, dt, prm)
-    p = state["p"] + phi
-    # S5/S6
-    lam = float("nan")
-    if method == VOS_IVOS:
-        faces = ivos_faces(eps, state["c"], prm)
-        A, b = transport_system(eps_old, eps, state["c"], u, prm, dt, faces=faces)
-        c = _solve(A, b, False, solver, rtol).reshape(shp)
-        R, Rf = ivos_rates(eps, c, faces, prm)
-    else:
-        lam = prm["lam"] if method == VOS_PSI else vos_lambda(eps, prm)
-        kr = vos_coefficient(eps, prm, lam)
-        A, b = transport_system(eps_old, eps, state["c"], u, prm, dt, kr=kr)
-        c = _solve(A, b, True, solver, rtol).reshape(shp)
-        R = kr * c
-        Rf = R.copy()
+    M = int(prm.get("flow_subiters", 1))
+    qs_rtol = float(prm.get("qs_rtol", 0.0))
+    dtau = float(prm.get("qs_dtau", 0.0)) if M > 1 else 0.0
+    if not dtau > 0.0:
+        dtau = dt
+    eps_n = state["eps"]
+    eps, excess = solid_update(eps_n, state["R"], dt, prm)
+    eps_store = eps_n if M == 1 else eps
+    u_it, p_it, c_it, R_it = state["u"], state["p"], state["c"], state["R"]
+    qs_iters, du, dp, dc = 0, float("nan"), float("nan"), float("nan")
+    for m in range(M):
+        # S2
+        ustar = [x.copy() for x in u_it]
+        for a in axes:
+            A, b, unk = momentum_system(a, eps, p_it, u_it[a], dtau, prm)
+            ustar[a][unk] = _solve(A, b, True, solver, rtol)
+        # S3
+        A, b = pressure_system(eps, ustar, R_it, dtau, prm)
+        phi = _solve(A, b, True, solver, rtol).reshape(shp)
+        u = project(ustar, phi, eps, dtau, prm)
+        p = p_it + phi
+        # S5/S6
+        lam = float("nan")
+        if method == VOS_IVOS:
+            faces = ivos_faces(eps, c_it, prm)
+            A, b = transport_system(eps_store, eps, c_it, u, prm, dtau, faces=faces)
+            c = _solve(A, b, False, solver, rtol).reshape(shp)
+            R, Rf = ivos_rates(eps, c, faces, prm)
+        else:
+            lam = prm["lam"] if method == VOS_PSI else vos_lambda(eps, prm)
+            kr = vos_coefficient(eps, prm, lam)
+            A, b = transport_system(eps_store, eps, c_it, u, prm, dtau, kr=kr)
+            c = _solve(A, b, True, solver, rtol).reshape(shp)
+            R = kr * c
+            Rf = R.copy()
+        qs_iters = m + 1
+        if M > 1:
+            du_num = sum(float(np.sum((u[a] - u_it[a]) ** 2)) for a in axes)
+            du_den = sum(float(np.sum(u[a] ** 2)) for a in axes)
+            du = float(np.sqrt(du_num / du_den)) if du_den > 0 else 0.0
+            dcn, dcd = float(np.sum((c - c_it) ** 2)), float(np.sum(c ** 2))
+            dc = float(np.sqrt(dcn / dcd)) if dcd > 0 else 0.0
+            dpn, dpd = float(np.sum(eps * phi ** 2)), float(np.sum(eps * p ** 2))
+            dp = float(np.sqrt(dpn / dpd)) if dpd > 0 else 0.0
+        prev_c = c_it
+        u_it, p_it, c_it, R_it = u, p, c, R
+        if M > 1 and qs_rtol > 0 and du <= qs_rtol and dp <= qs_rtol and dc <= qs_rtol:
+            break
     new = dict(eps=eps, c=c, p=p, u=u, R=R, Rf=Rf, t=state["t"] + dt,
                step=state["step"] + 1)
-    stats = diagnostics(state, new, prm)
-    stats.update(lam=lam, clamp_excess=excess)
+    stats = diagnostics(dict(state, c=prev_c), new, prm)
+    stats.update(lam=lam, clamp_excess=excess, qs_iters=qs_iters, qs_du=du, qs_dp=dp, qs_dc=dc)
     return new, stats
+
+
+def run(eps_s, prm, dts, solver="direct", rtol=1e-13):
+    st = init_state(eps_s, prm)
+    stats = []
+    for dt in dts:
+        st, s = step(st, dt, prm, solver=solver, rtol=rtol)
+        stats.append(s)
+    return st, stats
 
 
 def diagnostics(prev, new, prm):
@@ -626,13 +677,55 @@ def diagnostics(prev, new, prm):
                 umax=interstitial_speed_max(new, prm), rmax=float(np.max(np.abs(prm["Vm"] * new["R"]))))
 
 
-def run(eps_s, prm, dts, solver="direct", rtol=1e-13):
-    st = init_state(eps_s, prm)
-    stats = []
-    for dt in dts:
-        st, s = step(st, dt, prm, solver=solver, rtol=rtol)
-        stats.append(s)
-    return st, stats
+def upscaled(state, prm):
+    """Darcy-scale characterisation of the domain (Sec. 2.5).
+
+    * phi: total porosity, mean eps;
+    * U_D = Q_i / A_i: inlet flow rate over inlet area (sum over the inlet
+      faces of u_f A_f, over ny nz A_f);
+    * K = nu U_D L_D / dP.  Reading: the pressure is stored at cell centres
+      with a zero-gradient inlet condition, so dP is the mean pressure of the
+      first cell column (i = 0) minus the outlet face value 0 and L_D is the
+      distance between them, (nx - 1/2) dx (for uniform Darcy flow this
+      gives K = k of Eq. perm exactly);
+    * a = (1/V_Omega) int_Gamma dS, with the surface area density of the
+      micro-continuum |grad eps| (the integral VoS-psi' normalises by,
+      Sec. 2.4; centred gradient): a = mean |grad eps|;
+    * alpha = (1/a) int_Gamma c dS / int_Omega_f c dV with
+      int_Gamma c dS = sum c |grad eps| V and int_Omega_f c dV = sum eps c V;
+    * reference length L = sqrt(f K / phi), f = 12 in 2D (channel size of a
+      bundle of straight channels, BM2) and f = 8 in 3D (throat radius of a
+      capillary bundle, BM3); reference velocity U = U_D / phi; with them
+      Pe = U L / D, Da = k_c / U, Ki = Da Pe (Sec. 2.5).
+    Quantities whose denominator vanishes are NaN."""
+    shp = _shape(prm)
+    dim = int(prm["dim"])
+    dx = prm["dx"]
+    nz, ny, nx = shp
+    eps, c, p = state["eps"], state["c"], state["p"]
+    A = dx ** (dim - 1)
+    V = dx ** dim
+    phi = float(np.mean(eps))
+    Q = float(np.sum(state["u"][0][_sl(0, 0, 1)]) * A)
+    Ai = ny * nz * A
+    UD = Q / Ai
+    dP = float(np.mean(p[_sl(0, 0, 1)]))
+    LD = (nx - 0.5) * dx
+    nan = float("nan")
+    K = prm["nu"] * UD * LD / dP if dP != 0.0 else nan
+    g = central_gradient(eps, dx, _axes(prm))
+    mag = np.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2)
+    a = float(np.sum(mag) * V / (eps.size * V))
+    cs = float(np.sum(c * mag) * V)
+    cv = float(np.sum(eps * c) * V)
+    alpha = (cs / cv) / a if (a != 0.0 and cv != 0.0) else nan
+    f = 12.0 if dim == 2 else 8.0
+    Lr = float(np.sqrt(f * K / phi)) if K == K and K > 0 else nan
+    Ur = UD / phi
+    Pe = Ur * Lr / prm["D"] if prm["D"] > 0 else nan
+    Da = prm["kc"] / Ur if Ur != 0 else nan
+    return dict(phi=phi, Q_in=Q, A_in=Ai, U_D=UD, dP=dP, L_D=LD, K=K, a=a, alpha=alpha,
+                L_ref=Lr, U_ref=Ur, Pe=Pe, Da=Da, Ki=Da * Pe)
 
 
 def interstitial_speed_max(state, prm):

@@ -63,6 +63,7 @@ struct vos_handle {
   double* dstats;
   double* hstats;  // pinned
   double* d_dt;    // device copy of the step's dt (read by the physics kernels)
+  double* dups;    // device sums of vos_upscaled (6)
   // graph mode: the whole step captured once per momentum-preconditioner
   // choice and replayed on an internal stream ordered after the caller's
   SolveStats* dsolve;  // device, one per system
@@ -241,63 +242,106 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
   const int ivos = (h->prm.method == VOS_IVOS);
   vos_stats& s = h->stats;
   int status = VOS_OK;
+  // quasi-static step: M sub-iterations of S2-S6 with eps frozen (see vos.h)
+  const int M = h->prm.flow_subiters > 1 ? h->prm.flow_subiters : 1;
+  const bool qs = M > 1;
+  const double dtau = (qs && h->prm.qs_dtau > 0.0) ? h->prm.qs_dtau : dt;
+  const long long N = (long long)P.nx * P.ny * P.nz;
   launch_set_scalar(h->d_dt, dt, st);
   const double* dtp = h->d_dt;
   // S1: solid fraction and (implicitly) permeability
   launch_eps_update(P, h->eps, h->eps_old, h->R, dtp, h->dstats, h->rs, h->kic, st);
-  // S2: momentum predictor per component
-  for (int a = 0; a < nd; ++a) {
-    cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (qs) {
+    // the sub-iterations march in the pseudo step, with eps^{n+1} in both
+    // storage terms of the transport equation
+    launch_set_scalar(h->d_dt, dtau, st);
+    cudaMemcpyAsync(h->eps_old, h->eps, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  }
+  const bool mom_mg = mom_mg_for(h, dtau);
+  for (int a = 0; a < 3; ++a) {
     s.iters_u[a] = 0;
     s.outer_u[a] = 0;
     s.res_u[a] = 0.0;
-    if (box_cells(S[a].box) == 0) continue;
-    launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
-    const bool mom_mg = mom_mg_for(h, dt);
-    SolveResult r = solve<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
-                             h->work, h->rs, st, mom_mg);
-    s.iters_u[a] = r.iters;
-    s.outer_u[a] = r.outer;
-    s.res_u[a] = r.relres;
-    if (!r.converged) status = VOS_ENOCONV;
   }
-  // S3: pressure correction, projection
-  launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, h->eps32, st);
-  launch_defl_energy(S[3].h.defl, S[3].op64, st);
-  cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st);
-  {
-    SolveResult r =
-        solve<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter, h->work, h->rs, st,
-                 true);
-    h->net_iters = r.net_iters;
-    h->net_fallback = r.fallback;
-    s.iters_p = r.iters;
-    s.outer_p = r.outer;
-    s.res_p = r.relres;
-    if (!r.converged) status = VOS_ENOCONV;
+  s.iters_p = s.outer_p = s.iters_c = s.outer_c = 0;
+  s.qs_iters = 0;
+  s.qs_du = s.qs_dp = s.qs_dc = NAN;
+  h->net_iters = h->net_fallback = 0;
+  bool converged_qs = !qs || !(h->prm.qs_rtol > 0.0);
+  for (int m = 0; m < M; ++m) {
+    // S2: momentum predictor per component
+    for (int a = 0; a < nd; ++a) {
+      cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      if (box_cells(S[a].box) == 0) continue;
+      launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
+      SolveResult r = solve<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
+                               h->work, h->rs, st, mom_mg);
+      s.iters_u[a] += r.iters;
+      s.outer_u[a] += r.outer;
+      s.res_u[a] = r.relres;
+      if (!r.converged) status = VOS_ENOCONV;
+    }
+    // S3: pressure correction, projection
+    launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, h->eps32, st);
+    launch_defl_energy(S[3].h.defl, S[3].op64, st);
+    cudaMemsetAsync(h->phi, 0, (size_t)N * sizeof(double), st);
+    {
+      SolveResult r = solve<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter,
+                               h->work, h->rs, st, true);
+      h->net_iters += r.net_iters;
+      h->net_fallback |= r.fallback;
+      s.iters_p += r.iters;
+      s.outer_p += r.outer;
+      s.res_p = r.relres;
+      if (!r.converged) status = VOS_ENOCONV;
+    }
+    if (qs) {
+      launch_project_sums(P, h->eps, h->phi, dtp, h->us, h->u, h->p, h->dstats, h->rs, st);
+      launch_qs_sums(N, false, h->p, h->phi, h->eps, h->dstats + ST_QSP, h->rs, st);  // phi is p^{m+1} - p^m
+      // phi is dead from here on: it keeps c^m for the change of c
+      cudaMemcpyAsync(h->phi, h->c, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    } else {
+      launch_project(P, h->eps, h->phi, dtp, h->us, h->u, h->p, st);
+    }
+    // S4-S6: face data (convective fluxes of c^n; iVoS: reactive surface data
+    // from eps^{n+1}, c^n), transport, rates.  us[a] is dead from the
+    // projection until the next step copies u into it, so it holds the
+    // convective face fluxes meanwhile.
+    launch_face_data(P, ivos, h->eps, h->c, h->u, h->us, h->fd, st);
+    if (!ivos) {
+      launch_vos_lambda(P, h->eps, h->prm.lambda, h->prm.method == VOS_PSI_PRIME, h->dstats, h->rs, st);
+      launch_vos_coef(P, h->eps, h->dstats, h->kr, st);
+    }
+    launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->us, h->kr, h->fd, dtp, S[4].h.mg.omega, S[4].op64,
+                          S[4].rhs, st);
+    {
+      SolveResult r = solve<T>(S[4].op64, S[4].h, S[4].rhs, unknown_view(h, 4), h->prm.c_rtol, h->prm.max_iter,
+                               h->work, h->rs, st, true);
+      s.iters_c += r.iters;
+      s.outer_c += r.outer;
+      s.res_c = r.relres;
+      if (!r.converged) status = VOS_ENOCONV;
+    }
+    launch_rates(P, ivos, h->eps, h->c, h->kr, h->fd, h->R, h->Rf, h->dstats, h->rs, st);
+    s.qs_iters = m + 1;
+    if (qs) {
+      launch_qs_sums(N, true, h->c, h->phi, nullptr, h->dstats + ST_QSC, h->rs, st);
+      double q[10];
+      cudaMemcpyAsync(q, h->dstats + ST_QSU, sizeof(q), cudaMemcpyDeviceToHost, st);
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_step: %s", cudaGetErrorString(e));
+      const double dun = q[0] + q[2] + q[4], dud = q[1] + q[3] + q[5];
+      s.qs_du = dud > 0.0 ? std::sqrt(dun / dud) : 0.0;
+      s.qs_dp = q[7] > 0.0 ? std::sqrt(q[6] / q[7]) : 0.0;
+      s.qs_dc = q[9] > 0.0 ? std::sqrt(q[8] / q[9]) : 0.0;
+      const double tol = h->prm.qs_rtol;
+      if (tol > 0.0 && s.qs_du <= tol && s.qs_dp <= tol && s.qs_dc <= tol) {
+        converged_qs = true;
+        break;
+      }
+    }
   }
-  launch_project(P, h->eps, h->phi, dtp, h->us, h->u, h->p, st);
-  // S4-S6: face data (convective fluxes of c^n; iVoS: reactive surface data
-  // from eps^{n+1}, c^n), transport, rates.  us[a] is dead from the
-  // projection until the next step copies u into it, so it holds the
-  // convective face fluxes meanwhile.
-  launch_face_data(P, ivos, h->eps, h->c, h->u, h->us, h->fd, st);
-  if (!ivos) {
-    launch_vos_lambda(P, h->eps, h->prm.lambda, h->prm.method == VOS_PSI_PRIME, h->dstats, h->rs, st);
-    launch_vos_coef(P, h->eps, h->dstats, h->kr, st);
-  }
-  launch_trans_assemble(P, ivos, h->eps, h->eps_old, h->c, h->us, h->kr, h->fd, dtp, S[4].h.mg.omega, S[4].op64,
-                        S[4].rhs, st);
-  {
-    SolveResult r =
-        solve<T>(S[4].op64, S[4].h, S[4].rhs, unknown_view(h, 4), h->prm.c_rtol, h->prm.max_iter, h->work, h->rs, st,
-                 true);
-    s.iters_c = r.iters;
-    s.outer_c = r.outer;
-    s.res_c = r.relres;
-    if (!r.converged) status = VOS_ENOCONV;
-  }
-  launch_rates(P, ivos, h->eps, h->c, h->kr, h->fd, h->R, h->Rf, h->dstats, h->rs, st);
+  if (!converged_qs) status = VOS_ENOCONV;
   launch_step_diag(P, h->eps, h->u, h->R, h->c, h->us[0], h->dstats, h->rs, st);  // S7
   cudaMemcpyAsync(h->hstats, h->dstats, ST_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaGetLastError();
@@ -305,7 +349,9 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
   s.step += 1;
   s.t += dt;
   s.status = status;
-  if (status == VOS_ENOCONV) set_err(h, VOS_ENOCONV, "vos_step: a linear solve reached max_iter");
+  if (status == VOS_ENOCONV)
+    set_err(h, VOS_ENOCONV, converged_qs ? "vos_step: a linear solve reached max_iter"
+                                         : "vos_step: the quasi-static sub-iterations reached flow_subiters");
   return status;
 }
 
@@ -404,6 +450,8 @@ int finish_graph_step(vos_handle* h, Sys<T>* S, double dt) {
   s.iters_c = h->hsolve[4].iters;
   s.outer_c = h->hsolve[4].outer;
   s.res_c = h->hsolve[4].relres;
+  s.qs_iters = 1;
+  s.qs_du = s.qs_dp = s.qs_dc = NAN;
   if (!h->hsolve[3].converged || !h->hsolve[4].converged) status = VOS_ENOCONV;
   s.step += 1;
   s.t += dt;
@@ -482,7 +530,9 @@ int validate(const vos_params* p) {
     return set_err(nullptr, VOS_EINVAL, "unknown precond flags %d", p->precond);
   if ((p->precond & VOS_PRECOND_MOM_DIAG) && (p->precond & VOS_PRECOND_MOM_MG))
     return set_err(nullptr, VOS_EINVAL, "VOS_PRECOND_MOM_DIAG and VOS_PRECOND_MOM_MG exclude each other");
-  if (p->flow_subiters != 1) return set_err(nullptr, VOS_EINVAL, "flow_subiters must be 1");
+  if (p->flow_subiters < 1) return set_err(nullptr, VOS_EINVAL, "flow_subiters must be >= 1");
+  if (!(p->qs_rtol >= 0.0) || !std::isfinite(p->qs_rtol) || !(p->qs_dtau >= 0.0) || !std::isfinite(p->qs_dtau))
+    return set_err(nullptr, VOS_EINVAL, "qs_rtol and qs_dtau must be finite and >= 0");
   const double tol[] = {p->p_rtol, p->u_rtol, p->c_rtol};
   for (double v : tol)
     if (!(v > 0.0) || !(v < 1.0)) return set_err(nullptr, VOS_EINVAL, "tolerances must be in (0, 1)");
@@ -616,6 +666,7 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     h->rs.counter = (unsigned int*)(rsb + kMaxRedValues * kMaxRedBlocks * sizeof(double));
     h->dstats = (double*)(rsb + kMaxRedValues * kMaxRedBlocks * sizeof(double) + 256);
     h->d_dt = h->dstats + ST_COUNT;
+    h->dups = h->d_dt + 1;  // 6 doubles, inside the block's 256-byte tail
   }
   for (int sys = 0; sys < 5; ++sys) {
     if (prm->precision == VOS_FP64) {
@@ -676,7 +727,7 @@ int vos_step(vos_handle* h, double dt) {
   // CUDA-graph replay unless per-kernel timing is on (timing brackets each
   // launch with events, so it uses the eager launch sequence -- the same
   // kernels in the same order).
-  const bool graphs = g_use_graphs && !vos::g_prof_any && !h->net;
+  const bool graphs = g_use_graphs && !vos::g_prof_any && !h->net && h->prm.flow_subiters <= 1;
   h->net_iters = h->net_fallback = 0;
   if (h->prm.precision == VOS_FP64) return graphs ? step_graph<double>(h, h->sd, dt) : step_impl<double>(h, h->sd, dt);
   return graphs ? step_graph<float>(h, h->sf, dt) : step_impl<float>(h, h->sf, dt);
@@ -775,6 +826,38 @@ int vos_get_stats(vos_handle* h, vos_stats* out) {
     s.rmax = h->hstats[ST_RMAX];
   }
   *out = s;
+  return VOS_OK;
+}
+
+int vos_upscaled(vos_handle* h, vos_upscaled_props* out) {
+  if (!h || !out) return set_err(h, VOS_EINVAL, "vos_upscaled: NULL argument");
+  const Phys& P = h->ph;
+  launch_upscaled_sums(P, h->eps, h->c, h->p, h->u[0], h->dups, h->rs, h->st);
+  double v[6];
+  cudaMemcpyAsync(v, h->dups, sizeof(v), cudaMemcpyDeviceToHost, h->st);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_upscaled: %s", cudaGetErrorString(e));
+  const double N = (double)P.nx * P.ny * P.nz;
+  const double A = (P.dim == 2) ? P.dx : P.dx * P.dx;
+  const double V = A * P.dx;
+  vos_upscaled_props r;
+  r.phi = v[0] / N;
+  r.Q_in = v[5] * A;
+  r.A_in = (double)P.ny * P.nz * A;
+  r.U_D = r.Q_in / r.A_in;
+  r.dP = v[4] / ((double)P.ny * P.nz);
+  r.L_D = (P.nx - 0.5) * P.dx;
+  r.K = (r.dP != 0.0) ? P.nu * r.U_D * r.L_D / r.dP : NAN;
+  r.a = v[1] * V / (N * V);
+  const double cs = v[2] * V, cv = v[3] * V;
+  r.alpha = (r.a != 0.0 && cv != 0.0) ? (cs / cv) / r.a : NAN;
+  const double f = (P.dim == 2) ? 12.0 : 8.0;
+  r.L_ref = (r.K == r.K && r.K > 0.0) ? std::sqrt(f * r.K / r.phi) : NAN;
+  r.U_ref = r.U_D / r.phi;
+  r.Pe = (P.D > 0.0) ? r.U_ref * r.L_ref / P.D : NAN;
+  r.Da = (r.U_ref != 0.0) ? P.kc / r.U_ref : NAN;
+  r.Ki = r.Da * r.Pe;
+  *out = r;
   return VOS_OK;
 }
 
@@ -904,6 +987,11 @@ int vos_set_launch_mode(int graphs) {
   return VOS_OK;
 }
 
+int vos_set_coarse_cycle(int on) {
+  vos::g_tail_enabled = on != 0;
+  return VOS_OK;
+}
+
 }  // extern "C"
 
 namespace vos {
@@ -920,7 +1008,7 @@ const double* handle_eps(vos_handle* h) { return h ? h->eps : nullptr; }
 // ---------------------------------------------------------------------------
 namespace vos {
 bool graphs_enabled() { return g_use_graphs && !g_prof_any; }
-bool batch_graphable(const vos_handle* h) { return h->net == nullptr; }
+bool batch_graphable(const vos_handle* h) { return h->net == nullptr && h->prm.flow_subiters <= 1; }
 unsigned batch_generation(const vos_handle* h) { return h->graph_gen; }
 int batch_key(const vos_handle* h, double dt) { return mom_mg_for(h, dt) ? 1 : 0; }
 double* batch_dt_slot(vos_handle* h) { return h->d_dt; }

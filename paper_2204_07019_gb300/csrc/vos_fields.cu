@@ -265,12 +265,16 @@ void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3],
 }
 
 // u^{n+1} = u* - dt eps_f grad phi on interior faces and the outlet face;
-// fixed faces copy u*.
+// fixed faces copy u*.  SUMS: also reduce sum (u^{n+1} - u^{old})^2 and
+// sum (u^{n+1})^2 into sums[0], sums[1] (u^{old} is the value overwritten).
+template <bool SUMS>
 __global__ void k_project(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ phi,
-                          const double* __restrict__ dtp, const double* __restrict__ us, double* __restrict__ u) {
+                          const double* __restrict__ dtp, const double* __restrict__ us, double* __restrict__ u,
+                          double* sums, RedScratch rs) {
   VOS_COUNT_EXEC();
   const double dt = *dtp, idx = 1.0 / P.dx;
   const Seg s = make_seg(fb);
+  double acc[2] = {0.0, 0.0};
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
     seg_decode(s, fb, q, i, j, k);
@@ -288,8 +292,48 @@ __global__ void k_project(Phys P, int a, Box fb, const double* __restrict__ eps,
       const long long cm = cidx(P, i - 1, j, k);
       val -= dt * eps[cm] * (-2.0 * phi[cm]) * idx;
     }
+    if (SUMS) {
+      const double du = val - u[fcx];
+      acc[0] += du * du;
+      acc[1] += val * val;
+    }
     u[fcx] = val;
   }
+  if (SUMS) {
+    if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+      sums[0] = acc[0];
+      sums[1] = acc[1];
+    }
+  }
+}
+
+template <bool DIFF>
+__global__ void k_qs_sums(long long n, const double* __restrict__ x, const double* __restrict__ y,
+                          const double* __restrict__ w, double* out, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  double acc[2] = {0.0, 0.0};
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const double wc = w ? w[c] : 1.0;
+    const double d = DIFF ? x[c] - y[c] : y[c];
+    acc[0] += wc * d * d;
+    acc[1] += wc * x[c] * x[c];
+  }
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    out[0] = acc[0];
+    out[1] = acc[1];
+  }
+}
+
+void launch_qs_sums(long long n, bool diff, const double* x, const double* y, const double* w, double* out,
+                    const RedScratch& rs, cudaStream_t st) {
+  long long g = (n + kThreads - 1) / kThreads;
+  const long long cap = (long long)g_num_sms * 8 < kMaxRedBlocks ? (long long)g_num_sms * 8 : kMaxRedBlocks;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  if (diff)
+    vlaunch("qs_sums", 24.0 * n, k_qs_sums<true>, (int)g, kThreads, st, n, x, y, w, out, rs);
+  else
+    vlaunch("qs_sums", 24.0 * n, k_qs_sums<false>, (int)g, kThreads, st, n, x, y, w, out, rs);
 }
 
 __global__ void k_add(long long n, double* __restrict__ p, const double* __restrict__ phi) {
@@ -303,7 +347,26 @@ void launch_project(const Phys& P, const double* eps, const double* phi, const d
   const int nb = (P.dim == 2) ? 2 : 3;
   for (int a = 0; a < nb; ++a) {
     Box fb{P.nx + (a == 0), P.ny + (a == 1), P.nz + (a == 2)};
-    vlaunch("project", 32.0 * box_cells(fb), k_project, grid_for(fb, 0), kThreads, st, P, a, fb, eps, phi, dtp, us[a], u[a]);
+    vlaunch("project", 32.0 * box_cells(fb), k_project<false>, grid_for(fb, 0), kThreads, st, P, a, fb, eps, phi, dtp,
+            us[a], u[a], (double*)nullptr, RedScratch{nullptr, nullptr});
+  }
+  long long n = (long long)P.nx * P.ny * P.nz;
+  vlaunch("p_update", 24.0 * n, k_add, grid_for(Box{P.nx, P.ny, P.nz}, 0), kThreads, st, n, p, phi);
+}
+
+void launch_project_sums(const Phys& P, const double* eps, const double* phi, const double* __restrict__ dtp,
+                         double* const us[3], double* const u[3], double* p, double* stats, const RedScratch& rs,
+                         cudaStream_t st) {
+  const int nb = (P.dim == 2) ? 2 : 3;
+  for (int a = 0; a < 3; ++a) {
+    if (a >= nb) {
+      launch_set_scalar(stats + ST_QSU + 2 * a, 0.0, st);
+      launch_set_scalar(stats + ST_QSU + 2 * a + 1, 0.0, st);
+      continue;
+    }
+    Box fb{P.nx + (a == 0), P.ny + (a == 1), P.nz + (a == 2)};
+    vlaunch("project", 40.0 * box_cells(fb), k_project<true>, grid_for(fb, 0), kThreads, st, P, a, fb, eps, phi, dtp,
+            us[a], u[a], stats + ST_QSU + 2 * a, rs);
   }
   long long n = (long long)P.nx * P.ny * P.nz;
   vlaunch("p_update", 24.0 * n, k_add, grid_for(Box{P.nx, P.ny, P.nz}, 0), kThreads, st, n, p, phi);
@@ -824,6 +887,45 @@ void launch_step_diag(const Phys& P, const double* eps, double* const u[3], cons
   Box bx{P.nx, P.ny, P.nz};
   vlaunch("step_diag", (2.0 + P.dim) * 8.0 * box_cells(bx), k_step_diag, grid_for(bx, kMaxRedBlocks), kThreads, st,
           P, eps, u[0], u[1], u[2] ? u[2] : u[0], R, c, cf0, stats, rs);
+}
+
+// Sums behind the Darcy-scale properties of Sec. 2.5 (FP64, fixed order):
+// out[0] sum eps, out[1] sum |grad eps| (centred), out[2] sum c |grad eps|,
+// out[3] sum eps c, out[4] sum of p over the first cell column (i = 0),
+// out[5] sum of u over the inlet faces.
+__global__ void k_upscaled_sums(Phys P, const double* __restrict__ eps, const double* __restrict__ c,
+                                const double* __restrict__ p, const double* __restrict__ u0, double* out,
+                                RedScratch rs) {
+  VOS_COUNT_EXEC();
+  const Box bx{P.nx, P.ny, P.nz};
+  const Seg s = make_seg(bx);
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, bx, q, i, j, k);
+    if (i >= bx.mx) continue;
+    const long long c0 = cidx(P, i, j, k);
+    const double e = eps[c0], cc = c[c0];
+    const double g = gradmag(P, eps, i, j, k);
+    acc[0] += e;
+    acc[1] += g;
+    acc[2] += cc * g;
+    acc[3] += e * cc;
+    if (i == 0) {
+      acc[4] += p[c0];
+      acc[5] += u0[fidx(P, 0, 0, j, k)];
+    }
+  }
+  if (grid_sum<6>(acc, rs.partials, rs.counter) && threadIdx.x == 0) {
+    for (int q = 0; q < 6; ++q) out[q] = acc[q];
+  }
+}
+
+void launch_upscaled_sums(const Phys& P, const double* eps, const double* c, const double* p, const double* u0,
+                          double* out, const RedScratch& rs, cudaStream_t st) {
+  Box bx{P.nx, P.ny, P.nz};
+  vlaunch("upscaled_sums", 3.0 * 8.0 * box_cells(bx), k_upscaled_sums, grid_for(bx, kMaxRedBlocks), kThreads, st, P,
+          eps, c, p, u0, out, rs);
 }
 
 void launch_dt_limits(const Phys& P, const double* eps, double* const u[3], const double* R, double* stats,

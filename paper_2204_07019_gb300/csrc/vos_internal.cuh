@@ -363,7 +363,24 @@ struct Hier {
   MGParams mg;
   Defl defl;     // floating-cluster deflation (pressure only)
   vos_unet* net; // learned preconditioner (pressure only; eager solves)
+  int tail;      // first level of the cluster-resident coarse cycle (nlev: none)
 };
+
+// Cluster-resident coarse cycle (vos_mgtail.cu): levels tail..nlev-1 of a
+// V-cycle in one launch of one thread-block cluster, from lev[tail].b to
+// lev[tail].x, bit-identical to the separate launches.  tail_plan picks the
+// first level (nlev: none; g_tail_enabled = false disables it for
+// hierarchies set up afterwards); tail_supported checks that the device can
+// run the cluster with that much shared memory.
+extern bool g_tail_enabled;
+template <typename T>
+int tail_plan(const Hier<T>& h);
+template <typename T>
+size_t tail_smem(const Hier<T>& h, int ls);
+template <typename T, bool SYM>
+bool tail_supported(size_t smem);
+template <typename T, bool SYM>
+void tail_launch(Hier<T>& h, int ls, const KScal* sc, cudaStream_t st);
 
 // Host: label the floating clusters of the pressure operator built from the
 // fluid fraction eps (nx*ny*nz, x fastest).  Faces with 0.5 (eps_a + eps_b)

@@ -1,0 +1,461 @@
+// Cluster-resident coarse part of the multigrid V-cycle.
+//
+// On the coarse levels of a hierarchy (here: every level from the first one
+// with at most kTailMaxCells cells down to the coarsest) each smoothing
+// sweep, residual, restriction and prolongation touches a few thousand to a
+// few tens of thousands of cells: as separate kernel launches they are
+// bound by launch latency and by the latency of their loads, not by
+// bandwidth (about 22 launches per V-cycle on a 256^3 grid).  Here all of
+// them run in ONE launch of one thread-block cluster of kTailCTAs CTAs:
+//   * every tail level's operator (diag, omega/diag, links) and its three
+//     vectors (b, x, t) live in distributed shared memory: CTA r holds the
+//     cells [r * chunk, (r + 1) * chunk) of the level in x-fastest order
+//     (the coarsest level, at most kThreads cells, sits in CTA 0);
+//   * a stencil reads a neighbour held by another CTA of the cluster through
+//     its mapped shared-memory address (DSMEM);
+//   * the phases (first sweep, sweeps, residual, restriction, coarse solve,
+//     prolongation, sweeps) are separated by cluster barriers, which are
+//     hardware barriers: no CTA of the cluster can be missing, since the
+//     cluster is co-scheduled and every thread passes every barrier (the
+//     only early exit, a finished solve, is taken by all threads before the
+//     first barrier).
+// Each cell is updated with the same arithmetic, in the same order, as the
+// separate sweep (k_stencil, k_jac0), restriction (k_restrict_sum),
+// prolongation (k_prolong_add) and coarsest-level (k_coarse_solve) kernels,
+// so the cycle's result is bit-identical to the multi-launch one.
+#include <cooperative_groups.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "vos_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace vos {
+
+static __device__ unsigned long long vos_exec_count = 0;
+unsigned long long exec_count_mgtail() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, vos_exec_count, sizeof(v));
+  return v;
+}
+
+namespace {
+
+constexpr int kTailCTAs = 8;         // CTAs per cluster (the portable maximum)
+constexpr int kTailThreads = 1024;   // threads per CTA
+constexpr int kTailMaxLev = 8;
+constexpr long long kTailMaxCells = 32768;  // largest level in the tail (32^3)
+constexpr int kTailSmemMax = 200 * 1024;    // shared memory per CTA (of 227 KB)
+constexpr int kNoArr = -1;
+enum TArr { TA_DIAG = 0, TA_DINV, TA_XP, TA_YP, TA_ZP, TA_XM, TA_YM, TA_ZM, TA_B, TA_X, TA_T, TA_COUNT };
+
+template <typename T>
+struct TailLev {
+  int mx, my, mz;
+  int n;      // cells
+  int chunk;  // cells per CTA (the coarsest level: n, all in CTA 0)
+  int off[TA_COUNT];  // byte offset of each array in shared memory (kNoArr: absent)
+  const T* g[TA_ZM + 1];  // the level's operator in global memory
+};
+
+template <typename T>
+struct TailArgs {
+  int nlev;  // tail levels, the last one the coarsest (>= 2)
+  int nu, coarse_sweeps;
+  T omega, wc;
+  const T* b0;  // right-hand side of the first tail level (global)
+  T* x0;        // result of the first tail level (global)
+  const KScal* sc;
+  TailLev<T> lev[kTailMaxLev];
+};
+
+// Shared-memory base of every CTA of the cluster (generic addresses), held
+// in shared memory so that a dynamic rank index does not spill to the stack.
+struct Peers {
+  char* const* p;
+};
+
+template <typename T>
+__device__ __forceinline__ T tget(const Peers& P, const TailLev<T>& L, int arr, int c) {
+  const int r = c / L.chunk;
+  const int o = c - r * L.chunk;
+  return reinterpret_cast<const T*>(P.p[r] + L.off[arr])[o];
+}
+template <typename T>
+__device__ __forceinline__ T* tloc(char* smem, const TailLev<T>& L, int arr) {
+  return reinterpret_cast<T*>(smem + L.off[arr]);
+}
+
+// (A v)_c of level L, v the level's vector `va` (same term order as
+// k_stencil; an absent z link adds nothing).
+template <typename T, bool SYM>
+__device__ __forceinline__ T tail_ax(const Peers& P, const TailLev<T>& L, int va, int c, T vc, T d) {
+  const int mx = L.mx, my = L.my, mz = L.mz;
+  const int i = c % mx;
+  const int j = (c / mx) % my;
+  const int k = c / (mx * my);
+  const int sy = mx, sz = mx * my;
+  T ax = d * vc;
+  if (i + 1 < mx) ax += tget(P, L, TA_XP, c) * tget(P, L, va, c + 1);
+  if (i > 0) ax += (SYM ? tget(P, L, TA_XP, c - 1) : tget(P, L, TA_XM, c)) * tget(P, L, va, c - 1);
+  if (j + 1 < my) ax += tget(P, L, TA_YP, c) * tget(P, L, va, c + sy);
+  if (j > 0) ax += (SYM ? tget(P, L, TA_YP, c - sy) : tget(P, L, TA_YM, c)) * tget(P, L, va, c - sy);
+  if (mz > 1) {
+    if (k + 1 < mz) ax += tget(P, L, TA_ZP, c) * tget(P, L, va, c + sz);
+    if (k > 0) ax += (SYM ? tget(P, L, TA_ZP, c - sz) : tget(P, L, TA_ZM, c)) * tget(P, L, va, c - sz);
+  }
+  return ax;
+}
+
+template <typename T>
+__device__ __forceinline__ T jac_weight(T omega, T d, T dinv) {
+  if constexpr (sizeof(T) == 4)
+    return __fdividef(omega, d);  // as k_stencil / k_jac0 in FP32
+  else
+    return dinv;
+}
+
+template <typename T, bool SYM>
+__global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailArgs<T> a) {
+  VOS_COUNT_EXEC();
+  if (a.sc != nullptr && a.sc->done) return;  // uniform: every thread of every CTA leaves here
+  extern __shared__ __align__(16) char smem[];
+  __shared__ char* s_peer[kTailCTAs];
+  __shared__ int pre[kTailMaxLev];  // buffer (TA_X / TA_T) holding level l's pre-smoothed iterate
+  __shared__ int fin[kTailMaxLev];  // buffer holding level l's result
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  if (tid < kTailCTAs) s_peer[tid] = cl.map_shared_rank(smem, tid);
+  const Peers P{s_peer};
+
+  // own cell range of level L in this CTA
+  auto own = [&](const TailLev<T>& L, int& c0, int& c1) {
+    c0 = rank * L.chunk;
+    c1 = min(c0 + L.chunk, L.n);
+  };
+  // load the operators of every tail level and the first level's b
+  for (int l = 0; l < a.nlev; ++l) {
+    const TailLev<T>& L = a.lev[l];
+    int c0, c1;
+    own(L, c0, c1);
+    for (int arr = TA_DIAG; arr <= TA_ZM; ++arr) {
+      if (L.off[arr] == kNoArr) continue;
+      T* dst = tloc(smem, L, arr);
+      const T* src = L.g[arr];
+      for (int c = c0 + tid; c < c1; c += kTailThreads) dst[c - c0] = __ldg(src + c);
+    }
+    if (l == 0) {
+      T* dst = tloc(smem, L, TA_B);
+      for (int c = c0 + tid; c < c1; c += kTailThreads) dst[c - c0] = __ldcg(a.b0 + c);
+    }
+  }
+  cl.sync();
+
+  const int nu = a.nu < 1 ? 1 : a.nu;
+  // ---- down: pre-smoothing, residual, restriction
+  for (int l = 0; l + 1 < a.nlev; ++l) {
+    const TailLev<T>& L = a.lev[l];
+    int c0, c1;
+    own(L, c0, c1);
+    int cur = TA_T, oth = TA_X;
+    {  // first sweep from zero: cur = w b
+      T* o = tloc(smem, L, cur);
+      const T* bl = tloc(smem, L, TA_B);
+      const T* dg = tloc(smem, L, TA_DIAG);
+      const T* dv = tloc(smem, L, TA_DINV);
+      for (int c = c0 + tid; c < c1; c += kTailThreads) o[c - c0] = jac_weight(a.omega, dg[c - c0], dv[c - c0]) * bl[c - c0];
+    }
+    cl.sync();
+    for (int s = 1; s < nu; ++s) {
+      T* o = tloc(smem, L, oth);
+      const T* bl = tloc(smem, L, TA_B);
+      const T* dg = tloc(smem, L, TA_DIAG);
+      const T* dv = tloc(smem, L, TA_DINV);
+      const T* v = tloc(smem, L, cur);
+      for (int c = c0 + tid; c < c1; c += kTailThreads) {
+        const T d = dg[c - c0], vc = v[c - c0];
+        const T ax = tail_ax<T, SYM>(P, L, cur, c, vc, d);
+        o[c - c0] = vc + jac_weight(a.omega, d, dv[c - c0]) * (bl[c - c0] - ax);
+      }
+      cl.sync();
+      const int tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+    if (tid == 0) pre[l] = cur;  // read after later barriers
+    {  // residual into the other buffer
+      T* o = tloc(smem, L, oth);
+      const T* bl = tloc(smem, L, TA_B);
+      const T* dg = tloc(smem, L, TA_DIAG);
+      const T* v = tloc(smem, L, cur);
+      for (int c = c0 + tid; c < c1; c += kTailThreads) {
+        const T ax = tail_ax<T, SYM>(P, L, cur, c, v[c - c0], dg[c - c0]);
+        o[c - c0] = bl[c - c0] - ax;
+      }
+    }
+    cl.sync();
+    {  // restriction: b of the next level = sum of the children's residuals
+      const TailLev<T>& C = a.lev[l + 1];
+      int k0, k1;
+      own(C, k0, k1);
+      T* bc = tloc(smem, C, TA_B);
+      const int ni = L.mx > 1 ? 2 : 1, nj = L.my > 1 ? 2 : 1, nk = L.mz > 1 ? 2 : 1;
+      for (int q = k0 + tid; q < k1; q += kTailThreads) {
+        const int I = q % C.mx, J = (q / C.mx) % C.my, K = q / (C.mx * C.my);
+        T sum = 0;
+        for (int dk = 0; dk < nk; ++dk) {
+          const int k = (L.mz > 1) ? 2 * K + dk : 0;
+          if (k >= L.mz) continue;
+          for (int dj = 0; dj < nj; ++dj) {
+            const int j = (L.my > 1) ? 2 * J + dj : 0;
+            if (j >= L.my) continue;
+            const int row = L.mx * (j + L.my * k);
+            for (int di = 0; di < ni; ++di) {
+              const int i = (L.mx > 1) ? 2 * I + di : 0;
+              if (i < L.mx) sum += tget(P, L, oth, row + i);
+            }
+          }
+        }
+        bc[q - k0] = sum;
+      }
+    }
+    cl.sync();
+  }
+  // ---- coarsest level: damped Jacobi sweeps from zero in CTA 0 (as k_coarse_solve)
+  {
+    const int lc = a.nlev - 1;
+    const TailLev<T>& L = a.lev[lc];
+    const int ns = a.coarse_sweeps;
+    int cur = TA_X;
+    if (rank == 0) {
+      T* bufs[2] = {tloc(smem, L, TA_X), tloc(smem, L, TA_T)};
+      const T* bl = tloc(smem, L, TA_B);
+      const T* dv = tloc(smem, L, TA_DINV);
+      const T* dg = tloc(smem, L, TA_DIAG);
+      const int c = tid;
+      const bool in = c < L.n;
+      const T bc = in ? bl[c] : T(0);
+      const T w = in ? dv[c] : T(0);
+      if (in) bufs[0][c] = w * bc;
+      __syncthreads();
+      int cb = 0;
+      for (int it = 1; it < ns; ++it) {
+        if (in) {
+          const T ax = tail_ax<T, SYM>(P, L, cb == 0 ? TA_X : TA_T, c, bufs[cb][c], dg[c]);
+          bufs[cb ^ 1][c] = bufs[cb][c] + w * (bc - ax);
+        }
+        __syncthreads();
+        cb ^= 1;
+      }
+      cur = cb == 0 ? TA_X : TA_T;
+    }
+    // every CTA needs to know the buffer: the sweep count fixes it
+    cur = ((ns > 1 ? ns - 1 : 0) % 2 == 0) ? TA_X : TA_T;
+    if (tid == 0) fin[lc] = cur;
+  }
+  cl.sync();
+  // ---- up: prolongation and post-smoothing
+  for (int l = a.nlev - 2; l >= 0; --l) {
+    const TailLev<T>& L = a.lev[l];
+    const TailLev<T>& C = a.lev[l + 1];
+    int c0, c1;
+    own(L, c0, c1);
+    int cur = pre[l];
+    int oth = (cur == TA_X) ? TA_T : TA_X;
+    {  // x += wc * e_coarse(parent)
+      T* v = tloc(smem, L, cur);
+      const int ec = fin[l + 1];
+      for (int c = c0 + tid; c < c1; c += kTailThreads) {
+        const int i = c % L.mx, j = (c / L.mx) % L.my, k = c / (L.mx * L.my);
+        const int pc = (i >> 1) + C.mx * ((j >> 1) + C.my * (k >> 1));
+        v[c - c0] += a.wc * tget(P, C, ec, pc);
+      }
+    }
+    cl.sync();
+    for (int s = 0; s < nu; ++s) {
+      T* o = tloc(smem, L, oth);
+      const T* bl = tloc(smem, L, TA_B);
+      const T* dg = tloc(smem, L, TA_DIAG);
+      const T* dv = tloc(smem, L, TA_DINV);
+      const T* v = tloc(smem, L, cur);
+      for (int c = c0 + tid; c < c1; c += kTailThreads) {
+        const T d = dg[c - c0], vc = v[c - c0];
+        const T ax = tail_ax<T, SYM>(P, L, cur, c, vc, d);
+        o[c - c0] = vc + jac_weight(a.omega, d, dv[c - c0]) * (bl[c - c0] - ax);
+      }
+      cl.sync();
+      const int tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+    if (tid == 0) fin[l] = cur;
+    __syncthreads();
+  }
+  {  // the first tail level's result to global memory (own cells; no remote
+     // access follows the last barrier)
+    const TailLev<T>& L = a.lev[0];
+    int c0, c1;
+    own(L, c0, c1);
+    const T* v = tloc(smem, L, fin[0]);
+    for (int c = c0 + tid; c < c1; c += kTailThreads) a.x0[c] = v[c - c0];
+  }
+}
+
+std::mutex g_attr_mu;
+bool g_attr_done[2][2] = {};
+
+template <typename T, bool SYM>
+bool ensure_attr(size_t smem) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  bool& done = g_attr_done[sizeof(T) == 8][SYM];
+  if (!done) {
+    if (cudaFuncSetAttribute(k_mg_tail<T, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemMax) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    done = true;
+  }
+  return smem <= (size_t)kTailSmemMax;
+}
+
+}  // namespace
+
+bool g_tail_enabled = true;
+
+// Shared-memory layout of the tail starting at level ls: per level, its
+// operator arrays and b, x, t, each `chunk` values rounded up to 16 bytes.
+template <typename T>
+static size_t tail_layout(const Hier<T>& h, int ls, TailArgs<T>* a) {
+  size_t off = 0;
+  auto take = [&](int n) {
+    size_t o = off;
+    off += ((size_t)n * sizeof(T) + 15) & ~(size_t)15;
+    return (int)o;
+  };
+  for (int l = ls; l < h.nlev; ++l) {
+    const Op<T>& A = h.lev[l].op;
+    TailLev<T> L;
+    L.mx = A.box.mx;
+    L.my = A.box.my;
+    L.mz = A.box.mz;
+    L.n = (int)box_cells(A.box);
+    L.chunk = (l == h.nlev - 1) ? L.n : (L.n + kTailCTAs - 1) / kTailCTAs;
+    const T* src[TA_ZM + 1] = {A.diag, A.dinv, A.xp, A.yp, A.zp, A.xm, A.ym, A.zm};
+    for (int arr = 0; arr < TA_COUNT; ++arr) L.off[arr] = kNoArr;
+    for (int arr = TA_DIAG; arr <= TA_ZM; ++arr) {
+      L.g[arr] = src[arr];
+      if (src[arr]) L.off[arr] = take(L.chunk);
+    }
+    L.off[TA_B] = take(L.chunk);
+    L.off[TA_X] = take(L.chunk);
+    L.off[TA_T] = take(L.chunk);
+    if (a) a->lev[l - ls] = L;
+  }
+  return off;
+}
+
+// First level of h run by the cluster-resident tail (h.nlev: none).  The
+// tail starts at the largest level l >= 1 with at most kTailMaxCells cells
+// whose levels l..nlev-1 fit the shared memory of the cluster, and it needs
+// at least one level above the coarsest.
+template <typename T>
+int tail_plan(const Hier<T>& h) {
+  if (!g_tail_enabled || h.nlev < 3) return h.nlev;
+  if (box_cells(h.lev[h.nlev - 1].op.box) > kThreads) return h.nlev;
+  for (int l = 1; l + 1 < h.nlev; ++l) {
+    if (h.nlev - l > kTailMaxLev) continue;
+    if (box_cells(h.lev[l].op.box) > kTailMaxCells) continue;
+    if (tail_layout<T>(h, l, nullptr) <= (size_t)kTailSmemMax) return l;
+  }
+  return h.nlev;
+}
+template int tail_plan<double>(const Hier<double>&);
+template int tail_plan<float>(const Hier<float>&);
+
+// One launch: levels ls..nlev-1 of the V-cycle, from lev[ls].b to lev[ls].x.
+template <typename T, bool SYM>
+void tail_launch(Hier<T>& h, int ls, const KScal* sc, cudaStream_t st) {
+  TailArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.nlev = h.nlev - ls;
+  a.nu = h.mg.nu;
+  a.coarse_sweeps = h.mg.coarse_sweeps;
+  a.omega = (T)h.mg.omega;
+  a.wc = (T)h.mg.wc;
+  a.b0 = h.lev[ls].b;
+  a.x0 = h.lev[ls].x;
+  a.sc = sc;
+  const size_t smem = tail_layout<T>(h, ls, &a);
+  ensure_attr<T, SYM>(smem);
+  double words = 0.0;  // operator and b in, x out, per tail level
+  for (int l = ls; l < h.nlev; ++l) {
+    const Op<T>& A = h.lev[l].op;
+    const double nop = 2.0 + (A.box.mz > 1 ? 3.0 : 2.0) * (SYM ? 1.0 : 2.0);
+    words += (nop + (l == ls ? 2.0 : 0.0)) * (double)box_cells(A.box);
+  }
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(kTailCTAs, 1, 1);
+  cfg.blockDim = dim3(kTailThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kTailCTAs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);
+  const char* name = sizeof(T) == 4 ? "mg_tail_f32_Lc" : "mg_tail_f64_Lc";
+  int slot = g_prof_any ? prof_before(name, words * sizeof(T), st) : -1;
+  cudaLaunchKernelEx(&cfg, k_mg_tail<T, SYM>, a);
+  if (slot >= 0) prof_after(slot, st);
+}
+template void tail_launch<float, true>(Hier<float>&, int, const KScal*, cudaStream_t);
+template void tail_launch<float, false>(Hier<float>&, int, const KScal*, cudaStream_t);
+template void tail_launch<double, true>(Hier<double>&, int, const KScal*, cudaStream_t);
+template void tail_launch<double, false>(Hier<double>&, int, const KScal*, cudaStream_t);
+
+// Can a cluster of kTailCTAs CTAs with `smem` bytes each run on this device
+// (checked once per process and size class; false disables the tail).
+template <typename T, bool SYM>
+bool tail_supported(size_t smem) {
+  if (!ensure_attr<T, SYM>(smem)) return false;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(kTailCTAs, 1, 1);
+  cfg.blockDim = dim3(kTailThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kTailCTAs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_mg_tail<T, SYM>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return nclusters > 0;
+}
+template bool tail_supported<float, true>(size_t);
+template bool tail_supported<float, false>(size_t);
+template bool tail_supported<double, true>(size_t);
+template bool tail_supported<double, false>(size_t);
+
+template <typename T>
+size_t tail_smem(const Hier<T>& h, int ls) {
+  return tail_layout<T>(h, ls, nullptr);
+}
+template size_t tail_smem<double>(const Hier<double>&, int);
+template size_t tail_smem<float>(const Hier<float>&, int);
+
+}  // namespace vos

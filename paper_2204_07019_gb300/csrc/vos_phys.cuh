@@ -48,7 +48,10 @@ enum StatIdx {
   ST_QOUT = 9,    // sum over outlet faces of u_f A_f
   ST_FIN = 10,    // reactant inflow: inlet convective + diffusive flux, times A_f
   ST_FOUT = 11,   // reactant outflow: outlet convective flux (c^n), times A_f
-  ST_COUNT = 12
+  ST_QSU = 12,    // quasi-static sub-iterations: per axis a, [12 + 2a] sum (u - u_old)^2, [13 + 2a] sum u^2
+  ST_QSP = 18,    // sum eps phi^2, sum eps p^2 (the pressure change of the sub-iteration)
+  ST_QSC = 20,    // sum (c - c_old)^2, sum c^2
+  ST_COUNT = 22
 };
 
 struct FaceData {  // iVoS per-face data for one axis (face-array layout)
@@ -73,6 +76,16 @@ void launch_pres_assemble(const Phys& P, const double* eps, double* const us[3],
                           double omega, Op<double> A, double* rhs, float* eps32, cudaStream_t st);
 void launch_project(const Phys& P, const double* eps, const double* phi, const double* dtp, double* const us[3],
                     double* const u[3], double* p, cudaStream_t st);
+// The same projection that also reduces, per axis, sum (u^{new} - u^{old})^2
+// and sum (u^{new})^2 into stats[ST_QSU + 2a], stats[ST_QSU + 2a + 1]
+// (quasi-static sub-iterations).
+void launch_project_sums(const Phys& P, const double* eps, const double* phi, const double* dtp,
+                         double* const us[3], double* const u[3], double* p, double* stats, const RedScratch& rs,
+                         cudaStream_t st);
+// out[0] = sum w (x - y)^2 (DIFF) or sum w y^2, out[1] = sum w x^2 over n
+// cells (w NULL: 1).
+void launch_qs_sums(long long n, bool diff, const double* x, const double* y, const double* w, double* out,
+                    const RedScratch& rs, cudaStream_t st);
 // S5/S6
 // cf[a]: receives the convective flux of c^n through every face of axis a
 // (read by the transport assembly); fd: the iVoS face data (ivos only).
@@ -96,6 +109,10 @@ void launch_dt_limits(const Phys& P, const double* eps, double* const u[3], cons
 // End-of-step diagnostics (S7): ST_UMAX, ST_RMAX of u^{n+1}, R^{n+1} and
 // the boundary sums ST_QIN..ST_FOUT.  cf0: convective face fluxes of axis x
 // written by launch_face_data (inlet u c_in, outlet u c^n); c: c^{n+1}.
+// Sums of the Darcy-scale properties (out: 6 device doubles, see
+// k_upscaled_sums).
+void launch_upscaled_sums(const Phys& P, const double* eps, const double* c, const double* p, const double* u0,
+                          double* out, const RedScratch& rs, cudaStream_t st);
 void launch_step_diag(const Phys& P, const double* eps, double* const u[3], const double* R, const double* c,
                       const double* cf0, double* stats, const RedScratch& rs, cudaStream_t st);
 

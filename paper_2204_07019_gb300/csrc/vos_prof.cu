@@ -19,8 +19,10 @@ unsigned long long exec_count_fields();
 unsigned long long exec_count_deflate();
 unsigned long long exec_count_unet();
 unsigned long long exec_count_batch();
+unsigned long long exec_count_mgtail();
 unsigned long long exec_count_sum() {
-  return exec_count_solver() + exec_count_fields() + exec_count_deflate() + exec_count_unet() + exec_count_batch();
+  return exec_count_solver() + exec_count_fields() + exec_count_deflate() + exec_count_unet() + exec_count_batch() +
+         exec_count_mgtail();
 }
 bool g_prof_any = false;
 

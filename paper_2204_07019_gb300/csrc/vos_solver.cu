@@ -1223,6 +1223,7 @@ void hier_carve(Hier<T>& h, Box fine, int sym, char*& cur, const MGParams& mg, b
   h.mg = mg;
   h.defl = Defl{0, nullptr, nullptr, nullptr};
   h.net = nullptr;
+  h.tail = h.nlev;
   Box b = fine;
   for (int l = 0; l < h.nlev; ++l) {
     Level<T>& L = h.lev[l];
@@ -1243,6 +1244,13 @@ void hier_carve(Hier<T>& h, Box fine, int sym, char*& cur, const MGParams& mg, b
       L.x = L.t = L.b = nullptr;
     }
     b = coarse_box(b);
+  }
+  // cluster-resident coarse cycle, if the device runs the cluster it needs
+  const int ts = tail_plan<T>(h);
+  if (ts < h.nlev) {
+    const size_t smem = tail_smem<T>(h, ts);
+    const bool ok = sym ? tail_supported<T, true>(smem) : tail_supported<T, false>(smem);
+    if (ok) h.tail = ts;
   }
 }
 
@@ -1505,8 +1513,12 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     }
     return;
   }
+  // levels h.tail..L-1 run as one cluster launch (vos_mgtail.cu) when the
+  // hierarchy has a tail; the separate launches below cover the levels above
+  const int ts = (h.tail > 0 && h.tail < L) ? h.tail : L;
+  const int Ld = (ts < L) ? ts : L - 1;
   T* pre[16];
-  for (int l = 0; l < L - 1; ++l) {
+  for (int l = 0; l < Ld; ++l) {
     const Op<T>& A = h.lev[l].op;
     const T* b;
     T *x, *t;
@@ -1526,12 +1538,14 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     vlaunch(KN("mg_restrict", l == 0), (ncell(A) + ncell(C)) * sizeof(T), k_restrict_sum<T>, grid_for(C.box, 0),
             kThreads, st, A.box, C.box, (const T*)oth, h.lev[l + 1].b, (const KScal*)sc);
   }
-  {
+  if (ts < L) {
+    tail_launch<T, SYM>(h, ts, sc, st);
+  } else {
     const Op<T>& A = h.lev[L - 1].op;
     vlaunch(KN("mg_coarse", false), (4.0 + n_offs(A)) * ncell(A) * sizeof(T), k_coarse_solve<T, SYM>, 1, kThreads, st,
             A, h.lev[L - 1].b, h.lev[L - 1].x, h.mg.coarse_sweeps, (const KScal*)sc);
   }
-  for (int l = L - 2; l >= 0; --l) {
+  for (int l = Ld - 1; l >= 0; --l) {
     const Op<T>& A = h.lev[l].op;
     const T* b;
     T *x, *t;

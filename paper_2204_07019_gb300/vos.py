@@ -18,8 +18,9 @@ from . import inputs as _inputs
 
 __all__ = [
     "VosError", "load_library", "vos_create", "vos_step", "vos_fields", "vos_set_fields",
-    "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy",
-    "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
+    "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_upscaled", "vos_last_error", "vos_destroy",
+    "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_set_coarse_cycle", "vos_prof_enable",
+    "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
     "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16", "UNet", "vos_set_unet_preconditioner",
     "vos_unet_solve_stats", "vos_pressure_snapshots", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
@@ -37,9 +38,10 @@ PRECOND_MOM_MG = 4
 
 EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
-    "vos_get_stats", "vos_suggest_dt", "vos_last_error", "vos_destroy", "vos_device_bytes",
-    "vos_kernel_launches", "vos_set_launch_mode", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
-    "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle", "vos_batch_destroy",
+    "vos_get_stats", "vos_suggest_dt", "vos_upscaled", "vos_last_error", "vos_destroy", "vos_device_bytes",
+    "vos_kernel_launches", "vos_set_launch_mode", "vos_set_coarse_cycle", "vos_prof_enable", "vos_prof_report",
+    "vos_prof_reset", "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle",
+    "vos_batch_destroy",
     "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16",
     "vos_unet_create", "vos_unet_num_params", "vos_unet_set_params", "vos_unet_get_params", "vos_unet_get_grads",
     "vos_unet_forward", "vos_unet_backward", "vos_unet_train_step", "vos_unet_eval_loss", "vos_unet_destroy",
@@ -63,6 +65,7 @@ class VosParams(ctypes.Structure):
         ("method", ctypes.c_int32), ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
         ("p_rtol", ctypes.c_double), ("u_rtol", ctypes.c_double), ("c_rtol", ctypes.c_double),
         ("max_iter", ctypes.c_int32), ("flow_subiters", ctypes.c_int32), ("wall_mask", ctypes.c_uint32),
+        ("qs_rtol", ctypes.c_double), ("qs_dtau", ctypes.c_double),
     ]
 
 
@@ -77,7 +80,14 @@ class VosStats(ctypes.Structure):
         ("status", ctypes.c_int32),
         ("q_in", ctypes.c_double), ("q_out", ctypes.c_double), ("flux_in", ctypes.c_double),
         ("flux_out", ctypes.c_double), ("umax", ctypes.c_double), ("rmax", ctypes.c_double),
+        ("qs_iters", ctypes.c_int32), ("qs_du", ctypes.c_double), ("qs_dp", ctypes.c_double),
+        ("qs_dc", ctypes.c_double),
     ]
+
+
+class VosUpscaled(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("phi", "Q_in", "A_in", "U_D", "dP", "L_D", "K", "a", "alpha",
+                                                "L_ref", "U_ref", "Pe", "Da", "Ki")]
 
 
 class VosDeviceFields(ctypes.Structure):
@@ -119,6 +129,8 @@ def load_library(path=None):
     lib.vos_device_fields_get.restype = ctypes.c_int
     lib.vos_get_stats.argtypes = [H, ctypes.POINTER(VosStats)]
     lib.vos_get_stats.restype = ctypes.c_int
+    lib.vos_upscaled.argtypes = [H, ctypes.POINTER(VosUpscaled)]
+    lib.vos_upscaled.restype = ctypes.c_int
     lib.vos_suggest_dt.argtypes = [H, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.vos_suggest_dt.restype = ctypes.c_int
     lib.vos_last_error.argtypes = [H]
@@ -131,6 +143,8 @@ def load_library(path=None):
     lib.vos_kernel_launches.restype = ctypes.c_uint64
     lib.vos_set_launch_mode.argtypes = [ctypes.c_int]
     lib.vos_set_launch_mode.restype = ctypes.c_int
+    lib.vos_set_coarse_cycle.argtypes = [ctypes.c_int]
+    lib.vos_set_coarse_cycle.restype = ctypes.c_int
     lib.vos_prof_enable.argtypes = [ctypes.c_char_p]
     lib.vos_prof_enable.restype = ctypes.c_int
     lib.vos_prof_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -345,6 +359,14 @@ def vos_get_stats(h):
         v = getattr(s, n)
         d["lambda" if n == "lambda_" else n] = list(v) if hasattr(v, "__len__") else v
     return d
+
+
+def vos_upscaled(h):
+    """vos_upscaled: Darcy-scale properties (phi, U_D, K, a, alpha, ...) as a dict."""
+    lib = load_library()
+    r = VosUpscaled()
+    _check(lib, h.ptr, lib.vos_upscaled(h.ptr, ctypes.byref(r)))
+    return {n: getattr(r, n) for n, _ in VosUpscaled._fields_}
 
 
 def vos_suggest_dt(h, cfl=0.5, deps_max=0.005):
@@ -631,6 +653,12 @@ def vos_set_launch_mode(graphs):
     """1: replay each step as a CUDA graph with device-side loops (default);
     0: launch the same kernels one by one."""
     load_library().vos_set_launch_mode(1 if graphs else 0)
+
+
+def vos_set_coarse_cycle(on):
+    """1: the coarse multigrid levels of hierarchies set up afterwards run as
+    one cluster launch per V-cycle (default); 0: one launch per operation."""
+    load_library().vos_set_coarse_cycle(1 if on else 0)
 
 
 def vos_prof_enable(filt):

@@ -63,7 +63,7 @@ def test_invalid_parameters_rejected_without_gpu(lib):
     from paper_2204_07019_gb300 import inputs as I, vos
     es = np.zeros((1, 4, 4))
     for bad in (dict(dim=4), dict(nx=1), dict(eps_min=0.0), dict(method=7), dict(p_rtol=2.0),
-                dict(flow_subiters=3)):
+                dict(flow_subiters=0), dict(qs_rtol=-1.0)):
         prm = I.make_params(es.shape, Pe=1, Da=1, L=1, **bad)
         with pytest.raises(vos.VosError) as ei:
             vos.vos_create(es, prm, allocator="cuda")

@@ -514,3 +514,162 @@ def test_vos_psi_rate_on_linear_ramp():
     # the fitted lambda of VoS-psi' replaces the 4, nothing else changes
     lam = O.vos_lambda(eps, prm)
     np.testing.assert_allclose(O.vos_coefficient(eps, prm, lam), kr * lam / 4.0, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- upscaled properties (Sec. 2.5)
+
+def test_upscaled_permeability_poiseuille():
+    """Sec. 2.5: K = nu U_D L_D / dP.  Plane Poiseuille flow between no-slip
+    plates H apart has K = H^2/12; the discrete developed profile
+    y(H - y) + dx^2/4 (no-slip ghost) gives exactly K = H^2/12 + dx^2/6.  The
+    plug inlet adds a fixed entrance loss to dP, so the whole-domain K
+    approaches that value as the channel lengthens (error ~ 1/L) and the
+    difference of the pressure drops of two lengths is the developed
+    gradient exactly.  The reference length sqrt(12 K / phi) of BM2 is then
+    the channel width up to the O(dx^2) term."""
+    for ny in (6, 10):
+        kdev = ny ** 2 / 12.0 + 1.0 / 6.0
+        ups = []
+        for mult in (12, 24):
+            nx = mult * ny
+            es = np.zeros((1, ny, nx))
+            prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=1.0, c_in=0.0, kc=0.0, u_in=0.7)
+            st = _run_to_steady(es, prm, dt=1.0)
+            up = O.upscaled(st, prm)
+            assert up["U_D"] == pytest.approx(0.7, rel=1e-14)
+            assert up["phi"] == 1.0
+            assert up["L_D"] == (nx - 0.5) * prm["dx"]
+            assert up["K"] == pytest.approx(prm["nu"] * up["U_D"] * up["L_D"] / up["dP"], rel=1e-15)
+            ups.append(up)
+        G = (ups[1]["dP"] - ups[0]["dP"]) / (ups[1]["L_D"] - ups[0]["L_D"])
+        assert 1.0 * 0.7 / G == pytest.approx(kdev, rel=1e-9)
+        e1, e2 = kdev - ups[0]["K"], kdev - ups[1]["K"]
+        assert 0 < e2 < 0.6 * e1 and e1 < 0.05 * kdev
+        assert ups[1]["L_ref"] == pytest.approx(np.sqrt(12.0 * ups[1]["K"]), rel=1e-14)
+
+
+def test_upscaled_permeability_darcy():
+    """Uniform eps0 with free-slip sides: Darcy flow, K = k = k0 eps^3/(1-eps)^2
+    (Eq. perm) exactly; in 3D the reference length is sqrt(8 K / phi)."""
+    eps0, k0, nu = 0.6, 0.5, 0.7
+    for shape in ((1, 4, 24), (3, 4, 20)):
+        es = np.full(shape, 1.0 - eps0)
+        prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=nu, c_in=0.0, kc=0.0, k0=k0,
+                            u_in=0.9, wall_mask=0)
+        st = _run_to_steady(es, prm, dt=1.0)
+        up = O.upscaled(st, prm)
+        k = k0 * eps0 ** 3 / (1 - eps0) ** 2
+        assert up["K"] == pytest.approx(k, rel=1e-10)
+        f = 12.0 if shape[0] == 1 else 8.0
+        assert up["L_ref"] == pytest.approx(np.sqrt(f * k / eps0), rel=1e-10)
+        assert up["U_ref"] == pytest.approx(0.9 / eps0, rel=1e-14)
+
+
+def test_upscaled_surface_area_and_alpha():
+    """Sec. 2.5 a = (1/V) int_Gamma dS with |grad eps| as the surface density:
+    across a flat solid layer (any monotone ramp) the centred-gradient sum
+    telescopes to the jump of eps, so a = (1 - eps_min) A_perp / V_Omega per
+    interface.  With a uniform concentration alpha = 1/phi (the surface sees
+    the same c as the fluid volume)."""
+    ny, nx = 10, 30
+    es = np.zeros((1, ny, nx))
+    es[0, :, 12:] = 1.0
+    es[0, :, 11] = 0.37  # partial ramp cell
+    prm = I.make_params(es.shape, Pe=1, Da=1, L=1, dx=0.5)
+    st = O.init_state(es, prm)
+    st["c"][:] = 0.8
+    up = O.upscaled(st, prm)
+    dx = prm["dx"]
+    area = (1.0 - prm["eps_min"]) * ny * dx
+    assert up["a"] == pytest.approx(area / (nx * ny * dx * dx), rel=1e-13)
+    assert up["alpha"] == pytest.approx(1.0 / up["phi"], rel=1e-13)
+    # a concentration vanishing on the surface cells lowers alpha
+    st["c"][0, :, 9:13] = 0.0
+    assert O.upscaled(st, prm)["alpha"] < 1e-12
+
+
+# ---------------------------------------------------------------- quasi-static variant (App. A, App. B)
+
+def test_quasi_static_step_reaches_poiseuille_and_darcy():
+    """App. B: with flow_subiters > 1 one step iterates flow and transport
+    to a steady state with eps frozen.  From rest, a single call reaches the
+    discrete-exact plane-Poiseuille profile (no-slip ghost) and the Darcy
+    plug flow with dp/dx = -nu k^-1 u_in (Eq. perm)."""
+    ny, nx = 6, 84
+    es = np.zeros((1, ny, nx))
+    prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=1.0, c_in=0.0, kc=0.0,
+                        flow_subiters=2000, qs_rtol=1e-14)
+    st, s = O.step(O.init_state(es, prm), 1.0, prm)
+    assert 1 < s["qs_iters"] < 2000 and s["qs_du"] <= 1e-14
+    y = np.arange(ny) + 0.5
+    f = y * (ny - y) + 0.25
+    assert np.max(np.abs(st["u"][0][0, :, nx // 2] - f / f.mean())) < 1e-11
+    eps0, k0, nu, uin = 0.6, 0.5, 0.7, 0.9
+    es = np.full((1, 4, 24), 1.0 - eps0)
+    prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=nu, c_in=0.0, kc=0.0, k0=k0, u_in=uin,
+                        wall_mask=0, flow_subiters=2000, qs_rtol=1e-14)
+    st, s = O.step(O.init_state(es, prm), 1.0, prm)
+    kinv = (1 - eps0) ** 2 / (k0 * eps0 ** 3)
+    assert np.allclose(st["u"][0], uin, rtol=1e-12)
+    assert np.allclose(np.diff(st["p"][0], axis=1), -nu * kinv * uin, rtol=1e-10)
+
+
+def _smooth_porous(method, **over):
+    """A porous field without solid cells (eps in [0.55, 0.95]): no near-null
+    pressure modes, so the quasi-static sub-iterations converge quickly."""
+    ny, nx = 10, 30
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    eps = 0.75 + 0.2 * np.sin(2 * np.pi * x)[None, :] * np.cos(np.pi * y)[:, None]
+    prm = I.make_params((1, ny, nx), Pe=2.0, Da=2.0, L=8, method=method, Vm=0.0, Sc=1.0, k0=0.5)
+    prm.update(over)
+    return (1.0 - eps)[None], prm
+
+
+@pytest.mark.parametrize("method", ["ivos", "psi"])
+def test_quasi_static_fixed_point_solves_steady_transport(method):
+    """App. A, Eq. concentrationDBSQS: at the converged sub-iteration the
+    concentration satisfies div(c u) - div(eps D grad c) + zeta R_f = 0 (the
+    pseudo-time storage terms cancel), checked by assembling the transport
+    operator with an infinite time step; the flow is divergence-free
+    (Eq. contDBSQS)."""
+    es, prm = _smooth_porous(method, flow_subiters=3000, qs_rtol=1e-12, qs_dtau=0.5)
+    st, s = O.step(O.init_state(es, prm), 1.0, prm)
+    assert s["qs_iters"] < 3000 and max(s["qs_du"], s["qs_dp"], s["qs_dc"]) <= 1e-12
+    eps, c, u = st["eps"], st["c"], st["u"]
+    if method == "ivos":
+        A, b = O.transport_system(eps, eps, c, u, prm, 1e300, faces=O.ivos_faces(eps, c, prm))
+    else:
+        kr = O.vos_coefficient(eps, prm, prm["lam"])
+        A, b = O.transport_system(eps, eps, c, u, prm, 1e300, kr=kr)
+    res = A @ c.ravel() - b
+    scale = np.abs(O.advection_divergence(c, u, prm)).max()
+    assert np.abs(res).max() < 1e-9 * scale
+    assert np.abs(O.divergence(u, prm)).max() < 1e-10
+    # the sink is active: the reactant does not just pass through
+    assert s["sum_Rf"] > 1e-3 * s["flux_in"]
+
+
+def test_quasi_static_result_independent_of_pseudo_step():
+    """The converged quasi-static flow and concentration do not depend on
+    the pseudo time step of the sub-iterations (eps frozen: V_m = 0)."""
+    es, prm = _smooth_porous("ivos", flow_subiters=4000, qs_rtol=1e-13)
+    out = []
+    for dtau in (0.5, 2.0):
+        prm["qs_dtau"] = dtau
+        out.append(O.step(O.init_state(es, prm), 1.0, prm)[0])
+    a, b = out
+    for n in ("c", "p", "R"):
+        assert np.linalg.norm(a[n] - b[n]) <= 1e-9 * np.linalg.norm(b[n]), n
+    assert np.linalg.norm(a["u"][0] - b["u"][0]) <= 1e-9 * np.linalg.norm(b["u"][0])
+
+
+def test_quasi_static_single_subiteration_is_the_transient_step():
+    """flow_subiters = 1 is the transient step: identical fields."""
+    es, prm = _small_case("ivos")
+    st = O.init_state(es, prm)
+    a, _ = O.step(st, 0.4, prm)
+    p2 = dict(prm, flow_subiters=1, qs_rtol=1e-3, qs_dtau=0.1)
+    b, _ = O.step(st, 0.4, p2)
+    for n in ("eps", "c", "p", "R", "Rf"):
+        assert np.array_equal(a[n], b[n]), n

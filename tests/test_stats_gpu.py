@@ -141,3 +141,41 @@ def test_max_iter_reports_nonconvergence_and_applies_step(V, graphs):
             V.vos_destroy(h)
     finally:
         V.vos_set_launch_mode(1)
+
+
+@pytest.mark.parametrize("name,method", [("calcite", "ivos"), ("rock", "psi_prime")])
+def test_upscaled_properties_against_oracle(V, name, method):
+    """vos_upscaled equals the oracle's Sec. 2.5 properties evaluated on the
+    GPU's own fields (FP64 sums, 1e-12)."""
+    es, prm, dts = _case(name, method)
+    prm = _tight(prm)
+    h = V.vos_create(es, prm)
+    try:
+        V.vos_set_fields(h, c=_c_start(es, prm))
+        for dt in dts:
+            V.vos_step(h, dt)
+        got = V.vos_upscaled(h)
+        ref = O.upscaled(_gpu_state(V, h, prm), prm)
+        for k, v in ref.items():
+            assert got[k] == pytest.approx(v, rel=1e-12), k
+        assert 0 < got["phi"] < 1 and got["K"] > 0 and got["a"] > 0 and got["alpha"] > 0
+    finally:
+        V.vos_destroy(h)
+
+
+def test_upscaled_darcy_permeability_on_gpu(V):
+    """Uniform eps0, free-slip sides, run to a steady state on the GPU: the
+    measured K is the Kozeny-Carman k of Eq. perm (Sec. 2.5 definition)."""
+    eps0, k0, nu = 0.6, 0.5, 0.7
+    es = np.full((4, 6, 28), 1.0 - eps0)
+    prm = _tight(I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=nu, c_in=0.0, kc=0.0, k0=k0,
+                               u_in=0.9, wall_mask=0))
+    h = V.vos_create(es, prm)
+    try:
+        for _ in range(60):
+            V.vos_step(h, 1.0)
+        up = V.vos_upscaled(h)
+        assert up["K"] == pytest.approx(k0 * eps0 ** 3 / (1 - eps0) ** 2, rel=1e-8)
+        assert up["U_D"] == pytest.approx(0.9, rel=1e-14)
+    finally:
+        V.vos_destroy(h)
