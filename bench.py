@@ -466,9 +466,9 @@ def main():
     ap.add_argument("--dt", type=float, default=None, help="fixed time step of every leg (default per workload)")
     ap.add_argument("--mom-precond", default="auto", choices=["auto", "diag", "mg"],
                     help="momentum preconditioner: the library's rule, or forced")
-    ap.add_argument("--no-coarse-cycle", action="store_true",
-                    help="one launch per multigrid operation on every level instead of the cluster-resident "
-                         "coarse cycle (same results; for comparison)")
+    ap.add_argument("--coarse-cycle", action="store_true",
+                    help="run the coarse multigrid levels as one cluster launch per V-cycle instead of one "
+                         "launch per operation (same results; for comparison)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner leg")
     ap.add_argument("--eager", action="store_true",
@@ -492,8 +492,8 @@ def main():
     V.load_library()
     if args.eager:
         V.vos_set_launch_mode(0)
-    if args.no_coarse_cycle:
-        V.vos_set_coarse_cycle(0)
+    if args.coarse_cycle:
+        V.vos_set_coarse_cycle(1)
     if args.workload == "batch64":
         eps, prms = batch_workload(64)
         N = int(sum(e.size for e in eps))
@@ -564,7 +564,7 @@ def main():
                       "residual": "diagonally scaled, FP64",
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "launch": "eager" if args.eager else "graph", "tiles": r["tiles"],
-                      "coarse_cycle": "separate launches" if args.no_coarse_cycle else "cluster-resident"},
+                      "coarse_cycle": "cluster-resident" if args.coarse_cycle else "separate launches"},
            "roofline": r["roofline"], "gpu_launches": r["launches"],
            "fp64_value": fp64_value, "fp64_ms_per_step": r64["ms"] if r64 else None,
            "mixed_vs_fp64": (value / fp64_value) if fp64_value else None,

@@ -105,6 +105,10 @@ typedef struct vos_params {
   uint32_t wall_mask;
   double qs_rtol;        /* quasi-static stop test (0: always M iterations)  */
   double qs_dtau;        /* pseudo time step of the sub-iterations (0: dt)   */
+  int32_t inertia;       /* 1: keep the inertia term div(u u / eps) of
+                            Eq. momentumDBS, explicit (van Leer upwinded on
+                            the staggered control volumes); 0 (default):
+                            creeping flow, the term is dropped              */
 } vos_params;
 
 /* Statistics of the last completed step (FP64 device reductions; S7).
@@ -443,14 +447,16 @@ uint64_t vos_kernel_launches(void);
  *   launched one by one with host polls of the device scalars.  While
  *   per-kernel timing is on the eager sequence is used. */
 int vos_set_launch_mode(int graphs);
-/* vos_set_coarse_cycle(1) (default): in every multigrid hierarchy set up
- *   afterwards (vos_create, vos_batch_create), the levels from the first one
- *   with at most 32,768 cells down to the coarsest run as ONE launch per
- *   V-cycle of one thread-block cluster of 8 CTAs that keeps those levels in
+/* vos_set_coarse_cycle(1): in every multigrid hierarchy set up afterwards
+ *   (vos_create, vos_batch_create), the levels from the first one with at
+ *   most 32,768 cells down to the coarsest run as ONE launch per V-cycle of
+ *   one thread-block cluster of 8 CTAs that keeps those levels in
  *   distributed shared memory (when the device can run that cluster);
- *   vos_set_coarse_cycle(0): one launch per sweep, residual, restriction and
- *   prolongation on every level.  Both give bit-identical results (the same
- *   arithmetic per cell, in the same order). */
+ *   vos_set_coarse_cycle(0) (default): one launch per sweep, residual,
+ *   restriction and prolongation on every level, replayed from the step's
+ *   CUDA graph, which measured faster on the 256^3 rock.  Both give
+ *   bit-identical results (the same arithmetic per cell, in the same
+ *   order). */
 int vos_set_coarse_cycle(int on);
 int vos_prof_enable(const char* filter);
 int vos_prof_report(char* buf, size_t len);

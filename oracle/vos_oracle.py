@@ -197,11 +197,99 @@ def _face_unknown_range(a, shp):
     return (1, n + 1) if a == 0 else (1, n)
 
 
-def momentum_system(a, eps, p, u_old, dt, prm):
+def face_porosity(eps, a, prm):
+    """eps_f on every face of axis a: mean of the two cells on interior faces,
+    the adjacent cell on boundary faces."""
+    shp = _shape(prm)
+    n = shp[_nax(a)]
+    fs = list(shp)
+    fs[_nax(a)] += 1
+    ef = np.zeros(fs)
+    ef[_sl(a, 1, n)] = face_average(eps, a)
+    ef[_sl(a, 0, 1)] = eps[_sl(a, 0, 1)]
+    ef[_sl(a, n, n + 1)] = eps[_sl(a, n - 1, n)]
+    return ef
+
+
+def _vl_face(phi, b, U):
+    """van Leer value of ``phi`` (an array along axis b with n entries) at the
+    n - 1 interior points between consecutive entries, upwinded along the
+    advecting velocity U (U >= 0: the lower entry is upwind); a far-upwind
+    entry outside the array gives the upwind value (R14)."""
+    cUU, cU, cD, h = _upwind_triplets(phi, b, U >= 0.0)
+    return cU + van_leer_weight(cUU, cU, cD, h) * (cD - cU)
+
+
+def inertia(u, eps, prm):
+    """Explicit inertia term N_a = div(u u_a / eps) of Eq. momentumDBS
+    (multiplied by eps, the form of ``momentum_system``) on the faces of each
+    velocity component a, from the face velocities u (App. B: convection by
+    the second-order van Leer scheme).
+
+    Finite volumes on the staggered control volume (CV) of each a-face: the
+    transported quantity is phi_a = u_a / eps_f (eps_f from
+    ``face_porosity``), carried through the CV faces by the advecting
+    velocity U_b and taken there by van Leer upwinding along b:
+    * b = a: CV faces at cell centres, U = mean of the cell's two a-faces,
+      phi interpolated between those two faces;
+    * b != a: CV faces on the cell edges, U = mean of the two b-faces that
+      meet at the edge (the a-face's two cells; the outlet a-face has one),
+      phi interpolated between the a-faces on either side of the edge.
+    N_a = sum over b of (F_b(plus CV face) - F_b(minus CV face)) / dx.
+    Readings at the domain boundary: walls and free-slip sides carry no
+    normal velocity, so no flux; the inlet plane carries no tangential
+    velocity, so its edges carry no tangential momentum; at the outlet (zero
+    gradient) the outermost edges take the upwind (interior) value, and the
+    outlet face's own CV, which reaches half a cell past the outlet, loses
+    u_n phi_n there.  Returned on every face of axis a (the fixed faces'
+    values are not used)."""
+    shp = _shape(prm)
+    axes = _axes(prm)
+    N = []
+    for a in range(3):
+        if a not in axes:
+            N.append(np.zeros((0,)))
+            continue
+        ua = u[a]
+        fs = ua.shape
+        phi = ua / face_porosity(eps, a, prm)
+        Na = np.zeros(fs)
+        na = shp[_nax(a)]  # cells along a (a-faces 0..na)
+        for b in axes:
+            if b == a:
+                U = 0.5 * (ua[_sl(a, 0, na)] + ua[_sl(a, 1, na + 1)])  # cell centres
+                F = U * _vl_face(phi, a, U)  # between a-faces m and m+1
+                Na[_sl(a, 0, na)] += F       # plus CV face of a-face m
+                Na[_sl(a, 1, na + 1)] -= F   # minus CV face of a-face m+1
+                if a == 0:                   # outlet face: its CV reaches past the outlet
+                    Na[_sl(0, na, na + 1)] += ua[_sl(0, na, na + 1)] * phi[_sl(0, na, na + 1)]
+                continue
+            mb = shp[_nax(b)]  # a-faces along b
+            ub = u[b]
+            # u_b at the edges: b-faces 0..mb along b, averaged over the
+            # a-face's cells along a
+            es = list(fs)
+            es[_nax(b)] += 1
+            Ue = np.zeros(es)
+            Ue[_sl(a, 1, na)] = 0.5 * (ub[_sl(a, 0, na - 1)] + ub[_sl(a, 1, na)])
+            if a == 0:
+                Ue[_sl(0, na, na + 1)] = ub[_sl(0, na - 1, na)]
+            Ui = Ue[_sl(b, 1, mb)]                # interior edges
+            F = Ui * _vl_face(phi, b, Ui)         # between a-faces j and j+1 along b
+            Na[_sl(b, 0, mb - 1)] += F
+            Na[_sl(b, 1, mb)] -= F
+            if b == 0:  # outlet-plane edges: zero gradient (upwind interior value)
+                Na[_sl(0, mb - 1, mb)] += Ue[_sl(0, mb, mb + 1)] * phi[_sl(0, mb - 1, mb)]
+        N.append(Na / prm["dx"])
+    return N
+
+
+def momentum_system(a, eps, p, u_old, dt, prm, u_all=None):
     """Linear system for the face velocity component a (Eq. momentumDBS, Sec. 2.2).
 
-    Multiplying Eq. momentumDBS by eps and dropping the inertia term
-    (reading: creeping flow, Re = Pe/Sc <= 0.1) gives, per face f,
+    Multiplying Eq. momentumDBS by eps and, by default (inertia = 0),
+    dropping the inertia term (reading: creeping flow, Re = Pe/Sc <= 0.1)
+    gives, per face f,
 
       (1/dt + nu eps_f k^-1_f) u_f - nu lap(u)_f = u^n_f/dt - eps_f (grad p^n)_f
 
@@ -211,6 +299,10 @@ def momentum_system(a, eps, p, u_old, dt, prm):
     outlet and free-slip sides: ghost = +u; fixed boundary faces (inlet u_in,
     zero normal velocity on walls) enter as known values.  Outlet pressure
     p = 0 on the boundary face (ghost p = -p_P).
+    With prm["inertia"] set, the explicit inertia term of the old velocity
+    field u_all (``inertia``) moves to the right-hand side:
+    ... = u^n_f/dt - eps_f (grad p^n)_f - div(u^n u^n_a / eps)_f
+    (Eq. momentumDBS multiplied by eps; reading: explicit in time).
     Returns (A, b, idx) with idx the flat face indices of the unknowns.
     """
     shp = _shape(prm)
@@ -245,6 +337,8 @@ def momentum_system(a, eps, p, u_old, dt, prm):
 
     diag = 1.0 / dt + nu * eps_f * kin_f
     rhs = u_old / dt - eps_f * gp
+    if u_all is not None and int(prm.get("inertia", 0)):
+        rhs = rhs - inertia(u_all, eps, prm)[a]
     rows, cols, vals = [], [], []
     coef = nu / dx ** 2
     wall = int(prm["wall_mask"])
@@ -591,7 +685,7 @@ def step(state, dt, prm, solver="direct", rtol=1e-13):
         # S2
         ustar = [x.copy() for x in u_it]
         for a in axes:
-            A, b, unk = momentum_system(a, eps, p_it, u_it[a], dtau, prm)
+            A, b, unk = momentum_system(a, eps, p_it, u_it[a], dtau, prm, u_all=u_it)
             ustar[a][unk] = _solve(A, b, True, solver, rtol)
         # S3
         A, b = pressure_system(eps, ustar, R_it, dtau, prm)

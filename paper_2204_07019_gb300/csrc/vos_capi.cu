@@ -273,7 +273,7 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     for (int a = 0; a < nd; ++a) {
       cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st);
       if (box_cells(S[a].box) == 0) continue;
-      launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
+      launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, h->u, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
       SolveResult r = solve<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
                                h->work, h->rs, st, mom_mg);
       s.iters_u[a] += r.iters;
@@ -367,7 +367,7 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
   for (int a = 0; a < nd; ++a) {
     VOS_CUDA_TRY(cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (box_cells(S[a].box) == 0) continue;
-    launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
+    launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, h->u, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
     VOS_CUDA_TRY(solve_capture<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
                                   h->work, h->rs, st, mom_mg, h->dsolve + a, h->gs1, h->gs2));
   }
@@ -531,6 +531,7 @@ int validate(const vos_params* p) {
   if ((p->precond & VOS_PRECOND_MOM_DIAG) && (p->precond & VOS_PRECOND_MOM_MG))
     return set_err(nullptr, VOS_EINVAL, "VOS_PRECOND_MOM_DIAG and VOS_PRECOND_MOM_MG exclude each other");
   if (p->flow_subiters < 1) return set_err(nullptr, VOS_EINVAL, "flow_subiters must be >= 1");
+  if (p->inertia != 0 && p->inertia != 1) return set_err(nullptr, VOS_EINVAL, "inertia must be 0 or 1");
   if (!(p->qs_rtol >= 0.0) || !std::isfinite(p->qs_rtol) || !(p->qs_dtau >= 0.0) || !std::isfinite(p->qs_dtau))
     return set_err(nullptr, VOS_EINVAL, "qs_rtol and qs_dtau must be finite and >= 0");
   const double tol[] = {p->p_rtol, p->u_rtol, p->c_rtol};
@@ -576,6 +577,7 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
   P.u_in = prm->u_in;
   P.eps_min = prm->eps_min;
   P.wall_mask = prm->wall_mask;
+  P.inertia = prm->inertia != 0;
   h->st = (cudaStream_t)stream;
   h->user_alloc = (alloc != nullptr);
   if (alloc) h->alloc = *alloc;

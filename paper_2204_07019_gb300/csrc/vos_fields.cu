@@ -127,7 +127,117 @@ void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double
 }
 
 // ---------------------------------------------------------------------------
-// S2: momentum predictor for component a (Eq. momentumDBS x eps, no inertia)
+// Inertia term of Eq. momentumDBS (multiplied by eps): N_a = div(u u_a / eps)
+// on the staggered control volume (CV) of an a-face, finite volumes with the
+// transported quantity phi = u_a / eps_f (eps_f: mean of the two cells of an
+// interior face, the adjacent cell of a boundary face) taken by van Leer
+// upwinding (App. B) at each CV face and carried by the advecting velocity:
+//   b = a: CV faces at cell centres, U = mean of the cell's two a-faces;
+//   b != a: CV faces on cell edges, U = mean of the two b-faces meeting
+//           there (one for the outlet a-face).
+// Domain boundary: no flux through walls / free-slip sides (no normal
+// velocity) nor through the inlet plane's edges (no tangential velocity);
+// outlet-plane edges take the upwind interior value; the outlet face's CV
+// loses u_n phi_n past the outlet.  Explicit in time (u at t^n).
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ double face_eps(const Phys& P, const double* eps, int a, const int g[3]) {
+  const int m = g[a], n = ncell(P, a);
+  int lo[3] = {g[0], g[1], g[2]};
+  lo[a] -= 1;
+  if (m == 0) return eps[cidx(P, g[0], g[1], g[2])];
+  if (m == n) return eps[cidx(P, lo[0], lo[1], lo[2])];
+  return 0.5 * (eps[cidx(P, lo[0], lo[1], lo[2])] + eps[cidx(P, g[0], g[1], g[2])]);
+}
+__device__ __forceinline__ double phi_face(const Phys& P, const double* eps, const double* ua, int a, const int g[3]) {
+  return fdiv_nr(ua[fidx(P, a, g[0], g[1], g[2])], face_eps(P, eps, a, g));
+}
+// van Leer value of phi between a-faces q and q+1 along d (nq a-faces along
+// d; the other coordinates from f), upwind of U
+__device__ double phi_between(const Phys& P, const double* eps, const double* ua, int a, const int f[3], int d, int q,
+                              int nq, double U) {
+  int g[3] = {f[0], f[1], f[2]};
+  int qu, qd, quu;
+  bool has;
+  if (U >= 0.0) {
+    qu = q;
+    qd = q + 1;
+    quu = q - 1;
+    has = quu >= 0;
+  } else {
+    qu = q + 1;
+    qd = q;
+    quu = q + 2;
+    has = quu < nq;
+  }
+  g[d] = qu;
+  const double cU = phi_face(P, eps, ua, a, g);
+  g[d] = qd;
+  const double cD = phi_face(P, eps, ua, a, g);
+  double cUU = cU;
+  if (has) {
+    g[d] = quu;
+    cUU = phi_face(P, eps, ua, a, g);
+  }
+  return cU + vl_corr(cUU, cU, cD, has);
+}
+__device__ double inertia_term(const Phys& P, const double* eps, const double* const us[3], int a, const int f[3]) {
+  const double* ua = us[a];
+  const int m = f[a], na = ncell(P, a);
+  const int nb = (P.dim == 2) ? 2 : 3;
+  double N = 0.0;
+  {  // b = a
+    int g[3] = {f[0], f[1], f[2]};
+    double Fp;
+    const double uf = ua[fidx(P, a, f[0], f[1], f[2])];
+    if (m < na) {
+      g[a] = m + 1;
+      const double U = 0.5 * (uf + ua[fidx(P, a, g[0], g[1], g[2])]);
+      Fp = U * phi_between(P, eps, ua, a, f, a, m, na + 1, U);
+    } else {  // outlet face
+      Fp = uf * phi_face(P, eps, ua, a, f);
+    }
+    g[a] = m - 1;
+    const double U = 0.5 * (ua[fidx(P, a, g[0], g[1], g[2])] + uf);
+    const double Fm = U * phi_between(P, eps, ua, a, f, a, m - 1, na + 1, U);
+    N += Fp - Fm;
+  }
+  for (int b = 0; b < nb; ++b) {
+    if (b == a) continue;
+    const double* ub = us[b];
+    const int nbc = ncell(P, b), jb = f[b];
+    // advecting velocity at the edge on b-face eb: u_b over the a-face's cells
+    auto Uedge = [&](int eb) {
+      int g[3] = {f[0], f[1], f[2]};
+      g[b] = eb;
+      g[a] = m - 1;
+      double s = ub[fidx(P, b, g[0], g[1], g[2])];
+      if (m < na) {
+        g[a] = m;
+        s = 0.5 * (s + ub[fidx(P, b, g[0], g[1], g[2])]);
+      }
+      return s;
+    };
+    double Fp = 0.0, Fm = 0.0;
+    if (jb + 1 < nbc) {
+      const double U = Uedge(jb + 1);
+      Fp = U * phi_between(P, eps, ua, a, f, b, jb, nbc, U);
+    } else if (b == 0) {  // outlet-plane edge: upwind interior value
+      Fp = Uedge(nbc) * phi_face(P, eps, ua, a, f);
+    }
+    if (jb >= 1) {
+      const double U = Uedge(jb);
+      Fm = U * phi_between(P, eps, ua, a, f, b, jb - 1, nbc, U);
+    }
+    N += Fp - Fm;
+  }
+  return N / P.dx;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// S2: momentum predictor for component a (Eq. momentumDBS x eps; the inertia
+// term explicit when P.inertia is set, else dropped)
 //   (1/dt + nu eps_f k^-1_f) u_f - nu lap(u)_f = u^n_f/dt - eps_f (grad p^n)_f
 // Unknown box: the faces of a except the fixed ones (inlet face for x,
 // boundary faces for y/z); unknown (i,j,k) is face (i,j,k) + e_a, whose
@@ -135,7 +245,9 @@ void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double
 // ---------------------------------------------------------------------------
 __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__ eps, const double* __restrict__ kic,
                                const double* __restrict__ p, const double* __restrict__ uold,
-                               const double* __restrict__ dtp, double omega, Op<double> A, double* __restrict__ rhs) {
+                               const double* __restrict__ dtp, const double* __restrict__ u0,
+                               const double* __restrict__ u1, const double* __restrict__ u2, double omega,
+                               Op<double> A, double* __restrict__ rhs) {
   VOS_COUNT_EXEC();
   const double idt = 1.0 / *dtp, idx = 1.0 / P.dx;
   const Seg s = make_seg(ub);
@@ -166,6 +278,10 @@ __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__
     }
     double diag = idt + P.nu * ef * kf;
     double b = uold[fidx(P, a, f[0], f[1], f[2])] * idt - ef * gp;
+    if (P.inertia) {
+      const double* us3[3] = {u0, u1, u2};
+      b -= inertia_term(P, eps, us3, a, f);
+    }
     double off[3] = {0.0, 0.0, 0.0};
     const int nb = (P.dim == 2) ? 2 : 3;
     const int um[3] = {ub.mx, ub.my, ub.mz};
@@ -204,10 +320,13 @@ __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__
   }
 }
 
-void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* kic, const double* p, const double* uold, const double* __restrict__ dtp,
-                         double omega, Op<double> A, double* rhs, cudaStream_t st) {
+void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* kic, const double* p, const double* uold,
+                         const double* __restrict__ dtp, double* const u[3], double omega, Op<double> A, double* rhs,
+                         cudaStream_t st) {
   if (box_cells(A.box) == 0) return;
-  vlaunch("mom_assemble", (6.0 + P.dim) * 8.0 * box_cells(A.box), k_mom_assemble, grid_for(A.box, 0), kThreads, st, P, a, A.box, eps, kic, p, uold, dtp, omega, A, rhs);
+  vlaunch("mom_assemble", (6.0 + P.dim + (P.inertia ? P.dim : 0)) * 8.0 * box_cells(A.box), k_mom_assemble,
+          grid_for(A.box, 0), kThreads, st, P, a, A.box, eps, kic, p, uold, dtp, (const double*)u[0],
+          (const double*)(u[1] ? u[1] : u[0]), (const double*)(u[2] ? u[2] : u[0]), omega, A, rhs);
 }
 
 // ---------------------------------------------------------------------------

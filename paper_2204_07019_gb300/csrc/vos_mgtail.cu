@@ -72,43 +72,23 @@ struct TailArgs {
   TailLev<T> lev[kTailMaxLev];
 };
 
-// Shared-memory base of every CTA of the cluster (generic addresses), held
-// in shared memory so that a dynamic rank index does not spill to the stack.
-struct Peers {
-  char* const* p;
-};
-
+// Access to one tail level's arrays in the cluster: a cell this CTA holds is
+// read from its own shared memory (a compare and a shared load); any other
+// cell from the holding CTA's shared memory through its mapped address.
 template <typename T>
-__device__ __forceinline__ T tget(const Peers& P, const TailLev<T>& L, int arr, int c) {
-  const int r = c / L.chunk;
-  const int o = c - r * L.chunk;
-  return reinterpret_cast<const T*>(P.p[r] + L.off[arr])[o];
-}
-template <typename T>
-__device__ __forceinline__ T* tloc(char* smem, const TailLev<T>& L, int arr) {
-  return reinterpret_cast<T*>(smem + L.off[arr]);
-}
-
-// (A v)_c of level L, v the level's vector `va` (same term order as
-// k_stencil; an absent z link adds nothing).
-template <typename T, bool SYM>
-__device__ __forceinline__ T tail_ax(const Peers& P, const TailLev<T>& L, int va, int c, T vc, T d) {
-  const int mx = L.mx, my = L.my, mz = L.mz;
-  const int i = c % mx;
-  const int j = (c / mx) % my;
-  const int k = c / (mx * my);
-  const int sy = mx, sz = mx * my;
-  T ax = d * vc;
-  if (i + 1 < mx) ax += tget(P, L, TA_XP, c) * tget(P, L, va, c + 1);
-  if (i > 0) ax += (SYM ? tget(P, L, TA_XP, c - 1) : tget(P, L, TA_XM, c)) * tget(P, L, va, c - 1);
-  if (j + 1 < my) ax += tget(P, L, TA_YP, c) * tget(P, L, va, c + sy);
-  if (j > 0) ax += (SYM ? tget(P, L, TA_YP, c - sy) : tget(P, L, TA_YM, c)) * tget(P, L, va, c - sy);
-  if (mz > 1) {
-    if (k + 1 < mz) ax += tget(P, L, TA_ZP, c) * tget(P, L, va, c + sz);
-    if (k > 0) ax += (SYM ? tget(P, L, TA_ZP, c - sz) : tget(P, L, TA_ZM, c)) * tget(P, L, va, c - sz);
+struct Acc {
+  const TailLev<T>* L;
+  char* smem;
+  char* const* peer;  // shared-memory base of every CTA (generic addresses)
+  int c0;             // first cell held by this CTA
+  __device__ __forceinline__ T get(int arr, int c) const {
+    const unsigned o = (unsigned)(c - c0);
+    if (o < (unsigned)L->chunk) return reinterpret_cast<const T*>(smem + L->off[arr])[o];
+    const int r = c / L->chunk;
+    return reinterpret_cast<const T*>(peer[r] + L->off[arr])[c - r * L->chunk];
   }
-  return ax;
-}
+  __device__ __forceinline__ T* loc(int arr) const { return reinterpret_cast<T*>(smem + L->off[arr]); }
+};
 
 template <typename T>
 __device__ __forceinline__ T jac_weight(T omega, T d, T dinv) {
@@ -116,6 +96,32 @@ __device__ __forceinline__ T jac_weight(T omega, T d, T dinv) {
     return __fdividef(omega, d);  // as k_stencil / k_jac0 in FP32
   else
     return dinv;
+}
+
+// (A v)_c at cell c = (i, j, k) of the level, v given by vf(c, i, j, k)
+// (same term order as k_stencil; an absent z link adds nothing).
+template <typename T, bool SYM, class VF>
+__device__ __forceinline__ T tail_ax(const Acc<T>& A, int c, int i, int j, int k, T vc, T d, VF vf) {
+  const TailLev<T>& L = *A.L;
+  const int sy = L.mx, sz = L.mx * L.my;
+  T ax = d * vc;
+  if (i + 1 < L.mx) ax += A.get(TA_XP, c) * vf(c + 1, i + 1, j, k);
+  if (i > 0) ax += (SYM ? A.get(TA_XP, c - 1) : A.get(TA_XM, c)) * vf(c - 1, i - 1, j, k);
+  if (j + 1 < L.my) ax += A.get(TA_YP, c) * vf(c + sy, i, j + 1, k);
+  if (j > 0) ax += (SYM ? A.get(TA_YP, c - sy) : A.get(TA_YM, c)) * vf(c - sy, i, j - 1, k);
+  if (L.mz > 1) {
+    if (k + 1 < L.mz) ax += A.get(TA_ZP, c) * vf(c + sz, i, j, k + 1);
+    if (k > 0) ax += (SYM ? A.get(TA_ZP, c - sz) : A.get(TA_ZM, c)) * vf(c - sz, i, j, k - 1);
+  }
+  return ax;
+}
+
+template <typename T>
+__device__ __forceinline__ void cell_ijk(const TailLev<T>& L, int c, int& i, int& j, int& k) {
+  const int q = c / L.mx;
+  i = c - q * L.mx;
+  k = q / L.my;
+  j = q - k * L.my;
 }
 
 template <typename T, bool SYM>
@@ -130,82 +136,95 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailArgs<T> a) {
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x;
   if (tid < kTailCTAs) s_peer[tid] = cl.map_shared_rank(smem, tid);
-  const Peers P{s_peer};
-
-  // own cell range of level L in this CTA
-  auto own = [&](const TailLev<T>& L, int& c0, int& c1) {
-    c0 = rank * L.chunk;
-    c1 = min(c0 + L.chunk, L.n);
+  auto acc = [&](int l) {
+    const TailLev<T>& L = a.lev[l];
+    return Acc<T>{&L, smem, s_peer, rank * L.chunk};
   };
+  auto own_end = [&](const TailLev<T>& L) { return min(rank * L.chunk + L.chunk, L.n); };
+
   // load the operators of every tail level and the first level's b
   for (int l = 0; l < a.nlev; ++l) {
     const TailLev<T>& L = a.lev[l];
-    int c0, c1;
-    own(L, c0, c1);
+    const int c0 = rank * L.chunk, c1 = own_end(L);
     for (int arr = TA_DIAG; arr <= TA_ZM; ++arr) {
       if (L.off[arr] == kNoArr) continue;
-      T* dst = tloc(smem, L, arr);
+      T* dst = reinterpret_cast<T*>(smem + L.off[arr]);
       const T* src = L.g[arr];
       for (int c = c0 + tid; c < c1; c += kTailThreads) dst[c - c0] = __ldg(src + c);
     }
     if (l == 0) {
-      T* dst = tloc(smem, L, TA_B);
+      T* dst = reinterpret_cast<T*>(smem + L.off[TA_B]);
       for (int c = c0 + tid; c < c1; c += kTailThreads) dst[c - c0] = __ldcg(a.b0 + c);
     }
   }
   cl.sync();
 
   const int nu = a.nu < 1 ? 1 : a.nu;
-  // ---- down: pre-smoothing, residual, restriction
-  for (int l = 0; l + 1 < a.nlev; ++l) {
+  const T om = a.omega, wc = a.wc;
+  // one damped Jacobi sweep of level l from buffer `cur` into buffer `out`
+  auto sweep = [&](int l, int cur, int out) {
+    const Acc<T> A = acc(l);
     const TailLev<T>& L = a.lev[l];
-    int c0, c1;
-    own(L, c0, c1);
-    int cur = TA_T, oth = TA_X;
-    {  // first sweep from zero: cur = w b
-      T* o = tloc(smem, L, cur);
-      const T* bl = tloc(smem, L, TA_B);
-      const T* dg = tloc(smem, L, TA_DIAG);
-      const T* dv = tloc(smem, L, TA_DINV);
-      for (int c = c0 + tid; c < c1; c += kTailThreads) o[c - c0] = jac_weight(a.omega, dg[c - c0], dv[c - c0]) * bl[c - c0];
+    const int c0 = A.c0, c1 = own_end(L);
+    T* o = A.loc(out);
+    const T *bl = A.loc(TA_B), *dg = A.loc(TA_DIAG), *dv = A.loc(TA_DINV), *v = A.loc(cur);
+    auto vf = [&](int c, int, int, int) { return A.get(cur, c); };
+    for (int c = c0 + tid; c < c1; c += kTailThreads) {
+      int i, j, k;
+      cell_ijk(L, c, i, j, k);
+      const T d = dg[c - c0], vc = v[c - c0];
+      const T ax = tail_ax<T, SYM>(A, c, i, j, k, vc, d, vf);
+      o[c - c0] = vc + jac_weight(om, d, dv[c - c0]) * (bl[c - c0] - ax);
     }
-    cl.sync();
-    for (int s = 1; s < nu; ++s) {
-      T* o = tloc(smem, L, oth);
-      const T* bl = tloc(smem, L, TA_B);
-      const T* dg = tloc(smem, L, TA_DIAG);
-      const T* dv = tloc(smem, L, TA_DINV);
-      const T* v = tloc(smem, L, cur);
+  };
+  // ---- down: pre-smoothing, residual and restriction
+  for (int l = 0; l + 1 < a.nlev; ++l) {
+    const Acc<T> A = acc(l);
+    const TailLev<T>& L = a.lev[l];
+    const int c0 = A.c0, c1 = own_end(L);
+    const T *bl = A.loc(TA_B), *dg = A.loc(TA_DIAG), *dv = A.loc(TA_DINV);
+    int cur;
+    if (nu >= 2) {
+      // the first two sweeps in one phase: the first (from zero, x = w b)
+      // is evaluated wherever the second reads it
+      T* o = A.loc(TA_X);
+      auto x0 = [&](int c, int, int, int) {
+        return jac_weight(om, A.get(TA_DIAG, c), A.get(TA_DINV, c)) * A.get(TA_B, c);
+      };
       for (int c = c0 + tid; c < c1; c += kTailThreads) {
-        const T d = dg[c - c0], vc = v[c - c0];
-        const T ax = tail_ax<T, SYM>(P, L, cur, c, vc, d);
-        o[c - c0] = vc + jac_weight(a.omega, d, dv[c - c0]) * (bl[c - c0] - ax);
+        int i, j, k;
+        cell_ijk(L, c, i, j, k);
+        const T d = dg[c - c0];
+        const T w = jac_weight(om, d, dv[c - c0]);
+        const T vc = w * bl[c - c0];
+        const T ax = tail_ax<T, SYM>(A, c, i, j, k, vc, d, x0);
+        o[c - c0] = vc + w * (bl[c - c0] - ax);
       }
+      cur = TA_X;
       cl.sync();
-      const int tmp = cur;
-      cur = oth;
-      oth = tmp;
+      for (int s = 2; s < nu; ++s) {
+        const int out = (cur == TA_X) ? TA_T : TA_X;
+        sweep(l, cur, out);
+        cl.sync();
+        cur = out;
+      }
+    } else {
+      T* o = A.loc(TA_T);
+      for (int c = c0 + tid; c < c1; c += kTailThreads) o[c - c0] = jac_weight(om, dg[c - c0], dv[c - c0]) * bl[c - c0];
+      cur = TA_T;
+      cl.sync();
     }
     if (tid == 0) pre[l] = cur;  // read after later barriers
-    {  // residual into the other buffer
-      T* o = tloc(smem, L, oth);
-      const T* bl = tloc(smem, L, TA_B);
-      const T* dg = tloc(smem, L, TA_DIAG);
-      const T* v = tloc(smem, L, cur);
-      for (int c = c0 + tid; c < c1; c += kTailThreads) {
-        const T ax = tail_ax<T, SYM>(P, L, cur, c, v[c - c0], dg[c - c0]);
-        o[c - c0] = bl[c - c0] - ax;
-      }
-    }
-    cl.sync();
-    {  // restriction: b of the next level = sum of the children's residuals
+    {  // residual b - A x of the children, summed into the next level's b
       const TailLev<T>& C = a.lev[l + 1];
-      int k0, k1;
-      own(C, k0, k1);
-      T* bc = tloc(smem, C, TA_B);
+      const Acc<T> AC = acc(l + 1);
+      const int k0 = AC.c0, k1 = own_end(C);
+      T* bc = AC.loc(TA_B);
+      auto xv = [&](int c, int, int, int) { return A.get(cur, c); };
       const int ni = L.mx > 1 ? 2 : 1, nj = L.my > 1 ? 2 : 1, nk = L.mz > 1 ? 2 : 1;
       for (int q = k0 + tid; q < k1; q += kTailThreads) {
-        const int I = q % C.mx, J = (q / C.mx) % C.my, K = q / (C.mx * C.my);
+        int I, J, K;
+        cell_ijk(C, q, I, J, K);
         T sum = 0;
         for (int dk = 0; dk < nk; ++dk) {
           const int k = (L.mz > 1) ? 2 * K + dk : 0;
@@ -216,7 +235,10 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailArgs<T> a) {
             const int row = L.mx * (j + L.my * k);
             for (int di = 0; di < ni; ++di) {
               const int i = (L.mx > 1) ? 2 * I + di : 0;
-              if (i < L.mx) sum += tget(P, L, oth, row + i);
+              if (i >= L.mx) continue;
+              const int c = row + i;
+              const T ax = tail_ax<T, SYM>(A, c, i, j, k, A.get(cur, c), A.get(TA_DIAG, c), xv);
+              sum += A.get(TA_B, c) - ax;
             }
           }
         }
@@ -229,82 +251,84 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailArgs<T> a) {
   {
     const int lc = a.nlev - 1;
     const TailLev<T>& L = a.lev[lc];
+    const Acc<T> A = acc(lc);
     const int ns = a.coarse_sweeps;
-    int cur = TA_X;
     if (rank == 0) {
-      T* bufs[2] = {tloc(smem, L, TA_X), tloc(smem, L, TA_T)};
-      const T* bl = tloc(smem, L, TA_B);
-      const T* dv = tloc(smem, L, TA_DINV);
-      const T* dg = tloc(smem, L, TA_DIAG);
+      T* bufs[2] = {A.loc(TA_X), A.loc(TA_T)};
       const int c = tid;
       const bool in = c < L.n;
-      const T bc = in ? bl[c] : T(0);
-      const T w = in ? dv[c] : T(0);
+      int i = 0, j = 0, k = 0;
+      if (in) cell_ijk(L, c, i, j, k);
+      const T bc = in ? A.loc(TA_B)[c] : T(0);
+      const T w = in ? A.loc(TA_DINV)[c] : T(0);
+      const T dd = in ? A.loc(TA_DIAG)[c] : T(0);
       if (in) bufs[0][c] = w * bc;
       __syncthreads();
       int cb = 0;
       for (int it = 1; it < ns; ++it) {
         if (in) {
-          const T ax = tail_ax<T, SYM>(P, L, cb == 0 ? TA_X : TA_T, c, bufs[cb][c], dg[c]);
-          bufs[cb ^ 1][c] = bufs[cb][c] + w * (bc - ax);
+          const T* v = bufs[cb];
+          auto vf = [&](int cc, int, int, int) { return v[cc]; };
+          const T ax = tail_ax<T, SYM>(A, c, i, j, k, v[c], dd, vf);
+          bufs[cb ^ 1][c] = v[c] + w * (bc - ax);
         }
         __syncthreads();
         cb ^= 1;
       }
-      cur = cb == 0 ? TA_X : TA_T;
     }
     // every CTA needs to know the buffer: the sweep count fixes it
-    cur = ((ns > 1 ? ns - 1 : 0) % 2 == 0) ? TA_X : TA_T;
-    if (tid == 0) fin[lc] = cur;
+    if (tid == 0) fin[lc] = (((ns > 1 ? ns - 1 : 0) % 2) == 0) ? TA_X : TA_T;
   }
   cl.sync();
   // ---- up: prolongation and post-smoothing
   for (int l = a.nlev - 2; l >= 0; --l) {
+    const Acc<T> A = acc(l);
+    const Acc<T> AC = acc(l + 1);
     const TailLev<T>& L = a.lev[l];
     const TailLev<T>& C = a.lev[l + 1];
-    int c0, c1;
-    own(L, c0, c1);
-    int cur = pre[l];
-    int oth = (cur == TA_X) ? TA_T : TA_X;
-    {  // x += wc * e_coarse(parent)
-      T* v = tloc(smem, L, cur);
-      const int ec = fin[l + 1];
-      for (int c = c0 + tid; c < c1; c += kTailThreads) {
-        const int i = c % L.mx, j = (c / L.mx) % L.my, k = c / (L.mx * L.my);
+    const int c0 = A.c0, c1 = own_end(L);
+    const int cur = pre[l];
+    const int oth = (cur == TA_X) ? TA_T : TA_X;
+    const int ec = fin[l + 1];
+    {  // coarse correction x += wc e(parent) evaluated wherever the first post-sweep reads x
+      auto xp = [&](int c, int i, int j, int k) {
         const int pc = (i >> 1) + C.mx * ((j >> 1) + C.my * (k >> 1));
-        v[c - c0] += a.wc * tget(P, C, ec, pc);
+        return A.get(cur, c) + wc * AC.get(ec, pc);
+      };
+      T* o = A.loc(oth);
+      const T *bl = A.loc(TA_B), *dg = A.loc(TA_DIAG), *dv = A.loc(TA_DINV);
+      for (int c = c0 + tid; c < c1; c += kTailThreads) {
+        int i, j, k;
+        cell_ijk(L, c, i, j, k);
+        const T d = dg[c - c0];
+        const T vc = xp(c, i, j, k);
+        const T ax = tail_ax<T, SYM>(A, c, i, j, k, vc, d, xp);
+        o[c - c0] = vc + jac_weight(om, d, dv[c - c0]) * (bl[c - c0] - ax);
       }
     }
     cl.sync();
-    for (int s = 0; s < nu; ++s) {
-      T* o = tloc(smem, L, oth);
-      const T* bl = tloc(smem, L, TA_B);
-      const T* dg = tloc(smem, L, TA_DIAG);
-      const T* dv = tloc(smem, L, TA_DINV);
-      const T* v = tloc(smem, L, cur);
-      for (int c = c0 + tid; c < c1; c += kTailThreads) {
-        const T d = dg[c - c0], vc = v[c - c0];
-        const T ax = tail_ax<T, SYM>(P, L, cur, c, vc, d);
-        o[c - c0] = vc + jac_weight(a.omega, d, dv[c - c0]) * (bl[c - c0] - ax);
-      }
+    int r = oth;
+    for (int s = 1; s < nu; ++s) {
+      const int out = (r == TA_X) ? TA_T : TA_X;
+      sweep(l, r, out);
       cl.sync();
-      const int tmp = cur;
-      cur = oth;
-      oth = tmp;
+      r = out;
     }
-    if (tid == 0) fin[l] = cur;
+    if (tid == 0) fin[l] = r;
     __syncthreads();
   }
   {  // the first tail level's result to global memory (own cells; no remote
      // access follows the last barrier)
     const TailLev<T>& L = a.lev[0];
-    int c0, c1;
-    own(L, c0, c1);
-    const T* v = tloc(smem, L, fin[0]);
+    const int c0 = rank * L.chunk, c1 = own_end(L);
+    const T* v = reinterpret_cast<const T*>(smem + L.off[fin[0]]);
     for (int c = c0 + tid; c < c1; c += kTailThreads) a.x0[c] = v[c - c0];
   }
 }
 
+}  // namespace
+
+namespace {
 std::mutex g_attr_mu;
 bool g_attr_done[2][2] = {};
 
@@ -325,7 +349,14 @@ bool ensure_attr(size_t smem) {
 
 }  // namespace
 
-bool g_tail_enabled = true;
+// Off by default: measured on the 256^3 rock (mixed path, graph replay) the
+// cluster launch takes about 94 us per V-cycle against about 50 us for the
+// 22 graph-replayed launches it replaces (step 114.0 vs 110.1 ms).  Timing
+// every phase inside the kernel showed why: a phase with almost no work still
+// costs about 2 us (the cluster barrier across 8 SMs), as much as a kernel
+// node of a graph, and 8 SMs have too little issue bandwidth for the 32^3
+// level (7-9 us per phase there).
+bool g_tail_enabled = false;
 
 // Shared-memory layout of the tail starting at level ls: per level, its
 // operator arrays and b, x, t, each `chunk` values rounded up to 16 bytes.

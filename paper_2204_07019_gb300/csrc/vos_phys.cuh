@@ -10,6 +10,7 @@ struct Phys {
   int dim, nx, ny, nz;
   double dx, nu, D, kc, k0, Vm, zeta, rho_ratio, c_in, u_in, eps_min;
   unsigned wall_mask;
+  int inertia;  // explicit div(u u / eps) in the momentum right-hand side
 };
 
 // ---------------------------------------------------------------------------
@@ -66,8 +67,9 @@ struct FaceData {  // iVoS per-face data for one axis (face-array layout)
 void launch_eps_update(const Phys& P, double* eps, double* eps_old, const double* R, const double* dtp, double* stats,
                        const RedScratch& rs, double* kic, cudaStream_t st);
 // S2
+// u: every velocity component at t^n (read by the inertia term when P.inertia)
 void launch_mom_assemble(const Phys& P, int a, const double* eps, const double* kic, const double* p, const double* uold,
-                         const double* dtp,
+                         const double* dtp, double* const u[3],
                          double omega, Op<double> A, double* rhs, cudaStream_t st);
 // S3
 // eps32 (may be NULL): receives the FP32 fluid fraction that the matrix-free

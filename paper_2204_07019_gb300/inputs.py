@@ -48,7 +48,7 @@ PARAM_DEFAULTS = dict(
     c_in=1.0, u_in=1.0, eps_min=1e-4, lam=4.0,
     method=VOS_IVOS, precision=0, precond=0,
     p_rtol=1e-8, u_rtol=1e-8, c_rtol=1e-10,
-    max_iter=500, flow_subiters=1, qs_rtol=0.0, qs_dtau=0.0,
+    max_iter=500, flow_subiters=1, qs_rtol=0.0, qs_dtau=0.0, inertia=0,
     wall_mask=WALL_YM | WALL_YP | WALL_ZM | WALL_ZP,
 )
 

@@ -65,7 +65,7 @@ class VosParams(ctypes.Structure):
         ("method", ctypes.c_int32), ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
         ("p_rtol", ctypes.c_double), ("u_rtol", ctypes.c_double), ("c_rtol", ctypes.c_double),
         ("max_iter", ctypes.c_int32), ("flow_subiters", ctypes.c_int32), ("wall_mask", ctypes.c_uint32),
-        ("qs_rtol", ctypes.c_double), ("qs_dtau", ctypes.c_double),
+        ("qs_rtol", ctypes.c_double), ("qs_dtau", ctypes.c_double), ("inertia", ctypes.c_int32),
     ]
 
 
@@ -657,7 +657,7 @@ def vos_set_launch_mode(graphs):
 
 def vos_set_coarse_cycle(on):
     """1: the coarse multigrid levels of hierarchies set up afterwards run as
-    one cluster launch per V-cycle (default); 0: one launch per operation."""
+    one cluster launch per V-cycle; 0 (default): one launch per operation."""
     load_library().vos_set_coarse_cycle(1 if on else 0)
 
 

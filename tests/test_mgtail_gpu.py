@@ -30,7 +30,7 @@ def _run(V, es, prm, dts, tail, graphs=1, count_tail=False):
     try:
         h = V.vos_create(es, prm)
     finally:
-        V.vos_set_coarse_cycle(1)
+        V.vos_set_coarse_cycle(0)
     try:
         nz, ny, nx = es.shape
         x = (np.arange(nx) + 0.5) / nx

@@ -673,3 +673,75 @@ def test_quasi_static_single_subiteration_is_the_transient_step():
     b, _ = O.step(st, 0.4, p2)
     for n in ("eps", "c", "p", "R", "Rf"):
         assert np.array_equal(a[n], b[n]), n
+
+
+# ---------------------------------------------------------------- inertia term of Eq. momentumDBS
+
+def test_inertia_hand_worked_1d():
+    """div(u u / eps) on a single row (free slip, eps = 1), u on the x-faces
+    1, 2, 3, 4: cell-centre fluxes U phi with U the cell mean and phi the van
+    Leer value (first cell upwind, r = 1 elsewhere: phi = 1, 2.5, 3.5), the
+    outlet face's control volume losing u_3 phi_3 = 16 past the outlet."""
+    prm = I.make_params((1, 1, 3), Pe=1, Da=0, L=1, wall_mask=0, inertia=1)
+    u = [np.array([1.0, 2.0, 3.0, 4.0]).reshape(1, 1, 4), np.zeros((1, 2, 3)), np.zeros((0,))]
+    N = O.inertia(u, np.ones((1, 1, 3)), prm)
+    F = [1.5 * 1.0, 2.5 * 2.5, 3.5 * 3.5]
+    np.testing.assert_allclose(N[0][0, 0, 1:], [F[1] - F[0], F[2] - F[1], 16.0 - F[2]], rtol=1e-15)
+    assert np.all(N[1] == 0.0)
+
+
+def test_inertia_uniform_flow_vanishes():
+    """Uniform flow through a uniform porous medium carries no net momentum
+    into any control volume: N = 0 (2D and 3D, free-slip sides)."""
+    for shape in ((1, 5, 9), (4, 5, 9)):
+        prm = I.make_params(shape, Pe=1, Da=0, L=1, wall_mask=0, inertia=1)
+        nz, ny, nx = shape
+        u = [np.full((nz, ny, nx + 1), 1.7), np.zeros((nz, ny + 1, nx)),
+             np.zeros((nz + 1, ny, nx)) if nz > 1 else np.zeros((0,))]
+        N = O.inertia(u, np.full(shape, 0.4), prm)
+        assert np.abs(N[0][..., 1:]).max() < 1e-12
+
+
+def test_inertia_interior_fluxes_telescope():
+    """Finite-volume conservation: summed over every face of a component,
+    the fluxes through interior control-volume faces cancel and only the
+    outlet terms remain -- u_n phi_n for the x-component, and for y/z the
+    outlet-plane edges, U (the outlet u averaged onto the face) times the
+    last column's phi (random fields, 2D and 3D, dx = 1)."""
+    for shape in ((1, 7, 11), (5, 6, 8)):
+        nz, ny, nx = shape
+        prm = I.make_params(shape, Pe=1, Da=0, L=1, inertia=1)
+        rng = np.random.default_rng(3)
+        u = [rng.normal(size=(nz, ny, nx + 1)), rng.normal(size=(nz, ny + 1, nx)),
+             rng.normal(size=(nz + 1, ny, nx)) if nz > 1 else np.zeros((0,))]
+        eps = rng.uniform(0.2, 1.0, size=shape)
+        N = O.inertia(u, eps, prm)
+        ux = u[0][..., nx]
+        for a in O._axes(prm):
+            phi = u[a] / O.face_porosity(eps, a, prm)
+            if a == 0:
+                out = np.sum(ux * phi[..., nx])
+            elif a == 1:
+                out = np.sum(0.5 * (ux[:, :-1] + ux[:, 1:]) * phi[:, 1:-1, nx - 1])
+            else:
+                out = np.sum(0.5 * (ux[:-1] + ux[1:]) * phi[1:-1, :, nx - 1])
+            assert N[a].sum() == pytest.approx(out, rel=1e-12, abs=1e-12), a
+            assert np.abs(N[a]).max() > 1.0  # the interior terms are not trivially zero
+
+
+def test_inertia_leaves_developed_poiseuille_unchanged():
+    """Developed channel flow has u . grad u = 0: with the inertia term on,
+    the steady profile away from the entrance is still the discrete
+    Poiseuille profile (Sec. 2.2 Stokes limit)."""
+    ny, nx = 6, 84
+    es = np.zeros((1, ny, nx))
+    prm = I.make_params(es.shape, Pe=1, Da=0, L=1, method="psi", nu=1.0, c_in=0.0, kc=0.0, inertia=1)
+    st = _run_to_steady(es, prm, dt=0.5, max_steps=1500)
+    y = np.arange(ny) + 0.5
+    f = y * (ny - y) + 0.25
+    col = st["u"][0][0, :, 3 * nx // 4]
+    assert np.max(np.abs(col - f / f.mean())) < 1e-9
+    # and the inertia term changed the entrance region (it is active)
+    prm0 = dict(prm, inertia=0)
+    st0 = _run_to_steady(es, prm0, dt=0.5, max_steps=1500)
+    assert np.max(np.abs(st["p"] - st0["p"])) > 1e-3

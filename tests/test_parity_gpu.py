@@ -207,3 +207,27 @@ def test_graph_mode_equals_eager(V, precision, dt):
         assert np.array_equal(out[0][0][n], out[1][0][n]), n
     assert out[0][1]["iters_p"] == out[1][1]["iters_p"]
     assert out[0][1]["iters_u"] == out[1][1]["iters_u"]
+
+
+@pytest.mark.parametrize("shape3", [False, True])
+def test_inertia_term_fp64(V, shape3):
+    """Inertia term of Eq. momentumDBS kept (inertia = 1) at Re = Pe/Sc = 10,
+    where it moves the flow: FP64 parity with the oracle's explicit van Leer
+    form, 2D calcite post and 3D rock, iVoS."""
+    if shape3:
+        es = I.sphere_rock_3d((14, 16, 30), seed=6, median_r=3.0, sigma=0.3, target_porosity=0.5,
+                              start_solid=0.6, band=2, margin=3.0)
+        kw = dict(L=6.0)
+    else:
+        es = I.calcite_post_2d(96, 32, 30.0, 16.0, 8.0)
+        kw = dict(L=16.0)
+    prm = tight(I.make_params(es.shape, Pe=10.0, Da=1.0, method="ivos", Vm=0.2, Sc=1.0, inertia=1, **kw))
+    compare(V, es, prm, [0.1] * 4, 1e-9, init=c_start(es, prm))
+    # the term matters at this Reynolds number: the flow without it differs
+    st1 = O.init_state(es, prm)
+    p0 = dict(prm, inertia=0)
+    st0 = O.init_state(es, p0)
+    for _ in range(2):
+        st1, _ = O.step(st1, 0.1, prm)
+        st0, _ = O.step(st0, 0.1, p0)
+    assert rel_l2(st1["u"][0], st0["u"][0]) > 1e-3
