@@ -267,38 +267,10 @@ def measured_bf16_peak():
         return 1900.0, "fallback"
 
 
-def learned_leg(V, es, prm, dt, steps, warmup, torch, crop=64, rounds=2, adam_per_round=60, lr=2e-3, seed=0):
-    """The learned pressure preconditioner on the same workload: train the
-    U-Net with the library's own kernels on residual snapshots of short runs
-    on crop^3 pieces of the rock (the network is fully convolutional), then
-    time steps of the full workload with the network attached (flexible CG,
-    MG-PCG fallback; eager launches).  Also the tensor-core conv throughput."""
-    t0 = time.time()
-    net_t = V.UNet((crop,) * 3, train=True)
-    net_t.set_params(V.UNet.he_init(seed))
-    snap_iters = [0, 2, 5, 10, 20, 40]
-    losses = []
-    n = es.shape[0]
-    offsets = [(0, 0, 0), (n - crop, n - crop, n - crop)]
-    for oz, oy, ox in offsets:
-        esc = np.ascontiguousarray(es[oz:oz + crop, oy:oy + crop, ox:ox + crop])
-        prc = dict(prm)
-        prc.update(nx=crop, ny=crop, nz=crop)
-        h = V.vos_create(esc, prc)
-        try:
-            V.vos_step(h, dt)
-            snaps = torch.empty((len(snap_iters), crop ** 3), dtype=torch.float32, device="cuda")
-            for _ in range(rounds):
-                V.vos_step(h, dt)
-                V.vos_pressure_snapshots(h, snap_iters, snaps)
-                for k in range(adam_per_round):
-                    losses.append(net_t.train_step(h, snaps[k % len(snap_iters)], lr))
-        finally:
-            V.vos_destroy(h)
-    params = net_t.get_params()
-    net_t.close()
-    torch.cuda.synchronize()
-    train_s = time.time() - t0
+def _unet_eval(V, es, prm, dt, steps, warmup, params, torch):
+    """Steps of the workload with a network of the given parameters attached
+    to the pressure solve (flexible CG, MG-PCG fallback; eager launches):
+    ms per step and iteration counts."""
     net = V.UNet(es.shape, train=False)
     net.set_params(params)
     h = V.vos_create(es, prm)
@@ -332,14 +304,56 @@ def learned_leg(V, es, prm, dt, steps, warmup, torch, crop=64, rounds=2, adam_pe
     finally:
         V.vos_destroy(h)
         net.close()
+    return ms, its, nets, fbs, rep
+
+
+def learned_leg(V, es, prm, dt, steps, warmup, torch, train_size=128, seeds=tuple(range(1, 21)), adam_per_seed=12,
+                lr=2e-3, init_seed=0):
+    """The learned pressure preconditioner under the held-out protocol:
+    train the U-Net with the library's own kernels on MG-PCG residual
+    snapshots of short runs on independently seeded rocks (seeds 1-20,
+    train_size^3, the same generator and parameters), then evaluate it on
+    the workload's own rock (seed 0, not seen in training) against the
+    untrained network and against MG-PCG alone, at the same dt and step
+    sequence.  Also the tensor-core convolution throughput."""
+    t0 = time.time()
+    net_t = V.UNet((train_size,) * 3, train=True)
+    p0 = V.UNet.he_init(init_seed)
+    net_t.set_params(p0)
+    snap_iters = [0, 2, 5, 10, 20, 40]
+    losses = []
+    r = 12.0 * train_size / 256.0
+    for seed in seeds:
+        est = I.sphere_rock_3d(train_size, seed=seed, median_r=r)
+        prt = dict(prm)
+        prt.update(nx=train_size, ny=train_size, nz=train_size)
+        h = V.vos_create(est, prt)
+        try:
+            for _ in range(max(warmup, 1)):
+                V.vos_step(h, dt)
+            snaps = torch.empty((len(snap_iters), train_size ** 3), dtype=torch.float32, device="cuda")
+            V.vos_pressure_snapshots(h, snap_iters, snaps)
+            for k in range(adam_per_seed):
+                losses.append(net_t.train_step(h, snaps[k % len(snap_iters)], lr))
+        finally:
+            V.vos_destroy(h)
+    params = net_t.get_params()
+    net_t.close()
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    ms, its, nets, fbs, rep = _unet_eval(V, es, prm, dt, steps, warmup, params, torch)
+    ms_u, its_u, nets_u, fbs_u, _ = _unet_eval(V, es, prm, dt, steps, warmup, p0, torch)
     nconv, cms, cflops = rep.get("unet_conv", (0, 0.0, 0.0))
     peak, src = measured_bf16_peak()
     tf = cflops / (cms * 1e-3) / 1e12 if cms > 0 else None
     return {"ms_per_step": ms, "value": es.size / (ms * 1e-3), "iters_p_mean": float(np.mean(its)),
             "net_iters_mean": float(np.mean(nets)), "fallbacks": int(sum(fbs)), "steps": steps,
-            "train": {"seconds": train_s, "adam_steps": len(losses), "crop": crop, "crops": len(offsets),
-                      "snapshot_iters": snap_iters, "loss_first": float(np.mean(losses[:6])),
-                      "loss_last": float(np.mean(losses[-6:]))},
+            "untrained": {"ms_per_step": ms_u, "iters_p_mean": float(np.mean(its_u)),
+                          "net_iters_mean": float(np.mean(nets_u)), "fallbacks": int(sum(fbs_u))},
+            "train": {"protocol": f"snapshots of {len(seeds)} seeded {train_size}^3 rocks (seeds "
+                                  f"{seeds[0]}-{seeds[-1]}); evaluated on the held-out seed-0 rock",
+                      "seconds": train_s, "adam_steps": len(losses), "snapshot_iters": snap_iters,
+                      "loss_first": float(np.mean(losses[:6])), "loss_last": float(np.mean(losses[-6:]))},
             "conv": {"launches": nconv, "ms": cms, "tflops": tf, "peak_tflops": peak, "peak_source": src,
                      "frac": (tf / peak) if tf else None, "bound": "tensor"}}
 
@@ -466,6 +480,8 @@ def main():
     ap.add_argument("--dt", type=float, default=None, help="fixed time step of every leg (default per workload)")
     ap.add_argument("--mom-precond", default="auto", choices=["auto", "diag", "mg"],
                     help="momentum preconditioner: the library's rule, or forced")
+    ap.add_argument("--p-warm", action="store_true",
+                    help="start each pressure-correction solve from the previous step's correction")
     ap.add_argument("--coarse-cycle", action="store_true",
                     help="run the coarse multigrid levels as one cluster launch per V-cycle instead of one "
                          "launch per operation (same results; for comparison)")
@@ -516,6 +532,8 @@ def main():
     es, prm, desc = workload(args.workload, args.size)
     if args.mom_precond != "auto":
         prm["precond"] = int(prm.get("precond", 0)) | (2 if args.mom_precond == "diag" else 4)
+    if args.p_warm:
+        prm["precond"] = int(prm.get("precond", 0)) | 8
     dt = args.dt if args.dt else DEFAULT_DT[args.workload]
     N = es.size
     clocks = ClockSampler(local)
@@ -548,9 +566,11 @@ def main():
     e2e = time_e2e(V, es, prm, max(2, args.steps // 2), dt)
     learned = None
     if not args.no_learned and es.ndim == 3 and min(es.shape) >= 64:
-        learned = learned_leg(V, es, prm, dt, 3, args.warmup, torch)
+        learned = learned_leg(V, es, prm, dt, 3, args.warmup, torch,
+                              train_size=min(128, es.shape[0]))
         learned["vs_fp64"] = learned["value"] / (N / (r64["ms"] * 1e-3)) if r64 else None
         learned["vs_mixed"] = learned["value"] / (N / (r["ms"] * 1e-3))
+        learned["mgpcg_iters_p_mean"] = float(np.mean([i[1] for i in iters]))
     fp64_value = N * world / (r64["ms"] * 1e-3) if r64 else None
     mom = mom_precond_name(prm, dt)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

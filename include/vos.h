@@ -74,12 +74,15 @@ typedef enum { VOS_FP64 = 0, VOS_MIXED = 1 } vos_precision;
  * through solid cells; see vos_floating_clusters).
  * VOS_PRECOND_NO_DEFLATION drops the deflation; VOS_PRECOND_MOM_DIAG /
  * VOS_PRECOND_MOM_MG make every momentum solve use the diagonal / the
- * multigrid preconditioner whatever dt is (at most one of the two).
+ * multigrid preconditioner whatever dt is (at most one of the two);
+ * VOS_PRECOND_P_WARM starts the pressure-correction solve of a transient
+ * step from the previous step's correction instead of zero.
  * Solver aids, not part of the paper's method: they change the iteration
  * count, not the converged solution. */
 #define VOS_PRECOND_NO_DEFLATION 1
 #define VOS_PRECOND_MOM_DIAG 2
 #define VOS_PRECOND_MOM_MG 4
+#define VOS_PRECOND_P_WARM 8
 
 /* Physical and numerical parameters (non-dimensional units are fine).
  * Symbols follow Sec. 2.2-2.5: nu kinematic viscosity, D diffusion

@@ -284,7 +284,10 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
     // S3: pressure correction, projection
     launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, h->eps32, st);
     launch_defl_energy(S[3].h.defl, S[3].op64, st);
-    cudaMemsetAsync(h->phi, 0, (size_t)N * sizeof(double), st);
+    // initial guess of the correction: zero, or the previous step's
+    // correction (VOS_PRECOND_P_WARM; transient steps only -- in a
+    // quasi-static step phi holds the previous concentration)
+    if (qs || !(h->prm.precond & VOS_PRECOND_P_WARM)) cudaMemsetAsync(h->phi, 0, (size_t)N * sizeof(double), st);
     {
       SolveResult r = solve<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter,
                                h->work, h->rs, st, true);
@@ -373,7 +376,8 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
   }
   launch_pres_assemble(P, h->eps, h->us, h->R, dtp, S[3].h.mg.omega, S[3].op64, S[3].rhs, h->eps32, st);
   launch_defl_energy(S[3].h.defl, S[3].op64, st);
-  VOS_CUDA_TRY(cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st));
+  if (!(h->prm.precond & VOS_PRECOND_P_WARM))
+    VOS_CUDA_TRY(cudaMemsetAsync(h->phi, 0, (size_t)P.nx * P.ny * P.nz * sizeof(double), st));
   VOS_CUDA_TRY(solve_capture<T>(S[3].op64, S[3].h, S[3].rhs, unknown_view(h, 3), h->prm.p_rtol, h->prm.max_iter,
                                 h->work, h->rs, st, true, h->dsolve + 3, h->gs1, h->gs2));
   launch_project(P, h->eps, h->phi, dtp, h->us, h->u, h->p, st);
@@ -526,7 +530,7 @@ int validate(const vos_params* p) {
   if (!std::isfinite(p->u_in)) return set_err(nullptr, VOS_EINVAL, "u_in must be finite");
   if (p->method < 0 || p->method > 2) return set_err(nullptr, VOS_EINVAL, "unknown method %d", p->method);
   if (p->precision < 0 || p->precision > 1) return set_err(nullptr, VOS_EINVAL, "unknown precision %d", p->precision);
-  if (p->precond & ~(VOS_PRECOND_NO_DEFLATION | VOS_PRECOND_MOM_DIAG | VOS_PRECOND_MOM_MG))
+  if (p->precond & ~(VOS_PRECOND_NO_DEFLATION | VOS_PRECOND_MOM_DIAG | VOS_PRECOND_MOM_MG | VOS_PRECOND_P_WARM))
     return set_err(nullptr, VOS_EINVAL, "unknown precond flags %d", p->precond);
   if ((p->precond & VOS_PRECOND_MOM_DIAG) && (p->precond & VOS_PRECOND_MOM_MG))
     return set_err(nullptr, VOS_EINVAL, "VOS_PRECOND_MOM_DIAG and VOS_PRECOND_MOM_MG exclude each other");

@@ -1,0 +1,80 @@
+"""Measured error bounds of the production-tolerance paths against the FP64
+oracle (exact solves), per field, in 3D and for every reactive-surface
+method: pressure and momentum solved to a diagonally scaled relative
+residual of 1e-8 and the concentration to 1e-10, FP64 and mixed precision
+(FP32 multigrid / Krylov inner solves, FP64 refinement), with the porosity
+error (mean eps) after the steps.  The bounds below are the stated
+per-field bounds; each run prints its measured errors."""
+import json
+
+import numpy as np
+import pytest
+
+from oracle import vos_oracle as O
+from paper_2204_07019_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+# stated bounds (relative L2; R and R_f on the k_c c_in / dx scale)
+BOUNDS = {"eps": 1e-9, "c": 1e-6, "u": 1e-5, "v": 1e-5, "w": 1e-5, "p": 1e-5, "R": 1e-6, "Rf": 1e-6}
+POROSITY_BOUND = 1e-10
+_ORACLE = {}
+
+
+@pytest.fixture(scope="module")
+def V():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_07019_gb300 import build_lib, vos
+    build_lib.build()
+    vos.load_library()
+    return vos
+
+
+@pytest.fixture(scope="module")
+def rock():
+    es = I.sphere_rock_3d((16, 20, 32), seed=11, median_r=3.0, sigma=0.3, target_porosity=0.45, start_solid=0.6,
+                          band=2, margin=3.0)
+    return es
+
+
+@pytest.mark.parametrize("method", ["ivos", "psi", "psi_prime"])
+@pytest.mark.parametrize("precision", [1, 0])
+def test_production_tolerance_bounds_3d(V, rock, method, precision):
+    es = rock
+    prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=6.0, method=method, Vm=0.5, precision=precision,
+                        p_rtol=1e-8, u_rtol=1e-8, c_rtol=1e-10, max_iter=4000)
+    nz, ny, nx = es.shape
+    x = (np.arange(nx) + 0.5) / nx
+    c0 = np.broadcast_to(1.0 - 0.5 * x, es.shape).copy()
+    dts = [0.2, 0.2, 0.2]
+    if method not in _ORACLE:  # the oracle's exact solves, shared by both precisions
+        st = O.init_state(es, prm)
+        st["c"] = c0.copy()
+        for dt in dts:
+            st, _ = O.step(st, dt, prm)
+        _ORACLE[method] = st
+    st = _ORACLE[method]
+    h = V.vos_create(es, prm)
+    try:
+        V.vos_set_fields(h, c=c0)
+        for dt in dts:
+            assert V.vos_step(h, dt) == 0
+        got = V.vos_fields(h)
+        s = V.vos_get_stats(h)
+    finally:
+        V.vos_destroy(h)
+    ref = dict(eps=st["eps"], c=st["c"], p=st["p"], u=st["u"][0], v=st["u"][1], w=st["u"][2], R=st["R"], Rf=st["Rf"])
+    scale = prm["kc"] * prm["c_in"] / prm["dx"] * np.sqrt(es.size)
+    errs = {}
+    for n, r in ref.items():
+        d = np.linalg.norm(got[n] - r)
+        errs[n] = float(d / scale if n in ("R", "Rf") else d / max(np.linalg.norm(r), 1e-300))
+    perr = abs(float(np.mean(got["eps"])) - float(np.mean(st["eps"])))
+    print("PRECISION_BOUNDS", json.dumps({"method": method, "precision": precision, "errors": errs,
+                                          "porosity_err": perr, "res_p": s["res_p"], "res_c": s["res_c"]}))
+    assert s["res_p"] <= 1e-8 and s["res_c"] <= 1e-10
+    bad = {n: e for n, e in errs.items() if not e <= BOUNDS[n]}
+    assert not bad, (bad, errs)
+    assert perr <= POROSITY_BOUND
