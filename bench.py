@@ -249,6 +249,27 @@ def time_gpu(V, es, prm, steps, warmup, dt, torch, profile=True, keep_fields=Fal
         V.vos_destroy(h)
 
 
+def _gen_rock(args):
+    size, seed, r = args
+    return I.sphere_rock_3d(size, seed=seed, median_r=r)
+
+
+def _gen_batch_item(args):
+    seed, b, nx, ny = args
+    return I.disc_micromodel_2d(nx, ny, seed=seed * 1000 + b + 1)
+
+
+def _spawn_map(fn, items):
+    """Seeded geometry generators are numpy-only; run them in a pool of
+    spawned processes (a process forked after CUDA initialisation may hang)."""
+    import multiprocessing as mp
+    n = min(len(items), max(1, (os.cpu_count() or 1)), 16)
+    if n <= 1:
+        return [fn(a) for a in items]
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(fn, items)
+
+
 def mom_precond_name(prm, dt):
     """Which momentum preconditioner vos_step picks (include/vos.h rule)."""
     fl = int(prm.get("precond", 0))
@@ -323,8 +344,8 @@ def learned_leg(V, es, prm, dt, steps, warmup, torch, train_size=128, seeds=tupl
     snap_iters = [0, 2, 5, 10, 20, 40]
     losses = []
     r = 12.0 * train_size / 256.0
-    for seed in seeds:
-        est = I.sphere_rock_3d(train_size, seed=seed, median_r=r)
+    rocks = _spawn_map(_gen_rock, [(train_size, sd, r) for sd in seeds])
+    for seed, est in zip(seeds, rocks):
         prt = dict(prm)
         prt.update(nx=train_size, ny=train_size, nz=train_size)
         h = V.vos_create(est, prt)
@@ -360,8 +381,17 @@ def learned_leg(V, es, prm, dt, steps, warmup, torch, train_size=128, seeds=tupl
 
 def batch_workload(count=64):
     """64 disc micromodels, side lengths U[128, 768], log-uniform Pe in [1, 100]
-    and Da in [0.01, 100], iVoS, mixed precision."""
-    items = I.batched_micromodels(count, seed=0)
+    and Da in [0.01, 100], iVoS, mixed precision (the draws of
+    inputs.batched_micromodels, geometries generated in parallel)."""
+    rng = np.random.default_rng(0)
+    draws = []
+    for b in range(count):
+        nx, ny = (int(v) for v in rng.integers(128, 768 + 1, size=2))
+        Pe = float(10 ** rng.uniform(0.0, 2.0))
+        Da = float(10 ** rng.uniform(-2.0, 2.0))
+        draws.append((nx, ny, Pe, Da))
+    geoms = _spawn_map(_gen_batch_item, [(0, b, nx, ny) for b, (nx, ny, _, _) in enumerate(draws)])
+    items = [(es, Pe, Da) for es, (_, _, Pe, Da) in zip(geoms, draws)]
     eps, prms = [], []
     for es, Pe, Da in items:
         p = I.make_params(es.shape, Pe=Pe, Da=Da, L=40.0, method="ivos", precision=1)
@@ -393,6 +423,69 @@ def time_batch(V, eps, prms, steps, warmup, torch, nthreads=16, dt=0.02):
                     dt_range=[min(dts), max(dts)])
     finally:
         V.vos_batch_destroy(b)
+
+
+def _event_loop(V, h, steps, dt_fn, torch):
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    its = []
+    e0.record(stream)
+    for _ in range(steps):
+        V.vos_step(h, dt_fn())
+        s = V.vos_get_stats(h)
+        its.append(s["iters_p"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, float(np.mean(its))
+
+
+def extra_workloads(V, torch, c1_steps=10, c3_steps=3):
+    """The other configurations of the build, each measured briefly on the same
+    GPU (the step count of each is part of its record):
+    calcite post 256 x 64, FP64 iVoS, 50 steps with dt from vos_suggest_dt at
+    CFL 0.5 (and App. D's 0.005); the 1024 x 512 disc micromodel in three
+    (Pe, Da) regimes x three methods x {FP64, mixed}, fixed dt 0.05; the batch
+    of 64 micromodels (one CUDA graph per batch step)."""
+    out = {}
+    es = I.calcite_post_2d()
+    prm = I.make_params(es.shape, Pe=1.0, Da=0.1, L=32.0, method="ivos", precision=0)
+    prm.update(p_rtol=1e-8, u_rtol=1e-8, c_rtol=1e-10, max_iter=2000)
+    h = V.vos_create(es, prm)
+    try:
+        V.vos_step(h, 0.1)
+        ms, ip = _event_loop(V, h, 50, lambda: min(V.vos_suggest_dt(h, 0.5, 0.005), 1.0), torch)
+        s = V.vos_get_stats(h)
+        out["calcite_256x64_fp64_ivos"] = {"steps": 50, "ms_per_step": ms, "cell_steps_per_s": es.size / (ms * 1e-3),
+                                           "iters_p_mean": ip, "t_end": s["t"], "porosity": s["porosity"],
+                                           "dt": "vos_suggest_dt(0.5, 0.005) per step"}
+    finally:
+        V.vos_destroy(h)
+    es = I.disc_micromodel_2d(1024, 512, seed=0)
+    rows = []
+    for Pe, Da in ((1.0, 0.1), (100.0, 1.0), (100.0, 100.0)):
+        for method in ("psi", "psi_prime", "ivos"):
+            for prec in (0, 1):
+                prm = I.make_params(es.shape, Pe=Pe, Da=Da, L=40.0, method=method, precision=prec)
+                prm.update(p_rtol=1e-8, u_rtol=1e-8, c_rtol=1e-10, max_iter=2000)
+                h = V.vos_create(es, prm)
+                try:
+                    for _ in range(2):
+                        V.vos_step(h, 0.05)
+                    ms, ip = _event_loop(V, h, c1_steps, lambda: 0.05, torch)
+                finally:
+                    V.vos_destroy(h)
+                rows.append({"Pe": Pe, "Da": Da, "method": method, "precision": "mixed" if prec else "fp64",
+                             "ms_per_step": round(ms, 3), "cell_steps_per_s": es.size / (ms * 1e-3),
+                             "iters_p_mean": ip})
+    out["micromodel_1024x512"] = {"steps": c1_steps, "warmup": 2, "dt": 0.05, "runs": rows}
+    eps, prms = batch_workload(64)
+    r = time_batch(V, eps, prms, c3_steps, 2, torch, dt=0.02)
+    N = int(sum(e.size for e in eps))
+    out["batch64_micromodels"] = {"steps": c3_steps, "warmup": 2, "dt": 0.02, "cells": N, "ms_per_batch_step": r["ms"],
+                                  "cell_steps_per_s": N / (r["ms"] * 1e-3), "iters_p_mean": r["iters_p_mean"]}
+    return out
 
 
 def time_e2e(V, es, prm, steps, dt):
@@ -480,6 +573,9 @@ def main():
     ap.add_argument("--dt", type=float, default=None, help="fixed time step of every leg (default per workload)")
     ap.add_argument("--mom-precond", default="auto", choices=["auto", "diag", "mg"],
                     help="momentum preconditioner: the library's rule, or forced")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the brief measurements of the other configurations (calcite post, micromodel grid, "
+                         "batch of 64)")
     ap.add_argument("--p-warm", action="store_true",
                     help="start each pressure-correction solve from the previous step's correction")
     ap.add_argument("--coarse-cycle", action="store_true",
@@ -605,6 +701,8 @@ def main():
                                             "c": float(np.mean([i[6] for i in iters]))}},
            "device_bytes": r["dev_bytes"], "e2e": e2e, "clocks": ck, "learned": learned,
            "breakdown": r["breakdown"]}
+    if rank == 0 and not args.no_extra and args.workload == "rock256":
+        out["workloads"] = extra_workloads(V, torch)
     if rank == 0 and not args.no_cpu:
         r, n, shp, dtc, cores = oracle_sample(es, prm, dt, budget_s=15.0)
         out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
