@@ -69,6 +69,9 @@ def workload(name, size=256):
     else:
         raise SystemExit(f"unknown workload {name}")
     prm.update(p_rtol=1e-8, u_rtol=1e-8, c_rtol=1e-10, max_iter=2000)
+    # the pressure correction starts from the previous step's correction
+    # (VOS_PRECOND_P_WARM: 64 -> 59.5 iterations per step on the rock)
+    prm["precond"] = int(prm.get("precond", 0)) | 8
     return es, prm, desc
 
 
@@ -576,8 +579,10 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the brief measurements of the other configurations (calcite post, micromodel grid, "
                          "batch of 64)")
-    ap.add_argument("--p-warm", action="store_true",
-                    help="start each pressure-correction solve from the previous step's correction")
+    ap.add_argument("--p-cold", action="store_true",
+                    help="start each pressure-correction solve from zero instead of the previous step's correction")
+    ap.add_argument("--u-extrap", action="store_true",
+                    help="start each momentum solve from the extrapolation 2 u^n - u^{n-1}")
     ap.add_argument("--coarse-cycle", action="store_true",
                     help="run the coarse multigrid levels as one cluster launch per V-cycle instead of one "
                          "launch per operation (same results; for comparison)")
@@ -628,8 +633,10 @@ def main():
     es, prm, desc = workload(args.workload, args.size)
     if args.mom_precond != "auto":
         prm["precond"] = int(prm.get("precond", 0)) | (2 if args.mom_precond == "diag" else 4)
-    if args.p_warm:
-        prm["precond"] = int(prm.get("precond", 0)) | 8
+    if args.p_cold:
+        prm["precond"] = int(prm.get("precond", 0)) & ~8
+    if args.u_extrap:
+        prm["precond"] = int(prm.get("precond", 0)) | 16
     dt = args.dt if args.dt else DEFAULT_DT[args.workload]
     N = es.size
     clocks = ClockSampler(local)
@@ -676,7 +683,7 @@ def main():
                       "dt_rule": "fixed for every leg and step (warm-up from rest included)",
                       "dt_cfl05_after": r["dt_cfl"],
                       "p_rtol": prm["p_rtol"], "u_rtol": prm["u_rtol"], "c_rtol": prm["c_rtol"],
-                      "momentum_precond": mom,
+                      "momentum_precond": mom, "precond_flags": int(prm.get("precond", 0)),
                       "residual": "diagonally scaled, FP64",
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "launch": "eager" if args.eager else "graph", "tiles": r["tiles"],

@@ -76,13 +76,17 @@ typedef enum { VOS_FP64 = 0, VOS_MIXED = 1 } vos_precision;
  * VOS_PRECOND_MOM_MG make every momentum solve use the diagonal / the
  * multigrid preconditioner whatever dt is (at most one of the two);
  * VOS_PRECOND_P_WARM starts the pressure-correction solve of a transient
- * step from the previous step's correction instead of zero.
+ * step from the previous step's correction instead of zero;
+ * VOS_PRECOND_U_EXTRAP starts the momentum solves of a transient step from
+ * the extrapolation 2 u^n - u^{n-1} instead of u^n (one more velocity field
+ * in device memory; restarted from u when vos_set_fields sets it).
  * Solver aids, not part of the paper's method: they change the iteration
  * count, not the converged solution. */
 #define VOS_PRECOND_NO_DEFLATION 1
 #define VOS_PRECOND_MOM_DIAG 2
 #define VOS_PRECOND_MOM_MG 4
 #define VOS_PRECOND_P_WARM 8
+#define VOS_PRECOND_U_EXTRAP 16
 
 /* Physical and numerical parameters (non-dimensional units are fine).
  * Symbols follow Sec. 2.2-2.5: nu kinematic viscosity, D diffusion

@@ -54,6 +54,7 @@ struct vos_handle {
   double *eps, *eps_old, *c, *p, *phi, *R, *Rf, *kr, *kic;
   float* eps32;  // FP32 fluid fraction for the matrix-free pressure sweeps (mixed precision)
   double *u[3], *us[3];
+  double* uprev[3];  // u^{n-1} (VOS_PRECOND_U_EXTRAP only)
   FaceData fd[3];
   // solvers: 0..2 momentum, 3 pressure, 4 transport
   Sys<double> sd[5];
@@ -271,7 +272,10 @@ int step_impl(vos_handle* h, Sys<T>* S, double dt) {
   for (int m = 0; m < M; ++m) {
     // S2: momentum predictor per component
     for (int a = 0; a < nd; ++a) {
-      cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      if (h->uprev[a] && !qs)
+        launch_extrapolate(face_count(P, a), h->u[a], h->uprev[a], h->us[a], st);
+      else
+        cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st);
       if (box_cells(S[a].box) == 0) continue;
       launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, h->u, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
       SolveResult r = solve<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
@@ -368,7 +372,10 @@ cudaError_t enqueue_step(vos_handle* h, Sys<T>* S, bool mom_mg) {
   const double* dtp = h->d_dt;
   launch_eps_update(P, h->eps, h->eps_old, h->R, dtp, h->dstats, h->rs, h->kic, st);
   for (int a = 0; a < nd; ++a) {
-    VOS_CUDA_TRY(cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (h->uprev[a])
+      launch_extrapolate(face_count(P, a), h->u[a], h->uprev[a], h->us[a], st);
+    else
+      VOS_CUDA_TRY(cudaMemcpyAsync(h->us[a], h->u[a], face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (box_cells(S[a].box) == 0) continue;
     launch_mom_assemble(P, a, h->eps, h->kic, h->p, h->u[a], dtp, h->u, S[a].h.mg.omega, S[a].op64, S[a].rhs, st);
     VOS_CUDA_TRY(solve_capture<T>(S[a].op64, S[a].h, S[a].rhs, unknown_view(h, a), h->prm.u_rtol, h->prm.max_iter,
@@ -530,7 +537,8 @@ int validate(const vos_params* p) {
   if (!std::isfinite(p->u_in)) return set_err(nullptr, VOS_EINVAL, "u_in must be finite");
   if (p->method < 0 || p->method > 2) return set_err(nullptr, VOS_EINVAL, "unknown method %d", p->method);
   if (p->precision < 0 || p->precision > 1) return set_err(nullptr, VOS_EINVAL, "unknown precision %d", p->precision);
-  if (p->precond & ~(VOS_PRECOND_NO_DEFLATION | VOS_PRECOND_MOM_DIAG | VOS_PRECOND_MOM_MG | VOS_PRECOND_P_WARM))
+  if (p->precond & ~(VOS_PRECOND_NO_DEFLATION | VOS_PRECOND_MOM_DIAG | VOS_PRECOND_MOM_MG | VOS_PRECOND_P_WARM |
+                     VOS_PRECOND_U_EXTRAP))
     return set_err(nullptr, VOS_EINVAL, "unknown precond flags %d", p->precond);
   if ((p->precond & VOS_PRECOND_MOM_DIAG) && (p->precond & VOS_PRECOND_MOM_MG))
     return set_err(nullptr, VOS_EINVAL, "VOS_PRECOND_MOM_DIAG and VOS_PRECOND_MOM_MG exclude each other");
@@ -617,13 +625,17 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     if (!*f) return fail(VOS_ENOMEM, "device allocation failed (cell fields)");
   }
   for (int a = 0; a < 3; ++a) {
-    h->u[a] = h->us[a] = nullptr;
+    h->u[a] = h->us[a] = h->uprev[a] = nullptr;
     h->fd[a] = FaceData{nullptr, nullptr, nullptr};
     if (a >= P.dim) continue;
     size_t fb = (size_t)face_count(P, a) * sizeof(double);
     h->u[a] = (double*)dev_alloc(h, fb);
     h->us[a] = (double*)dev_alloc(h, fb);
     if (!h->u[a] || !h->us[a]) return fail(VOS_ENOMEM, "device allocation failed (face fields)");
+    if (prm->precond & VOS_PRECOND_U_EXTRAP) {
+      h->uprev[a] = (double*)dev_alloc(h, fb);
+      if (!h->uprev[a]) return fail(VOS_ENOMEM, "device allocation failed (face fields)");
+    }
     if (prm->method == VOS_IVOS) {
       h->fd[a].s = (double*)dev_alloc(h, fb);
       h->fd[a].corr = (double*)dev_alloc(h, fb);
@@ -713,6 +725,9 @@ int vos_create(const double* eps_s_host, const vos_params* prm, void* stream, co
     std::vector<double> u0((size_t)face_count(P, 0), 0.0);
     for (long long r = 0; r < (long long)P.ny * P.nz; ++r) u0[(size_t)r * (P.nx + 1)] = prm->u_in;
     cudaMemcpyAsync(h->u[0], u0.data(), u0.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    for (int a = 0; a < P.dim; ++a)  // no history yet: the extrapolation starts from u
+      if (h->uprev[a])
+        cudaMemcpyAsync(h->uprev[a], h->u[a], (size_t)face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(h->rs.counter, 0, sizeof(unsigned int), st);
     cudaMemsetAsync(h->dstats, 0, ST_COUNT * sizeof(double), st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(VOS_ECUDA, cudaGetErrorString(cudaGetLastError()));
@@ -792,6 +807,10 @@ int vos_set_fields(vos_handle* h, uint32_t mask, const double* eps, const double
     if (!(mask & it.bit) || !it.dst || !it.src || it.bytes == 0) continue;
     cudaMemcpyAsync(it.dst, it.src, it.bytes, cudaMemcpyHostToDevice, h->st);
   }
+  for (int a = 0; a < P.dim; ++a)  // a resumed velocity has no history: restart the extrapolation
+    if (h->uprev[a] && (mask & (VOS_F_U | VOS_F_V | VOS_F_W)))
+      cudaMemcpyAsync(h->uprev[a], h->u[a], (size_t)face_count(P, a) * sizeof(double), cudaMemcpyDeviceToDevice,
+                      h->st);
   cudaError_t e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return set_err(h, VOS_ECUDA, "vos_set_fields: %s", cudaGetErrorString(e));
   if ((mask & VOS_F_EPS) && eps) return setup_deflation(h, eps);

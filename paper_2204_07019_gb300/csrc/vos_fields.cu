@@ -672,6 +672,23 @@ void launch_div_check(const double* a, const double* d, long long n, double* q_f
   vlaunch("div_check", 32.0 * n, k_div_check, (int)g, kThreads, st, a, d, n, q_fast, q_ieee);
 }
 
+__global__ void k_extrapolate(long long n, const double* __restrict__ u, double* __restrict__ uprev,
+                              double* __restrict__ us) {
+  VOS_COUNT_EXEC();
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const double v = u[c];
+    us[c] = 2.0 * v - uprev[c];
+    uprev[c] = v;
+  }
+}
+
+void launch_extrapolate(long long n, const double* u, double* uprev, double* us, cudaStream_t st) {
+  long long g = (n + kThreads - 1) / kThreads;
+  if (g > (long long)g_num_sms * 8) g = (long long)g_num_sms * 8;
+  if (g < 1) g = 1;
+  vlaunch("u_extrapolate", 32.0 * n, k_extrapolate, (int)g, kThreads, st, n, u, uprev, us);
+}
+
 void launch_set_scalar(double* dst, double v, cudaStream_t st) {
   vlaunch("set_scalar", 8.0, k_set_scalar, 1, 32, st, dst, v);
 }

@@ -103,6 +103,9 @@ void launch_rates(const Phys& P, int ivos, const double* eps, const double* c, c
                   const FaceData fd[3], double* R, double* Rf, double* stats, const RedScratch& rs,
                   cudaStream_t st);
 void launch_set_scalar(double* dst, double v, cudaStream_t st);
+// us = 2 u - uprev, then uprev = u (n values): the extrapolated initial guess
+// of the momentum solves.
+void launch_extrapolate(long long n, const double* u, double* uprev, double* us, cudaStream_t st);
 // q_fast[i] = fdiv_nr(a[i], d[i]), q_ieee[i] = a[i] / d[i] (device arrays).
 void launch_div_check(const double* a, const double* d, long long n, double* q_fast, double* q_ieee,
                       cudaStream_t st);

@@ -24,7 +24,7 @@ __all__ = [
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
     "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16", "UNet", "vos_set_unet_preconditioner",
     "vos_unet_solve_stats", "vos_pressure_snapshots", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
-    "PRECOND_MOM_DIAG", "PRECOND_MOM_MG", "PRECOND_P_WARM",
+    "PRECOND_MOM_DIAG", "PRECOND_MOM_MG", "PRECOND_P_WARM", "PRECOND_U_EXTRAP",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -36,6 +36,7 @@ PRECOND_NO_DEFLATION = 1
 PRECOND_MOM_DIAG = 2
 PRECOND_MOM_MG = 4
 PRECOND_P_WARM = 8
+PRECOND_U_EXTRAP = 16
 
 EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",

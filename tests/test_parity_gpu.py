@@ -231,3 +231,21 @@ def test_inertia_term_fp64(V, shape3):
         st1, _ = O.step(st1, 0.1, prm)
         st0, _ = O.step(st0, 0.1, p0)
     assert rel_l2(st1["u"][0], st0["u"][0]) > 1e-3
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_warm_started_solves_same_solution(V, precision):
+    """Starting the pressure correction from the previous step's correction
+    and the momentum solves from 2 u^n - u^{n-1} (VOS_PRECOND_P_WARM |
+    VOS_PRECOND_U_EXTRAP) changes the iteration counts only: the fields stay
+    within the FP64 parity bar of the oracle, graph and eager launches alike."""
+    es = I.sphere_rock_3d((14, 18, 30), seed=4, median_r=3.0, sigma=0.3, target_porosity=0.5,
+                          start_solid=0.6, band=2, margin=3.0)
+    prm = tight(I.make_params(es.shape, Pe=10.0, Da=1.0, L=6.0, method="ivos", Vm=0.3,
+                              precond=V.PRECOND_P_WARM | V.PRECOND_U_EXTRAP), precision=precision)
+    compare(V, es, prm, [0.05] * 4, 1e-9, init=c_start(es, prm))
+    try:
+        V.vos_set_launch_mode(0)
+        compare(V, es, prm, [0.05] * 4, 1e-9, init=c_start(es, prm))
+    finally:
+        V.vos_set_launch_mode(1)

@@ -15,9 +15,12 @@ from paper_2204_07019_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-# stated bounds (relative L2; R and R_f on the k_c c_in / dx scale)
-BOUNDS = {"eps": 1e-9, "c": 1e-6, "u": 1e-5, "v": 1e-5, "w": 1e-5, "p": 1e-5, "R": 1e-6, "Rf": 1e-6}
-POROSITY_BOUND = 1e-10
+# stated bounds (relative L2; R and R_f on the k_c c_in / dx scale), about 5x
+# the largest error measured over the six method / precision combinations
+# (3 steps, 16 x 20 x 32 rock): eps 1.5e-12, c 2.2e-9, p 4.3e-11,
+# u/v/w 2.4e-10, R/R_f 1.1e-11, porosity 1.9e-14
+BOUNDS = {"eps": 1e-11, "c": 1e-8, "u": 2e-9, "v": 2e-9, "w": 2e-9, "p": 5e-10, "R": 1e-10, "Rf": 1e-10}
+POROSITY_BOUND = 1e-12
 _ORACLE = {}
 
 
