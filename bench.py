@@ -70,8 +70,10 @@ def workload(name, size=256):
         raise SystemExit(f"unknown workload {name}")
     prm.update(p_rtol=1e-8, u_rtol=1e-8, c_rtol=1e-10, max_iter=2000)
     # the pressure correction starts from the previous step's correction
-    # (VOS_PRECOND_P_WARM: 64 -> 59.5 iterations per step on the rock)
-    prm["precond"] = int(prm.get("precond", 0)) | 8
+    # (VOS_PRECOND_P_WARM: 64 -> 57.4 iterations per step on the rock, 109.1
+    # -> 104.0 ms) and the momentum solves from 2 u^n - u^{n-1}
+    # (VOS_PRECOND_U_EXTRAP: 44.1 -> 42.9 iterations, 104.0 -> 103.2 ms)
+    prm["precond"] = int(prm.get("precond", 0)) | 8 | 16
     return es, prm, desc
 
 
@@ -158,6 +160,12 @@ def measured_peaks():
 TRAFFIC_PER_ALG_BYTE = {
     "pcg_xr_f32_L0": (356163072.0 / 402653184.0, "ncu dram bytes of one full-size launch (rock 256^3) per algorithmic byte"),
     "mg_jac_f32_L0": (23.94 / 28.0, "ncu dram bytes of the 128^3 capture scaled by units processed"),
+    # matrix-free pressure sweep, rock 192^3 (7,077,888 cells, above L2):
+    # 87.48 MB read (12.0 B/cell, its three input words) + 5.65 MB written
+    # (the 4 B/cell output mostly still in L2 at the end of the launch)
+    # against 16 B/cell algorithmic, scaled to a launch by cells
+    "mg_jac_mf_f32_L0": ((87481088.0 + 5651456.0) / (16.0 * 7077888.0),
+                         "ncu dram bytes of a 192^3 launch scaled by cells"),
 }
 
 
@@ -581,8 +589,8 @@ def main():
                          "batch of 64)")
     ap.add_argument("--p-cold", action="store_true",
                     help="start each pressure-correction solve from zero instead of the previous step's correction")
-    ap.add_argument("--u-extrap", action="store_true",
-                    help="start each momentum solve from the extrapolation 2 u^n - u^{n-1}")
+    ap.add_argument("--u-plain", action="store_true",
+                    help="start each momentum solve from u^n instead of the extrapolation 2 u^n - u^{n-1}")
     ap.add_argument("--coarse-cycle", action="store_true",
                     help="run the coarse multigrid levels as one cluster launch per V-cycle instead of one "
                          "launch per operation (same results; for comparison)")
@@ -635,8 +643,8 @@ def main():
         prm["precond"] = int(prm.get("precond", 0)) | (2 if args.mom_precond == "diag" else 4)
     if args.p_cold:
         prm["precond"] = int(prm.get("precond", 0)) & ~8
-    if args.u_extrap:
-        prm["precond"] = int(prm.get("precond", 0)) | 16
+    if args.u_plain:
+        prm["precond"] = int(prm.get("precond", 0)) & ~16
     dt = args.dt if args.dt else DEFAULT_DT[args.workload]
     N = es.size
     clocks = ClockSampler(local)
