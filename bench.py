@@ -591,6 +591,8 @@ def main():
                     help="start each pressure-correction solve from zero instead of the previous step's correction")
     ap.add_argument("--u-plain", action="store_true",
                     help="start each momentum solve from u^n instead of the extrapolation 2 u^n - u^{n-1}")
+    ap.add_argument("--scalar-sweeps", action="store_true",
+                    help="one cell per thread in the matrix-free pressure sweeps (same results; for comparison)")
     ap.add_argument("--coarse-cycle", action="store_true",
                     help="run the coarse multigrid levels as one cluster launch per V-cycle instead of one "
                          "launch per operation (same results; for comparison)")
@@ -619,6 +621,8 @@ def main():
         V.vos_set_launch_mode(0)
     if args.coarse_cycle:
         V.vos_set_coarse_cycle(1)
+    if args.scalar_sweeps:
+        V.vos_set_vector_sweeps(0)
     if args.workload == "batch64":
         eps, prms = batch_workload(64)
         N = int(sum(e.size for e in eps))

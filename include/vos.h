@@ -465,6 +465,12 @@ int vos_set_launch_mode(int graphs);
  *   bit-identical results (the same arithmetic per cell, in the same
  *   order). */
 int vos_set_coarse_cycle(int on);
+/* vos_set_vector_sweeps(1) (default): the matrix-free FP32 sweeps of the
+ *   pressure fine level (mixed precision) give each thread four consecutive
+ *   cells along x with 16-byte loads and stores when nx is a multiple of 4;
+ *   vos_set_vector_sweeps(0): one cell per thread.  Identical results (each
+ *   cell's arithmetic is the same); takes effect at the next launch. */
+int vos_set_vector_sweeps(int on);
 int vos_prof_enable(const char* filter);
 int vos_prof_report(char* buf, size_t len);
 void vos_prof_reset(void);

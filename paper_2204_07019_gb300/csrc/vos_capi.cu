@@ -1012,6 +1012,11 @@ int vos_set_launch_mode(int graphs) {
   return VOS_OK;
 }
 
+int vos_set_vector_sweeps(int on) {
+  vos::g_mf4 = on != 0;
+  return VOS_OK;
+}
+
 int vos_set_coarse_cycle(int on) {
   vos::g_tail_enabled = on != 0;
   return VOS_OK;

@@ -373,6 +373,9 @@ struct Hier {
 // hierarchies set up afterwards); tail_supported checks that the device can
 // run the cluster with that much shared memory.
 extern bool g_tail_enabled;
+// Matrix-free FP32 pressure sweeps with four cells per thread and 16-byte
+// accesses when the row length is a multiple of 4 (vos_solver.cu).
+extern bool g_mf4;
 template <typename T>
 int tail_plan(const Hier<T>& h);
 template <typename T>

@@ -62,3 +62,37 @@ def test_2d_tiles(V):
         assert tuned == 1 and (tx, ty) == (256, 1) and zc >= 1
     finally:
         V.vos_destroy(h)
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 36), (1, 96, 160), (10, 14, 30)])
+def test_vector_sweeps_identical(V, shape):
+    """The four-cells-per-thread matrix-free pressure sweeps (16-byte rows,
+    nx % 4 == 0) compute each cell with the arithmetic of the one-cell
+    kernel: whole mixed-precision steps give identical fields and iteration
+    counts, graph launches; a grid with nx % 4 != 0 (30) keeps the one-cell
+    kernel."""
+    if shape[0] == 1:
+        es = I.disc_micromodel_2d(shape[2], shape[1], seed=2, rmin=5, rmax=12, target_porosity=0.6)
+    else:
+        es = I.sphere_rock_3d(shape, seed=5, median_r=3.0, sigma=0.3, target_porosity=0.45,
+                              start_solid=0.6, band=2, margin=3.0)
+    prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=8.0, method="ivos", Vm=0.2, precision=1)
+    out = []
+    try:
+        for vec in (1, 0):
+            V.vos_set_vector_sweeps(vec)
+            h = V.vos_create(es, prm)
+            try:
+                its = []
+                for _ in range(3):
+                    assert V.vos_step(h, 0.02) == 0
+                    s = V.vos_get_stats(h)
+                    its.append((s["iters_p"], s["outer_p"]))
+                out.append((V.vos_fields(h), its))
+            finally:
+                V.vos_destroy(h)
+    finally:
+        V.vos_set_vector_sweeps(1)
+    assert out[0][1] == out[1][1]
+    for n in out[0][0]:
+        assert np.array_equal(out[0][0][n], out[1][0][n]), n
