@@ -158,14 +158,19 @@ def measured_peaks():
 #   mg_jac_f32_L0: 23.94 B/cell read against 28 B/cell algorithmic (rock 128^3,
 #     the output stays in L2).
 TRAFFIC_PER_ALG_BYTE = {
-    "pcg_xr_f32_L0": (356163072.0 / 402653184.0, "ncu dram bytes of one full-size launch (rock 256^3) per algorithmic byte"),
+    # DRAM bytes (read + write) per algorithmic byte from one ncu capture of
+    # the bench workload at 192^3 (7,077,888 cells, above L2, about 4.8 GB on
+    # the device), scaled to a launch by the units processed: the reads scale
+    # exactly (every input word once); the part of the writes that reaches
+    # DRAM inside the launch depends on the L2, so the write part is an
+    # estimate.
+    # FP32 x/r update: 113.28 MB read (16 B per unknown) + 9.04 MB written
+    # against 24 B per unknown
+    "pcg_xr_f32_L0": ((113283840.0 + 9038848.0) / (24.0 * 7077888.0), "ncu dram bytes of a 192^3 launch scaled by units"),
+    # matrix-free pressure Jacobi sweep (four cells per thread): 84.95 MB read
+    # (12.0 B per cell) + 6.61 MB written against 16 B per cell
+    "mg_jac_mf_f32_L0": ((84949248.0 + 6610688.0) / (16.0 * 7077888.0), "ncu dram bytes of a 192^3 launch scaled by cells"),
     "mg_jac_f32_L0": (23.94 / 28.0, "ncu dram bytes of the 128^3 capture scaled by units processed"),
-    # matrix-free pressure sweep, rock 192^3 (7,077,888 cells, above L2):
-    # 87.48 MB read (12.0 B/cell, its three input words) + 5.65 MB written
-    # (the 4 B/cell output mostly still in L2 at the end of the launch)
-    # against 16 B/cell algorithmic, scaled to a launch by cells
-    "mg_jac_mf_f32_L0": ((87481088.0 + 5651456.0) / (16.0 * 7077888.0),
-                         "ncu dram bytes of a 192^3 launch scaled by cells"),
 }
 
 
