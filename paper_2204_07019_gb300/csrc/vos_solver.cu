@@ -1153,6 +1153,159 @@ __global__ void __launch_bounds__(kThreads) k_matvec_mf_dot(Box bx, const float*
   }
 }
 
+// Four-cells-per-thread forms of the two fused matvec + p.q kernels above
+// (16-byte rows: nx % 4 == 0), with the per-cell arithmetic of the one-cell
+// kernels; each thread adds its four cells' products in x order to its
+// partial sum, so the summation order (and the last bits of p.q) differs
+// from the one-cell kernels.
+__device__ __forceinline__ void fin_alpha(KScal* sc, double pq) {
+  sc->pq = pq;
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    sc->breakdown = 1;
+    sc->done = 1;
+    sc->alpha = 0.0;
+  } else {
+    sc->alpha = sc->rz / pq;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_matvec_mfc4_dot(Box bx, const float* __restrict__ dg, float a,
+                                                             const float* __restrict__ x, float* __restrict__ out,
+                                                             int zc, KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  PSum<float> ps;
+  if (i0 < bx.mx && j < bx.my && k0 < k1) {
+    const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    auto ld4 = [](const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); };
+    const bool hxm = i0 > 0, hxp = i0 + 4 < bx.mx, hym = j > 0, hyp = j + 1 < bx.my;
+    long long c = i0 + sy * j + sz * k0;
+    float4 vlo = (k0 > 0) ? ld4(x + c - sz) : z4;
+    float4 vc = ld4(x + c);
+    float4 vhi = (k0 + 1 < bx.mz) ? ld4(x + c + sz) : z4;
+    float4 dc = ld4(dg + c);
+    for (int k = k0; k < k1; ++k, c += sz) {
+      const bool nxt = k + 1 < k1;
+      const float4 v2 = (nxt && k + 2 < bx.mz) ? ld4(x + c + 2 * sz) : z4;
+      const float4 dn = nxt ? ld4(dg + c + sz) : z4;
+      const float vxm = hxm ? __ldg(x + c - 1) : 0.0f, vxp = hxp ? __ldg(x + c + 4) : 0.0f;
+      const float4 vym = hym ? ld4(x + c - sy) : z4, vyp = hyp ? ld4(x + c + sy) : z4;
+      float r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q;
+        float sum = 0.0f;
+        if (i + 1 < bx.mx) sum += q < 3 ? f4get(vc, q + 1) : vxp;
+        if (i > 0) sum += q > 0 ? f4get(vc, q - 1) : vxm;
+        if (hyp) sum += f4get(vyp, q);
+        if (hym) sum += f4get(vym, q);
+        if (k + 1 < bx.mz) sum += f4get(vhi, q);
+        if (k > 0) sum += f4get(vlo, q);
+        const float vq = f4get(vc, q);
+        r[q] = f4get(dc, q) * vq + a * sum;
+        ps.add(vq, r[q]);
+      }
+      *reinterpret_cast<float4*>(out + c) = make_float4(r[0], r[1], r[2], r[3]);
+      vlo = vc;
+      vc = vhi;
+      vhi = v2;
+      dc = dn;
+    }
+  }
+  double acc[1] = {ps.get()};
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_alpha(sc, acc[0]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_matvec_mf4_dot(Box bx, const float* __restrict__ e, float s,
+                                                            const float* __restrict__ x, float* __restrict__ out,
+                                                            int zc, KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  PSum<float> ps;
+  if (i0 < bx.mx && j < bx.my && k0 < k1) {
+    const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+    const float hs = 0.5f * s;
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    auto ld4 = [](const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); };
+    const bool hxm = i0 > 0, hxp = i0 + 4 < bx.mx, hym = j > 0, hyp = j + 1 < bx.my;
+    long long c = i0 + sy * j + sz * k0;
+    float4 elo = (k0 > 0) ? ld4(e + c - sz) : z4;
+    float4 ec = ld4(e + c);
+    float4 ehi = (k0 + 1 < bx.mz) ? ld4(e + c + sz) : z4;
+    float4 vlo = (k0 > 0) ? ld4(x + c - sz) : z4;
+    float4 vc = ld4(x + c);
+    float4 vhi = (k0 + 1 < bx.mz) ? ld4(x + c + sz) : z4;
+    for (int k = k0; k < k1; ++k, c += sz) {
+      const bool up2 = (k + 2 < bx.mz) && (k + 1 < k1);
+      const float4 e2 = up2 ? ld4(e + c + 2 * sz) : z4;
+      const float4 v2 = up2 ? ld4(x + c + 2 * sz) : z4;
+      const float exm = hxm ? __ldg(e + c - 1) : 0.0f, exp_ = hxp ? __ldg(e + c + 4) : 0.0f;
+      const float vxm = hxm ? __ldg(x + c - 1) : 0.0f, vxp = hxp ? __ldg(x + c + 4) : 0.0f;
+      const float4 eym = hym ? ld4(e + c - sy) : z4, eyp = hyp ? ld4(e + c + sy) : z4;
+      const float4 vym = hym ? ld4(x + c - sy) : z4, vyp = hyp ? ld4(x + c + sy) : z4;
+      float r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q;
+        const float ecq = f4get(ec, q);
+        float d = (i == bx.mx - 1) ? 2.0f * ecq * s : 0.0f;
+        float off = 0.0f;
+        if (i + 1 < bx.mx) {
+          const float a = (ecq + (q < 3 ? f4get(ec, q + 1) : exp_)) * hs;
+          d += a;
+          off += a * (q < 3 ? f4get(vc, q + 1) : vxp);
+        }
+        if (i > 0) {
+          const float a = (ecq + (q > 0 ? f4get(ec, q - 1) : exm)) * hs;
+          d += a;
+          off += a * (q > 0 ? f4get(vc, q - 1) : vxm);
+        }
+        if (hyp) {
+          const float a = (ecq + f4get(eyp, q)) * hs;
+          d += a;
+          off += a * f4get(vyp, q);
+        }
+        if (hym) {
+          const float a = (ecq + f4get(eym, q)) * hs;
+          d += a;
+          off += a * f4get(vym, q);
+        }
+        if (k + 1 < bx.mz) {
+          const float a = (ecq + f4get(ehi, q)) * hs;
+          d += a;
+          off += a * f4get(vhi, q);
+        }
+        if (k > 0) {
+          const float a = (ecq + f4get(elo, q)) * hs;
+          d += a;
+          off += a * f4get(vlo, q);
+        }
+        const float vq = f4get(vc, q);
+        r[q] = d * vq - off;
+        ps.add(vq, r[q]);
+      }
+      *reinterpret_cast<float4*>(out + c) = make_float4(r[0], r[1], r[2], r[3]);
+      elo = ec;
+      ec = ehi;
+      ehi = e2;
+      vlo = vc;
+      vc = vhi;
+      vhi = v2;
+    }
+  }
+  double acc[1] = {ps.get()};
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_alpha(sc, acc[0]);
+}
+
 // BiCGStab: p = r + beta (p - omega v)   (first iteration: p = r)
 template <typename T>
 __global__ void k_bicg_p(long long n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ p,
@@ -1757,9 +1910,21 @@ static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork*
   if constexpr (sizeof(T) == 4 && SYM) {
     if (A.mfc != 0.0f && !use_mg && !use_net) {  // constant-link matvec fused with p.q
       const Op<T> Z = zview(A);
-      const ZCfg z = zcfg(Z.box);  // grid-reduction kernel: default shape, fixed summation order
-      vlaunch("pcg_matvec_dot_mfc_f32_L0", 4.0 * n * 4.0, k_matvec_mfc_dot, z.grid, z.block, st, Z.box,
-              (const float*)Z.diag, A.mfc, (const float*)k.p, (float*)k.q, z.zc, w->sc, rs);
+      if (Z.box.mx % 4 == 0) {  // 16-byte rows: four cells per thread (fixed shape, fixed summation order)
+        const ZCfg z = zcfg_mf4(Z.box);
+        vlaunch("pcg_matvec_dot_mfc_f32_L0", 4.0 * n * 4.0, k_matvec_mfc4_dot, z.grid, z.block, st, Z.box,
+                (const float*)Z.diag, A.mfc, (const float*)k.p, (float*)k.q, z.zc, w->sc, rs);
+      } else {
+        const ZCfg z = zcfg(Z.box);  // grid-reduction kernel: default shape, fixed summation order
+        vlaunch("pcg_matvec_dot_mfc_f32_L0", 4.0 * n * 4.0, k_matvec_mfc_dot, z.grid, z.block, st, Z.box,
+                (const float*)Z.diag, A.mfc, (const float*)k.p, (float*)k.q, z.zc, w->sc, rs);
+      }
+      fused_mv = true;
+    } else if (A.mfe && !use_net && zview(A).box.mx % 4 == 0) {  // the same, matrix-free pressure, four cells
+      const Op<T> Z = zview(A);
+      const ZCfg z = zcfg_mf4(Z.box);
+      vlaunch("pcg_matvec_dot_mf_f32_L0", 4.0 * n * 4.0, k_matvec_mf4_dot, z.grid, z.block, st, Z.box, A.mfe, A.mfs,
+              (const float*)k.p, (float*)k.q, z.zc, w->sc, rs);
       fused_mv = true;
     } else if (A.mfe && !use_net) {  // matrix-free pressure matvec fused with p.q
       const Op<T> Z = zview(A);
