@@ -16,14 +16,15 @@ struct Phys {
 // ---------------------------------------------------------------------------
 // FP64 arithmetic is the scarce resource of the physics kernels on this part
 // (a few FP64 operations per SM and clock, against 128 FP32 ones), so their
-// divisions use this quotient instead of the IEEE one: Newton-Raphson on the
-// reciprocal seeded by the hardware estimate (PTX rcp.approx.ftz.f64),
-// y1 = y0 + y0 (1 - d y0), then one Newton step on the quotient,
-// q1 = q0 + y1 (a - d q0) with q0 = a y1.  A seed with relative error e
-// leaves e^2 after the first step and e^4 after the second, so q1 is within
-// a couple of ulp of a/d (vos_fp64_div_check compares it with the IEEE
-// quotient): five FP64 operations.  |d| outside [2^-1000, 2^1000], zero,
-// infinite or NaN takes the IEEE division.
+// divisions use this quotient instead of the IEEE one: the FMA-based
+// Newton-Raphson division of P. W. Markstein (IBM J. Res. Dev. 34(1), 1990),
+// seeded by the hardware reciprocal estimate (PTX rcp.approx.ftz.f64): one
+// step on the reciprocal, y1 = y0 + y0 (1 - d y0), then one on the
+// quotient, q1 = q0 + y1 (a - d q0) with q0 = a y1.  A seed with relative
+// error e leaves e^2 after the first step and e^4 after the second, so q1 is
+// within a couple of ulp of a/d (vos_fp64_div_check compares it with the
+// IEEE quotient): five FP64 operations.  |d| outside [2^-1000, 2^1000],
+// zero, infinite or NaN takes the IEEE division.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double fdiv_nr(double a, double d) {
   const unsigned ex = ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;
