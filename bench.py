@@ -149,14 +149,6 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes per algorithmic byte of the kernels that can be the roofline's
-# dominant kernel, each from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of a full launch, caches flushed):
-#   pcg_xr_f32_L0: 356,163,072 B against 402,653,184 B algorithmic (24 B per
-#     unknown, 16,777,216 unknowns of the rock 256^3 momentum system; every
-#     operand read once, part of the writes still in L2 when the kernel ends);
-#   mg_jac_f32_L0: 23.94 B/cell read against 28 B/cell algorithmic (rock 128^3,
-#     the output stays in L2).
 TRAFFIC_PER_ALG_BYTE = {
     # DRAM bytes (read + write) per algorithmic byte from one ncu capture of
     # the bench workload at 192^3 (7,077,888 cells, above L2, about 4.8 GB on
@@ -170,7 +162,6 @@ TRAFFIC_PER_ALG_BYTE = {
     # matrix-free pressure Jacobi sweep (four cells per thread): 84.95 MB read
     # (12.0 B per cell) + 6.61 MB written against 16 B per cell
     "mg_jac_mf_f32_L0": ((84949248.0 + 6610688.0) / (16.0 * 7077888.0), "ncu dram bytes of a 192^3 launch scaled by cells"),
-    "mg_jac_f32_L0": (23.94 / 28.0, "ncu dram bytes of the 128^3 capture scaled by units processed"),
 }
 
 
