@@ -589,6 +589,9 @@ def main():
                     help="start each momentum solve from u^n instead of the extrapolation 2 u^n - u^{n-1}")
     ap.add_argument("--scalar-sweeps", action="store_true",
                     help="one cell per thread in the matrix-free pressure sweeps (same results; for comparison)")
+    ap.add_argument("--four-kernel-pcg", action="store_true",
+                    help="diagonally preconditioned CG in four kernels per iteration instead of two (for "
+                         "comparison)")
     ap.add_argument("--coarse-cycle", action="store_true",
                     help="run the coarse multigrid levels as one cluster launch per V-cycle instead of one "
                          "launch per operation (same results; for comparison)")
@@ -619,6 +622,8 @@ def main():
         V.vos_set_coarse_cycle(1)
     if args.scalar_sweeps:
         V.vos_set_vector_sweeps(0)
+    if args.four_kernel_pcg:
+        V.vos_set_fused_pcg(0)
     if args.workload == "batch64":
         eps, prms = batch_workload(64)
         N = int(sum(e.size for e in eps))
@@ -695,7 +700,8 @@ def main():
                       "residual": "diagonally scaled, FP64",
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "launch": "eager" if args.eager else "graph", "tiles": r["tiles"],
-                      "coarse_cycle": "cluster-resident" if args.coarse_cycle else "separate launches"},
+                      "coarse_cycle": "cluster-resident" if args.coarse_cycle else "separate launches",
+                      "diag_pcg": "four kernels per iteration" if args.four_kernel_pcg else "two kernels per iteration"},
            "roofline": r["roofline"], "gpu_launches": r["launches"],
            "fp64_value": fp64_value, "fp64_ms_per_step": r64["ms"] if r64 else None,
            "mixed_vs_fp64": (value / fp64_value) if fp64_value else None,

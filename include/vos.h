@@ -471,6 +471,18 @@ int vos_set_coarse_cycle(int on);
  *   vos_set_vector_sweeps(0): one cell per thread.  Identical results (each
  *   cell's arithmetic is the same); takes effect at the next launch. */
 int vos_set_vector_sweeps(int on);
+/* vos_set_fused_pcg(1) (default): diagonally preconditioned CG passes on a
+ *   constant-link FP32 operator (the momentum systems of the mixed path when
+ *   they take the diagonal preconditioner) run two kernels per iteration:
+ *   the direction update fused with the matrix-vector product and p.q, then
+ *   the x/r update fused with the preconditioner and r.r, r.z, z.z (20 + 32
+ *   bytes per unknown against 64).  vos_set_fused_pcg(0): four kernels per
+ *   iteration (direction update, matrix-vector product with p.q, x/r update,
+ *   preconditioner with r.z).  Both compute every value with the same
+ *   operations and every dot product in the same order: identical results.
+ *   Takes effect at the next launch; a step already captured as a CUDA graph
+ *   keeps the form it was captured with. */
+int vos_set_fused_pcg(int on);
 int vos_prof_enable(const char* filter);
 int vos_prof_report(char* buf, size_t len);
 void vos_prof_reset(void);

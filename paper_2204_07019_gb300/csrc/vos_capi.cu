@@ -1017,6 +1017,11 @@ int vos_set_vector_sweeps(int on) {
   return VOS_OK;
 }
 
+int vos_set_fused_pcg(int on) {
+  vos::g_fused_pcg = on != 0;
+  return VOS_OK;
+}
+
 int vos_set_coarse_cycle(int on) {
   vos::g_tail_enabled = on != 0;
   return VOS_OK;

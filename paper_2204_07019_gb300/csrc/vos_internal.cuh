@@ -376,6 +376,7 @@ extern bool g_tail_enabled;
 // Matrix-free FP32 pressure sweeps with four cells per thread and 16-byte
 // accesses when the row length is a multiple of 4 (vos_solver.cu).
 extern bool g_mf4;
+extern bool g_fused_pcg;  // two-kernel diagonal PCG iteration (vos_set_fused_pcg)
 template <typename T>
 int tail_plan(const Hier<T>& h);
 template <typename T>

@@ -236,6 +236,32 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Op<T> A, const T* __restri
   }
 }
 
+// Row arithmetic of the matrix-free FP32 pressure operator, shared by every
+// kernel that applies it (one or four cells per thread, fused passes): the
+// link to a neighbour n is a_cn = (e_c + e_n) s / 2, the diagonal the sum of
+// the links present (plus 2 e_c s on the outlet face of the last column),
+// the links taken in the order x+, x-, y+, y-, z+, z-; explicit rounding,
+// so that all these kernels give identical values.
+__device__ __forceinline__ float mf_outlet(float ec, float s, bool outlet) {
+  return outlet ? __fmul_rn(__fmul_rn(2.0f, ec), s) : 0.0f;
+}
+// adds the link to a neighbour (fluid fraction en, value vn) to d and off
+__device__ __forceinline__ void mf_link(float ec, float en, float vn, float hs, bool has_x, float& d, float& off) {
+  const float a = __fmul_rn(__fadd_rn(ec, en), hs);
+  d = __fadd_rn(d, a);
+  if (has_x) off = __fmaf_rn(a, vn, off);
+}
+// SK_JAC0: (omega / d) b; SK_JAC: x + (omega / d)(b - A x); SK_MV: A x;
+// SK_RES: b - A x (A x = d x_c - off)
+template <int KIND>
+__device__ __forceinline__ float mf_result(float d, float off, float vc, float bc, float omega) {
+  if (KIND == SK_JAC0) return __fmul_rn(__fdividef(omega, d), bc);
+  const float ax = __fmaf_rn(d, vc, -off);
+  if (KIND == SK_JAC) return __fmaf_rn(__fdividef(omega, d), __fsub_rn(bc, ax), vc);
+  if (KIND == SK_MV) return ax;
+  return __fsub_rn(bc, ax);
+}
+
 // First Jacobi sweep from zero: x = (omega / diag) b.
 // Matrix-free FP32 sweeps of the pressure operator (Op::mfe): the same z
 // march as k_stencil, but the links and the diagonal are formed from the
@@ -273,49 +299,15 @@ __global__ void __launch_bounds__(kThreads) k_stencil_mf(Box bx, const float* __
     const float e2 = up2 ? __ldg(e + c + 2 * sz) : 0.0f;
     const float v2 = (has_x && up2) ? __ldg(x + c + 2 * sz) : 0.0f;
     const float bn = (KIND != SK_MV && k + 1 < k1) ? __ldg(b + c + sz) : 0.0f;
-    float d = (i == bx.mx - 1) ? 2.0f * ec * s : 0.0f;  // outlet: phi = 0 on the face
-    float off = 0.0f;                                    // sum over links of a_cn x_n
-    if (i + 1 < bx.mx) {
-      const float a = (ec + __ldg(e + c + 1)) * hs;
-      d += a;
-      if (has_x) off += a * __ldg(x + c + 1);
-    }
-    if (i > 0) {
-      const float a = (ec + __ldg(e + c - 1)) * hs;
-      d += a;
-      if (has_x) off += a * __ldg(x + c - 1);
-    }
-    if (j + 1 < bx.my) {
-      const float a = (ec + __ldg(e + c + sy)) * hs;
-      d += a;
-      if (has_x) off += a * __ldg(x + c + sy);
-    }
-    if (j > 0) {
-      const float a = (ec + __ldg(e + c - sy)) * hs;
-      d += a;
-      if (has_x) off += a * __ldg(x + c - sy);
-    }
-    if (up) {
-      const float a = (ec + ehi) * hs;
-      d += a;
-      off += a * vhi;
-    }
-    if (k > 0) {
-      const float a = (ec + elo) * hs;
-      d += a;
-      off += a * vlo;
-    }
-    if (KIND == SK_JAC0) {
-      out[c] = __fdividef(omega, d) * bc;
-    } else {
-      const float ax = d * vc - off;
-      if (KIND == SK_JAC)
-        out[c] = vc + __fdividef(omega, d) * (bc - ax);
-      else if (KIND == SK_MV)
-        out[c] = ax;
-      else
-        out[c] = bc - ax;
-    }
+    float d = mf_outlet(ec, s, i == bx.mx - 1);  // outlet: phi = 0 on the face
+    float off = 0.0f;                              // sum over links of a_cn x_n
+    if (i + 1 < bx.mx) mf_link(ec, __ldg(e + c + 1), has_x ? __ldg(x + c + 1) : 0.0f, hs, has_x, d, off);
+    if (i > 0) mf_link(ec, __ldg(e + c - 1), has_x ? __ldg(x + c - 1) : 0.0f, hs, has_x, d, off);
+    if (j + 1 < bx.my) mf_link(ec, __ldg(e + c + sy), has_x ? __ldg(x + c + sy) : 0.0f, hs, has_x, d, off);
+    if (j > 0) mf_link(ec, __ldg(e + c - sy), has_x ? __ldg(x + c - sy) : 0.0f, hs, has_x, d, off);
+    if (up) mf_link(ec, ehi, vhi, hs, has_x, d, off);
+    if (k > 0) mf_link(ec, elo, vlo, hs, has_x, d, off);
+    out[c] = mf_result<KIND>(d, off, vc, bc, omega);
     elo = ec;
     ec = ehi;
     ehi = e2;
@@ -337,95 +329,100 @@ __global__ void __launch_bounds__(kThreads) k_stencil_mf(Box bx, const float* __
 __device__ __forceinline__ float f4get(const float4& v, int q) {
   return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
 }
-template <int KIND>
-__global__ void __launch_bounds__(kThreads) k_stencil_mf4(Box bx, const float* __restrict__ e, float s,
-                                                         const float* __restrict__ b, const float* __restrict__ x,
-                                                         float* __restrict__ out, float omega, int zc,
-                                                         const KScal* sc) {
-  VOS_COUNT_EXEC();
-  DONE_RETURN(sc);
-  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k0 = blockIdx.z * zc;
-  const int k1 = min(k0 + zc, bx.mz);
-  if (i0 >= bx.mx || j >= bx.my || k0 >= k1) return;
-  const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
-  const float hs = 0.5f * s;
-  const bool has_x = KIND != SK_JAC0;
-  const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  auto ld4 = [](const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); };
-  long long c = i0 + sy * j + sz * k0;
-  float4 elo = (k0 > 0) ? ld4(e + c - sz) : z4;
-  float4 ec = ld4(e + c);
-  float4 ehi = (k0 + 1 < bx.mz) ? ld4(e + c + sz) : z4;
-  float4 vlo = (has_x && k0 > 0) ? ld4(x + c - sz) : z4;
-  float4 vc = has_x ? ld4(x + c) : z4;
-  float4 vhi = (has_x && k0 + 1 < bx.mz) ? ld4(x + c + sz) : z4;
-  float4 bc = (KIND != SK_MV) ? ld4(b + c) : z4;
-  const bool hxm = i0 > 0, hxp = i0 + 4 < bx.mx, hym = j > 0, hyp = j + 1 < bx.my;
-  for (int k = k0; k < k1; ++k, c += sz) {
+// Register march of the four-cells-per-thread sweep, shared by the sweep,
+// matrix-vector and fused residual-restriction kernels so that all compute
+// each cell with the same arithmetic.  XS says where the iterate x comes from:
+//   XS_PLAIN: x itself;
+//   XS_PRO:   the prolongated iterate x + wc * xc[parent] (the coarse
+//             correction of the V-cycle, added on the fly with the FMA of
+//             k_prolong_add), so the first post-smoothing sweep needs no
+//             separate prolongation pass.
+enum XSrc { XS_PLAIN = 0, XS_PRO = 1 };
+template <int KIND, int XS>
+struct Mf4March {
+  static constexpr bool has_x = KIND != SK_JAC0;
+  Box bx;
+  const float* __restrict__ e;
+  const float* __restrict__ b;
+  const float* __restrict__ x;
+  float s, hs, omega;
+  Box cb;                        // XS_PRO: coarse box (z view)
+  const float* __restrict__ xc;  // XS_PRO: coarse correction
+  float wc;                      // XS_PRO: coarse weight
+  int i0, j;
+  long long sy, sz;
+  bool hxm, hxp, hym, hyp;
+  float4 elo, ec, ehi, vlo, vc, vhi, bc;
+
+  __device__ __forceinline__ static float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+  __device__ __forceinline__ long long parent(int ii, int jj, int kk) const {
+    return (ii >> 1) + (long long)cb.mx * ((jj >> 1) + (long long)cb.my * (kk >> 1));
+  }
+  // x of cells i0..i0+3 of row (jj, kk), flat index c of cell i0 (i0 % 4 == 0:
+  // parents i0/2 and i0/2 + 1)
+  __device__ __forceinline__ float4 x4(long long c, int jj, int kk) const {
+    float4 v = ld4(x + c);
+    if (XS == XS_PRO) {
+      const long long p = parent(i0, jj, kk);
+      const float ca = __ldg(xc + p), cq = __ldg(xc + p + 1);
+      v = make_float4(__fmaf_rn(wc, ca, v.x), __fmaf_rn(wc, ca, v.y), __fmaf_rn(wc, cq, v.z), __fmaf_rn(wc, cq, v.w));
+    }
+    return v;
+  }
+  __device__ __forceinline__ float x1(long long c, int ii, int jj, int kk) const {
+    const float v = __ldg(x + c);
+    if (XS == XS_PRO) return __fmaf_rn(wc, __ldg(xc + parent(ii, jj, kk)), v);
+    return v;
+  }
+  __device__ __forceinline__ void init(int k0) {
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    sy = bx.mx;
+    sz = (long long)bx.mx * bx.my;
+    hs = 0.5f * s;
+    hxm = i0 > 0;
+    hxp = i0 + 4 < bx.mx;
+    hym = j > 0;
+    hyp = j + 1 < bx.my;
+    const long long c = i0 + sy * j + sz * k0;
+    elo = (k0 > 0) ? ld4(e + c - sz) : z4;
+    ec = ld4(e + c);
+    ehi = (k0 + 1 < bx.mz) ? ld4(e + c + sz) : z4;
+    vlo = (has_x && k0 > 0) ? x4(c - sz, j, k0 - 1) : z4;
+    vc = has_x ? x4(c, j, k0) : z4;
+    vhi = (has_x && k0 + 1 < bx.mz) ? x4(c + sz, j, k0 + 1) : z4;
+    bc = (KIND != SK_MV) ? ld4(b + c) : z4;
+  }
+  // Results of the four cells of plane k (flat index c of cell i0; k1: end of
+  // the block's planes), then the march advances one plane.  Registers hold
+  // planes k-1, k, k+1 of e and x; the loads of plane k+2 (and of b at k+1)
+  // are issued before plane k is computed.
+  __device__ __forceinline__ void plane(int k, int k1, long long c, float r[4]) {
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const bool up = (k + 1 < bx.mz);
     const bool up2 = (k + 2 < bx.mz) && (k + 1 < k1);
     const float4 e2 = up2 ? ld4(e + c + 2 * sz) : z4;
-    const float4 v2 = (has_x && up2) ? ld4(x + c + 2 * sz) : z4;
+    const float4 v2 = (has_x && up2) ? x4(c + 2 * sz, j, k + 2) : z4;
     const float4 bn = (KIND != SK_MV && k + 1 < k1) ? ld4(b + c + sz) : z4;
     const float exm = hxm ? __ldg(e + c - 1) : 0.0f, exp_ = hxp ? __ldg(e + c + 4) : 0.0f;
-    const float vxm = (has_x && hxm) ? __ldg(x + c - 1) : 0.0f, vxp = (has_x && hxp) ? __ldg(x + c + 4) : 0.0f;
+    const float vxm = (has_x && hxm) ? x1(c - 1, i0 - 1, j, k) : 0.0f;
+    const float vxp = (has_x && hxp) ? x1(c + 4, i0 + 4, j, k) : 0.0f;
     const float4 eym = hym ? ld4(e + c - sy) : z4, eyp = hyp ? ld4(e + c + sy) : z4;
-    const float4 vym = (has_x && hym) ? ld4(x + c - sy) : z4, vyp = (has_x && hyp) ? ld4(x + c + sy) : z4;
-    float r[4];
+    const float4 vym = (has_x && hym) ? x4(c - sy, j - 1, k) : z4, vyp = (has_x && hyp) ? x4(c + sy, j + 1, k) : z4;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = i0 + q;
       const float ecq = f4get(ec, q);
-      float d = (i == bx.mx - 1) ? 2.0f * ecq * s : 0.0f;  // outlet: phi = 0 on the face
+      float d = mf_outlet(ecq, s, i == bx.mx - 1);  // outlet: phi = 0 on the face
       float off = 0.0f;
-      if (i + 1 < bx.mx) {
-        const float en = q < 3 ? f4get(ec, q + 1) : exp_;
-        const float a = (ecq + en) * hs;
-        d += a;
-        if (has_x) off += a * (q < 3 ? f4get(vc, q + 1) : vxp);
-      }
-      if (i > 0) {
-        const float en = q > 0 ? f4get(ec, q - 1) : exm;
-        const float a = (ecq + en) * hs;
-        d += a;
-        if (has_x) off += a * (q > 0 ? f4get(vc, q - 1) : vxm);
-      }
-      if (hyp) {
-        const float a = (ecq + f4get(eyp, q)) * hs;
-        d += a;
-        if (has_x) off += a * f4get(vyp, q);
-      }
-      if (hym) {
-        const float a = (ecq + f4get(eym, q)) * hs;
-        d += a;
-        if (has_x) off += a * f4get(vym, q);
-      }
-      if (up) {
-        const float a = (ecq + f4get(ehi, q)) * hs;
-        d += a;
-        off += a * f4get(vhi, q);
-      }
-      if (k > 0) {
-        const float a = (ecq + f4get(elo, q)) * hs;
-        d += a;
-        off += a * f4get(vlo, q);
-      }
-      const float bq = f4get(bc, q), vq = f4get(vc, q);
-      if (KIND == SK_JAC0) {
-        r[q] = __fdividef(omega, d) * bq;
-      } else {
-        const float ax = d * vq - off;
-        if (KIND == SK_JAC)
-          r[q] = vq + __fdividef(omega, d) * (bq - ax);
-        else if (KIND == SK_MV)
-          r[q] = ax;
-        else
-          r[q] = bq - ax;
-      }
+      if (i + 1 < bx.mx)
+        mf_link(ecq, q < 3 ? f4get(ec, q + 1) : exp_, q < 3 ? f4get(vc, q + 1) : vxp, hs, has_x, d, off);
+      if (i > 0) mf_link(ecq, q > 0 ? f4get(ec, q - 1) : exm, q > 0 ? f4get(vc, q - 1) : vxm, hs, has_x, d, off);
+      if (hyp) mf_link(ecq, f4get(eyp, q), f4get(vyp, q), hs, has_x, d, off);
+      if (hym) mf_link(ecq, f4get(eym, q), f4get(vym, q), hs, has_x, d, off);
+      if (up) mf_link(ecq, f4get(ehi, q), f4get(vhi, q), hs, has_x, d, off);
+      if (k > 0) mf_link(ecq, f4get(elo, q), f4get(vlo, q), hs, has_x, d, off);
+      r[q] = mf_result<KIND>(d, off, f4get(vc, q), f4get(bc, q), omega);
     }
-    *reinterpret_cast<float4*>(out + c) = make_float4(r[0], r[1], r[2], r[3]);
     elo = ec;
     ec = ehi;
     ehi = e2;
@@ -433,6 +430,181 @@ __global__ void __launch_bounds__(kThreads) k_stencil_mf4(Box bx, const float* _
     vc = vhi;
     vhi = v2;
     bc = bn;
+  }
+};
+
+template <int KIND, int XS>
+__global__ void __launch_bounds__(kThreads, (KIND == SK_JAC0) ? 4 : 3) k_stencil_mf4(Box bx, const float* __restrict__ e, float s,
+                                                         const float* __restrict__ b, const float* __restrict__ x,
+                                                         float* __restrict__ out, float omega, int zc,
+                                                         const KScal* sc, Box cb, const float* __restrict__ xc,
+                                                         float wc) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  Mf4March<KIND, XS> m;
+  m.i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  m.j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  if (m.i0 >= bx.mx || m.j >= bx.my || k0 >= k1) return;
+  m.bx = bx;
+  m.e = e;
+  m.b = b;
+  m.x = x;
+  m.s = s;
+  m.omega = omega;
+  m.cb = cb;
+  m.xc = xc;
+  m.wc = wc;
+  m.init(k0);
+  long long c = m.i0 + m.sy * m.j + m.sz * k0;
+  for (int k = k0; k < k1; ++k, c += m.sz) {
+    float r[4];
+    m.plane(k, k1, c, r);
+    *reinterpret_cast<float4*>(out + c) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+}
+
+// Residual of the matrix-free fine level fused with its restriction: the
+// residual b - A x of each cell (the row arithmetic of the sweeps) goes
+// straight into the coarse right-hand side bc[I] = sum of its children, added
+// in the order of k_restrict_sum (z pair, then y pair, then x pair), so the
+// result is bit-identical to the two separate passes while the fine residual
+// never reaches memory.  Each thread owns 2 x 2 cells of a plane (x pair, y
+// pair: one aggregate) and marches an even number of planes from an even
+// plane (z pairs).
+__global__ void __launch_bounds__(kThreads, 3) k_resid_restrict_mf22(Box bx, const float* __restrict__ e, float s,
+                                                                 const float* __restrict__ b,
+                                                                 const float* __restrict__ x, Box cb,
+                                                                 float* __restrict__ bcoarse, int zc,
+                                                                 const KScal* sc) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j0 = 2 * (blockIdx.y * blockDim.y + threadIdx.y);
+  const int k0 = blockIdx.z * zc;  // zc even
+  const int k1 = min(k0 + zc, bx.mz);
+  if (i0 >= bx.mx || j0 >= bx.my || k0 >= k1) return;
+  const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+  const float hs = 0.5f * s;
+  const bool row1 = j0 + 1 < bx.my;          // the pair's second row exists
+  const bool hxm = i0 > 0, hxp = i0 + 2 < bx.mx;  // i0 + 1 < mx: mx is even
+  const bool hym = j0 > 0, hyp = j0 + 2 < bx.my;
+  const float2 z2 = make_float2(0.0f, 0.0f);
+  auto ld2 = [](const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); };
+  auto g2 = [](const float2& v, int q) { return q == 0 ? v.x : v.y; };
+  float2 elo[2], ec[2], ehi[2], vlo[2], vc[2], vhi[2], bc[2];
+  long long c = i0 + sy * j0 + sz * k0;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const bool on = (r == 0) || row1;
+    const long long cr = c + r * sy;
+    elo[r] = (on && k0 > 0) ? ld2(e + cr - sz) : z2;
+    ec[r] = on ? ld2(e + cr) : z2;
+    ehi[r] = (on && k0 + 1 < bx.mz) ? ld2(e + cr + sz) : z2;
+    vlo[r] = (on && k0 > 0) ? ld2(x + cr - sz) : z2;
+    vc[r] = on ? ld2(x + cr) : z2;
+    vhi[r] = (on && k0 + 1 < bx.mz) ? ld2(x + cr + sz) : z2;
+    bc[r] = on ? ld2(b + cr) : z2;
+  }
+  float acc = 0.0f;
+  for (int k = k0; k < k1; ++k, c += sz) {
+    const bool up = (k + 1 < bx.mz);
+    const bool up2 = (k + 2 < bx.mz) && (k + 1 < k1);
+    float2 e2[2], v2[2], bn[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const bool on = (r == 0) || row1;
+      const long long cr = c + r * sy;
+      e2[r] = (on && up2) ? ld2(e + cr + 2 * sz) : z2;
+      v2[r] = (on && up2) ? ld2(x + cr + 2 * sz) : z2;
+      bn[r] = (on && k + 1 < k1) ? ld2(b + cr + sz) : z2;
+    }
+    const float2 eym = hym ? ld2(e + c - sy) : z2, vym = hym ? ld2(x + c - sy) : z2;
+    const float2 eyp = (row1 && hyp) ? ld2(e + c + 2 * sy) : z2, vyp = (row1 && hyp) ? ld2(x + c + 2 * sy) : z2;
+    if ((k & 1) == 0) acc = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (r == 1 && !row1) break;
+      const int j = j0 + r;
+      const long long cr = c + r * sy;
+      const float exm = hxm ? __ldg(e + cr - 1) : 0.0f, exp_ = hxp ? __ldg(e + cr + 2) : 0.0f;
+      const float vxm = hxm ? __ldg(x + cr - 1) : 0.0f, vxp = hxp ? __ldg(x + cr + 2) : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int i = i0 + q;
+        const float ecq = g2(ec[r], q);
+        float d = mf_outlet(ecq, s, i == bx.mx - 1);
+        float off = 0.0f;
+        if (i + 1 < bx.mx) mf_link(ecq, q == 0 ? ec[r].y : exp_, q == 0 ? vc[r].y : vxp, hs, true, d, off);
+        if (i > 0) mf_link(ecq, q == 1 ? ec[r].x : exm, q == 1 ? vc[r].x : vxm, hs, true, d, off);
+        if (j + 1 < bx.my) mf_link(ecq, r == 0 ? g2(ec[1], q) : g2(eyp, q), r == 0 ? g2(vc[1], q) : g2(vyp, q), hs,
+                                   true, d, off);
+        if (j > 0) mf_link(ecq, r == 0 ? g2(eym, q) : g2(ec[0], q), r == 0 ? g2(vym, q) : g2(vc[0], q), hs, true, d,
+                           off);
+        if (up) mf_link(ecq, g2(ehi[r], q), g2(vhi[r], q), hs, true, d, off);
+        if (k > 0) mf_link(ecq, g2(elo[r], q), g2(vlo[r], q), hs, true, d, off);
+        acc += mf_result<SK_RES>(d, off, g2(vc[r], q), g2(bc[r], q), 0.0f);
+      }
+    }
+    if ((k & 1) == 1 || k + 1 == bx.mz)
+      bcoarse[(i0 >> 1) + (long long)cb.mx * ((j0 >> 1) + (long long)cb.my * (k >> 1))] = acc;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      elo[r] = ec[r];
+      ec[r] = ehi[r];
+      ehi[r] = e2[r];
+      vlo[r] = vc[r];
+      vc[r] = vhi[r];
+      vhi[r] = v2[r];
+      bc[r] = bn[r];
+    }
+  }
+}
+
+// The same on boxes of one row per plane (the z view of a 2D grid): four x
+// cells per thread, aggregates of an x pair and a z pair.
+__global__ void __launch_bounds__(kThreads) k_resid_restrict_mf4row(Box bx, const float* __restrict__ e, float s,
+                                                                   const float* __restrict__ b,
+                                                                   const float* __restrict__ x, Box cb,
+                                                                   float* __restrict__ bcoarse, int zc,
+                                                                   const KScal* sc) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  Mf4March<SK_RES, XS_PLAIN> m;
+  m.i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  m.j = 0;
+  const int k0 = blockIdx.z * zc;  // zc even
+  const int k1 = min(k0 + zc, bx.mz);
+  if (m.i0 >= bx.mx || bx.my != 1 || k0 >= k1) return;
+  m.bx = bx;
+  m.e = e;
+  m.b = b;
+  m.x = x;
+  m.s = s;
+  m.omega = 0.0f;
+  m.cb = cb;
+  m.xc = nullptr;
+  m.wc = 0.0f;
+  m.init(k0);
+  float sa = 0.0f, sb = 0.0f;  // aggregates i0/2 and i0/2 + 1
+  long long c = m.i0 + m.sz * k0;
+  for (int k = k0; k < k1; ++k, c += m.sz) {
+    float r[4];
+    m.plane(k, k1, c, r);
+    if ((k & 1) == 0) {
+      sa = 0.0f;
+      sb = 0.0f;
+    }
+    sa += r[0];
+    sa += r[1];
+    sb += r[2];
+    sb += r[3];
+    if ((k & 1) == 1 || k + 1 == bx.mz) {
+      const long long pc = (m.i0 >> 1) + (long long)cb.mx * (k >> 1);
+      bcoarse[pc] = sa;
+      bcoarse[pc + 1] = sb;
+    }
   }
 }
 
@@ -473,7 +645,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil_mfc(Box bx, const float* _
       if (j > 0) sum += __ldg(x + c - sy);
       if (k + 1 < bx.mz) sum += vhi;
       if (k > 0) sum += vlo;
-      const float ax = dc * vc + a * sum;
+      const float ax = __fmaf_rn(dc, vc, __fmul_rn(a, sum));  // explicit rounding: the same in every kernel
       if (KIND == SK_JAC)
         out[c] = vc + __fdividef(omega, dc) * (bc - ax);
       else if (KIND == SK_MV)
@@ -518,7 +690,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(Box fb, Box cb, T* __r
   const long long sz = (long long)fb.mx * fb.my, csz = (long long)cb.mx * cb.my;
   long long c = i + (long long)fb.mx * j + sz * k0;
   const long long pc0 = (i >> 1) + (long long)cb.mx * (j >> 1);
-  for (int k = k0; k < k1; ++k, c += sz) x[c] += wc * __ldg(ec + pc0 + csz * (k >> 1));
+  for (int k = k0; k < k1; ++k, c += sz) x[c] = fma(wc, __ldg(ec + pc0 + csz * (k >> 1)), x[c]);
 }
 
 // Restriction of a fine residual: bc[I] = sum of its (up to 8) children.
@@ -629,13 +801,14 @@ __global__ void k_pcg_p(long long n, const T* __restrict__ z, T* __restrict__ p,
         p4[v] = zv;
       } else {
         const float4 pv = p4[v];
-        p4[v] = make_float4(zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, zv.w + beta * pv.w);
+        p4[v] = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y), fmaf(beta, pv.z, zv.z),
+                            fmaf(beta, pv.w, zv.w));
       }
     }
     c0 = n4 << 2;
   }
   for (long long c = c0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-    p[c] = first ? __ldg(z + c) : __ldg(z + c) + beta * p[c];
+    p[c] = first ? __ldg(z + c) : fma(beta, p[c], __ldg(z + c));
 }
 
 // FP64 true residual (see k_outer_residual) in the 2.5D form.
@@ -732,7 +905,7 @@ static ZCfg zcfg_mf4(Box b) {
   return zcfg_tile(q, (b.my == 1) ? 256 : 32, 4096, 1);
 }
 // Process-wide switch of the four-cells-per-thread matrix-free sweeps
-// (vos_set_sweep_width; results are identical either way).
+// (vos_set_vector_sweeps; results are identical either way).
 bool g_mf4 = true;
 
 // ---------------------------------------------------------------------------
@@ -979,14 +1152,10 @@ __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restri
            v += (long long)gridDim.x * blockDim.x) {
         const float4 pv = __ldg((const float4*)p + v), qv4 = __ldg((const float4*)qv + v);
         float4 ev = ((float4*)e)[v], rv = ((float4*)r)[v];
-        ev.x += alpha * pv.x;
-        ev.y += alpha * pv.y;
-        ev.z += alpha * pv.z;
-        ev.w += alpha * pv.w;
-        rv.x -= alpha * qv4.x;
-        rv.y -= alpha * qv4.y;
-        rv.z -= alpha * qv4.z;
-        rv.w -= alpha * qv4.w;
+        ev = make_float4(fmaf(alpha, pv.x, ev.x), fmaf(alpha, pv.y, ev.y), fmaf(alpha, pv.z, ev.z),
+                         fmaf(alpha, pv.w, ev.w));
+        rv = make_float4(fmaf(-alpha, qv4.x, rv.x), fmaf(-alpha, qv4.y, rv.y), fmaf(-alpha, qv4.z, rv.z),
+                         fmaf(-alpha, qv4.w, rv.w));
         ((float4*)e)[v] = ev;
         ((float4*)r)[v] = rv;
         ps.add(rv.x, rv.x);
@@ -998,8 +1167,8 @@ __global__ void k_pcg_xr(long long n, const T* __restrict__ p, const T* __restri
     }
   }
   for (long long c = c0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    e[c] += alpha * p[c];
-    T rc = r[c] - alpha * qv[c];
+    e[c] = fma(alpha, p[c], e[c]);
+    T rc = fma(-alpha, qv[c], r[c]);
     r[c] = rc;
     ps.add(rc, rc);
     if (dscale) {
@@ -1046,7 +1215,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec_mfc_dot(Box bx, const float
       if (j > 0) sum += __ldg(x + c - sy);
       if (k + 1 < bx.mz) sum += vhi;
       if (k > 0) sum += vlo;
-      const float ax = dc * vc + a * sum;
+      const float ax = __fmaf_rn(dc, vc, __fmul_rn(a, sum));  // explicit rounding: the same in every kernel
       out[c] = ax;
       ps.add(vc, ax);
       vlo = vc;
@@ -1096,39 +1265,15 @@ __global__ void __launch_bounds__(kThreads) k_matvec_mf_dot(Box bx, const float*
       const bool up2 = (k + 2 < bx.mz) && (k + 1 < k1);
       const float e2 = up2 ? __ldg(e + c + 2 * sz) : 0.0f;
       const float v2 = up2 ? __ldg(x + c + 2 * sz) : 0.0f;
-      float d = (i == bx.mx - 1) ? 2.0f * ec * s : 0.0f;
+      float d = mf_outlet(ec, s, i == bx.mx - 1);
       float off = 0.0f;
-      if (i + 1 < bx.mx) {
-        const float a = (ec + __ldg(e + c + 1)) * hs;
-        d += a;
-        off += a * __ldg(x + c + 1);
-      }
-      if (i > 0) {
-        const float a = (ec + __ldg(e + c - 1)) * hs;
-        d += a;
-        off += a * __ldg(x + c - 1);
-      }
-      if (j + 1 < bx.my) {
-        const float a = (ec + __ldg(e + c + sy)) * hs;
-        d += a;
-        off += a * __ldg(x + c + sy);
-      }
-      if (j > 0) {
-        const float a = (ec + __ldg(e + c - sy)) * hs;
-        d += a;
-        off += a * __ldg(x + c - sy);
-      }
-      if (k + 1 < bx.mz) {
-        const float a = (ec + ehi) * hs;
-        d += a;
-        off += a * vhi;
-      }
-      if (k > 0) {
-        const float a = (ec + elo) * hs;
-        d += a;
-        off += a * vlo;
-      }
-      const float ax = d * vc - off;
+      if (i + 1 < bx.mx) mf_link(ec, __ldg(e + c + 1), __ldg(x + c + 1), hs, true, d, off);
+      if (i > 0) mf_link(ec, __ldg(e + c - 1), __ldg(x + c - 1), hs, true, d, off);
+      if (j + 1 < bx.my) mf_link(ec, __ldg(e + c + sy), __ldg(x + c + sy), hs, true, d, off);
+      if (j > 0) mf_link(ec, __ldg(e + c - sy), __ldg(x + c - sy), hs, true, d, off);
+      if (k + 1 < bx.mz) mf_link(ec, ehi, vhi, hs, true, d, off);
+      if (k > 0) mf_link(ec, elo, vlo, hs, true, d, off);
+      const float ax = mf_result<SK_MV>(d, off, vc, 0.0f, 0.0f);
       out[c] = ax;
       ps.add(vc, ax);
       elo = ec;
@@ -1207,7 +1352,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec_mfc4_dot(Box bx, const floa
         if (k + 1 < bx.mz) sum += f4get(vhi, q);
         if (k > 0) sum += f4get(vlo, q);
         const float vq = f4get(vc, q);
-        r[q] = f4get(dc, q) * vq + a * sum;
+        r[q] = __fmaf_rn(f4get(dc, q), vq, __fmul_rn(a, sum));
         ps.add(vq, r[q]);
       }
       *reinterpret_cast<float4*>(out + c) = make_float4(r[0], r[1], r[2], r[3]);
@@ -1221,11 +1366,121 @@ __global__ void __launch_bounds__(kThreads) k_matvec_mfc4_dot(Box bx, const floa
   if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_alpha(sc, acc[0]);
 }
 
-__global__ void __launch_bounds__(kThreads) k_matvec_mf4_dot(Box bx, const float* __restrict__ e, float s,
+__global__ void __launch_bounds__(kThreads, 4) k_matvec_mf4_dot(Box bx, const float* __restrict__ e, float s,
                                                             const float* __restrict__ x, float* __restrict__ out,
                                                             int zc, KScal* sc, RedScratch rs) {
   VOS_COUNT_EXEC();
   DONE_RETURN(sc);
+  Mf4March<SK_MV, XS_PLAIN> m;
+  m.i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  m.j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  PSum<float> ps;
+  if (m.i0 < bx.mx && m.j < bx.my && k0 < k1) {
+    m.bx = bx;
+    m.e = e;
+    m.b = nullptr;
+    m.x = x;
+    m.s = s;
+    m.omega = 0.0f;
+    m.cb = bx;
+    m.xc = nullptr;
+    m.wc = 0.0f;
+      m.init(k0);
+    long long c = m.i0 + m.sy * m.j + m.sz * k0;
+    for (int k = k0; k < k1; ++k, c += m.sz) {
+      const float4 pc = m.vc;
+      float r[4];
+      m.plane(k, k1, c, r);
+      *reinterpret_cast<float4*>(out + c) = make_float4(r[0], r[1], r[2], r[3]);
+      ps.add(pc.x, r[0]);
+      ps.add(pc.y, r[1]);
+      ps.add(pc.z, r[2]);
+      ps.add(pc.w, r[3]);
+    }
+  }
+  double acc[1] = {ps.get()};
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_alpha(sc, acc[0]);
+}
+
+
+// ---------------------------------------------------------------------------
+// Diagonally preconditioned CG on a constant-link operator in two kernels per
+// iteration instead of four (direction update, matvec with p.q, x/r update,
+// preconditioner with r.z):
+//   k_pcg_pmv_mfc*: p = z + beta p_prev (p = z on the first iteration),
+//                   q = A p and p.q (alpha = r.z / p.q);
+//   k_pcg_xrz:      e += alpha p, r -= alpha q, z = (omega / diag) r, with
+//                   r.r, r.z and z.z (beta = r.z / r.z_prev; the pass ends
+//                   on z.z, the scaled norm of the FP64 refinement test).
+// The matvec needs p at the six neighbours, so the direction update is
+// evaluated there too, from z and p_prev; p_prev and the p written are two
+// buffers.  Each value is computed with the operations (and each dot summed
+// in the order) of the four-kernel form, so both give identical iterates.
+// DRAM words per unknown: 5 (read z, p_prev, diagonal; write p, q) and 8
+// (read p, q, e, r, omega / diagonal; write e, r, z), against 16 for the
+// four-kernel iteration.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float pnew(float z, float pp, float beta, bool first) {
+  return first ? z : __fmaf_rn(beta, pp, z);
+}
+
+__global__ void __launch_bounds__(kThreads) k_pcg_pmv_mfc(Box bx, const float* __restrict__ dg, float a,
+                                                         const float* __restrict__ z, const float* __restrict__ pprev,
+                                                         float* __restrict__ pout, float* __restrict__ q, int zc,
+                                                         KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const bool first = (sc->iters == 0);
+  const float beta = first ? 0.0f : (float)sc->beta;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  PSum<float> ps;
+  if (i < bx.mx && j < bx.my && k0 < k1) {
+    const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+    auto pv = [&](long long c) { return pnew(__ldg(z + c), first ? 0.0f : __ldg(pprev + c), beta, first); };
+    long long c = i + sy * j + sz * k0;
+    float vlo = (k0 > 0) ? pv(c - sz) : 0.0f;
+    float vc = pv(c);
+    float vhi = (k0 + 1 < bx.mz) ? pv(c + sz) : 0.0f;
+    float dc = __ldg(dg + c);
+    for (int k = k0; k < k1; ++k, c += sz) {
+      const bool nxt = k + 1 < k1;
+      const float v2 = (nxt && k + 2 < bx.mz) ? pv(c + 2 * sz) : 0.0f;
+      const float dn = nxt ? __ldg(dg + c + sz) : 0.0f;
+      float sum = 0.0f;
+      if (i + 1 < bx.mx) sum += pv(c + 1);
+      if (i > 0) sum += pv(c - 1);
+      if (j + 1 < bx.my) sum += pv(c + sy);
+      if (j > 0) sum += pv(c - sy);
+      if (k + 1 < bx.mz) sum += vhi;
+      if (k > 0) sum += vlo;
+      const float ax = __fmaf_rn(dc, vc, __fmul_rn(a, sum));  // explicit rounding: the same in every kernel
+      pout[c] = vc;
+      q[c] = ax;
+      ps.add(vc, ax);
+      vlo = vc;
+      vc = vhi;
+      vhi = v2;
+      dc = dn;
+    }
+  }
+  double acc[1] = {ps.get()};
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_alpha(sc, acc[0]);
+}
+
+// The same, four consecutive x cells per thread (nx % 4 == 0: 16-byte rows).
+__global__ void __launch_bounds__(kThreads) k_pcg_pmv_mfc4(Box bx, const float* __restrict__ dg, float a,
+                                                          const float* __restrict__ z,
+                                                          const float* __restrict__ pprev, float* __restrict__ pout,
+                                                          float* __restrict__ q, int zc, KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const bool first = (sc->iters == 0);
+  const float beta = first ? 0.0f : (float)sc->beta;
   const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k0 = blockIdx.z * zc;
@@ -1233,77 +1488,109 @@ __global__ void __launch_bounds__(kThreads) k_matvec_mf4_dot(Box bx, const float
   PSum<float> ps;
   if (i0 < bx.mx && j < bx.my && k0 < k1) {
     const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
-    const float hs = 0.5f * s;
     const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     auto ld4 = [](const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); };
+    auto pv = [&](long long c) { return pnew(__ldg(z + c), first ? 0.0f : __ldg(pprev + c), beta, first); };
+    auto pv4 = [&](long long c) {
+      const float4 zv = ld4(z + c);
+      const float4 pp = first ? z4 : ld4(pprev + c);
+      return make_float4(pnew(zv.x, pp.x, beta, first), pnew(zv.y, pp.y, beta, first), pnew(zv.z, pp.z, beta, first),
+                         pnew(zv.w, pp.w, beta, first));
+    };
     const bool hxm = i0 > 0, hxp = i0 + 4 < bx.mx, hym = j > 0, hyp = j + 1 < bx.my;
     long long c = i0 + sy * j + sz * k0;
-    float4 elo = (k0 > 0) ? ld4(e + c - sz) : z4;
-    float4 ec = ld4(e + c);
-    float4 ehi = (k0 + 1 < bx.mz) ? ld4(e + c + sz) : z4;
-    float4 vlo = (k0 > 0) ? ld4(x + c - sz) : z4;
-    float4 vc = ld4(x + c);
-    float4 vhi = (k0 + 1 < bx.mz) ? ld4(x + c + sz) : z4;
+    float4 vlo = (k0 > 0) ? pv4(c - sz) : z4;
+    float4 vc = pv4(c);
+    float4 vhi = (k0 + 1 < bx.mz) ? pv4(c + sz) : z4;
+    float4 dc = ld4(dg + c);
     for (int k = k0; k < k1; ++k, c += sz) {
-      const bool up2 = (k + 2 < bx.mz) && (k + 1 < k1);
-      const float4 e2 = up2 ? ld4(e + c + 2 * sz) : z4;
-      const float4 v2 = up2 ? ld4(x + c + 2 * sz) : z4;
-      const float exm = hxm ? __ldg(e + c - 1) : 0.0f, exp_ = hxp ? __ldg(e + c + 4) : 0.0f;
-      const float vxm = hxm ? __ldg(x + c - 1) : 0.0f, vxp = hxp ? __ldg(x + c + 4) : 0.0f;
-      const float4 eym = hym ? ld4(e + c - sy) : z4, eyp = hyp ? ld4(e + c + sy) : z4;
-      const float4 vym = hym ? ld4(x + c - sy) : z4, vyp = hyp ? ld4(x + c + sy) : z4;
-      float r[4];
+      const bool nxt = k + 1 < k1;
+      const float4 v2 = (nxt && k + 2 < bx.mz) ? pv4(c + 2 * sz) : z4;
+      const float4 dn = nxt ? ld4(dg + c + sz) : z4;
+      const float vxm = hxm ? pv(c - 1) : 0.0f, vxp = hxp ? pv(c + 4) : 0.0f;
+      const float4 vym = hym ? pv4(c - sy) : z4, vyp = hyp ? pv4(c + sy) : z4;
+      float res[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = i0 + q;
-        const float ecq = f4get(ec, q);
-        float d = (i == bx.mx - 1) ? 2.0f * ecq * s : 0.0f;
-        float off = 0.0f;
-        if (i + 1 < bx.mx) {
-          const float a = (ecq + (q < 3 ? f4get(ec, q + 1) : exp_)) * hs;
-          d += a;
-          off += a * (q < 3 ? f4get(vc, q + 1) : vxp);
-        }
-        if (i > 0) {
-          const float a = (ecq + (q > 0 ? f4get(ec, q - 1) : exm)) * hs;
-          d += a;
-          off += a * (q > 0 ? f4get(vc, q - 1) : vxm);
-        }
-        if (hyp) {
-          const float a = (ecq + f4get(eyp, q)) * hs;
-          d += a;
-          off += a * f4get(vyp, q);
-        }
-        if (hym) {
-          const float a = (ecq + f4get(eym, q)) * hs;
-          d += a;
-          off += a * f4get(vym, q);
-        }
-        if (k + 1 < bx.mz) {
-          const float a = (ecq + f4get(ehi, q)) * hs;
-          d += a;
-          off += a * f4get(vhi, q);
-        }
-        if (k > 0) {
-          const float a = (ecq + f4get(elo, q)) * hs;
-          d += a;
-          off += a * f4get(vlo, q);
-        }
-        const float vq = f4get(vc, q);
-        r[q] = d * vq - off;
-        ps.add(vq, r[q]);
+      for (int t = 0; t < 4; ++t) {
+        const int i = i0 + t;
+        float sum = 0.0f;
+        if (i + 1 < bx.mx) sum += t < 3 ? f4get(vc, t + 1) : vxp;
+        if (i > 0) sum += t > 0 ? f4get(vc, t - 1) : vxm;
+        if (hyp) sum += f4get(vyp, t);
+        if (hym) sum += f4get(vym, t);
+        if (k + 1 < bx.mz) sum += f4get(vhi, t);
+        if (k > 0) sum += f4get(vlo, t);
+        const float vt = f4get(vc, t);
+        res[t] = __fmaf_rn(f4get(dc, t), vt, __fmul_rn(a, sum));
+        ps.add(vt, res[t]);
       }
-      *reinterpret_cast<float4*>(out + c) = make_float4(r[0], r[1], r[2], r[3]);
-      elo = ec;
-      ec = ehi;
-      ehi = e2;
+      *reinterpret_cast<float4*>(pout + c) = vc;
+      *reinterpret_cast<float4*>(q + c) = make_float4(res[0], res[1], res[2], res[3]);
       vlo = vc;
       vc = vhi;
       vhi = v2;
+      dc = dn;
     }
   }
   double acc[1] = {ps.get()};
   if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) fin_alpha(sc, acc[0]);
+}
+
+__global__ void k_pcg_xrz(long long n, const float* __restrict__ p, const float* __restrict__ qv, float* __restrict__ e,
+                          float* __restrict__ r, const float* __restrict__ dinv, float* __restrict__ z, KScal* sc,
+                          RedScratch rs) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const float alpha = (float)sc->alpha;
+  PSum<float> prr, prz, pzz;
+  const long long n4 = n >> 2;  // 16-byte accesses (vectors are 256-byte aligned)
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n4; v += (long long)gridDim.x * blockDim.x) {
+    const float4 pv = __ldg((const float4*)p + v), q4 = __ldg((const float4*)qv + v);
+    const float4 dv = __ldg((const float4*)dinv + v);
+    float4 ev = ((float4*)e)[v], rv = ((float4*)r)[v];
+    ev = make_float4(__fmaf_rn(alpha, pv.x, ev.x), __fmaf_rn(alpha, pv.y, ev.y), __fmaf_rn(alpha, pv.z, ev.z),
+                     __fmaf_rn(alpha, pv.w, ev.w));
+    rv = make_float4(__fmaf_rn(-alpha, q4.x, rv.x), __fmaf_rn(-alpha, q4.y, rv.y), __fmaf_rn(-alpha, q4.z, rv.z),
+                     __fmaf_rn(-alpha, q4.w, rv.w));
+    const float4 zv = make_float4(dv.x * rv.x, dv.y * rv.y, dv.z * rv.z, dv.w * rv.w);
+    ((float4*)e)[v] = ev;
+    ((float4*)r)[v] = rv;
+    ((float4*)z)[v] = zv;
+    prr.add(rv.x, rv.x);
+    prr.add(rv.y, rv.y);
+    prr.add(rv.z, rv.z);
+    prr.add(rv.w, rv.w);
+    prz.add(rv.x, zv.x);
+    prz.add(rv.y, zv.y);
+    prz.add(rv.z, zv.z);
+    prz.add(rv.w, zv.w);
+    pzz.add(zv.x, zv.x);
+    pzz.add(zv.y, zv.y);
+    pzz.add(zv.z, zv.z);
+    pzz.add(zv.w, zv.w);
+  }
+  for (long long c = (n4 << 2) + (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    e[c] = __fmaf_rn(alpha, p[c], e[c]);
+    const float rc = __fmaf_rn(-alpha, qv[c], r[c]);
+    r[c] = rc;
+    const float zc = dinv[c] * rc;
+    z[c] = zc;
+    prr.add(rc, rc);
+    prz.add(rc, zc);
+    pzz.add(zc, zc);
+  }
+  double acc[3] = {prr.get(), prz.get(), pzz.get()};
+  if (grid_sum<3>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    sc->rr = acc[0];
+    sc->iters += 1;
+    if (sc->iters >= sc->max_iters || !isfinite(acc[0])) {
+      sc->done = 1;
+    } else {
+      fin_pcg_beta(sc, acc[1]);
+      if (acc[2] <= sc->tol2s) sc->done = 1;
+    }
+  }
 }
 
 // BiCGStab: p = r + beta (p - omega v)   (first iteration: p = r)
@@ -1717,17 +2004,17 @@ static void stencil_launch(const char* name, int kind, const Op<T>& A, const T* 
       if (g_mf4 && Z.box.mx % 4 == 0) {  // 16-byte rows: four cells per thread
         const ZCfg z4 = zcfg_mf4(Z.box);
         if (kind == SK_JAC)
-          vlaunch(name, words * n * 4.0, k_stencil_mf4<SK_JAC>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, bb, xx,
-                  oo, om, z4.zc, sc);
+          vlaunch(name, words * n * 4.0, k_stencil_mf4<SK_JAC, XS_PLAIN>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, bb,
+                  xx, oo, om, z4.zc, sc, Box{0, 0, 0}, (const float*)nullptr, 0.0f);
         else if (kind == SK_MV)
-          vlaunch(name, words * n * 4.0, k_stencil_mf4<SK_MV>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, bb, xx,
-                  oo, om, z4.zc, sc);
+          vlaunch(name, words * n * 4.0, k_stencil_mf4<SK_MV, XS_PLAIN>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, bb,
+                  xx, oo, om, z4.zc, sc, Box{0, 0, 0}, (const float*)nullptr, 0.0f);
         else if (kind == SK_RES)
-          vlaunch(name, words * n * 4.0, k_stencil_mf4<SK_RES>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, bb, xx,
-                  oo, om, z4.zc, sc);
+          vlaunch(name, words * n * 4.0, k_stencil_mf4<SK_RES, XS_PLAIN>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, bb,
+                  xx, oo, om, z4.zc, sc, Box{0, 0, 0}, (const float*)nullptr, 0.0f);
         else
-          vlaunch(name, words * n * 4.0, k_stencil_mf4<SK_JAC0>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, bb, xx,
-                  oo, om, z4.zc, sc);
+          vlaunch(name, words * n * 4.0, k_stencil_mf4<SK_JAC0, XS_PLAIN>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, bb,
+                  xx, oo, om, z4.zc, sc, Box{0, 0, 0}, (const float*)nullptr, 0.0f);
         return;
       }
       if (kind == SK_JAC)
@@ -1771,6 +2058,16 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
       x = h.lev[l].x;
       t = h.lev[l].t;
     }
+  };
+  // The matrix-free FP32 fine level with four-cell rows fuses its residual
+  // with the restriction and its prolongation with the first post-smoothing
+  // sweep (bit-identical to the separate passes).
+  auto fused_fine = [&](int l) {
+    if constexpr (sizeof(T) == 4 && SYM) {
+      const Op<T>& A = h.lev[l].op;
+      return l == 0 && A.mfe != nullptr && g_mf4 && zview(A).box.mx % 4 == 0 && l + 1 < L;
+    }
+    return false;
   };
   auto jac0 = [&](int l, T* dst) {
     const Op<T>& A = h.lev[l].op;
@@ -1822,10 +2119,34 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
       oth = tmp;
     }
     pre[l] = cur;
-    stencil_launch<T, SYM>(KN("mg_resid", l == 0), SK_RES, A, b, cur, oth, om, sc, st);
     const Op<T>& C = h.lev[l + 1].op;
-    vlaunch(KN("mg_restrict", l == 0), (ncell(A) + ncell(C)) * sizeof(T), k_restrict_sum<T>, grid_for(C.box, 0),
-            kThreads, st, A.box, C.box, (const T*)oth, h.lev[l + 1].b, (const KScal*)sc);
+    if (fused_fine(l)) {
+      const Op<T> Z = zview(A);
+      const double rb = (3.0 * ncell(A) + ncell(C)) * 4.0;
+      // an even number of planes per block, from an even plane
+      auto even = [&](ZCfg z) {
+        if (z.zc & 1) {
+          z.zc += 1;
+          z.grid.z = (unsigned)((Z.box.mz + z.zc - 1) / z.zc);
+        }
+        return z;
+      };
+      if (Z.box.my == 1) {
+        const ZCfg z = even(zcfg_mf4(Z.box));
+        vlaunch("mg_resid_restrict_mf_f32_L0", rb, k_resid_restrict_mf4row, z.grid, z.block, st, Z.box, A.mfe,
+                A.mfs, (const float*)b, (const float*)cur, zbox(C.box), (float*)h.lev[l + 1].b, z.zc,
+                (const KScal*)sc);
+      } else {  // 2 x 2 cells per thread
+        const ZCfg z = even(zcfg_tile(Box{(Z.box.mx + 1) / 2, (Z.box.my + 1) / 2, Z.box.mz}, 32, 4096, 2));
+        vlaunch("mg_resid_restrict_mf_f32_L0", rb, k_resid_restrict_mf22, z.grid, z.block, st, Z.box, A.mfe,
+                A.mfs, (const float*)b, (const float*)cur, zbox(C.box), (float*)h.lev[l + 1].b, z.zc,
+                (const KScal*)sc);
+      }
+    } else {
+      stencil_launch<T, SYM>(KN("mg_resid", l == 0), SK_RES, A, b, cur, oth, om, sc, st);
+      vlaunch(KN("mg_restrict", l == 0), (ncell(A) + ncell(C)) * sizeof(T), k_restrict_sum<T>, grid_for(C.box, 0),
+              kThreads, st, A.box, C.box, (const T*)oth, h.lev[l + 1].b, (const KScal*)sc);
+    }
   }
   if (ts < L) {
     tail_launch<T, SYM>(h, ts, sc, st);
@@ -1842,10 +2163,23 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     T* cur = pre[l];
     T* oth = (cur == x) ? t : x;
     const Box fz = zbox(A.box), cz = zbox(h.lev[l + 1].op.box);
-    const ZCfg zc = zcfg_sweep(fz);
-    vlaunch(KN("mg_prolong", l == 0), (2.0 * ncell(A) + ncell(h.lev[l + 1].op)) * sizeof(T), k_prolong_add<T>,
-            zc.grid, zc.block, st, fz, cz, cur, (const T*)h.lev[l + 1].x, wc, zc.zc, (const KScal*)sc);
-    for (int s = 0; s < nu; ++s) {
+    int s0 = 0;
+    if (fused_fine(l)) {  // first sweep on x + wc P x_coarse, formed on the fly
+      const Op<T> Z = zview(A);
+      const ZCfg z4 = zcfg_mf4(Z.box);
+      vlaunch("mg_jac_pro_mf_f32_L0", (4.0 * ncell(A) + ncell(h.lev[l + 1].op)) * 4.0, k_stencil_mf4<SK_JAC, XS_PRO>,
+              z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, (const float*)b, (const float*)cur, (float*)oth, (float)om,
+              z4.zc, (const KScal*)sc, cz, (const float*)h.lev[l + 1].x, (float)wc);
+      T* tmp = cur;
+      cur = oth;
+      oth = tmp;
+      s0 = 1;
+    } else {
+      const ZCfg zc = zcfg_sweep(fz);
+      vlaunch(KN("mg_prolong", l == 0), (2.0 * ncell(A) + ncell(h.lev[l + 1].op)) * sizeof(T), k_prolong_add<T>,
+              zc.grid, zc.block, st, fz, cz, cur, (const T*)h.lev[l + 1].x, wc, zc.zc, (const KScal*)sc);
+    }
+    for (int s = s0; s < nu; ++s) {
       stencil_launch<T, SYM>(KN("mg_jac", l == 0), SK_JAC, A, b, cur, oth, om, sc, st);
       T* tmp = cur;
       cur = oth;
@@ -1898,12 +2232,37 @@ static void pcg_precond(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w
   }
 }
 
-// One PCG iteration (kernels early-exit once the solve is done).
+// Process-wide switch of the two-kernel diagonal PCG iteration on
+// constant-link operators (vos_set_fused_pcg).
+bool g_fused_pcg = true;
+
+// One PCG iteration (kernels early-exit once the solve is done).  parity:
+// the iteration's index within its pass modulo 2 (the two-kernel diagonal
+// iteration alternates its two direction buffers, k.p and k.s, by it).
 template <typename T, bool SYM>
 static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w, const RedScratch& rs,
-                          cudaStream_t st, bool use_mg, bool use_net = false) {
+                          cudaStream_t st, bool use_mg, bool use_net = false, int parity = 0) {
   const Op<T>& A = h.lev[0].op;
   const int gf = flat_grid(n);
+  if constexpr (sizeof(T) == 4 && SYM) {
+    if (g_fused_pcg && A.mfc != 0.0f && !use_mg && !use_net) {
+      const Op<T> Z = zview(A);
+      const float* pin = (const float*)(parity ? k.s : k.p);
+      float* pout = (float*)(parity ? k.p : k.s);
+      if (Z.box.mx % 4 == 0) {  // same shape as the four-kernel matvec: the same summation order
+        const ZCfg z = zcfg_mf4(Z.box);
+        vlaunch("pcg_pmv_mfc_f32_L0", 5.0 * n * 4.0, k_pcg_pmv_mfc4, z.grid, z.block, st, Z.box,
+                (const float*)Z.diag, A.mfc, (const float*)k.z, pin, pout, (float*)k.q, z.zc, w->sc, rs);
+      } else {
+        const ZCfg z = zcfg(Z.box);
+        vlaunch("pcg_pmv_mfc_f32_L0", 5.0 * n * 4.0, k_pcg_pmv_mfc, z.grid, z.block, st, Z.box, (const float*)Z.diag,
+                A.mfc, (const float*)k.z, pin, pout, (float*)k.q, z.zc, w->sc, rs);
+      }
+      vlaunch("pcg_xrz_f32_L0", 8.0 * n * 4.0, k_pcg_xrz, gf, kThreads, st, n, (const float*)pout,
+              (const float*)k.q, (float*)k.e, (float*)k.r, (const float*)A.dinv, (float*)k.z, w->sc, rs);
+      return;
+    }
+  }
   vlaunch(KN("pcg_p", true), 3.0 * n * sizeof(T), k_pcg_p<T>, gf, kThreads, st, n, (const T*)k.z, k.p,
           (const KScal*)w->sc);
   bool fused_mv = false;
@@ -2001,7 +2360,7 @@ static int inner_pcg(Hier<T>& h, SolverWork* w, double rtol_inner, int max_iters
   int slow = 0;
   if (stagnated) *stagnated = false;
   while (true) {
-    for (int c = 0; c < chunk; ++c) pcg_iteration<T, SYM>(h, k, n, w, rs, st, use_mg, use_net);
+    for (int c = 0; c < chunk; ++c) pcg_iteration<T, SYM>(h, k, n, w, rs, st, use_mg, use_net, c & 1);
     it += chunk;
     cudaMemcpyAsync(w->sc_host, w->sc, sizeof(KScal), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -2238,7 +2597,7 @@ cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, V
     }
     VOS_CUDA_TRY(begin_while(s1, hi, s2));
     if (sym) {
-      for (int c = 0; c < 2; ++c) pcg_iteration<T, true>(h, k, n, w, rs, s2, use_mg);
+      for (int c = 0; c < 2; ++c) pcg_iteration<T, true>(h, k, n, w, rs, s2, use_mg, false, c);
     } else {
       bicg_iteration<T, false>(h, k, n, w, rs, s2);
     }
@@ -2366,7 +2725,7 @@ int residual_snapshots(const Op<double>& op64, Hier<T>& h, const double* b, View
   vlaunch("kscal_init", 0.0, k_kscal_init, 1, 32, st, w->sc, w->outer, 1e-30, maxit + 1, 0);
   pcg_precond<T, true>(h, k, n, w, rs, st, true, false);
   for (int it = 0; it <= maxit; ++it) {
-    if (it > 0) pcg_iteration<T, true>(h, k, n, w, rs, st, true, false);
+    if (it > 0) pcg_iteration<T, true>(h, k, n, w, rs, st, true, false, (it - 1) & 1);
     for (int i = 0; i < count; ++i)
       if (iters[i] == it)
         vlaunch("to_float", 0.0, k_to_float<T>, flat_grid(n), kThreads, st, n, (const T*)k.r, out + (long long)i * n);

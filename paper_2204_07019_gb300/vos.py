@@ -20,7 +20,7 @@ __all__ = [
     "VosError", "load_library", "vos_create", "vos_step", "vos_fields", "vos_set_fields",
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_upscaled", "vos_last_error", "vos_destroy",
     "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_set_coarse_cycle", "vos_set_vector_sweeps",
-    "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
+    "vos_set_fused_pcg", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
     "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16", "UNet", "vos_set_unet_preconditioner",
     "vos_unet_solve_stats", "vos_pressure_snapshots", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
@@ -41,8 +41,8 @@ PRECOND_U_EXTRAP = 16
 EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
     "vos_get_stats", "vos_suggest_dt", "vos_upscaled", "vos_last_error", "vos_destroy", "vos_device_bytes",
-    "vos_kernel_launches", "vos_set_launch_mode", "vos_set_coarse_cycle", "vos_set_vector_sweeps", "vos_prof_enable",
-    "vos_prof_report",
+    "vos_kernel_launches", "vos_set_launch_mode", "vos_set_coarse_cycle", "vos_set_vector_sweeps", "vos_set_fused_pcg",
+    "vos_prof_enable", "vos_prof_report",
     "vos_prof_reset", "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle",
     "vos_batch_destroy",
     "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16",
@@ -150,6 +150,8 @@ def load_library(path=None):
     lib.vos_set_coarse_cycle.restype = ctypes.c_int
     lib.vos_set_vector_sweeps.argtypes = [ctypes.c_int]
     lib.vos_set_vector_sweeps.restype = ctypes.c_int
+    lib.vos_set_fused_pcg.argtypes = [ctypes.c_int]
+    lib.vos_set_fused_pcg.restype = ctypes.c_int
     lib.vos_prof_enable.argtypes = [ctypes.c_char_p]
     lib.vos_prof_enable.restype = ctypes.c_int
     lib.vos_prof_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -664,6 +666,14 @@ def vos_set_vector_sweeps(on):
     """1 (default): four-cells-per-thread matrix-free pressure sweeps when nx
     is a multiple of 4; 0: one cell per thread (identical results)."""
     load_library().vos_set_vector_sweeps(1 if on else 0)
+
+
+def vos_set_fused_pcg(on):
+    """1 (default): diagonally preconditioned CG on constant-link FP32
+    operators in two kernels per iteration (z formed on the fly); 0: four
+    kernels per iteration.  Set before the handle's first step (a captured
+    step graph keeps its form)."""
+    load_library().vos_set_fused_pcg(1 if on else 0)
 
 
 def vos_set_coarse_cycle(on):

@@ -64,13 +64,15 @@ def test_2d_tiles(V):
         V.vos_destroy(h)
 
 
-@pytest.mark.parametrize("shape", [(24, 20, 36), (1, 96, 160), (10, 14, 30)])
+@pytest.mark.parametrize("shape", [(24, 20, 36), (15, 13, 36), (1, 96, 160), (1, 97, 160), (10, 14, 30)])
 def test_vector_sweeps_identical(V, shape):
     """The four-cells-per-thread matrix-free pressure sweeps (16-byte rows,
     nx % 4 == 0) compute each cell with the arithmetic of the one-cell
-    kernel: whole mixed-precision steps give identical fields and iteration
-    counts, graph launches; a grid with nx % 4 != 0 (30) keeps the one-cell
-    kernel."""
+    kernel, and their fused residual-restriction and prolongation-sweep
+    passes sum and round as the separate passes do: whole mixed-precision
+    steps give identical fields and iteration counts, graph launches (odd
+    ny and nz: y pairs and z pairs without a partner); a grid with
+    nx % 4 != 0 (30) keeps the one-cell kernel."""
     if shape[0] == 1:
         es = I.disc_micromodel_2d(shape[2], shape[1], seed=2, rmin=5, rmax=12, target_porosity=0.6)
     else:
