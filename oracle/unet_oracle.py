@@ -164,8 +164,9 @@ def backward(P, C, dz, bf16_emulation=False):
     """Gradients of sum(dz * z) for every parameter (same keys as P).
 
     With BF16 emulation the upstream gradient of each conv is rounded to
-    BF16 before the data-gradient convolution (the tensor-core path takes
-    BF16 operands); weight and bias gradients use it unrounded."""
+    BF16 before the data-gradient convolution and the weight-gradient
+    contraction (the tensor-core path takes BF16 operands for both); the
+    bias gradient sums it unrounded."""
     rnd = bf16 if bf16_emulation else (lambda a: a)
     G = {}
     G["head.W"] = C["d1"].reshape(-1, 16).T @ dz.ravel()
@@ -175,13 +176,10 @@ def backward(P, C, dz, bf16_emulation=False):
     def cvb(name, g_out, need_dx=True):
         x, W, pre = C[name]
         g_pre = g_out * (pre > 0.0)
-        _, dW, db = conv3_backward(x, W, g_pre)
+        dx, dW, _ = conv3_backward(x, W, rnd(g_pre))
         G[name + ".W"] = dW
-        G[name + ".b"] = db
-        if not need_dx:
-            return None
-        dx, _, _ = conv3_backward(x, W, rnd(g_pre))
-        return dx
+        G[name + ".b"] = g_pre.reshape(-1, g_pre.shape[-1]).sum(axis=0)
+        return dx if need_dx else None
 
     g = cvb("dec1a", cvb("dec1b", g))
     g_up_d2, g_e1 = g[..., :32], g[..., 32:]

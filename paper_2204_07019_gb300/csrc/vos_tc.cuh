@@ -31,6 +31,22 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);  // M / 16
 }
 
+// The same with both operands MN-major (bits 15 and 16: A and B transposed,
+// the 8 consecutive bf16 of a core-matrix row running along M or N).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
+  return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
+}
+
+// Shared-memory matrix descriptor, no swizzle, MN-major canonical layout:
+// core matrices of 8 rows along K x 16 bytes (8 bf16 along M or N); mn =
+// byte distance between core matrices adjacent along M (N), k = between
+// core matrices adjacent along K.  In this (interleaved) mode the leading
+// byte offset field holds the K distance and the stride byte offset field
+// the M (N) distance, as for the K-major layout above.
+__device__ __forceinline__ uint64_t desc_mnmajor(uint32_t saddr, uint32_t mn, uint32_t k) {
+  return desc_kmajor(saddr, k, mn);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(

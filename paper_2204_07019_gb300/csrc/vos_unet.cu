@@ -513,93 +513,190 @@ __global__ void k_relu_bwd(long long n, const float* __restrict__ g, const __nv_
   }
 }
 
-// Weight gradient of one tap for a chunk of voxels (CUDA cores, FP32):
-// partial[chunk][tap][o][i] = sum over the chunk's voxels v of
-// g[v][o] x[v + t][i].  A thread owns a 4 x 4 (o, i) tile; when the layer has
-// fewer than 256 tiles, R replicas of the tile set split the voxels and are
-// added in a fixed order at the end.
-constexpr int kDwSub = 32;
-__global__ void __launch_bounds__(kThreads) k_dw(int nx, int ny, int nz, int Cin, int Cout, long long chunk,
-                                                const __nv_bfloat16* __restrict__ x, const float* __restrict__ g,
-                                                float* __restrict__ partial) {
+// Weight gradient on the tensor cores.  For one chunk of voxels v and the
+// taps t, partial[chunk][t][o][i] = sum_v x[v + t][i] g[v][o] is a GEMM
+// D[m][n] = sum_k A[m][k] B[n][k] with rows m = (tap, input channel) stacked
+// 128 per MMA tile (27 * cin rows in ceil(27 cin / 128) tiles), n = output
+// channel and k = voxel: K = 16 voxels per MMA, BF16 operands (x and the
+// BF16 copy of g that the data-gradient convolution also reads), FP32
+// accumulators in tensor memory, one N = cout column block per tile.  Both
+// operands are MN-major: a core matrix is 8 voxels (rows along K) x 8
+// channels (16 bytes along M or N), so each row is one channels-last vector
+// copied as it is -- x at the tap's neighbour (zero outside the box) or g
+// at the voxel -- with no transpose; core matrices adjacent along M (N) are
+// 256 B apart, the two K halves 128 B.  Each K step the 128 threads fill one
+// of two buffers; one thread issues the MMAs and commits them to the
+// buffer's barrier, which is waited on before the buffer is refilled two
+// steps later.  CTA (chunk, tile group): blockIdx.y selects the tiles this
+// CTA accumulates (tensor memory holds at most 256 columns per CTA).
+constexpr int kDwK = 16;            // voxels per MMA (K)
+constexpr int kDwTileBytes = 4096;  // one 128-row A tile of one K step
+struct DwArgs {
+  const __nv_bfloat16* x;  // [V][cin] layer input
+  const __nv_bfloat16* g;  // [V][cout] gradient at the layer's pre-activation output
+  float* partial;          // [nchunk][27][cout][cin]
+  int nx, ny, nz, cin, cout;
+  long long chunk;         // voxels per CTA (multiple of 16)
+  int tiles, tpc;          // A tiles in all; tiles per CTA
+};
+__host__ __device__ inline int dw_tiles(int cin) { return (27 * cin + 127) / 128; }
+__host__ __device__ inline int dw_tpc(int cin, int cout) {
+  const int t = dw_tiles(cin), cap = 256 / cout;
+  return t < cap ? t : cap;
+}
+inline size_t dw_smem_bytes(int cin, int cout) {
+  return 2 * ((size_t)dw_tpc(cin, cout) * kDwTileBytes + (size_t)cout * 32) + 64;
+}
+
+__global__ void __launch_bounds__(kTM) k_dw_tc(DwArgs a) {
   VOS_COUNT_EXEC();
-  __shared__ float xs[kDwSub][96];
-  __shared__ float gs[kDwSub][64];
-  __shared__ float red[128 * 16];  // replicas > 1 only when tiles <= 128
-  const int tap = blockIdx.y;
-  const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dzz = tap / 9 - 1;
-  const long long V = (long long)nx * ny * nz;
-  const long long v0 = (long long)blockIdx.x * chunk;
-  const long long v1 = min(V, v0 + chunk);
-  const int to = Cout / 4, ti = Cin / 4, tiles = to * ti;
-  const int R = kThreads / tiles;
-  const int t = threadIdx.x;
-  const int tile = t % tiles, rep = t / tiles;
-  const bool active = rep < R;
-  const int o0 = (tile / ti) * 4, i0 = (tile % ti) * 4;
-  float acc[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
-  for (long long s0 = v0; s0 < v1; s0 += kDwSub) {
-    const int ns = (int)min((long long)kDwSub, v1 - s0);
-    for (int e = t; e < kDwSub * Cin; e += kThreads) {
-      const int vv = e / Cin, ci = e % Cin;
-      float val = 0.0f;
-      if (vv < ns) {
-        const long long v = s0 + vv;
-        const int k = (int)(v / ((long long)nx * ny)), j = (int)((v / nx) % ny), i = (int)(v % nx);
-        const int ii = i + dx, jj = j + dy, kk = k + dzz;
-        if (ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz)
-          val = __bfloat162float(x[(ii + (long long)nx * (jj + (long long)ny * kk)) * Cin + ci]);
-      }
-      xs[vv][ci] = val;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int T0 = blockIdx.y * a.tpc;
+  const int nt = min(a.tpc, a.tiles - T0);
+  const int bufA = a.tpc * kDwTileBytes, bufB = a.cout * 32;
+  unsigned char* sA = smem;                // two A buffers
+  unsigned char* sB = smem + 2 * bufA;     // two B buffers
+  uint64_t* empty = (uint64_t*)(sB + 2 * bufB);
+  uint32_t* slot = (uint32_t*)(empty + 2);
+  int* s_ok = (int*)(slot + 1);
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(nt * a.cout)) ncols <<= 1;
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), ncols);
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_addr(&empty[0]), 1);
+    tc::mbar_init(tc::smem_addr(&empty[1]), 1);
+    tc::fence_mbar_init();
+    *s_ok = 1;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *slot;
+  const long long V = (long long)a.nx * a.ny * a.nz;
+  const long long v0 = (long long)blockIdx.x * a.chunk;
+  const long long v1 = min(V, v0 + a.chunk);
+  const int nsteps = (int)((v1 - v0 + kDwK - 1) / kDwK);
+  const int ngA = nt * 16;         // 8-row groups of this CTA's A rows
+  const int ngB = a.cout >> 3;     // 8-row groups of B
+  const uint32_t idesc = tc::idesc_bf16_f32_mn(128, a.cout);
+  // per A group: element offset of its tap's neighbour plus first channel,
+  // and the tap's offsets + 1 (bits 0-1 x, 2-3 y, 4-5 z; 63 = padding row)
+  __shared__ long long s_off[256];
+  __shared__ unsigned char s_code[256];
+  for (int gq = tid; gq < ngA; gq += kTM) {
+    const int m = (T0 * 16 + gq) * 8;
+    const int tap = m / a.cin, c0 = m - tap * a.cin;
+    if (tap < 27) {
+      const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+      s_off[gq] = ((long long)(dx - 1) + (long long)a.nx * ((dy - 1) + (long long)a.ny * (dz - 1))) * a.cin + c0;
+      s_code[gq] = (unsigned char)(dx | (dy << 2) | (dz << 4));
+    } else {
+      s_off[gq] = 0;
+      s_code[gq] = 63;  // bits 3 of every mask are zero: never loaded
     }
-    for (int e = t; e < kDwSub * Cout; e += kThreads) {
-      const int vv = e / Cout, co = e % Cout;
-      gs[vv][co] = (vv < ns) ? g[(s0 + vv) * Cout + co] : 0.0f;
+  }
+  __syncthreads();
+  uint32_t eph0 = 0u, eph1 = 0u;  // phases of the two buffers' barriers
+  for (int s = 0; s < nsteps; ++s) {
+    const int b = s & 1;
+    if (tid == 0 && s >= 2) {  // the MMAs of step s - 2 have read buffer b
+      if (!tc::mbar_wait(tc::smem_addr(&empty[b]), b ? eph1 : eph0, kWaitNs)) *s_ok = 0;
+      if (b) eph1 ^= 1u; else eph0 ^= 1u;
     }
     __syncthreads();
-    if (active) {
-      for (int vv = rep; vv < kDwSub; vv += R) {
-        float a[4], b[4];
+    if (!*s_ok) break;
+    unsigned char* A = sA + b * bufA;
+    unsigned char* B = sB + b * bufB;
+    // Items (8-channel group, voxel kk): one 16-byte channel vector, the
+    // row kk % 8 of an MN-major core matrix (A groups: x at the tap's
+    // neighbour of voxel kk, zero outside the box; B groups: g at voxel
+    // kk).  A thread keeps one voxel (kk = tid % 16) for the whole step.
+    const int kk = tid & (kDwK - 1);
+    const long long v = v0 + (long long)s * kDwK + kk;
+    const bool vin = v < v1;
+    unsigned mx = 0u, my = 0u, mz = 0u;  // bit d: the neighbour at offset d - 1 is in the box
+    if (vin) {
+      const unsigned vu = (unsigned)v, nxu = (unsigned)a.nx, nyu = (unsigned)a.ny;  // V < 2^31
+      const int vi = (int)(vu % nxu), vj = (int)((vu / nxu) % nyu), vk = (int)(vu / (nxu * nyu));
+      mx = (vi > 0 ? 1u : 0u) | 2u | (vi + 1 < a.nx ? 4u : 0u);
+      my = (vj > 0 ? 1u : 0u) | 2u | (vj + 1 < a.ny ? 4u : 0u);
+      mz = (vk > 0 ? 1u : 0u) | 2u | (vk + 1 < a.nz ? 4u : 0u);
+    }
+    const __nv_bfloat16* xv = a.x + v * a.cin;
+    const int row = (kk >> 3) * 128 + (kk & 7) * 16;
+    // batches of 8 items: the 8 loads are in flight together
+    constexpr int kStride = kTM / kDwK;  // 8 groups per pass of the block
+    for (int g0 = tid >> 4; g0 < ngA + ngB; g0 += 8 * kStride) {
+      uint4 val[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          a[q] = gs[vv][o0 + q];
-          b[q] = xs[vv][i0 + q];
+      for (int r = 0; r < 8; ++r) {
+        const int grp = g0 + r * kStride;
+        val[r] = make_uint4(0u, 0u, 0u, 0u);
+        if (grp < ngA) {
+          const unsigned code = s_code[grp];
+          if (((mx >> (code & 3u)) & (my >> ((code >> 2) & 3u)) & (mz >> (code >> 4))) & 1u)
+            val[r] = __ldg(reinterpret_cast<const uint4*>(xv + s_off[grp]));
+        } else if (grp < ngA + ngB && vin) {
+          val[r] = __ldg(reinterpret_cast<const uint4*>(a.g + v * a.cout + (grp - ngA) * 8));
         }
+      }
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[p * 4 + q] += a[p] * b[q];
+      for (int r = 0; r < 8; ++r) {
+        const int grp = g0 + r * kStride;
+        if (grp < ngA)
+          *reinterpret_cast<uint4*>(A + (grp >> 4) * kDwTileBytes + (grp & 15) * 256 + row) = val[r];
+        else if (grp < ngA + ngB)
+          *reinterpret_cast<uint4*>(B + (grp - ngA) * 256 + row) = val[r];
       }
     }
+    tc::fence_proxy_async_smem();
     __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint64_t bd = tc::desc_mnmajor(tc::smem_addr(B), 256, 128);
+      for (int t = 0; t < nt; ++t) {
+        const uint64_t ad = tc::desc_mnmajor(tc::smem_addr(A + t * kDwTileBytes), 256, 128);
+        tc::mma_bf16(tmem + (uint32_t)(t * a.cout), ad, bd, idesc, s > 0 ? 1u : 0u);
+      }
+      tc::commit(tc::smem_addr(&empty[b]));
+    }
   }
-  float* dst = partial + ((long long)blockIdx.x * 27 + tap) * Cout * Cin;
-  if (R == 1) {
-    if (active)
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[(o0 + p) * Cin + i0 + q] = acc[p * 4 + q];
-    return;
+  if (tid == 0 && *s_ok) {  // the last commit of each buffer: every MMA done
+    for (int s = (nsteps >= 2 ? nsteps - 2 : 0); s < nsteps && *s_ok; ++s) {
+      const int b = s & 1;
+      if (!tc::mbar_wait(tc::smem_addr(&empty[b]), b ? eph1 : eph0, kWaitNs)) *s_ok = 0;
+      if (b) eph1 ^= 1u; else eph0 ^= 1u;
+    }
+    if (!*s_ok) atomicExch(&g_tc_timeout, 1);
+  } else if (tid == 0) {
+    atomicExch(&g_tc_timeout, 1);
   }
-  // replicas: tiles * 16 * R <= 256 * 16 floats; sum in replica order
-  for (int r = 1; r < R; ++r) {
-    if (active && rep == r)
+  __syncthreads();
+  if (*s_ok && nsteps > 0) {
+    tc::fence_after_sync();
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    float* part = a.partial + (long long)blockIdx.x * 27 * a.cout * a.cin;
+    for (int t = 0; t < nt; ++t) {
+      const int m = (T0 + t) * 128 + tid;  // TMEM lane = row of tile t
+      const int tap = m / a.cin, ci = m - tap * a.cin;
+      for (int n0 = 0; n0 < a.cout; n0 += 16) {
+        uint32_t r[16];
+        tc::tmem_ld16(trow + (uint32_t)(t * a.cout + n0), r);
+        if (tap < 27) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) red[tile * 16 + q] = acc[q];
-    __syncthreads();
-    if (active && rep == 0)
-#pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] += red[tile * 16 + q];
-    __syncthreads();
+          for (int q = 0; q < 16; ++q)
+            part[((long long)tap * a.cout + n0 + q) * a.cin + ci] = __uint_as_float(r[q]);
+        }
+      }
+    }
   }
-  if (active && rep == 0)
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dst[(o0 + p) * Cin + i0 + q] = acc[p * 4 + q];
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, ncols);
+  }
 }
 
 // dW[o][tap][i] = sum over chunks of partial[chunk][tap][o][i] (fixed order).
@@ -900,8 +997,17 @@ static cudaError_t layer_backward(vos_unet* u, int li, const __nv_bfloat16* xin,
   vlaunch("unet_relu_bwd", 0.0, k_relu_bwd, ugrid(V * l.cout), kThreads, st, V * l.cout, g_out,
           (const __nv_bfloat16*)l.out, u->gpre, u->gpre16);
   const int nch = u->nchunk[l.lev];
-  vlaunch("unet_dw", 0.0, k_dw, dim3((unsigned)nch, 27), kThreads, st, u->lx[l.lev], u->ly[l.lev], u->lz[l.lev],
-          l.cing, l.cout, u->chunk[l.lev], xin, (const float*)u->gpre, u->part_dw);
+  static bool dw_attr = false;
+  if (!dw_attr) {
+    VOS_CUDA_TRY(cudaFuncSetAttribute(k_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(2 * (16 * kDwTileBytes + 96 * 32) + 64)));
+    dw_attr = true;
+  }
+  const DwArgs da{xin, u->gpre16, u->part_dw, u->lx[l.lev], u->ly[l.lev], u->lz[l.lev], l.cing, l.cout,
+                  u->chunk[l.lev], dw_tiles(l.cing), dw_tpc(l.cing, l.cout)};
+  const dim3 gdw((unsigned)nch, (unsigned)((da.tiles + da.tpc - 1) / da.tpc));
+  vlaunch_smem("unet_dw_tc", 2.0 * 27.0 * l.cing * l.cout * (double)V, k_dw_tc, gdw, dim3(kTM),
+               dw_smem_bytes(l.cing, l.cout), st, da);
   vlaunch("unet_dw_reduce", 0.0, k_dw_reduce, ugrid(27LL * l.cout * l.cing), kThreads, st, nch, l.cing, l.cout,
           (const float*)u->part_dw, l.gW);
   vlaunch("unet_db", 0.0, k_db, u->ndb, kThreads, st, V, l.cout, (const float*)u->gpre, u->part_db);
@@ -1072,9 +1178,10 @@ static vos_unet* create_net(int px, int py, int pz, bool train, cudaStream_t st)
     u->gpre = (float*)A(pmax * 4);
     u->gpre16 = (__nv_bfloat16*)A(pmax * 2);
     long long pdw = 0;
-    for (int l = 0; l < 3; ++l) {
-      long long ch = 2048;
-      while ((u->V[l] + ch - 1) / ch > 512) ch *= 2;
+    for (int l = 0; l < 3; ++l) {  // weight-gradient chunks: about two CTAs per SM, 256 voxels at least
+      const long long target = 2LL * g_num_sms;
+      long long ch = ((u->V[l] + target - 1) / target + 15) / 16 * 16;
+      if (ch < 256) ch = 256;
       u->chunk[l] = ch;
       u->nchunk[l] = (int)((u->V[l] + ch - 1) / ch);
     }
