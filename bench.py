@@ -162,6 +162,14 @@ TRAFFIC_PER_ALG_BYTE = {
     # matrix-free pressure Jacobi sweep (four cells per thread): 84.95 MB read
     # (12.0 B per cell) + 6.61 MB written against 16 B per cell
     "mg_jac_mf_f32_L0": ((84949248.0 + 6610688.0) / (16.0 * 7077888.0), "ncu dram bytes of a 192^3 launch scaled by cells"),
+    # two-kernel diagonal PCG (momentum), mean of eight launches each:
+    # x/r update + preconditioner: 141.61 MB read (20.0 B per unknown) +
+    # 31.93 MB written against 32 B per unknown; direction update + matvec:
+    # 84.98 MB read (12.0 B) + 20.85 MB written against 20 B per unknown
+    "pcg_xrz_f32_L0": ((141609984.0 + 31928000.0) / (32.0 * 7077888.0),
+                       "ncu dram bytes of 192^3 launches scaled by units"),
+    "pcg_pmv_mfc_f32_L0": ((84976992.0 + 20846368.0) / (20.0 * 7077888.0),
+                           "ncu dram bytes of 192^3 launches scaled by units"),
 }
 
 
