@@ -598,8 +598,8 @@ def main():
     ap.add_argument("--scalar-sweeps", action="store_true",
                     help="one cell per thread in the matrix-free pressure sweeps (same results; for comparison)")
     ap.add_argument("--four-kernel-pcg", action="store_true",
-                    help="diagonally preconditioned CG in four kernels per iteration instead of two (for "
-                         "comparison)")
+                    help="the FP32 inner Krylov solves with separate kernels (vos_set_fused_pcg(0)) instead of "
+                         "the fused forms (for comparison)")
     ap.add_argument("--coarse-cycle", action="store_true",
                     help="run the coarse multigrid levels as one cluster launch per V-cycle instead of one "
                          "launch per operation (same results; for comparison)")
@@ -709,7 +709,8 @@ def main():
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "launch": "eager" if args.eager else "graph", "tiles": r["tiles"],
                       "coarse_cycle": "cluster-resident" if args.coarse_cycle else "separate launches",
-                      "diag_pcg": "four kernels per iteration" if args.four_kernel_pcg else "two kernels per iteration"},
+                      "krylov": "separate kernels" if args.four_kernel_pcg else
+                      "fused (two-kernel diagonal PCG; MG-PCG with the first and last fine sweeps)"},
            "roofline": r["roofline"], "gpu_launches": r["launches"],
            "fp64_value": fp64_value, "fp64_ms_per_step": r64["ms"] if r64 else None,
            "mixed_vs_fp64": (value / fp64_value) if fp64_value else None,

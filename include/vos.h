@@ -471,18 +471,28 @@ int vos_set_coarse_cycle(int on);
  *   vos_set_vector_sweeps(0): one cell per thread.  Identical results (each
  *   cell's arithmetic is the same); takes effect at the next launch. */
 int vos_set_vector_sweeps(int on);
-/* vos_set_fused_pcg(1) (default): diagonally preconditioned CG passes on a
- *   constant-link FP32 operator (the momentum systems of the mixed path when
- *   they take the diagonal preconditioner) run two kernels per iteration:
- *   the direction update fused with the matrix-vector product and p.q, then
- *   the x/r update fused with the preconditioner and r.r, r.z, z.z (20 + 32
- *   bytes per unknown against 64).  vos_set_fused_pcg(0): four kernels per
- *   iteration (direction update, matrix-vector product with p.q, x/r update,
- *   preconditioner with r.z).  Both compute every value with the same
- *   operations and every dot product in the same order: identical results.
- *   Takes effect at the next launch; a step already captured as a CUDA graph
- *   keeps the form it was captured with. */
-int vos_set_fused_pcg(int on);
+/* vos_set_fused_pcg(mask): fused forms of the FP32 inner Krylov solves of
+ *   the mixed path; default 3 (both), 0 for the separate kernels.
+ *   Bit 0 (VOS_FUSED_DIAG_PCG): diagonally preconditioned CG on a
+ *   constant-link operator (the momentum systems when they take the
+ *   diagonal preconditioner) in two kernels per iteration -- the direction
+ *   update fused with the matrix-vector product and p.q, the x/r update
+ *   fused with the preconditioner and r.r, r.z, z.z (20 + 32 bytes per
+ *   unknown against 64).  Every value is computed with the operations, and
+ *   every dot summed in the order, of the four separate kernels: identical
+ *   results.
+ *   Bit 1 (VOS_FUSED_MG_PCG): multigrid PCG on the matrix-free pressure level
+ *   (rows of a multiple of 4 cells) with the x/r update fused into the
+ *   V-cycle's first fine sweep and r.z into its last (the floating-cluster
+ *   deflation adds its share of r.z): two fewer passes over the vectors per
+ *   iteration.  The cell values are the separate kernels'; two dot products
+ *   are summed in another order, so the iterates agree to rounding.
+ *   Returns VOS_EINVAL for a mask outside 0..3.  Takes effect at the next
+ *   launch; a step already captured as a CUDA graph keeps the form it was
+ *   captured with. */
+#define VOS_FUSED_DIAG_PCG 1
+#define VOS_FUSED_MG_PCG 2
+int vos_set_fused_pcg(int mask);
 int vos_prof_enable(const char* filter);
 int vos_prof_report(char* buf, size_t len);
 void vos_prof_reset(void);

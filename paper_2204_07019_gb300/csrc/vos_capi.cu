@@ -1017,8 +1017,9 @@ int vos_set_vector_sweeps(int on) {
   return VOS_OK;
 }
 
-int vos_set_fused_pcg(int on) {
-  vos::g_fused_pcg = on != 0;
+int vos_set_fused_pcg(int mask) {
+  if (mask < 0 || mask > 3) return VOS_EINVAL;
+  vos::g_fused_pcg = mask;
   return VOS_OK;
 }
 

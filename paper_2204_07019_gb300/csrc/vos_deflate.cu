@@ -162,6 +162,49 @@ __global__ void __launch_bounds__(kThreads) k_defl_apply(Defl D, const T* __rest
   for (int t = b + threadIdx.x; t < e; t += kThreads) z[D.ent[t] & kDeflCellMask] += add;
 }
 
+// The same, also completing r.z for PCG: the fine sweep that produced z
+// stored sum r.z_mg in sc->rz_part; cluster q adds add_q (sum over its cells
+// of r), the change of r.z its correction makes, into partials[q], and the
+// last block to finish adds those in cluster order and finalises beta.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_defl_apply_rz(Defl D, const T* __restrict__ r, T* __restrict__ z,
+                                                           KScal* sc, RedScratch rs) {
+  VOS_COUNT_EXEC();
+  if (sc->done) return;  // the same for every block of the launch
+  const int q = blockIdx.x;
+  const int b = D.ptr[q], e = D.ptr[q + 1];
+  double v[1] = {0.0};
+  for (int t = b + threadIdx.x; t < e; t += kThreads) v[0] += (double)r[D.ent[t] & kDeflCellMask];
+  block_sum<1>(v);
+  __shared__ double s_add;
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) s_add = v[0] * D.Einv[q];
+  __syncthreads();
+  const T add = (T)s_add;
+  for (int t = b + threadIdx.x; t < e; t += kThreads) z[D.ent[t] & kDeflCellMask] += add;
+  if (threadIdx.x == 0) {
+    rs.partials[q] = (double)add * v[0];
+    __threadfence();
+    s_last = atomicAdd(rs.counter, 1u) == (unsigned)D.K - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double c[1] = {0.0};
+  for (int t = threadIdx.x; t < D.K; t += kThreads) c[0] += __ldcg(rs.partials + t);
+  block_sum<1>(c);
+  if (threadIdx.x == 0) {
+    *rs.counter = 0u;
+    fin_pcg_beta(sc, sc->rz_part + c[0]);
+  }
+}
+
+template <typename T>
+void launch_defl_apply_rz(const Defl& D, const T* r, T* z, KScal* sc, const RedScratch& rs, cudaStream_t st) {
+  vlaunch("defl_apply", 0.0, k_defl_apply_rz<T>, D.K, kThreads, st, D, r, z, sc, rs);
+}
+template void launch_defl_apply_rz<float>(const Defl&, const float*, float*, KScal*, const RedScratch&, cudaStream_t);
+
 void launch_defl_energy(const Defl& D, const Op<double>& A, cudaStream_t st) {
   if (D.K <= 0) return;
   vlaunch("defl_energy", 0.0, k_defl_energy, D.K, kThreads, st, D, A);

@@ -317,6 +317,7 @@ struct KScal {
   double bb, rr, rz, rz_old, pq, alpha, beta, omega, rho, rhv, tol2;
   double tol2s;  // diagonally preconditioned CG: stop when z.z <= tol2s (scaled norm)
   double ss, ts, tt;
+  double rz_part;  // r.z of the fine sweep before the deflation's share (fused PCG)
   int done, iters, max_iters, breakdown;
 };
 
@@ -376,7 +377,7 @@ extern bool g_tail_enabled;
 // Matrix-free FP32 pressure sweeps with four cells per thread and 16-byte
 // accesses when the row length is a multiple of 4 (vos_solver.cu).
 extern bool g_mf4;
-extern bool g_fused_pcg;  // two-kernel diagonal PCG iteration (vos_set_fused_pcg)
+extern int g_fused_pcg;  // fused Krylov forms, bit mask (vos_set_fused_pcg)
 template <typename T>
 int tail_plan(const Hier<T>& h);
 template <typename T>
@@ -402,6 +403,22 @@ void launch_defl_energy(const Defl& D, const Op<double>& A, cudaStream_t st);
 // z += W E^-1 W^T r (skipped when the solve is done).
 template <typename T>
 void launch_defl_apply(const Defl& D, const T* r, T* z, const KScal* sc, cudaStream_t st);
+// The same for PCG with r.z fused into the fine sweep: adds the correction's
+// share of r.z to sc->rz_part and finalises beta (D.K >= 1, D.K <= the
+// reduction scratch's kMaxRedValues * kMaxRedBlocks partials).
+template <typename T>
+void launch_defl_apply_rz(const Defl& D, const T* r, T* z, KScal* sc, const RedScratch& rs, cudaStream_t st);
+
+// PCG: beta = r.z / r.z_prev (0 on a pass's first iteration), keep r.z;
+// a non-positive or non-finite r.z ends the pass as a breakdown.
+__device__ __forceinline__ void fin_pcg_beta(KScal* sc, double rz) {
+  sc->beta = (sc->iters == 0) ? 0.0 : rz / sc->rz;
+  sc->rz = rz;
+  if (!(rz > 0.0) || !isfinite(rz)) {
+    sc->breakdown = 1;
+    sc->done = 1;
+  }
+}
 
 // Device-side record of one solve when the loops run inside a CUDA graph.
 struct SolveStats {

@@ -110,18 +110,6 @@ static inline double ncell(const Op<T>& A) {
 // FIN codes for the fused dot of the last level-0 smoothing sweep.
 enum Fin { FIN_NONE = 0, FIN_PCG_BETA = 1 };
 
-__device__ void fin_pcg_beta(KScal* sc, double rz) {
-  if (sc->iters == 0) {
-    sc->beta = 0.0;
-  } else {
-    sc->beta = rz / sc->rz;
-  }
-  sc->rz = rz;
-  if (!(rz > 0.0) || !isfinite(rz)) {
-    sc->breakdown = 1;
-    sc->done = 1;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // 2.5D stencil sweeps: a (blockDim.x x blockDim.y) tile of threads in the
@@ -608,6 +596,118 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_mf4row(Box bx, cons
   }
 }
 
+// MG-PCG on the matrix-free pressure level, fused with the V-cycle's first
+// and last fine sweeps (four cells per thread, float):
+//   k_xr_jac0_mf4: e += alpha p, r -= alpha q (the FMAs of k_pcg_xr), |r|^2
+//     and the pass's stop test, and the V-cycle's first sweep from zero on
+//     the new residual, x1 = (omega / diag) r, written to the V-cycle's
+//     scratch vector;
+//   k_jac_mf4_rz: the last post-smoothing sweep (z = its output, r = its
+//     right-hand side) with sum r.z, finalising beta, or -- when the
+//     floating-cluster deflation follows -- leaving the partial in
+//     sc->rz_part for k_defl_apply_rz.
+// The cell values are those of the separate kernels; the sums run in the
+// sweep's thread order instead of the flat kernels', so the iterates agree
+// to rounding, not bit for bit.
+__global__ void __launch_bounds__(kThreads, 3) k_xr_jac0_mf4(Box bx, const float* __restrict__ e, float s,
+                                                            const float* __restrict__ p, const float* __restrict__ q,
+                                                            float* __restrict__ ex, float* __restrict__ r,
+                                                            float* __restrict__ x1, float omega, int zc, KScal* sc,
+                                                            RedScratch rs) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const float alpha = (float)sc->alpha;
+  Mf4March<SK_JAC0, XS_PLAIN> m;
+  m.i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  m.j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  PSum<float> ps;
+  if (m.i0 < bx.mx && m.j < bx.my && k0 < k1) {
+    m.bx = bx;
+    m.e = e;
+    m.b = q;  // the march's right-hand-side loads are dummies: each plane's b is the new r below
+    m.x = nullptr;
+    m.s = s;
+    m.omega = omega;
+    m.cb = bx;
+    m.xc = nullptr;
+    m.wc = 0.0f;
+    m.init(k0);
+    long long c = m.i0 + m.sy * m.j + m.sz * k0;
+    for (int k = k0; k < k1; ++k, c += m.sz) {
+      const float4 pv = Mf4March<SK_JAC0, XS_PLAIN>::ld4(p + c), qv = Mf4March<SK_JAC0, XS_PLAIN>::ld4(q + c);
+      float4 ev = *reinterpret_cast<const float4*>(ex + c), rv = *reinterpret_cast<const float4*>(r + c);
+      ev = make_float4(fmaf(alpha, pv.x, ev.x), fmaf(alpha, pv.y, ev.y), fmaf(alpha, pv.z, ev.z),
+                       fmaf(alpha, pv.w, ev.w));
+      rv = make_float4(fmaf(-alpha, qv.x, rv.x), fmaf(-alpha, qv.y, rv.y), fmaf(-alpha, qv.z, rv.z),
+                       fmaf(-alpha, qv.w, rv.w));
+      *reinterpret_cast<float4*>(ex + c) = ev;
+      *reinterpret_cast<float4*>(r + c) = rv;
+      ps.add(rv.x, rv.x);
+      ps.add(rv.y, rv.y);
+      ps.add(rv.z, rv.z);
+      ps.add(rv.w, rv.w);
+      m.bc = rv;
+      float o[4];
+      m.plane(k, k1, c, o);
+      *reinterpret_cast<float4*>(x1 + c) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+  }
+  double acc[1] = {ps.get()};
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    sc->rr = acc[0];
+    sc->iters += 1;
+    if (acc[0] <= sc->tol2 || sc->iters >= sc->max_iters || !isfinite(acc[0])) sc->done = 1;
+  }
+}
+
+template <int XS>
+__global__ void __launch_bounds__(kThreads, 3) k_jac_mf4_rz(Box bx, const float* __restrict__ e, float s,
+                                                           const float* __restrict__ b, const float* __restrict__ x,
+                                                           float* __restrict__ out, float omega, int zc, KScal* sc,
+                                                           RedScratch rs, Box cb, const float* __restrict__ xc,
+                                                           float wc, int defer) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  Mf4March<SK_JAC, XS> m;
+  m.i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  m.j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, bx.mz);
+  PSum<float> ps;
+  if (m.i0 < bx.mx && m.j < bx.my && k0 < k1) {
+    m.bx = bx;
+    m.e = e;
+    m.b = b;
+    m.x = x;
+    m.s = s;
+    m.omega = omega;
+    m.cb = cb;
+    m.xc = xc;
+    m.wc = wc;
+    m.init(k0);
+    long long c = m.i0 + m.sy * m.j + m.sz * k0;
+    for (int k = k0; k < k1; ++k, c += m.sz) {
+      const float4 bq = m.bc;
+      float o[4];
+      m.plane(k, k1, c, o);
+      *reinterpret_cast<float4*>(out + c) = make_float4(o[0], o[1], o[2], o[3]);
+      ps.add(bq.x, o[0]);
+      ps.add(bq.y, o[1]);
+      ps.add(bq.z, o[2]);
+      ps.add(bq.w, o[3]);
+    }
+  }
+  double acc[1] = {ps.get()};
+  if (grid_sum<1>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    if (defer)
+      sc->rz_part = acc[0];
+    else
+      fin_pcg_beta(sc, acc[0]);
+  }
+}
+
 // Constant-link FP32 sweeps (Op::mfc): links to the neighbours inside the
 // box are all `a`, so a sweep reads diag and x (and b), not xp/yp/zp.
 template <int KIND>
@@ -725,7 +825,6 @@ __global__ void k_restrict_sum(Box fb, Box cb, const T* __restrict__ r, T* __res
 // Dot products with a device-side finalisation (deterministic FP64 reduce).
 enum DotFin { DF_PCG_BETA = 0, DF_PCG_ALPHA = 1, DF_BICG_ALPHA = 2, DF_BICG_OMEGA = 3, DF_FCG_BETA = 4 };
 
-__device__ void fin_pcg_beta(KScal* sc, double rz);
 
 template <typename T, int NV, int FIN>
 __global__ void k_dots(long long n, const T* __restrict__ a0, const T* __restrict__ b0, const T* __restrict__ a1,
@@ -2044,7 +2143,12 @@ static void stencil_launch(const char* name, int kind, const Op<T>& A, const T* 
 }
 
 template <typename T, bool SYM>
-static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cudaStream_t st) {
+// rz (fused MG-PCG only, see fused_mg_pcg): the last fine sweep also sums
+// rhs.out (k_jac_mf4_rz; deferred to the deflation when the hierarchy has
+// one); jac0_done: the first fine sweep's output is already in scratch
+// (k_xr_jac0_mf4).
+static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cudaStream_t st,
+                   const RedScratch* rz = nullptr, bool jac0_done = false) {
   const int L = h.nlev;
   const int nu = h.mg.nu < 1 ? 1 : h.mg.nu;
   const T wc = (T)h.mg.wc, om = (T)h.mg.omega;
@@ -2111,7 +2215,7 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     bufs(l, b, x, t);
     T* cur = t;
     T* oth = x;
-    jac0(l, cur);
+    if (!(l == 0 && jac0_done)) jac0(l, cur);
     for (int s = 1; s < nu; ++s) {
       stencil_launch<T, SYM>(KN("mg_jac", l == 0), SK_JAC, A, b, cur, oth, om, sc, st);
       T* tmp = cur;
@@ -2164,12 +2268,20 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     T* oth = (cur == x) ? t : x;
     const Box fz = zbox(A.box), cz = zbox(h.lev[l + 1].op.box);
     int s0 = 0;
+    const bool rz_here = (l == 0 && rz != nullptr);
+    const int dfr = h.defl.K > 0 ? 1 : 0;
     if (fused_fine(l)) {  // first sweep on x + wc P x_coarse, formed on the fly
       const Op<T> Z = zview(A);
       const ZCfg z4 = zcfg_mf4(Z.box);
-      vlaunch("mg_jac_pro_mf_f32_L0", (4.0 * ncell(A) + ncell(h.lev[l + 1].op)) * 4.0, k_stencil_mf4<SK_JAC, XS_PRO>,
-              z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, (const float*)b, (const float*)cur, (float*)oth, (float)om,
-              z4.zc, (const KScal*)sc, cz, (const float*)h.lev[l + 1].x, (float)wc);
+      const double bytes = (4.0 * ncell(A) + ncell(h.lev[l + 1].op)) * 4.0;
+      if (rz_here && nu == 1)
+        vlaunch("mg_jac_pro_rz_mf_f32_L0", bytes, k_jac_mf4_rz<XS_PRO>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs,
+                (const float*)b, (const float*)cur, (float*)oth, (float)om, z4.zc, sc, *rz, cz,
+                (const float*)h.lev[l + 1].x, (float)wc, dfr);
+      else
+        vlaunch("mg_jac_pro_mf_f32_L0", bytes, k_stencil_mf4<SK_JAC, XS_PRO>, z4.grid, z4.block, st, Z.box, A.mfe,
+                A.mfs, (const float*)b, (const float*)cur, (float*)oth, (float)om, z4.zc, (const KScal*)sc, cz,
+                (const float*)h.lev[l + 1].x, (float)wc);
       T* tmp = cur;
       cur = oth;
       oth = tmp;
@@ -2180,7 +2292,15 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
               zc.grid, zc.block, st, fz, cz, cur, (const T*)h.lev[l + 1].x, wc, zc.zc, (const KScal*)sc);
     }
     for (int s = s0; s < nu; ++s) {
-      stencil_launch<T, SYM>(KN("mg_jac", l == 0), SK_JAC, A, b, cur, oth, om, sc, st);
+      if (rz_here && s == nu - 1 && fused_fine(l)) {  // the last fine sweep with rhs.out
+        const Op<T> Z = zview(A);
+        const ZCfg z4 = zcfg_mf4(Z.box);
+        vlaunch("mg_jac_rz_mf_f32_L0", 4.0 * ncell(A) * 4.0, k_jac_mf4_rz<XS_PLAIN>, z4.grid, z4.block, st, Z.box,
+                A.mfe, A.mfs, (const float*)b, (const float*)cur, (float*)oth, (float)om, z4.zc, sc, *rz, Z.box,
+                (const float*)nullptr, 0.0f, dfr);
+      } else {
+        stencil_launch<T, SYM>(KN("mg_jac", l == 0), SK_JAC, A, b, cur, oth, om, sc, st);
+      }
       T* tmp = cur;
       cur = oth;
       oth = tmp;
@@ -2211,12 +2331,31 @@ static KVec<T> kvec(SolverWork* w, bool bicg) {
   return k;
 }
 
+// MG-PCG on the matrix-free FP32 pressure level with its V-cycle's first
+// and last fine sweeps fused with the Krylov x/r update and with r.z
+// (k_xr_jac0_mf4, k_jac_mf4_rz; vos_set_fused_pcg).
+template <typename T, bool SYM>
+static bool fused_mg_pcg(const Hier<T>& h) {
+  if constexpr (sizeof(T) == 4 && SYM) {
+    const Op<T>& A = h.lev[0].op;
+    return (g_fused_pcg & 2) && g_mf4 && A.mfe != nullptr && h.nlev >= 2 && zview(A).box.mx % 4 == 0 &&
+           h.defl.K <= kMaxRedBlocks * kMaxRedValues;
+  }
+  return false;
+}
+
 // z = M^-1 r and the PCG beta (multigrid V-cycle plus the floating-cluster
-// deflation when the hierarchy has one, or the diagonal).
+// deflation when the hierarchy has one, or the diagonal).  jac0_done: the
+// V-cycle's first fine sweep already ran, fused with the x/r update.
 template <typename T, bool SYM>
 static void pcg_precond(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w, const RedScratch& rs,
-                        cudaStream_t st, bool use_mg, bool use_net = false) {
+                        cudaStream_t st, bool use_mg, bool use_net = false, bool jac0_done = false) {
   const int gf = flat_grid(n);
+  if (use_mg && !use_net && fused_mg_pcg<T, SYM>(h)) {
+    vcycle<T, SYM>(h, k.r, k.z, k.scratch, w->sc, st, &rs, jac0_done);
+    if (h.defl.K > 0) launch_defl_apply_rz<float>(h.defl, (const float*)k.r, (float*)k.z, w->sc, rs, st);
+    return;
+  }
   if (use_net && h.net) {
     unet_precond<T>(h.net, k.r, k.z, &w->sc->rr, st);
     vlaunch(KN("dot_rz_zq", true), 3.0 * n * sizeof(T), k_dots<T, 2, DF_FCG_BETA>, gf, kThreads, st, n,
@@ -2232,9 +2371,10 @@ static void pcg_precond(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w
   }
 }
 
-// Process-wide switch of the two-kernel diagonal PCG iteration on
-// constant-link operators (vos_set_fused_pcg).
-bool g_fused_pcg = true;
+// Process-wide switches of the fused Krylov forms (vos_set_fused_pcg): bit 0
+// the two-kernel diagonal PCG on constant-link operators, bit 1 MG-PCG on the
+// matrix-free level fused with the V-cycle's first and last fine sweeps.
+int g_fused_pcg = 3;
 
 // One PCG iteration (kernels early-exit once the solve is done).  parity:
 // the iteration's index within its pass modulo 2 (the two-kernel diagonal
@@ -2245,7 +2385,7 @@ static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork*
   const Op<T>& A = h.lev[0].op;
   const int gf = flat_grid(n);
   if constexpr (sizeof(T) == 4 && SYM) {
-    if (g_fused_pcg && A.mfc != 0.0f && !use_mg && !use_net) {
+    if ((g_fused_pcg & 1) && A.mfc != 0.0f && !use_mg && !use_net) {
       const Op<T> Z = zview(A);
       const float* pin = (const float*)(parity ? k.s : k.p);
       float* pout = (float*)(parity ? k.p : k.s);
@@ -2302,6 +2442,15 @@ static void pcg_iteration(Hier<T>& h, const KVec<T>& k, long long n, SolverWork*
   // tests z.z itself; FP32 MG-PCG and the learned path keep |r|, see
   // scaled_test)
   const T* dscale = (sizeof(T) == 8 && use_mg && !use_net) ? (const T*)A.dinv : nullptr;
+  if (use_mg && !use_net && fused_mg_pcg<T, SYM>(h)) {  // x/r update with the V-cycle's first sweep
+    const Op<T> Z = zview(A);
+    const ZCfg z = zcfg_mf4(Z.box);
+    vlaunch("pcg_xr_jac0_mf_f32_L0", 9.0 * n * 4.0, k_xr_jac0_mf4, z.grid, z.block, st, Z.box, A.mfe, A.mfs,
+            (const float*)k.p, (const float*)k.q, (float*)k.e, (float*)k.r, (float*)k.scratch, (float)h.mg.omega,
+            z.zc, w->sc, rs);
+    pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg, use_net, true);
+    return;
+  }
   vlaunch(KN("pcg_xr", true), (dscale ? 7.0 : 6.0) * n * sizeof(T), k_pcg_xr<T>, gf, kThreads, st, n, (const T*)k.p,
           (const T*)k.q, k.e, k.r, dscale, w->sc, rs);
   pcg_precond<T, SYM>(h, k, n, w, rs, st, use_mg, use_net);

@@ -24,7 +24,7 @@ __all__ = [
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
     "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16", "UNet", "vos_set_unet_preconditioner",
     "vos_unet_solve_stats", "vos_pressure_snapshots", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
-    "PRECOND_MOM_DIAG", "PRECOND_MOM_MG", "PRECOND_P_WARM", "PRECOND_U_EXTRAP",
+    "PRECOND_MOM_DIAG", "PRECOND_MOM_MG", "PRECOND_P_WARM", "PRECOND_U_EXTRAP", "FUSED_DIAG_PCG", "FUSED_MG_PCG",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -37,6 +37,8 @@ PRECOND_MOM_DIAG = 2
 PRECOND_MOM_MG = 4
 PRECOND_P_WARM = 8
 PRECOND_U_EXTRAP = 16
+FUSED_DIAG_PCG = 1
+FUSED_MG_PCG = 2
 
 EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
@@ -668,12 +670,16 @@ def vos_set_vector_sweeps(on):
     load_library().vos_set_vector_sweeps(1 if on else 0)
 
 
-def vos_set_fused_pcg(on):
-    """1 (default): diagonally preconditioned CG on constant-link FP32
-    operators in two kernels per iteration (z formed on the fly); 0: four
-    kernels per iteration.  Set before the handle's first step (a captured
-    step graph keeps its form)."""
-    load_library().vos_set_fused_pcg(1 if on else 0)
+def vos_set_fused_pcg(mask):
+    """Fused FP32 Krylov forms, a bit mask (default 3): FUSED_DIAG_PCG (1)
+    two-kernel diagonal PCG on constant-link operators (results identical to
+    the separate kernels), FUSED_MG_PCG (2) MG-PCG on the matrix-free pressure
+    level with the x/r update and r.z fused into the V-cycle's first and last
+    fine sweeps (iterates equal up to rounding).  Set before the handle's first
+    step (a captured step graph keeps its form)."""
+    rc = load_library().vos_set_fused_pcg(int(mask))
+    if rc != VOS_OK:
+        raise VosError(rc, f"vos_set_fused_pcg: mask {mask} outside 0..3")
 
 
 def vos_set_coarse_cycle(on):

@@ -1,8 +1,10 @@
-"""Two-kernel diagonally preconditioned CG (the momentum solves of the mixed
-path at small 2 d nu dt / dx^2): the fused form (direction update fused with
-the matrix-vector product, x/r update fused with the preconditioner and the
-dot products) gives the four-kernel form's results bit for bit, and both
-match the FP64 oracle.  Shapes cover the four-cells-per-thread kernel (v, w with nx
+"""Fused FP32 Krylov forms of the mixed path.  The two-kernel diagonally
+preconditioned CG (the momentum solves at small 2 d nu dt / dx^2: direction
+update fused with the matrix-vector product, x/r update fused with the
+preconditioner and the dot products) gives the four-kernel form's results
+bit for bit.  The MG-PCG form fused with the V-cycle's first and last fine
+sweeps (pressure) agrees with the separate kernels to the solve tolerance.
+Both match the FP64 oracle.  Shapes cover the four-cells-per-thread kernel (v, w with nx
 a multiple of 4), the one-cell kernel (u: nx + 1 faces; nx = 30) and 2D
 boxes; both launch modes (graph replay, eager)."""
 import numpy as np
@@ -48,7 +50,7 @@ def _run(V, es, prm, dts, fused, graphs):
         finally:
             V.vos_destroy(h)
     finally:
-        V.vos_set_fused_pcg(1)
+        V.vos_set_fused_pcg(V.FUSED_DIAG_PCG | V.FUSED_MG_PCG)
         V.vos_set_launch_mode(1)
 
 
@@ -60,12 +62,19 @@ def test_fused_diag_pcg(V, shape, graphs):
                         p_rtol=1e-11, u_rtol=1e-11, c_rtol=1e-11, max_iter=4000)
     prm["precond"] = int(prm.get("precond", 0)) | V.PRECOND_MOM_DIAG
     dts = [2e-3, 2e-3, 2e-3]  # 2 d nu dt / dx^2 = 7.2 (3D), 4.8 (2D): the diagonal regime
-    f1, it1 = _run(V, es, prm, dts, 1, graphs)
+    # momentum: two kernels against four, the pressure form fixed
+    f1, it1 = _run(V, es, prm, dts, V.FUSED_DIAG_PCG, graphs)
     f0, it0 = _run(V, es, prm, dts, 0, graphs)
-    # the same operations and summation orders: identical iterates
     assert it1 == it0
     for n in f0:
         assert np.array_equal(f1[n], f0[n]), n
+    # pressure: MG-PCG fused with the V-cycle sweeps, to the solve tolerance
+    f3, _ = _run(V, es, prm, dts, V.FUSED_DIAG_PCG | V.FUSED_MG_PCG, graphs)
+    for n in ("u", "v", "w", "p", "c", "eps"):
+        if n == "w" and shape[0] == 1:
+            continue
+        ref = np.linalg.norm(f1[n])
+        assert np.linalg.norm(f3[n] - f1[n]) <= 1e-9 * max(ref, 1e-300), n
     # and the FP64 oracle's exact solves
     st = O.init_state(es, prm)
     for dt in dts:
@@ -73,5 +82,11 @@ def test_fused_diag_pcg(V, shape, graphs):
     ref = dict(u=st["u"][0], v=st["u"][1], p=st["p"], c=st["c"])
     if shape[0] > 1:
         ref["w"] = st["u"][2]
-    for n, r in ref.items():
-        assert np.linalg.norm(f1[n] - r) <= 1e-9 * max(np.linalg.norm(r), 1e-300), n
+    for f in (f1, f3):
+        for n, r in ref.items():
+            assert np.linalg.norm(f[n] - r) <= 1e-9 * max(np.linalg.norm(r), 1e-300), n
+
+
+def test_fused_pcg_mask_checked(V):
+    with pytest.raises(V.VosError):
+        V.vos_set_fused_pcg(4)
