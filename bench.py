@@ -40,6 +40,13 @@ import time
 
 import numpy as np
 
+# Hardware work queues of this process's CUDA context (read when the context
+# is created): the 64-instance batch replays one graph branch per instance,
+# and 32 queues instead of the default 8 let more branches run at once
+# (measured 250.5 -> 222.2 ms per batch step; the single-grid steps do not
+# change).  A per-process setting, not a device setting.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
