@@ -467,9 +467,12 @@ int vos_set_launch_mode(int graphs);
 int vos_set_coarse_cycle(int on);
 /* vos_set_vector_sweeps(1) (default): the matrix-free FP32 sweeps of the
  *   pressure fine level (mixed precision) give each thread four consecutive
- *   cells along x with 16-byte loads and stores when nx is a multiple of 4;
- *   vos_set_vector_sweeps(0): one cell per thread.  Identical results (each
- *   cell's arithmetic is the same); takes effect at the next launch. */
+ *   cells along x with 16-byte loads and stores when nx is a multiple of 4,
+ *   and the multigrid cycles fuse the residual with the restriction and the
+ *   prolongation with the first post-smoothing sweep on every level but the
+ *   coarsest; vos_set_vector_sweeps(0): one cell per thread and separate
+ *   passes.  Identical results (each cell's arithmetic and each sum's order
+ *   are the same); takes effect at the next launch. */
 int vos_set_vector_sweeps(int on);
 /* vos_set_fused_pcg(mask): fused forms of the FP32 inner Krylov solves of
  *   the mixed path; default 3 (both), 0 for the separate kernels.

@@ -98,6 +98,15 @@ struct Op {
   float mfc;
 };
 
+// Rows of the assembled stencil operators are formed with explicit rounding
+// in every kernel that applies them (separate sweeps, fused passes, the
+// cluster-resident cycle, the coarsest-level solve): A x = d x_c, then one
+// FMA per link in the order x+, x-, y+, y-, z+, z-; a Jacobi update is one
+// FMA, x + w (b - A x); the prolongation x + wc x_c[parent] one FMA.  So
+// their results agree bit for bit whatever the compiler would contract.
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+
 // Work split: a warp handles one 32-cell row segment along x; blocks stride
 // over segments.  Grid size is fixed per box so reductions are deterministic.
 struct Seg {

@@ -104,14 +104,14 @@ template <typename T, bool SYM, class VF>
 __device__ __forceinline__ T tail_ax(const Acc<T>& A, int c, int i, int j, int k, T vc, T d, VF vf) {
   const TailLev<T>& L = *A.L;
   const int sy = L.mx, sz = L.mx * L.my;
-  T ax = d * vc;
-  if (i + 1 < L.mx) ax += A.get(TA_XP, c) * vf(c + 1, i + 1, j, k);
-  if (i > 0) ax += (SYM ? A.get(TA_XP, c - 1) : A.get(TA_XM, c)) * vf(c - 1, i - 1, j, k);
-  if (j + 1 < L.my) ax += A.get(TA_YP, c) * vf(c + sy, i, j + 1, k);
-  if (j > 0) ax += (SYM ? A.get(TA_YP, c - sy) : A.get(TA_YM, c)) * vf(c - sy, i, j - 1, k);
+  T ax = rn_mul(d, vc);
+  if (i + 1 < L.mx) ax = fma(A.get(TA_XP, c), vf(c + 1, i + 1, j, k), ax);
+  if (i > 0) ax = fma((SYM ? A.get(TA_XP, c - 1) : A.get(TA_XM, c)), vf(c - 1, i - 1, j, k), ax);
+  if (j + 1 < L.my) ax = fma(A.get(TA_YP, c), vf(c + sy, i, j + 1, k), ax);
+  if (j > 0) ax = fma((SYM ? A.get(TA_YP, c - sy) : A.get(TA_YM, c)), vf(c - sy, i, j - 1, k), ax);
   if (L.mz > 1) {
-    if (k + 1 < L.mz) ax += A.get(TA_ZP, c) * vf(c + sz, i, j, k + 1);
-    if (k > 0) ax += (SYM ? A.get(TA_ZP, c - sz) : A.get(TA_ZM, c)) * vf(c - sz, i, j, k - 1);
+    if (k + 1 < L.mz) ax = fma(A.get(TA_ZP, c), vf(c + sz, i, j, k + 1), ax);
+    if (k > 0) ax = fma((SYM ? A.get(TA_ZP, c - sz) : A.get(TA_ZM, c)), vf(c - sz, i, j, k - 1), ax);
   }
   return ax;
 }
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailArgs<T> a) {
       cell_ijk(L, c, i, j, k);
       const T d = dg[c - c0], vc = v[c - c0];
       const T ax = tail_ax<T, SYM>(A, c, i, j, k, vc, d, vf);
-      o[c - c0] = vc + jac_weight(om, d, dv[c - c0]) * (bl[c - c0] - ax);
+      o[c - c0] = fma(jac_weight(om, d, dv[c - c0]), bl[c - c0] - ax, vc);
     }
   };
   // ---- down: pre-smoothing, residual and restriction
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailArgs<T> a) {
         const T w = jac_weight(om, d, dv[c - c0]);
         const T vc = w * bl[c - c0];
         const T ax = tail_ax<T, SYM>(A, c, i, j, k, vc, d, x0);
-        o[c - c0] = vc + w * (bl[c - c0] - ax);
+        o[c - c0] = fma(w, bl[c - c0] - ax, vc);
       }
       cur = TA_X;
       cl.sync();
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailArgs<T> a) {
           const T* v = bufs[cb];
           auto vf = [&](int cc, int, int, int) { return v[cc]; };
           const T ax = tail_ax<T, SYM>(A, c, i, j, k, v[c], dd, vf);
-          bufs[cb ^ 1][c] = v[c] + w * (bc - ax);
+          bufs[cb ^ 1][c] = fma(w, bc - ax, v[c]);
         }
         __syncthreads();
         cb ^= 1;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailArgs<T> a) {
     {  // coarse correction x += wc e(parent) evaluated wherever the first post-sweep reads x
       auto xp = [&](int c, int i, int j, int k) {
         const int pc = (i >> 1) + C.mx * ((j >> 1) + C.my * (k >> 1));
-        return A.get(cur, c) + wc * AC.get(ec, pc);
+        return fma(wc, AC.get(ec, pc), A.get(cur, c));
       };
       T* o = A.loc(oth);
       const T *bl = A.loc(TA_B), *dg = A.loc(TA_DIAG), *dv = A.loc(TA_DINV);
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailArgs<T> a) {
         const T d = dg[c - c0];
         const T vc = xp(c, i, j, k);
         const T ax = tail_ax<T, SYM>(A, c, i, j, k, vc, d, xp);
-        o[c - c0] = vc + jac_weight(om, d, dv[c - c0]) * (bl[c - c0] - ax);
+        o[c - c0] = fma(jac_weight(om, d, dv[c - c0]), bl[c - c0] - ax, vc);
       }
     }
     cl.sync();

@@ -53,16 +53,16 @@ struct SolverWork {
 template <typename T, bool SYM, typename F>
 __device__ __forceinline__ T stencil(const Op<T>& A, int i, int j, int k, long long c, F xat) {
   const Box b = A.box;
-  T y = A.diag[c] * xat(c, i, j, k);
-  if (i + 1 < b.mx) y += A.xp[c] * xat(c + 1, i + 1, j, k);
-  if (i > 0) y += (SYM ? A.xp[c - 1] : A.xm[c]) * xat(c - 1, i - 1, j, k);
+  T y = rn_mul(A.diag[c], xat(c, i, j, k));
+  if (i + 1 < b.mx) y = fma(A.xp[c], xat(c + 1, i + 1, j, k), y);
+  if (i > 0) y = fma((SYM ? A.xp[c - 1] : A.xm[c]), xat(c - 1, i - 1, j, k), y);
   const long long sy = b.mx;
-  if (j + 1 < b.my) y += A.yp[c] * xat(c + sy, i, j + 1, k);
-  if (j > 0) y += (SYM ? A.yp[c - sy] : A.ym[c]) * xat(c - sy, i, j - 1, k);
+  if (j + 1 < b.my) y = fma(A.yp[c], xat(c + sy, i, j + 1, k), y);
+  if (j > 0) y = fma((SYM ? A.yp[c - sy] : A.ym[c]), xat(c - sy, i, j - 1, k), y);
   if (b.mz > 1) {
     const long long sz = (long long)b.mx * b.my;
-    if (k + 1 < b.mz) y += A.zp[c] * xat(c + sz, i, j, k + 1);
-    if (k > 0) y += (SYM ? A.zp[c - sz] : A.zm[c]) * xat(c - sz, i, j, k - 1);
+    if (k + 1 < b.mz) y = fma(A.zp[c], xat(c + sz, i, j, k + 1), y);
+    if (k > 0) y = fma((SYM ? A.zp[c - sz] : A.zm[c]), xat(c - sz, i, j, k - 1), y);
   }
   return y;
 }
@@ -144,15 +144,15 @@ __device__ __forceinline__ void zmarch(const Op<T>& A, int zc, VAL val, EMIT emi
     const bool up = (k + 1 < bx.mz);
     const T v_hi = up ? val(c + sz, i, j, k + 1) : T(0);
     const T d = __ldg(dg + c);
-    T ax = d * v_c;
-    if (i + 1 < bx.mx) ax += __ldg(xp + c) * val(c + 1, i + 1, j, k);
-    if (i > 0) ax += (SYM ? __ldg(xp + c - 1) : __ldg(A.xm + c)) * val(c - 1, i - 1, j, k);
-    if (j + 1 < bx.my) ax += __ldg(yp + c) * val(c + sy, i, j + 1, k);
-    if (j > 0) ax += (SYM ? __ldg(yp + c - sy) : __ldg(A.ym + c)) * val(c - sy, i, j - 1, k);
+    T ax = rn_mul(d, v_c);
+    if (i + 1 < bx.mx) ax = fma(__ldg(xp + c), val(c + 1, i + 1, j, k), ax);
+    if (i > 0) ax = fma((SYM ? __ldg(xp + c - 1) : __ldg(A.xm + c)), val(c - 1, i - 1, j, k), ax);
+    if (j + 1 < bx.my) ax = fma(__ldg(yp + c), val(c + sy, i, j + 1, k), ax);
+    if (j > 0) ax = fma((SYM ? __ldg(yp + c - sy) : __ldg(A.ym + c)), val(c - sy, i, j - 1, k), ax);
     if (bx.mz > 1) {
       const T zu = up ? __ldg(zp + c) : T(0);
-      ax += zu * v_hi;
-      if (k > 0) ax += (SYM ? zl : __ldg(A.zm + c)) * v_lo;
+      ax = fma(zu, v_hi, ax);
+      if (k > 0) ax = fma((SYM ? zl : __ldg(A.zm + c)), v_lo, ax);
       zl = zu;
     }
     emit(c, i, j, k, v_c, ax, d);
@@ -196,15 +196,15 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Op<T> A, const T* __restri
     const bool up = (k + 1 < bx.mz);
     const T vhi = up ? __ldg(x + c + sz) : T(0);
     const T d = __ldg(dg + c);
-    T ax = d * vc;
-    if (i + 1 < bx.mx) ax += __ldg(xp + c) * __ldg(x + c + 1);
-    if (i > 0) ax += (SYM ? __ldg(xp + c - 1) : __ldg(A.xm + c)) * __ldg(x + c - 1);
-    if (j + 1 < bx.my) ax += __ldg(yp + c) * __ldg(x + c + sy);
-    if (j > 0) ax += (SYM ? __ldg(yp + c - sy) : __ldg(A.ym + c)) * __ldg(x + c - sy);
+    T ax = rn_mul(d, vc);
+    if (i + 1 < bx.mx) ax = fma(__ldg(xp + c), __ldg(x + c + 1), ax);
+    if (i > 0) ax = fma((SYM ? __ldg(xp + c - 1) : __ldg(A.xm + c)), __ldg(x + c - 1), ax);
+    if (j + 1 < bx.my) ax = fma(__ldg(yp + c), __ldg(x + c + sy), ax);
+    if (j > 0) ax = fma((SYM ? __ldg(yp + c - sy) : __ldg(A.ym + c)), __ldg(x + c - sy), ax);
     if (has_z) {
       const T zu = up ? __ldg(zp + c) : T(0);
-      ax += zu * vhi;
-      if (k > 0) ax += (SYM ? zl : __ldg(A.zm + c)) * vlo;
+      ax = fma(zu, vhi, ax);
+      if (k > 0) ax = fma((SYM ? zl : __ldg(A.zm + c)), vlo, ax);
       zl = zu;
     }
     if (KIND == SK_JAC) {
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Op<T> A, const T* __restri
         w = __fdividef(omega, d);
       else
         w = __ldg(A.dinv + c);
-      out[c] = vc + w * (__ldg(b + c) - ax);
+      out[c] = fma(w, __ldg(b + c) - ax, vc);
     } else if (KIND == SK_MV) {
       out[c] = ax;
     } else {
@@ -822,6 +822,95 @@ __global__ void k_restrict_sum(Box fb, Box cb, const T* __restrict__ r, T* __res
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused passes on the assembled (coarse) levels, one thread per output cell
+// in the z view: the residual with the restriction (k_resid_restrict_c: each
+// coarse cell sums the residuals b - A x of its children, added in the order
+// of k_restrict_sum) and the prolongation with the first post-smoothing
+// sweep (k_prolong_jac_c: x + wc x_c[parent] formed at the cell and its
+// neighbours with the FMA of k_prolong_add, then the Jacobi update of
+// k_stencil).  row_ax repeats k_stencil's statements for one cell, so both
+// give the separate launches' values bit for bit with one launch fewer each
+// per level and V-cycle (the coarse levels are launch-latency bound).
+// ---------------------------------------------------------------------------
+template <typename T, bool SYM, class XV>
+__device__ __forceinline__ T row_ax(const Op<T>& Z, long long c, int i, int j, int k, T vc, XV xv) {
+  const Box bx = Z.box;
+  const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+  const T d = __ldg(Z.diag + c);
+  T ax = rn_mul(d, vc);
+  if (i + 1 < bx.mx) ax = fma(__ldg(Z.xp + c), xv(c + 1, i + 1, j, k), ax);
+  if (i > 0) ax = fma((SYM ? __ldg(Z.xp + c - 1) : __ldg(Z.xm + c)), xv(c - 1, i - 1, j, k), ax);
+  if (j + 1 < bx.my) ax = fma(__ldg(Z.yp + c), xv(c + sy, i, j + 1, k), ax);
+  if (j > 0) ax = fma((SYM ? __ldg(Z.yp + c - sy) : __ldg(Z.ym + c)), xv(c - sy, i, j - 1, k), ax);
+  if (bx.mz > 1) {
+    const bool up = (k + 1 < bx.mz);
+    const T vhi = up ? xv(c + sz, i, j, k + 1) : T(0);
+    const T zu = up ? __ldg(Z.zp + c) : T(0);
+    ax = fma(zu, vhi, ax);
+    if (k > 0) ax = fma((SYM ? __ldg(Z.zp + c - sz) : __ldg(Z.zm + c)), xv(c - sz, i, j, k - 1), ax);
+  }
+  return ax;
+}
+
+template <typename T, bool SYM>
+__global__ void k_resid_restrict_c(Op<T> Z, const T* __restrict__ b, const T* __restrict__ x, Box cz,
+                                   T* __restrict__ bc, const KScal* sc) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const Box fb = Z.box;
+  const Seg s = make_seg(cz);
+  const int ni = fb.mx > 1 ? 2 : 1, nj = fb.my > 1 ? 2 : 1, nk = fb.mz > 1 ? 2 : 1;
+  auto xv = [&](long long n, int, int, int) { return __ldg(x + n); };
+  VOS_SEG_LOOP(s, q) {
+    int I, J, K;
+    seg_decode(s, cz, q, I, J, K);
+    if (I >= cz.mx) continue;
+    T sum = 0;
+    for (int dk = 0; dk < nk; ++dk) {
+      const int k = (fb.mz > 1) ? 2 * K + dk : 0;
+      if (k >= fb.mz) continue;
+      for (int dj = 0; dj < nj; ++dj) {
+        const int j = (fb.my > 1) ? 2 * J + dj : 0;
+        if (j >= fb.my) continue;
+        for (int di = 0; di < ni; ++di) {
+          const int i = (fb.mx > 1) ? 2 * I + di : 0;
+          if (i >= fb.mx) continue;
+          const long long c = i + (long long)fb.mx * (j + (long long)fb.my * k);
+          sum += __ldg(b + c) - row_ax<T, SYM>(Z, c, i, j, k, __ldg(x + c), xv);
+        }
+      }
+    }
+    bc[I + (long long)cz.mx * (J + (long long)cz.my * K)] = sum;
+  }
+}
+
+template <typename T, bool SYM>
+__global__ void k_prolong_jac_c(Op<T> Z, const T* __restrict__ b, const T* __restrict__ x, Box cz,
+                                const T* __restrict__ ec, T wc, T omega, T* __restrict__ out, const KScal* sc) {
+  VOS_COUNT_EXEC();
+  DONE_RETURN(sc);
+  const Box fb = Z.box;
+  const Seg s = make_seg(fb);
+  auto xv = [&](long long n, int i, int j, int k) {
+    return fma(wc, __ldg(ec + (i >> 1) + (long long)cz.mx * ((j >> 1) + (long long)cz.my * (k >> 1))), __ldg(x + n));
+  };
+  VOS_SEG_LOOP(s, q) {
+    int i, j, k;
+    seg_decode(s, fb, q, i, j, k);
+    if (i >= fb.mx) continue;
+    const long long c = i + (long long)fb.mx * (j + (long long)fb.my * k);
+    const T vc = xv(c, i, j, k);
+    const T ax = row_ax<T, SYM>(Z, c, i, j, k, vc, xv);
+    T w;
+    if constexpr (sizeof(T) == 4)
+      w = __fdividef(omega, __ldg(Z.diag + c));
+    else
+      w = __ldg(Z.dinv + c);
+    out[c] = fma(w, __ldg(b + c) - ax, vc);
+  }
+}
+
 // Dot products with a device-side finalisation (deterministic FP64 reduce).
 enum DotFin { DF_PCG_BETA = 0, DF_PCG_ALPHA = 1, DF_BICG_ALPHA = 2, DF_BICG_OMEGA = 3, DF_FCG_BETA = 4 };
 
@@ -1109,7 +1198,7 @@ __global__ void k_coarse_solve(Op<T> A, const T* __restrict__ b, T* __restrict__
     if (c < n) {
       auto xat = [&](long long cc, int, int, int) -> T { return xs[cur][cc]; };
       T ax = stencil<T, SYM>(A, i, j, k, c, xat);
-      xs[cur ^ 1][c] = xs[cur][c] + dinv * (bc - ax);
+      xs[cur ^ 1][c] = fma(dinv, bc - ax, xs[cur][c]);
     }
     __syncthreads();
     cur ^= 1;
@@ -2173,6 +2262,14 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     }
     return false;
   };
+  // coarse (assembled) levels of at most 2^18 cells: residual with
+  // restriction, prolongation with the first post-smoothing sweep
+  // (bit-identical to the separate launches).  On larger levels the
+  // one-thread-per-cell gathers are slower than the z-marching sweep plus a
+  // streaming pass.
+  auto fused_coarse = [&](int l) {
+    return g_mf4 && l >= 1 && l + 1 < L && box_cells(h.lev[l].op.box) <= (1LL << 18);
+  };
   auto jac0 = [&](int l, T* dst) {
     const Op<T>& A = h.lev[l].op;
     const T* b;
@@ -2246,6 +2343,12 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
                 A.mfs, (const float*)b, (const float*)cur, zbox(C.box), (float*)h.lev[l + 1].b, z.zc,
                 (const KScal*)sc);
       }
+    } else if (fused_coarse(l)) {
+      const Op<T> Z = zview(A);
+      const Box cz = zbox(C.box);
+      vlaunch(KN("mg_resid_restrict", false), ((3.0 + n_offs(A)) * ncell(A) + ncell(C)) * sizeof(T),
+              k_resid_restrict_c<T, SYM>, grid_for(cz, 0), kThreads, st, Z, b, (const T*)cur, cz, h.lev[l + 1].b,
+              (const KScal*)sc);
     } else {
       stencil_launch<T, SYM>(KN("mg_resid", l == 0), SK_RES, A, b, cur, oth, om, sc, st);
       vlaunch(KN("mg_restrict", l == 0), (ncell(A) + ncell(C)) * sizeof(T), k_restrict_sum<T>, grid_for(C.box, 0),
@@ -2282,6 +2385,14 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
         vlaunch("mg_jac_pro_mf_f32_L0", bytes, k_stencil_mf4<SK_JAC, XS_PRO>, z4.grid, z4.block, st, Z.box, A.mfe,
                 A.mfs, (const float*)b, (const float*)cur, (float*)oth, (float)om, z4.zc, (const KScal*)sc, cz,
                 (const float*)h.lev[l + 1].x, (float)wc);
+      T* tmp = cur;
+      cur = oth;
+      oth = tmp;
+      s0 = 1;
+    } else if (fused_coarse(l)) {  // first sweep on x + wc P x_coarse, formed on the fly
+      vlaunch(KN("mg_jac_pro", false), ((4.0 + n_offs(A)) * ncell(A) + ncell(h.lev[l + 1].op)) * sizeof(T),
+              k_prolong_jac_c<T, SYM>, grid_for(fz, 0), kThreads, st, zview(A), b, (const T*)cur, cz,
+              (const T*)h.lev[l + 1].x, wc, om, oth, (const KScal*)sc);
       T* tmp = cur;
       cur = oth;
       oth = tmp;

@@ -666,7 +666,9 @@ def vos_set_launch_mode(graphs):
 
 def vos_set_vector_sweeps(on):
     """1 (default): four-cells-per-thread matrix-free pressure sweeps when nx
-    is a multiple of 4; 0: one cell per thread (identical results)."""
+    is a multiple of 4 and fused residual-restriction / prolongation-sweep
+    passes in the multigrid cycles; 0: one cell per thread and separate
+    passes (identical results)."""
     load_library().vos_set_vector_sweeps(1 if on else 0)
 
 

@@ -64,12 +64,14 @@ def test_2d_tiles(V):
         V.vos_destroy(h)
 
 
+@pytest.mark.parametrize("precision", [1, 0])
 @pytest.mark.parametrize("shape", [(24, 20, 36), (15, 13, 36), (1, 96, 160), (1, 97, 160), (10, 14, 30)])
-def test_vector_sweeps_identical(V, shape):
+def test_vector_sweeps_identical(V, shape, precision):
     """The four-cells-per-thread matrix-free pressure sweeps (16-byte rows,
     nx % 4 == 0) compute each cell with the arithmetic of the one-cell
-    kernel, and their fused residual-restriction and prolongation-sweep
-    passes sum and round as the separate passes do: whole mixed-precision
+    kernel, and the fused residual-restriction and prolongation-sweep
+    passes (fine level and assembled coarse levels) sum and round as the
+    separate passes do: whole mixed-precision
     steps give identical fields and iteration counts, graph launches (odd
     ny and nz: y pairs and z pairs without a partner); a grid with
     nx % 4 != 0 (30) keeps the one-cell kernel."""
@@ -78,7 +80,7 @@ def test_vector_sweeps_identical(V, shape):
     else:
         es = I.sphere_rock_3d(shape, seed=5, median_r=3.0, sigma=0.3, target_porosity=0.45,
                               start_solid=0.6, band=2, margin=3.0)
-    prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=8.0, method="ivos", Vm=0.2, precision=1)
+    prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=8.0, method="ivos", Vm=0.2, precision=precision)
     out = []
     # the MG-PCG form fused with the fine sweeps sums two dots in the sweeps'
     # order (not bit-identical to the separate kernels): off for this test
