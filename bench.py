@@ -604,6 +604,8 @@ def main():
                     help="start each momentum solve from u^n instead of the extrapolation 2 u^n - u^{n-1}")
     ap.add_argument("--scalar-sweeps", action="store_true",
                     help="one cell per thread in the matrix-free pressure sweeps (same results; for comparison)")
+    ap.add_argument("--fused-mask", type=int, default=None,
+                    help="vos_set_fused_pcg mask (default: the library's, all fused forms)")
     ap.add_argument("--four-kernel-pcg", action="store_true",
                     help="the FP32 inner Krylov solves with separate kernels (vos_set_fused_pcg(0)) instead of "
                          "the fused forms (for comparison)")
@@ -639,6 +641,8 @@ def main():
         V.vos_set_vector_sweeps(0)
     if args.four_kernel_pcg:
         V.vos_set_fused_pcg(0)
+    elif args.fused_mask is not None:
+        V.vos_set_fused_pcg(args.fused_mask)
     if args.workload == "batch64":
         eps, prms = batch_workload(64)
         N = int(sum(e.size for e in eps))
@@ -716,8 +720,7 @@ def main():
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "launch": "eager" if args.eager else "graph", "tiles": r["tiles"],
                       "coarse_cycle": "cluster-resident" if args.coarse_cycle else "separate launches",
-                      "krylov": "separate kernels" if args.four_kernel_pcg else
-                      "fused (two-kernel diagonal PCG; MG-PCG with the first and last fine sweeps)"},
+                      "fused_mask": 0 if args.four_kernel_pcg else (7 if args.fused_mask is None else args.fused_mask)},
            "roofline": r["roofline"], "gpu_launches": r["launches"],
            "fp64_value": fp64_value, "fp64_ms_per_step": r64["ms"] if r64 else None,
            "mixed_vs_fp64": (value / fp64_value) if fp64_value else None,

@@ -474,8 +474,8 @@ int vos_set_coarse_cycle(int on);
  *   passes.  Identical results (each cell's arithmetic and each sum's order
  *   are the same); takes effect at the next launch. */
 int vos_set_vector_sweeps(int on);
-/* vos_set_fused_pcg(mask): fused forms of the FP32 inner Krylov solves of
- *   the mixed path; default 3 (both), 0 for the separate kernels.
+/* vos_set_fused_pcg(mask): fused forms of the mixed path's solves; default
+ *   7 (all three), 0 for the separate kernels and the FP64 residual.
  *   Bit 0 (VOS_FUSED_DIAG_PCG): diagonally preconditioned CG on a
  *   constant-link operator (the momentum systems when they take the
  *   diagonal preconditioner) in two kernels per iteration -- the direction
@@ -490,11 +490,20 @@ int vos_set_vector_sweeps(int on);
  *   deflation adds its share of r.z): two fewer passes over the vectors per
  *   iteration.  The cell values are the separate kernels'; two dot products
  *   are summed in another order, so the iterates agree to rounding.
- *   Returns VOS_EINVAL for a mask outside 0..3.  Takes effect at the next
+ *   Bit 2 (VOS_FUSED_DF_RESIDUAL): the refinement residual b - A x of a
+ *   symmetric system solved to 1e-9 or looser is evaluated after the first
+ *   pass in double-FP32 arithmetic on the FP32 pipes (FP32 hi + lo pairs of
+ *   b, x and the operator, cut from the FP64 values by integer operations,
+ *   relative error below 2^-46 per value) instead of FP64; the first pass,
+ *   tighter solves and values of magnitude 2^127 or more keep the FP64
+ *   residual.  The solves still reach their tolerance; the fields agree with
+ *   the FP64-residual path to that tolerance.
+ *   Returns VOS_EINVAL for a mask outside 0..7.  Takes effect at the next
  *   launch; a step already captured as a CUDA graph keeps the form it was
  *   captured with. */
 #define VOS_FUSED_DIAG_PCG 1
 #define VOS_FUSED_MG_PCG 2
+#define VOS_FUSED_DF_RESIDUAL 4
 int vos_set_fused_pcg(int mask);
 int vos_prof_enable(const char* filter);
 int vos_prof_report(char* buf, size_t len);

@@ -1018,7 +1018,7 @@ int vos_set_vector_sweeps(int on) {
 }
 
 int vos_set_fused_pcg(int mask) {
-  if (mask < 0 || mask > 3) return VOS_EINVAL;
+  if (mask < 0 || mask > 7) return VOS_EINVAL;
   vos::g_fused_pcg = mask;
   return VOS_OK;
 }

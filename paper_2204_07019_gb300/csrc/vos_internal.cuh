@@ -455,6 +455,13 @@ struct SolveResult {
 // x: solution view (initial guess on entry).  sym selects PCG or BiCGStab;
 // use_mg selects the multigrid V-cycle (else the diagonal) preconditioner
 // for PCG (BiCGStab always uses multigrid).
+// Double-FP32 copies of a symmetric system for the refinement residual of
+// the mixed path (each value v as float hi + lo, see df_split): the
+// operator's diagonal and plus links in the z view, the right-hand side and
+// the current solution, in the solve box's flat layout.
+struct DFBuf {
+  float2 *dg, *xp, *yp, *zp, *b, *x;
+};
 struct SolverWork;  // opaque: Krylov vectors + scalars
 template <typename T>
 SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol,

@@ -41,6 +41,8 @@ __host__ int grid_for(Box b, int max_blocks) {
 struct SolverWork {
   long long cap;
   void *r, *z, *p, *p2, *q, *e, *rh, *v, *s, *t, *ph, *sh;
+  DFBuf df;         // double-FP32 copies for the refinement residual (mixed path)
+  int* dfbad;       // device: 1 once a value did not fit the double-FP32 form
   KScal* sc;        // device
   KScal* sc_host;   // pinned
   double* outer;    // device [|D^-1 r|^2, |D^-1 b|^2, |r|^2]
@@ -999,23 +1001,69 @@ __global__ void k_pcg_p(long long n, const T* __restrict__ z, T* __restrict__ p,
     p[c] = first ? __ldg(z + c) : fma(beta, p[c], __ldg(z + c));
 }
 
-// FP64 true residual (see k_outer_residual) in the 2.5D form.
+// ---------------------------------------------------------------------------
+// Double-FP32 ("double-float") form of FP64 values for the refinement
+// residual of the mixed path.  FP64 arithmetic is the bottleneck of the FP64
+// residual on this part, so after the first refinement pass of a solve the
+// residual b - A x is evaluated from FP32 pairs on the FP32 pipes.
+// df_split cuts a double into hi = its leading 24 significand bits (exact,
+// truncated) and lo = the next 23 bits (exact), by integer operations on the
+// bit pattern, so it costs no FP64 instruction: |v - hi - lo| < 2^-46 |v|.
+// Magnitudes below 2^-80 keep hi only (below 2^-126, nothing); a magnitude of
+// 2^127 or more does not fit and is reported through the return value.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool df_split(double v, float2& out) {
+  const unsigned h = (unsigned)__double2hiint(v), l = (unsigned)__double2loint(v);
+  const unsigned e = (h >> 20) & 0x7ffu, sgn = h & 0x80000000u;
+  if (e > 1150u) {
+    out = make_float2(0.0f, 0.0f);
+    return false;
+  }
+  if (e < 897u) {
+    out = make_float2(0.0f, 0.0f);
+    return true;
+  }
+  const float hi = __uint_as_float(sgn | ((e - 896u) << 23) | ((h & 0xfffffu) << 3) | (l >> 29));
+  float lo = 0.0f;
+  if (e >= 943u) {
+    const float unit = __uint_as_float(0x4b000000u | ((l & 0x1fffffffu) >> 6)) - 8388608.0f;  // bits 28..6, exactly
+    lo = __uint_as_float(__float_as_uint(unit * __uint_as_float((e - 942u) << 23)) | sgn);
+  }
+  out = make_float2(hi, lo);
+  return true;
+}
+
+// s - a * x in double-FP32: (s.x, s.y) is an unevaluated sum, a * x is
+// formed from the exact product of the leading parts (FMA error term) and
+// the two cross terms; the new leading part comes from an exact two-sum.
+__device__ __forceinline__ void df_sub_prod(float2& s, float2 a, float2 x) {
+  const float p = __fmul_rn(a.x, x.x);
+  const float pe = __fmaf_rn(a.x, x.x, -p);
+  const float cr = __fmaf_rn(a.x, x.y, __fmul_rn(a.y, x.x));
+  const float t = __fsub_rn(s.x, p);
+  const float bp = __fsub_rn(t, s.x);
+  const float err = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bp)), __fsub_rn(-p, bp));
+  s.x = t;
+  s.y = __fsub_rn(__fadd_rn(s.y, err), __fadd_rn(pe, cr));
+}
+
+// FP64 true residual b - A x in the 2.5D form (device body shared by the
+// kernels below).  outer[0] = |D^-1 r|^2 and outer[1] = |D^-1 b|^2 (the
+// convergence test); outer[2] = |r|^2, the unscaled norm the inner Krylov
+// loop measures.  b is fixed during a solve, so |D^-1 b|^2 is summed on its
+// first pass only (need_bb) and kept in outer[1]: FP64 arithmetic, not
+// memory, bounds this kernel on this part.  dfo (non-null): also write the
+// double-FP32 copies of b, x and the operator's diagonal and plus links
+// (dfbad = 1 if a value does not fit that form).
 template <typename T, bool SYM>
-__global__ void __launch_bounds__(kThreads) k_outer_residual_z(Op<double> A, const double* __restrict__ b,
-                                                              View<double> x, T* __restrict__ rT, double* outer,
-                                                              const int* pass, int zc, RedScratch rs) {
-  VOS_COUNT_EXEC();
-  // outer[0] = |D^-1 r|^2 and outer[1] = |D^-1 b|^2 (convergence test);
-  // outer[2] = |r|^2, the unscaled norm the inner Krylov loop measures.
-  // b is fixed during a solve, so |D^-1 b|^2 is summed on its first pass
-  // only (*pass == 0; always when pass is null) and kept in outer[1]: FP64
-  // arithmetic, not memory, bounds this kernel on this part.
-  const bool need_bb = (pass == nullptr) || (*pass == 0);
+__device__ __forceinline__ void resid64_body(const Op<double>& A, const double* __restrict__ b, View<double> x,
+                                             T* __restrict__ rT, double* outer, bool need_bb, int zc,
+                                             const RedScratch& rs, const DFBuf* dfo, int* dfbad) {
   double acc[3] = {0.0, 0.0, 0.0};
   auto val = [&](long long, int i, int j, int k) -> double {
     return __ldg(x.base + i + (long long)x.sy * j + (long long)x.sz * k);
   };
-  auto emit = [&](long long c, int, int, int, double, double ax, double) {
+  auto emit = [&](long long c, int i, int j, int k, double vc, double ax, double d) {
     const double bc = __ldg(b + c);
     const double r = bc - ax;
     rT[c] = (T)r;
@@ -1027,12 +1075,121 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual_z(Op<double> A, con
       acc[1] += b1 * b1;
     }
     acc[2] += r * r;
+    if (dfo) {
+      bool ok = df_split(bc, dfo->b[c]);
+      ok &= df_split(vc, dfo->x[c]);
+      ok &= df_split(d, dfo->dg[c]);
+      if (i + 1 < A.box.mx) ok &= df_split(__ldg(A.xp + c), dfo->xp[c]);
+      if (j + 1 < A.box.my) ok &= df_split(__ldg(A.yp + c), dfo->yp[c]);
+      if (k + 1 < A.box.mz) ok &= df_split(__ldg(A.zp + c), dfo->zp[c]);
+      if (!ok) *dfbad = 1;
+    }
   };
   zmarch<double, SYM>(A, zc, val, emit);
   if (grid_sum<3>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
     outer[0] = acc[0];
     if (need_bb) outer[1] = acc[1];
     outer[2] = acc[2];
+  }
+}
+
+// The FP64 residual.  pass: the solve's refinement pass counter (null: a
+// first pass); only0: run on the first pass only (later passes use
+// k_outer_residual_df); dfo.x non-null: write the double-FP32 copies.
+template <typename T, bool SYM>
+__global__ void __launch_bounds__(kThreads) k_outer_residual_z(Op<double> A, const double* __restrict__ b,
+                                                              View<double> x, T* __restrict__ rT, double* outer,
+                                                              const int* pass, int zc, RedScratch rs, DFBuf dfo,
+                                                              int* dfbad, int only0) {
+  VOS_COUNT_EXEC();
+  const bool first = (pass == nullptr) || (*pass == 0);
+  if (only0 && !first) return;  // the same for every thread of the launch
+  resid64_body<T, SYM>(A, b, x, rT, outer, first, zc, rs, dfo.x ? &dfo : nullptr, dfbad);
+}
+
+// The refinement residual of passes after the first in double-FP32 (mixed
+// path, symmetric systems solved to 1e-9 or looser): from the copies written
+// by the first pass (operator, b) and by the outer updates (x), with the
+// row's terms subtracted in the FP64 kernel's order, r = hi + lo rounded to
+// FP32.  The norms are summed in compensated FP32 after scaling by powers of
+// two taken from the previous pass's norms (so the squares stay in range)
+// and rescaled exactly in FP64.  If a value did not fit the double-FP32 form
+// (*dfbad), the FP64 body runs instead.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_outer_residual_df(DFBuf d, const float* __restrict__ dinv32,
+                                                               Op<double> A, const double* __restrict__ b,
+                                                               View<double> x, T* __restrict__ rT, double* outer,
+                                                               const int* pass, const int* dfbad, int zc,
+                                                               RedScratch rs) {
+  VOS_COUNT_EXEC();
+  if (pass != nullptr && *pass == 0) return;  // the same for every thread of the launch
+  if (*dfbad) {
+    resid64_body<T, true>(A, b, x, rT, outer, false, zc, rs, nullptr, nullptr);
+    return;
+  }
+  const Box bx = A.box;
+  auto scale_exp = [](double o) {  // k with o * 4^-k near 1, |k| <= 100
+    int e = 0;
+    if (o > 0.0) frexp(o, &e);
+    e /= 2;
+    return e > 100 ? 100 : (e < -100 ? -100 : e);
+  };
+  const int k0s = scale_exp(outer[0]), k2s = scale_exp(outer[2]);
+  const float s0 = ldexpf(1.0f, -k0s), s2 = ldexpf(1.0f, -k2s);
+  PSum<float> p0, p2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int kb = blockIdx.z * zc;
+  const int ke = min(kb + zc, bx.mz);
+  if (i < bx.mx && j < bx.my && kb < ke) {
+    const long long sy = bx.mx, sz = (long long)bx.mx * bx.my;
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    // z march: x at k-1, k, k+1 and the plane's own words in registers; the
+    // loads of plane k+1 (x at k+2) are issued before plane k is computed
+    long long c = i + sy * j + sz * kb;
+    float2 xlo = (kb > 0) ? __ldg(d.x + c - sz) : z2;
+    float2 xc = __ldg(d.x + c);
+    float2 xhi = (kb + 1 < bx.mz) ? __ldg(d.x + c + sz) : z2;
+    float2 zl = (kb > 0) ? __ldg(d.zp + c - sz) : z2;
+    float2 bc = __ldg(d.b + c), dgc = __ldg(d.dg + c);
+    float2 zu = (kb + 1 < bx.mz) ? __ldg(d.zp + c) : z2;
+    float dic = __ldg(dinv32 + c);
+    for (int k = kb; k < ke; ++k, c += sz) {
+      const bool up = (k + 1 < bx.mz);
+      const bool nxt = (k + 1 < ke);
+      const float2 x2 = (nxt && k + 2 < bx.mz) ? __ldg(d.x + c + 2 * sz) : z2;
+      const float2 bn = nxt ? __ldg(d.b + c + sz) : z2, dgn = nxt ? __ldg(d.dg + c + sz) : z2;
+      const float2 zun = (nxt && k + 2 < bx.mz) ? __ldg(d.zp + c + sz) : z2;
+      const float din = nxt ? __ldg(dinv32 + c + sz) : 0.0f;
+      float2 S = bc;
+      df_sub_prod(S, dgc, xc);
+      if (i + 1 < bx.mx) df_sub_prod(S, __ldg(d.xp + c), __ldg(d.x + c + 1));
+      if (i > 0) df_sub_prod(S, __ldg(d.xp + c - 1), __ldg(d.x + c - 1));
+      if (j + 1 < bx.my) df_sub_prod(S, __ldg(d.yp + c), __ldg(d.x + c + sy));
+      if (j > 0) df_sub_prod(S, __ldg(d.yp + c - sy), __ldg(d.x + c - sy));
+      if (bx.mz > 1) {
+        if (up) df_sub_prod(S, zu, xhi);
+        if (k > 0) df_sub_prod(S, zl, xlo);
+      }
+      const float r = __fadd_rn(S.x, S.y);
+      rT[c] = (T)r;
+      const float r1 = __fmul_rn(__fmul_rn(r, dic), s0), r2 = __fmul_rn(r, s2);
+      p0.add(r1, r1);
+      p2.add(r2, r2);
+      xlo = xc;
+      xc = xhi;
+      xhi = x2;
+      zl = zu;
+      zu = zun;
+      bc = bn;
+      dgc = dgn;
+      dic = din;
+    }
+  }
+  double acc[2] = {p0.get(), p2.get()};
+  if (grid_sum<2>(acc, rs.partials, rs.counter) && lin_tid() == 0) {
+    outer[0] = ldexp(acc[0], 2 * k0s);
+    outer[2] = ldexp(acc[1], 2 * k2s);
   }
 }
 
@@ -1842,7 +1999,8 @@ __global__ void k_bicg_x(long long n, const T* __restrict__ ph, const T* __restr
 // ---------------------------------------------------------------------------
 // x += e (x a strided view)
 template <typename T>
-__global__ void k_outer_update(Box bx, View<double> x, const T* __restrict__ e) {
+__global__ void k_outer_update(Box bx, View<double> x, const T* __restrict__ e, float2* __restrict__ xdf,
+                               int* dfbad) {
   VOS_COUNT_EXEC();
   const Seg s = make_seg(bx);
   VOS_SEG_LOOP(s, q) {
@@ -1850,7 +2008,10 @@ __global__ void k_outer_update(Box bx, View<double> x, const T* __restrict__ e) 
     seg_decode(s, bx, q, i, j, k);
     if (i >= bx.mx) continue;
     long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
-    x.base[i + (long long)x.sy * j + (long long)x.sz * k] += (double)e[c];
+    double* px = x.base + i + (long long)x.sy * j + (long long)x.sz * k;
+    const double nx = *px + (double)e[c];
+    *px = nx;
+    if (xdf && !df_split(nx, xdf[c])) *dfbad = 1;  // double-FP32 copy for the next residual
   }
 }
 
@@ -2008,7 +2169,8 @@ template void hier_carve<double>(Hier<double>&, Box, int, char*&, const MGParams
 template void hier_carve<float>(Hier<float>&, Box, int, char*&, const MGParams&, bool, const Op<double>*);
 
 size_t solver_work_bytes(long long max_cells) {
-  return 12 * align256((size_t)max_cells * sizeof(double)) + align256(sizeof(KScal)) + align256(4 * sizeof(double));
+  return 18 * align256((size_t)max_cells * sizeof(double)) + align256(sizeof(KScal)) + align256(4 * sizeof(double)) +
+         align256(sizeof(int));
 }
 
 SolverWork* solver_work_carve(char*& cur, long long max_cells) {
@@ -2024,6 +2186,13 @@ SolverWork* solver_work_carve(char*& cur, long long max_cells) {
   cur += align256(sizeof(KScal));
   w->outer = (double*)cur;
   cur += align256(4 * sizeof(double));
+  float2** dfv[6] = {&w->df.dg, &w->df.xp, &w->df.yp, &w->df.zp, &w->df.b, &w->df.x};
+  for (int i = 0; i < 6; ++i) {
+    *dfv[i] = (float2*)cur;
+    cur += vs;
+  }
+  w->dfbad = (int*)cur;
+  cur += align256(sizeof(int));
   cudaMallocHost((void**)&w->sc_host, sizeof(KScal));
   cudaMallocHost((void**)&w->outer_host, 2 * sizeof(double));
   return w;
@@ -2484,8 +2653,9 @@ static void pcg_precond(Hier<T>& h, const KVec<T>& k, long long n, SolverWork* w
 
 // Process-wide switches of the fused Krylov forms (vos_set_fused_pcg): bit 0
 // the two-kernel diagonal PCG on constant-link operators, bit 1 MG-PCG on the
-// matrix-free level fused with the V-cycle's first and last fine sweeps.
-int g_fused_pcg = 3;
+// matrix-free level fused with the V-cycle's first and last fine sweeps, bit
+// 2 the double-FP32 refinement residual (see df_residual).
+int g_fused_pcg = 7;
 
 // One PCG iteration (kernels early-exit once the solve is done).  parity:
 // the iteration's index within its pass modulo 2 (the two-kernel diagonal
@@ -2755,7 +2925,8 @@ __global__ void k_loop_check(const KScal* sc, cudaGraphConditionalHandle hi) {
 
 // x += e, or x = 0 when the right-hand side was zero.
 template <typename T>
-__global__ void k_outer_update_g(Box bx, View<double> x, const T* __restrict__ e, const SolveStats* ss) {
+__global__ void k_outer_update_g(Box bx, View<double> x, const T* __restrict__ e, const SolveStats* ss,
+                                 float2* __restrict__ xdf, int* dfbad) {
   VOS_COUNT_EXEC();
   const bool zero = ss->zero != 0;
   const Seg s = make_seg(bx);
@@ -2765,7 +2936,9 @@ __global__ void k_outer_update_g(Box bx, View<double> x, const T* __restrict__ e
     if (i >= bx.mx) continue;
     long long c = i + (long long)bx.mx * (j + (long long)bx.my * k);
     double* px = x.base + i + (long long)x.sy * j + (long long)x.sz * k;
-    *px = zero ? 0.0 : *px + (double)e[c];
+    const double nx = zero ? 0.0 : *px + (double)e[c];
+    *px = nx;
+    if (xdf && !df_split(nx, xdf[c])) *dfbad = 1;  // double-FP32 copy for the next residual
   }
 }
 
@@ -2804,6 +2977,22 @@ static cudaError_t capture_graph_of(cudaStream_t st, cudaGraph_t* g) {
   return cs == cudaStreamCaptureStatusActive ? cudaSuccess : cudaErrorStreamCaptureInvalidated;
 }
 
+// The double-FP32 refinement residual (after the first pass) is used by
+// mixed-precision solves of symmetric systems to a tolerance of 1e-9 or
+// looser: its error, a few 2^-46 of the row's terms (measured about 5e-11 of
+// norm(D^-1 b) on the rock's pressure system near its solution, where the
+// rows cancel by 2e4), stays well below such a tolerance (vos_set_fused_pcg
+// bit 2).
+template <typename T>
+static bool df_residual(const Op<double>& op64, double rtol) {
+  return sizeof(T) == 4 && op64.sym && rtol >= 1e-9 && (g_fused_pcg & 4) != 0;
+}
+// words moved per cell: b, x (and its six neighbours through L1), diagonal
+// and three links as double-FP32 pairs, FP32 omega/diag in, FP32 r out
+static double df_bytes(const Op<double>& A) {
+  return (double)box_cells(A.box) * ((2.0 + n_offs(A) + 2.0) * 8.0 + 8.0);
+}
+
 template <typename T>
 cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, View<double> x, double rtol,
                           int max_iter, SolverWork* w, const RedScratch& rs, cudaStream_t st, bool use_mg,
@@ -2820,6 +3009,8 @@ cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, V
             kThreads, st, op64, h.lev[0].op, n, links);
   }
   if (use_mg || !sym) build_coarse_levels<T>(h, st);
+  const bool dfmode = df_residual<T>(op64, rtol);
+  if (dfmode) VOS_CUDA_TRY(cudaMemsetAsync(w->dfbad, 0, sizeof(int), st));
   vlaunch("ctrl_init", 0.0, k_ctrl_init, 1, 32, st, ss, w->sc);
   cudaGraph_t g0;
   VOS_CUDA_TRY(capture_graph_of(st, &g0));
@@ -2834,10 +3025,13 @@ cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, V
     const int* pass = &ss->outer;  // 0 until the controller starts the first pass
     if (op64.sym)
       vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, true>, zr.grid, zr.block, s1, oz, b, xz, (T*)w->r,
-              w->outer, pass, zr.zc, rs);
+              w->outer, pass, zr.zc, rs, dfmode ? w->df : DFBuf{}, w->dfbad, dfmode ? 1 : 0);
     else
       vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, false>, zr.grid, zr.block, s1, oz, b, xz, (T*)w->r,
-              w->outer, pass, zr.zc, rs);
+              w->outer, pass, zr.zc, rs, DFBuf{}, w->dfbad, 0);
+    if (dfmode)
+      vlaunch("outer_residual_df", df_bytes(op64), k_outer_residual_df<T>, zr.grid, zr.block, s1, w->df,
+              (const float*)h.lev[0].op.dinv, oz, b, xz, (T*)w->r, w->outer, pass, (const int*)w->dfbad, zr.zc, rs);
     cudaGraph_t g1;
     VOS_CUDA_TRY(capture_graph_of(s1, &g1));
     VOS_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, g1, 0, cudaGraphCondAssignDefault));
@@ -2864,7 +3058,7 @@ cudaError_t solve_capture(const Op<double>& op64, Hier<T>& h, const double* b, V
     vlaunch("loop_check", 0.0, k_loop_check, 1, 32, s2, (const KScal*)w->sc, hi);
     VOS_CUDA_TRY(end_body(s2));
     vlaunch("outer_update", (double)n * (sizeof(T) + 16.0), k_outer_update_g<T>, grid_for(bx, 0), kThreads, s1, bx, x,
-            (const T*)k.e, (const SolveStats*)ss);
+            (const T*)k.e, (const SolveStats*)ss, dfmode ? w->df.x : (float2*)nullptr, w->dfbad);
   }
   VOS_CUDA_TRY(end_body(s1));
   return cudaGetLastError();
@@ -2897,13 +3091,19 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
   const Op<double> oz = zview(op64);
   const View<double> xz = zview_x(x, bx);
   const ZCfg zr = zcfg(oz.box);
+  const bool dfmode = df_residual<T>(op64, rtol);
+  if (dfmode) cudaMemsetAsync(w->dfbad, 0, sizeof(int), st);
   for (int outer = 0;; ++outer) {
-    if (op64.sym)
+    if (dfmode && outer > 0)
+      vlaunch("outer_residual_df", df_bytes(op64), k_outer_residual_df<T>, zr.grid, zr.block, st, w->df,
+              (const float*)h.lev[0].op.dinv, oz, b, xz, (T*)w->r, w->outer, (const int*)nullptr,
+              (const int*)w->dfbad, zr.zc, rs);
+    else if (op64.sym)
       vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, true>, zr.grid, zr.block, st, oz, b, xz, (T*)w->r,
-              w->outer, (const int*)nullptr, zr.zc, rs);
+              w->outer, (const int*)nullptr, zr.zc, rs, dfmode ? w->df : DFBuf{}, w->dfbad, 0);
     else
       vlaunch("outer_residual_f64", rbytes, k_outer_residual_z<T, false>, zr.grid, zr.block, st, oz, b, xz, (T*)w->r,
-              w->outer, (const int*)nullptr, zr.zc, rs);
+              w->outer, (const int*)nullptr, zr.zc, rs, DFBuf{}, w->dfbad, 0);
     cudaMemcpyAsync(w->outer_host, w->outer, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     const double rr = w->outer_host[0], bb = w->outer_host[1];
@@ -2949,7 +3149,8 @@ SolveResult solve(const Op<double>& op64, Hier<T>& h, const double* b, View<doub
       its = inner_bicgstab<T, false>(h, w, rin, left, rs, st);
     }
     total += its;
-    vlaunch("outer_update", (double)n * (sizeof(T) + 16.0), k_outer_update<T>, g, kThreads, st, bx, x, (const T*)w->e);
+    vlaunch("outer_update", (double)n * (sizeof(T) + 16.0), k_outer_update<T>, g, kThreads, st, bx, x, (const T*)w->e,
+            dfmode ? w->df.x : (float2*)nullptr, w->dfbad);
   }
   res.iters = total;
   return res;
@@ -2977,7 +3178,7 @@ int residual_snapshots(const Op<double>& op64, Hier<T>& h, const double* b, View
   const View<double> xz = zview_x(x, bx);
   const ZCfg zr = zcfg(oz.box);
   vlaunch("outer_residual_f64", 0.0, k_outer_residual_z<T, true>, zr.grid, zr.block, st, oz, b, xz, (T*)w->r,
-          w->outer, (const int*)nullptr, zr.zc, rs);
+          w->outer, (const int*)nullptr, zr.zc, rs, DFBuf{}, w->dfbad, 0);
   int maxit = 0;
   for (int i = 0; i < count; ++i) maxit = iters[i] > maxit ? iters[i] : maxit;
   const KVec<T> k = kvec<T>(w, false);

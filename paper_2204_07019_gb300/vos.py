@@ -24,7 +24,7 @@ __all__ = [
     "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
     "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16", "UNet", "vos_set_unet_preconditioner",
     "vos_unet_solve_stats", "vos_pressure_snapshots", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
-    "PRECOND_MOM_DIAG", "PRECOND_MOM_MG", "PRECOND_P_WARM", "PRECOND_U_EXTRAP", "FUSED_DIAG_PCG", "FUSED_MG_PCG",
+    "PRECOND_MOM_DIAG", "PRECOND_MOM_MG", "PRECOND_P_WARM", "PRECOND_U_EXTRAP", "FUSED_DIAG_PCG", "FUSED_MG_PCG", "FUSED_DF_RESIDUAL", "FUSED_ALL",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
@@ -39,6 +39,8 @@ PRECOND_P_WARM = 8
 PRECOND_U_EXTRAP = 16
 FUSED_DIAG_PCG = 1
 FUSED_MG_PCG = 2
+FUSED_DF_RESIDUAL = 4
+FUSED_ALL = 7
 
 EXPORTED_SYMBOLS = [
     "vos_create", "vos_step", "vos_fields", "vos_set_fields", "vos_device_fields_get",
@@ -673,15 +675,17 @@ def vos_set_vector_sweeps(on):
 
 
 def vos_set_fused_pcg(mask):
-    """Fused FP32 Krylov forms, a bit mask (default 3): FUSED_DIAG_PCG (1)
-    two-kernel diagonal PCG on constant-link operators (results identical to
-    the separate kernels), FUSED_MG_PCG (2) MG-PCG on the matrix-free pressure
-    level with the x/r update and r.z fused into the V-cycle's first and last
-    fine sweeps (iterates equal up to rounding).  Set before the handle's first
-    step (a captured step graph keeps its form)."""
+    """Fused forms of the mixed path's solves, a bit mask (default FUSED_ALL =
+    7): FUSED_DIAG_PCG (1) two-kernel diagonal PCG on constant-link operators
+    (results identical to the separate kernels), FUSED_MG_PCG (2) MG-PCG on
+    the matrix-free pressure level with the x/r update and r.z fused into the
+    V-cycle's first and last fine sweeps (iterates equal up to rounding),
+    FUSED_DF_RESIDUAL (4) the refinement residual after the first pass in
+    double-FP32 for symmetric solves to 1e-9 or looser.  Set before the
+    handle's first step (a captured step graph keeps its form)."""
     rc = load_library().vos_set_fused_pcg(int(mask))
     if rc != VOS_OK:
-        raise VosError(rc, f"vos_set_fused_pcg: mask {mask} outside 0..3")
+        raise VosError(rc, f"vos_set_fused_pcg: mask {mask} outside 0..7")
 
 
 def vos_set_coarse_cycle(on):

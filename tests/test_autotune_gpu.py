@@ -84,7 +84,7 @@ def test_vector_sweeps_identical(V, shape, precision):
     out = []
     # the MG-PCG form fused with the fine sweeps sums two dots in the sweeps'
     # order (not bit-identical to the separate kernels): off for this test
-    V.vos_set_fused_pcg(V.FUSED_DIAG_PCG)
+    V.vos_set_fused_pcg(V.FUSED_DIAG_PCG | V.FUSED_DF_RESIDUAL)
     try:
         for vec in (1, 0):
             V.vos_set_vector_sweeps(vec)
@@ -100,7 +100,7 @@ def test_vector_sweeps_identical(V, shape, precision):
                 V.vos_destroy(h)
     finally:
         V.vos_set_vector_sweeps(1)
-        V.vos_set_fused_pcg(V.FUSED_DIAG_PCG | V.FUSED_MG_PCG)
+        V.vos_set_fused_pcg(V.FUSED_ALL)
     assert out[0][1] == out[1][1]
     for n in out[0][0]:
         assert np.array_equal(out[0][0][n], out[1][0][n]), n

@@ -50,7 +50,7 @@ def _run(V, es, prm, dts, fused, graphs):
         finally:
             V.vos_destroy(h)
     finally:
-        V.vos_set_fused_pcg(V.FUSED_DIAG_PCG | V.FUSED_MG_PCG)
+        V.vos_set_fused_pcg(V.FUSED_ALL)
         V.vos_set_launch_mode(1)
 
 
@@ -89,4 +89,31 @@ def test_fused_diag_pcg(V, shape, graphs):
 
 def test_fused_pcg_mask_checked(V):
     with pytest.raises(V.VosError):
-        V.vos_set_fused_pcg(4)
+        V.vos_set_fused_pcg(8)
+
+
+@pytest.mark.parametrize("shape", [(16, 20, 32), (1, 48, 64)])
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_df_residual(V, shape, graphs):
+    """Refinement residual in double-FP32 after the first pass (symmetric
+    solves to 1e-8): the solves reach their tolerance and the fields agree
+    with the FP64-residual path and the FP64 oracle at that tolerance."""
+    es = _geometry(shape)
+    prm = I.make_params(es.shape, Pe=10.0, Da=1.0, L=6.0, method="ivos", Vm=0.5, precision=1,
+                        p_rtol=1e-8, u_rtol=1e-8, c_rtol=1e-10, max_iter=4000)
+    dts = [0.05, 0.05, 0.05]
+    f_df, it_df = _run(V, es, prm, dts, V.FUSED_ALL, graphs)
+    f_64, it_64 = _run(V, es, prm, dts, V.FUSED_DIAG_PCG | V.FUSED_MG_PCG, graphs)
+    for a, b in zip(it_df, it_64):
+        assert abs(a - b) <= max(4, 0.1 * b), (it_df, it_64)
+    st = O.init_state(es, prm)
+    for dt in dts:
+        st, _ = O.step(st, dt, prm)
+    ref = dict(u=st["u"][0], v=st["u"][1], p=st["p"], c=st["c"])
+    if shape[0] > 1:
+        ref["w"] = st["u"][2]
+    for n, r in ref.items():
+        rn = max(np.linalg.norm(r), 1e-300)
+        e_df = np.linalg.norm(f_df[n] - r) / rn
+        e_64 = np.linalg.norm(f_64[n] - r) / rn
+        assert e_df <= 2e-8 and np.linalg.norm(f_df[n] - f_64[n]) / rn <= 2e-8, (n, e_df, e_64)
