@@ -370,7 +370,7 @@ __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const do
     const double src = R[c] * P.Vm * (1.0 - P.rho_ratio);
     A.diag[c] = diag;
     A.dinv[c] = jacobi_weight(omega, diag);
-    if (eps32) eps32[c] = (float)e;  // the matrix-free FP32 form of this operator
+    if (eps32) eps32[c] = f32_rn(e);  // the matrix-free FP32 form of this operator
     A.xp[c] = off[0];
     A.yp[c] = off[1];
     if (A.zp) A.zp[c] = off[2];

@@ -104,6 +104,21 @@ struct Op {
 // FMA per link in the order x+, x-, y+, y-, z+, z-; a Jacobi update is one
 // FMA, x + w (b - A x); the prolongation x + wc x_c[parent] one FMA.  So
 // their results agree bit for bit whatever the compiler would contract.
+// FP64 -> FP32 rounded to nearest (ties to even) by integer operations on the
+// bit pattern: the conversion instruction executes on the FP64 pipe of this
+// part, which bounds the kernels that convert.  Results in the normal FP32
+// range (including the rounding up to infinity above the largest float) are
+// those of the IEEE conversion; other magnitudes, NaN and infinity take the
+// instruction.
+__device__ __forceinline__ float f32_rn(double v) {
+  const unsigned h = (unsigned)__double2hiint(v), l = (unsigned)__double2loint(v);
+  const unsigned e = (h >> 20) & 0x7ffu;
+  if (e < 897u || e > 1150u) return __double2float_rn(v);
+  unsigned bits = ((e - 896u) << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
+  const unsigned rem = l & 0x1fffffffu;  // the 29 bits dropped
+  if (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) ++bits;  // a carry moves into the exponent
+  return __uint_as_float((h & 0x80000000u) | bits);
+}
 __device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
 

@@ -1066,7 +1066,10 @@ __device__ __forceinline__ void resid64_body(const Op<double>& A, const double* 
   auto emit = [&](long long c, int i, int j, int k, double vc, double ax, double d) {
     const double bc = __ldg(b + c);
     const double r = bc - ax;
-    rT[c] = (T)r;
+    if constexpr (sizeof(T) == 4)
+      rT[c] = f32_rn(r);
+    else
+      rT[c] = (T)r;
     const double di = A.dinv[c];  // omega / diag: the constant omega cancels in the ratio
     const double r1 = r * di;
     acc[0] += r1 * r1;
@@ -2033,17 +2036,23 @@ __global__ void k_view_zero(Box bx, View<double> x) {
 template <typename T>
 __global__ void k_op_convert(Op<double> A, Op<T> B, long long n, int links) {
   VOS_COUNT_EXEC();
+  auto cv = [](double v) -> T {
+    if constexpr (sizeof(T) == 4)
+      return f32_rn(v);
+    else
+      return (T)v;
+  };
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    B.diag[c] = (T)A.diag[c];
-    B.dinv[c] = (T)A.dinv[c];
+    B.diag[c] = cv(A.diag[c]);
+    B.dinv[c] = cv(A.dinv[c]);
     if (!links) continue;
-    B.xp[c] = (T)A.xp[c];
-    B.yp[c] = (T)A.yp[c];
-    if (A.box.mz > 1) B.zp[c] = (T)A.zp[c];
+    B.xp[c] = cv(A.xp[c]);
+    B.yp[c] = cv(A.yp[c]);
+    if (A.box.mz > 1) B.zp[c] = cv(A.zp[c]);
     if (!A.sym) {
-      B.xm[c] = (T)A.xm[c];
-      B.ym[c] = (T)A.ym[c];
-      if (A.box.mz > 1) B.zm[c] = (T)A.zm[c];
+      B.xm[c] = cv(A.xm[c]);
+      B.ym[c] = cv(A.ym[c]);
+      if (A.box.mz > 1) B.zm[c] = cv(A.zm[c]);
     }
   }
 }
