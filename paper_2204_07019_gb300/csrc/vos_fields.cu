@@ -276,12 +276,15 @@ __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__
       kf = kic[cidx(P, i, j, k)];
       gp = -2.0 * pm * idx;
     }
-    double diag = idt + P.nu * ef * kf;
     double b = uold[fidx(P, a, f[0], f[1], f[2])] * idt - ef * gp;
     if (P.inertia) {
       const double* us3[3] = {u0, u1, u2};
       b -= inertia_term(P, eps, us3, a, f);
     }
+    // the viscous part of the diagonal counts its cnu terms in integers:
+    // one per unknown or fixed neighbour, two per antisymmetric ghost
+    // (no-slip wall, inlet tangential), none per zero-gradient ghost
+    int nvis = 0;
     double off[3] = {0.0, 0.0, 0.0};
     const int nb = (P.dim == 2) ? 2 : 3;
     const int um[3] = {ub.mx, ub.my, ub.mz};
@@ -290,27 +293,27 @@ __global__ void k_mom_assemble(Phys P, int a, Box ub, const double* __restrict__
         int u2[3] = {i, j, k};
         u2[d] += sg;
         if (u2[d] >= 0 && u2[d] < um[d]) {  // unknown neighbour
-          diag += cnu;
+          ++nvis;
           if (sg > 0) off[d] = -cnu;
           continue;
         }
         int f2 = f[d] + sg;  // neighbour face coordinate along d
         if (f2 >= 0 && f2 < fdim(P, a, d)) {  // fixed boundary face
-          diag += cnu;
-          double g = (a == 0 && d == 0 && f2 == 0) ? P.u_in : 0.0;
-          b += cnu * g;
+          ++nvis;
+          if (a == 0 && d == 0 && f2 == 0) b += cnu * P.u_in;
         } else {  // ghost outside the face array
-          double sgh;
+          bool anti;
           if (d == 0) {
-            sgh = (sg < 0) ? -1.0 : 1.0;  // inlet plane: tangential 0; outlet: zero gradient
+            anti = (sg < 0);  // inlet plane: tangential 0; outlet: zero gradient
           } else {
             unsigned bit = (d == 1) ? (sg < 0 ? 1u : 2u) : (sg < 0 ? 4u : 8u);
-            sgh = (P.wall_mask & bit) ? -1.0 : 1.0;
+            anti = (P.wall_mask & bit) != 0;
           }
-          diag += cnu * (1.0 - sgh);
+          if (anti) nvis += 2;
         }
       }
     }
+    const double diag = fma((double)nvis, cnu, fma(P.nu * ef, kf, idt));
     A.diag[c] = diag;
     A.dinv[c] = jacobi_weight(omega, diag);
     A.xp[c] = off[0];
@@ -351,22 +354,32 @@ __global__ void k_pres_assemble(Phys P, const double* __restrict__ eps, const do
     if (i >= bx.mx) continue;
     const long long c = cidx(P, i, j, k);
     const double e = eps[c];
-    double diag = 0.0, off[3] = {0.0, 0.0, 0.0}, div = 0.0;
+    // diagonal = sum of the links a_n = (e + e_n) idx2 / 2 (plus 2 e idx2 on
+    // the outlet column), formed as (n e + sum e_n) idx2 / 2 with the
+    // neighbours summed first; plus links stored one by one
+    double off[3] = {0.0, 0.0, 0.0}, esum = 0.0, dsum = 0.0;
+    int nl = 0;
     for (int d = 0; d < nb; ++d) {
       int lo[3] = {i, j, k}, hi[3] = {i, j, k};
       lo[d] -= 1;
       hi[d] += 1;
       if (cell_in(P, hi[0], hi[1], hi[2])) {
-        double a = 0.5 * (e + eps[cidx(P, hi[0], hi[1], hi[2])]) * idx2;
-        diag += a;
-        off[d] = -a;
+        const double en = eps[cidx(P, hi[0], hi[1], hi[2])];
+        off[d] = -0.5 * (e + en) * idx2;
+        esum += en;
+        ++nl;
       }
-      if (cell_in(P, lo[0], lo[1], lo[2])) diag += 0.5 * (e + eps[cidx(P, lo[0], lo[1], lo[2])]) * idx2;
+      if (cell_in(P, lo[0], lo[1], lo[2])) {
+        esum += eps[cidx(P, lo[0], lo[1], lo[2])];
+        ++nl;
+      }
       int fp[3] = {i, j, k};
       fp[d] += 1;
-      div += (us[d][fidx(P, d, fp[0], fp[1], fp[2])] - us[d][fidx(P, d, i, j, k)]) * idx;
+      dsum += us[d][fidx(P, d, fp[0], fp[1], fp[2])] - us[d][fidx(P, d, i, j, k)];
     }
+    double diag = 0.5 * idx2 * fma((double)nl, e, esum);
     if (i == P.nx - 1) diag += 2.0 * e * idx2;
+    const double div = dsum * idx;
     const double src = R[c] * P.Vm * (1.0 - P.rho_ratio);
     A.diag[c] = diag;
     A.dinv[c] = jacobi_weight(omega, diag);
@@ -780,8 +793,11 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
       if (IVOS) {
         // reactive flux F = s (c_U^{n+1} + corr): upwind value implicit,
         // the deferred van Leer correction on the right-hand side
+        // faces away from the solid surface have s = +-0 (zero eps gradient):
+        // their terms vanish and are skipped on the bit pattern
         const double zc = P.zeta * e;
-        if (hasp) {  // this cell is the minus cell of its plus face
+        auto nonzero = [](double v) { return (__double_as_longlong(v) << 1) != 0; };
+        if (hasp && nonzero(fds[d].s[fidx(P, d, fp[0], fp[1], fp[2])])) {  // the minus cell of its plus face
           const long long fx = fidx(P, d, fp[0], fp[1], fp[2]);
           const double sf = fds[d].s[fx];
           if (sf > 0.0)
@@ -790,7 +806,7 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
             offp[d] += zc * sf;  // U = plus
           b -= zc * sf * fds[d].corr[fx];
         }
-        if (hasm) {  // this cell is the plus cell of its minus face (outward flux -F)
+        if (hasm && nonzero(fds[d].s[fidx(P, d, i, j, k)])) {  // the plus cell of its minus face (outward -F)
           const long long fx = fidx(P, d, i, j, k);
           const double sf = fds[d].s[fx];
           if (sf > 0.0)
@@ -861,14 +877,17 @@ __global__ void k_rates(Phys P, const double* __restrict__ eps, const double* __
     const double e = eps[c];
     double r, rf;
     if (IVOS) {
+      // faces with s = +-0 (no eps gradient) carry no reactive flux: skipped
+      // on the bit pattern
+      auto nonzero = [](double v) { return (__double_as_longlong(v) << 1) != 0; };
       double sumF = 0.0, sumEF = 0.0;
       for (int d = 0; d < nb; ++d) {
         int lo[3] = {i, j, k}, hi[3] = {i, j, k};
         lo[d] -= 1;
         hi[d] += 1;
-        if (cell_in(P, hi[0], hi[1], hi[2])) {
-          int fp[3] = {i, j, k};
-          fp[d] += 1;
+        int fp[3] = {i, j, k};
+        fp[d] += 1;
+        if (cell_in(P, hi[0], hi[1], hi[2]) && nonzero(fds[d].s[fidx(P, d, fp[0], fp[1], fp[2])])) {
           const long long fx = fidx(P, d, fp[0], fp[1], fp[2]);
           const double sf = fds[d].s[fx];
           const double cU = sf > 0.0 ? cn[c] : cn[cidx(P, hi[0], hi[1], hi[2])];
@@ -876,7 +895,7 @@ __global__ void k_rates(Phys P, const double* __restrict__ eps, const double* __
           sumF += F;
           sumEF += fds[d].evl[fx] * F;
         }
-        if (cell_in(P, lo[0], lo[1], lo[2])) {
+        if (cell_in(P, lo[0], lo[1], lo[2]) && nonzero(fds[d].s[fidx(P, d, i, j, k)])) {
           const long long fx = fidx(P, d, i, j, k);
           const double sf = fds[d].s[fx];
           const double cU = sf > 0.0 ? cn[cidx(P, lo[0], lo[1], lo[2])] : cn[c];
