@@ -583,6 +583,15 @@ __global__ void k_face_data(Phys P, int a, Box fb, const double* __restrict__ ep
     // the two cells' centred components; n_a = -g_n / (|g| + 1e-8/dx)
     // = -dn / (|dx g| + 1e-8)
     const double dn = eps[cp] - eps[cm];
+    if ((__double_as_longlong(dn) << 1) == 0) {
+      // no normal eps difference: n_a = -0, so s = -0 and the face carries no
+      // reactive flux; its correction and eps_vl are never read (the transport
+      // assembly and the rates skip s = +-0 faces)
+      fd.s[fcx] = -0.0;
+      fd.corr[fcx] = 0.0;
+      fd.evl[fcx] = 0.0;
+      continue;
+    }
     double g2 = dn * dn;
     for (int b = 0; b < nb; ++b) {
       if (b == a) continue;
