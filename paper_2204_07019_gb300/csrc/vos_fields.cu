@@ -1006,6 +1006,19 @@ __global__ void k_step_diag(Phys P, const double* __restrict__ eps, const double
   const double idx = 1.0 / P.dx;
   double mx[2] = {0.0, 0.0};
   double sm[4] = {0.0, 0.0, 0.0, 0.0};
+  // the thread's largest abs(u_f) / eps_f is kept as the pair (bu, be) and
+  // a face replaces it when abs(u_f) be > bu eps_f, so the quotient is taken
+  // once per thread; a NaN velocity makes the maximum infinite
+  double bu = 0.0, be = 1.0;
+  bool nan_u = false;
+  auto consider = [&](double uf, double ef) {
+    const double au = fabs(uf);
+    if (au != au) nan_u = true;
+    else if (au * be > bu * ef) {
+      bu = au;
+      be = ef;
+    }
+  };
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
     seg_decode(s, bx, q, i, j, k);
@@ -1016,11 +1029,11 @@ __global__ void k_step_diag(Phys P, const double* __restrict__ eps, const double
       int lo[3] = {i, j, k};
       lo[d] -= 1;
       const double ef = cell_in(P, lo[0], lo[1], lo[2]) ? 0.5 * (e + eps[cidx(P, lo[0], lo[1], lo[2])]) : e;
-      mx[0] = fmax(mx[0], nan_inf(fdiv_nr(fabs(us[d][fidx(P, d, i, j, k)]), ef)));
+      consider(us[d][fidx(P, d, i, j, k)], ef);
       int f[3] = {i, j, k};
       if (f[d] == ncell(P, d) - 1) {
         f[d] += 1;
-        mx[0] = fmax(mx[0], nan_inf(fdiv_nr(fabs(us[d][fidx(P, d, f[0], f[1], f[2])]), e)));
+        consider(us[d][fidx(P, d, f[0], f[1], f[2])], e);
       }
     }
     mx[1] = fmax(mx[1], nan_inf(fabs(P.Vm * R[c0])));
@@ -1035,6 +1048,7 @@ __global__ void k_step_diag(Phys P, const double* __restrict__ eps, const double
       sm[3] += cf0[fx];
     }
   }
+  mx[0] = nan_u ? INFINITY : nan_inf(fdiv_nr(bu, be));
   if (grid_sum_max<4, 2>(sm, mx, rs.partials, rs.counter) && threadIdx.x == 0) {
     const double A = (P.dim == 2) ? P.dx : P.dx * P.dx;
     stats[ST_UMAX] = mx[0];
