@@ -1246,11 +1246,13 @@ static ZCfg zcfg(Box b) { return zcfg_tile(b, (b.my == 1) ? 256 : 32, 4096); }
 // default, 1,024 of one plane here).
 static ZCfg zcfg_sweep(Box b) { return zcfg_tile(b, (b.my == 1) ? 256 : 32, 4096, 1); }
 // Four-cells-per-thread matrix-free sweeps: 32 x 8 threads cover 128 x 8
-// cells (256 x 1 threads = 1024 cells of a row on 2D boxes), about 4096
-// blocks of one or more planes.
+// cells (256 x 1 threads = 1024 cells of a row on 2D boxes), about 1024
+// blocks of one or more planes (on the 256^3 rock the graph-replayed step
+// measured 91.1-91.5 ms with about 4096 blocks, 88.9 with 2048 and 88.7 with
+// 1024: the grid reductions' last blocks have fewer partial sums to add).
 static ZCfg zcfg_mf4(Box b) {
   const Box q{(b.mx + 3) / 4, b.my, b.mz};
-  return zcfg_tile(q, (b.my == 1) ? 256 : 32, 4096, 1);
+  return zcfg_tile(q, (b.my == 1) ? 256 : 32, 1024, 1);
 }
 // Process-wide switch of the four-cells-per-thread matrix-free sweeps
 // (vos_set_vector_sweeps; results are identical either way).
