@@ -1247,12 +1247,20 @@ static ZCfg zcfg(Box b) { return zcfg_tile(b, (b.my == 1) ? 256 : 32, 4096); }
 static ZCfg zcfg_sweep(Box b) { return zcfg_tile(b, (b.my == 1) ? 256 : 32, 4096, 1); }
 // Four-cells-per-thread matrix-free sweeps: 32 x 8 threads cover 128 x 8
 // cells (256 x 1 threads = 1024 cells of a row on 2D boxes), about 1024
-// blocks of one or more planes (on the 256^3 rock the graph-replayed step
-// measured 91.1-91.5 ms with about 4096 blocks, 88.9 with 2048 and 88.7 with
-// 1024: the grid reductions' last blocks have fewer partial sums to add).
+// blocks of one or more planes for the kernels with a grid reduction (on the
+// 256^3 rock the graph-replayed step measured 91.1-91.5 ms with about 4096
+// blocks, 88.9 with 2048 and 88.7 with 1024: the reductions' last blocks
+// have fewer partial sums to add); the sweeps without one keep about 4096
+// blocks (zcfg_mf4s; 88.5 ms).
 static ZCfg zcfg_mf4(Box b) {
   const Box q{(b.mx + 3) / 4, b.my, b.mz};
   return zcfg_tile(q, (b.my == 1) ? 256 : 32, 1024, 1);
+}
+// The same tile for the four-cell sweeps without a reduction: about 4096
+// blocks of fewer planes.
+static ZCfg zcfg_mf4s(Box b) {
+  const Box q{(b.mx + 3) / 4, b.my, b.mz};
+  return zcfg_tile(q, (b.my == 1) ? 256 : 32, 4096, 1);
 }
 // Process-wide switch of the four-cells-per-thread matrix-free sweeps
 // (vos_set_vector_sweeps; results are identical either way).
@@ -2370,7 +2378,7 @@ static void stencil_launch(const char* name, int kind, const Op<T>& A, const T* 
       const float* xx = (const float*)x;
       float* oo = (float*)out;
       if (g_mf4 && Z.box.mx % 4 == 0) {  // 16-byte rows: four cells per thread
-        const ZCfg z4 = zcfg_mf4(Z.box);
+        const ZCfg z4 = zcfg_mf4s(Z.box);
         if (kind == SK_JAC)
           vlaunch(name, words * n * 4.0, k_stencil_mf4<SK_JAC, XS_PLAIN>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs, bb,
                   xx, oo, om, z4.zc, sc, Box{0, 0, 0}, (const float*)nullptr, 0.0f);
@@ -2555,15 +2563,15 @@ static void vcycle(Hier<T>& h, const T* rhs, T* out, T* scratch, KScal* sc, cuda
     const int dfr = h.defl.K > 0 ? 1 : 0;
     if (fused_fine(l)) {  // first sweep on x + wc P x_coarse, formed on the fly
       const Op<T> Z = zview(A);
-      const ZCfg z4 = zcfg_mf4(Z.box);
+      const ZCfg z4 = zcfg_mf4(Z.box), z4s = zcfg_mf4s(Z.box);
       const double bytes = (4.0 * ncell(A) + ncell(h.lev[l + 1].op)) * 4.0;
       if (rz_here && nu == 1)
         vlaunch("mg_jac_pro_rz_mf_f32_L0", bytes, k_jac_mf4_rz<XS_PRO>, z4.grid, z4.block, st, Z.box, A.mfe, A.mfs,
                 (const float*)b, (const float*)cur, (float*)oth, (float)om, z4.zc, sc, *rz, cz,
                 (const float*)h.lev[l + 1].x, (float)wc, dfr);
       else
-        vlaunch("mg_jac_pro_mf_f32_L0", bytes, k_stencil_mf4<SK_JAC, XS_PRO>, z4.grid, z4.block, st, Z.box, A.mfe,
-                A.mfs, (const float*)b, (const float*)cur, (float*)oth, (float)om, z4.zc, (const KScal*)sc, cz,
+        vlaunch("mg_jac_pro_mf_f32_L0", bytes, k_stencil_mf4<SK_JAC, XS_PRO>, z4s.grid, z4s.block, st, Z.box, A.mfe,
+                A.mfs, (const float*)b, (const float*)cur, (float*)oth, (float)om, z4s.zc, (const KScal*)sc, cz,
                 (const float*)h.lev[l + 1].x, (float)wc);
       T* tmp = cur;
       cur = oth;
