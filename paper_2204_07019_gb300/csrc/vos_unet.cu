@@ -513,59 +513,97 @@ __global__ void k_relu_bwd(long long n, const float* __restrict__ g, const __nv_
   }
 }
 
-// Weight gradient on the tensor cores.  For one chunk of voxels v and the
-// taps t, partial[chunk][t][o][i] = sum_v x[v + t][i] g[v][o] is a GEMM
+// Weight gradient on the tensor cores.  For the rows (j, k) of one chunk and
+// the taps t, partial[chunk][t][o][i] = sum_v x[v + t][i] g[v][o] is a GEMM
 // D[m][n] = sum_k A[m][k] B[n][k] with rows m = (tap, input channel) stacked
 // 128 per MMA tile (27 * cin rows in ceil(27 cin / 128) tiles), n = output
 // channel and k = voxel: K = 16 voxels per MMA, BF16 operands (x and the
 // BF16 copy of g that the data-gradient convolution also reads), FP32
 // accumulators in tensor memory, one N = cout column block per tile.  Both
 // operands are MN-major: a core matrix is 8 voxels (rows along K) x 8
-// channels (16 bytes along M or N), so each row is one channels-last vector
-// copied as it is -- x at the tap's neighbour (zero outside the box) or g
-// at the voxel -- with no transpose; core matrices adjacent along M (N) are
-// 256 B apart, the two K halves 128 B.  Each K step the 128 threads fill one
-// of two buffers; one thread issues the MMAs and commits them to the
-// buffer's barrier, which is waited on before the buffer is refilled two
-// steps later.  CTA (chunk, tile group): blockIdx.y selects the tiles this
-// CTA accumulates (tensor memory holds at most 256 columns per CTA).
-constexpr int kDwK = 16;            // voxels per MMA (K)
-constexpr int kDwTileBytes = 4096;  // one 128-row A tile of one K step
+// channels (16 bytes along M or N), i.e. 8 channels-last vectors as they lie
+// in memory.  So each operand group (tap, 8 input channels) of a stage is one
+// TMA box of 8 channels x w voxels along x of the tap's neighbour row,
+// with zeros outside the grid from the TMA's own fill: no thread copies
+// anything.  A stage is w (16..64) voxels of one row; its groups sit w x 16 B
+// apart (the descriptors' M / N stride), the two K halves of an MMA 128 B
+// apart, consecutive MMAs of the stage 256 B apart.  One thread drives the
+// pipeline (two stage buffers with full / empty mbarriers, as the forward
+// convolution); blockIdx.y selects the tiles a CTA accumulates (at most four
+// tiles and 256 tensor-memory columns), blockIdx.x its rows.
+constexpr int kDwTiles = 4;  // A tiles per CTA at most
 struct DwArgs {
-  const __nv_bfloat16* x;  // [V][cin] layer input
-  const __nv_bfloat16* g;  // [V][cout] gradient at the layer's pre-activation output
-  float* partial;          // [nchunk][27][cout][cin]
+  float* partial;  // [nchunk][27][cout][cin]
   int nx, ny, nz, cin, cout;
-  long long chunk;         // voxels per CTA (multiple of 16)
-  int tiles, tpc;          // A tiles in all; tiles per CTA
+  int w, segs;     // voxels per stage (box x extent); stages per row
+  int rows;        // rows (j, k) per CTA
+  int tiles, tpc;  // A tiles in all; tiles per CTA
 };
 __host__ __device__ inline int dw_tiles(int cin) { return (27 * cin + 127) / 128; }
 __host__ __device__ inline int dw_tpc(int cin, int cout) {
-  const int t = dw_tiles(cin), cap = 256 / cout;
+  const int t = dw_tiles(cin), cap = 256 / cout < kDwTiles ? 256 / cout : kDwTiles;
   return t < cap ? t : cap;
 }
-inline size_t dw_smem_bytes(int cin, int cout) {
-  return 2 * ((size_t)dw_tpc(cin, cout) * kDwTileBytes + (size_t)cout * 32) + 64;
+__host__ __device__ inline int dw_width(int nx) { return nx >= 64 ? 64 : (nx >= 32 ? 32 : 16); }
+inline size_t dw_stage_bytes(int cin, int cout, int w) {
+  return ((size_t)dw_tpc(cin, cout) * 16 + (size_t)(cout / 8)) * (size_t)w * 16;
+}
+inline size_t dw_smem_bytes(int cin, int cout, int w) { return 2 * dw_stage_bytes(cin, cout, w) + 128; }
+
+// TMA descriptor of a channels-last BF16 tensor [nz][ny][nx][C] with boxes of
+// 8 channels x w voxels of one row.
+static cudaError_t make_row_map(CUtensorMap* m, const __nv_bfloat16* p, int C, int nx, int ny, int nz, int w) {
+  if (!g_encode_tiled) {
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&g_encode_tiled, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !g_encode_tiled) {
+      g_encode_tiled = nullptr;
+      return e != cudaSuccess ? e : cudaErrorNotSupported;
+    }
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * nx, (cuuint64_t)C * 2 * nx * ny};
+  const cuuint32_t box[4] = {8, (cuuint32_t)w, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = g_encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)p, dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-__global__ void __launch_bounds__(kTM) k_dw_tc(DwArgs a) {
+__global__ void __launch_bounds__(kTM) k_dw_tc(const __grid_constant__ CUtensorMap tmx,
+                                              const __grid_constant__ CUtensorMap tmg, DwArgs a) {
   VOS_COUNT_EXEC();
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int T0 = blockIdx.y * a.tpc;
   const int nt = min(a.tpc, a.tiles - T0);
-  const int bufA = a.tpc * kDwTileBytes, bufB = a.cout * 32;
-  unsigned char* sA = smem;                // two A buffers
-  unsigned char* sB = smem + 2 * bufA;     // two B buffers
-  uint64_t* empty = (uint64_t*)(sB + 2 * bufB);
+  const int ngA = nt * 16, ngB = a.cout >> 3;
+  const int gbytes = a.w * 16;                 // one group's box
+  const int sbytes = (a.tpc * 16 + ngB) * gbytes;  // one stage buffer
+  unsigned char* buf = smem;
+  uint64_t* full = (uint64_t*)(smem + 2 * sbytes);
+  uint64_t* empty = full + 2;
   uint32_t* slot = (uint32_t*)(empty + 2);
   int* s_ok = (int*)(slot + 1);
   uint32_t ncols = 32;
   while (ncols < (uint32_t)(nt * a.cout)) ncols <<= 1;
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(slot), ncols);
+  // rows of the last tile past 27 taps: zero in both buffers, never loaded
+  int nvalid = 0;
+  for (int g = 0; g < ngA; ++g)
+    if ((T0 * 16 + g) * 8 / a.cin < 27) ++nvalid;
+  for (int b = 0; b < 2; ++b)
+    for (int g = nvalid; g < ngA; ++g)
+      for (int e = tid; e < gbytes / 16; e += kTM)
+        reinterpret_cast<uint4*>(buf + b * sbytes + g * gbytes)[e] = make_uint4(0u, 0u, 0u, 0u);
+  tc::fence_proxy_async_smem();
   if (tid == 0) {
-    tc::mbar_init(tc::smem_addr(&empty[0]), 1);
-    tc::mbar_init(tc::smem_addr(&empty[1]), 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(tc::smem_addr(&full[i]), 1);
+      tc::mbar_init(tc::smem_addr(&empty[i]), 1);
+    }
     tc::fence_mbar_init();
     *s_ok = 1;
   }
@@ -573,110 +611,76 @@ __global__ void __launch_bounds__(kTM) k_dw_tc(DwArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
-  const long long V = (long long)a.nx * a.ny * a.nz;
-  const long long v0 = (long long)blockIdx.x * a.chunk;
-  const long long v1 = min(V, v0 + a.chunk);
-  const int nsteps = (int)((v1 - v0 + kDwK - 1) / kDwK);
-  const int ngA = nt * 16;         // 8-row groups of this CTA's A rows
-  const int ngB = a.cout >> 3;     // 8-row groups of B
-  const uint32_t idesc = tc::idesc_bf16_f32_mn(128, a.cout);
-  // per A group: element offset of its tap's neighbour plus first channel,
-  // and the tap's offsets + 1 (bits 0-1 x, 2-3 y, 4-5 z; 63 = padding row)
-  __shared__ long long s_off[256];
-  __shared__ unsigned char s_code[256];
-  for (int gq = tid; gq < ngA; gq += kTM) {
-    const int m = (T0 * 16 + gq) * 8;
-    const int tap = m / a.cin, c0 = m - tap * a.cin;
-    if (tap < 27) {
-      const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
-      s_off[gq] = ((long long)(dx - 1) + (long long)a.nx * ((dy - 1) + (long long)a.ny * (dz - 1))) * a.cin + c0;
-      s_code[gq] = (unsigned char)(dx | (dy << 2) | (dz << 4));
-    } else {
-      s_off[gq] = 0;
-      s_code[gq] = 63;  // bits 3 of every mask are zero: never loaded
-    }
-  }
-  __syncthreads();
-  uint32_t eph0 = 0u, eph1 = 0u;  // phases of the two buffers' barriers
-  for (int s = 0; s < nsteps; ++s) {
-    const int b = s & 1;
-    if (tid == 0 && s >= 2) {  // the MMAs of step s - 2 have read buffer b
-      if (!tc::mbar_wait(tc::smem_addr(&empty[b]), b ? eph1 : eph0, kWaitNs)) *s_ok = 0;
-      if (b) eph1 ^= 1u; else eph0 ^= 1u;
-    }
-    __syncthreads();
-    if (!*s_ok) break;
-    unsigned char* A = sA + b * bufA;
-    unsigned char* B = sB + b * bufB;
-    // Items (8-channel group, voxel kk): one 16-byte channel vector, the
-    // row kk % 8 of an MN-major core matrix (A groups: x at the tap's
-    // neighbour of voxel kk, zero outside the box; B groups: g at voxel
-    // kk).  A thread keeps one voxel (kk = tid % 16) for the whole step.
-    const int kk = tid & (kDwK - 1);
-    const long long v = v0 + (long long)s * kDwK + kk;
-    const bool vin = v < v1;
-    unsigned mx = 0u, my = 0u, mz = 0u;  // bit d: the neighbour at offset d - 1 is in the box
-    if (vin) {
-      const unsigned vu = (unsigned)v, nxu = (unsigned)a.nx, nyu = (unsigned)a.ny;  // V < 2^31
-      const int vi = (int)(vu % nxu), vj = (int)((vu / nxu) % nyu), vk = (int)(vu / (nxu * nyu));
-      mx = (vi > 0 ? 1u : 0u) | 2u | (vi + 1 < a.nx ? 4u : 0u);
-      my = (vj > 0 ? 1u : 0u) | 2u | (vj + 1 < a.ny ? 4u : 0u);
-      mz = (vk > 0 ? 1u : 0u) | 2u | (vk + 1 < a.nz ? 4u : 0u);
-    }
-    const __nv_bfloat16* xv = a.x + v * a.cin;
-    const int row = (kk >> 3) * 128 + (kk & 7) * 16;
-    // batches of 8 items: the 8 loads are in flight together
-    constexpr int kStride = kTM / kDwK;  // 8 groups per pass of the block
-    for (int g0 = tid >> 4; g0 < ngA + ngB; g0 += 8 * kStride) {
-      uint4 val[8];
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int grp = g0 + r * kStride;
-        val[r] = make_uint4(0u, 0u, 0u, 0u);
-        if (grp < ngA) {
-          const unsigned code = s_code[grp];
-          if (((mx >> (code & 3u)) & (my >> ((code >> 2) & 3u)) & (mz >> (code >> 4))) & 1u)
-            val[r] = __ldg(reinterpret_cast<const uint4*>(xv + s_off[grp]));
-        } else if (grp < ngA + ngB && vin) {
-          val[r] = __ldg(reinterpret_cast<const uint4*>(a.g + v * a.cout + (grp - ngA) * 8));
+  const int nrow = a.ny * a.nz;
+  const int r0 = blockIdx.x * a.rows, r1 = min(r0 + a.rows, nrow);
+  const int nst = (r1 - r0) * a.segs;  // stages of this CTA
+  if (warp == 0) {  // the pipeline: lane 0 waits, issues the MMAs and commits; all lanes issue the TMAs
+    const int lane = tid & 31;
+    bool ok = true;
+    uint32_t fph[2] = {0u, 0u}, eph[2] = {0u, 0u};
+    const uint32_t idesc = tc::idesc_bf16_f32_mn(128, a.cout);
+    auto issue = [&](int q) {
+      const int s = q & 1;
+      const int row = r0 + q / a.segs, i0 = (q % a.segs) * a.w;
+      const int j = row % a.ny, k = row / a.ny;
+      const uint32_t fb = tc::smem_addr(&full[s]);
+      if (lane == 0) tc::mbar_arrive_expect_tx(fb, (uint32_t)((nvalid + ngB) * gbytes));
+      __syncwarp();
+      const uint32_t base = tc::smem_addr(buf + s * sbytes);
+      for (int g = lane; g < nvalid; g += 32) {
+        const int m = (T0 * 16 + g) * 8, tap = m / a.cin, c0 = m - tap * a.cin;
+        tc::tma_load_4d(base + (uint32_t)(g * gbytes), &tmx, c0, i0 + tap % 3 - 1, j + (tap / 3) % 3 - 1,
+                        k + tap / 9 - 1, fb);
+      }
+      const uint32_t bbase = base + (uint32_t)(a.tpc * 16 * gbytes);
+      for (int og = lane; og < ngB; og += 32)
+        tc::tma_load_4d(bbase + (uint32_t)(og * gbytes), &tmg, og * 8, i0, j, k, fb);
+    };
+    if (nst > 0) issue(0);
+    if (nst > 1) issue(1);
+    for (int q = 0; q < nst && ok; ++q) {
+      const int s = q & 1;
+      if (lane == 0) {
+        ok = tc::mbar_wait(tc::smem_addr(&full[s]), fph[s], kWaitNs);
+        if (ok) {
+          tc::fence_after_sync();
+          const uint32_t base = tc::smem_addr(buf + s * sbytes);
+          const uint32_t bbase = base + (uint32_t)(a.tpc * 16 * gbytes);
+          for (int kk = 0; kk < a.w / 16; ++kk) {  // MMAs of 16 voxels
+            const uint64_t bd = tc::desc_mnmajor(bbase + (uint32_t)(kk * 256), (uint32_t)gbytes, 128);
+            for (int t = 0; t < nt; ++t) {
+              const uint64_t ad =
+                  tc::desc_mnmajor(base + (uint32_t)(t * 16 * gbytes + kk * 256), (uint32_t)gbytes, 128);
+              tc::mma_bf16(tmem + (uint32_t)(t * a.cout), ad, bd, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc::commit(tc::smem_addr(&empty[s]));
+          if (q + 2 < nst) {  // the buffer is refilled once the MMAs just issued have read it
+            ok = tc::mbar_wait(tc::smem_addr(&empty[s]), eph[s], kWaitNs);
+            eph[s] ^= 1u;
+          }
         }
       }
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int grp = g0 + r * kStride;
-        if (grp < ngA)
-          *reinterpret_cast<uint4*>(A + (grp >> 4) * kDwTileBytes + (grp & 15) * 256 + row) = val[r];
-        else if (grp < ngA + ngB)
-          *reinterpret_cast<uint4*>(B + (grp - ngA) * 256 + row) = val[r];
+      fph[s] ^= 1u;
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (ok && q + 2 < nst) issue(q + 2);
+    }
+    if (lane == 0) {
+      // the last commit of each buffer: every MMA done, no arrival pending
+      for (int q = (nst >= 2 ? nst - 2 : 0); q < nst && ok; ++q) {
+        const int s = q & 1;
+        ok = tc::mbar_wait(tc::smem_addr(&empty[s]), eph[s], kWaitNs);
+        eph[s] ^= 1u;
       }
+      *s_ok = ok ? 1 : 0;
+      if (!ok) atomicExch(&g_tc_timeout, 1);
     }
-    tc::fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const uint64_t bd = tc::desc_mnmajor(tc::smem_addr(B), 256, 128);
-      for (int t = 0; t < nt; ++t) {
-        const uint64_t ad = tc::desc_mnmajor(tc::smem_addr(A + t * kDwTileBytes), 256, 128);
-        tc::mma_bf16(tmem + (uint32_t)(t * a.cout), ad, bd, idesc, s > 0 ? 1u : 0u);
-      }
-      tc::commit(tc::smem_addr(&empty[b]));
-    }
-  }
-  if (tid == 0 && *s_ok) {  // the last commit of each buffer: every MMA done
-    for (int s = (nsteps >= 2 ? nsteps - 2 : 0); s < nsteps && *s_ok; ++s) {
-      const int b = s & 1;
-      if (!tc::mbar_wait(tc::smem_addr(&empty[b]), b ? eph1 : eph0, kWaitNs)) *s_ok = 0;
-      if (b) eph1 ^= 1u; else eph0 ^= 1u;
-    }
-    if (!*s_ok) atomicExch(&g_tc_timeout, 1);
-  } else if (tid == 0) {
-    atomicExch(&g_tc_timeout, 1);
   }
   __syncthreads();
-  if (*s_ok && nsteps > 0) {
+  float* part = a.partial + (long long)blockIdx.x * 27 * a.cout * a.cin;
+  if (*s_ok && nst > 0) {
     tc::fence_after_sync();
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    float* part = a.partial + (long long)blockIdx.x * 27 * a.cout * a.cin;
     for (int t = 0; t < nt; ++t) {
       const int m = (T0 + t) * 128 + tid;  // TMEM lane = row of tile t
       const int tap = m / a.cin, ci = m - tap * a.cin;
@@ -689,6 +693,12 @@ __global__ void __launch_bounds__(kTM) k_dw_tc(DwArgs a) {
             part[((long long)tap * a.cout + n0 + q) * a.cin + ci] = __uint_as_float(r[q]);
         }
       }
+    }
+  } else if (nst == 0) {  // a CTA without rows contributes zeros
+    for (int t = 0; t < nt; ++t) {
+      const int m = (T0 + t) * 128 + tid, tap = m / a.cin, ci = m - tap * a.cin;
+      if (tap < 27)
+        for (int n = 0; n < a.cout; ++n) part[((long long)tap * a.cout + n) * a.cin + ci] = 0.0f;
     }
   }
   tc::fence_before_sync();
@@ -1000,14 +1010,18 @@ static cudaError_t layer_backward(vos_unet* u, int li, const __nv_bfloat16* xin,
   static bool dw_attr = false;
   if (!dw_attr) {
     VOS_CUDA_TRY(cudaFuncSetAttribute(k_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(2 * (16 * kDwTileBytes + 96 * 32) + 64)));
+                                      (int)dw_smem_bytes(96, 16, 64)));
     dw_attr = true;
   }
-  const DwArgs da{xin, u->gpre16, u->part_dw, u->lx[l.lev], u->ly[l.lev], u->lz[l.lev], l.cing, l.cout,
-                  u->chunk[l.lev], dw_tiles(l.cing), dw_tpc(l.cing, l.cout)};
+  const int lx = u->lx[l.lev], ly = u->ly[l.lev], lz = u->lz[l.lev], w = dw_width(lx);
+  alignas(64) CUtensorMap tmx, tmg;
+  VOS_CUDA_TRY(make_row_map(&tmx, xin, l.cing, lx, ly, lz, w));
+  VOS_CUDA_TRY(make_row_map(&tmg, u->gpre16, l.cout, lx, ly, lz, w));
+  const DwArgs da{u->part_dw, lx, ly, lz, l.cing, l.cout, w, (lx + w - 1) / w, (int)u->chunk[l.lev],
+                  dw_tiles(l.cing), dw_tpc(l.cing, l.cout)};
   const dim3 gdw((unsigned)nch, (unsigned)((da.tiles + da.tpc - 1) / da.tpc));
   vlaunch_smem("unet_dw_tc", 2.0 * 27.0 * l.cing * l.cout * (double)V, k_dw_tc, gdw, dim3(kTM),
-               dw_smem_bytes(l.cing, l.cout), st, da);
+               dw_smem_bytes(l.cing, l.cout, w), st, tmx, tmg, da);
   vlaunch("unet_dw_reduce", 0.0, k_dw_reduce, ugrid(27LL * l.cout * l.cing), kThreads, st, nch, l.cing, l.cout,
           (const float*)u->part_dw, l.gW);
   vlaunch("unet_db", 0.0, k_db, u->ndb, kThreads, st, V, l.cout, (const float*)u->gpre, u->part_db);
@@ -1178,12 +1192,13 @@ static vos_unet* create_net(int px, int py, int pz, bool train, cudaStream_t st)
     u->gpre = (float*)A(pmax * 4);
     u->gpre16 = (__nv_bfloat16*)A(pmax * 2);
     long long pdw = 0;
-    for (int l = 0; l < 3; ++l) {  // weight-gradient chunks: about two CTAs per SM, 256 voxels at least
-      const long long target = 2LL * g_num_sms;
-      long long ch = ((u->V[l] + target - 1) / target + 15) / 16 * 16;
-      if (ch < 256) ch = 256;
+    for (int l = 0; l < 3; ++l) {  // weight-gradient chunks: rows (j, k) per CTA, about two CTAs per SM
+      const long long rows = (long long)u->ly[l] * u->lz[l], target = 2LL * g_num_sms;
+      long long ch = (rows + target - 1) / target;
+      const long long minrows = (256 + u->lx[l] - 1) / u->lx[l];  // 256 voxels per CTA at least
+      if (ch < minrows) ch = minrows;
       u->chunk[l] = ch;
-      u->nchunk[l] = (int)((u->V[l] + ch - 1) / ch);
+      u->nchunk[l] = (int)((rows + ch - 1) / ch);
     }
     for (auto& l : u->L) pdw = std::max(pdw, (long long)u->nchunk[l.lev] * 27 * l.cout * l.cing);
     u->part_dw = (float*)A(pdw * 4);
