@@ -1009,8 +1009,11 @@ static cudaError_t layer_backward(vos_unet* u, int li, const __nv_bfloat16* xin,
   const int nch = u->nchunk[l.lev];
   static bool dw_attr = false;
   if (!dw_attr) {
-    VOS_CUDA_TRY(cudaFuncSetAttribute(k_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)dw_smem_bytes(96, 16, 64)));
+    // the widest stage: 64-voxel boxes (any level at least 64 cells along x)
+    // and the layer with the most A tiles per CTA and output channels
+    size_t mx = 0;
+    for (const auto& s : kSpec) mx = std::max(mx, dw_smem_bytes(s.cin < 8 ? 8 : s.cin, s.cout, 64));
+    VOS_CUDA_TRY(cudaFuncSetAttribute(k_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
     dw_attr = true;
   }
   const int lx = u->lx[l.lev], ly = u->ly[l.lev], lz = u->lz[l.lev], w = dw_width(lx);

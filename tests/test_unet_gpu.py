@@ -182,13 +182,15 @@ def test_unet_gradients_match_oracle(env):
         net.close()
 
 
-@pytest.mark.parametrize("phys", [(8, 8, 12), (20, 24, 28)])
+@pytest.mark.parametrize("phys", [(8, 8, 12), (20, 24, 28), (4, 8, 256)])
 def test_unet_exact_on_dyadic_values(env, phys):
     """Weights k 2^-5 (|k| <= 2), r = +-1 (rms 1), eps in quarters, dz = +-1:
     every FP32 sum of the GPU is exact (or off in its last bit), so both
     sides round to BF16 identically and forward and gradients agree to FP32
     rounding.  The larger box spreads each weight gradient over several
-    voxel chunks of the tensor-core contraction, the last one partial."""
+    voxel chunks of the tensor-core contraction, the last one partial; the
+    256-wide box runs every level's weight gradient on 64-voxel stages
+    (the largest shared-memory footprint, four stages per finest row)."""
     torch, V = env
     g = np.random.default_rng(40)
     P = {}
