@@ -554,72 +554,140 @@ __device__ __forceinline__ double conv_flux(const Phys& P, int a, int i, int j, 
   return uf * (vU + vl_corr(vUU, vU, vD, has));
 }
 
-template <bool IVOS>
-__global__ void k_face_data(Phys P, int a, Box fb, const double* __restrict__ eps, const double* __restrict__ cold,
-                            const double* __restrict__ ua, double* __restrict__ cf, FaceData fd) {
+// Convective flux of every face of axis a (VoS-psi methods: no per-face
+// reactive data).
+__global__ void k_face_flux(Phys P, int a, Box fb, const double* __restrict__ cold, const double* __restrict__ ua,
+                            double* __restrict__ cf) {
   VOS_COUNT_EXEC();
   const Seg s = make_seg(fb);
-  const int nb = (P.dim == 2) ? 2 : 3;
-  const double kcx = P.kc / P.dx;
   VOS_SEG_LOOP(s, q) {
     int i, j, k;
     seg_decode(s, fb, q, i, j, k);
     if (i >= fb.mx) continue;
-    const long long fcx = i + (long long)fb.mx * (j + (long long)fb.my * k);
-    cf[fcx] = conv_flux(P, a, i, j, k, cold, ua);
-    if (!IVOS) continue;
-    int f[3] = {i, j, k};
-    const int m = f[a], n = ncell(P, a);
-    if (m < 1 || m > n - 1) {
-      fd.s[fcx] = 0.0;
-      fd.corr[fcx] = 0.0;
-      fd.evl[fcx] = 0.0;
-      continue;
+    cf[i + (long long)fb.mx * (j + (long long)fb.my * k)] = conv_flux(P, a, i, j, k, cold, ua);
+  }
+}
+
+// iVoS data of one interface face (i, j, k) of axis a: interior along a, with
+// a non-zero normal eps difference.
+__device__ __forceinline__ void ivos_face(const Phys& P, int a, const Box& fb, int i, int j, int k, double kcx,
+                                          const double* __restrict__ eps, const double* __restrict__ cold,
+                                          const FaceData& fd) {
+  const int nb = (P.dim == 2) ? 2 : 3;
+  const int n = ncell(P, a);
+  int f[3] = {i, j, k};
+  const int m = f[a];
+  int mc[3] = {i, j, k};
+  mc[a] -= 1;
+  const long long fcx = i + (long long)fb.mx * (j + (long long)fb.my * k);
+  const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
+  // gradient in eps differences (dx g): normal dn, tangential the mean of
+  // the two cells' centred components; n_a = -g_n / (|g| + 1e-8/dx)
+  // = -dn / (|dx g| + 1e-8)
+  const double dn = eps[cp] - eps[cm];
+  double g2 = dn * dn;
+  for (int b = 0; b < nb; ++b) {
+    if (b == a) continue;
+    const double tg = 0.25 * (cdiff(P, eps, b, mc[0], mc[1], mc[2]) + cdiff(P, eps, b, i, j, k));
+    g2 += tg * tg;
+  }
+  const double na = (__double_as_longlong(g2) != 0) ? -fdiv_nr(dn, sqrt(g2) + 1e-8) : -dn * 1e8;
+  const long long idn = __double_as_longlong(dn);
+  const bool pos = idn < 0 && (idn << 1) != 0;  // n_a > 0
+  // upwind U, downwind D, far upwind UU along a
+  int uu[3] = {i, j, k};
+  long long cU, cD;
+  bool has;
+  if (pos) {
+    cU = cm;
+    cD = cp;
+    uu[a] = m - 2;
+    has = m - 2 >= 0;
+  } else {
+    cU = cp;
+    cD = cm;
+    uu[a] = m + 1;
+    has = m + 1 <= n - 1;
+  }
+  const long long cUU = has ? cidx(P, uu[0], uu[1], uu[2]) : cU;
+  fd.s[fcx] = kcx * na;
+  fd.corr[fcx] = vl_corr(cold[cUU], cold[cU], cold[cD], has);
+  fd.evl[fcx] = eps[cU] + vl_corr(eps[cUU], eps[cU], eps[cD], has);
+}
+
+// iVoS: the convective flux of every face and the reactive data of the
+// interface faces.  About a fifth of the faces of a porous medium carry an
+// eps difference, but nearly every warp of 32 consecutive faces holds a few
+// of them, and their FP64 work (a square root, three quotients) would run at
+// a fraction of the warp's lanes.  So each block collects its interface faces
+// (eight row segments per pass) in shared memory and hands them to its first
+// threads: the FP64 instructions of that work run on full warps.  Every face
+// is computed by the same operations wherever it lands, and outside the
+// interface the data are written in the first pass (s = -0 marks "no
+// reactive flux" for the transport assembly and the rates).
+__global__ void __launch_bounds__(kThreads) k_face_data_ivos(Phys P, int a, Box fb, const double* __restrict__ eps,
+                                                            const double* __restrict__ cold,
+                                                            const double* __restrict__ ua, double* __restrict__ cf,
+                                                            FaceData fd) {
+  VOS_COUNT_EXEC();
+  __shared__ int sl_i[kThreads], sl_j[kThreads], sl_k[kThreads];
+  __shared__ int s_wc[kWarps];
+  const Seg s = make_seg(fb);
+  const int n = ncell(P, a);
+  const double kcx = P.kc / P.dx;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // block-uniform trip count: every thread reaches every barrier
+  for (long long q0 = (long long)blockIdx.x * kWarps; q0 < s.nseg; q0 += (long long)gridDim.x * kWarps) {
+    const long long q = q0 + warp;
+    bool iface = false;
+    int i = 0, j = 0, k = 0;
+    if (q < s.nseg) {
+      seg_decode(s, fb, q, i, j, k);
+      if (i < fb.mx) {
+        const long long fcx = i + (long long)fb.mx * (j + (long long)fb.my * k);
+        cf[fcx] = conv_flux(P, a, i, j, k, cold, ua);
+        int f[3] = {i, j, k};
+        const int m = f[a];
+        if (m < 1 || m > n - 1) {
+          fd.s[fcx] = 0.0;
+          fd.corr[fcx] = 0.0;
+          fd.evl[fcx] = 0.0;
+        } else {
+          int mc[3] = {i, j, k};
+          mc[a] -= 1;
+          const double dn = eps[cidx(P, i, j, k)] - eps[cidx(P, mc[0], mc[1], mc[2])];
+          if ((__double_as_longlong(dn) << 1) == 0) {
+            // no normal eps difference: n_a = -0, so s = -0 and the face
+            // carries no reactive flux; its correction and eps_vl are never
+            // read (the transport assembly and the rates skip s = +-0 faces)
+            fd.s[fcx] = -0.0;
+            fd.corr[fcx] = 0.0;
+            fd.evl[fcx] = 0.0;
+          } else {
+            iface = true;
+          }
+        }
+      }
     }
-    int mc[3] = {i, j, k};
-    mc[a] -= 1;
-    const long long cm = cidx(P, mc[0], mc[1], mc[2]), cp = cidx(P, i, j, k);
-    // gradient in eps differences (dx g): normal dn, tangential the mean of
-    // the two cells' centred components; n_a = -g_n / (|g| + 1e-8/dx)
-    // = -dn / (|dx g| + 1e-8)
-    const double dn = eps[cp] - eps[cm];
-    if ((__double_as_longlong(dn) << 1) == 0) {
-      // no normal eps difference: n_a = -0, so s = -0 and the face carries no
-      // reactive flux; its correction and eps_vl are never read (the transport
-      // assembly and the rates skip s = +-0 faces)
-      fd.s[fcx] = -0.0;
-      fd.corr[fcx] = 0.0;
-      fd.evl[fcx] = 0.0;
-      continue;
+    const unsigned bal = __ballot_sync(0xffffffffu, iface);
+    if (lane == 0) s_wc[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0, cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const int c = s_wc[w];
+      off += (w < warp) ? c : 0;
+      cnt += c;
     }
-    double g2 = dn * dn;
-    for (int b = 0; b < nb; ++b) {
-      if (b == a) continue;
-      const double tg = 0.25 * (cdiff(P, eps, b, mc[0], mc[1], mc[2]) + cdiff(P, eps, b, i, j, k));
-      g2 += tg * tg;
+    if (iface) {
+      const int slot = off + __popc(bal & ((1u << lane) - 1u));
+      sl_i[slot] = i;
+      sl_j[slot] = j;
+      sl_k[slot] = k;
     }
-    const double na = (__double_as_longlong(g2) != 0) ? -fdiv_nr(dn, sqrt(g2) + 1e-8) : -dn * 1e8;
-    const long long idn = __double_as_longlong(dn);
-    const bool pos = idn < 0 && (idn << 1) != 0;  // n_a > 0
-    // upwind U, downwind D, far upwind UU along a
-    int uu[3] = {i, j, k};
-    long long cU, cD;
-    bool has;
-    if (pos) {
-      cU = cm;
-      cD = cp;
-      uu[a] = m - 2;
-      has = m - 2 >= 0;
-    } else {
-      cU = cp;
-      cD = cm;
-      uu[a] = m + 1;
-      has = m + 1 <= n - 1;
-    }
-    const long long cUU = has ? cidx(P, uu[0], uu[1], uu[2]) : cU;
-    fd.s[fcx] = kcx * na;
-    fd.corr[fcx] = vl_corr(cold[cUU], cold[cU], cold[cD], has);
-    fd.evl[fcx] = eps[cU] + vl_corr(eps[cUU], eps[cU], eps[cD], has);
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) ivos_face(P, a, fb, sl_i[threadIdx.x], sl_j[threadIdx.x], sl_k[threadIdx.x], kcx, eps, cold, fd);
+    __syncthreads();  // the list and the counts are rewritten by the next pass
   }
 }
 
@@ -629,11 +697,11 @@ void launch_face_data(const Phys& P, int ivos, const double* eps, const double* 
   for (int a = 0; a < nb; ++a) {
     Box fb{P.nx + (a == 0), P.ny + (a == 1), P.nz + (a == 2)};
     if (ivos)
-      vlaunch("face_data", 64.0 * box_cells(fb), k_face_data<true>, grid_for(fb, 0), kThreads, st, P, a, fb, eps, cold,
+      vlaunch("face_data", 64.0 * box_cells(fb), k_face_data_ivos, grid_for(fb, 0), kThreads, st, P, a, fb, eps, cold,
               u[a], cf[a], fd[a]);
     else
-      vlaunch("face_data", 24.0 * box_cells(fb), k_face_data<false>, grid_for(fb, 0), kThreads, st, P, a, fb, eps, cold,
-              u[a], cf[a], fd[a]);
+      vlaunch("face_data", 24.0 * box_cells(fb), k_face_flux, grid_for(fb, 0), kThreads, st, P, a, fb, cold, u[a],
+              cf[a]);
   }
 }
 
@@ -795,7 +863,7 @@ __global__ void k_trans_assemble(Phys P, const double* __restrict__ eps, const d
         diag += a;
         offm[d] -= a;
       }
-      // convective fluxes through the plus and minus faces (k_face_data)
+      // convective fluxes through the plus and minus faces (k_face_flux / k_face_data_ivos)
       int fp[3] = {i, j, k};
       fp[d] += 1;
       adv += (cfs[d][fidx(P, d, fp[0], fp[1], fp[2])] - cfs[d][fidx(P, d, i, j, k)]) * idx1;
