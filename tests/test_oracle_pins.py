@@ -7,7 +7,9 @@ exact identities of the method (Sec. 2.3 conservative term, Sec. 2.4
 global area, Eq. mbs mass balance), and limiting cases (sharp interface,
 front speed of Eq. Ws).
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -586,6 +588,39 @@ def test_upscaled_surface_area_and_alpha():
     # a concentration vanishing on the surface cells lowers alpha
     st["c"][0, :, 9:13] = 0.0
     assert O.upscaled(st, prm)["alpha"] < 1e-12
+
+
+def _printed_tol(value, digits):
+    """Half a unit in the last significant digit of a printed value."""
+    e = math.floor(math.log10(abs(value)))
+    return 0.5 * 10.0 ** (e - digits + 1)
+
+
+def test_upscaled_reference_numbers_of_benchmark3():
+    """Sec. 3.3 worked example (tests/golden/bm3_ketton_reference_numbers.json):
+    from Table param3, the 1.7 mm sample radius, K = 16 D and phi = 0.173 the
+    paper obtains U = U_D / phi = 5.3e-3 m/s, L = sqrt(8 K / phi) = 27 um,
+    Pe = U L / D = 190 and Da = k_c / U = 4.4e-2.  A state with that porosity,
+    the Darcy velocity Q_i / (pi r^2) through the inlet and the Darcy pressure
+    profile of K gives these numbers back through the oracle to the printed
+    digits (12 for 8 in the length, U_D for U or Ki for Da each miss)."""
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "bm3_ketton_reference_numbers.json")))
+    inp, out, dig = g["inputs"], g["printed"], g["printed_significant_digits"]
+    darcy = 9.869233e-13
+    K0 = inp["K0_darcy"] * darcy
+    UD = inp["Q_i_m3_s"] / (math.pi * inp["sample_radius_m"] ** 2)
+    nz, ny, nx, dx = 3, 4, 10, 2.0e-5
+    prm = dict(dim=3, nx=nx, ny=ny, nz=nz, dx=dx, nu=inp["nu_m2_s"], D=inp["D_m2_s"], kc=inp["k_c_m_s"])
+    eps = np.full((nz, ny, nx), inp["phi0"])
+    u = [np.full((nz, ny, nx + 1), UD), np.zeros((nz, ny + 1, nx)), np.zeros((nz + 1, ny, nx))]
+    # Darcy's law in a uniform medium of permeability K0, outlet face at p = 0
+    xc = (np.arange(nx) + 0.5) * dx
+    p = np.broadcast_to(inp["nu_m2_s"] * UD / K0 * (nx * dx - xc), (nz, ny, nx)).copy()
+    st = dict(eps=eps, c=np.ones_like(eps), p=p, u=u)
+    up = O.upscaled(st, prm)
+    assert up["K"] == pytest.approx(K0, rel=1e-12)
+    for key, name in (("U_ref", "U_m_s"), ("L_ref", "L_m"), ("Pe", "Pe"), ("Da", "Da")):
+        assert abs(up[key] - out[name]) <= _printed_tol(out[name], dig[name]), (key, up[key], out[name])
 
 
 # ---------------------------------------------------------------- quasi-static variant (App. A, App. B)
