@@ -54,3 +54,42 @@ def test_reference_arm_two_ranks_rank0_prints():
                          "--gpus", "2", "--steps", "1", "--warmup", "0"])
     assert len(lines) == 1
     _check(lines[0], 2)
+
+
+def _bench_module():
+    # imported here, not at collection: importing bench.py sets the
+    # process's CUDA connection count, which only its own runs should see
+    import importlib
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    return importlib.import_module("bench")
+
+
+def test_clock_sampler_summary_from_samples():
+    """The clocks entry of the line: median SM clock under load, the largest
+    maximum clock seen, and every throttle reason seen active at least once
+    (a run that saw hw_slowdown, hw_thermal_slowdown or sw_thermal_slowdown
+    is not a valid measurement, sw_power_cap is noted); unparsable samples do
+    not enter the median."""
+    B = _bench_module()
+    cs = B.ClockSampler(0)
+    na, act = "Not Active", "Active"
+    cs.rows = [["2070", "2070", "910.2", na, na, na, act],
+               ["1995", "2070", "1013.0", na, na, na, na],
+               ["[N/A]", "2070", "[N/A]", na, na, na, na],
+               ["2040", "2070", "980.0", na, act, na, na]]
+    out = cs.stop()
+    assert out["sm_mhz"] == 2040.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 4
+    assert out["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    empty = B.ClockSampler(0).stop()
+    assert empty["sm_mhz"] is None and empty["reasons"] == [] and empty["samples"] == 0
+
+
+def test_measured_peaks_fallback(tmp_path, monkeypatch):
+    """Without MEASURED_PEAKS.json the HBM roofline takes the 6.8 TB/s
+    fallback and says so; with it, the file's measured copy bandwidth."""
+    B = _bench_module()
+    monkeypatch.setattr(B, "ROOT", str(tmp_path))
+    assert B.measured_peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6663.2}))
+    assert B.measured_peaks() == (6663.2, "measured")
