@@ -21,7 +21,9 @@ __all__ = [
     "vos_device_fields_get", "vos_get_stats", "vos_suggest_dt", "vos_upscaled", "vos_last_error", "vos_destroy",
     "vos_device_bytes", "vos_kernel_launches", "vos_set_launch_mode", "vos_set_coarse_cycle", "vos_set_vector_sweeps",
     "vos_set_fused_pcg", "vos_prof_enable", "vos_prof_report", "vos_prof_reset",
-    "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_destroy",
+    "vos_suggest_dt_noalloc", "vos_batch_create", "vos_batch_step", "vos_batch_handle", "vos_batch_destroy",
+    "vos_unet_create", "vos_unet_num_params", "vos_unet_set_params", "vos_unet_get_params", "vos_unet_get_grads",
+    "vos_unet_forward", "vos_unet_backward", "vos_unet_train_step", "vos_unet_eval_loss", "vos_unet_destroy",
     "vos_floating_clusters", "vos_tile_config", "vos_fp64_div_check", "vos_conv3d_bf16", "UNet", "vos_set_unet_preconditioner",
     "vos_unet_solve_stats", "vos_pressure_snapshots", "Simulation", "LIB_PATH", "EXPORTED_SYMBOLS", "PRECOND_NO_DEFLATION",
     "PRECOND_MOM_DIAG", "PRECOND_MOM_MG", "PRECOND_P_WARM", "PRECOND_U_EXTRAP", "FUSED_DIAG_PCG", "FUSED_MG_PCG", "FUSED_DF_RESIDUAL", "FUSED_ALL",
@@ -29,7 +31,7 @@ __all__ = [
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libvos.so")
 
-VOS_OK, VOS_EINVAL, VOS_ENOMEM, VOS_ECUDA, VOS_ENOCONV = 0, -1, -2, -3, -4
+VOS_OK, VOS_EINVAL, VOS_ENOMEM, VOS_ECUDA, VOS_ENOCONV, VOS_ETIMEOUT = 0, -1, -2, -3, -4, -5
 F_EPS, F_C, F_U, F_V, F_W, F_P, F_R, F_RF = 1, 2, 4, 8, 16, 32, 64, 128
 F_ALL = 255
 PRECOND_NO_DEFLATION = 1
@@ -529,6 +531,50 @@ class UNet:
             pass
 
 
+# The vos_unet_* calls under their C names (the UNet class carries the
+# marshalling; a network is a UNet object).
+def vos_unet_create(shape, train=True, stream=None):
+    """vos_unet_create: a network for grids of shape (nz, ny, nx)."""
+    return UNet(shape, train=train, stream=stream)
+
+
+def vos_unet_num_params():
+    return UNet.num_params()
+
+
+def vos_unet_set_params(net, flat):
+    net.set_params(flat)
+
+
+def vos_unet_get_params(net):
+    return net.get_params()
+
+
+def vos_unet_get_grads(net):
+    return net.get_grads()
+
+
+def vos_unet_forward(net, r, eps, z):
+    net.forward(r, eps, z)
+
+
+def vos_unet_backward(net, dz):
+    net.backward(dz)
+
+
+def vos_unet_train_step(net, h, r, lr):
+    return net.train_step(h, r, lr)
+
+
+def vos_unet_eval_loss(net, h, r):
+    return net.eval_loss(h, r)
+
+
+def vos_unet_destroy(net):
+    if net is not None:
+        net.close()
+
+
 def vos_set_unet_preconditioner(h, net):
     lib = load_library()
     _raise(lib, lib.vos_set_unet_preconditioner(h.ptr, net.ptr if net is not None else None), h.ptr)
@@ -622,9 +668,21 @@ def vos_batch_create(eps_list, prm_list, stream=None, nthreads=8, allocator="aut
     b = _Batch(out, [dict(p) for p in prm_list], keep)
     for i in range(n):
         hp = ctypes.c_void_p()
-        lib.vos_batch_handle(out, i, ctypes.byref(hp))
+        rc = lib.vos_batch_handle(out, i, ctypes.byref(hp))
+        if rc != VOS_OK:
+            msg = lib.vos_last_error(None).decode()
+            lib.vos_batch_destroy(out)
+            raise VosError(rc, msg)
         b.handles.append(_Handle(hp, prm_list[i], []))
     return b
+
+
+def vos_batch_handle(b, i):
+    """vos_batch_handle: instance i's handle, owned by the batch (do not
+    destroy it, nor use it while a batch step runs)."""
+    if b is None or not b.ptr or not 0 <= int(i) < len(b.handles):
+        raise VosError(VOS_EINVAL, "vos_batch_handle: bad argument")
+    return b.handles[int(i)]
 
 
 def vos_batch_step(b, dts):

@@ -39,6 +39,20 @@ def test_library_exports_every_declared_symbol(lib):
     assert sorted(vos.EXPORTED_SYMBOLS) == names
 
 
+def test_binding_has_every_declared_call_under_its_name():
+    """The Python binding offers each C entry point under the same name."""
+    from paper_2204_07019_gb300 import vos
+    names = _declared()
+    missing = [n for n in names if not callable(getattr(vos, n, None)) or n not in vos.__all__]
+    assert not missing, missing
+
+
+def test_batch_handle_rejects_bad_index_without_gpu():
+    from paper_2204_07019_gb300 import vos
+    with pytest.raises(vos.VosError):
+        vos.vos_batch_handle(None, 0)
+
+
 def test_struct_layout_matches_c(tmp_path):
     from paper_2204_07019_gb300 import vos
     src = tmp_path / "probe.c"
